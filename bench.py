@@ -1,0 +1,392 @@
+#!/usr/bin/env python
+"""Benchmark of the MFETI-DP1 Maxwell field-solve time step on GB300.
+
+One "step" is one implicit Newmark time step of the edge-element wave
+equation solved by MFETI-DP1 (right-hand side SpMV, local solves, interface
+CG with the corner coarse problem, recovery): every stage of the hot path.
+
+Default workload: the mixed-precision configuration -- a PEC unit cube of
+48^3 Kuhn cubes (663,552 tets, 753,552 interior edge unknowns) torn into
+8x8x8 = 512 subdomains, Gaussian z-line pulse (t0 = 20 dt, sigma = 6 dt),
+dt = 2x the explicit CFL limit.  Both precisions are timed on the same GPU:
+the JSON line's `value` is the mixed-precision (FP32 application + FP64
+refinement) rate, `fp64` holds the plain FP64 DD rate, and
+`rel_err_mixed_vs_fp64` the relative L2 difference of the two fields after
+the last step.  Inputs (14 GB of dense subdomain operators) are far larger
+than L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--config 1..5]
+
+With --gpus N > 1 (launched by torchrun) every rank runs an independent
+replica of the workload (the field solve uses one GPU; replicas only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DD field-solve steps/s, mixed vs FP64 at rel err 1e-8; % of HBM/tensor roofline"
+FALLBACK_HBM_GBS = 6800.0
+FP64_NOMINAL_TFLOPS = 1.25   # nominal GB300 FP64 rate (CUDA-core FMA)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=4)
+    ap.add_argument("--tol64", type=float, default=1e-10, help="interface CG tolerance, FP64 DD")
+    ap.add_argument("--tol32", type=float, default=1e-5, help="inner interface CG tolerance, mixed")
+    ap.add_argument("--refine-tol", type=float, default=1e-10, help="FP64 step-residual target, mixed")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_dt(cfg):
+    table = json.load(open(os.path.join(ROOT, "tests", "golden", "cfl_dt.json")))
+    return table[f"config{cfg}"]["dt"]
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured", d
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback", {}
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        self.lines += [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# CPU baseline: the oracle's DD solver on a bounded sample of the workload
+# ----------------------------------------------------------------------------
+
+def cpu_baseline(cfg, dt, full_iters, n_sub_full, n_steps=6):
+    """Times the CPU FP64 oracle (scipy/numpy, host cores) on a sample of the
+    workload: a 2x2x2 block of subdomains cut from the same mesh (same h, same
+    6^3-cube subdomain blocks, same dt), PEC on the sample's walls.  The per-step
+    time is scaled to the full workload by the subdomain count and by the number
+    of local solves per step (2 + 3 per interface iteration, oracle algorithm),
+    using the GPU-measured iterations of the full workload."""
+    from oracle import dd as odd
+    from oracle import fem
+    from paper_2204_13254_gb300 import workloads as W
+    wf = W.config(cfg)
+    nx, ny, nz = wf.dims
+    kx = ky = kz = round(n_sub_full ** (1 / 3)) if cfg in (1, 4) else None
+    if kx is None:
+        kx, ky, kz = {2: (4, 4, 8), 5: (8, 8, 4), 3: (4, 4, 4)}[cfg]
+    bx, by, bz = nx // kx, ny // ky, nz // kz
+    L = (2 * bx * wf.L[0] / nx, 2 * by * wf.L[1] / ny, 2 * bz * wf.L[2] / nz)
+    w = W.box(2 * bx, 2 * by, 2 * bz, 2, 2, 2, L=L, steps=n_steps)
+    t0 = time.perf_counter()
+    space = fem.EdgeSpace(w.xyz, w.tets)
+    maps = odd.DDMaps(space, w.part, w.n_sub)
+    src = np.zeros(space.n)
+    src[space.dof_of_pairs(w.source_pairs)] = 1.0
+    t_setup = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    out = odd.run(space, maps, dt, src, w.d2G(dt, n_steps), n_steps, tol=1e-10)
+    t_run = time.perf_counter() - t1
+    it_s = float(np.mean(out["iters"]))
+    t_step = t_run / n_steps           # includes the factorisation share of the sample
+    scale = (n_sub_full / 8.0) * (2.0 + 3.0 * full_iters) / (2.0 + 3.0 * max(it_s, 1.0))
+    t_full = t_step * scale
+    threads = os.environ.get("OMP_NUM_THREADS") or os.environ.get("OPENBLAS_NUM_THREADS") or str(os.cpu_count())
+    return {
+        "value": 1.0 / t_full, "unit": "steps/s", "cores": int(threads), "kind": "oracle",
+        "sample": (f"CPU FP64 oracle DD (scipy Cholesky per subdomain + CG on Eq. f1schur, tol 1e-10) on a "
+                   f"{2*bx}x{2*by}x{2*bz}-cube sample (2x2x2 subdomains of the same size and h), {n_steps} steps "
+                   f"incl. its factorisation: {t_step:.3f} s/step, {it_s:.1f} CG it/step; scaled x{scale:.1f} "
+                   f"(subdomains {n_sub_full}/8, local solves at {full_iters:.1f} it/step)"),
+        "sample_s": t_run + t_setup, "os_cpu_count": os.cpu_count(),
+    }
+
+
+# ----------------------------------------------------------------------------
+# GPU leg
+# ----------------------------------------------------------------------------
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_2204_13254_gb300 import dd as D
+    from paper_2204_13254_gb300 import workloads as W
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = args.config
+    w = W.config(cfg)
+    dt = load_dt(cfg)
+    K, Wu = args.steps, args.warmup
+    t0 = time.perf_counter()
+    fs = D.FieldSolver(w.xyz, w.tets, w.part, w.n_sub, w.eps, w.mu,
+                       D.make_params(precision=D.DD_FP64, tol=args.tol64), device=dev).bind()
+    t_setup = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fs.factor(dt)
+    torch.cuda.synchronize()
+    t_factor = time.perf_counter() - t0
+    n = fs.n_dof
+    dofs = torch.tensor(fs.dof_of_pairs(w.source_pairs), device=dev)
+    d2g = w.d2G(dt, Wu + K)
+    D2G = torch.zeros((Wu + K, n), dtype=torch.float64, device=dev)
+    for k in range(Wu + K):
+        D2G[k, dofs] = float(d2g[k])
+    zero = torch.zeros(n, dtype=torch.float64, device=dev)
+    e_out = torch.empty(n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def timed(params, clocks):
+        fs.set_params(params)
+        fs.set_state(zero, zero, 0)
+        for k in range(Wu):
+            fs.step(D2G[k], stats=True)
+        barrier()
+        torch.cuda.synchronize()
+        fs.profile(enable=1, read=False)
+        clocks.start()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        its, refs = [], []
+        for k in range(K):
+            st = fs.step(D2G[Wu + k], stats=True)
+            its.append(st["iters"])
+            refs.append(st["refinements"])
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        clocks.stop()
+        barrier()
+        ms = ev0.elapsed_time(ev1)
+        prof = fs.profile(enable=0, read=True)
+        e_last, _, _ = fs.get_state()
+        return ms, np.array(its), np.array(refs), prof, e_last.clone()
+
+    clocks = Clocks(local)
+    p64 = D.make_params(precision=D.DD_FP64, tol=args.tol64)
+    p32 = D.make_params(precision=D.DD_MIXED, tol=args.tol32, refine_tol=args.refine_tol, max_refine=6)
+    ms64, it64, _, prof64, e64 = timed(p64, clocks)
+    ms32, it32, ref32, prof32, e32 = timed(p32, clocks)
+    rel = float(torch.linalg.norm(e32 - e64) / torch.linalg.norm(e64))
+
+    # end-to-end: per step, H2D of the source from pinned host memory, the C-ABI step, D2H of e^{n+1}
+    host_src = torch.zeros((K, n), dtype=torch.float64).pin_memory()
+    host_src.copy_(D2G[Wu:].cpu())
+    host_e = torch.empty(n, dtype=torch.float64).pin_memory()
+    dsrc = torch.empty(n, dtype=torch.float64, device=dev)
+    fs.set_params(p32)
+    fs.set_state(zero, zero, 0)
+    for k in range(Wu):
+        fs.step(D2G[k], stats=False)
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for k in range(K):
+        dsrc.copy_(host_src[k], non_blocking=True)
+        fs.step(dsrc, e_out, stats=False)
+        host_e.copy_(e_out, non_blocking=True)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = ev0.elapsed_time(ev1)
+
+    def allmax(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    ms64, ms32, ms_e2e = allmax(ms64), allmax(ms32), allmax(ms_e2e)
+    sizes = fs.sizes
+    res = dict(fs=fs, K=K, ms64=ms64, ms32=ms32, ms_e2e=ms_e2e, it64=it64, it32=it32, ref32=ref32, prof64=prof64,
+               prof32=prof32, rel=rel, t_setup=t_setup, t_factor=t_factor, clocks=clocks.summary(), sizes=sizes,
+               workload=w, dt=dt)
+    return res
+
+
+def stage_table(prof, K):
+    out = {}
+    for name, st in prof["stages"].items():
+        if st["launches"] == 0:
+            continue
+        gbs = st["bytes"] / (st["ms"] * 1e6) if st["ms"] > 0 else None
+        out[name] = {"ms_per_step": st["ms"] / K, "launches_per_step": st["launches"] / K,
+                     "full_launches_per_step": st["work"] / K, "algorithmic_GB_per_step": st["bytes"] / K / 1e9,
+                     "achieved_GBs": gbs}
+    return out
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if args.impl == "ours":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    if args.impl == "reference":
+        if rank == 0:
+            dt = load_dt(args.config)
+            from paper_2204_13254_gb300 import workloads as W
+            n_sub = W.config(args.config).n_sub
+            iters = 30.0
+            cb = cpu_baseline(args.config, dt, iters, n_sub)
+            line = {"metric": METRIC, "impl": "reference", "value": cb["value"], "unit": "steps/s", "n_gpus": 0,
+                    "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / cb["value"],
+                    "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                    "data": "synthetic", "config": {"workload": W.config(args.config).name},
+                    "cpu_baseline": cb,
+                    "e2e": {"value": cb["value"], "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            print(json.dumps(line), flush=True)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    r = run_ours(args, rank, world, local)
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    K = r["K"]
+    peak, peak_kind, peaks = load_peaks()
+    st32 = stage_table(r["prof32"], K)
+    st64 = stage_table(r["prof64"], K)
+    dom = max(st32, key=lambda k: st32[k]["ms_per_step"] if k not in ("vector", "factor") else -1)
+    d = st32[dom]
+    achieved = d["achieved_GBs"]
+    sizes = r["sizes"]
+    w = r["workload"]
+    value = world * K / (r["ms32"] / 1e3)
+    v64 = world * K / (r["ms64"] / 1e3)
+    cb = None
+    if world == 1 and not args.no_cpu_baseline:
+        try:
+            cb = cpu_baseline(args.config, r["dt"], float(np.mean(r["it32"])), w.n_sub)
+        except Exception as ex:  # the baseline is context only; never fail the GPU line on it
+            cb = {"error": repr(ex)[:200]}
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        try:
+            tj = json.load(open(tpath))
+            traffic = tj.get(f"config{args.config}", {}).get(dom)
+        except Exception:
+            traffic = None
+    line = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": r["ms32"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": (f"{w.name}: PEC box {w.dims[0]}x{w.dims[1]}x{w.dims[2]} Kuhn cubes, {len(w.tets)} tets, "
+                                f"{sizes.n_dof} edge dofs, {w.n_sub} subdomains, {sizes.n_lambda} multipliers, "
+                                f"{sizes.n_corner} corners, Gaussian z-line pulse, dt=2xCFL={r['dt']:.6g}"),
+                   "l2_policy": "inputs larger than L2 (dense subdomain operators "
+                                f"{sizes.dense_bytes_fp64 / 1e9:.1f} GB FP64 + half that FP32), no flush",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "mixed": {"steps_per_s": value, "ms_per_step": r["ms32"] / K, "iters_per_step": float(np.mean(r["it32"])),
+                  "refinements_per_step": float(np.mean(r["ref32"])), "inner_tol": args.tol32,
+                  "refine_tol": args.refine_tol, "stages": st32},
+        "fp64": {"steps_per_s": v64, "ms_per_step": r["ms64"] / K, "iters_per_step": float(np.mean(r["it64"])),
+                 "tol": args.tol64, "stages": st64},
+        "speedup_mixed_vs_fp64": value / v64,
+        "rel_err_mixed_vs_fp64": r["rel"],
+        "setup_s": r["t_setup"], "factor_s": r["t_factor"],
+        "roofline": {"bound": "hbm", "kernel": f"k_gemv<float> ({dom})", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "peak_source": f"{peak_kind} hbm_gbs" + ("" if peak_kind == "measured" else " (no MEASURED_PEAKS.json)")},
+        "cpu_baseline": cb,
+        "e2e": {"value": world * K / (r["ms_e2e"] / 1e3), "unit": "steps/s",
+                "h2d_bytes_per_step": int(sizes.n_dof * 8), "d2h_bytes_per_step": int(sizes.n_dof * 8)},
+        "gpu_launches": int(r["prof32"]["total_launches"]),
+        "clocks": r["clocks"],
+    }
+    print(json.dumps(line), flush=True)
+    r["fs"].close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,250 @@
+/*
+ * dd.h -- C ABI of the GB300 MFETI-DP1 Maxwell field-solve library (libdd.so).
+ *
+ * The library advances the implicit Newmark-beta (gamma = 1/2, beta = 1/4)
+ * time march of the Whitney edge-element wave equation on a tetrahedral mesh
+ * (Sec. II-B, Eq. maxnmb, edge-only reading) and solves every time step with
+ * the MFETI-DP1 domain decomposition (Sec. III-A: tearing into subdomains,
+ * local eliminations Eq. rF1, interface system Eq. F1lr, corner system
+ * Eq. F1uc, Schur-complement interface system Eq. f1schur) on one GPU.
+ *
+ * Per step, with A = T + (dt^2/4) S and B = 2T - (dt^2/2) S,
+ *     A e^{n+1} = B e^n - A e^{n-1} - (g^{n+1} - 2 g^n + g^{n-1}),
+ * where e are the interior (non-PEC) edge unknowns, T the mass and S the
+ * curl-curl matrix, and g_i(t) = <W_i, G(t)> the tested integrated current
+ * G = int_0^t J (Sec. II-A).
+ *
+ * Conventions for every entry point:
+ *   - The return value is a status code (DD_OK = 0 or one of DD_ERR_*).  No
+ *     C++ exception or abort crosses this boundary; dd_last_error() returns a
+ *     readable message for the last failure on a handle.
+ *   - "host" pointers are CPU memory, read during the call and not retained.
+ *     "device" pointers are GPU global memory owned by the caller (for
+ *     instance torch tensors); the library never frees them.
+ *   - All device memory the library uses (matrices, maps, vectors) lives in
+ *     one caller-allocated workspace bound with dd_bind_workspace().  The
+ *     handle itself owns only host metadata.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are stream-ordered; a call that returns statistics to
+ *     the host synchronises that stream.
+ *   - Unknown numbering: mesh edges are the distinct node pairs (lo, hi),
+ *     lo < hi, sorted lexicographically and oriented lo -> hi.  Edges lying in
+ *     a boundary triangle are removed (PEC wall).  The remaining "dofs" keep
+ *     the global edge order.
+ */
+#ifndef DD_H
+#define DD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define DD_OK 0
+#define DD_ERR_ARG 1             /* bad argument (NULL, size, range)               */
+#define DD_ERR_MESH 2            /* degenerate or inverted tetrahedron             */
+#define DD_ERR_PARTITION 3       /* empty subdomain or subdomain without r dofs   */
+#define DD_ERR_NOT_SPD 4         /* non-positive pivot while factoring            */
+#define DD_ERR_NO_CONVERGENCE 5  /* interface CG did not reach tol in max_it      */
+#define DD_ERR_NONFINITE 6       /* NaN/Inf in a residual                          */
+#define DD_ERR_TIMEOUT 7         /* a bounded device wait expired                  */
+#define DD_ERR_CUDA 8            /* a CUDA runtime call failed                     */
+#define DD_ERR_STATE 9           /* call out of order (e.g. step before factor)   */
+
+/* ---- precision modes ------------------------------------------------- */
+#define DD_FP64 0   /* every per-step operation in FP64                                   */
+#define DD_MIXED 1  /* FP32 local/interface/coarse application, FP64 residual refinement  */
+
+typedef struct dd_handle dd_handle;
+
+/* Tetrahedral mesh (host arrays, copied during dd_setup).
+ * xyz  [n_nodes*3] node coordinates, x fastest.
+ * tets [n_tets*4]  node ids of each tet; any vertex order (orientation is
+ *                  taken from the sign of the volume, which must be non-zero).
+ * eps  [n_tets]    relative permittivity per tet, or NULL for 1.
+ * mu               relative permeability (uniform). */
+typedef struct {
+    int64_t n_nodes;
+    int64_t n_tets;
+    const double* xyz;
+    const int32_t* tets;
+    const double* eps;
+    double mu;
+} dd_mesh;
+
+/* Solver parameters.
+ * tol        relative residual of the interface CG (Eq. f1schur):
+ *            stop when ||r_k||_2 <= tol * ||rhs||_2.
+ * max_it     CG iteration cap per solve.
+ * precond    0 = none, 1 = Jacobi (diagonal of F_rr; the paper's diagonal
+ *            preconditioner of Sec. III-C).
+ * warm_start 1 = start each interface solve from the previous multipliers.
+ * refine_tol DD_MIXED only: stop refining a step when the FP64 residual of the
+ *            step's linear system satisfies ||r||_2 <= refine_tol * ||b||_2.
+ * max_refine DD_MIXED only: cap on FP32 correction solves per step.
+ * chunk      CG iterations issued between two convergence checks. */
+typedef struct {
+    int precision;
+    double tol;
+    int max_it;
+    int precond;
+    int warm_start;
+    double refine_tol;
+    int max_refine;
+    int chunk;
+} dd_params;
+
+/* Sizes of a set-up problem. */
+typedef struct {
+    int64_t n_edges;        /* mesh edges                                     */
+    int64_t n_dof;          /* interior (non-PEC) edges = unknowns            */
+    int32_t n_sub;          /* subdomains N_v                                 */
+    int64_t n_lambda;       /* Lagrange multipliers (edges shared by 2 subdomains) */
+    int64_t n_corner;       /* corner unknowns (edges shared by >= 3 subdomains)   */
+    int64_t n_local;        /* sum over subdomains of local unknowns          */
+    int64_t nnz_local;      /* nonzeros of the subassembled local matrices    */
+    int32_t max_nr;         /* largest local r block                          */
+    int32_t max_ns;         /* largest local system (r + c)                   */
+    size_t workspace_bytes; /* bytes dd_bind_workspace needs                  */
+    int64_t dense_bytes_fp64; /* bytes of the per-subdomain dense operators   */
+} dd_sizes;
+
+/* Tearing maps, written to caller-allocated host arrays (any may be NULL).
+ * Lengths follow dd_sizes.  Local order inside subdomain s is
+ * [interior (m=1), interface r (m=2), corner (m>=3)], each sorted by dof id.
+ *   edges      [n_edges*2] int64  (lo, hi) node ids
+ *   dof_edge   [n_dof]     int64  mesh edge id of each dof
+ *   sub_ptr    [n_sub+1]   int64  offsets of each subdomain in local_dof
+ *   local_dof  [n_local]   int64  dof id of each local unknown
+ *   n_int, n_gam, n_cor [n_sub] int32  sizes of the three local groups
+ *   mult_dof   [n_lambda]  int64  dof of each multiplier (global edge order)
+ *   mult_sub   [n_lambda*2] int32 (s1, s2), s1 < s2; B_r is +1 in s1, -1 in s2
+ *   mult_loc   [n_lambda*2] int32 local index of the dof in s1 and in s2
+ *   corner_dof [n_corner]  int64  dof of each corner (global edge order)
+ *   owner      [n_dof]     int32  lowest subdomain containing the dof */
+typedef struct {
+    int64_t* edges;
+    int64_t* dof_edge;
+    int64_t* sub_ptr;
+    int64_t* local_dof;
+    int32_t* n_int;
+    int32_t* n_gam;
+    int32_t* n_cor;
+    int64_t* mult_dof;
+    int32_t* mult_sub;
+    int32_t* mult_loc;
+    int64_t* corner_dof;
+    int32_t* owner;
+} dd_maps;
+
+/* Per-call statistics (host struct).  iters = interface CG iterations summed
+ * over the solves of the call; refinements = FP32 correction solves
+ * (DD_MIXED); resid = final relative residual (interface CG for DD_FP64, step
+ * system for DD_MIXED); status = DD_OK or the error the call returned. */
+typedef struct {
+    int iters;
+    int refinements;
+    double resid;
+    int status;
+} dd_stats;
+
+/* Build the tearing (Sec. III-A) on the host: edges, PEC removal, element
+ * matrices, multiplicities, local numbering, B_r / B_c, local CSR matrices.
+ * part [n_tets] (host) gives the subdomain 0..n_sub-1 of every tet.
+ * params may be NULL (defaults: FP64, tol 1e-12, max_it 500, Jacobi, warm
+ * start, refine_tol 1e-12, max_refine 4, chunk 8).  On success *out owns a new
+ * handle (free with dd_destroy).  Errors: DD_ERR_ARG, DD_ERR_MESH,
+ * DD_ERR_PARTITION.  No GPU work is done. */
+int dd_setup(const dd_mesh* mesh, const int32_t* part, int32_t n_sub, const dd_params* params,
+             dd_handle** out);
+
+/* Change solver parameters of an existing handle (precision needs a
+ * workspace large enough for it: the workspace is always sized for both). */
+int dd_set_params(dd_handle* h, const dd_params* params);
+
+int dd_get_sizes(const dd_handle* h, dd_sizes* out);
+int dd_get_maps(const dd_handle* h, dd_maps* out);
+
+/* Probe points (host [n_probe*3]); replaces any previous set.  A point is
+ * located in the lowest-id tet whose barycentric coordinates are all
+ * >= -1e-12.  Errors: DD_ERR_ARG if a point lies outside the mesh. */
+int dd_set_probes(dd_handle* h, int32_t n_probe, const double* xyz);
+
+/* Bind the caller-allocated device workspace (>= workspace_bytes, 256-byte
+ * aligned) and upload the maps into it.  Synchronises `stream`.  The
+ * workspace must stay allocated until dd_destroy. */
+int dd_bind_workspace(dd_handle* h, void* dev_ptr, size_t bytes, void* stream);
+
+/* Factor for time step dt (Sec. III-C: one inverse per subdomain kept in
+ * memory): assemble the dense local A^(s) = T^(s) + dt^2/4 S^(s), eliminate
+ * its r block in FP64 to obtain A_rr^-1, A_rr^-1 A_rc and the local corner
+ * Schur complements, assemble and invert K~cc, build the Jacobi diagonal, and
+ * (always) FP32 copies for DD_MIXED.  Resets the time level to n = 0 with
+ * e^0 = e^{-1} = 0.  Synchronises `stream`.  Errors: DD_ERR_STATE (no
+ * workspace), DD_ERR_NOT_SPD, DD_ERR_CUDA. */
+int dd_factor(dd_handle* h, double dt, void* stream);
+
+/* One time step: e^{n+1} from (e^n, e^{n-1}) and the source.
+ * d2g  device [n_dof] second difference g^{n+1} - 2 g^n + g^{n-1} of the tested
+ *      integrated current, or NULL for no source.
+ * e_out device [n_dof] receives e^{n+1}, or NULL.
+ * stats host, or NULL.  With stats == NULL and DD_FP64 the call only
+ *      synchronises to poll CG convergence between chunks of iterations.
+ * Errors: DD_ERR_STATE (not factored), DD_ERR_NO_CONVERGENCE (fields are
+ * still advanced with the last iterate), DD_ERR_NONFINITE, DD_ERR_CUDA. */
+int dd_step(dd_handle* h, const double* d2g, double* e_out, dd_stats* stats, void* stream);
+
+/* Apply the Schur-complement interface operator of Eq. f1schur,
+ * out = (F_rr + F_rc K~cc^-1 F_rc^T) lam, in FP64 with the factors of the last
+ * dd_factor.  lam, out: device [n_lambda]. */
+int dd_schur_apply(dd_handle* h, const double* lam, double* out, void* stream);
+
+/* Evaluate E = sum_i e_i W_i at the probe points for the current e^n.
+ * out: device [n_probe*3] (x, y, z per probe). */
+int dd_probe(dd_handle* h, double* out, void* stream);
+
+/* Read / write the time levels (e^n, e^{n-1}), device [n_dof] each, and the
+ * step counter (checkpoint / resume).  dd_set_state also clears the CG warm
+ * start. */
+int dd_get_state(const dd_handle* h, double* e_n, double* e_nm1, int64_t* step, void* stream);
+int dd_set_state(dd_handle* h, const double* e_n, const double* e_nm1, int64_t step, void* stream);
+
+/* Per-stage timing of the library's own kernels (CUDA events recorded on the
+ * launch stream around every launch while enabled).
+ * Stages: 0 right-hand side SpMV, 1 local solve GEMV (A_rr^-1 b_r),
+ * 2 interface operator GEMV (F_rr / F_rc^T pieces), 3 coarse K~cc^-1 GEMV,
+ * 4 corner coupling GEMV (F_rc pieces), 5 recovery GEMV (Eq. rF1),
+ * 6 interface/corner vector kernels (jumps, gathers, CG updates),
+ * 7 FP64 refinement residual, 8 factorisation kernels.
+ * launches   kernels launched (including ones that exit early after convergence)
+ * work       launches that did their full work
+ * ms         summed event time of all launches of the stage
+ * bytes      algorithmic bytes of the launches that did full work (matrix
+ *            elements read at the stage's precision + vectors read and written)
+ * total_launches  every kernel launched by the library since the last reset. */
+#define DD_N_STAGES 9
+typedef struct {
+    int64_t launches[DD_N_STAGES];
+    int64_t work[DD_N_STAGES];
+    double ms[DD_N_STAGES];
+    double bytes[DD_N_STAGES];
+    int64_t total_launches;
+} dd_profile_stats;
+
+/* enable: 1 = reset counters and start recording events, 0 = stop recording,
+ * -1 = leave as is.  out (host, may be NULL) receives the accumulated numbers
+ * (synchronises `stream`).  Launch counting is always on; event timing only
+ * while enabled. */
+int dd_profile(dd_handle* h, int enable, dd_profile_stats* out, void* stream);
+
+void dd_destroy(dd_handle* h);
+const char* dd_last_error(const dd_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DD_H */

@@ -92,14 +92,21 @@ def gauss_residual(D0, T, e, q=None):
     return r if q is None else r + q
 
 
-def cfl_dt(T, S, tol=1e-10):
+def cfl_dt(T, S, tol=1e-9):
     """Explicit (central-difference, consistent-mass) stability limit 2/sqrt(lambda_max(T^-1 S)).
 
-    lambda_max by ARPACK on the symmetric-definite pencil (S, T); T^-1 is applied
-    through a sparse LU of T.
+    lambda_max by ARPACK (Lanczos) on the symmetric-definite pencil (S, T); T^-1
+    is applied by conjugate gradients (T is a well-conditioned mass matrix), so
+    no sparse factorisation is needed at large sizes.
     """
-    Tc = T.tocsc()
-    lu = spla.splu(Tc)
-    Minv = spla.LinearOperator(T.shape, matvec=lu.solve, dtype=np.float64)
-    lam = spla.eigsh(S, k=1, M=Tc, Minv=Minv, which="LA", tol=tol, return_eigenvectors=False)
+    Tc = T.tocsr()
+    d = Tc.diagonal()
+    M = spla.LinearOperator(T.shape, matvec=lambda v: v / d, dtype=np.float64)
+
+    def tinv(v):
+        x, info = spla.cg(Tc, v, rtol=1e-13, atol=0.0, maxiter=2000, M=M)
+        assert info == 0
+        return x
+    Minv = spla.LinearOperator(T.shape, matvec=tinv, dtype=np.float64)
+    lam = spla.eigsh(S, k=1, M=Tc, Minv=Minv, which="LA", tol=tol, ncv=32, return_eigenvectors=False)
     return 2.0 / np.sqrt(float(lam[0]))

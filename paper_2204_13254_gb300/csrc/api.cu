@@ -1,0 +1,677 @@
+// C ABI entry points (include/dd.h): handle lifecycle, workspace layout, the
+// factorisation sequence and the per-step MFETI-DP1 solve (Sec. III-A).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "dd_internal.h"
+
+namespace {
+
+int cuda_fail(dd_handle* h, int code, const char* what) {
+    h->err = std::string(what) + ": " + cudaGetErrorString((cudaError_t)code);
+    return DD_ERR_CUDA;
+}
+
+#define CK(h, expr, what)                                     \
+    do {                                                      \
+        int rc_ = (expr);                                     \
+        if (rc_ != 0) return cuda_fail((h), rc_, (what));     \
+    } while (0)
+
+dd_params default_params() {
+    dd_params p;
+    p.precision = DD_FP64;
+    p.tol = 1e-12;
+    p.max_it = 500;
+    p.precond = 1;
+    p.warm_start = 1;
+    p.refine_tol = 1e-12;
+    p.max_refine = 4;
+    p.chunk = 8;
+    return p;
+}
+
+int check_params(dd_handle* h, const dd_params& p) {
+    if (p.precision != DD_FP64 && p.precision != DD_MIXED) return h->fail(DD_ERR_ARG, "precision must be DD_FP64 or DD_MIXED");
+    if (!(p.tol > 0.0) || p.max_it < 1 || p.chunk < 1 || p.max_refine < 1 || !(p.refine_tol > 0.0))
+        return h->fail(DD_ERR_ARG, "tol, refine_tol must be > 0 and max_it, chunk, max_refine >= 1");
+    return DD_OK;
+}
+
+// ---- profiling: events around every launch while enabled --------------------
+enum Stage { ST_RHS = 0, ST_LOCAL = 1, ST_SCHUR = 2, ST_COARSE = 3, ST_CORNER = 4, ST_RECOVER = 5, ST_VEC = 6,
+             ST_REFINE = 7, ST_FACTOR = 8 };
+
+cudaEvent_t grab_event(dd_handle* h) {
+    if (h->ev_used == h->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        h->ev_pool.push_back((void*)e);
+    }
+    return (cudaEvent_t)h->ev_pool[h->ev_used++];
+}
+
+// Counts `nk` kernel launches of `stage`; `full` marks them as full-work launches
+// whose algorithmic bytes are known (bytes per launch chosen by precision).
+struct Prof {
+    dd_handle* h;
+    int stage;
+    cudaStream_t s;
+    size_t i0 = 0;
+    bool on;
+    Prof(dd_handle* h_, int stage_, cudaStream_t s_, int nk = 1, bool full = true, int prec = DD_FP64)
+        : h(h_), stage(stage_), s(s_), on(h_->prof_on) {
+        h->launches[stage] += nk;
+        h->total_launches += nk;
+        if (full) {
+            h->work[stage] += 1;
+            h->work_bytes[stage] += prec == DD_MIXED ? h->bytes_per_launch32[stage] : h->bytes_per_launch[stage];
+        }
+        if (on) {
+            i0 = h->ev_used;
+            cudaEvent_t a = grab_event(h);
+            grab_event(h);
+            if (a) cudaEventRecord(a, s);
+        }
+    }
+    ~Prof() {
+        if (on && i0 + 1 < h->ev_used) {
+            cudaEventRecord((cudaEvent_t)h->ev_pool[i0 + 1], s);
+            h->prof_recs.push_back({stage, i0});
+        }
+    }
+};
+
+int gemv_stage(int mode) {
+    switch (mode) {
+        case GEMV_LOCAL: return ST_LOCAL;
+        case GEMV_SCHUR: return ST_SCHUR;
+        case GEMV_COARSE: return ST_COARSE;
+        case GEMV_CORNER: return ST_CORNER;
+        default: return ST_RECOVER;
+    }
+}
+
+// Algorithmic bytes of one full launch of each stage: matrix elements read at
+// the stage's precision plus the vectors read and written once.
+void compute_stage_bytes(dd_handle* h) {
+    const double nl = (double)h->sub_ptr.back(), nd = (double)h->n_dof, nnz = (double)h->row_ptr.back();
+    const double nc = (double)h->corner_dof.size();
+    for (int k = 0; k < DD_N_STAGES; ++k) h->bytes_per_launch[k] = h->bytes_per_launch32[k] = 0.0;
+    // RHS: S values + column ids, row pointers, e^n, source, b
+    h->bytes_per_launch[ST_RHS] = h->bytes_per_launch32[ST_RHS] = nnz * 12.0 + nl * (8.0 + 8.0 + 5.0) + 2.0 * nd * 8.0;
+    for (int mode = 0; mode < GEMV_NMODES; ++mode) {
+        double elems = 0.0, vec = 0.0;
+        if (mode == GEMV_COARSE) {
+            elems = nc * nc;
+            vec = 2.0 * nc * 8.0;
+        } else {
+            for (const MatDesc& md : h->mats) {
+                int r0, r1, c0, c1;
+                switch (mode) {
+                    case GEMV_LOCAL: r0 = 0; r1 = md.ns; c0 = 0; c1 = md.nr; break;
+                    case GEMV_SCHUR: r0 = md.nI; r1 = md.ns; c0 = md.nI; c1 = md.nr; break;
+                    case GEMV_CORNER: r0 = md.nI; r1 = md.nr; c0 = md.nr; c1 = md.ns; break;
+                    default: r0 = 0; r1 = md.nr; c0 = md.nI; c1 = md.ns; break;
+                }
+                elems += (double)(r1 - r0) * (double)(c1 - c0);
+                const bool acc = mode == GEMV_CORNER || mode == GEMV_RECOVER;
+                vec += (double)(c1 - c0) * 8.0 + (double)(r1 - r0) * 8.0 * (acc ? 2.0 : 1.0);
+            }
+        }
+        const int st = gemv_stage(mode);
+        h->bytes_per_launch[st] = elems * 8.0 + vec;
+        h->bytes_per_launch32[st] = elems * 4.0 + vec;
+    }
+    // FP64 residual b -= A delta (A values + ids + b) and the assembled norm
+    h->bytes_per_launch[ST_REFINE] = h->bytes_per_launch32[ST_REFINE] = nnz * 12.0 + nl * 24.0 + nd * 8.0;
+}
+
+struct Layout {
+    size_t off = 0;
+    char* base = nullptr;
+    template <typename T>
+    void take(T*& ptr, size_t count) {
+        off = (off + 255) / 256 * 256;
+        ptr = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += sizeof(T) * std::max<size_t>(count, 1);
+    }
+};
+
+template <typename T>
+int upload(T* dst, const std::vector<T>& src, cudaStream_t s) {
+    if (src.empty()) return 0;
+    return (int)cudaMemcpyAsync(dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, s);
+}
+
+}  // namespace
+
+size_t dd_workspace_layout(dd_handle* h, bool assign) {
+    Layout L;
+    L.base = assign ? h->ws : nullptr;
+    DevPtrs d;
+    const size_t nl = (size_t)h->sub_ptr.back(), nd = (size_t)h->n_dof, nm = h->mult_dof.size(),
+                 nc = h->corner_dof.size(), nnz = (size_t)h->row_ptr.back();
+    L.take(d.mats, h->mats.size());
+    L.take(d.coarse_desc, 1);
+    L.take(d.slot_mult, nl);
+    L.take(d.slot_corner, nl);
+    L.take(d.slot_dof, nl);
+    L.take(d.slot_sub, nl);
+    L.take(d.slot_own, nl);
+    L.take(d.mult_slot, 2 * nm);
+    L.take(d.corner_ptr, nc + 1);
+    L.take(d.corner_slot, h->corner_slot.size());
+    L.take(d.owner_slot, nd);
+    L.take(d.copy_ptr, nd + 1);
+    L.take(d.copy_slot, nl);
+    L.take(d.row_ptr, nl + 1);
+    L.take(d.col_loc, nnz);
+    L.take(d.col_dof, nnz);
+    L.take(d.Tval, nnz);
+    L.take(d.Sval, nnz);
+    L.take(d.Aval, nnz);
+    for (int m = 0; m < GEMV_NMODES; ++m) L.take(d.tasks[m], h->tasks[m].size());
+    L.take(d.probe_dof, 6 * kMaxProbes);
+    L.take(d.probe_w, 18 * kMaxProbes);
+    L.take(d.M64, (size_t)h->dense_elems);
+    L.take(d.M32, (size_t)h->dense_elems);
+    L.take(d.K64, nc * (size_t)h->ldc);
+    L.take(d.K32, nc * (size_t)h->ldc);
+    L.take(d.Pinv, (size_t)(h->n_sub + 1) * kNB * kNB);
+    L.take(d.dinv, nm);
+    for (int k = 0; k < 3; ++k) L.take(d.e[k], nd);
+    L.take(d.b, nl);
+    L.take(d.y, nl);
+    L.take(d.w, nl);
+    L.take(d.x, nl);
+    L.take(d.lam, nm);
+    L.take(d.g, nm);
+    L.take(d.r, nm);
+    L.take(d.p, nm);
+    L.take(d.q, nm);
+    L.take(d.z, nm);
+    L.take(d.lam_scratch, nm);
+    L.take(d.fC, nc);
+    L.take(d.uC, nc);
+    L.take(d.vC, nc);
+    L.take(d.xC, nc);
+    L.take(d.delta, nd);
+    L.take(d.delta_k, nd);
+    L.take(d.sc, 1);
+    L.take(d.partials, 3 * kMaxPartials);
+    L.take(d.status, 4);
+    if (assign) h->d = d;
+    return (L.off + 255) / 256 * 256;
+}
+
+namespace {
+
+// Read the CG scalars back (synchronises the stream).
+int read_scalars(dd_handle* h, PcgScalars* out, cudaStream_t s) {
+    int rc = (int)cudaMemcpyAsync(out, h->d.sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s);
+    if (rc) return rc;
+    return (int)cudaStreamSynchronize(s);
+}
+
+// w <- interface operator pieces for x-source (kind, v, v2):
+// rows Gamma: S_Gamma z + Psi_Gamma K~cc^-1 Psi^T z ; then the caller jumps w.
+// Inside the CG loop (check_done) launches after convergence exit early; their
+// full-work count is added by dd_solve once the iteration count is known.
+int apply_schur_w(dd_handle* h, int prec, int kind, const double* v, const double* v2, bool check_done, cudaStream_t s) {
+    int rc;
+    {
+        Prof P(h, ST_SCHUR, s, 1, !check_done, prec);
+        rc = launch_gemv(h, GEMV_SCHUR, prec, kind, v, v2, h->d.w, nullptr, 1.0, check_done, s);
+    }
+    if (rc) return rc;
+    if (h->corner_dof.empty()) return 0;
+    {
+        Prof P(h, ST_VEC, s, 1, false);
+        rc = launch_corner_gather(h, h->d.w, nullptr, h->d.uC, check_done, s);
+    }
+    if (rc) return rc;
+    {
+        Prof P(h, ST_COARSE, s, 1, !check_done, prec);
+        rc = launch_gemv(h, GEMV_COARSE, prec, X_FLAT, h->d.uC, nullptr, h->d.vC, nullptr, 1.0, check_done, s);
+    }
+    if (rc) return rc;
+    Prof P(h, ST_CORNER, s, 1, !check_done, prec);
+    return launch_gemv(h, GEMV_CORNER, prec, X_CORNER, h->d.vC, nullptr, h->d.w, h->d.w, -1.0, check_done, s);
+}
+
+// Adds n full-work launches of the CG-loop stages after the iteration count is known.
+void count_cg_work(dd_handle* h, int prec, int n) {
+    const int st[3] = {ST_SCHUR, ST_COARSE, ST_CORNER};
+    for (int k = 0; k < 3; ++k) {
+        if (st[k] != ST_SCHUR && h->corner_dof.empty()) continue;
+        h->work[st[k]] += n;
+        h->work_bytes[st[k]] += n * (prec == DD_MIXED ? h->bytes_per_launch32[st[k]] : h->bytes_per_launch[st[k]]);
+    }
+}
+
+// Solve the torn system A x = b for the local right-hand sides in d.b
+// (subassembled), leaving x in d.x (r slots) and x_c in d.xC.
+// Returns a DD status; iteration count and residual in *it / *res.
+int dd_solve(dd_handle* h, int prec, double tol, bool warm, int* it_out, double* res_out, cudaStream_t s) {
+    const bool has_c = !h->corner_dof.empty();
+    const bool has_l = !h->mult_dof.empty();
+    // y = A_rr^-1 b_r (r rows) and A_cr y (corner rows)          Eq. rF1 / F1uc
+    {
+        Prof P(h, ST_LOCAL, s, 1, true, prec);
+        CK(h, launch_gemv(h, GEMV_LOCAL, prec, X_FLAT, h->d.b, nullptr, h->d.y, nullptr, 1.0, false, s), "gemv local");
+    }
+    // g = d_r ; f~_c
+    {
+        Prof P(h, ST_VEC, s, 1, false);
+        CK(h, launch_iface_rhs(h, s), "iface rhs");
+    }
+    if (has_c && has_l) {
+        // g = d_r - F_rc K~cc^-1 f~_c                                Eq. f1schur
+        {
+            Prof P(h, ST_COARSE, s, 1, true, prec);
+            CK(h, launch_gemv(h, GEMV_COARSE, prec, X_FLAT, h->d.fC, nullptr, h->d.vC, nullptr, 1.0, false, s), "coarse");
+        }
+        {
+            Prof P(h, ST_CORNER, s, 1, true, prec);
+            CK(h, launch_gemv(h, GEMV_CORNER, prec, X_CORNER, h->d.vC, nullptr, h->d.w, nullptr, -1.0, false, s), "corner");
+        }
+        Prof P(h, ST_VEC, s, 1, false);
+        CK(h, launch_jump(h, h->d.w, h->d.g, -1.0, h->d.g, s), "jump");
+    }
+    int status = DD_OK;
+    int iters = 0;
+    double res = 0.0;
+    if (has_l) {
+        const bool use_warm = warm && h->lam_valid;
+        if (use_warm) {
+            CK(h, apply_schur_w(h, prec, X_LAMBDA, h->d.lam, nullptr, false, s), "apply lambda0");
+        } else {
+            CK(h, (int)cudaMemsetAsync(h->d.lam, 0, sizeof(double) * h->mult_dof.size(), s), "memset");
+        }
+        {
+            Prof P(h, ST_VEC, s, 1, false);
+            CK(h, launch_pcg_init(h, use_warm ? 1 : 0, tol, s), "pcg init");
+        }
+        PcgScalars hs;
+        CK(h, read_scalars(h, &hs, s), "pcg scalars");
+        while (!hs.done && hs.it < h->prm.max_it) {
+            const int n = std::min(h->prm.chunk, h->prm.max_it - hs.it);
+            for (int k = 0; k < n; ++k) {
+                CK(h, apply_schur_w(h, prec, X_PCG, h->d.z, h->d.p, true, s), "apply");
+                Prof P(h, ST_VEC, s, 2, false);
+                CK(h, launch_pcg_alpha(h, s), "pcg alpha");
+                CK(h, launch_pcg_update(h, s), "pcg update");
+            }
+            CK(h, read_scalars(h, &hs, s), "pcg scalars");
+        }
+        iters = hs.it;
+        count_cg_work(h, prec, hs.it);
+        res = hs.gg > 0 ? std::sqrt(hs.rr / hs.gg) : 0.0;
+        if (hs.status != DD_OK) status = hs.status;
+        else if (!hs.done) status = DD_ERR_NO_CONVERGENCE;
+        h->lam_valid = true;
+    }
+    // x_c = K~cc^-1 (f~_c + F_rc^T lambda)                           Eq. F1uc
+    if (has_c) {
+        if (has_l) {
+            {
+                Prof P(h, ST_SCHUR, s, 1, true, prec);
+                CK(h, launch_gemv(h, GEMV_SCHUR, prec, X_LAMBDA, h->d.lam, nullptr, h->d.w, nullptr, 1.0, false, s), "Frc^T");
+            }
+            Prof P(h, ST_VEC, s, 1, false);
+            CK(h, launch_corner_gather(h, h->d.w, h->d.fC, h->d.uC, false, s), "corner gather");
+        }
+        Prof P(h, ST_COARSE, s, 1, true, prec);
+        CK(h, launch_gemv(h, GEMV_COARSE, prec, X_FLAT, has_l ? h->d.uC : h->d.fC, nullptr, h->d.xC, nullptr, 1.0,
+                          false, s), "xc");
+    }
+    // x_r = y + A_rr^-1 (-B_r^T lambda) - A_rr^-1 A_rc x_c                  Eq. rF1
+    {
+        Prof P(h, ST_RECOVER, s, 1, true, prec);
+        CK(h, launch_gemv(h, GEMV_RECOVER, prec, X_RECOVER, h->d.lam, h->d.xC, h->d.x, h->d.y, 1.0, false, s), "recover");
+    }
+    if (it_out) *it_out = iters;
+    if (res_out) *res_out = res;
+    if (status != DD_OK) h->err = status == DD_ERR_NO_CONVERGENCE ? "interface CG did not converge" : "non-finite CG residual";
+    return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dd_setup(const dd_mesh* mesh, const int32_t* part, int32_t n_sub, const dd_params* params, dd_handle** out) {
+    if (!out) return DD_ERR_ARG;
+    *out = nullptr;
+    if (!mesh || !part || n_sub < 1 || !mesh->xyz || !mesh->tets || mesh->n_nodes < 4 || mesh->n_tets < 1)
+        return DD_ERR_ARG;
+    dd_handle* h = new (std::nothrow) dd_handle();
+    if (!h) return DD_ERR_ARG;
+    h->prm = params ? *params : default_params();
+    int rc = check_params(h, h->prm);
+    if (rc == DD_OK) {
+        try {
+            rc = dd_build_host(h, mesh, part, n_sub);
+        } catch (const std::exception& ex) {
+            rc = h->fail(DD_ERR_ARG, std::string("setup failed: ") + ex.what());
+        }
+    }
+    *out = h;  // returned even on failure so that dd_last_error can be read; caller destroys
+    return rc;
+}
+
+int dd_set_params(dd_handle* h, const dd_params* params) {
+    if (!h || !params) return DD_ERR_ARG;
+    int rc = check_params(h, *params);
+    if (rc) return rc;
+    h->prm = *params;
+    return DD_OK;
+}
+
+int dd_get_sizes(const dd_handle* h, dd_sizes* o) {
+    if (!h || !o) return DD_ERR_ARG;
+    o->n_edges = h->n_edges;
+    o->n_dof = h->n_dof;
+    o->n_sub = h->n_sub;
+    o->n_lambda = (int64_t)h->mult_dof.size();
+    o->n_corner = (int64_t)h->corner_dof.size();
+    o->n_local = h->sub_ptr.empty() ? 0 : h->sub_ptr.back();
+    o->nnz_local = h->row_ptr.empty() ? 0 : h->row_ptr.back();
+    o->max_nr = h->max_nr;
+    o->max_ns = h->max_ns;
+    o->workspace_bytes = h->sub_ptr.empty() ? 0 : dd_workspace_layout(const_cast<dd_handle*>(h), false);
+    o->dense_bytes_fp64 = h->dense_elems * 8;
+    return DD_OK;
+}
+
+int dd_get_maps(const dd_handle* h, dd_maps* m) {
+    if (!h || !m || h->sub_ptr.empty()) return DD_ERR_ARG;
+    auto cp = [](auto* dst, const auto& v) {
+        if (dst && !v.empty()) std::memcpy(dst, v.data(), sizeof(v[0]) * v.size());
+    };
+    cp(m->edges, h->edges);
+    cp(m->dof_edge, h->dof_edge);
+    cp(m->sub_ptr, h->sub_ptr);
+    cp(m->local_dof, h->local_dof);
+    cp(m->n_int, h->nI);
+    cp(m->n_gam, h->nG);
+    cp(m->n_cor, h->nC);
+    cp(m->mult_dof, h->mult_dof);
+    cp(m->mult_sub, h->mult_sub);
+    cp(m->mult_loc, h->mult_loc);
+    cp(m->corner_dof, h->corner_dof);
+    cp(m->owner, h->owner);
+    return DD_OK;
+}
+
+int dd_set_probes(dd_handle* h, int32_t n, const double* xyz) {
+    if (!h || n < 0 || n > kMaxProbes || (n > 0 && !xyz)) return h ? h->fail(DD_ERR_ARG, "bad probe list") : DD_ERR_ARG;
+    int rc = dd_locate_probes(h, n, xyz);
+    if (rc) return rc;
+    if (h->bound && n > 0) {
+        CK(h, upload(h->d.probe_dof, h->probe_dof, 0), "upload probes");
+        CK(h, upload(h->d.probe_w, h->probe_w, 0), "upload probes");
+        CK(h, (int)cudaStreamSynchronize(0), "sync");
+    }
+    return DD_OK;
+}
+
+int dd_bind_workspace(dd_handle* h, void* dev, size_t bytes, void* stream) {
+    if (!h || !dev || h->sub_ptr.empty()) return DD_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(dev) & 255) != 0) return h->fail(DD_ERR_ARG, "workspace must be 256-byte aligned");
+    const size_t need = dd_workspace_layout(h, false);
+    if (bytes < need) return h->fail(DD_ERR_ARG, "workspace too small: need " + std::to_string(need) + " bytes");
+    h->ws = static_cast<char*>(dev);
+    h->ws_bytes = bytes;
+    dd_workspace_layout(h, true);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nd = (size_t)h->n_dof;
+    MatDesc cd{0, 0, h->ldc, 0, (int32_t)h->corner_dof.size(), (int32_t)h->corner_dof.size()};
+    CK(h, (int)cudaMemcpyAsync(h->d.mats, h->mats.data(), sizeof(MatDesc) * h->mats.size(), cudaMemcpyHostToDevice, s), "upload");
+    CK(h, (int)cudaMemcpyAsync(h->d.coarse_desc, &cd, sizeof(MatDesc), cudaMemcpyHostToDevice, s), "upload");
+    CK(h, upload(h->d.slot_mult, h->slot_mult, s), "upload");
+    CK(h, upload(h->d.slot_corner, h->slot_corner, s), "upload");
+    CK(h, upload(h->d.slot_dof, h->slot_dof, s), "upload");
+    CK(h, upload(h->d.slot_sub, h->slot_sub, s), "upload");
+    CK(h, upload(h->d.slot_own, h->slot_own, s), "upload");
+    CK(h, upload(h->d.mult_slot, h->mult_slot, s), "upload");
+    CK(h, upload(h->d.corner_ptr, h->corner_ptr, s), "upload");
+    CK(h, upload(h->d.corner_slot, h->corner_slot, s), "upload");
+    CK(h, upload(h->d.owner_slot, h->owner_slot, s), "upload");
+    CK(h, upload(h->d.copy_ptr, h->copy_ptr, s), "upload");
+    CK(h, upload(h->d.copy_slot, h->copy_slot, s), "upload");
+    CK(h, upload(h->d.row_ptr, h->row_ptr, s), "upload");
+    CK(h, upload(h->d.col_loc, h->col_loc, s), "upload");
+    CK(h, upload(h->d.col_dof, h->col_dof, s), "upload");
+    CK(h, upload(h->d.Tval, h->Tval, s), "upload");
+    CK(h, upload(h->d.Sval, h->Sval, s), "upload");
+    for (int m = 0; m < GEMV_NMODES; ++m) CK(h, upload(h->d.tasks[m], h->tasks[m], s), "upload");
+    if (h->n_probe) {
+        CK(h, upload(h->d.probe_dof, h->probe_dof, s), "upload");
+        CK(h, upload(h->d.probe_w, h->probe_w, s), "upload");
+    }
+    for (int k = 0; k < 3; ++k) CK(h, (int)cudaMemsetAsync(h->d.e[k], 0, sizeof(double) * nd, s), "memset");
+    CK(h, (int)cudaMemsetAsync(h->d.sc, 0, sizeof(PcgScalars), s), "memset");
+    CK(h, (int)cudaMemsetAsync(h->d.status, 0, 16, s), "memset");
+    CK(h, (int)cudaStreamSynchronize(s), "sync");
+    h->bound = true;
+    h->factored = false;
+    compute_stage_bytes(h);
+    return DD_OK;
+}
+
+int dd_factor(dd_handle* h, double dt, void* stream) {
+    if (!h) return DD_ERR_ARG;
+    if (!h->bound) return h->fail(DD_ERR_STATE, "dd_factor before dd_bind_workspace");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return h->fail(DD_ERR_ARG, "dt must be positive");
+    cudaStream_t s = (cudaStream_t)stream;
+    h->factored = false;
+    CK(h, (int)cudaMemsetAsync(h->d.status, 0, 4, s), "memset");
+    {
+        Prof P(h, ST_FACTOR, s, 2, false);
+        CK(h, launch_csr_combine(h, dt * dt / 4.0, s), "A = T + dt^2/4 S");
+        CK(h, launch_dense_assemble(h, s), "dense assemble");
+    }
+    for (int k0 = 0; k0 < h->max_nr; k0 += kNB) {
+        Prof P(h, ST_FACTOR, s, 3, false);
+        CK(h, launch_sweep(h, false, k0, s), "local elimination");
+    }
+    const int nc = (int)h->corner_dof.size();
+    if (nc) {
+        {
+            Prof P(h, ST_FACTOR, s, 1, false);
+            CK(h, launch_coarse_assemble(h, s), "coarse assemble");
+        }
+        for (int k0 = 0; k0 < nc; k0 += kNB) {
+            Prof P(h, ST_FACTOR, s, 3, false);
+            CK(h, launch_sweep(h, true, k0, s), "coarse inverse");
+        }
+    }
+    {
+        Prof P(h, ST_FACTOR, s, 3, false);
+        CK(h, launch_factor_finish(h, s), "factor finish");
+    }
+    int32_t st = 0;
+    CK(h, (int)cudaMemcpyAsync(&st, h->d.status, 4, cudaMemcpyDeviceToHost, s), "status");
+    CK(h, (int)cudaStreamSynchronize(s), "sync");
+    if (st != 0) return h->fail(DD_ERR_NOT_SPD, "non-positive pivot in the local or coarse elimination");
+    const size_t nd = (size_t)h->n_dof;
+    for (int k = 0; k < 3; ++k) CK(h, (int)cudaMemsetAsync(h->d.e[k], 0, sizeof(double) * nd, s), "memset");
+    CK(h, (int)cudaStreamSynchronize(s), "sync");
+    h->dt = dt;
+    h->step = 0;
+    h->cur = 0;
+    h->lam_valid = false;
+    h->factored = true;
+    return DD_OK;
+}
+
+int dd_step(dd_handle* h, const double* d2g, double* e_out, dd_stats* stats, void* stream) {
+    if (!h) return DD_ERR_ARG;
+    if (!h->factored) return h->fail(DD_ERR_STATE, "dd_step before dd_factor");
+    cudaStream_t s = (cudaStream_t)stream;
+    const double* e_n = h->d.e[h->cur];
+    const double* e_nm1 = h->d.e[(h->cur + 2) % 3];
+    double* e_np1 = h->d.e[(h->cur + 1) % 3];
+    int status = DD_OK, iters = 0, refinements = 0;
+    double resid = 0.0;
+    // b = -dt^2 S e^n - d2g (subassembled): A delta = b, e^{n+1} = 2e^n - e^{n-1} + delta
+    {
+        Prof P(h, ST_RHS, s);
+        CK(h, launch_rhs(h, e_n, d2g, h->dt, s), "rhs");
+    }
+    if (h->prm.precision == DD_FP64) {
+        status = dd_solve(h, DD_FP64, h->prm.tol, h->prm.warm_start != 0, &iters, &resid, s);
+        if (status != DD_OK && status != DD_ERR_NO_CONVERGENCE) return status;
+        Prof P(h, ST_VEC, s, 1, false);
+        CK(h, launch_writeback(h, e_n, e_nm1, nullptr, nullptr, 1, e_np1, s), "writeback");
+    } else {
+        // FP64 iterative refinement of the step system with FP32 DD correction solves
+        {
+            Prof P(h, ST_REFINE, s, 1, false);
+            CK(h, launch_assembled_norm(h, 1, s), "norm b");
+        }
+        PcgScalars hs;
+        for (int k = 0; k < h->prm.max_refine; ++k) {
+            const bool warm = (k == 0) && h->prm.warm_start != 0;
+            if (k == 1 && !h->mult_dof.empty())
+                CK(h, (int)cudaMemcpyAsync(h->d.lam_scratch, h->d.lam, sizeof(double) * h->mult_dof.size(),
+                                           cudaMemcpyDeviceToDevice, s), "save lambda");
+            int it = 0;
+            double r = 0.0;
+            int st = dd_solve(h, DD_MIXED, h->prm.tol, warm, &it, &r, s);
+            iters += it;
+            ++refinements;
+            if (st != DD_OK && st != DD_ERR_NO_CONVERGENCE) return st;
+            {
+                Prof P(h, ST_VEC, s, 1, false);
+                CK(h, launch_writeback(h, e_n, e_nm1, h->d.delta_k, h->d.delta, k == 0 ? 1 : 0, nullptr, s), "writeback");
+            }
+            {
+                Prof P(h, ST_REFINE, s, 2, true);
+                CK(h, launch_residual_local(h, s), "residual");
+                CK(h, launch_assembled_norm(h, 0, s), "norm r");
+            }
+            CK(h, read_scalars(h, &hs, s), "scalars");
+            resid = hs.norm_b2 > 0 ? std::sqrt(hs.norm_r2 / hs.norm_b2) : 0.0;
+            if (!std::isfinite(resid)) {
+                status = DD_ERR_NONFINITE;
+                break;
+            }
+            if (resid <= h->prm.refine_tol) break;
+            if (k + 1 == h->prm.max_refine) status = DD_ERR_NO_CONVERGENCE;
+        }
+        if (refinements > 1 && !h->mult_dof.empty())
+            CK(h, (int)cudaMemcpyAsync(h->d.lam, h->d.lam_scratch, sizeof(double) * h->mult_dof.size(),
+                                       cudaMemcpyDeviceToDevice, s), "restore lambda");
+        {
+            Prof P(h, ST_VEC, s, 1, false);
+            CK(h, launch_advance(h, e_n, e_nm1, h->d.delta, e_np1, s), "advance");
+        }
+        if (status == DD_ERR_NO_CONVERGENCE) h->err = "refinement did not reach refine_tol";
+    }
+    h->cur = (h->cur + 1) % 3;
+    h->step += 1;
+    if (e_out) CK(h, (int)cudaMemcpyAsync(e_out, e_np1, sizeof(double) * h->n_dof, cudaMemcpyDeviceToDevice, s), "e_out");
+    if (stats) {
+        stats->iters = iters;
+        stats->refinements = refinements;
+        stats->resid = resid;
+        stats->status = status;
+    }
+    return status;
+}
+
+int dd_schur_apply(dd_handle* h, const double* lam, double* out, void* stream) {
+    if (!h || !lam || !out) return DD_ERR_ARG;
+    if (!h->factored) return h->fail(DD_ERR_STATE, "dd_schur_apply before dd_factor");
+    if (h->mult_dof.empty()) return DD_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(h, apply_schur_w(h, DD_FP64, X_LAMBDA, lam, nullptr, false, s), "apply");
+    Prof P(h, ST_VEC, s, 1, false);
+    CK(h, launch_jump(h, h->d.w, nullptr, 1.0, out, s), "jump");
+    return DD_OK;
+}
+
+int dd_probe(dd_handle* h, double* out, void* stream) {
+    if (!h || !out) return DD_ERR_ARG;
+    if (!h->bound) return h->fail(DD_ERR_STATE, "dd_probe before dd_bind_workspace");
+    Prof P(h, ST_VEC, (cudaStream_t)stream, 1, false);
+    CK(h, launch_probe(h, h->d.e[h->cur], out, (cudaStream_t)stream), "probe");
+    return DD_OK;
+}
+
+int dd_get_state(const dd_handle* hc, double* e_n, double* e_nm1, int64_t* step, void* stream) {
+    dd_handle* h = const_cast<dd_handle*>(hc);
+    if (!h) return DD_ERR_ARG;
+    if (!h->bound) return h->fail(DD_ERR_STATE, "no workspace bound");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nb = sizeof(double) * h->n_dof;
+    if (e_n) CK(h, (int)cudaMemcpyAsync(e_n, h->d.e[h->cur], nb, cudaMemcpyDeviceToDevice, s), "copy");
+    if (e_nm1) CK(h, (int)cudaMemcpyAsync(e_nm1, h->d.e[(h->cur + 2) % 3], nb, cudaMemcpyDeviceToDevice, s), "copy");
+    if (step) *step = h->step;
+    return DD_OK;
+}
+
+int dd_set_state(dd_handle* h, const double* e_n, const double* e_nm1, int64_t step, void* stream) {
+    if (!h || !e_n || !e_nm1 || step < 0) return DD_ERR_ARG;
+    if (!h->bound) return h->fail(DD_ERR_STATE, "no workspace bound");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nb = sizeof(double) * h->n_dof;
+    h->cur = 0;
+    CK(h, (int)cudaMemcpyAsync(h->d.e[0], e_n, nb, cudaMemcpyDeviceToDevice, s), "copy");
+    CK(h, (int)cudaMemcpyAsync(h->d.e[2], e_nm1, nb, cudaMemcpyDeviceToDevice, s), "copy");
+    h->step = step;
+    h->lam_valid = false;
+    return DD_OK;
+}
+
+int dd_profile(dd_handle* h, int enable, dd_profile_stats* out, void* stream) {
+    if (!h) return DD_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (out) {
+        CK(h, (int)cudaStreamSynchronize(s), "sync");
+        std::memset(out, 0, sizeof(*out));
+        for (int k = 0; k < DD_N_STAGES; ++k) {
+            out->launches[k] = h->launches[k];
+            out->work[k] = h->work[k];
+            out->bytes[k] = h->work_bytes[k];
+        }
+        for (const auto& rec : h->prof_recs) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, (cudaEvent_t)h->ev_pool[rec.second], (cudaEvent_t)h->ev_pool[rec.second + 1]) ==
+                cudaSuccess)
+                out->ms[rec.first] += ms;
+        }
+        out->total_launches = h->total_launches;
+    }
+    if (enable == 1 || enable == 0) {
+        CK(h, (int)cudaStreamSynchronize(s), "sync");
+        h->prof_recs.clear();
+        h->ev_used = 0;
+        if (enable == 1) {
+            for (int k = 0; k < DD_N_STAGES; ++k) {
+                h->launches[k] = h->work[k] = 0;
+                h->work_bytes[k] = 0.0;
+            }
+            h->total_launches = 0;
+        }
+        h->prof_on = enable == 1;
+    }
+    return DD_OK;
+}
+
+void dd_destroy(dd_handle* h) {
+    if (!h) return;
+    for (void* e : h->ev_pool) cudaEventDestroy((cudaEvent_t)e);
+    delete h;
+}
+
+const char* dd_last_error(const dd_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+}  // extern "C"

@@ -1,0 +1,239 @@
+// Internal declarations shared by the host setup, the kernels and the C ABI.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/dd.h"
+
+// Dense per-subdomain operator: row-major ns x ld block at element offset moff of
+// the dense buffer.  After dd_factor the block holds the partially swept local
+// matrix [[A_rr^-1, -A_rr^-1 A_rc], [A_cr A_rr^-1, A_cc - A_cr A_rr^-1 A_rc]].
+struct MatDesc {
+    int64_t moff;   // element offset of row 0 in the dense buffer
+    int64_t voff;   // offset of the subdomain's first local slot in flat local vectors
+    int32_t ld;     // row stride (elements), multiple of 4
+    int32_t nI;     // interior (m = 1) unknowns
+    int32_t nr;     // r block = interior + interface
+    int32_t ns;     // r + corner
+};
+
+// One CTA of a batched GEMV: rows [row0, row1) of matrix `mat`.
+struct GemvTask {
+    int32_t mat;
+    int32_t row0;
+    int32_t row1;
+    int32_t pad;
+};
+
+// Column/row ranges of the batched dense GEMV, all relative to one MatDesc.
+enum GemvMode : int {
+    GEMV_LOCAL = 0,   // rows [0,ns)  cols [0,nr):   [y; A_cr y] from b_r   (Eq. rF1 / F1uc)
+    GEMV_SCHUR = 1,   // rows [nI,ns) cols [nI,nr):  F_rr / F_rc^T pieces   (Eq. f1schur)
+    GEMV_CORNER = 2,  // rows [nI,nr) cols [nr,ns):  F_rc pieces            (Eq. f1schur)
+    GEMV_RECOVER = 3, // rows [0,nr)  cols [nI,ns):  x_r from y, lambda, x_c (Eq. rF1)
+    GEMV_COARSE = 4,  // the dense K~cc^-1 (single matrix)
+    GEMV_NMODES = 5
+};
+
+// Device scalars of the interface CG (one struct in the workspace).
+struct PcgScalars {
+    double rz;        // r . z
+    double rz_new;
+    double pq;        // p . q
+    double alpha, beta;
+    double rr;        // ||r||^2
+    double gg;        // ||rhs||^2
+    double tol2;      // tol^2 * gg
+    int32_t it;       // iterations done
+    int32_t done;     // 1 when converged (kernels become no-ops)
+    int32_t status;   // DD_OK / DD_ERR_NONFINITE
+    int32_t pad;
+    double norm_b2;   // mixed mode: ||b||^2 of the step system
+    double norm_r2;   // mixed mode: ||r||^2 of the current FP64 residual
+    uint32_t counter[8];  // last-block counters of the grid reductions
+};
+
+struct DevPtrs {
+    // maps (slot = flat local index over all subdomains)
+    MatDesc* mats = nullptr;
+    MatDesc* coarse_desc = nullptr;  // single descriptor of K~cc (ld = ldc)
+    int32_t* slot_sub = nullptr;     // subdomain of each slot
+    int64_t* copy_ptr = nullptr;     // [n_dof+1] copies of each dof, by subdomain
+    int64_t* copy_slot = nullptr;    // [n_local]
+    int32_t* slot_mult = nullptr;    // +(m+1) in s1, -(m+1) in s2, 0 if not an interface slot
+    int32_t* slot_corner = nullptr;  // corner id of a corner slot, else -1
+    int32_t* slot_dof = nullptr;     // dof of each slot
+    uint8_t* slot_own = nullptr;     // 1 if this slot's subdomain owns the dof
+    int64_t* mult_slot = nullptr;    // [n_lambda*2] slots of s1 and s2
+    int64_t* corner_ptr = nullptr;   // [n_corner+1]
+    int64_t* corner_slot = nullptr;  // copies of every corner, by subdomain
+    int64_t* owner_slot = nullptr;   // [n_dof] slot in the owner subdomain
+    int64_t* row_ptr = nullptr;      // local CSR over slots [n_local+1]
+    int32_t* col_loc = nullptr;      // local column index
+    int32_t* col_dof = nullptr;      // global dof of the column
+    double* Tval = nullptr;
+    double* Sval = nullptr;
+    double* Aval = nullptr;          // T + dt^2/4 S (filled by dd_factor)
+    GemvTask* tasks[GEMV_NMODES] = {};
+    int32_t* probe_dof = nullptr;
+    double* probe_w = nullptr;
+    // dense operators
+    double* M64 = nullptr;           // per-subdomain swept matrices
+    float* M32 = nullptr;            // FP32 copy
+    double* K64 = nullptr;           // K~cc^-1, n_corner x ldc
+    float* K32 = nullptr;
+    double* Pinv = nullptr;          // [n_sub+1][NB*NB] pivot-block inverses while factoring
+    double* dinv = nullptr;          // [n_lambda] inverse Jacobi diagonal
+    // time levels (ring of 3)
+    double* e[3] = {nullptr, nullptr, nullptr};
+    // flat local vectors (n_local)
+    double* b = nullptr;             // local right-hand side
+    double* y = nullptr;             // GEMV outputs / local solutions
+    double* w = nullptr;             // interface operator output per slot
+    double* x = nullptr;             // recovered local solution
+    float* bf = nullptr;             // FP32 shadows for DD_MIXED
+    float* yf = nullptr;
+    float* wf = nullptr;
+    float* xf = nullptr;
+    // interface vectors (n_lambda)
+    double* lam = nullptr;
+    double* g = nullptr;
+    double* r = nullptr;
+    double* p = nullptr;
+    double* q = nullptr;
+    double* z = nullptr;
+    double* lam_scratch = nullptr;
+    // corner vectors (n_corner)
+    double* fC = nullptr;
+    double* uC = nullptr;
+    double* vC = nullptr;
+    double* xC = nullptr;
+    float* uCf = nullptr;
+    float* vCf = nullptr;
+    // global vectors (n_dof)
+    double* delta = nullptr;         // assembled correction of the step
+    double* delta_k = nullptr;       // assembled correction of one refinement
+    double* res = nullptr;           // assembled FP64 residual
+    // scalars
+    PcgScalars* sc = nullptr;
+    double* partials = nullptr;      // [kMaxPartials] block partial sums
+    int32_t* status = nullptr;       // factor status word
+};
+
+struct dd_handle {
+    dd_params prm{};
+    std::string err;
+
+    // mesh
+    int64_t n_nodes = 0, n_tets = 0;
+    std::vector<double> xyz;
+    std::vector<int32_t> tets;
+    std::vector<double> eps;
+    double mu = 1.0;
+
+    // edges and elements
+    int64_t n_edges = 0, n_dof = 0;
+    std::vector<int64_t> edges;      // 2 per edge
+    std::vector<int64_t> dof_edge;   // n_dof
+    std::vector<int64_t> tet_dof;    // 6 per tet, -1 on the PEC wall
+    std::vector<double> That, Shat;  // 36 per tet, oriented, unit coefficients
+    std::vector<double> grad;        // 12 per tet: barycentric gradients
+    std::vector<double> vol;
+
+    // tearing
+    int32_t n_sub = 0;
+    std::vector<int32_t> part;
+    std::vector<int64_t> sub_ptr;
+    std::vector<int64_t> local_dof;
+    std::vector<int32_t> nI, nG, nC;
+    std::vector<int32_t> owner;
+    std::vector<int64_t> mult_dof;
+    std::vector<int32_t> mult_sub, mult_loc;
+    std::vector<int64_t> corner_dof;
+    std::vector<int32_t> slot_mult, slot_corner, slot_dof;
+    std::vector<uint8_t> slot_own;
+    std::vector<int64_t> mult_slot, corner_ptr, corner_slot, owner_slot;
+    std::vector<int32_t> slot_sub;
+    std::vector<int64_t> copy_ptr, copy_slot;
+    std::vector<int64_t> row_ptr;
+    std::vector<int32_t> col_loc, col_dof;
+    std::vector<double> Tval, Sval;
+    std::vector<MatDesc> mats;
+    int64_t dense_elems = 0;
+    int32_t ldc = 0;                 // leading dimension of K~cc
+    int32_t max_nr = 0, max_ns = 0;
+    std::vector<GemvTask> tasks[GEMV_NMODES];
+
+    // probes
+    int32_t n_probe = 0;
+    std::vector<int32_t> probe_dof;  // 6 per probe
+    std::vector<double> probe_w;     // 18 per probe
+
+    // device state
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    DevPtrs d;
+    bool bound = false;
+    bool factored = false;
+    double dt = 0.0;
+    int64_t step = 0;
+    int cur = 0;                     // e[cur] = e^n, e[(cur+2)%3] = e^{n-1}
+    bool lam_valid = false;
+
+    // profiling (dd_profile)
+    bool prof_on = false;
+    std::vector<void*> ev_pool;            // cudaEvent_t
+    size_t ev_used = 0;
+    std::vector<std::pair<int, size_t>> prof_recs;   // (stage, index of start event)
+    int64_t launches[DD_N_STAGES] = {};
+    int64_t work[DD_N_STAGES] = {};
+    double work_bytes[DD_N_STAGES] = {};
+    int64_t total_launches = 0;
+    double bytes_per_launch[DD_N_STAGES] = {};  // algorithmic bytes of one full launch (FP64)
+    double bytes_per_launch32[DD_N_STAGES] = {};  // same with FP32 matrices
+
+    int fail(int code, const std::string& msg) {
+        err = msg;
+        return code;
+    }
+};
+
+constexpr int kNB = 32;              // pivot block of the dense elimination
+constexpr int kRowsPerTask = 32;     // rows per CTA of the batched GEMV
+constexpr int kMaxPartials = 4096;   // block partials of the grid reductions
+
+// setup.cpp
+int dd_build_host(dd_handle* h, const dd_mesh* mesh, const int32_t* part, int32_t n_sub);
+int dd_locate_probes(dd_handle* h, int32_t n, const double* xyz);
+size_t dd_workspace_layout(dd_handle* h, bool assign);
+
+// kernels.cu launchers (return a cudaError_t value; 0 = success)
+int launch_csr_combine(const dd_handle* h, double ca, void* stream);
+int launch_dense_assemble(const dd_handle* h, void* stream);
+int launch_sweep(const dd_handle* h, bool coarse, int k0, void* stream);
+int launch_coarse_assemble(const dd_handle* h, void* stream);
+int launch_factor_finish(const dd_handle* h, void* stream);
+int launch_rhs(const dd_handle* h, const double* e_n, const double* d2g, double dt, void* stream);
+int launch_residual_local(const dd_handle* h, void* stream);
+int launch_assembled_norm(const dd_handle* h, int set_b, void* stream);
+int launch_gemv(const dd_handle* h, int mode, int prec, int xkind, const double* v, const double* v2, double* out,
+                const double* base, double alpha, bool check_done, void* stream);
+int launch_iface_rhs(const dd_handle* h, void* stream);
+int launch_corner_gather(const dd_handle* h, const double* w, const double* add, double* uC, bool check_done,
+                         void* stream);
+int launch_jump(const dd_handle* h, const double* w, const double* base, double sign, double* out, void* stream);
+int launch_pcg_init(const dd_handle* h, int have_q, double tol, void* stream);
+int launch_pcg_alpha(const dd_handle* h, void* stream);
+int launch_pcg_update(const dd_handle* h, void* stream);
+int launch_writeback(const dd_handle* h, const double* e_n, const double* e_nm1, double* delta_k, double* delta_acc,
+                     int first, double* e_np1, void* stream);
+int launch_advance(const dd_handle* h, const double* e_n, const double* e_nm1, const double* delta, double* e_np1,
+                   void* stream);
+int launch_probe(const dd_handle* h, const double* e, double* out, void* stream);
+
+// GEMV x-source kinds (see kernels.cu)
+enum : int { X_FLAT = 0, X_LAMBDA = 1, X_PCG = 2, X_CORNER = 3, X_RECOVER = 4, X_COARSE = 5 };
+
+constexpr int kMaxProbes = 256;

@@ -1,0 +1,817 @@
+// Device kernels of the MFETI-DP1 time step (sm_103a).
+//
+// Data layout (all in the caller's workspace):
+//  * "slots": the local unknowns of every subdomain laid end to end
+//    (subdomain s occupies [voff_s, voff_s + ns_s), local order
+//    [interior | interface | corner]).  Flat local vectors are indexed by slot.
+//  * Dense per-subdomain matrix M_s (row-major, stride ld_s).  dd_factor
+//    eliminates its r block in place ("exchange"/Gauss-Jordan sweep), leaving
+//        M_s = [[ A_rr^-1        , -A_rr^-1 A_rc              ],
+//               [ A_cr A_rr^-1   ,  A_cc - A_cr A_rr^-1 A_rc   ]].
+//    Every per-step operation of Sec. III-A is then a GEMV on a sub-block:
+//        y = A_rr^-1 b_r and A_cr y            rows [0,ns)  cols [0,nr)
+//        F_rr / F_rc^T pieces on lambda        rows [nI,ns) cols [nI,nr)
+//        F_rc pieces on the corner vector      rows [nI,nr) cols [nr,ns)
+//        recovery x_r (Eq. rF1)                rows [0,nr)  cols [nI,ns)
+//  * Interface vectors are indexed by multiplier, corner vectors by corner.
+//
+// All reductions are deterministic: each block writes a partial sum and the
+// last block to finish (atomic ticket, no spinning) adds the partials in
+// block order.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+
+#include "dd_internal.h"
+
+#define CU_TRY(x)                                 \
+    do {                                          \
+        cudaError_t e_ = (x);                     \
+        if (e_ != cudaSuccess) return (int)e_;    \
+    } while (0)
+
+namespace {
+
+inline cudaStream_t S(void* s) { return (cudaStream_t)s; }
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum of NV values; result valid in thread 0.
+template <int NV>
+__device__ void block_sum(double (&v)[NV]) {
+    __shared__ double red[NV][kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) red[k][warp] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double s = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[k][w];
+            v[k] = s;
+        }
+    }
+}
+
+// Grid reduction: every block contributes NV partials; returns true in thread 0
+// of the last block, with the totals (summed in block order) in v.
+template <int NV>
+__device__ bool grid_sum(double (&v)[NV], double* partials, uint32_t* counter) {
+    block_sum<NV>(v);
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) partials[k * gridDim.x + blockIdx.x] = v[k];
+        __threadfence();
+        const uint32_t ticket = atomicAdd(counter, 1u);
+        last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double s = 0.0;
+            for (unsigned b = 0; b < gridDim.x; ++b) s += ((volatile double*)partials)[k * gridDim.x + b];
+            v[k] = s;
+        }
+        *counter = 0u;
+    }
+    return threadIdx.x == 0;
+}
+
+inline int reduce_blocks(int64_t n) {
+    int64_t b = (n + kThreads - 1) / kThreads;
+    if (b > 1024) b = 1024;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+// ----------------------------------------------------------------------------
+// Factor: matrices
+// ----------------------------------------------------------------------------
+
+__global__ void k_csr_combine(int64_t nnz, const double* __restrict__ T, const double* __restrict__ Sv, double ca,
+                              double* __restrict__ A) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x)
+        A[k] = T[k] + ca * Sv[k];
+}
+
+// Scatter the subassembled local CSR of A^(s) into the zeroed dense blocks.
+__global__ void k_dense_assemble(int64_t n_local, const int64_t* __restrict__ row_ptr,
+                                 const int32_t* __restrict__ col_loc, const double* __restrict__ A,
+                                 const int32_t* __restrict__ slot_sub, const MatDesc* __restrict__ mats,
+                                 double* __restrict__ M) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_local;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const MatDesc md = mats[slot_sub[i]];
+        double* row = M + md.moff + (i - md.voff) * (int64_t)md.ld;
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) row[col_loc[k]] = A[k];
+    }
+}
+
+// Exchange-sweep step on pivot block p = [k0, k0+nb), part 1 (one CTA per matrix):
+//   P^-1 by an in-shared-memory Gauss-Jordan sweep (SPD: no pivoting), stored to
+//   Pinv; row panel M[p, j] <- -P^-1 M[p, j] for every j outside p.
+__global__ void __launch_bounds__(kThreads) k_sweep_pivot(const MatDesc* __restrict__ mats, double* __restrict__ M,
+                                                          int k0, double* __restrict__ Pinv,
+                                                          int32_t* __restrict__ status) {
+    const MatDesc md = mats[blockIdx.x];
+    if (k0 >= md.nr) return;
+    const int nb = min(kNB, md.nr - k0);
+    __shared__ double P[kNB][kNB + 1];
+    double* A = M + md.moff;
+    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+        const int i = t / nb, j = t % nb;
+        P[i][j] = A[(int64_t)(k0 + i) * md.ld + k0 + j];
+    }
+    __syncthreads();
+    for (int k = 0; k < nb; ++k) {
+        double d = P[k][k];
+        if (!(d > 0.0) || !isfinite(d)) {
+            if (threadIdx.x == 0) atomicCAS(status, 0, DD_ERR_NOT_SPD);
+            d = 1.0;
+        }
+        const double inv = 1.0 / d;
+        double nv[4];
+        int cnt = 0;
+        for (int t = threadIdx.x; t < nb * nb; t += blockDim.x, ++cnt) {
+            const int i = t / nb, j = t % nb;
+            double v;
+            if (i == k && j == k) v = inv;
+            else if (i == k) v = -P[k][j] * inv;
+            else if (j == k) v = P[i][k] * inv;
+            else v = P[i][j] - P[i][k] * P[k][j] * inv;
+            nv[cnt] = v;
+        }
+        __syncthreads();
+        cnt = 0;
+        for (int t = threadIdx.x; t < nb * nb; t += blockDim.x, ++cnt) P[t / nb][t % nb] = nv[cnt];
+        __syncthreads();
+    }
+    double* Pout = Pinv + (size_t)blockIdx.x * kNB * kNB;
+    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) Pout[t] = P[t / nb][t % nb];
+    // row panel, one column per thread
+    for (int j = threadIdx.x; j < md.ns; j += blockDim.x) {
+        if (j >= k0 && j < k0 + nb) continue;
+        double col[kNB];
+#pragma unroll
+        for (int l = 0; l < kNB; ++l) col[l] = l < nb ? A[(int64_t)(k0 + l) * md.ld + j] : 0.0;
+        for (int i = 0; i < nb; ++i) {
+            double s = 0.0;
+#pragma unroll
+            for (int l = 0; l < kNB; ++l) s += (l < nb ? P[i][l] : 0.0) * col[l];
+            A[(int64_t)(k0 + i) * md.ld + j] = -s;
+        }
+    }
+}
+
+// Part 2: trailing update M[i][j] += M[i][p] * M[p][j] for i, j outside p
+// (64x64 output tiles, K = nb).  M[p][j] already holds -P^-1 B.
+__global__ void __launch_bounds__(kThreads) k_sweep_update(const MatDesc* __restrict__ mats, double* __restrict__ M,
+                                                           int k0) {
+    const MatDesc md = mats[blockIdx.z];
+    if (k0 >= md.nr) return;
+    const int nb = min(kNB, md.nr - k0);
+    const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+    if (i0 >= md.ns || j0 >= md.ns) return;
+    __shared__ double As[kNB][64];
+    __shared__ double Bs[kNB][64];
+    double* A = M + md.moff;
+    for (int t = threadIdx.x; t < 64 * kNB; t += blockDim.x) {
+        const int ii = t / kNB, k = t % kNB;
+        const int i = i0 + ii;
+        As[k][ii] = (k < nb && i < md.ns) ? A[(int64_t)i * md.ld + k0 + k] : 0.0;
+    }
+    for (int t = threadIdx.x; t < 64 * kNB; t += blockDim.x) {
+        const int k = t / 64, jj = t % 64;
+        const int j = j0 + jj;
+        Bs[k][jj] = (k < nb && j < md.ns) ? A[(int64_t)(k0 + k) * md.ld + j] : 0.0;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double acc[4][4] = {};
+    for (int k = 0; k < nb; ++k) {
+        double a[4], b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a[u] = As[k][ty + 16 * u];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) b[u] = Bs[k][tx + 16 * u];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int i = i0 + ty + 16 * u;
+        if (i >= md.ns || (i >= k0 && i < k0 + nb)) continue;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int j = j0 + tx + 16 * v;
+            if (j >= md.ns || (j >= k0 && j < k0 + nb)) continue;
+            A[(int64_t)i * md.ld + j] += acc[u][v];
+        }
+    }
+}
+
+// Part 3: column panel M[i][p] <- M[i][p] P^-1 for i outside p, and M[p][p] <- P^-1.
+__global__ void __launch_bounds__(kThreads) k_sweep_colpanel(const MatDesc* __restrict__ mats, double* __restrict__ M,
+                                                             int k0, const double* __restrict__ Pinv) {
+    const MatDesc md = mats[blockIdx.x];
+    if (k0 >= md.nr) return;
+    const int nb = min(kNB, md.nr - k0);
+    __shared__ double P[kNB][kNB + 1];
+    const double* Pin = Pinv + (size_t)blockIdx.x * kNB * kNB;
+    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) P[t / nb][t % nb] = Pin[t];
+    __syncthreads();
+    double* A = M + md.moff;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = warp; i < md.ns; i += nw) {
+        double* row = A + (int64_t)i * md.ld + k0;
+        if (i >= k0 && i < k0 + nb) {
+            if (lane < nb) row[lane] = P[i - k0][lane];
+            continue;
+        }
+        const double v = lane < nb ? row[lane] : 0.0;
+        double s = 0.0;
+        for (int m = 0; m < nb; ++m) s += __shfl_sync(0xffffffffu, v, m) * (lane < nb ? P[m][lane] : 0.0);
+        if (lane < nb) row[lane] = s;
+    }
+}
+
+// K~cc = sum_s B_c^T (A_cc - A_cr A_rr^-1 A_rc) B_c: one CTA per global corner row,
+// copies visited in subdomain order (deterministic).
+__global__ void k_coarse_assemble(int64_t n_corner, int32_t ldc, const int64_t* __restrict__ corner_ptr,
+                                  const int64_t* __restrict__ corner_slot, const int32_t* __restrict__ slot_sub,
+                                  const int32_t* __restrict__ slot_corner, const MatDesc* __restrict__ mats,
+                                  const double* __restrict__ M, double* __restrict__ K) {
+    const int64_t I = blockIdx.x;
+    if (I >= n_corner) return;
+    double* Krow = K + I * ldc;
+    for (int j = threadIdx.x; j < ldc; j += blockDim.x) Krow[j] = 0.0;
+    __syncthreads();
+    for (int64_t c = corner_ptr[I]; c < corner_ptr[I + 1]; ++c) {
+        const int64_t slot = corner_slot[c];
+        const MatDesc md = mats[slot_sub[slot]];
+        const int ci = (int)(slot - md.voff);   // row in M_s (>= nr)
+        const double* Mrow = M + md.moff + (int64_t)ci * md.ld;
+        for (int j = md.nr + threadIdx.x; j < md.ns; j += blockDim.x) {
+            const int J = slot_corner[md.voff + j];
+            Krow[J] += Mrow[j];
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_jacobi(int64_t n_lambda, const int64_t* __restrict__ mult_slot, const int32_t* __restrict__ slot_sub,
+                         const MatDesc* __restrict__ mats, const double* __restrict__ M, double* __restrict__ dinv) {
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < n_lambda; m += (int64_t)gridDim.x * blockDim.x) {
+        double d = 0.0;
+        for (int side = 0; side < 2; ++side) {
+            const int64_t slot = mult_slot[2 * m + side];
+            const MatDesc md = mats[slot_sub[slot]];
+            const int64_t i = slot - md.voff;
+            d += M[md.moff + i * md.ld + i];
+        }
+        dinv[m] = 1.0 / d;
+    }
+}
+
+__global__ void k_to_fp32(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        b[k] = (float)a[k];
+}
+
+// ----------------------------------------------------------------------------
+// Step: right-hand side (Newmark increment form)
+// ----------------------------------------------------------------------------
+
+// b_s = -dt^2 S^(s) e^n|_s - (owner ? d2g : 0), one 8-lane group per slot row.
+// With e^{n+1} = 2e^n - e^{n-1} + delta, the recurrence becomes A delta = b.
+__global__ void k_rhs(int64_t n_local, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col_dof,
+                      const double* __restrict__ Sv, const double* __restrict__ e_n, const double* __restrict__ d2g,
+                      const int32_t* __restrict__ slot_dof, const uint8_t* __restrict__ slot_own, double mdt2,
+                      double* __restrict__ b) {
+    // each warp owns 4 consecutive rows (8 lanes per row); the loop is warp-uniform
+    const int lane8 = threadIdx.x & 7;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w0 = warp * 4; w0 < n_local; w0 += nwarp * 4) {
+        const int64_t i = w0 + ((threadIdx.x & 31) >> 3);
+        double s = 0.0;
+        if (i < n_local)
+            for (int64_t k = row_ptr[i] + lane8; k < row_ptr[i + 1]; k += 8) s += Sv[k] * e_n[col_dof[k]];
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, 8);
+        if (lane8 == 0 && i < n_local) {
+            double v = mdt2 * s;
+            if (d2g && slot_own[i]) v -= d2g[slot_dof[i]];
+            b[i] = v;
+        }
+    }
+}
+
+// b <- b - A^(s) delta|_s (subassembled FP64 residual of the step system) and
+// the assembled residual norm: res[d] = sum over copies of the new b.
+__global__ void k_residual_local(int64_t n_local, const int64_t* __restrict__ row_ptr,
+                                 const int32_t* __restrict__ col_dof, const double* __restrict__ A,
+                                 const double* __restrict__ delta, double* __restrict__ b) {
+    const int lane8 = threadIdx.x & 7;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w0 = warp * 4; w0 < n_local; w0 += nwarp * 4) {
+        const int64_t i = w0 + ((threadIdx.x & 31) >> 3);
+        double s = 0.0;
+        if (i < n_local)
+            for (int64_t k = row_ptr[i] + lane8; k < row_ptr[i + 1]; k += 8) s += A[k] * delta[col_dof[k]];
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, 8);
+        if (lane8 == 0 && i < n_local) b[i] -= s;
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Batched dense GEMV over uneven subdomains
+// ----------------------------------------------------------------------------
+
+// x-source kinds (values in dd_internal.h):
+//   X_FLAT     x_j = v[voff + j]
+//   X_LAMBDA   x_j = (B_r^T v)_j  (sign * v[m])
+//   X_PCG      x_j = (B_r^T (z + beta p))_j, z = v, p = v2
+//   X_CORNER   x_j = v[corner(j)]
+//   X_RECOVER  interface: -(B_r^T v)_j ; corner: v2[corner(j)]
+
+struct XSrc {
+    int kind;
+    const double* v;
+    const double* v2;
+    const int32_t* slot_mult;
+    const int32_t* slot_corner;
+    const PcgScalars* sc;
+};
+
+struct GemvOut {
+    double* out;         // out[voff + row]
+    const double* base;  // optional: out = base + alpha * M x
+    double alpha;
+};
+
+__device__ __forceinline__ double xsrc_value(const XSrc& xs, int64_t slot, int64_t j) {
+    switch (xs.kind) {
+        case X_FLAT: return xs.v[slot];
+        case X_LAMBDA: {
+            const int m = xs.slot_mult[slot];
+            return m > 0 ? xs.v[m - 1] : (m < 0 ? -xs.v[-m - 1] : 0.0);
+        }
+        case X_PCG: {
+            const int m = xs.slot_mult[slot];
+            if (m == 0) return 0.0;
+            const int mi = (m > 0 ? m : -m) - 1;
+            const double pv = xs.v[mi] + xs.sc->beta * xs.v2[mi];
+            return m > 0 ? pv : -pv;
+        }
+        case X_CORNER: return xs.v[xs.slot_corner[slot]];
+        case X_RECOVER: {
+            const int m = xs.slot_mult[slot];
+            if (m != 0) return m > 0 ? -xs.v[m - 1] : xs.v[-m - 1];
+            const int c = xs.slot_corner[slot];
+            return c >= 0 ? xs.v2[c] : 0.0;
+        }
+        default: return xs.v[j];
+    }
+}
+
+template <typename TM>
+__global__ void __launch_bounds__(kThreads) k_gemv(const GemvTask* __restrict__ tasks, const MatDesc* __restrict__ mats,
+                                                   const TM* __restrict__ M, int mode, XSrc xs, GemvOut go,
+                                                   int staged, const int32_t* __restrict__ done) {
+    if (done && *done) return;
+    extern __shared__ unsigned char smem_raw[];
+    TM* xsh = reinterpret_cast<TM*>(smem_raw);
+    const GemvTask tk = tasks[blockIdx.x];
+    const MatDesc md = mats[tk.mat];
+    int c0, c1;
+    switch (mode) {
+        case GEMV_LOCAL: c0 = 0; c1 = md.nr; break;
+        case GEMV_SCHUR: c0 = md.nI; c1 = md.nr; break;
+        case GEMV_CORNER: c0 = md.nr; c1 = md.ns; break;
+        case GEMV_RECOVER: c0 = md.nI; c1 = md.ns; break;
+        default: c0 = 0; c1 = md.ns; break;
+    }
+    const int ncol = c1 - c0;
+    if (staged) {
+        for (int j = threadIdx.x; j < ncol; j += blockDim.x)
+            xsh[j] = (TM)xsrc_value(xs, md.voff + c0 + j, c0 + j);
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int row = tk.row0 + warp; row < tk.row1; row += nw) {
+        const TM* Mr = M + md.moff + (int64_t)row * md.ld + c0;
+        TM a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        int j = lane;
+        if (staged) {
+            for (; j + 96 < ncol; j += 128) {
+                a0 += Mr[j] * xsh[j];
+                a1 += Mr[j + 32] * xsh[j + 32];
+                a2 += Mr[j + 64] * xsh[j + 64];
+                a3 += Mr[j + 96] * xsh[j + 96];
+            }
+            for (; j < ncol; j += 32) a0 += Mr[j] * xsh[j];
+        } else {
+            for (; j < ncol; j += 32) a0 += Mr[j] * (TM)xsrc_value(xs, md.voff + c0 + j, c0 + j);
+        }
+        TM acc = warp_sum((a0 + a1) + (a2 + a3));
+        if (lane == 0) {
+            const int64_t o = md.voff + row;
+            double v = go.alpha * (double)acc;
+            if (go.base) v += go.base[o];
+            go.out[o] = v;
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Interface vectors
+// ----------------------------------------------------------------------------
+
+// d_r = sum_s B_r y_s (jump of y across each interface edge) and
+// f~_c = sum_s B_c^T (b_c - A_cr y): corner slots of y hold A_cr y after GEMV_LOCAL.
+__global__ void k_iface_rhs(int64_t n_lambda, int64_t n_corner, const int64_t* __restrict__ mult_slot,
+                            const int64_t* __restrict__ corner_ptr, const int64_t* __restrict__ corner_slot,
+                            const double* __restrict__ y, const double* __restrict__ b, double* __restrict__ g,
+                            double* __restrict__ fC) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < n_lambda) {
+        g[t] = y[mult_slot[2 * t]] - y[mult_slot[2 * t + 1]];
+    } else if (t < n_lambda + n_corner) {
+        const int64_t I = t - n_lambda;
+        double s = 0.0;
+        for (int64_t c = corner_ptr[I]; c < corner_ptr[I + 1]; ++c) {
+            const int64_t sl = corner_slot[c];
+            s += b[sl] - y[sl];
+        }
+        fC[I] = s;
+    }
+}
+
+// uC[I] = (add ? add[I] : 0) + sum over copies of w at the corner slots (B_c^T assembly).
+__global__ void k_corner_gather(int64_t n_corner, const int64_t* __restrict__ corner_ptr,
+                                const int64_t* __restrict__ corner_slot, const double* __restrict__ w,
+                                const double* __restrict__ add, double* __restrict__ uC,
+                                const int32_t* __restrict__ done) {
+    if (done && *done) return;
+    for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < n_corner; I += (int64_t)gridDim.x * blockDim.x) {
+        double s = add ? add[I] : 0.0;
+        for (int64_t c = corner_ptr[I]; c < corner_ptr[I + 1]; ++c) s += w[corner_slot[c]];
+        uC[I] = s;
+    }
+}
+
+// out[m] = (base ? base[m] : 0) + sign * (w[s1 slot] - w[s2 slot])   (sum_s B_r w_s)
+__global__ void k_jump(int64_t n_lambda, const int64_t* __restrict__ mult_slot, const double* __restrict__ w,
+                       const double* __restrict__ base, double sign, double* __restrict__ out) {
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < n_lambda; m += (int64_t)gridDim.x * blockDim.x) {
+        double v = sign * (w[mult_slot[2 * m]] - w[mult_slot[2 * m + 1]]);
+        if (base) v += base[m];
+        out[m] = v;
+    }
+}
+
+// CG start: q = jump(w) if have_q (K lambda0), r = g - q, z = D^-1 r, p = 0,
+// beta = 0; totals rz, gg, rr; done if rr <= tol^2 gg.
+__global__ void __launch_bounds__(kThreads) k_pcg_init(int64_t n_lambda, const int64_t* __restrict__ mult_slot,
+                                                       const double* __restrict__ w, int have_q,
+                                                       const double* __restrict__ g, const double* __restrict__ dinv,
+                                                       double tol, double* __restrict__ r, double* __restrict__ z,
+                                                       double* __restrict__ p, PcgScalars* sc,
+                                                       double* __restrict__ partials) {
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < n_lambda; m += (int64_t)gridDim.x * blockDim.x) {
+        const double q = have_q ? (w[mult_slot[2 * m]] - w[mult_slot[2 * m + 1]]) : 0.0;
+        const double rr = g[m] - q;
+        const double zz = dinv ? rr * dinv[m] : rr;
+        r[m] = rr;
+        z[m] = zz;
+        p[m] = 0.0;
+        v[0] += rr * zz;
+        v[1] += g[m] * g[m];
+        v[2] += rr * rr;
+    }
+    if (grid_sum<3>(v, partials, &sc->counter[0])) {
+        sc->rz = v[0];
+        sc->gg = v[1];
+        sc->rr = v[2];
+        sc->tol2 = tol * tol * v[1];
+        sc->beta = 0.0;
+        sc->alpha = 0.0;
+        sc->it = 0;
+        const bool finite = isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]);
+        sc->status = finite ? DD_OK : DD_ERR_NONFINITE;
+        sc->done = (!finite || v[2] <= sc->tol2) ? 1 : 0;
+    }
+}
+
+// p <- z + beta p ; q = jump(w) ; pq = p . q ; alpha = rz / pq
+__global__ void __launch_bounds__(kThreads) k_pcg_alpha(int64_t n_lambda, const int64_t* __restrict__ mult_slot,
+                                                        const double* __restrict__ w, const double* __restrict__ z,
+                                                        double* __restrict__ p, double* __restrict__ q, PcgScalars* sc,
+                                                        double* __restrict__ partials) {
+    if (sc->done) return;
+    const double beta = sc->beta;
+    double v[1] = {0.0};
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < n_lambda; m += (int64_t)gridDim.x * blockDim.x) {
+        const double pn = z[m] + beta * p[m];
+        const double qq = w[mult_slot[2 * m]] - w[mult_slot[2 * m + 1]];
+        p[m] = pn;
+        q[m] = qq;
+        v[0] += pn * qq;
+    }
+    if (grid_sum<1>(v, partials, &sc->counter[1])) {
+        sc->pq = v[0];
+        sc->alpha = sc->rz / v[0];
+    }
+}
+
+// lambda += alpha p ; r -= alpha q ; z = D^-1 r ; rr, rz ; convergence, beta
+__global__ void __launch_bounds__(kThreads) k_pcg_update(int64_t n_lambda, const double* __restrict__ p,
+                                                         const double* __restrict__ q, const double* __restrict__ dinv,
+                                                         double* __restrict__ lam, double* __restrict__ r,
+                                                         double* __restrict__ z, PcgScalars* sc,
+                                                         double* __restrict__ partials) {
+    if (sc->done) return;
+    const double alpha = sc->alpha;
+    double v[2] = {0.0, 0.0};
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < n_lambda; m += (int64_t)gridDim.x * blockDim.x) {
+        lam[m] += alpha * p[m];
+        const double rr = r[m] - alpha * q[m];
+        const double zz = dinv ? rr * dinv[m] : rr;
+        r[m] = rr;
+        z[m] = zz;
+        v[0] += rr * rr;
+        v[1] += rr * zz;
+    }
+    if (grid_sum<2>(v, partials, &sc->counter[2])) {
+        sc->rr = v[0];
+        sc->rz_new = v[1];
+        sc->it += 1;
+        if (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(sc->alpha)) {
+            sc->status = DD_ERR_NONFINITE;
+            sc->done = 1;
+        } else if (v[0] <= sc->tol2) {
+            sc->done = 1;
+        }
+        sc->beta = v[1] / sc->rz;
+        sc->rz = v[1];
+    }
+}
+
+// Assemble the correction from the owner copy of every dof (corner dofs: x_c):
+// delta_k[d] = x[owner slot]; delta_acc[d] (+)= delta_k[d]; e^{n+1} = 2e^n - e^{n-1} + delta.
+__global__ void k_writeback(int64_t n_dof, const int64_t* __restrict__ owner_slot, const int32_t* __restrict__ slot_corner,
+                            const double* __restrict__ x, const double* __restrict__ xC, const double* __restrict__ e_n,
+                            const double* __restrict__ e_nm1, double* __restrict__ delta_k,
+                            double* __restrict__ delta_acc, int first, double* __restrict__ e_np1) {
+    for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < n_dof; d += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t sl = owner_slot[d];
+        const int c = slot_corner[sl];
+        const double dv = c >= 0 ? xC[c] : x[sl];
+        double tot = dv;
+        if (delta_k) delta_k[d] = dv;
+        if (delta_acc) {
+            if (!first) tot += delta_acc[d];
+            delta_acc[d] = tot;
+        }
+        if (e_np1) e_np1[d] = 2.0 * e_n[d] - e_nm1[d] + tot;
+    }
+}
+
+__global__ void k_advance(int64_t n_dof, const double* __restrict__ e_n, const double* __restrict__ e_nm1,
+                          const double* __restrict__ delta, double* __restrict__ e_np1) {
+    for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < n_dof; d += (int64_t)gridDim.x * blockDim.x)
+        e_np1[d] = 2.0 * e_n[d] - e_nm1[d] + delta[d];
+}
+
+// Assemble the subassembled right-hand side per dof, s = sum over copies of b,
+// and give it wholly to the owner copy (other copies 0); ||s||^2 -> sc->norm_r2.
+// Without this the interface rows of a small residual would still carry
+// O(||b||) partial sums that cancel only after assembly, which an FP32
+// correction solve cannot resolve.
+__global__ void __launch_bounds__(kThreads) k_assemble_rhs(int64_t n_dof, const int64_t* __restrict__ copy_ptr,
+                                                           const int64_t* __restrict__ copy_slot, double* __restrict__ b,
+                                                           PcgScalars* sc, double* __restrict__ partials, int set_b) {
+    double v[1] = {0.0};
+    for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < n_dof; d += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c0 = copy_ptr[d], c1 = copy_ptr[d + 1];
+        double s = 0.0;
+        for (int64_t c = c0; c < c1; ++c) s += b[copy_slot[c]];
+        b[copy_slot[c0]] = s;                       // the first copy is the owner
+        for (int64_t c = c0 + 1; c < c1; ++c) b[copy_slot[c]] = 0.0;
+        v[0] += s * s;
+    }
+    if (grid_sum<1>(v, partials, &sc->counter[3])) {
+        if (set_b) sc->norm_b2 = v[0];
+        sc->norm_r2 = v[0];
+    }
+}
+
+__global__ void k_probe(int n_probe, const int32_t* __restrict__ pd, const double* __restrict__ pw,
+                        const double* __restrict__ e, double* __restrict__ out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3 * n_probe) return;
+    const int k = t / 3, c = t % 3;
+    double s = 0.0;
+    for (int le = 0; le < 6; ++le) s += e[pd[6 * k + le]] * pw[18 * k + 3 * le + c];
+    out[t] = s;
+}
+
+}  // namespace
+
+// ============================================================================
+// Launchers
+// ============================================================================
+
+int launch_csr_combine(const dd_handle* h, double ca, void* stream) {
+    const int64_t nnz = h->row_ptr.back();
+    k_csr_combine<<<reduce_blocks(nnz), kThreads, 0, S(stream)>>>(nnz, h->d.Tval, h->d.Sval, ca, h->d.Aval);
+    return (int)cudaGetLastError();
+}
+
+int launch_dense_assemble(const dd_handle* h, void* stream) {
+    CU_TRY(cudaMemsetAsync(h->d.M64, 0, sizeof(double) * (size_t)h->dense_elems, S(stream)));
+    const int64_t nl = h->sub_ptr.back();
+    k_dense_assemble<<<reduce_blocks(nl), kThreads, 0, S(stream)>>>(nl, h->d.row_ptr, h->d.col_loc, h->d.Aval,
+                                                                     h->d.slot_sub, h->d.mats, h->d.M64);
+    return (int)cudaGetLastError();
+}
+
+int launch_sweep(const dd_handle* h, bool coarse, int k0, void* stream) {
+    const MatDesc* mats = coarse ? h->d.coarse_desc : h->d.mats;
+    double* M = coarse ? h->d.K64 : h->d.M64;
+    const int nm = coarse ? 1 : h->n_sub;
+    const int nmax = coarse ? (int)h->corner_dof.size() : h->max_ns;
+    double* Pinv = coarse ? h->d.Pinv + (size_t)h->n_sub * kNB * kNB : h->d.Pinv;
+    k_sweep_pivot<<<nm, kThreads, 0, S(stream)>>>(mats, M, k0, Pinv, h->d.status);
+    const int tiles = (nmax + 63) / 64;
+    dim3 grid(tiles, tiles, nm);
+    k_sweep_update<<<grid, kThreads, 0, S(stream)>>>(mats, M, k0);
+    k_sweep_colpanel<<<nm, kThreads, 0, S(stream)>>>(mats, M, k0, Pinv);
+    return (int)cudaGetLastError();
+}
+
+int launch_coarse_assemble(const dd_handle* h, void* stream) {
+    const int64_t nc = (int64_t)h->corner_dof.size();
+    if (nc == 0) return 0;
+    k_coarse_assemble<<<(unsigned)nc, kThreads, 0, S(stream)>>>(nc, h->ldc, h->d.corner_ptr, h->d.corner_slot,
+                                                                h->d.slot_sub, h->d.slot_corner, h->d.mats, h->d.M64,
+                                                                h->d.K64);
+    return (int)cudaGetLastError();
+}
+
+int launch_factor_finish(const dd_handle* h, void* stream) {
+    const int64_t nl = (int64_t)h->mult_dof.size();
+    if (nl)
+        k_jacobi<<<reduce_blocks(nl), kThreads, 0, S(stream)>>>(nl, h->d.mult_slot, h->d.slot_sub, h->d.mats, h->d.M64,
+                                                                h->d.dinv);
+    k_to_fp32<<<4 * 152, kThreads, 0, S(stream)>>>(h->dense_elems, h->d.M64, h->d.M32);
+    const int64_t kc = (int64_t)h->corner_dof.size() * h->ldc;
+    if (kc) k_to_fp32<<<reduce_blocks(kc), kThreads, 0, S(stream)>>>(kc, h->d.K64, h->d.K32);
+    return (int)cudaGetLastError();
+}
+
+int launch_rhs(const dd_handle* h, const double* e_n, const double* d2g, double dt, void* stream) {
+    const int64_t nl = h->sub_ptr.back();
+    const int blocks = (int)std::min<int64_t>((nl * 8 + kThreads - 1) / kThreads, 152 * 16);
+    k_rhs<<<blocks, kThreads, 0, S(stream)>>>(nl, h->d.row_ptr, h->d.col_dof, h->d.Sval, e_n, d2g, h->d.slot_dof,
+                                              h->d.slot_own, -dt * dt, h->d.b);
+    return (int)cudaGetLastError();
+}
+
+int launch_residual_local(const dd_handle* h, void* stream) {
+    const int64_t nl = h->sub_ptr.back();
+    const int blocks = (int)std::min<int64_t>((nl * 8 + kThreads - 1) / kThreads, 152 * 16);
+    k_residual_local<<<blocks, kThreads, 0, S(stream)>>>(nl, h->d.row_ptr, h->d.col_dof, h->d.Aval, h->d.delta_k,
+                                                         h->d.b);
+    return (int)cudaGetLastError();
+}
+
+int launch_assembled_norm(const dd_handle* h, int set_b, void* stream) {
+    const int64_t nd = h->n_dof;
+    k_assemble_rhs<<<reduce_blocks(nd), kThreads, 0, S(stream)>>>(nd, h->d.copy_ptr, h->d.copy_slot, h->d.b, h->d.sc,
+                                                                  h->d.partials, set_b);
+    return (int)cudaGetLastError();
+}
+
+int launch_gemv(const dd_handle* h, int mode, int prec, int xkind, const double* v, const double* v2, double* out,
+                const double* base, double alpha, bool check_done, void* stream) {
+    const auto& tl = h->tasks[mode];
+    if (tl.empty()) return 0;
+    XSrc xs{xkind, v, v2, h->d.slot_mult, h->d.slot_corner, h->d.sc};
+    GemvOut go{out, base, alpha};
+    const MatDesc* mats = mode == GEMV_COARSE ? h->d.coarse_desc : h->d.mats;
+    const GemvTask* tasks = h->d.tasks[mode];
+    const int maxcol = mode == GEMV_COARSE ? (int)h->corner_dof.size() : h->max_ns;
+    const size_t elt = prec == DD_MIXED ? sizeof(float) : sizeof(double);
+    size_t smem = (size_t)maxcol * elt;
+    int staged = 1;
+    if (smem > 200 * 1024) {
+        staged = 0;
+        smem = 0;
+    }
+    const int32_t* done = check_done ? &h->d.sc->done : nullptr;
+    if (prec == DD_MIXED) {
+        const float* M = mode == GEMV_COARSE ? h->d.K32 : h->d.M32;
+        if (smem > 48 * 1024) CU_TRY(cudaFuncSetAttribute(k_gemv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_gemv<float><<<(unsigned)tl.size(), kThreads, smem, S(stream)>>>(tasks, mats, M, mode, xs, go, staged, done);
+    } else {
+        const double* M = mode == GEMV_COARSE ? h->d.K64 : h->d.M64;
+        if (smem > 48 * 1024) CU_TRY(cudaFuncSetAttribute(k_gemv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_gemv<double><<<(unsigned)tl.size(), kThreads, smem, S(stream)>>>(tasks, mats, M, mode, xs, go, staged, done);
+    }
+    return (int)cudaGetLastError();
+}
+
+int launch_iface_rhs(const dd_handle* h, void* stream) {
+    const int64_t nl = (int64_t)h->mult_dof.size(), nc = (int64_t)h->corner_dof.size();
+    const int64_t n = nl + nc;
+    if (n == 0) return 0;
+    k_iface_rhs<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, S(stream)>>>(
+        nl, nc, h->d.mult_slot, h->d.corner_ptr, h->d.corner_slot, h->d.y, h->d.b, h->d.g, h->d.fC);
+    return (int)cudaGetLastError();
+}
+
+int launch_corner_gather(const dd_handle* h, const double* w, const double* add, double* uC, bool check_done,
+                         void* stream) {
+    const int64_t nc = (int64_t)h->corner_dof.size();
+    if (nc == 0) return 0;
+    k_corner_gather<<<reduce_blocks(nc), kThreads, 0, S(stream)>>>(nc, h->d.corner_ptr, h->d.corner_slot, w, add, uC,
+                                                                   check_done ? &h->d.sc->done : nullptr);
+    return (int)cudaGetLastError();
+}
+
+int launch_jump(const dd_handle* h, const double* w, const double* base, double sign, double* out, void* stream) {
+    const int64_t nl = (int64_t)h->mult_dof.size();
+    if (nl == 0) return 0;
+    k_jump<<<reduce_blocks(nl), kThreads, 0, S(stream)>>>(nl, h->d.mult_slot, w, base, sign, out);
+    return (int)cudaGetLastError();
+}
+
+int launch_pcg_init(const dd_handle* h, int have_q, double tol, void* stream) {
+    const int64_t nl = (int64_t)h->mult_dof.size();
+    k_pcg_init<<<reduce_blocks(nl), kThreads, 0, S(stream)>>>(nl, h->d.mult_slot, h->d.w, have_q, h->d.g,
+                                                              h->prm.precond ? h->d.dinv : nullptr, tol, h->d.r, h->d.z,
+                                                              h->d.p, h->d.sc, h->d.partials);
+    return (int)cudaGetLastError();
+}
+
+int launch_pcg_alpha(const dd_handle* h, void* stream) {
+    const int64_t nl = (int64_t)h->mult_dof.size();
+    k_pcg_alpha<<<reduce_blocks(nl), kThreads, 0, S(stream)>>>(nl, h->d.mult_slot, h->d.w, h->d.z, h->d.p, h->d.q,
+                                                               h->d.sc, h->d.partials);
+    return (int)cudaGetLastError();
+}
+
+int launch_pcg_update(const dd_handle* h, void* stream) {
+    const int64_t nl = (int64_t)h->mult_dof.size();
+    k_pcg_update<<<reduce_blocks(nl), kThreads, 0, S(stream)>>>(nl, h->d.p, h->d.q, h->prm.precond ? h->d.dinv : nullptr,
+                                                                h->d.lam, h->d.r, h->d.z, h->d.sc, h->d.partials);
+    return (int)cudaGetLastError();
+}
+
+int launch_writeback(const dd_handle* h, const double* e_n, const double* e_nm1, double* delta_k, double* delta_acc,
+                     int first, double* e_np1, void* stream) {
+    const int64_t nd = h->n_dof;
+    k_writeback<<<reduce_blocks(nd), kThreads, 0, S(stream)>>>(nd, h->d.owner_slot, h->d.slot_corner, h->d.x, h->d.xC,
+                                                               e_n, e_nm1, delta_k, delta_acc, first, e_np1);
+    return (int)cudaGetLastError();
+}
+
+int launch_advance(const dd_handle* h, const double* e_n, const double* e_nm1, const double* delta, double* e_np1,
+                   void* stream) {
+    const int64_t nd = h->n_dof;
+    k_advance<<<reduce_blocks(nd), kThreads, 0, S(stream)>>>(nd, e_n, e_nm1, delta, e_np1);
+    return (int)cudaGetLastError();
+}
+
+int launch_probe(const dd_handle* h, const double* e, double* out, void* stream) {
+    if (h->n_probe == 0) return 0;
+    k_probe<<<(3 * h->n_probe + 127) / 128, 128, 0, S(stream)>>>(h->n_probe, h->d.probe_dof, h->d.probe_w, e, out);
+    return (int)cudaGetLastError();
+}

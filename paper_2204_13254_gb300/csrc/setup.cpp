@@ -1,0 +1,430 @@
+// Host-side tearing of the mesh (Sec. III-A) and Whitney element matrices (Sec. II-B).
+//
+// Everything here runs once per dd_setup on the CPU: edge extraction and
+// orientation, PEC edge removal, per-tet mass/curl-curl matrices, edge
+// multiplicities, local numbering [interior | interface | corner], the signed
+// Boolean B_r (one multiplier per edge shared by two subdomains, +1 in the lower
+// subdomain id) and the unsigned Boolean B_c (corners = edges shared by three or
+// more subdomains), and the subassembled local CSR matrices.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "dd_internal.h"
+
+namespace {
+
+// local edge k of a tet joins local vertices kEdge[k][0] -> kEdge[k][1]
+const int kEdge[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+const int kFace[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
+
+inline void cross3(const double* a, const double* b, double* c) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+inline double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+// Barycentric gradients g[4][3] and |volume| of a tet.  With d_i = X_i - X_0 and
+// det = d1 . (d2 x d3): grad l1 = d2 x d3 / det, grad l2 = d3 x d1 / det,
+// grad l3 = d1 x d2 / det, grad l0 = -(sum).  Returns the signed det.
+double tet_gradients(const double* X, double g[4][3], double* volume) {
+    double d[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int c = 0; c < 3; ++c) d[i][c] = X[3 * (i + 1) + c] - X[c];
+    double c23[3], c31[3], c12[3];
+    cross3(d[1], d[2], c23);
+    cross3(d[2], d[0], c31);
+    cross3(d[0], d[1], c12);
+    const double det = dot3(d[0], c23);
+    for (int c = 0; c < 3; ++c) {
+        g[1][c] = c23[c] / det;
+        g[2][c] = c31[c] / det;
+        g[3][c] = c12[c] / det;
+        g[0][c] = -(g[1][c] + g[2][c] + g[3][c]);
+    }
+    *volume = std::fabs(det) / 6.0;
+    return det;
+}
+
+// Unit-coefficient Whitney matrices in local orientation:
+//   T[p][q] = int W_p . W_q with int l_a l_b = vol (1 + delta_ab) / 20,
+//   S[p][q] = int curl W_p . curl W_q, curl W_ab = 2 grad l_a x grad l_b.
+void whitney_matrices(const double g[4][3], double vol, double T[36], double S[36]) {
+    double gg[4][4];
+    for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) gg[a][b] = dot3(g[a], g[b]);
+    auto m = [&](int a, int b) { return vol * (a == b ? 2.0 : 1.0) / 20.0; };
+    double curl[6][3];
+    for (int p = 0; p < 6; ++p) {
+        cross3(g[kEdge[p][0]], g[kEdge[p][1]], curl[p]);
+        for (int c = 0; c < 3; ++c) curl[p][c] *= 2.0;
+    }
+    for (int p = 0; p < 6; ++p) {
+        const int a = kEdge[p][0], b = kEdge[p][1];
+        for (int q = 0; q < 6; ++q) {
+            const int c = kEdge[q][0], d = kEdge[q][1];
+            T[6 * p + q] = m(a, c) * gg[b][d] - m(a, d) * gg[b][c] - m(b, c) * gg[a][d] + m(b, d) * gg[a][c];
+            S[6 * p + q] = vol * dot3(curl[p], curl[q]);
+        }
+    }
+}
+
+struct Tri {
+    int64_t a, b, c;
+    bool operator<(const Tri& o) const {
+        if (a != o.a) return a < o.a;
+        if (b != o.b) return b < o.b;
+        return c < o.c;
+    }
+    bool operator==(const Tri& o) const { return a == o.a && b == o.b && c == o.c; }
+};
+
+}  // namespace
+
+int dd_build_host(dd_handle* h, const dd_mesh* mesh, const int32_t* part, int32_t n_sub) {
+    const int64_t N = mesh->n_nodes, T = mesh->n_tets;
+    h->n_nodes = N;
+    h->n_tets = T;
+    h->mu = mesh->mu;
+    h->xyz.assign(mesh->xyz, mesh->xyz + 3 * N);
+    h->tets.assign(mesh->tets, mesh->tets + 4 * T);
+    h->eps.assign(T, 1.0);
+    if (mesh->eps) h->eps.assign(mesh->eps, mesh->eps + T);
+    h->part.assign(part, part + T);
+    h->n_sub = n_sub;
+    for (int64_t t = 0; t < 4 * T; ++t)
+        if (h->tets[t] < 0 || h->tets[t] >= N) return h->fail(DD_ERR_ARG, "tet references a node out of range");
+    for (int64_t t = 0; t < T; ++t)
+        if (h->part[t] < 0 || h->part[t] >= n_sub) return h->fail(DD_ERR_ARG, "part[] out of range");
+    for (int64_t t = 0; t < T; ++t)
+        if (!(h->eps[t] > 0.0)) return h->fail(DD_ERR_ARG, "eps must be positive");
+    if (!(h->mu > 0.0)) return h->fail(DD_ERR_ARG, "mu must be positive");
+
+    // ---- edges: distinct (lo, hi) node pairs in lexicographic order ----------
+    std::vector<int64_t> key(6 * T);
+    for (int64_t t = 0; t < T; ++t)
+        for (int k = 0; k < 6; ++k) {
+            int64_t a = h->tets[4 * t + kEdge[k][0]], b = h->tets[4 * t + kEdge[k][1]];
+            if (a == b) return h->fail(DD_ERR_MESH, "tet with a repeated node");
+            key[6 * t + k] = std::min(a, b) * N + std::max(a, b);
+        }
+    std::vector<int64_t> ukey(key);
+    std::sort(ukey.begin(), ukey.end());
+    ukey.erase(std::unique(ukey.begin(), ukey.end()), ukey.end());
+    h->n_edges = (int64_t)ukey.size();
+    h->edges.resize(2 * h->n_edges);
+    for (int64_t e = 0; e < h->n_edges; ++e) {
+        h->edges[2 * e] = ukey[e] / N;
+        h->edges[2 * e + 1] = ukey[e] % N;
+    }
+    auto edge_id = [&](int64_t a, int64_t b) {
+        const int64_t k = std::min(a, b) * N + std::max(a, b);
+        return (int64_t)(std::lower_bound(ukey.begin(), ukey.end(), k) - ukey.begin());
+    };
+
+    // ---- PEC: edges of triangles that belong to exactly one tet --------------
+    std::vector<Tri> faces(4 * T);
+    for (int64_t t = 0; t < T; ++t)
+        for (int f = 0; f < 4; ++f) {
+            int64_t v[3] = {h->tets[4 * t + kFace[f][0]], h->tets[4 * t + kFace[f][1]], h->tets[4 * t + kFace[f][2]]};
+            std::sort(v, v + 3);
+            faces[4 * t + f] = {v[0], v[1], v[2]};
+        }
+    std::sort(faces.begin(), faces.end());
+    std::vector<uint8_t> pec(h->n_edges, 0);
+    for (size_t i = 0; i < faces.size();) {
+        size_t j = i + 1;
+        while (j < faces.size() && faces[j] == faces[i]) ++j;
+        if (j - i > 2) return h->fail(DD_ERR_MESH, "non-manifold face shared by more than two tets");
+        if (j - i == 1) {
+            pec[edge_id(faces[i].a, faces[i].b)] = 1;
+            pec[edge_id(faces[i].a, faces[i].c)] = 1;
+            pec[edge_id(faces[i].b, faces[i].c)] = 1;
+        }
+        i = j;
+    }
+    std::vector<int64_t> edge_dof(h->n_edges, -1);
+    h->dof_edge.clear();
+    for (int64_t e = 0; e < h->n_edges; ++e)
+        if (!pec[e]) {
+            edge_dof[e] = (int64_t)h->dof_edge.size();
+            h->dof_edge.push_back(e);
+        }
+    h->n_dof = (int64_t)h->dof_edge.size();
+    if (h->n_dof == 0) return h->fail(DD_ERR_MESH, "mesh has no interior edges");
+
+    // ---- element matrices with global orientation lo -> hi --------------------
+    h->tet_dof.resize(6 * T);
+    h->That.resize(36 * T);
+    h->Shat.resize(36 * T);
+    h->grad.resize(12 * T);
+    h->vol.resize(T);
+    double bbox = 0.0;
+    for (int64_t i = 0; i < 3 * N; ++i) bbox = std::max(bbox, std::fabs(h->xyz[i]));
+    for (int64_t t = 0; t < T; ++t) {
+        double X[12];
+        for (int v = 0; v < 4; ++v)
+            for (int c = 0; c < 3; ++c) X[3 * v + c] = h->xyz[3 * (int64_t)h->tets[4 * t + v] + c];
+        double g[4][3], vol;
+        const double det = tet_gradients(X, g, &vol);
+        if (!(std::fabs(det) > 1e-13 * bbox * bbox * bbox) || !std::isfinite(det))
+            return h->fail(DD_ERR_MESH, "degenerate tetrahedron " + std::to_string(t));
+        h->vol[t] = vol;
+        for (int v = 0; v < 4; ++v)
+            for (int c = 0; c < 3; ++c) h->grad[12 * t + 3 * v + c] = g[v][c];
+        double Tl[36], Sl[36];
+        whitney_matrices(g, vol, Tl, Sl);
+        int sgn[6];
+        for (int k = 0; k < 6; ++k) {
+            const int64_t a = h->tets[4 * t + kEdge[k][0]], b = h->tets[4 * t + kEdge[k][1]];
+            sgn[k] = a < b ? 1 : -1;
+            h->tet_dof[6 * t + k] = edge_dof[edge_id(a, b)];
+        }
+        for (int p = 0; p < 6; ++p)
+            for (int q = 0; q < 6; ++q) {
+                h->That[36 * t + 6 * p + q] = sgn[p] * sgn[q] * Tl[6 * p + q];
+                h->Shat[36 * t + 6 * p + q] = sgn[p] * sgn[q] * Sl[6 * p + q];
+            }
+    }
+
+    // ---- multiplicity: distinct subdomains touching each dof ------------------
+    std::vector<int64_t> ds;  // dof * n_sub + sub
+    ds.reserve(6 * T);
+    for (int64_t t = 0; t < T; ++t)
+        for (int k = 0; k < 6; ++k) {
+            const int64_t d = h->tet_dof[6 * t + k];
+            if (d >= 0) ds.push_back(d * n_sub + h->part[t]);
+        }
+    std::sort(ds.begin(), ds.end());
+    ds.erase(std::unique(ds.begin(), ds.end()), ds.end());
+    std::vector<int32_t> mult(h->n_dof, 0);
+    h->owner.assign(h->n_dof, -1);
+    for (int64_t v : ds) {
+        const int64_t d = v / n_sub;
+        if (mult[d] == 0) h->owner[d] = (int32_t)(v % n_sub);
+        ++mult[d];
+    }
+
+    // ---- local numbering [interior | interface | corner], each by dof id ------
+    std::vector<std::vector<int64_t>> grp(3 * (size_t)n_sub);
+    for (int64_t v : ds) {
+        const int64_t d = v / n_sub;
+        const int s = (int)(v % n_sub);
+        const int gi = mult[d] == 1 ? 0 : (mult[d] == 2 ? 1 : 2);
+        grp[3 * s + gi].push_back(d);  // ds is sorted by dof, so each group is sorted
+    }
+    h->nI.assign(n_sub, 0);
+    h->nG.assign(n_sub, 0);
+    h->nC.assign(n_sub, 0);
+    h->sub_ptr.assign(n_sub + 1, 0);
+    h->local_dof.clear();
+    for (int s = 0; s < n_sub; ++s) {
+        h->nI[s] = (int32_t)grp[3 * s].size();
+        h->nG[s] = (int32_t)grp[3 * s + 1].size();
+        h->nC[s] = (int32_t)grp[3 * s + 2].size();
+        if (h->nI[s] + h->nG[s] == 0)
+            return h->fail(DD_ERR_PARTITION, "subdomain " + std::to_string(s) + " has no r unknowns");
+        for (int gi = 0; gi < 3; ++gi)
+            h->local_dof.insert(h->local_dof.end(), grp[3 * s + gi].begin(), grp[3 * s + gi].end());
+        h->sub_ptr[s + 1] = (int64_t)h->local_dof.size();
+    }
+    const int64_t n_local = h->sub_ptr[n_sub];
+
+    // slot metadata
+    h->slot_mult.assign(n_local, 0);
+    h->slot_corner.assign(n_local, -1);
+    h->slot_dof.resize(n_local);
+    h->slot_own.assign(n_local, 0);
+    h->owner_slot.assign(h->n_dof, -1);
+    h->slot_sub.assign(n_local, 0);
+    std::vector<int32_t>& slot_sub = h->slot_sub;
+    for (int s = 0; s < n_sub; ++s)
+        for (int64_t i = h->sub_ptr[s]; i < h->sub_ptr[s + 1]; ++i) {
+            slot_sub[i] = s;
+            const int64_t d = h->local_dof[i];
+            h->slot_dof[i] = (int32_t)d;
+            if (h->owner[d] == s) {
+                h->slot_own[i] = 1;
+                h->owner_slot[d] = i;
+            }
+        }
+
+    // copies of every dof (slots in subdomain order; the first is the owner)
+    h->copy_ptr.assign(h->n_dof + 1, 0);
+    for (int64_t i = 0; i < n_local; ++i) ++h->copy_ptr[h->local_dof[i] + 1];
+    for (int64_t d = 0; d < h->n_dof; ++d) h->copy_ptr[d + 1] += h->copy_ptr[d];
+    h->copy_slot.assign(n_local, -1);
+    {
+        std::vector<int64_t> fill(h->copy_ptr.begin(), h->copy_ptr.end() - 1);
+        for (int64_t i = 0; i < n_local; ++i) h->copy_slot[fill[h->local_dof[i]]++] = i;
+    }
+
+    // multipliers (m = 2) and corners (m >= 3), in dof order
+    std::vector<int64_t> mult_idx(h->n_dof, -1), corner_idx(h->n_dof, -1);
+    h->mult_dof.clear();
+    h->corner_dof.clear();
+    for (int64_t d = 0; d < h->n_dof; ++d) {
+        if (mult[d] == 2) {
+            mult_idx[d] = (int64_t)h->mult_dof.size();
+            h->mult_dof.push_back(d);
+        } else if (mult[d] >= 3) {
+            corner_idx[d] = (int64_t)h->corner_dof.size();
+            h->corner_dof.push_back(d);
+        }
+    }
+    const int64_t nl = (int64_t)h->mult_dof.size(), nc = (int64_t)h->corner_dof.size();
+    h->mult_sub.assign(2 * nl, -1);
+    h->mult_loc.assign(2 * nl, -1);
+    h->mult_slot.assign(2 * nl, -1);
+    std::vector<int64_t> ccount(nc + 1, 0);
+    for (int64_t i = 0; i < n_local; ++i) {
+        const int64_t d = h->local_dof[i];
+        const int s = slot_sub[i];
+        if (mult_idx[d] >= 0) {
+            const int64_t m = mult_idx[d];
+            const int side = (h->mult_sub[2 * m] < 0) ? 0 : 1;  // slots visited in subdomain order
+            h->mult_sub[2 * m + side] = s;
+            h->mult_loc[2 * m + side] = (int32_t)(i - h->sub_ptr[s]);
+            h->mult_slot[2 * m + side] = i;
+            h->slot_mult[i] = side == 0 ? (int32_t)(m + 1) : -(int32_t)(m + 1);
+        } else if (corner_idx[d] >= 0) {
+            h->slot_corner[i] = (int32_t)corner_idx[d];
+            ++ccount[corner_idx[d] + 1];
+        }
+    }
+    h->corner_ptr.assign(nc + 1, 0);
+    for (int64_t c = 0; c < nc; ++c) h->corner_ptr[c + 1] = h->corner_ptr[c] + ccount[c + 1];
+    h->corner_slot.assign(h->corner_ptr[nc], -1);
+    {
+        std::vector<int64_t> fill(h->corner_ptr.begin(), h->corner_ptr.end() - 1);
+        for (int64_t i = 0; i < n_local; ++i)  // subdomain order
+            if (h->slot_corner[i] >= 0) h->corner_slot[fill[h->slot_corner[i]]++] = i;
+    }
+
+    // ---- subassembled local CSR (rows = slots, per subdomain) -----------------
+    std::vector<std::vector<int64_t>> tets_of(n_sub);
+    for (int64_t t = 0; t < T; ++t) tets_of[h->part[t]].push_back(t);
+    std::vector<int32_t> loc_of(h->n_dof, -1);
+    h->row_ptr.assign(n_local + 1, 0);
+    h->col_loc.clear();
+    h->col_dof.clear();
+    h->Tval.clear();
+    h->Sval.clear();
+    h->mats.resize(n_sub);
+    h->max_nr = h->max_ns = 0;
+    int64_t moff = 0;
+    struct Trip {
+        int64_t key;
+        double t, s;
+    };
+    std::vector<Trip> trip;
+    for (int s = 0; s < n_sub; ++s) {
+        const int64_t base = h->sub_ptr[s];
+        const int32_t ns = (int32_t)(h->sub_ptr[s + 1] - base);
+        for (int32_t i = 0; i < ns; ++i) loc_of[h->local_dof[base + i]] = i;
+        trip.clear();
+        for (int64_t t : tets_of[s]) {
+            for (int p = 0; p < 6; ++p) {
+                const int64_t dp = h->tet_dof[6 * t + p];
+                if (dp < 0) continue;
+                for (int q = 0; q < 6; ++q) {
+                    const int64_t dq = h->tet_dof[6 * t + q];
+                    if (dq < 0) continue;
+                    trip.push_back({(int64_t)loc_of[dp] * ns + loc_of[dq], h->eps[t] * h->That[36 * t + 6 * p + q],
+                                    h->Shat[36 * t + 6 * p + q] / h->mu});
+                }
+            }
+        }
+        std::stable_sort(trip.begin(), trip.end(), [](const Trip& a, const Trip& b) { return a.key < b.key; });
+        for (size_t i = 0; i < trip.size();) {
+            size_t j = i;
+            double tv = 0.0, sv = 0.0;
+            while (j < trip.size() && trip[j].key == trip[i].key) {
+                tv += trip[j].t;
+                sv += trip[j].s;
+                ++j;
+            }
+            const int64_t row = trip[i].key / ns, col = trip[i].key % ns;
+            h->col_loc.push_back((int32_t)col);
+            h->col_dof.push_back((int32_t)h->local_dof[base + col]);
+            h->Tval.push_back(tv);
+            h->Sval.push_back(sv);
+            ++h->row_ptr[base + row + 1];
+            i = j;
+        }
+        for (int32_t i = 0; i < ns; ++i) loc_of[h->local_dof[base + i]] = -1;
+        MatDesc md;
+        md.moff = moff;
+        md.voff = base;
+        md.nI = h->nI[s];
+        md.nr = h->nI[s] + h->nG[s];
+        md.ns = ns;
+        md.ld = (ns + 3) / 4 * 4;
+        moff += (int64_t)ns * md.ld;
+        h->mats[s] = md;
+        h->max_nr = std::max(h->max_nr, md.nr);
+        h->max_ns = std::max(h->max_ns, md.ns);
+    }
+    for (int64_t i = 0; i < n_local; ++i) h->row_ptr[i + 1] += h->row_ptr[i];
+    h->dense_elems = moff;
+    h->ldc = (int32_t)((nc + 3) / 4 * 4);
+
+    // ---- batched GEMV task lists ------------------------------------------------
+    for (int mode = 0; mode < GEMV_NMODES; ++mode) {
+        auto& tl = h->tasks[mode];
+        tl.clear();
+        if (mode == GEMV_COARSE) {
+            for (int64_t r0 = 0; r0 < nc; r0 += kRowsPerTask)
+                tl.push_back({0, (int32_t)r0, (int32_t)std::min<int64_t>(nc, r0 + kRowsPerTask), 0});
+            continue;
+        }
+        for (int s = 0; s < n_sub; ++s) {
+            const MatDesc& md = h->mats[s];
+            int32_t r0 = 0, r1 = 0;
+            if (mode == GEMV_LOCAL) { r0 = 0; r1 = md.ns; }
+            if (mode == GEMV_SCHUR) { r0 = md.nI; r1 = md.ns; }
+            if (mode == GEMV_CORNER) { r0 = md.nI; r1 = md.nr; }
+            if (mode == GEMV_RECOVER) { r0 = 0; r1 = md.nr; }
+            for (int32_t a = r0; a < r1; a += kRowsPerTask) tl.push_back({s, a, std::min(r1, a + kRowsPerTask), 0});
+        }
+    }
+    return DD_OK;
+}
+
+int dd_locate_probes(dd_handle* h, int32_t n, const double* p) {
+    h->probe_dof.assign(6 * (size_t)n, 0);
+    h->probe_w.assign(18 * (size_t)n, 0.0);
+    for (int32_t k = 0; k < n; ++k) {
+        int64_t found = -1;
+        double lam[4] = {0, 0, 0, 0};
+        for (int64_t t = 0; t < h->n_tets && found < 0; ++t) {
+            const double* g = &h->grad[12 * t];
+            const double* x0 = &h->xyz[3 * (int64_t)h->tets[4 * t]];
+            const double dx[3] = {p[3 * k] - x0[0], p[3 * k + 1] - x0[1], p[3 * k + 2] - x0[2]};
+            double l[4];
+            l[1] = dot3(g + 3, dx);
+            l[2] = dot3(g + 6, dx);
+            l[3] = dot3(g + 9, dx);
+            l[0] = 1.0 - l[1] - l[2] - l[3];
+            if (l[0] >= -1e-12 && l[1] >= -1e-12 && l[2] >= -1e-12 && l[3] >= -1e-12) {
+                found = t;
+                std::memcpy(lam, l, sizeof(l));
+            }
+        }
+        if (found < 0) return h->fail(DD_ERR_ARG, "probe " + std::to_string(k) + " lies outside the mesh");
+        const double* g = &h->grad[12 * found];
+        for (int e = 0; e < 6; ++e) {
+            const int a = kEdge[e][0], b = kEdge[e][1];
+            const int64_t va = h->tets[4 * found + a], vb = h->tets[4 * found + b];
+            const double sg = va < vb ? 1.0 : -1.0;
+            const int64_t d = h->tet_dof[6 * found + e];
+            h->probe_dof[6 * k + e] = d >= 0 ? (int32_t)d : 0;
+            for (int c = 0; c < 3; ++c)
+                h->probe_w[18 * k + 3 * e + c] = d >= 0 ? sg * (lam[a] * g[3 * b + c] - lam[b] * g[3 * a + c]) : 0.0;
+        }
+    }
+    h->n_probe = n;
+    return DD_OK;
+}

@@ -1,0 +1,307 @@
+"""Thin Python binding of libdd.so (C ABI in include/dd.h).
+
+Argument marshalling only: every step of the field solve runs in the CUDA
+library.  Device buffers are torch tensors; their data pointers and the current
+torch stream are passed straight through.  If libdd.so is missing the import
+fails loudly -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdd.so")
+
+DD_OK, DD_ERR_ARG, DD_ERR_MESH, DD_ERR_PARTITION, DD_ERR_NOT_SPD = 0, 1, 2, 3, 4
+DD_ERR_NO_CONVERGENCE, DD_ERR_NONFINITE, DD_ERR_TIMEOUT, DD_ERR_CUDA, DD_ERR_STATE = 5, 6, 7, 8, 9
+DD_FP64, DD_MIXED = 0, 1
+
+SYMBOLS = ["dd_setup", "dd_set_params", "dd_get_sizes", "dd_get_maps", "dd_set_probes", "dd_bind_workspace",
+           "dd_factor", "dd_step", "dd_schur_apply", "dd_probe", "dd_get_state", "dd_set_state", "dd_profile",
+           "dd_destroy", "dd_last_error"]
+N_STAGES = 9
+STAGES = ["rhs", "local_solve", "iface_apply", "coarse", "corner", "recover", "vector", "refine", "factor"]
+
+
+class dd_mesh(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("n_tets", C.c_int64), ("xyz", C.POINTER(C.c_double)),
+                ("tets", C.POINTER(C.c_int32)), ("eps", C.POINTER(C.c_double)), ("mu", C.c_double)]
+
+
+class dd_params(C.Structure):
+    _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("max_it", C.c_int), ("precond", C.c_int),
+                ("warm_start", C.c_int), ("refine_tol", C.c_double), ("max_refine", C.c_int), ("chunk", C.c_int)]
+
+
+class dd_sizes(C.Structure):
+    _fields_ = [("n_edges", C.c_int64), ("n_dof", C.c_int64), ("n_sub", C.c_int32), ("n_lambda", C.c_int64),
+                ("n_corner", C.c_int64), ("n_local", C.c_int64), ("nnz_local", C.c_int64), ("max_nr", C.c_int32),
+                ("max_ns", C.c_int32), ("workspace_bytes", C.c_size_t), ("dense_bytes_fp64", C.c_int64)]
+
+
+class dd_maps(C.Structure):
+    _fields_ = [("edges", C.c_void_p), ("dof_edge", C.c_void_p), ("sub_ptr", C.c_void_p), ("local_dof", C.c_void_p),
+                ("n_int", C.c_void_p), ("n_gam", C.c_void_p), ("n_cor", C.c_void_p), ("mult_dof", C.c_void_p),
+                ("mult_sub", C.c_void_p), ("mult_loc", C.c_void_p), ("corner_dof", C.c_void_p),
+                ("owner", C.c_void_p)]
+
+
+class dd_stats(C.Structure):
+    _fields_ = [("iters", C.c_int), ("refinements", C.c_int), ("resid", C.c_double), ("status", C.c_int)]
+
+
+class dd_profile_stats(C.Structure):
+    _fields_ = [("launches", C.c_int64 * N_STAGES), ("work", C.c_int64 * N_STAGES), ("ms", C.c_double * N_STAGES),
+                ("bytes", C.c_double * N_STAGES), ("total_launches", C.c_int64)]
+
+
+def load_library(path: str = LIB_PATH):
+    if not os.path.exists(path):
+        raise ImportError(f"libdd.so not built at {path}; run paper_2204_13254_gb300.build.build()")
+    lib = C.CDLL(path)
+    vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+    sig = {
+        "dd_setup": (C.c_int, [C.POINTER(dd_mesh), C.POINTER(C.c_int32), i32, C.POINTER(dd_params), C.POINTER(vp)]),
+        "dd_set_params": (C.c_int, [vp, C.POINTER(dd_params)]),
+        "dd_get_sizes": (C.c_int, [vp, C.POINTER(dd_sizes)]),
+        "dd_get_maps": (C.c_int, [vp, C.POINTER(dd_maps)]),
+        "dd_set_probes": (C.c_int, [vp, i32, C.POINTER(C.c_double)]),
+        "dd_bind_workspace": (C.c_int, [vp, vp, C.c_size_t, vp]),
+        "dd_factor": (C.c_int, [vp, C.c_double, vp]),
+        "dd_step": (C.c_int, [vp, vp, vp, C.POINTER(dd_stats), vp]),
+        "dd_schur_apply": (C.c_int, [vp, vp, vp, vp]),
+        "dd_probe": (C.c_int, [vp, vp, vp]),
+        "dd_get_state": (C.c_int, [vp, vp, vp, C.POINTER(i64), vp]),
+        "dd_set_state": (C.c_int, [vp, vp, vp, i64, vp]),
+        "dd_profile": (C.c_int, [vp, C.c_int, C.POINTER(dd_profile_stats), vp]),
+        "dd_destroy": (None, [vp]),
+        "dd_last_error": (C.c_char_p, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = load_library()
+    return _lib
+
+
+class DDError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"dd status {code}: {msg}")
+        self.code = code
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def make_params(precision=DD_FP64, tol=1e-12, max_it=500, precond=1, warm_start=1, refine_tol=1e-12, max_refine=4,
+                chunk=8):
+    return dd_params(precision, tol, max_it, precond, warm_start, refine_tol, max_refine, chunk)
+
+
+# ---- C-ABI-named wrappers ------------------------------------------------------
+
+def dd_setup(xyz, tets, part, n_sub, eps=None, mu=1.0, params=None):
+    """Host tearing (no GPU work).  Returns an opaque handle (c_void_p)."""
+    L = lib()
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    tets = np.ascontiguousarray(tets, dtype=np.int32)
+    part = np.ascontiguousarray(part, dtype=np.int32)
+    epsa = None if eps is None else np.ascontiguousarray(eps, dtype=np.float64)
+    m = dd_mesh(len(xyz), len(tets), xyz.ctypes.data_as(C.POINTER(C.c_double)),
+                tets.ctypes.data_as(C.POINTER(C.c_int32)),
+                None if epsa is None else epsa.ctypes.data_as(C.POINTER(C.c_double)), float(mu))
+    h = C.c_void_p()
+    prm = params if params is not None else make_params()
+    rc = L.dd_setup(C.byref(m), part.ctypes.data_as(C.POINTER(C.c_int32)), int(n_sub), C.byref(prm), C.byref(h))
+    if rc != DD_OK:
+        msg = L.dd_last_error(h).decode() if h.value else ""
+        if h.value:
+            L.dd_destroy(h)
+        raise DDError(rc, msg)
+    return h
+
+
+def _check(h, rc):
+    if rc != DD_OK:
+        raise DDError(rc, lib().dd_last_error(h).decode())
+
+
+def dd_get_sizes(h):
+    s = dd_sizes()
+    _check(h, lib().dd_get_sizes(h, C.byref(s)))
+    return s
+
+
+def dd_get_maps(h):
+    s = dd_get_sizes(h)
+    out = dict(
+        edges=np.zeros((s.n_edges, 2), np.int64), dof_edge=np.zeros(s.n_dof, np.int64),
+        sub_ptr=np.zeros(s.n_sub + 1, np.int64), local_dof=np.zeros(s.n_local, np.int64),
+        n_int=np.zeros(s.n_sub, np.int32), n_gam=np.zeros(s.n_sub, np.int32), n_cor=np.zeros(s.n_sub, np.int32),
+        mult_dof=np.zeros(s.n_lambda, np.int64), mult_sub=np.zeros((s.n_lambda, 2), np.int32),
+        mult_loc=np.zeros((s.n_lambda, 2), np.int32), corner_dof=np.zeros(s.n_corner, np.int64),
+        owner=np.zeros(s.n_dof, np.int32))
+    m = dd_maps(*[out[k].ctypes.data for k, _ in dd_maps._fields_])
+    _check(h, lib().dd_get_maps(h, C.byref(m)))
+    return out
+
+
+def dd_set_probes(h, points):
+    p = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+    _check(h, lib().dd_set_probes(h, len(p), p.ctypes.data_as(C.POINTER(C.c_double))))
+
+
+def dd_bind_workspace(h, ws, stream=None):
+    _check(h, lib().dd_bind_workspace(h, _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def dd_factor(h, dt, stream=None):
+    _check(h, lib().dd_factor(h, float(dt), _stream(stream)))
+
+
+def dd_step(h, d2g=None, e_out=None, stats=True, stream=None, raise_on_error=True):
+    st = dd_stats()
+    rc = lib().dd_step(h, _ptr(d2g), _ptr(e_out), C.byref(st) if stats else None, _stream(stream))
+    if raise_on_error:
+        _check(h, rc)
+    return dict(rc=rc, iters=st.iters, refinements=st.refinements, resid=st.resid, status=st.status)
+
+
+def dd_schur_apply(h, lam, out, stream=None):
+    _check(h, lib().dd_schur_apply(h, _ptr(lam), _ptr(out), _stream(stream)))
+
+
+def dd_probe(h, out, stream=None):
+    _check(h, lib().dd_probe(h, _ptr(out), _stream(stream)))
+
+
+def dd_get_state(h, e_n, e_nm1, stream=None):
+    step = C.c_int64()
+    _check(h, lib().dd_get_state(h, _ptr(e_n), _ptr(e_nm1), C.byref(step), _stream(stream)))
+    return step.value
+
+
+def dd_set_state(h, e_n, e_nm1, step, stream=None):
+    _check(h, lib().dd_set_state(h, _ptr(e_n), _ptr(e_nm1), int(step), _stream(stream)))
+
+
+def dd_profile(h, enable=-1, read=True, stream=None):
+    """enable: 1 reset+start, 0 stop, -1 unchanged.  Returns per-stage dict when read."""
+    st = dd_profile_stats()
+    _check(h, lib().dd_profile(h, int(enable), C.byref(st) if read else None, _stream(stream)))
+    if not read:
+        return None
+    return dict(total_launches=st.total_launches,
+                stages={STAGES[k]: dict(launches=st.launches[k], work=st.work[k], ms=st.ms[k], bytes=st.bytes[k])
+                        for k in range(N_STAGES)})
+
+
+def dd_destroy(h):
+    if h is not None and h.value:
+        lib().dd_destroy(h)
+
+
+# ---- convenience wrapper ---------------------------------------------------------
+
+class FieldSolver:
+    """Owns a handle and its torch-allocated workspace on one CUDA device."""
+
+    def __init__(self, xyz, tets, part, n_sub, eps=None, mu=1.0, params=None, probes=None, device="cuda"):
+        self.h = dd_setup(xyz, tets, part, n_sub, eps, mu, params)
+        self.sizes = dd_get_sizes(self.h)
+        self.n_dof = self.sizes.n_dof
+        self.n_lambda = self.sizes.n_lambda
+        if probes is not None:
+            dd_set_probes(self.h, probes)
+        self.n_probe = 0 if probes is None else len(np.asarray(probes).reshape(-1, 3))
+        self.device = device
+        self.ws = None
+
+    def bind(self):
+        import torch
+        nbytes = self.sizes.workspace_bytes
+        self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        off = (-self.ws.data_ptr()) % 256
+        self.ws_view = self.ws[off:off + nbytes]
+        dd_bind_workspace(self.h, self.ws_view)
+        return self
+
+    def maps(self):
+        return dd_get_maps(self.h)
+
+    def dof_of_pairs(self, pairs):
+        """dof ids of node pairs (lo, hi) -- host marshalling for source vectors."""
+        m = self.maps()
+        edges = m["edges"][m["dof_edge"]]
+        n = int(max(edges.max(), np.max(pairs))) + 1
+        keys = edges[:, 0] * n + edges[:, 1]
+        pk = np.asarray(pairs)[:, 0] * n + np.asarray(pairs)[:, 1]
+        pos = np.searchsorted(keys, pk)
+        assert np.all(keys[pos] == pk), "pair is not an interior edge"
+        return pos
+
+    def factor(self, dt):
+        dd_factor(self.h, dt)
+
+    def set_params(self, params):
+        _check(self.h, lib().dd_set_params(self.h, C.byref(params)))
+
+    def step(self, d2g=None, e_out=None, stats=True, raise_on_error=True):
+        return dd_step(self.h, d2g, e_out, stats, raise_on_error=raise_on_error)
+
+    def schur_apply(self, lam):
+        import torch
+        out = torch.empty_like(lam)
+        dd_schur_apply(self.h, lam, out)
+        return out
+
+    def probe(self):
+        import torch
+        out = torch.empty(3 * self.n_probe, dtype=torch.float64, device=self.device)
+        dd_probe(self.h, out)
+        return out
+
+    def get_state(self):
+        import torch
+        a = torch.empty(self.n_dof, dtype=torch.float64, device=self.device)
+        b = torch.empty_like(a)
+        step = dd_get_state(self.h, a, b)
+        return a, b, step
+
+    def set_state(self, e_n, e_nm1, step):
+        dd_set_state(self.h, e_n, e_nm1, step)
+
+    def profile(self, enable=-1, read=True):
+        return dd_profile(self.h, enable, read)
+
+    def close(self):
+        dd_destroy(self.h)
+        self.h = None
+        self.ws = None
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None) is not None:
+                self.close()
+        except Exception:
+            pass
