@@ -51,6 +51,12 @@ def parse():
     ap.add_argument("--tol32", type=float, default=1e-5, help="inner interface CG tolerance, mixed")
     ap.add_argument("--refine-tol", type=float, default=1e-10, help="FP64 step-residual target, mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", choices=["fp64", "mixed"], default=None, help="time one precision only")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-profile", action="store_true", help="skip the per-stage event-profiled pass")
+    ap.add_argument("--cavity", type=int, nargs=2, metavar=("N", "K"), default=None,
+                    help="profiling case: unit PEC cavity of N^3 cubes in K^3 subdomains instead of --config "
+                         "(dt = the 48^3 cavity's dt scaled by 48/N)")
     return ap.parse_args()
 
 
@@ -187,8 +193,12 @@ def run_ours(args, rank, world, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     cfg = args.config
-    w = W.config(cfg)
-    dt = load_dt(cfg)
+    if args.cavity:
+        w = W.cavity(args.cavity[0], args.cavity[1])
+        dt = load_dt(4) * 48.0 / args.cavity[0]
+    else:
+        w = W.config(cfg)
+        dt = load_dt(cfg)
     K, Wu = args.steps, args.warmup
     t0 = time.perf_counter()
     fs = D.FieldSolver(w.xyz, w.tets, w.part, w.n_sub, w.eps, w.mu,
@@ -213,15 +223,19 @@ def run_ours(args, rank, world, local):
         if world > 1:
             torch.distributed.barrier()
 
-    def timed(params, clocks):
+    def run_steps(params, profile, clocks=None):
+        """W warm-up steps, then K timed steps (CUDA events on the launch stream)."""
         fs.set_params(params)
         fs.set_state(zero, zero, 0)
         for k in range(Wu):
             fs.step(D2G[k], stats=True)
         barrier()
         torch.cuda.synchronize()
-        fs.profile(enable=1, read=False)
-        clocks.start()
+        fs.profile(enable=1, read=False)          # reset the launch counters
+        if not profile:
+            fs.profile(enable=0, read=False)      # count launches, record no events
+        if clocks:
+            clocks.start()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         its, refs = [], []
@@ -231,7 +245,8 @@ def run_ours(args, rank, world, local):
             refs.append(st["refinements"])
         ev1.record(stream)
         torch.cuda.synchronize()
-        clocks.stop()
+        if clocks:
+            clocks.stop()
         barrier()
         ms = ev0.elapsed_time(ev1)
         prof = fs.profile(enable=0, read=True)
@@ -241,31 +256,47 @@ def run_ours(args, rank, world, local):
     clocks = Clocks(local)
     p64 = D.make_params(precision=D.DD_FP64, tol=args.tol64)
     p32 = D.make_params(precision=D.DD_MIXED, tol=args.tol32, refine_tol=args.refine_tol, max_refine=6)
-    ms64, it64, _, prof64, e64 = timed(p64, clocks)
-    ms32, it32, ref32, prof32, e32 = timed(p32, clocks)
-    rel = float(torch.linalg.norm(e32 - e64) / torch.linalg.norm(e64))
+    nan = float("nan")
+    ms64 = ms32 = nan
+    it64 = it32 = ref32 = np.zeros(1)
+    prof64 = prof32 = None
+    e64 = e32 = None
+    # headline timings: no event profiling inside the timed region
+    if args.only in (None, "fp64"):
+        ms64, it64, _, prof64, e64 = run_steps(p64, False, clocks)
+    if args.only in (None, "mixed"):
+        ms32, it32, ref32, prof32, e32 = run_steps(p32, False, clocks)
+    rel = float(torch.linalg.norm(e32 - e64) / torch.linalg.norm(e64)) if e32 is not None and e64 is not None else nan
+    # per-stage breakdown: a second pass over the same steps with CUDA events around every launch
+    if not args.no_profile:
+        if args.only in (None, "fp64"):
+            prof64 = run_steps(p64, True)[3]
+        if args.only in (None, "mixed"):
+            prof32 = run_steps(p32, True)[3]
 
     # end-to-end: per step, H2D of the source from pinned host memory, the C-ABI step, D2H of e^{n+1}
-    host_src = torch.zeros((K, n), dtype=torch.float64).pin_memory()
-    host_src.copy_(D2G[Wu:].cpu())
-    host_e = torch.empty(n, dtype=torch.float64).pin_memory()
-    dsrc = torch.empty(n, dtype=torch.float64, device=dev)
-    fs.set_params(p32)
-    fs.set_state(zero, zero, 0)
-    for k in range(Wu):
-        fs.step(D2G[k], stats=False)
-    barrier()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for k in range(K):
-        dsrc.copy_(host_src[k], non_blocking=True)
-        fs.step(dsrc, e_out, stats=False)
-        host_e.copy_(e_out, non_blocking=True)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    ms_e2e = ev0.elapsed_time(ev1)
+    ms_e2e = nan
+    if not args.no_e2e:
+        host_src = torch.zeros((K, n), dtype=torch.float64).pin_memory()
+        host_src.copy_(D2G[Wu:].cpu())
+        host_e = torch.empty(n, dtype=torch.float64).pin_memory()
+        dsrc = torch.empty(n, dtype=torch.float64, device=dev)
+        fs.set_params(p32 if args.only != "fp64" else p64)
+        fs.set_state(zero, zero, 0)
+        for k in range(Wu):
+            fs.step(D2G[k], stats=False)
+        barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for k in range(K):
+            dsrc.copy_(host_src[k], non_blocking=True)
+            fs.step(dsrc, e_out, stats=False)
+            host_e.copy_(e_out, non_blocking=True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms_e2e = ev0.elapsed_time(ev1)
 
     def allmax(x):
         if world == 1:
@@ -284,6 +315,8 @@ def run_ours(args, rank, world, local):
 
 def stage_table(prof, K):
     out = {}
+    if not prof:
+        return out
     for name, st in prof["stages"].items():
         if st["launches"] == 0:
             continue
@@ -292,6 +325,21 @@ def stage_table(prof, K):
                      "full_launches_per_step": st["work"] / K, "algorithmic_GB_per_step": st["bytes"] / K / 1e9,
                      "achieved_GBs": gbs}
     return out
+
+
+def _clean(x):
+    """JSON-safe copy: NaN/inf -> None."""
+    if isinstance(x, dict):
+        return {k: _clean(v) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [_clean(v) for v in x]
+    if isinstance(x, float) and not np.isfinite(x):
+        return None
+    if isinstance(x, (np.floating,)):
+        return _clean(float(x))
+    if isinstance(x, (np.integer,)):
+        return int(x)
+    return x
 
 
 def main():
@@ -333,55 +381,62 @@ def main():
     peak, peak_kind, peaks = load_peaks()
     st32 = stage_table(r["prof32"], K)
     st64 = stage_table(r["prof64"], K)
-    dom = max(st32, key=lambda k: st32[k]["ms_per_step"] if k not in ("vector", "factor") else -1)
-    d = st32[dom]
-    achieved = d["achieved_GBs"]
+    head = "mixed" if args.only != "fp64" else "fp64"
+    st_head = st32 if head == "mixed" else st64
+    cand = {k: v for k, v in st_head.items() if k not in ("vector", "factor")}
+    dom = max(cand, key=lambda k: cand[k]["ms_per_step"]) if cand else None
+    achieved = cand[dom]["achieved_GBs"] if dom else None
     sizes = r["sizes"]
     w = r["workload"]
-    value = world * K / (r["ms32"] / 1e3)
+    ms_head = r["ms32"] if head == "mixed" else r["ms64"]
+    value = world * K / (ms_head / 1e3)
     v64 = world * K / (r["ms64"] / 1e3)
+    v32 = world * K / (r["ms32"] / 1e3)
     cb = None
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and not args.cavity:
         try:
-            cb = cpu_baseline(args.config, r["dt"], float(np.mean(r["it32"])), w.n_sub)
+            its = r["it32"] if head == "mixed" else r["it64"]
+            cb = cpu_baseline(args.config, r["dt"], float(np.mean(its)), w.n_sub)
         except Exception as ex:  # the baseline is context only; never fail the GPU line on it
             cb = {"error": repr(ex)[:200]}
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
+    if os.path.exists(tpath) and dom:
         try:
             tj = json.load(open(tpath))
-            traffic = tj.get(f"config{args.config}", {}).get(dom)
+            traffic = tj.get(f"config{args.config}", {}).get(f"{head}:{dom}")
         except Exception:
             traffic = None
+    prof_head = r["prof32"] if head == "mixed" else r["prof64"]
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
-        "ms_per_step": r["ms32"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64", "data": "synthetic",
+        "ms_per_step": ms_head / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if head == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": (f"{w.name}: PEC box {w.dims[0]}x{w.dims[1]}x{w.dims[2]} Kuhn cubes, {len(w.tets)} tets, "
                                 f"{sizes.n_dof} edge dofs, {w.n_sub} subdomains, {sizes.n_lambda} multipliers, "
                                 f"{sizes.n_corner} corners, Gaussian z-line pulse, dt=2xCFL={r['dt']:.6g}"),
                    "l2_policy": "inputs larger than L2 (dense subdomain operators "
                                 f"{sizes.dense_bytes_fp64 / 1e9:.1f} GB FP64 + half that FP32), no flush",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
-        "mixed": {"steps_per_s": value, "ms_per_step": r["ms32"] / K, "iters_per_step": float(np.mean(r["it32"])),
+        "mixed": {"steps_per_s": v32, "ms_per_step": r["ms32"] / K, "iters_per_step": float(np.mean(r["it32"])),
                   "refinements_per_step": float(np.mean(r["ref32"])), "inner_tol": args.tol32,
                   "refine_tol": args.refine_tol, "stages": st32},
         "fp64": {"steps_per_s": v64, "ms_per_step": r["ms64"] / K, "iters_per_step": float(np.mean(r["it64"])),
                  "tol": args.tol64, "stages": st64},
-        "speedup_mixed_vs_fp64": value / v64,
+        "speedup_mixed_vs_fp64": v32 / v64,
         "rel_err_mixed_vs_fp64": r["rel"],
         "setup_s": r["t_setup"], "factor_s": r["t_factor"],
-        "roofline": {"bound": "hbm", "kernel": f"k_gemv<float> ({dom})", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": f"k_gemv<{'float' if head == 'mixed' else 'double'}> ({dom})",
+                     "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs" + ("" if peak_kind == "measured" else " (no MEASURED_PEAKS.json)")},
         "cpu_baseline": cb,
         "e2e": {"value": world * K / (r["ms_e2e"] / 1e3), "unit": "steps/s",
                 "h2d_bytes_per_step": int(sizes.n_dof * 8), "d2h_bytes_per_step": int(sizes.n_dof * 8)},
-        "gpu_launches": int(r["prof32"]["total_launches"]),
+        "gpu_launches": int(prof_head["total_launches"]) if prof_head else None,
         "clocks": r["clocks"],
     }
-    print(json.dumps(line), flush=True)
+    print(json.dumps(_clean(line)), flush=True)
     r["fs"].close()
     if world > 1:
         import torch.distributed as dist

@@ -189,6 +189,16 @@ size_t dd_workspace_layout(dd_handle* h, bool assign) {
     L.take(d.y, nl);
     L.take(d.w, nl);
     L.take(d.x, nl);
+    L.take(d.bf, nl);
+    L.take(d.wf, nl);
+    L.take(d.zf, nm);
+    L.take(d.pf, nm);
+    L.take(d.lamf, nm);
+    L.take(d.lamf_scratch, nm);
+    L.take(d.fCf, nc);
+    L.take(d.uCf, nc);
+    L.take(d.vCf, nc);
+    L.take(d.xCf, nc);
     L.take(d.lam, nm);
     L.take(d.g, nm);
     L.take(d.r, nm);
@@ -220,28 +230,74 @@ int read_scalars(dd_handle* h, PcgScalars* out, cudaStream_t s) {
 
 // w <- interface operator pieces for x-source (kind, v, v2):
 // rows Gamma: S_Gamma z + Psi_Gamma K~cc^-1 Psi^T z ; then the caller jumps w.
+// Vector set of one precision: DD_MIXED GEMVs read/write FP32 shadows.
+struct Vecs {
+    bool f32;
+    float* wf;      // interface-operator output (FP32) or null (FP64 path uses d.w)
+    float* zf;
+    float* pf;
+    float* lamf;
+    float* fCf;
+    float* uCf;
+    float* vCf;
+    float* xCf;
+    float* bf;
+};
+
+Vecs vecs(dd_handle* h, int prec) {
+    if (prec != DD_MIXED) return Vecs{false, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    const DevPtrs& d = h->d;
+    return Vecs{true, d.wf, d.zf, d.pf, d.lamf, d.fCf, d.uCf, d.vCf, d.xCf, d.bf};
+}
+
+XSrc xsrc(int kind, const double* v, const double* v2, const float* vf, const float* v2f) {
+    XSrc x{};
+    x.kind = kind;
+    x.v = v;
+    x.v2 = v2;
+    x.vf = vf;
+    x.v2f = v2f;
+    return x;
+}
+
+// FP64 path writes the double output; the FP32 path writes the FP32 output
+// (out32) and, where a double consumer exists, the double output too.
+GemvOut gout(double* out, const double* base, float* out32, const float* base32, double alpha) {
+    return GemvOut{out, base, out32, base32, alpha};
+}
+
+// w <- interface operator pieces for x-source (kind, v, v2) of Eq. f1schur:
+// rows Gamma: S_Gamma z + Psi_Gamma K~cc^-1 Psi^T z (the caller jumps w).
 // Inside the CG loop (check_done) launches after convergence exit early; their
 // full-work count is added by dd_solve once the iteration count is known.
-int apply_schur_w(dd_handle* h, int prec, int kind, const double* v, const double* v2, bool check_done, cudaStream_t s) {
+int apply_schur_w(dd_handle* h, int prec, int kind, const double* v, const double* v2, const float* vf,
+                  const float* v2f, bool check_done, cudaStream_t s) {
+    const Vecs V = vecs(h, prec);
     int rc;
     {
         Prof P(h, ST_SCHUR, s, 1, !check_done, prec);
-        rc = launch_gemv(h, GEMV_SCHUR, prec, kind, v, v2, h->d.w, nullptr, 1.0, check_done, s);
+        rc = launch_gemv(h, GEMV_SCHUR, prec, xsrc(kind, v, v2, vf, v2f),
+                         V.f32 ? gout(nullptr, nullptr, V.wf, nullptr, 1.0) : gout(h->d.w, nullptr, nullptr, nullptr, 1.0),
+                         check_done, s);
     }
     if (rc) return rc;
     if (h->corner_dof.empty()) return 0;
     {
         Prof P(h, ST_VEC, s, 1, false);
-        rc = launch_corner_gather(h, h->d.w, nullptr, h->d.uC, check_done, s);
+        rc = launch_corner_gather(h, h->d.w, V.wf, nullptr, h->d.uC, V.uCf, check_done, s);
     }
     if (rc) return rc;
     {
         Prof P(h, ST_COARSE, s, 1, !check_done, prec);
-        rc = launch_gemv(h, GEMV_COARSE, prec, X_FLAT, h->d.uC, nullptr, h->d.vC, nullptr, 1.0, check_done, s);
+        rc = launch_gemv(h, GEMV_COARSE, prec, xsrc(X_FLAT, h->d.uC, nullptr, V.uCf, nullptr),
+                         V.f32 ? gout(nullptr, nullptr, V.vCf, nullptr, 1.0) : gout(h->d.vC, nullptr, nullptr, nullptr, 1.0),
+                         check_done, s);
     }
     if (rc) return rc;
     Prof P(h, ST_CORNER, s, 1, !check_done, prec);
-    return launch_gemv(h, GEMV_CORNER, prec, X_CORNER, h->d.vC, nullptr, h->d.w, h->d.w, -1.0, check_done, s);
+    return launch_gemv(h, GEMV_CORNER, prec, xsrc(X_CORNER, h->d.vC, nullptr, V.vCf, nullptr),
+                       V.f32 ? gout(nullptr, nullptr, V.wf, V.wf, -1.0) : gout(h->d.w, h->d.w, nullptr, nullptr, -1.0),
+                       check_done, s);
 }
 
 // Adds n full-work launches of the CG-loop stages after the iteration count is known.
@@ -255,33 +311,41 @@ void count_cg_work(dd_handle* h, int prec, int n) {
 }
 
 // Solve the torn system A x = b for the local right-hand sides in d.b
-// (subassembled), leaving x in d.x (r slots) and x_c in d.xC.
-// Returns a DD status; iteration count and residual in *it / *res.
+// (subassembled; DD_MIXED also needs the FP32 shadow d.bf), leaving x in d.x
+// (r slots) and x_c in d.xC.  Returns a DD status; iteration count and the
+// final relative interface residual in *it_out / *res_out.
 int dd_solve(dd_handle* h, int prec, double tol, bool warm, int* it_out, double* res_out, cudaStream_t s) {
     const bool has_c = !h->corner_dof.empty();
     const bool has_l = !h->mult_dof.empty();
+    const Vecs V = vecs(h, prec);
+    const size_t nlb = sizeof(double) * h->mult_dof.size();
     // y = A_rr^-1 b_r (r rows) and A_cr y (corner rows)          Eq. rF1 / F1uc
     {
         Prof P(h, ST_LOCAL, s, 1, true, prec);
-        CK(h, launch_gemv(h, GEMV_LOCAL, prec, X_FLAT, h->d.b, nullptr, h->d.y, nullptr, 1.0, false, s), "gemv local");
+        CK(h, launch_gemv(h, GEMV_LOCAL, prec, xsrc(X_FLAT, h->d.b, nullptr, V.bf, nullptr),
+                          gout(h->d.y, nullptr, nullptr, nullptr, 1.0), false, s), "gemv local");
     }
     // g = d_r ; f~_c
     {
         Prof P(h, ST_VEC, s, 1, false);
-        CK(h, launch_iface_rhs(h, s), "iface rhs");
+        CK(h, launch_iface_rhs(h, V.fCf, s), "iface rhs");
     }
     if (has_c && has_l) {
         // g = d_r - F_rc K~cc^-1 f~_c                                Eq. f1schur
         {
             Prof P(h, ST_COARSE, s, 1, true, prec);
-            CK(h, launch_gemv(h, GEMV_COARSE, prec, X_FLAT, h->d.fC, nullptr, h->d.vC, nullptr, 1.0, false, s), "coarse");
+            CK(h, launch_gemv(h, GEMV_COARSE, prec, xsrc(X_FLAT, h->d.fC, nullptr, V.fCf, nullptr),
+                              V.f32 ? gout(nullptr, nullptr, V.vCf, nullptr, 1.0) : gout(h->d.vC, nullptr, nullptr, nullptr, 1.0),
+                              false, s), "coarse");
         }
         {
             Prof P(h, ST_CORNER, s, 1, true, prec);
-            CK(h, launch_gemv(h, GEMV_CORNER, prec, X_CORNER, h->d.vC, nullptr, h->d.w, nullptr, -1.0, false, s), "corner");
+            CK(h, launch_gemv(h, GEMV_CORNER, prec, xsrc(X_CORNER, h->d.vC, nullptr, V.vCf, nullptr),
+                              V.f32 ? gout(nullptr, nullptr, V.wf, nullptr, -1.0) : gout(h->d.w, nullptr, nullptr, nullptr, -1.0),
+                              false, s), "corner");
         }
         Prof P(h, ST_VEC, s, 1, false);
-        CK(h, launch_jump(h, h->d.w, h->d.g, -1.0, h->d.g, s), "jump");
+        CK(h, launch_jump(h, h->d.w, V.wf, h->d.g, -1.0, h->d.g, s), "jump");
     }
     int status = DD_OK;
     int iters = 0;
@@ -289,23 +353,24 @@ int dd_solve(dd_handle* h, int prec, double tol, bool warm, int* it_out, double*
     if (has_l) {
         const bool use_warm = warm && h->lam_valid;
         if (use_warm) {
-            CK(h, apply_schur_w(h, prec, X_LAMBDA, h->d.lam, nullptr, false, s), "apply lambda0");
+            CK(h, apply_schur_w(h, prec, X_LAMBDA, h->d.lam, nullptr, V.lamf, nullptr, false, s), "apply lambda0");
         } else {
-            CK(h, (int)cudaMemsetAsync(h->d.lam, 0, sizeof(double) * h->mult_dof.size(), s), "memset");
+            CK(h, (int)cudaMemsetAsync(h->d.lam, 0, nlb, s), "memset");
+            CK(h, (int)cudaMemsetAsync(h->d.lamf, 0, sizeof(float) * h->mult_dof.size(), s), "memset");
         }
         {
             Prof P(h, ST_VEC, s, 1, false);
-            CK(h, launch_pcg_init(h, use_warm ? 1 : 0, tol, s), "pcg init");
+            CK(h, launch_pcg_init(h, use_warm ? 1 : 0, tol, V.wf, V.zf, V.pf, s), "pcg init");
         }
         PcgScalars hs;
         CK(h, read_scalars(h, &hs, s), "pcg scalars");
         while (!hs.done && hs.it < h->prm.max_it) {
             const int n = std::min(h->prm.chunk, h->prm.max_it - hs.it);
             for (int k = 0; k < n; ++k) {
-                CK(h, apply_schur_w(h, prec, X_PCG, h->d.z, h->d.p, true, s), "apply");
+                CK(h, apply_schur_w(h, prec, X_PCG, h->d.z, h->d.p, V.zf, V.pf, true, s), "apply");
                 Prof P(h, ST_VEC, s, 2, false);
-                CK(h, launch_pcg_alpha(h, s), "pcg alpha");
-                CK(h, launch_pcg_update(h, s), "pcg update");
+                CK(h, launch_pcg_alpha(h, V.wf, V.pf, s), "pcg alpha");
+                CK(h, launch_pcg_update(h, V.zf, V.lamf, s), "pcg update");
             }
             CK(h, read_scalars(h, &hs, s), "pcg scalars");
         }
@@ -321,19 +386,24 @@ int dd_solve(dd_handle* h, int prec, double tol, bool warm, int* it_out, double*
         if (has_l) {
             {
                 Prof P(h, ST_SCHUR, s, 1, true, prec);
-                CK(h, launch_gemv(h, GEMV_SCHUR, prec, X_LAMBDA, h->d.lam, nullptr, h->d.w, nullptr, 1.0, false, s), "Frc^T");
+                CK(h, launch_gemv(h, GEMV_SCHUR, prec, xsrc(X_LAMBDA, h->d.lam, nullptr, V.lamf, nullptr),
+                                  V.f32 ? gout(nullptr, nullptr, V.wf, nullptr, 1.0) : gout(h->d.w, nullptr, nullptr, nullptr, 1.0),
+                                  false, s), "Frc^T");
             }
             Prof P(h, ST_VEC, s, 1, false);
-            CK(h, launch_corner_gather(h, h->d.w, h->d.fC, h->d.uC, false, s), "corner gather");
+            CK(h, launch_corner_gather(h, h->d.w, V.wf, h->d.fC, h->d.uC, V.uCf, false, s), "corner gather");
         }
         Prof P(h, ST_COARSE, s, 1, true, prec);
-        CK(h, launch_gemv(h, GEMV_COARSE, prec, X_FLAT, has_l ? h->d.uC : h->d.fC, nullptr, h->d.xC, nullptr, 1.0,
-                          false, s), "xc");
+        const double* src64 = has_l ? h->d.uC : h->d.fC;
+        const float* src32 = has_l ? V.uCf : V.fCf;
+        CK(h, launch_gemv(h, GEMV_COARSE, prec, xsrc(X_FLAT, src64, nullptr, src32, nullptr),
+                          gout(h->d.xC, nullptr, V.xCf, nullptr, 1.0), false, s), "xc");
     }
     // x_r = y + A_rr^-1 (-B_r^T lambda) - A_rr^-1 A_rc x_c                  Eq. rF1
     {
         Prof P(h, ST_RECOVER, s, 1, true, prec);
-        CK(h, launch_gemv(h, GEMV_RECOVER, prec, X_RECOVER, h->d.lam, h->d.xC, h->d.x, h->d.y, 1.0, false, s), "recover");
+        CK(h, launch_gemv(h, GEMV_RECOVER, prec, xsrc(X_RECOVER, h->d.lam, h->d.xC, V.lamf, V.xCf),
+                          gout(h->d.x, h->d.y, nullptr, nullptr, 1.0), false, s), "recover");
     }
     if (it_out) *it_out = iters;
     if (res_out) *res_out = res;
@@ -534,17 +604,24 @@ int dd_step(dd_handle* h, const double* d2g, double* e_out, dd_stats* stats, voi
         // FP64 iterative refinement of the step system with FP32 DD correction solves
         {
             Prof P(h, ST_REFINE, s, 1, false);
-            CK(h, launch_assembled_norm(h, 1, s), "norm b");
+            CK(h, launch_assembled_norm(h, 1, h->d.bf, s), "norm b");
         }
         PcgScalars hs;
         for (int k = 0; k < h->prm.max_refine; ++k) {
             const bool warm = (k == 0) && h->prm.warm_start != 0;
-            if (k == 1 && !h->mult_dof.empty())
+            if (k == 1 && !h->mult_dof.empty()) {
                 CK(h, (int)cudaMemcpyAsync(h->d.lam_scratch, h->d.lam, sizeof(double) * h->mult_dof.size(),
                                            cudaMemcpyDeviceToDevice, s), "save lambda");
+                CK(h, (int)cudaMemcpyAsync(h->d.lamf_scratch, h->d.lamf, sizeof(float) * h->mult_dof.size(),
+                                           cudaMemcpyDeviceToDevice, s), "save lambda");
+            }
             int it = 0;
             double r = 0.0;
-            int st = dd_solve(h, DD_MIXED, h->prm.tol, warm, &it, &r, s);
+            // the first pass solves to tol; a later pass only has to cut the current
+            // residual (resid, relative to ||b||) down to refine_tol, with a 3x margin
+            double tol_k = h->prm.tol;
+            if (k > 0 && resid > 0.0) tol_k = std::min(0.1, std::max(h->prm.tol, 0.3 * h->prm.refine_tol / resid));
+            int st = dd_solve(h, DD_MIXED, tol_k, warm, &it, &r, s);
             iters += it;
             ++refinements;
             if (st != DD_OK && st != DD_ERR_NO_CONVERGENCE) return st;
@@ -555,7 +632,7 @@ int dd_step(dd_handle* h, const double* d2g, double* e_out, dd_stats* stats, voi
             {
                 Prof P(h, ST_REFINE, s, 2, true);
                 CK(h, launch_residual_local(h, s), "residual");
-                CK(h, launch_assembled_norm(h, 0, s), "norm r");
+                CK(h, launch_assembled_norm(h, 0, h->d.bf, s), "norm r");
             }
             CK(h, read_scalars(h, &hs, s), "scalars");
             resid = hs.norm_b2 > 0 ? std::sqrt(hs.norm_r2 / hs.norm_b2) : 0.0;
@@ -566,9 +643,12 @@ int dd_step(dd_handle* h, const double* d2g, double* e_out, dd_stats* stats, voi
             if (resid <= h->prm.refine_tol) break;
             if (k + 1 == h->prm.max_refine) status = DD_ERR_NO_CONVERGENCE;
         }
-        if (refinements > 1 && !h->mult_dof.empty())
+        if (refinements > 1 && !h->mult_dof.empty()) {
             CK(h, (int)cudaMemcpyAsync(h->d.lam, h->d.lam_scratch, sizeof(double) * h->mult_dof.size(),
                                        cudaMemcpyDeviceToDevice, s), "restore lambda");
+            CK(h, (int)cudaMemcpyAsync(h->d.lamf, h->d.lamf_scratch, sizeof(float) * h->mult_dof.size(),
+                                       cudaMemcpyDeviceToDevice, s), "restore lambda");
+        }
         {
             Prof P(h, ST_VEC, s, 1, false);
             CK(h, launch_advance(h, e_n, e_nm1, h->d.delta, e_np1, s), "advance");
@@ -592,9 +672,9 @@ int dd_schur_apply(dd_handle* h, const double* lam, double* out, void* stream) {
     if (!h->factored) return h->fail(DD_ERR_STATE, "dd_schur_apply before dd_factor");
     if (h->mult_dof.empty()) return DD_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    CK(h, apply_schur_w(h, DD_FP64, X_LAMBDA, lam, nullptr, false, s), "apply");
+    CK(h, apply_schur_w(h, DD_FP64, X_LAMBDA, lam, nullptr, nullptr, nullptr, false, s), "apply");
     Prof P(h, ST_VEC, s, 1, false);
-    CK(h, launch_jump(h, h->d.w, nullptr, 1.0, out, s), "jump");
+    CK(h, launch_jump(h, h->d.w, nullptr, nullptr, 1.0, out, s), "jump");
     return DD_OK;
 }
 

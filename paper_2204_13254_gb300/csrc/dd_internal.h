@@ -37,6 +37,33 @@ enum GemvMode : int {
     GEMV_NMODES = 5
 };
 
+// Source of the x vector of a batched GEMV (staged in shared memory per CTA).
+// kind (X_*): X_FLAT x_j = v[slot]; X_LAMBDA x_j = (B_r^T v)_j; X_PCG x_j =
+// (B_r^T (z + beta p))_j with z = v, p = v2; X_CORNER x_j = v[corner(slot)];
+// X_RECOVER interface slot -(B_r^T v)_j, corner slot v2[corner(slot)];
+// X_COARSE x_j = v[j].  k_gemv<double> reads v/v2, k_gemv<float> reads the
+// FP32 shadows vf/v2f so that it executes no FP64 instruction.
+struct XSrc {
+    int kind;
+    const double* v;
+    const double* v2;
+    const float* vf;
+    const float* v2f;
+    const int32_t* slot_mult;
+    const int32_t* slot_corner;
+    const struct PcgScalars* sc;
+};
+
+// Output of a batched GEMV: out[voff+row] = base + alpha * (M x)_row, written in
+// FP64 (out/base) and/or FP32 (out32/base32; FP32 arithmetic).
+struct GemvOut {
+    double* out;
+    const double* base;
+    float* out32;
+    const float* base32;
+    double alpha;
+};
+
 // Device scalars of the interface CG (one struct in the workspace).
 struct PcgScalars {
     double rz;        // r . z
@@ -93,10 +120,8 @@ struct DevPtrs {
     double* y = nullptr;             // GEMV outputs / local solutions
     double* w = nullptr;             // interface operator output per slot
     double* x = nullptr;             // recovered local solution
-    float* bf = nullptr;             // FP32 shadows for DD_MIXED
-    float* yf = nullptr;
+    float* bf = nullptr;             // FP32 shadows for DD_MIXED (inputs/outputs of k_gemv<float>)
     float* wf = nullptr;
-    float* xf = nullptr;
     // interface vectors (n_lambda)
     double* lam = nullptr;
     double* g = nullptr;
@@ -110,8 +135,14 @@ struct DevPtrs {
     double* uC = nullptr;
     double* vC = nullptr;
     double* xC = nullptr;
+    float* fCf = nullptr;
     float* uCf = nullptr;
     float* vCf = nullptr;
+    float* xCf = nullptr;
+    float* zf = nullptr;             // [n_lambda] shadows
+    float* pf = nullptr;
+    float* lamf = nullptr;
+    float* lamf_scratch = nullptr;
     // global vectors (n_dof)
     double* delta = nullptr;         // assembled correction of the step
     double* delta_k = nullptr;       // assembled correction of one refinement
@@ -201,7 +232,8 @@ struct dd_handle {
 };
 
 constexpr int kNB = 32;              // pivot block of the dense elimination
-constexpr int kRowsPerTask = 32;     // rows per CTA of the batched GEMV
+// rows per CTA of the batched GEMV, per mode (LOCAL, SCHUR, CORNER, RECOVER, COARSE)
+constexpr int kRowsPerMode[5] = {32, 64, 64, 32, 8};
 constexpr int kMaxPartials = 4096;   // block partials of the grid reductions
 
 // setup.cpp
@@ -217,16 +249,16 @@ int launch_coarse_assemble(const dd_handle* h, void* stream);
 int launch_factor_finish(const dd_handle* h, void* stream);
 int launch_rhs(const dd_handle* h, const double* e_n, const double* d2g, double dt, void* stream);
 int launch_residual_local(const dd_handle* h, void* stream);
-int launch_assembled_norm(const dd_handle* h, int set_b, void* stream);
-int launch_gemv(const dd_handle* h, int mode, int prec, int xkind, const double* v, const double* v2, double* out,
-                const double* base, double alpha, bool check_done, void* stream);
-int launch_iface_rhs(const dd_handle* h, void* stream);
-int launch_corner_gather(const dd_handle* h, const double* w, const double* add, double* uC, bool check_done,
-                         void* stream);
-int launch_jump(const dd_handle* h, const double* w, const double* base, double sign, double* out, void* stream);
-int launch_pcg_init(const dd_handle* h, int have_q, double tol, void* stream);
-int launch_pcg_alpha(const dd_handle* h, void* stream);
-int launch_pcg_update(const dd_handle* h, void* stream);
+int launch_assembled_norm(const dd_handle* h, int set_b, float* bf, void* stream);
+int launch_gemv(const dd_handle* h, int mode, int prec, XSrc xs, GemvOut go, bool check_done, void* stream);
+int launch_iface_rhs(const dd_handle* h, float* fCf, void* stream);
+int launch_corner_gather(const dd_handle* h, const double* w, const float* wf, const double* add, double* uC, float* uCf,
+                         bool check_done, void* stream);
+int launch_jump(const dd_handle* h, const double* w, const float* wf, const double* base, double sign, double* out,
+                void* stream);
+int launch_pcg_init(const dd_handle* h, int have_q, double tol, const float* wf, float* zf, float* pf, void* stream);
+int launch_pcg_alpha(const dd_handle* h, const float* wf, float* pf, void* stream);
+int launch_pcg_update(const dd_handle* h, float* zf, float* lamf, void* stream);
 int launch_writeback(const dd_handle* h, const double* e_n, const double* e_nm1, double* delta_k, double* delta_acc,
                      int first, double* e_np1, void* stream);
 int launch_advance(const dd_handle* h, const double* e_n, const double* e_nm1, const double* delta, double* e_np1,

@@ -55,6 +55,7 @@ __device__ void block_sum(double (&v)[NV]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+    __syncthreads();  // red[] may still be read by a previous call
     if (lane == 0)
 #pragma unroll
         for (int k = 0; k < NV; ++k) red[k][warp] = v[k];
@@ -70,7 +71,9 @@ __device__ void block_sum(double (&v)[NV]) {
 }
 
 // Grid reduction: every block contributes NV partials; returns true in thread 0
-// of the last block, with the totals (summed in block order) in v.
+// of the last block, with the totals in v.  The last block adds the partials
+// with all its threads in a fixed assignment (thread t takes blocks t, t+256,
+// ...), so the result does not depend on which block finished last.
 template <int NV>
 __device__ bool grid_sum(double (&v)[NV], double* partials, uint32_t* counter) {
     block_sum<NV>(v);
@@ -85,21 +88,22 @@ __device__ bool grid_sum(double (&v)[NV], double* partials, uint32_t* counter) {
     __syncthreads();
     if (!last) return false;
     __threadfence();
-    if (threadIdx.x == 0) {
 #pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            double s = 0.0;
-            for (unsigned b = 0; b < gridDim.x; ++b) s += ((volatile double*)partials)[k * gridDim.x + b];
-            v[k] = s;
-        }
-        *counter = 0u;
+    for (int k = 0; k < NV; ++k) {
+        double s = 0.0;
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+            s += ((volatile double*)partials)[k * gridDim.x + b];
+        v[k] = s;
     }
+    __syncthreads();
+    block_sum<NV>(v);
+    if (threadIdx.x == 0) *counter = 0u;
     return threadIdx.x == 0;
 }
 
 inline int reduce_blocks(int64_t n) {
     int64_t b = (n + kThreads - 1) / kThreads;
-    if (b > 1024) b = 1024;
+    if (b > 2 * 152) b = 2 * 152;
     if (b < 1) b = 1;
     return (int)b;
 }
@@ -352,29 +356,7 @@ __global__ void k_residual_local(int64_t n_local, const int64_t* __restrict__ ro
 // Batched dense GEMV over uneven subdomains
 // ----------------------------------------------------------------------------
 
-// x-source kinds (values in dd_internal.h):
-//   X_FLAT     x_j = v[voff + j]
-//   X_LAMBDA   x_j = (B_r^T v)_j  (sign * v[m])
-//   X_PCG      x_j = (B_r^T (z + beta p))_j, z = v, p = v2
-//   X_CORNER   x_j = v[corner(j)]
-//   X_RECOVER  interface: -(B_r^T v)_j ; corner: v2[corner(j)]
-
-struct XSrc {
-    int kind;
-    const double* v;
-    const double* v2;
-    const int32_t* slot_mult;
-    const int32_t* slot_corner;
-    const PcgScalars* sc;
-};
-
-struct GemvOut {
-    double* out;         // out[voff + row]
-    const double* base;  // optional: out = base + alpha * M x
-    double alpha;
-};
-
-__device__ __forceinline__ double xsrc_value(const XSrc& xs, int64_t slot, int64_t j) {
+__device__ __forceinline__ double xsrc_value(const XSrc& xs, int64_t slot, int64_t j, double beta) {
     switch (xs.kind) {
         case X_FLAT: return xs.v[slot];
         case X_LAMBDA: {
@@ -385,7 +367,7 @@ __device__ __forceinline__ double xsrc_value(const XSrc& xs, int64_t slot, int64
             const int m = xs.slot_mult[slot];
             if (m == 0) return 0.0;
             const int mi = (m > 0 ? m : -m) - 1;
-            const double pv = xs.v[mi] + xs.sc->beta * xs.v2[mi];
+            const double pv = xs.v[mi] + beta * xs.v2[mi];
             return m > 0 ? pv : -pv;
         }
         case X_CORNER: return xs.v[xs.slot_corner[slot]];
@@ -399,6 +381,62 @@ __device__ __forceinline__ double xsrc_value(const XSrc& xs, int64_t slot, int64
     }
 }
 
+// FP32 staging: only FP32 loads and FP32 arithmetic (GB300's FP64 pipe is
+// ~1/64 of FP32 and would otherwise dominate short-row GEMVs).
+__device__ __forceinline__ float xsrc_value_f(const XSrc& xs, int64_t slot, int64_t j, float beta) {
+    switch (xs.kind) {
+        case X_FLAT: return xs.vf[slot];
+        case X_LAMBDA: {
+            const int m = xs.slot_mult[slot];
+            return m > 0 ? xs.vf[m - 1] : (m < 0 ? -xs.vf[-m - 1] : 0.0f);
+        }
+        case X_PCG: {
+            const int m = xs.slot_mult[slot];
+            if (m == 0) return 0.0f;
+            const int mi = (m > 0 ? m : -m) - 1;
+            const float pv = fmaf(beta, xs.v2f[mi], xs.vf[mi]);
+            return m > 0 ? pv : -pv;
+        }
+        case X_CORNER: return xs.vf[xs.slot_corner[slot]];
+        case X_RECOVER: {
+            const int m = xs.slot_mult[slot];
+            if (m != 0) return m > 0 ? -xs.vf[m - 1] : xs.vf[-m - 1];
+            const int c = xs.slot_corner[slot];
+            return c >= 0 ? xs.v2f[c] : 0.0f;
+        }
+        default: return xs.vf[j];
+    }
+}
+
+template <typename TM>
+__device__ __forceinline__ TM stage_value(const XSrc& xs, int64_t slot, int64_t j, TM beta);
+template <>
+__device__ __forceinline__ double stage_value<double>(const XSrc& xs, int64_t slot, int64_t j, double beta) {
+    return xsrc_value(xs, slot, j, beta);
+}
+template <>
+__device__ __forceinline__ float stage_value<float>(const XSrc& xs, int64_t slot, int64_t j, float beta) {
+    return xsrc_value_f(xs, slot, j, beta);
+}
+
+template <typename TM>
+__device__ __forceinline__ void gemv_store(const GemvOut& go, int64_t o, TM acc, TM alpha_t) {
+    if (go.out32) {
+        float v = (float)alpha_t * (float)acc;
+        if (go.base32) v += go.base32[o];
+        go.out32[o] = v;
+    }
+    if (go.out) {
+        double v = (double)acc;
+        if (go.alpha != 1.0) v *= go.alpha;
+        if (go.base) v += go.base[o];
+        go.out[o] = v;
+    }
+}
+
+// Batched GEMV: one CTA per task (matrix, row range); the CTA stages its x
+// segment in shared memory and streams the rows.  Rows of <= 128 columns
+// (the corner-coupling block) use 8 lanes per row, longer rows a warp per row.
 template <typename TM>
 __global__ void __launch_bounds__(kThreads) k_gemv(const GemvTask* __restrict__ tasks, const MatDesc* __restrict__ mats,
                                                    const TM* __restrict__ M, int mode, XSrc xs, GemvOut go,
@@ -417,12 +455,29 @@ __global__ void __launch_bounds__(kThreads) k_gemv(const GemvTask* __restrict__ 
         default: c0 = 0; c1 = md.ns; break;
     }
     const int ncol = c1 - c0;
+    const TM beta = xs.kind == X_PCG ? (TM)xs.sc->beta : (TM)0;
+    const TM alpha_t = (TM)go.alpha;
     if (staged) {
         for (int j = threadIdx.x; j < ncol; j += blockDim.x)
-            xsh[j] = (TM)xsrc_value(xs, md.voff + c0 + j, c0 + j);
+            xsh[j] = stage_value<TM>(xs, md.voff + c0 + j, c0 + j, beta);
         __syncthreads();
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (staged && ncol <= 128) {
+        const int sub = lane >> 3, l8 = lane & 7;
+        for (int rb = tk.row0 + 4 * warp; rb < tk.row1; rb += 4 * nw) {
+            const int row = rb + sub;
+            TM a = 0;
+            if (row < tk.row1) {
+                const TM* Mr = M + md.moff + (int64_t)row * md.ld + c0;
+                for (int j = l8; j < ncol; j += 8) a += Mr[j] * xsh[j];
+            }
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o, 8);
+            if (l8 == 0 && row < tk.row1) gemv_store<TM>(go, md.voff + row, a, alpha_t);
+        }
+        return;
+    }
     for (int row = tk.row0 + warp; row < tk.row1; row += nw) {
         const TM* Mr = M + md.moff + (int64_t)row * md.ld + c0;
         TM a0 = 0, a1 = 0, a2 = 0, a3 = 0;
@@ -436,15 +491,10 @@ __global__ void __launch_bounds__(kThreads) k_gemv(const GemvTask* __restrict__ 
             }
             for (; j < ncol; j += 32) a0 += Mr[j] * xsh[j];
         } else {
-            for (; j < ncol; j += 32) a0 += Mr[j] * (TM)xsrc_value(xs, md.voff + c0 + j, c0 + j);
+            for (; j < ncol; j += 32) a0 += Mr[j] * stage_value<TM>(xs, md.voff + c0 + j, c0 + j, beta);
         }
-        TM acc = warp_sum((a0 + a1) + (a2 + a3));
-        if (lane == 0) {
-            const int64_t o = md.voff + row;
-            double v = go.alpha * (double)acc;
-            if (go.base) v += go.base[o];
-            go.out[o] = v;
-        }
+        const TM acc = warp_sum((a0 + a1) + (a2 + a3));
+        if (lane == 0) gemv_store<TM>(go, md.voff + row, acc, alpha_t);
     }
 }
 
@@ -452,12 +502,16 @@ __global__ void __launch_bounds__(kThreads) k_gemv(const GemvTask* __restrict__ 
 // Interface vectors
 // ----------------------------------------------------------------------------
 
+__device__ __forceinline__ double wval(const double* w, const float* wf, int64_t i) {
+    return wf ? (double)wf[i] : w[i];
+}
+
 // d_r = sum_s B_r y_s (jump of y across each interface edge) and
 // f~_c = sum_s B_c^T (b_c - A_cr y): corner slots of y hold A_cr y after GEMV_LOCAL.
 __global__ void k_iface_rhs(int64_t n_lambda, int64_t n_corner, const int64_t* __restrict__ mult_slot,
                             const int64_t* __restrict__ corner_ptr, const int64_t* __restrict__ corner_slot,
                             const double* __restrict__ y, const double* __restrict__ b, double* __restrict__ g,
-                            double* __restrict__ fC) {
+                            double* __restrict__ fC, float* __restrict__ fCf) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t < n_lambda) {
         g[t] = y[mult_slot[2 * t]] - y[mult_slot[2 * t + 1]];
@@ -469,27 +523,30 @@ __global__ void k_iface_rhs(int64_t n_lambda, int64_t n_corner, const int64_t* _
             s += b[sl] - y[sl];
         }
         fC[I] = s;
+        if (fCf) fCf[I] = (float)s;
     }
 }
 
 // uC[I] = (add ? add[I] : 0) + sum over copies of w at the corner slots (B_c^T assembly).
 __global__ void k_corner_gather(int64_t n_corner, const int64_t* __restrict__ corner_ptr,
                                 const int64_t* __restrict__ corner_slot, const double* __restrict__ w,
-                                const double* __restrict__ add, double* __restrict__ uC,
-                                const int32_t* __restrict__ done) {
+                                const float* __restrict__ wf, const double* __restrict__ add, double* __restrict__ uC,
+                                float* __restrict__ uCf, const int32_t* __restrict__ done) {
     if (done && *done) return;
     for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < n_corner; I += (int64_t)gridDim.x * blockDim.x) {
         double s = add ? add[I] : 0.0;
-        for (int64_t c = corner_ptr[I]; c < corner_ptr[I + 1]; ++c) s += w[corner_slot[c]];
+        for (int64_t c = corner_ptr[I]; c < corner_ptr[I + 1]; ++c) s += wval(w, wf, corner_slot[c]);
         uC[I] = s;
+        if (uCf) uCf[I] = (float)s;
     }
 }
 
 // out[m] = (base ? base[m] : 0) + sign * (w[s1 slot] - w[s2 slot])   (sum_s B_r w_s)
 __global__ void k_jump(int64_t n_lambda, const int64_t* __restrict__ mult_slot, const double* __restrict__ w,
-                       const double* __restrict__ base, double sign, double* __restrict__ out) {
+                       const float* __restrict__ wf, const double* __restrict__ base, double sign,
+                       double* __restrict__ out) {
     for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < n_lambda; m += (int64_t)gridDim.x * blockDim.x) {
-        double v = sign * (w[mult_slot[2 * m]] - w[mult_slot[2 * m + 1]]);
+        double v = sign * (wval(w, wf, mult_slot[2 * m]) - wval(w, wf, mult_slot[2 * m + 1]));
         if (base) v += base[m];
         out[m] = v;
     }
@@ -498,19 +555,25 @@ __global__ void k_jump(int64_t n_lambda, const int64_t* __restrict__ mult_slot, 
 // CG start: q = jump(w) if have_q (K lambda0), r = g - q, z = D^-1 r, p = 0,
 // beta = 0; totals rz, gg, rr; done if rr <= tol^2 gg.
 __global__ void __launch_bounds__(kThreads) k_pcg_init(int64_t n_lambda, const int64_t* __restrict__ mult_slot,
-                                                       const double* __restrict__ w, int have_q,
-                                                       const double* __restrict__ g, const double* __restrict__ dinv,
-                                                       double tol, double* __restrict__ r, double* __restrict__ z,
-                                                       double* __restrict__ p, PcgScalars* sc,
+                                                       const double* __restrict__ w, const float* __restrict__ wf,
+                                                       int have_q, const double* __restrict__ g,
+                                                       const double* __restrict__ dinv, double tol,
+                                                       double* __restrict__ r, double* __restrict__ z,
+                                                       double* __restrict__ p, float* __restrict__ zf,
+                                                       float* __restrict__ pf, PcgScalars* sc,
                                                        double* __restrict__ partials) {
     double v[3] = {0.0, 0.0, 0.0};
     for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < n_lambda; m += (int64_t)gridDim.x * blockDim.x) {
-        const double q = have_q ? (w[mult_slot[2 * m]] - w[mult_slot[2 * m + 1]]) : 0.0;
+        const double q = have_q ? (wval(w, wf, mult_slot[2 * m]) - wval(w, wf, mult_slot[2 * m + 1])) : 0.0;
         const double rr = g[m] - q;
         const double zz = dinv ? rr * dinv[m] : rr;
         r[m] = rr;
         z[m] = zz;
         p[m] = 0.0;
+        if (zf) {
+            zf[m] = (float)zz;
+            pf[m] = 0.0f;
+        }
         v[0] += rr * zz;
         v[1] += g[m] * g[m];
         v[2] += rr * rr;
@@ -531,16 +594,18 @@ __global__ void __launch_bounds__(kThreads) k_pcg_init(int64_t n_lambda, const i
 
 // p <- z + beta p ; q = jump(w) ; pq = p . q ; alpha = rz / pq
 __global__ void __launch_bounds__(kThreads) k_pcg_alpha(int64_t n_lambda, const int64_t* __restrict__ mult_slot,
-                                                        const double* __restrict__ w, const double* __restrict__ z,
-                                                        double* __restrict__ p, double* __restrict__ q, PcgScalars* sc,
+                                                        const double* __restrict__ w, const float* __restrict__ wf,
+                                                        const double* __restrict__ z, double* __restrict__ p,
+                                                        float* __restrict__ pf, double* __restrict__ q, PcgScalars* sc,
                                                         double* __restrict__ partials) {
     if (sc->done) return;
     const double beta = sc->beta;
     double v[1] = {0.0};
     for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < n_lambda; m += (int64_t)gridDim.x * blockDim.x) {
         const double pn = z[m] + beta * p[m];
-        const double qq = w[mult_slot[2 * m]] - w[mult_slot[2 * m + 1]];
+        const double qq = wval(w, wf, mult_slot[2 * m]) - wval(w, wf, mult_slot[2 * m + 1]);
         p[m] = pn;
+        if (pf) pf[m] = (float)pn;
         q[m] = qq;
         v[0] += pn * qq;
     }
@@ -554,17 +619,23 @@ __global__ void __launch_bounds__(kThreads) k_pcg_alpha(int64_t n_lambda, const 
 __global__ void __launch_bounds__(kThreads) k_pcg_update(int64_t n_lambda, const double* __restrict__ p,
                                                          const double* __restrict__ q, const double* __restrict__ dinv,
                                                          double* __restrict__ lam, double* __restrict__ r,
-                                                         double* __restrict__ z, PcgScalars* sc,
+                                                         double* __restrict__ z, float* __restrict__ zf,
+                                                         float* __restrict__ lamf, PcgScalars* sc,
                                                          double* __restrict__ partials) {
     if (sc->done) return;
     const double alpha = sc->alpha;
     double v[2] = {0.0, 0.0};
     for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < n_lambda; m += (int64_t)gridDim.x * blockDim.x) {
-        lam[m] += alpha * p[m];
+        const double lm = lam[m] + alpha * p[m];
+        lam[m] = lm;
         const double rr = r[m] - alpha * q[m];
         const double zz = dinv ? rr * dinv[m] : rr;
         r[m] = rr;
         z[m] = zz;
+        if (zf) {
+            zf[m] = (float)zz;
+            lamf[m] = (float)lm;
+        }
         v[0] += rr * rr;
         v[1] += rr * zz;
     }
@@ -616,14 +687,19 @@ __global__ void k_advance(int64_t n_dof, const double* __restrict__ e_n, const d
 // correction solve cannot resolve.
 __global__ void __launch_bounds__(kThreads) k_assemble_rhs(int64_t n_dof, const int64_t* __restrict__ copy_ptr,
                                                            const int64_t* __restrict__ copy_slot, double* __restrict__ b,
-                                                           PcgScalars* sc, double* __restrict__ partials, int set_b) {
+                                                           float* __restrict__ bf, PcgScalars* sc,
+                                                           double* __restrict__ partials, int set_b) {
     double v[1] = {0.0};
     for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < n_dof; d += (int64_t)gridDim.x * blockDim.x) {
         const int64_t c0 = copy_ptr[d], c1 = copy_ptr[d + 1];
         double s = 0.0;
         for (int64_t c = c0; c < c1; ++c) s += b[copy_slot[c]];
         b[copy_slot[c0]] = s;                       // the first copy is the owner
-        for (int64_t c = c0 + 1; c < c1; ++c) b[copy_slot[c]] = 0.0;
+        if (bf) bf[copy_slot[c0]] = (float)s;
+        for (int64_t c = c0 + 1; c < c1; ++c) {
+            b[copy_slot[c]] = 0.0;
+            if (bf) bf[copy_slot[c]] = 0.0f;
+        }
         v[0] += s * s;
     }
     if (grid_sum<1>(v, partials, &sc->counter[3])) {
@@ -712,19 +788,19 @@ int launch_residual_local(const dd_handle* h, void* stream) {
     return (int)cudaGetLastError();
 }
 
-int launch_assembled_norm(const dd_handle* h, int set_b, void* stream) {
+int launch_assembled_norm(const dd_handle* h, int set_b, float* bf, void* stream) {
     const int64_t nd = h->n_dof;
-    k_assemble_rhs<<<reduce_blocks(nd), kThreads, 0, S(stream)>>>(nd, h->d.copy_ptr, h->d.copy_slot, h->d.b, h->d.sc,
-                                                                  h->d.partials, set_b);
+    k_assemble_rhs<<<reduce_blocks(nd), kThreads, 0, S(stream)>>>(nd, h->d.copy_ptr, h->d.copy_slot, h->d.b, bf,
+                                                                  h->d.sc, h->d.partials, set_b);
     return (int)cudaGetLastError();
 }
 
-int launch_gemv(const dd_handle* h, int mode, int prec, int xkind, const double* v, const double* v2, double* out,
-                const double* base, double alpha, bool check_done, void* stream) {
+int launch_gemv(const dd_handle* h, int mode, int prec, XSrc xs, GemvOut go, bool check_done, void* stream) {
     const auto& tl = h->tasks[mode];
     if (tl.empty()) return 0;
-    XSrc xs{xkind, v, v2, h->d.slot_mult, h->d.slot_corner, h->d.sc};
-    GemvOut go{out, base, alpha};
+    xs.slot_mult = h->d.slot_mult;
+    xs.slot_corner = h->d.slot_corner;
+    xs.sc = h->d.sc;
     const MatDesc* mats = mode == GEMV_COARSE ? h->d.coarse_desc : h->d.mats;
     const GemvTask* tasks = h->d.tasks[mode];
     const int maxcol = mode == GEMV_COARSE ? (int)h->corner_dof.size() : h->max_ns;
@@ -738,60 +814,64 @@ int launch_gemv(const dd_handle* h, int mode, int prec, int xkind, const double*
     const int32_t* done = check_done ? &h->d.sc->done : nullptr;
     if (prec == DD_MIXED) {
         const float* M = mode == GEMV_COARSE ? h->d.K32 : h->d.M32;
-        if (smem > 48 * 1024) CU_TRY(cudaFuncSetAttribute(k_gemv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (smem > 48 * 1024)
+            CU_TRY(cudaFuncSetAttribute(k_gemv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_gemv<float><<<(unsigned)tl.size(), kThreads, smem, S(stream)>>>(tasks, mats, M, mode, xs, go, staged, done);
     } else {
         const double* M = mode == GEMV_COARSE ? h->d.K64 : h->d.M64;
-        if (smem > 48 * 1024) CU_TRY(cudaFuncSetAttribute(k_gemv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (smem > 48 * 1024)
+            CU_TRY(cudaFuncSetAttribute(k_gemv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_gemv<double><<<(unsigned)tl.size(), kThreads, smem, S(stream)>>>(tasks, mats, M, mode, xs, go, staged, done);
     }
     return (int)cudaGetLastError();
 }
 
-int launch_iface_rhs(const dd_handle* h, void* stream) {
+int launch_iface_rhs(const dd_handle* h, float* fCf, void* stream) {
     const int64_t nl = (int64_t)h->mult_dof.size(), nc = (int64_t)h->corner_dof.size();
     const int64_t n = nl + nc;
     if (n == 0) return 0;
     k_iface_rhs<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, S(stream)>>>(
-        nl, nc, h->d.mult_slot, h->d.corner_ptr, h->d.corner_slot, h->d.y, h->d.b, h->d.g, h->d.fC);
+        nl, nc, h->d.mult_slot, h->d.corner_ptr, h->d.corner_slot, h->d.y, h->d.b, h->d.g, h->d.fC, fCf);
     return (int)cudaGetLastError();
 }
 
-int launch_corner_gather(const dd_handle* h, const double* w, const double* add, double* uC, bool check_done,
-                         void* stream) {
+int launch_corner_gather(const dd_handle* h, const double* w, const float* wf, const double* add, double* uC, float* uCf,
+                         bool check_done, void* stream) {
     const int64_t nc = (int64_t)h->corner_dof.size();
     if (nc == 0) return 0;
-    k_corner_gather<<<reduce_blocks(nc), kThreads, 0, S(stream)>>>(nc, h->d.corner_ptr, h->d.corner_slot, w, add, uC,
-                                                                   check_done ? &h->d.sc->done : nullptr);
+    k_corner_gather<<<reduce_blocks(nc), kThreads, 0, S(stream)>>>(nc, h->d.corner_ptr, h->d.corner_slot, w, wf, add, uC,
+                                                                   uCf, check_done ? &h->d.sc->done : nullptr);
     return (int)cudaGetLastError();
 }
 
-int launch_jump(const dd_handle* h, const double* w, const double* base, double sign, double* out, void* stream) {
+int launch_jump(const dd_handle* h, const double* w, const float* wf, const double* base, double sign, double* out,
+                void* stream) {
     const int64_t nl = (int64_t)h->mult_dof.size();
     if (nl == 0) return 0;
-    k_jump<<<reduce_blocks(nl), kThreads, 0, S(stream)>>>(nl, h->d.mult_slot, w, base, sign, out);
+    k_jump<<<reduce_blocks(nl), kThreads, 0, S(stream)>>>(nl, h->d.mult_slot, w, wf, base, sign, out);
     return (int)cudaGetLastError();
 }
 
-int launch_pcg_init(const dd_handle* h, int have_q, double tol, void* stream) {
+int launch_pcg_init(const dd_handle* h, int have_q, double tol, const float* wf, float* zf, float* pf, void* stream) {
     const int64_t nl = (int64_t)h->mult_dof.size();
-    k_pcg_init<<<reduce_blocks(nl), kThreads, 0, S(stream)>>>(nl, h->d.mult_slot, h->d.w, have_q, h->d.g,
+    k_pcg_init<<<reduce_blocks(nl), kThreads, 0, S(stream)>>>(nl, h->d.mult_slot, h->d.w, wf, have_q, h->d.g,
                                                               h->prm.precond ? h->d.dinv : nullptr, tol, h->d.r, h->d.z,
-                                                              h->d.p, h->d.sc, h->d.partials);
+                                                              h->d.p, zf, pf, h->d.sc, h->d.partials);
     return (int)cudaGetLastError();
 }
 
-int launch_pcg_alpha(const dd_handle* h, void* stream) {
+int launch_pcg_alpha(const dd_handle* h, const float* wf, float* pf, void* stream) {
     const int64_t nl = (int64_t)h->mult_dof.size();
-    k_pcg_alpha<<<reduce_blocks(nl), kThreads, 0, S(stream)>>>(nl, h->d.mult_slot, h->d.w, h->d.z, h->d.p, h->d.q,
-                                                               h->d.sc, h->d.partials);
+    k_pcg_alpha<<<reduce_blocks(nl), kThreads, 0, S(stream)>>>(nl, h->d.mult_slot, h->d.w, wf, h->d.z, h->d.p, pf,
+                                                               h->d.q, h->d.sc, h->d.partials);
     return (int)cudaGetLastError();
 }
 
-int launch_pcg_update(const dd_handle* h, void* stream) {
+int launch_pcg_update(const dd_handle* h, float* zf, float* lamf, void* stream) {
     const int64_t nl = (int64_t)h->mult_dof.size();
     k_pcg_update<<<reduce_blocks(nl), kThreads, 0, S(stream)>>>(nl, h->d.p, h->d.q, h->prm.precond ? h->d.dinv : nullptr,
-                                                                h->d.lam, h->d.r, h->d.z, h->d.sc, h->d.partials);
+                                                                h->d.lam, h->d.r, h->d.z, zf, lamf, h->d.sc,
+                                                                h->d.partials);
     return (int)cudaGetLastError();
 }
 

@@ -376,8 +376,9 @@ int dd_build_host(dd_handle* h, const dd_mesh* mesh, const int32_t* part, int32_
         auto& tl = h->tasks[mode];
         tl.clear();
         if (mode == GEMV_COARSE) {
-            for (int64_t r0 = 0; r0 < nc; r0 += kRowsPerTask)
-                tl.push_back({0, (int32_t)r0, (int32_t)std::min<int64_t>(nc, r0 + kRowsPerTask), 0});
+            const int rp = kRowsPerMode[mode];
+            for (int64_t r0 = 0; r0 < nc; r0 += rp)
+                tl.push_back({0, (int32_t)r0, (int32_t)std::min<int64_t>(nc, r0 + rp), 0});
             continue;
         }
         for (int s = 0; s < n_sub; ++s) {
@@ -387,7 +388,8 @@ int dd_build_host(dd_handle* h, const dd_mesh* mesh, const int32_t* part, int32_
             if (mode == GEMV_SCHUR) { r0 = md.nI; r1 = md.ns; }
             if (mode == GEMV_CORNER) { r0 = md.nI; r1 = md.nr; }
             if (mode == GEMV_RECOVER) { r0 = 0; r1 = md.nr; }
-            for (int32_t a = r0; a < r1; a += kRowsPerTask) tl.push_back({s, a, std::min(r1, a + kRowsPerTask), 0});
+            const int rp = kRowsPerMode[mode];
+            for (int32_t a = r0; a < r1; a += rp) tl.push_back({s, a, std::min(r1, a + rp), 0});
         }
     }
     return DD_OK;
