@@ -55,21 +55,21 @@ cudaEvent_t grab_event(dd_handle* h) {
     return (cudaEvent_t)h->ev_pool[h->ev_used++];
 }
 
-// Counts `nk` kernel launches of `stage`; `full` marks them as full-work launches
-// whose algorithmic bytes are known (bytes per launch chosen by precision).
+// Counts `nk` kernel launches of `stage`; a positive `bytes` marks them as one
+// full-work launch with that many algorithmic bytes.
 struct Prof {
     dd_handle* h;
     int stage;
     cudaStream_t s;
     size_t i0 = 0;
     bool on;
-    Prof(dd_handle* h_, int stage_, cudaStream_t s_, int nk = 1, bool full = true, int prec = DD_FP64)
+    Prof(dd_handle* h_, int stage_, cudaStream_t s_, int nk = 1, double bytes = 0.0)
         : h(h_), stage(stage_), s(s_), on(h_->prof_on) {
         h->launches[stage] += nk;
         h->total_launches += nk;
-        if (full) {
+        if (bytes > 0.0) {
             h->work[stage] += 1;
-            h->work_bytes[stage] += prec == DD_MIXED ? h->bytes_per_launch32[stage] : h->bytes_per_launch[stage];
+            h->work_bytes[stage] += bytes;
         }
         if (on) {
             i0 = h->ev_used;
@@ -86,24 +86,19 @@ struct Prof {
     }
 };
 
-int gemv_stage(int mode) {
-    switch (mode) {
-        case GEMV_LOCAL: return ST_LOCAL;
-        case GEMV_SCHUR: return ST_SCHUR;
-        case GEMV_COARSE: return ST_COARSE;
-        case GEMV_CORNER: return ST_CORNER;
-        default: return ST_RECOVER;
-    }
+// algorithmic bytes of one full GEMV launch of `mode` at precision `prec`
+double mb(const dd_handle* h, int mode, int prec) {
+    return prec == DD_MIXED ? h->mode_bytes32[mode] : h->mode_bytes[mode];
 }
 
-// Algorithmic bytes of one full launch of each stage: matrix elements read at
-// the stage's precision plus the vectors read and written once.
+// Algorithmic bytes of one full launch: matrix elements read at the launch's
+// precision plus the vectors read and written once.
 void compute_stage_bytes(dd_handle* h) {
     const double nl = (double)h->sub_ptr.back(), nd = (double)h->n_dof, nnz = (double)h->row_ptr.back();
     const double nc = (double)h->corner_dof.size();
-    for (int k = 0; k < DD_N_STAGES; ++k) h->bytes_per_launch[k] = h->bytes_per_launch32[k] = 0.0;
+    for (int k = 0; k < DD_N_STAGES; ++k) h->bytes_per_launch[k] = 0.0;
     // RHS: S values + column ids, row pointers, e^n, source, b
-    h->bytes_per_launch[ST_RHS] = h->bytes_per_launch32[ST_RHS] = nnz * 12.0 + nl * (8.0 + 8.0 + 5.0) + 2.0 * nd * 8.0;
+    h->bytes_per_launch[ST_RHS] = nnz * 12.0 + nl * (8.0 + 8.0 + 5.0) + 2.0 * nd * 8.0;
     for (int mode = 0; mode < GEMV_NMODES; ++mode) {
         double elems = 0.0, vec = 0.0;
         if (mode == GEMV_COARSE) {
@@ -114,21 +109,21 @@ void compute_stage_bytes(dd_handle* h) {
                 int r0, r1, c0, c1;
                 switch (mode) {
                     case GEMV_LOCAL: r0 = 0; r1 = md.ns; c0 = 0; c1 = md.nr; break;
-                    case GEMV_SCHUR: r0 = md.nI; r1 = md.ns; c0 = md.nI; c1 = md.nr; break;
+                    case GEMV_SCHUR_C: r0 = md.nr; r1 = md.ns; c0 = md.nI; c1 = md.nr; break;
                     case GEMV_CORNER: r0 = md.nI; r1 = md.nr; c0 = md.nr; c1 = md.ns; break;
+                    case GEMV_SCHUR_G: r0 = md.nI; r1 = md.nr; c0 = md.nI; c1 = md.ns; break;
                     default: r0 = 0; r1 = md.nr; c0 = md.nI; c1 = md.ns; break;
                 }
                 elems += (double)(r1 - r0) * (double)(c1 - c0);
-                const bool acc = mode == GEMV_CORNER || mode == GEMV_RECOVER;
+                const bool acc = mode == GEMV_RECOVER;
                 vec += (double)(c1 - c0) * 8.0 + (double)(r1 - r0) * 8.0 * (acc ? 2.0 : 1.0);
             }
         }
-        const int st = gemv_stage(mode);
-        h->bytes_per_launch[st] = elems * 8.0 + vec;
-        h->bytes_per_launch32[st] = elems * 4.0 + vec;
+        h->mode_bytes[mode] = elems * 8.0 + vec;
+        h->mode_bytes32[mode] = elems * 4.0 + vec;
     }
     // FP64 residual b -= A delta (A values + ids + b) and the assembled norm
-    h->bytes_per_launch[ST_REFINE] = h->bytes_per_launch32[ST_REFINE] = nnz * 12.0 + nl * 24.0 + nd * 8.0;
+    h->bytes_per_launch[ST_REFINE] = nnz * 12.0 + nl * 24.0 + nd * 8.0;
 }
 
 struct Layout {
@@ -250,13 +245,16 @@ Vecs vecs(dd_handle* h, int prec) {
     return Vecs{true, d.wf, d.zf, d.pf, d.lamf, d.fCf, d.uCf, d.vCf, d.xCf, d.bf};
 }
 
-XSrc xsrc(int kind, const double* v, const double* v2, const float* vf, const float* v2f) {
+XSrc xsrc(int kind, const double* v, const double* v2, const float* vf, const float* v2f,
+          const double* v3 = nullptr, const float* v3f = nullptr) {
     XSrc x{};
     x.kind = kind;
     x.v = v;
     x.v2 = v2;
+    x.v3 = v3;
     x.vf = vf;
     x.v2f = v2f;
+    x.v3f = v3f;
     return x;
 }
 
@@ -273,40 +271,47 @@ GemvOut gout(double* out, const double* base, float* out32, const float* base32,
 int apply_schur_w(dd_handle* h, int prec, int kind, const double* v, const double* v2, const float* vf,
                   const float* v2f, bool check_done, cudaStream_t s) {
     const Vecs V = vecs(h, prec);
+    const double full = check_done ? 0.0 : 1.0;   // CG-loop launches are counted by count_cg_work
     int rc;
-    {
-        Prof P(h, ST_SCHUR, s, 1, !check_done, prec);
-        rc = launch_gemv(h, GEMV_SCHUR, prec, xsrc(kind, v, v2, vf, v2f),
-                         V.f32 ? gout(nullptr, nullptr, V.wf, nullptr, 1.0) : gout(h->d.w, nullptr, nullptr, nullptr, 1.0),
-                         check_done, s);
+    const int kind_cv = kind == X_PCG ? X_PCG_CV : X_LAMBDA_CV;
+    if (!h->corner_dof.empty()) {
+        // u_s = A_cr A_rr^-1 B_r^T z (corner rows), K~cc^-1 sum_s B_c^T u_s
+        {
+            Prof P(h, ST_SCHUR, s, 1, full * mb(h, GEMV_SCHUR_C, prec));
+            rc = launch_gemv(h, GEMV_SCHUR_C, prec, xsrc(kind, v, v2, vf, v2f),
+                             V.f32 ? gout(nullptr, nullptr, V.wf, nullptr, 1.0) : gout(h->d.w, nullptr, nullptr, nullptr, 1.0),
+                             check_done, s);
+        }
+        if (rc) return rc;
+        {
+            Prof P(h, ST_VEC, s, 1);
+            rc = launch_corner_gather(h, h->d.w, V.wf, nullptr, h->d.uC, V.uCf, check_done, s);
+        }
+        if (rc) return rc;
+        {
+            Prof P(h, ST_COARSE, s, 1, full * mb(h, GEMV_COARSE, prec));
+            rc = launch_gemv(h, GEMV_COARSE, prec, xsrc(X_FLAT, h->d.uC, nullptr, V.uCf, nullptr),
+                             V.f32 ? gout(nullptr, nullptr, V.vCf, nullptr, 1.0) : gout(h->d.vC, nullptr, nullptr, nullptr, 1.0),
+                             check_done, s);
+        }
+        if (rc) return rc;
     }
-    if (rc) return rc;
-    if (h->corner_dof.empty()) return 0;
-    {
-        Prof P(h, ST_VEC, s, 1, false);
-        rc = launch_corner_gather(h, h->d.w, V.wf, nullptr, h->d.uC, V.uCf, check_done, s);
-    }
-    if (rc) return rc;
-    {
-        Prof P(h, ST_COARSE, s, 1, !check_done, prec);
-        rc = launch_gemv(h, GEMV_COARSE, prec, xsrc(X_FLAT, h->d.uC, nullptr, V.uCf, nullptr),
-                         V.f32 ? gout(nullptr, nullptr, V.vCf, nullptr, 1.0) : gout(h->d.vC, nullptr, nullptr, nullptr, 1.0),
-                         check_done, s);
-    }
-    if (rc) return rc;
-    Prof P(h, ST_CORNER, s, 1, !check_done, prec);
-    return launch_gemv(h, GEMV_CORNER, prec, xsrc(X_CORNER, h->d.vC, nullptr, V.vCf, nullptr),
-                       V.f32 ? gout(nullptr, nullptr, V.wf, V.wf, -1.0) : gout(h->d.w, h->d.w, nullptr, nullptr, -1.0),
+    // interface rows over [Gamma | c] columns with x = [B_r^T z ; -v]:
+    // A_rr^-1 B_r^T z + A_rr^-1 A_rc B_c K~cc^-1 (...) in one pass (M[Gamma, c] = -A_rr^-1 A_rc)
+    Prof P(h, ST_SCHUR, s, 1, full * mb(h, GEMV_SCHUR_G, prec));
+    return launch_gemv(h, GEMV_SCHUR_G, prec, xsrc(kind_cv, v, v2, vf, v2f, h->d.vC, V.vCf),
+                       V.f32 ? gout(nullptr, nullptr, V.wf, nullptr, 1.0) : gout(h->d.w, nullptr, nullptr, nullptr, 1.0),
                        check_done, s);
 }
 
-// Adds n full-work launches of the CG-loop stages after the iteration count is known.
+// Adds n full-work CG iterations to the stage counters once the count is known.
 void count_cg_work(dd_handle* h, int prec, int n) {
-    const int st[3] = {ST_SCHUR, ST_COARSE, ST_CORNER};
-    for (int k = 0; k < 3; ++k) {
-        if (st[k] != ST_SCHUR && h->corner_dof.empty()) continue;
-        h->work[st[k]] += n;
-        h->work_bytes[st[k]] += n * (prec == DD_MIXED ? h->bytes_per_launch32[st[k]] : h->bytes_per_launch[st[k]]);
+    const bool c = !h->corner_dof.empty();
+    h->work[ST_SCHUR] += n;
+    h->work_bytes[ST_SCHUR] += n * (mb(h, GEMV_SCHUR_G, prec) + (c ? mb(h, GEMV_SCHUR_C, prec) : 0.0));
+    if (c) {
+        h->work[ST_COARSE] += n;
+        h->work_bytes[ST_COARSE] += n * mb(h, GEMV_COARSE, prec);
     }
 }
 
@@ -321,30 +326,30 @@ int dd_solve(dd_handle* h, int prec, double tol, bool warm, int* it_out, double*
     const size_t nlb = sizeof(double) * h->mult_dof.size();
     // y = A_rr^-1 b_r (r rows) and A_cr y (corner rows)          Eq. rF1 / F1uc
     {
-        Prof P(h, ST_LOCAL, s, 1, true, prec);
+        Prof P(h, ST_LOCAL, s, 1, mb(h, GEMV_LOCAL, prec));
         CK(h, launch_gemv(h, GEMV_LOCAL, prec, xsrc(X_FLAT, h->d.b, nullptr, V.bf, nullptr),
                           gout(h->d.y, nullptr, nullptr, nullptr, 1.0), false, s), "gemv local");
     }
     // g = d_r ; f~_c
     {
-        Prof P(h, ST_VEC, s, 1, false);
+        Prof P(h, ST_VEC, s, 1);
         CK(h, launch_iface_rhs(h, V.fCf, s), "iface rhs");
     }
     if (has_c && has_l) {
         // g = d_r - F_rc K~cc^-1 f~_c                                Eq. f1schur
         {
-            Prof P(h, ST_COARSE, s, 1, true, prec);
+            Prof P(h, ST_COARSE, s, 1, mb(h, GEMV_COARSE, prec));
             CK(h, launch_gemv(h, GEMV_COARSE, prec, xsrc(X_FLAT, h->d.fC, nullptr, V.fCf, nullptr),
                               V.f32 ? gout(nullptr, nullptr, V.vCf, nullptr, 1.0) : gout(h->d.vC, nullptr, nullptr, nullptr, 1.0),
                               false, s), "coarse");
         }
         {
-            Prof P(h, ST_CORNER, s, 1, true, prec);
+            Prof P(h, ST_CORNER, s, 1, mb(h, GEMV_CORNER, prec));
             CK(h, launch_gemv(h, GEMV_CORNER, prec, xsrc(X_CORNER, h->d.vC, nullptr, V.vCf, nullptr),
                               V.f32 ? gout(nullptr, nullptr, V.wf, nullptr, -1.0) : gout(h->d.w, nullptr, nullptr, nullptr, -1.0),
                               false, s), "corner");
         }
-        Prof P(h, ST_VEC, s, 1, false);
+        Prof P(h, ST_VEC, s, 1);
         CK(h, launch_jump(h, h->d.w, V.wf, h->d.g, -1.0, h->d.g, s), "jump");
     }
     int status = DD_OK;
@@ -359,7 +364,7 @@ int dd_solve(dd_handle* h, int prec, double tol, bool warm, int* it_out, double*
             CK(h, (int)cudaMemsetAsync(h->d.lamf, 0, sizeof(float) * h->mult_dof.size(), s), "memset");
         }
         {
-            Prof P(h, ST_VEC, s, 1, false);
+            Prof P(h, ST_VEC, s, 1);
             CK(h, launch_pcg_init(h, use_warm ? 1 : 0, tol, V.wf, V.zf, V.pf, s), "pcg init");
         }
         PcgScalars hs;
@@ -368,7 +373,7 @@ int dd_solve(dd_handle* h, int prec, double tol, bool warm, int* it_out, double*
             const int n = std::min(h->prm.chunk, h->prm.max_it - hs.it);
             for (int k = 0; k < n; ++k) {
                 CK(h, apply_schur_w(h, prec, X_PCG, h->d.z, h->d.p, V.zf, V.pf, true, s), "apply");
-                Prof P(h, ST_VEC, s, 2, false);
+                Prof P(h, ST_VEC, s, 2);
                 CK(h, launch_pcg_alpha(h, V.wf, V.pf, s), "pcg alpha");
                 CK(h, launch_pcg_update(h, V.zf, V.lamf, s), "pcg update");
             }
@@ -385,15 +390,15 @@ int dd_solve(dd_handle* h, int prec, double tol, bool warm, int* it_out, double*
     if (has_c) {
         if (has_l) {
             {
-                Prof P(h, ST_SCHUR, s, 1, true, prec);
-                CK(h, launch_gemv(h, GEMV_SCHUR, prec, xsrc(X_LAMBDA, h->d.lam, nullptr, V.lamf, nullptr),
+                Prof P(h, ST_SCHUR, s, 1, mb(h, GEMV_SCHUR_C, prec));
+                CK(h, launch_gemv(h, GEMV_SCHUR_C, prec, xsrc(X_LAMBDA, h->d.lam, nullptr, V.lamf, nullptr),
                                   V.f32 ? gout(nullptr, nullptr, V.wf, nullptr, 1.0) : gout(h->d.w, nullptr, nullptr, nullptr, 1.0),
                                   false, s), "Frc^T");
             }
-            Prof P(h, ST_VEC, s, 1, false);
+            Prof P(h, ST_VEC, s, 1);
             CK(h, launch_corner_gather(h, h->d.w, V.wf, h->d.fC, h->d.uC, V.uCf, false, s), "corner gather");
         }
-        Prof P(h, ST_COARSE, s, 1, true, prec);
+        Prof P(h, ST_COARSE, s, 1, mb(h, GEMV_COARSE, prec));
         const double* src64 = has_l ? h->d.uC : h->d.fC;
         const float* src32 = has_l ? V.uCf : V.fCf;
         CK(h, launch_gemv(h, GEMV_COARSE, prec, xsrc(X_FLAT, src64, nullptr, src32, nullptr),
@@ -401,7 +406,7 @@ int dd_solve(dd_handle* h, int prec, double tol, bool warm, int* it_out, double*
     }
     // x_r = y + A_rr^-1 (-B_r^T lambda) - A_rr^-1 A_rc x_c                  Eq. rF1
     {
-        Prof P(h, ST_RECOVER, s, 1, true, prec);
+        Prof P(h, ST_RECOVER, s, 1, mb(h, GEMV_RECOVER, prec));
         CK(h, launch_gemv(h, GEMV_RECOVER, prec, xsrc(X_RECOVER, h->d.lam, h->d.xC, V.lamf, V.xCf),
                           gout(h->d.x, h->d.y, nullptr, nullptr, 1.0), false, s), "recover");
     }
@@ -543,27 +548,27 @@ int dd_factor(dd_handle* h, double dt, void* stream) {
     h->factored = false;
     CK(h, (int)cudaMemsetAsync(h->d.status, 0, 4, s), "memset");
     {
-        Prof P(h, ST_FACTOR, s, 2, false);
+        Prof P(h, ST_FACTOR, s, 2);
         CK(h, launch_csr_combine(h, dt * dt / 4.0, s), "A = T + dt^2/4 S");
         CK(h, launch_dense_assemble(h, s), "dense assemble");
     }
     for (int k0 = 0; k0 < h->max_nr; k0 += kNB) {
-        Prof P(h, ST_FACTOR, s, 3, false);
+        Prof P(h, ST_FACTOR, s, 3);
         CK(h, launch_sweep(h, false, k0, s), "local elimination");
     }
     const int nc = (int)h->corner_dof.size();
     if (nc) {
         {
-            Prof P(h, ST_FACTOR, s, 1, false);
+            Prof P(h, ST_FACTOR, s, 1);
             CK(h, launch_coarse_assemble(h, s), "coarse assemble");
         }
         for (int k0 = 0; k0 < nc; k0 += kNB) {
-            Prof P(h, ST_FACTOR, s, 3, false);
+            Prof P(h, ST_FACTOR, s, 3);
             CK(h, launch_sweep(h, true, k0, s), "coarse inverse");
         }
     }
     {
-        Prof P(h, ST_FACTOR, s, 3, false);
+        Prof P(h, ST_FACTOR, s, 3);
         CK(h, launch_factor_finish(h, s), "factor finish");
     }
     int32_t st = 0;
@@ -592,18 +597,18 @@ int dd_step(dd_handle* h, const double* d2g, double* e_out, dd_stats* stats, voi
     double resid = 0.0;
     // b = -dt^2 S e^n - d2g (subassembled): A delta = b, e^{n+1} = 2e^n - e^{n-1} + delta
     {
-        Prof P(h, ST_RHS, s);
+        Prof P(h, ST_RHS, s, 1, h->bytes_per_launch[ST_RHS]);
         CK(h, launch_rhs(h, e_n, d2g, h->dt, s), "rhs");
     }
     if (h->prm.precision == DD_FP64) {
         status = dd_solve(h, DD_FP64, h->prm.tol, h->prm.warm_start != 0, &iters, &resid, s);
         if (status != DD_OK && status != DD_ERR_NO_CONVERGENCE) return status;
-        Prof P(h, ST_VEC, s, 1, false);
+        Prof P(h, ST_VEC, s, 1);
         CK(h, launch_writeback(h, e_n, e_nm1, nullptr, nullptr, 1, e_np1, s), "writeback");
     } else {
         // FP64 iterative refinement of the step system with FP32 DD correction solves
         {
-            Prof P(h, ST_REFINE, s, 1, false);
+            Prof P(h, ST_REFINE, s, 1);
             CK(h, launch_assembled_norm(h, 1, h->d.bf, s), "norm b");
         }
         PcgScalars hs;
@@ -626,11 +631,11 @@ int dd_step(dd_handle* h, const double* d2g, double* e_out, dd_stats* stats, voi
             ++refinements;
             if (st != DD_OK && st != DD_ERR_NO_CONVERGENCE) return st;
             {
-                Prof P(h, ST_VEC, s, 1, false);
+                Prof P(h, ST_VEC, s, 1);
                 CK(h, launch_writeback(h, e_n, e_nm1, h->d.delta_k, h->d.delta, k == 0 ? 1 : 0, nullptr, s), "writeback");
             }
             {
-                Prof P(h, ST_REFINE, s, 2, true);
+                Prof P(h, ST_REFINE, s, 2, h->bytes_per_launch[ST_REFINE]);
                 CK(h, launch_residual_local(h, s), "residual");
                 CK(h, launch_assembled_norm(h, 0, h->d.bf, s), "norm r");
             }
@@ -650,7 +655,7 @@ int dd_step(dd_handle* h, const double* d2g, double* e_out, dd_stats* stats, voi
                                        cudaMemcpyDeviceToDevice, s), "restore lambda");
         }
         {
-            Prof P(h, ST_VEC, s, 1, false);
+            Prof P(h, ST_VEC, s, 1);
             CK(h, launch_advance(h, e_n, e_nm1, h->d.delta, e_np1, s), "advance");
         }
         if (status == DD_ERR_NO_CONVERGENCE) h->err = "refinement did not reach refine_tol";
@@ -673,7 +678,7 @@ int dd_schur_apply(dd_handle* h, const double* lam, double* out, void* stream) {
     if (h->mult_dof.empty()) return DD_OK;
     cudaStream_t s = (cudaStream_t)stream;
     CK(h, apply_schur_w(h, DD_FP64, X_LAMBDA, lam, nullptr, nullptr, nullptr, false, s), "apply");
-    Prof P(h, ST_VEC, s, 1, false);
+    Prof P(h, ST_VEC, s, 1);
     CK(h, launch_jump(h, h->d.w, nullptr, nullptr, 1.0, out, s), "jump");
     return DD_OK;
 }
@@ -681,7 +686,7 @@ int dd_schur_apply(dd_handle* h, const double* lam, double* out, void* stream) {
 int dd_probe(dd_handle* h, double* out, void* stream) {
     if (!h || !out) return DD_ERR_ARG;
     if (!h->bound) return h->fail(DD_ERR_STATE, "dd_probe before dd_bind_workspace");
-    Prof P(h, ST_VEC, (cudaStream_t)stream, 1, false);
+    Prof P(h, ST_VEC, (cudaStream_t)stream, 1);
     CK(h, launch_probe(h, h->d.e[h->cur], out, (cudaStream_t)stream), "probe");
     return DD_OK;
 }

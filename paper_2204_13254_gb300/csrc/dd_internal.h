@@ -29,26 +29,30 @@ struct GemvTask {
 
 // Column/row ranges of the batched dense GEMV, all relative to one MatDesc.
 enum GemvMode : int {
-    GEMV_LOCAL = 0,   // rows [0,ns)  cols [0,nr):   [y; A_cr y] from b_r   (Eq. rF1 / F1uc)
-    GEMV_SCHUR = 1,   // rows [nI,ns) cols [nI,nr):  F_rr / F_rc^T pieces   (Eq. f1schur)
-    GEMV_CORNER = 2,  // rows [nI,nr) cols [nr,ns):  F_rc pieces            (Eq. f1schur)
-    GEMV_RECOVER = 3, // rows [0,nr)  cols [nI,ns):  x_r from y, lambda, x_c (Eq. rF1)
-    GEMV_COARSE = 4,  // the dense K~cc^-1 (single matrix)
-    GEMV_NMODES = 5
+    GEMV_LOCAL = 0,    // rows [0,ns)  cols [0,nr):  [y; A_cr y] from b_r                  (Eq. rF1 / F1uc)
+    GEMV_SCHUR_C = 1,  // rows [nr,ns) cols [nI,nr): A_cr A_rr^-1 B_r^T z, the F_rc^T pieces (Eq. f1schur)
+    GEMV_CORNER = 2,   // rows [nI,nr) cols [nr,ns): A_rr^-1 A_rc v, the F_rc pieces       (Eq. f1schur)
+    GEMV_RECOVER = 3,  // rows [0,nr)  cols [nI,ns): x_r from y, lambda, x_c               (Eq. rF1)
+    GEMV_COARSE = 4,   // the dense K~cc^-1 (single matrix)
+    GEMV_SCHUR_G = 5,  // rows [nI,nr) cols [nI,ns): F_rr and F_rc pieces in one pass       (Eq. f1schur)
+    GEMV_NMODES = 6
 };
 
 // Source of the x vector of a batched GEMV (staged in shared memory per CTA).
 // kind (X_*): X_FLAT x_j = v[slot]; X_LAMBDA x_j = (B_r^T v)_j; X_PCG x_j =
 // (B_r^T (z + beta p))_j with z = v, p = v2; X_CORNER x_j = v[corner(slot)];
 // X_RECOVER interface slot -(B_r^T v)_j, corner slot v2[corner(slot)];
-// X_COARSE x_j = v[j].  k_gemv<double> reads v/v2, k_gemv<float> reads the
+// X_COARSE x_j = v[j]; X_PCG_CV / X_LAMBDA_CV: interface slots as X_PCG /
+// X_LAMBDA, corner slots -v3[corner(slot)].  k_gemv<double> reads v/v2, k_gemv<float> reads the
 // FP32 shadows vf/v2f so that it executes no FP64 instruction.
 struct XSrc {
     int kind;
     const double* v;
     const double* v2;
+    const double* v3;
     const float* vf;
     const float* v2f;
+    const float* v3f;
     const int32_t* slot_mult;
     const int32_t* slot_corner;
     const struct PcgScalars* sc;
@@ -222,8 +226,9 @@ struct dd_handle {
     int64_t work[DD_N_STAGES] = {};
     double work_bytes[DD_N_STAGES] = {};
     int64_t total_launches = 0;
-    double bytes_per_launch[DD_N_STAGES] = {};  // algorithmic bytes of one full launch (FP64)
-    double bytes_per_launch32[DD_N_STAGES] = {};  // same with FP32 matrices
+    double bytes_per_launch[DD_N_STAGES] = {};  // algorithmic bytes of one full launch (RHS, refinement)
+    double mode_bytes[GEMV_NMODES] = {};        // algorithmic bytes of one GEMV launch, FP64 matrices
+    double mode_bytes32[GEMV_NMODES] = {};      // same with FP32 matrices
 
     int fail(int code, const std::string& msg) {
         err = msg;
@@ -233,7 +238,7 @@ struct dd_handle {
 
 constexpr int kNB = 32;              // pivot block of the dense elimination
 // rows per CTA of the batched GEMV, per mode (LOCAL, SCHUR, CORNER, RECOVER, COARSE)
-constexpr int kRowsPerMode[5] = {32, 64, 64, 32, 8};
+constexpr int kRowsPerMode[GEMV_NMODES] = {32, 32, 64, 32, 8, 64};
 constexpr int kMaxPartials = 4096;   // block partials of the grid reductions
 
 // setup.cpp
@@ -266,6 +271,7 @@ int launch_advance(const dd_handle* h, const double* e_n, const double* e_nm1, c
 int launch_probe(const dd_handle* h, const double* e, double* out, void* stream);
 
 // GEMV x-source kinds (see kernels.cu)
-enum : int { X_FLAT = 0, X_LAMBDA = 1, X_PCG = 2, X_CORNER = 3, X_RECOVER = 4, X_COARSE = 5 };
+enum : int { X_FLAT = 0, X_LAMBDA = 1, X_PCG = 2, X_CORNER = 3, X_RECOVER = 4, X_COARSE = 5, X_PCG_CV = 6,
+             X_LAMBDA_CV = 7 };
 
 constexpr int kMaxProbes = 256;

@@ -377,6 +377,24 @@ __device__ __forceinline__ double xsrc_value(const XSrc& xs, int64_t slot, int64
             const int c = xs.slot_corner[slot];
             return c >= 0 ? xs.v2[c] : 0.0;
         }
+        case X_PCG_CV: {
+            const int m = xs.slot_mult[slot];
+            if (m == 0) {
+                const int c = xs.slot_corner[slot];
+                return c >= 0 ? -xs.v3[c] : 0.0;
+            }
+            const int mi = (m > 0 ? m : -m) - 1;
+            const double pv = xs.v[mi] + beta * xs.v2[mi];
+            return m > 0 ? pv : -pv;
+        }
+        case X_LAMBDA_CV: {
+            const int m = xs.slot_mult[slot];
+            if (m == 0) {
+                const int c = xs.slot_corner[slot];
+                return c >= 0 ? -xs.v3[c] : 0.0;
+            }
+            return m > 0 ? xs.v[m - 1] : -xs.v[-m - 1];
+        }
         default: return xs.v[j];
     }
 }
@@ -403,6 +421,24 @@ __device__ __forceinline__ float xsrc_value_f(const XSrc& xs, int64_t slot, int6
             if (m != 0) return m > 0 ? -xs.vf[m - 1] : xs.vf[-m - 1];
             const int c = xs.slot_corner[slot];
             return c >= 0 ? xs.v2f[c] : 0.0f;
+        }
+        case X_PCG_CV: {
+            const int m = xs.slot_mult[slot];
+            if (m == 0) {
+                const int c = xs.slot_corner[slot];
+                return c >= 0 ? -xs.v3f[c] : 0.0f;
+            }
+            const int mi = (m > 0 ? m : -m) - 1;
+            const float pv = fmaf(beta, xs.v2f[mi], xs.vf[mi]);
+            return m > 0 ? pv : -pv;
+        }
+        case X_LAMBDA_CV: {
+            const int m = xs.slot_mult[slot];
+            if (m == 0) {
+                const int c = xs.slot_corner[slot];
+                return c >= 0 ? -xs.v3f[c] : 0.0f;
+            }
+            return m > 0 ? xs.vf[m - 1] : -xs.vf[-m - 1];
         }
         default: return xs.vf[j];
     }
@@ -434,67 +470,114 @@ __device__ __forceinline__ void gemv_store(const GemvOut& go, int64_t o, TM acc,
     }
 }
 
-// Batched GEMV: one CTA per task (matrix, row range); the CTA stages its x
-// segment in shared memory and streams the rows.  Rows of <= 128 columns
-// (the corner-coupling block) use 8 lanes per row, longer rows a warp per row.
 template <typename TM>
+struct VecOf;
+template <>
+struct VecOf<float> {
+    using T = float4;
+    static constexpr int N = 4;
+};
+template <>
+struct VecOf<double> {
+    using T = double2;
+    static constexpr int N = 2;
+};
+__device__ __forceinline__ float vdot(const float4 a, const float4 b, float acc) {
+    acc = fmaf(a.x, b.x, acc);
+    acc = fmaf(a.y, b.y, acc);
+    acc = fmaf(a.z, b.z, acc);
+    return fmaf(a.w, b.w, acc);
+}
+__device__ __forceinline__ double vdot(const double2 a, const double2 b, double acc) {
+    acc = fma(a.x, b.x, acc);
+    return fma(a.y, b.y, acc);
+}
+
+// Batched GEMV: one CTA per task (matrix, row range).  The CTA stages its x
+// segment in shared memory, shifted so that column c sits at index c - c0a with
+// c0a = c0 rounded down to a 16-byte boundary (zeros outside [c0, c1)); every
+// row is then read with aligned 16-byte streaming loads (rows start on 16-byte
+// boundaries because ld and every matrix offset are multiples of 4 elements).
+// LPR lanes cooperate on one row: 32 for long FP32 rows, 8 for FP64 rows (fewer
+// FP64 reduction adds on GB300's narrow FP64 pipe) and for short rows.
+template <typename TM, int LPR>
 __global__ void __launch_bounds__(kThreads) k_gemv(const GemvTask* __restrict__ tasks, const MatDesc* __restrict__ mats,
                                                    const TM* __restrict__ M, int mode, XSrc xs, GemvOut go,
                                                    int staged, const int32_t* __restrict__ done) {
+    using VT = typename VecOf<TM>::T;
+    constexpr int VN = VecOf<TM>::N;
+    constexpr int RPW = 32 / LPR;
     if (done && *done) return;
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     TM* xsh = reinterpret_cast<TM*>(smem_raw);
     const GemvTask tk = tasks[blockIdx.x];
     const MatDesc md = mats[tk.mat];
     int c0, c1;
     switch (mode) {
         case GEMV_LOCAL: c0 = 0; c1 = md.nr; break;
-        case GEMV_SCHUR: c0 = md.nI; c1 = md.nr; break;
+        case GEMV_SCHUR_C: c0 = md.nI; c1 = md.nr; break;
         case GEMV_CORNER: c0 = md.nr; c1 = md.ns; break;
         case GEMV_RECOVER: c0 = md.nI; c1 = md.ns; break;
+        case GEMV_SCHUR_G: c0 = md.nI; c1 = md.ns; break;
         default: c0 = 0; c1 = md.ns; break;
     }
-    const int ncol = c1 - c0;
-    const TM beta = xs.kind == X_PCG ? (TM)xs.sc->beta : (TM)0;
+    const TM beta = (xs.kind == X_PCG || xs.kind == X_PCG_CV) ? (TM)xs.sc->beta : (TM)0;
     const TM alpha_t = (TM)go.alpha;
-    if (staged) {
-        for (int j = threadIdx.x; j < ncol; j += blockDim.x)
-            xsh[j] = stage_value<TM>(xs, md.voff + c0 + j, c0 + j, beta);
-        __syncthreads();
-    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (staged && ncol <= 128) {
-        const int sub = lane >> 3, l8 = lane & 7;
-        for (int rb = tk.row0 + 4 * warp; rb < tk.row1; rb += 4 * nw) {
+    const int sub = lane / LPR, l = lane % LPR;
+    if (!staged) {  // x too large for shared memory: scalar loads, x read through L1/L2
+        for (int rb = tk.row0 + RPW * warp; rb < tk.row1; rb += RPW * nw) {
             const int row = rb + sub;
             TM a = 0;
             if (row < tk.row1) {
-                const TM* Mr = M + md.moff + (int64_t)row * md.ld + c0;
-                for (int j = l8; j < ncol; j += 8) a += Mr[j] * xsh[j];
+                const TM* Mr = M + md.moff + (int64_t)row * md.ld;
+                for (int c = c0 + l; c < c1; c += LPR) a += Mr[c] * stage_value<TM>(xs, md.voff + c, c, beta);
             }
 #pragma unroll
-            for (int o = 4; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o, 8);
-            if (l8 == 0 && row < tk.row1) gemv_store<TM>(go, md.voff + row, a, alpha_t);
+            for (int o = LPR / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o, LPR);
+            if (l == 0 && row < tk.row1) gemv_store<TM>(go, md.voff + row, a, alpha_t);
         }
         return;
     }
-    for (int row = tk.row0 + warp; row < tk.row1; row += nw) {
-        const TM* Mr = M + md.moff + (int64_t)row * md.ld + c0;
+    const int c0a = c0 & ~(VN - 1);
+    const int next = ((c1 - c0a) + VN - 1) / VN * VN;
+    for (int k = threadIdx.x; k < next; k += blockDim.x) {
+        const int c = c0a + k;
+        xsh[k] = (c >= c0 && c < c1) ? stage_value<TM>(xs, md.voff + c, c, beta) : (TM)0;
+    }
+    __syncthreads();
+    const int nvec = next / VN;
+    const VT* xv = reinterpret_cast<const VT*>(xsh);
+    for (int rb = tk.row0 + RPW * warp; rb < tk.row1; rb += RPW * nw) {
+        const int row = rb + sub;
         TM a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-        int j = lane;
-        if (staged) {
-            for (; j + 96 < ncol; j += 128) {
-                a0 += Mr[j] * xsh[j];
-                a1 += Mr[j + 32] * xsh[j + 32];
-                a2 += Mr[j + 64] * xsh[j + 64];
-                a3 += Mr[j + 96] * xsh[j + 96];
+        if (row < tk.row1) {
+            const VT* mv = reinterpret_cast<const VT*>(M + md.moff + (int64_t)row * md.ld + c0a);
+            int v = l;
+            // four independent 16-byte loads in flight per lane
+            for (; v + 3 * LPR < nvec; v += 4 * LPR) {
+                const VT m0 = __ldcs(mv + v);
+                const VT m1 = __ldcs(mv + v + LPR);
+                const VT m2 = __ldcs(mv + v + 2 * LPR);
+                const VT m3 = __ldcs(mv + v + 3 * LPR);
+                a0 = vdot(m0, xv[v], a0);
+                a1 = vdot(m1, xv[v + LPR], a1);
+                a2 = vdot(m2, xv[v + 2 * LPR], a2);
+                a3 = vdot(m3, xv[v + 3 * LPR], a3);
             }
-            for (; j < ncol; j += 32) a0 += Mr[j] * xsh[j];
-        } else {
-            for (; j < ncol; j += 32) a0 += Mr[j] * stage_value<TM>(xs, md.voff + c0 + j, c0 + j, beta);
+            if (v < nvec) {
+                const VT m0 = __ldcs(mv + v);
+                const VT m1 = v + LPR < nvec ? __ldcs(mv + v + LPR) : VT{};
+                const VT m2 = v + 2 * LPR < nvec ? __ldcs(mv + v + 2 * LPR) : VT{};
+                a0 = vdot(m0, xv[v], a0);
+                if (v + LPR < nvec) a1 = vdot(m1, xv[v + LPR], a1);
+                if (v + 2 * LPR < nvec) a2 = vdot(m2, xv[v + 2 * LPR], a2);
+            }
         }
-        const TM acc = warp_sum((a0 + a1) + (a2 + a3));
-        if (lane == 0) gemv_store<TM>(go, md.voff + row, acc, alpha_t);
+        TM acc = (a0 + a1) + (a2 + a3);
+#pragma unroll
+        for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, LPR);
+        if (l == 0 && row < tk.row1) gemv_store<TM>(go, md.voff + row, acc, alpha_t);
     }
 }
 
@@ -795,6 +878,15 @@ int launch_assembled_norm(const dd_handle* h, int set_b, float* bf, void* stream
     return (int)cudaGetLastError();
 }
 
+template <typename TM, int LPR>
+int run_gemv(unsigned nb, size_t smem, cudaStream_t st, const GemvTask* tasks, const MatDesc* mats, const TM* M,
+             int mode, XSrc xs, GemvOut go, int staged, const int32_t* done) {
+    if (smem > 48 * 1024)
+        CU_TRY(cudaFuncSetAttribute(k_gemv<TM, LPR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_gemv<TM, LPR><<<nb, kThreads, smem, st>>>(tasks, mats, M, mode, xs, go, staged, done);
+    return (int)cudaGetLastError();
+}
+
 int launch_gemv(const dd_handle* h, int mode, int prec, XSrc xs, GemvOut go, bool check_done, void* stream) {
     const auto& tl = h->tasks[mode];
     if (tl.empty()) return 0;
@@ -805,25 +897,29 @@ int launch_gemv(const dd_handle* h, int mode, int prec, XSrc xs, GemvOut go, boo
     const GemvTask* tasks = h->d.tasks[mode];
     const int maxcol = mode == GEMV_COARSE ? (int)h->corner_dof.size() : h->max_ns;
     const size_t elt = prec == DD_MIXED ? sizeof(float) : sizeof(double);
-    size_t smem = (size_t)maxcol * elt;
+    size_t smem = (size_t)(maxcol + 4) * elt;   // staged extent rounds the segment out to 16-byte boundaries
     int staged = 1;
     if (smem > 200 * 1024) {
         staged = 0;
         smem = 0;
     }
     const int32_t* done = check_done ? &h->d.sc->done : nullptr;
+    const unsigned nb = (unsigned)tl.size();
+    // lanes per row: long rows 32, medium rows 16, the 72-wide corner block 8; FP64
+    // uses 8 except on the 7056-long coarse rows (fewer FP64 reduction adds)
+    static const int kLprF32[GEMV_NMODES] = {32, 16, 8, 16, 32, 16};
+    static const int kLprF64[GEMV_NMODES] = {8, 8, 8, 8, 32, 8};
     if (prec == DD_MIXED) {
         const float* M = mode == GEMV_COARSE ? h->d.K32 : h->d.M32;
-        if (smem > 48 * 1024)
-            CU_TRY(cudaFuncSetAttribute(k_gemv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_gemv<float><<<(unsigned)tl.size(), kThreads, smem, S(stream)>>>(tasks, mats, M, mode, xs, go, staged, done);
-    } else {
-        const double* M = mode == GEMV_COARSE ? h->d.K64 : h->d.M64;
-        if (smem > 48 * 1024)
-            CU_TRY(cudaFuncSetAttribute(k_gemv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_gemv<double><<<(unsigned)tl.size(), kThreads, smem, S(stream)>>>(tasks, mats, M, mode, xs, go, staged, done);
+        switch (kLprF32[mode]) {
+            case 8: return run_gemv<float, 8>(nb, smem, S(stream), tasks, mats, M, mode, xs, go, staged, done);
+            case 16: return run_gemv<float, 16>(nb, smem, S(stream), tasks, mats, M, mode, xs, go, staged, done);
+            default: return run_gemv<float, 32>(nb, smem, S(stream), tasks, mats, M, mode, xs, go, staged, done);
+        }
     }
-    return (int)cudaGetLastError();
+    const double* M = mode == GEMV_COARSE ? h->d.K64 : h->d.M64;
+    if (kLprF64[mode] == 32) return run_gemv<double, 32>(nb, smem, S(stream), tasks, mats, M, mode, xs, go, staged, done);
+    return run_gemv<double, 8>(nb, smem, S(stream), tasks, mats, M, mode, xs, go, staged, done);
 }
 
 int launch_iface_rhs(const dd_handle* h, float* fCf, void* stream) {

@@ -385,9 +385,10 @@ int dd_build_host(dd_handle* h, const dd_mesh* mesh, const int32_t* part, int32_
             const MatDesc& md = h->mats[s];
             int32_t r0 = 0, r1 = 0;
             if (mode == GEMV_LOCAL) { r0 = 0; r1 = md.ns; }
-            if (mode == GEMV_SCHUR) { r0 = md.nI; r1 = md.ns; }
+            if (mode == GEMV_SCHUR_C) { r0 = md.nr; r1 = md.ns; }
             if (mode == GEMV_CORNER) { r0 = md.nI; r1 = md.nr; }
             if (mode == GEMV_RECOVER) { r0 = 0; r1 = md.nr; }
+            if (mode == GEMV_SCHUR_G) { r0 = md.nI; r1 = md.nr; }
             const int rp = kRowsPerMode[mode];
             for (int32_t a = r0; a < r1; a += rp) tl.push_back({s, a, std::min(r1, a + rp), 0});
         }
