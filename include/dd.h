@@ -202,6 +202,21 @@ int dd_step(dd_handle* h, const double* d2g, double* e_out, dd_stats* stats, voi
  * dd_factor.  lam, out: device [n_lambda]. */
 int dd_schur_apply(dd_handle* h, const double* lam, double* out, void* stream);
 
+/* Same result as dd_schur_apply, for callers that must not allocate device
+ * memory (for example code running inside a fixed memory pool, a callback
+ * that may only use buffers it was handed, or a latency-critical loop where an
+ * allocation would synchronise the device).  The paper has no counterpart: this
+ * is a library convenience.  The call allocates nothing: its scratch vectors
+ * live in a file-scope device array of 2^20 doubles (8 MiB) that every GPU
+ * loading the library keeps until the process exits.  The caller passes lam and
+ * out (device [n_lambda]) and must have bound a workspace and factored.
+ * Limit: (n_local rounded up to 32) + 2 x (n_corner rounded up to 32) <= 2^20,
+ * else DD_ERR_ARG with a message.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current; make
+ * that first call before any stream capture.  All calls on a device share the
+ * array: calls whose kernels overlap on the GPU race on it. */
+int dd_schur_apply_static(dd_handle* h, const double* lam, double* out, void* stream);
+
 /* Evaluate E = sum_i e_i W_i at the probe points for the current e^n.
  * out: device [n_probe*3] (x, y, z per probe). */
 int dd_probe(dd_handle* h, double* out, void* stream);

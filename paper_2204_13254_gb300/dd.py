@@ -20,7 +20,7 @@ DD_ERR_NO_CONVERGENCE, DD_ERR_NONFINITE, DD_ERR_TIMEOUT, DD_ERR_CUDA, DD_ERR_STA
 DD_FP64, DD_MIXED = 0, 1
 
 SYMBOLS = ["dd_setup", "dd_set_params", "dd_get_sizes", "dd_get_maps", "dd_set_probes", "dd_bind_workspace",
-           "dd_factor", "dd_step", "dd_schur_apply", "dd_probe", "dd_get_state", "dd_set_state", "dd_profile",
+           "dd_factor", "dd_step", "dd_schur_apply", "dd_schur_apply_static", "dd_probe", "dd_get_state", "dd_set_state", "dd_profile",
            "dd_destroy", "dd_last_error"]
 N_STAGES = 9
 STAGES = ["rhs", "local_solve", "iface_apply", "coarse", "corner", "recover", "vector", "refine", "factor"]
@@ -73,6 +73,7 @@ def load_library(path: str = LIB_PATH):
         "dd_factor": (C.c_int, [vp, C.c_double, vp]),
         "dd_step": (C.c_int, [vp, vp, vp, C.POINTER(dd_stats), vp]),
         "dd_schur_apply": (C.c_int, [vp, vp, vp, vp]),
+        "dd_schur_apply_static": (C.c_int, [vp, vp, vp, vp]),
         "dd_probe": (C.c_int, [vp, vp, vp]),
         "dd_get_state": (C.c_int, [vp, vp, vp, C.POINTER(i64), vp]),
         "dd_set_state": (C.c_int, [vp, vp, vp, i64, vp]),
@@ -189,6 +190,11 @@ def dd_step(h, d2g=None, e_out=None, stats=True, stream=None, raise_on_error=Tru
 
 def dd_schur_apply(h, lam, out, stream=None):
     _check(h, lib().dd_schur_apply(h, _ptr(lam), _ptr(out), _stream(stream)))
+
+
+def dd_schur_apply_static(h, lam, out, stream=None):
+    """dd_schur_apply without any device allocation (scratch in a fixed device array)."""
+    _check(h, lib().dd_schur_apply_static(h, _ptr(lam), _ptr(out), _stream(stream)))
 
 
 def dd_probe(h, out, stream=None):

@@ -1,0 +1,53 @@
+"""dd_schur_apply_static: the interface-operator application for callers that
+cannot allocate device memory, checked against dd_schur_apply.
+
+Some callers may not call cudaMalloc at all -- code inside a fixed memory pool,
+a callback that may only touch the buffers it was given, or a latency-critical
+loop where an allocation would synchronise the device.  dd_schur_apply_static
+keeps its scratch in a fixed device array inside the library instead of the
+bound workspace.  This file is collected last so that a failure here cannot stop
+the other GPU tests; it passes alone in a fresh process and after them.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2204_13254_gb300 import dd as D
+from paper_2204_13254_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def test_static_scratch_matches_workspace_path_twice():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    w = W.cavity(6, 3)
+    fs = D.FieldSolver(w.xyz, w.tets, w.part, w.n_sub).bind()
+    fs.factor(0.05)
+    rng = np.random.default_rng(7)
+    for call in range(2):                   # two calls in a row share the static scratch
+        lam = torch.tensor(rng.standard_normal(fs.n_lambda), device="cuda")
+        ref = torch.empty_like(lam)
+        got = torch.empty_like(lam)
+        D.dd_schur_apply(fs.h, lam, ref)
+        D.dd_schur_apply_static(fs.h, lam, got)
+        torch.cuda.synchronize()
+        r, g = ref.cpu().numpy(), got.cpu().numpy()
+        assert np.linalg.norm(g - r) <= 1e-12 * np.linalg.norm(r), call
+    fs.close()
+
+
+def test_static_scratch_rejects_oversized_problem():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    w = W.cavity(56, 2)                      # > 2^20 local unknowns
+    h = D.dd_setup(w.xyz, w.tets, w.part, w.n_sub)
+    try:
+        assert D.dd_get_sizes(h).n_local > (1 << 20)
+        dummy = torch.zeros(4, dtype=torch.float64, device="cuda")
+        with pytest.raises(D.DDError) as e:
+            D.dd_schur_apply_static(h, dummy, dummy)
+        assert e.value.code == D.DD_ERR_ARG and "static limit" in str(e.value)
+    finally:
+        D.dd_destroy(h)
