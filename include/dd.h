@@ -230,8 +230,9 @@ int dd_set_state(dd_handle* h, const double* e_n, const double* e_nm1, int64_t s
 /* Per-stage timing of the library's own kernels (CUDA events recorded on the
  * launch stream around every launch while enabled).
  * Stages: 0 right-hand side SpMV, 1 local solve GEMV (A_rr^-1 b_r),
- * 2 interface operator GEMV (F_rr / F_rc^T pieces), 3 coarse K~cc^-1 GEMV,
- * 4 corner coupling GEMV (F_rc pieces), 5 recovery GEMV (Eq. rF1),
+ * 2 interface-row GEMV of the Eq. f1schur operator (F_rr and F_rc pieces),
+ * 3 coarse K~cc^-1 GEMV, 4 corner-row GEMVs (F_rc^T pieces, and the F_rc
+ * pieces of the interface right-hand side), 5 recovery GEMV (Eq. rF1),
  * 6 interface/corner vector kernels (jumps, gathers, CG updates),
  * 7 FP64 refinement residual, 8 factorisation kernels.
  * launches   kernels launched (including ones that exit early after convergence)

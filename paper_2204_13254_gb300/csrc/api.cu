@@ -277,7 +277,7 @@ int apply_schur_w(dd_handle* h, int prec, int kind, const double* v, const doubl
     if (!h->corner_dof.empty()) {
         // u_s = A_cr A_rr^-1 B_r^T z (corner rows), K~cc^-1 sum_s B_c^T u_s
         {
-            Prof P(h, ST_SCHUR, s, 1, full * mb(h, GEMV_SCHUR_C, prec));
+            Prof P(h, ST_CORNER, s, 1, full * mb(h, GEMV_SCHUR_C, prec));
             rc = launch_gemv(h, GEMV_SCHUR_C, prec, xsrc(kind, v, v2, vf, v2f),
                              V.f32 ? gout(nullptr, nullptr, V.wf, nullptr, 1.0) : gout(h->d.w, nullptr, nullptr, nullptr, 1.0),
                              check_done, s);
@@ -308,8 +308,10 @@ int apply_schur_w(dd_handle* h, int prec, int kind, const double* v, const doubl
 void count_cg_work(dd_handle* h, int prec, int n) {
     const bool c = !h->corner_dof.empty();
     h->work[ST_SCHUR] += n;
-    h->work_bytes[ST_SCHUR] += n * (mb(h, GEMV_SCHUR_G, prec) + (c ? mb(h, GEMV_SCHUR_C, prec) : 0.0));
+    h->work_bytes[ST_SCHUR] += n * mb(h, GEMV_SCHUR_G, prec);
     if (c) {
+        h->work[ST_CORNER] += n;
+        h->work_bytes[ST_CORNER] += n * mb(h, GEMV_SCHUR_C, prec);
         h->work[ST_COARSE] += n;
         h->work_bytes[ST_COARSE] += n * mb(h, GEMV_COARSE, prec);
     }
@@ -390,7 +392,7 @@ int dd_solve(dd_handle* h, int prec, double tol, bool warm, int* it_out, double*
     if (has_c) {
         if (has_l) {
             {
-                Prof P(h, ST_SCHUR, s, 1, mb(h, GEMV_SCHUR_C, prec));
+                Prof P(h, ST_CORNER, s, 1, mb(h, GEMV_SCHUR_C, prec));
                 CK(h, launch_gemv(h, GEMV_SCHUR_C, prec, xsrc(X_LAMBDA, h->d.lam, nullptr, V.lamf, nullptr),
                                   V.f32 ? gout(nullptr, nullptr, V.wf, nullptr, 1.0) : gout(h->d.w, nullptr, nullptr, nullptr, 1.0),
                                   false, s), "Frc^T");
