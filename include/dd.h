@@ -197,6 +197,35 @@ int dd_factor(dd_handle* h, double dt, void* stream);
  * still advanced with the last iterate), DD_ERR_NONFINITE, DD_ERR_CUDA. */
 int dd_step(dd_handle* h, const double* d2g, double* e_out, dd_stats* stats, void* stream);
 
+/* ---- discrete adjoint (gradients of a probe objective) ----------------
+ * Not in the paper; derived from the recurrence above.  For the objective
+ * J = sum_k sum_p |E(r_p; e^k)|^2 and the forward residuals
+ * R^k = A e^{k+1} - B e^k + A e^{k-1} + a d2g^k, the adjoint march runs backward,
+ *     A mu^k = B mu^{k+1} - A mu^{k+2} + dJ/de^k,   mu^{N+1} = mu^{N+2} = 0,
+ * with the same factors (A and B are symmetric), and
+ *     dJ/deps_K = -sum_k mu^k^T T_K (e^k - 2 e^{k-1} + e^{k-2}),
+ *     dJ/da     = -sum_k mu^k . d2g^{k-1}   (T_K: unit-eps element mass matrix of tet K).
+ * The adjoint keeps its own time levels and interface multipliers in the workspace. */
+
+/* mu^{k+1} = mu^{k+2} = 0: start of a backward sweep. */
+int dd_adjoint_reset(dd_handle* h, void* stream);
+
+/* One backward level: mu^k from (mu^{k+1}, mu^{k+2}) and seed = dJ/de^k
+ * (device [n_dof]), then, if grad_eps (device [n_tets]) is given,
+ * grad_eps[K] -= mu^k^T T_K (e_k - 2 e_km1 + e_km2) with the forward fields
+ * e_k = e^k, e_km1 = e^{k-1}, e_km2 = e^{k-2} (device [n_dof]); if grad_amp
+ * (device scalar) and d2g_hat (device [n_dof], unit-amplitude source second
+ * difference of forward step k-1) are given, *grad_amp -= mu^k . d2g_hat.
+ * mu_out (device [n_dof] or NULL) receives mu^k.  Uses the handle's precision
+ * and tolerances.  Errors as dd_step. */
+int dd_adjoint_step(dd_handle* h, const double* seed, const double* e_k, const double* e_km1, const double* e_km2,
+                    const double* d2g_hat, double* grad_eps, double* grad_amp, double* mu_out, dd_stats* stats,
+                    void* stream);
+
+/* seed = 2 * weight * P^T P e: dJ/de of weight * sum_p |E(r_p; e)|^2 over the
+ * probe set (device [n_dof] e and seed; seed is overwritten). */
+int dd_probe_seed(dd_handle* h, const double* e, double weight, double* seed, void* stream);
+
 /* Apply the Schur-complement interface operator of Eq. f1schur,
  * out = (F_rr + F_rc K~cc^-1 F_rc^T) lam, in FP64 with the factors of the last
  * dd_factor.  lam, out: device [n_lambda]. */

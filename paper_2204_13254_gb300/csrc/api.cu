@@ -180,6 +180,11 @@ size_t dd_workspace_layout(dd_handle* h, bool assign) {
     L.take(d.Pinv, (size_t)(h->n_sub + 1) * kNB * kNB);
     L.take(d.dinv, nm);
     for (int k = 0; k < 3; ++k) L.take(d.e[k], nd);
+    for (int k = 0; k < 3; ++k) L.take(d.mu[k], nd);
+    L.take(d.lam_adj, nm);
+    L.take(d.lamf_adj, nm);
+    L.take(d.tet_dof, 6 * (size_t)h->n_tets);
+    L.take(d.That, 36 * (size_t)h->n_tets);
     L.take(d.b, nl);
     L.take(d.y, nl);
     L.take(d.w, nl);
@@ -528,11 +533,19 @@ int dd_bind_workspace(dd_handle* h, void* dev, size_t bytes, void* stream) {
     CK(h, upload(h->d.Tval, h->Tval, s), "upload");
     CK(h, upload(h->d.Sval, h->Sval, s), "upload");
     for (int m = 0; m < GEMV_NMODES; ++m) CK(h, upload(h->d.tasks[m], h->tasks[m], s), "upload");
+    {
+        std::vector<int32_t> td(h->tet_dof.size());
+        for (size_t i = 0; i < td.size(); ++i) td[i] = (int32_t)h->tet_dof[i];
+        CK(h, upload(h->d.tet_dof, td, s), "upload");
+        CK(h, (int)cudaStreamSynchronize(s), "sync");   // td is a local
+    }
+    CK(h, upload(h->d.That, h->That, s), "upload");
     if (h->n_probe) {
         CK(h, upload(h->d.probe_dof, h->probe_dof, s), "upload");
         CK(h, upload(h->d.probe_w, h->probe_w, s), "upload");
     }
     for (int k = 0; k < 3; ++k) CK(h, (int)cudaMemsetAsync(h->d.e[k], 0, sizeof(double) * nd, s), "memset");
+    for (int k = 0; k < 3; ++k) CK(h, (int)cudaMemsetAsync(h->d.mu[k], 0, sizeof(double) * nd, s), "memset");
     CK(h, (int)cudaMemsetAsync(h->d.sc, 0, sizeof(PcgScalars), s), "memset");
     CK(h, (int)cudaMemsetAsync(h->d.status, 0, 16, s), "memset");
     CK(h, (int)cudaStreamSynchronize(s), "sync");
@@ -580,33 +593,37 @@ int dd_factor(dd_handle* h, double dt, void* stream) {
     const size_t nd = (size_t)h->n_dof;
     for (int k = 0; k < 3; ++k) CK(h, (int)cudaMemsetAsync(h->d.e[k], 0, sizeof(double) * nd, s), "memset");
     CK(h, (int)cudaStreamSynchronize(s), "sync");
+    for (int k = 0; k < 3; ++k) CK(h, (int)cudaMemsetAsync(h->d.mu[k], 0, sizeof(double) * nd, s), "memset");
+    CK(h, (int)cudaStreamSynchronize(s), "sync");
     h->dt = dt;
     h->step = 0;
     h->cur = 0;
+    h->cur_adj = 0;
     h->lam_valid = false;
+    h->lam_adj_valid = false;
     h->factored = true;
     return DD_OK;
 }
 
-int dd_step(dd_handle* h, const double* d2g, double* e_out, dd_stats* stats, void* stream) {
-    if (!h) return DD_ERR_ARG;
-    if (!h->factored) return h->fail(DD_ERR_STATE, "dd_step before dd_factor");
-    cudaStream_t s = (cudaStream_t)stream;
-    const double* e_n = h->d.e[h->cur];
-    const double* e_nm1 = h->d.e[(h->cur + 2) % 3];
-    double* e_np1 = h->d.e[(h->cur + 1) % 3];
+namespace {
+
+// One level of the Newmark recurrence from (u_n, u_nm1) into u_np1:
+// A delta = -dt^2 S u_n + src_sign * src (subassembled, source on the owner),
+// u_np1 = 2 u_n - u_nm1 + delta.  Used by the forward step (src = d2g, sign -1)
+// and by the adjoint step (src = seed, sign +1).
+int advance(dd_handle* h, const double* u_n, const double* u_nm1, double* u_np1, const double* src, double src_sign,
+            int* iters_out, int* refs_out, double* resid_out, cudaStream_t s) {
     int status = DD_OK, iters = 0, refinements = 0;
     double resid = 0.0;
-    // b = -dt^2 S e^n - d2g (subassembled): A delta = b, e^{n+1} = 2e^n - e^{n-1} + delta
     {
         Prof P(h, ST_RHS, s, 1, h->bytes_per_launch[ST_RHS]);
-        CK(h, launch_rhs(h, e_n, d2g, h->dt, s), "rhs");
+        CK(h, launch_rhs(h, u_n, src, src_sign, h->dt, s), "rhs");
     }
     if (h->prm.precision == DD_FP64) {
         status = dd_solve(h, DD_FP64, h->prm.tol, h->prm.warm_start != 0, &iters, &resid, s);
         if (status != DD_OK && status != DD_ERR_NO_CONVERGENCE) return status;
         Prof P(h, ST_VEC, s, 1);
-        CK(h, launch_writeback(h, e_n, e_nm1, nullptr, nullptr, 1, e_np1, s), "writeback");
+        CK(h, launch_writeback(h, u_n, u_nm1, nullptr, nullptr, 1, u_np1, s), "writeback");
     } else {
         // FP64 iterative refinement of the step system with FP32 DD correction solves
         {
@@ -634,7 +651,7 @@ int dd_step(dd_handle* h, const double* d2g, double* e_out, dd_stats* stats, voi
             if (st != DD_OK && st != DD_ERR_NO_CONVERGENCE) return st;
             {
                 Prof P(h, ST_VEC, s, 1);
-                CK(h, launch_writeback(h, e_n, e_nm1, h->d.delta_k, h->d.delta, k == 0 ? 1 : 0, nullptr, s), "writeback");
+                CK(h, launch_writeback(h, u_n, u_nm1, h->d.delta_k, h->d.delta, k == 0 ? 1 : 0, nullptr, s), "writeback");
             }
             {
                 Prof P(h, ST_REFINE, s, 2, h->bytes_per_launch[ST_REFINE]);
@@ -656,12 +673,41 @@ int dd_step(dd_handle* h, const double* d2g, double* e_out, dd_stats* stats, voi
             CK(h, (int)cudaMemcpyAsync(h->d.lamf, h->d.lamf_scratch, sizeof(float) * h->mult_dof.size(),
                                        cudaMemcpyDeviceToDevice, s), "restore lambda");
         }
+        if (status == DD_ERR_NONFINITE) return status;
         {
             Prof P(h, ST_VEC, s, 1);
-            CK(h, launch_advance(h, e_n, e_nm1, h->d.delta, e_np1, s), "advance");
+            CK(h, launch_advance(h, u_n, u_nm1, h->d.delta, u_np1, s), "advance");
         }
         if (status == DD_ERR_NO_CONVERGENCE) h->err = "refinement did not reach refine_tol";
     }
+    *iters_out = iters;
+    *refs_out = refinements;
+    *resid_out = resid;
+    return status;
+}
+
+// Swap the interface multipliers (warm start) between the forward and the
+// adjoint march, which share the factors but not their CG history.
+void swap_lambda(dd_handle* h) {
+    std::swap(h->d.lam, h->d.lam_adj);
+    std::swap(h->d.lamf, h->d.lamf_adj);
+    std::swap(h->lam_valid, h->lam_adj_valid);
+}
+
+}  // namespace
+
+int dd_step(dd_handle* h, const double* d2g, double* e_out, dd_stats* stats, void* stream) {
+    if (!h) return DD_ERR_ARG;
+    if (!h->factored) return h->fail(DD_ERR_STATE, "dd_step before dd_factor");
+    cudaStream_t s = (cudaStream_t)stream;
+    const double* e_n = h->d.e[h->cur];
+    const double* e_nm1 = h->d.e[(h->cur + 2) % 3];
+    double* e_np1 = h->d.e[(h->cur + 1) % 3];
+    int iters = 0, refinements = 0;
+    double resid = 0.0;
+    // b = -dt^2 S e^n - d2g (subassembled): A delta = b, e^{n+1} = 2e^n - e^{n-1} + delta
+    const int status = advance(h, e_n, e_nm1, e_np1, d2g, -1.0, &iters, &refinements, &resid, s);
+    if (status != DD_OK && status != DD_ERR_NO_CONVERGENCE) return status;
     h->cur = (h->cur + 1) % 3;
     h->step += 1;
     if (e_out) CK(h, (int)cudaMemcpyAsync(e_out, e_np1, sizeof(double) * h->n_dof, cudaMemcpyDeviceToDevice, s), "e_out");
@@ -672,6 +718,62 @@ int dd_step(dd_handle* h, const double* d2g, double* e_out, dd_stats* stats, voi
         stats->status = status;
     }
     return status;
+}
+
+int dd_adjoint_reset(dd_handle* h, void* stream) {
+    if (!h) return DD_ERR_ARG;
+    if (!h->bound) return h->fail(DD_ERR_STATE, "no workspace bound");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int k = 0; k < 3; ++k) CK(h, (int)cudaMemsetAsync(h->d.mu[k], 0, sizeof(double) * h->n_dof, s), "memset");
+    h->cur_adj = 0;
+    h->lam_adj_valid = false;
+    return DD_OK;
+}
+
+int dd_adjoint_step(dd_handle* h, const double* seed, const double* e_k, const double* e_km1, const double* e_km2,
+                    const double* d2g_hat, double* grad_eps, double* grad_amp, double* mu_out, dd_stats* stats,
+                    void* stream) {
+    if (!h || !seed) return DD_ERR_ARG;
+    if (!h->factored) return h->fail(DD_ERR_STATE, "dd_adjoint_step before dd_factor");
+    if (grad_eps && (!e_k || !e_km1 || !e_km2)) return h->fail(DD_ERR_ARG, "grad_eps needs e_k, e_km1, e_km2");
+    cudaStream_t s = (cudaStream_t)stream;
+    const double* mu_k1 = h->d.mu[h->cur_adj];
+    const double* mu_k2 = h->d.mu[(h->cur_adj + 2) % 3];
+    double* mu_k = h->d.mu[(h->cur_adj + 1) % 3];
+    int iters = 0, refinements = 0;
+    double resid = 0.0;
+    // A mu^k = B mu^{k+1} - A mu^{k+2} + seed   (A, B symmetric: same factors as the forward march)
+    swap_lambda(h);
+    const int status = advance(h, mu_k1, mu_k2, mu_k, seed, +1.0, &iters, &refinements, &resid, s);
+    swap_lambda(h);
+    if (status != DD_OK && status != DD_ERR_NO_CONVERGENCE) return status;
+    h->cur_adj = (h->cur_adj + 1) % 3;
+    if (grad_eps) {
+        Prof P(h, ST_VEC, s, 1);
+        CK(h, launch_grad_eps(h, mu_k, e_k, e_km1, e_km2, grad_eps, s), "grad eps");
+    }
+    if (grad_amp && d2g_hat) {
+        Prof P(h, ST_VEC, s, 1);
+        CK(h, launch_dot_sub(h, mu_k, d2g_hat, grad_amp, s), "grad amp");
+    }
+    if (mu_out) CK(h, (int)cudaMemcpyAsync(mu_out, mu_k, sizeof(double) * h->n_dof, cudaMemcpyDeviceToDevice, s), "mu_out");
+    if (stats) {
+        stats->iters = iters;
+        stats->refinements = refinements;
+        stats->resid = resid;
+        stats->status = status;
+    }
+    return status;
+}
+
+int dd_probe_seed(dd_handle* h, const double* e, double weight, double* seed, void* stream) {
+    if (!h || !e || !seed) return DD_ERR_ARG;
+    if (!h->bound) return h->fail(DD_ERR_STATE, "no workspace bound");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(h, (int)cudaMemsetAsync(seed, 0, sizeof(double) * h->n_dof, s), "memset");
+    Prof P(h, ST_VEC, s, 1);
+    CK(h, launch_probe_seed(h, e, weight, seed, s), "probe seed");
+    return DD_OK;
 }
 
 int dd_schur_apply(dd_handle* h, const double* lam, double* out, void* stream) {

@@ -117,8 +117,13 @@ struct DevPtrs {
     float* K32 = nullptr;
     double* Pinv = nullptr;          // [n_sub+1][NB*NB] pivot-block inverses while factoring
     double* dinv = nullptr;          // [n_lambda] inverse Jacobi diagonal
-    // time levels (ring of 3)
+    // time levels (ring of 3) of the forward and the adjoint march
     double* e[3] = {nullptr, nullptr, nullptr};
+    double* mu[3] = {nullptr, nullptr, nullptr};
+    double* lam_adj = nullptr;       // adjoint multipliers (warm start), swapped with lam
+    float* lamf_adj = nullptr;
+    int32_t* tet_dof = nullptr;      // [n_tets*6] dof of each tet edge, -1 on the PEC wall
+    double* That = nullptr;          // [n_tets*36] unit-eps oriented element mass matrices
     // flat local vectors (n_local)
     double* b = nullptr;             // local right-hand side
     double* y = nullptr;             // GEMV outputs / local solutions
@@ -215,7 +220,9 @@ struct dd_handle {
     double dt = 0.0;
     int64_t step = 0;
     int cur = 0;                     // e[cur] = e^n, e[(cur+2)%3] = e^{n-1}
+    int cur_adj = 0;                 // mu[cur_adj] = mu^{k+1}, mu[(cur_adj+2)%3] = mu^{k+2}
     bool lam_valid = false;
+    bool lam_adj_valid = false;
 
     // profiling (dd_profile)
     bool prof_on = false;
@@ -252,7 +259,11 @@ int launch_dense_assemble(const dd_handle* h, void* stream);
 int launch_sweep(const dd_handle* h, bool coarse, int k0, void* stream);
 int launch_coarse_assemble(const dd_handle* h, void* stream);
 int launch_factor_finish(const dd_handle* h, void* stream);
-int launch_rhs(const dd_handle* h, const double* e_n, const double* d2g, double dt, void* stream);
+int launch_rhs(const dd_handle* h, const double* e_n, const double* src, double src_sign, double dt, void* stream);
+int launch_grad_eps(const dd_handle* h, const double* mu, const double* e_k, const double* e_km1, const double* e_km2,
+                    double* grad_eps, void* stream);
+int launch_dot_sub(const dd_handle* h, const double* a, const double* b, double* acc, void* stream);
+int launch_probe_seed(const dd_handle* h, const double* e, double weight, double* seed, void* stream);
 int launch_residual_local(const dd_handle* h, void* stream);
 int launch_assembled_norm(const dd_handle* h, int set_b, float* bf, void* stream);
 int launch_gemv(const dd_handle* h, int mode, int prec, XSrc xs, GemvOut go, bool check_done, void* stream);

@@ -308,12 +308,13 @@ __global__ void k_to_fp32(int64_t n, const double* __restrict__ a, float* __rest
 // Step: right-hand side (Newmark increment form)
 // ----------------------------------------------------------------------------
 
-// b_s = -dt^2 S^(s) e^n|_s - (owner ? d2g : 0), one 8-lane group per slot row.
+// b_s = -dt^2 S^(s) e^n|_s + src_sign * (owner ? src : 0), one 8-lane group per slot row
+// (forward: src = d2g, sign -1; adjoint: src = seed, sign +1).
 // With e^{n+1} = 2e^n - e^{n-1} + delta, the recurrence becomes A delta = b.
 __global__ void k_rhs(int64_t n_local, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col_dof,
                       const double* __restrict__ Sv, const double* __restrict__ e_n, const double* __restrict__ d2g,
-                      const int32_t* __restrict__ slot_dof, const uint8_t* __restrict__ slot_own, double mdt2,
-                      double* __restrict__ b) {
+                      double src_sign, const int32_t* __restrict__ slot_dof, const uint8_t* __restrict__ slot_own,
+                      double mdt2, double* __restrict__ b) {
     // each warp owns 4 consecutive rows (8 lanes per row); the loop is warp-uniform
     const int lane8 = threadIdx.x & 7;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -327,7 +328,7 @@ __global__ void k_rhs(int64_t n_local, const int64_t* __restrict__ row_ptr, cons
         for (int o = 4; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, 8);
         if (lane8 == 0 && i < n_local) {
             double v = mdt2 * s;
-            if (d2g && slot_own[i]) v -= d2g[slot_dof[i]];
+            if (d2g && slot_own[i]) v += src_sign * d2g[slot_dof[i]];
             b[i] = v;
         }
     }
@@ -791,6 +792,55 @@ __global__ void __launch_bounds__(kThreads) k_assemble_rhs(int64_t n_dof, const 
     }
 }
 
+// grad_eps[K] -= mu|_K^T T_K (e_k - 2 e_km1 + e_km2)|_K  (dA/deps_K = T_K, dB/deps_K = 2 T_K)
+__global__ void k_grad_eps(int64_t n_tets, const int32_t* __restrict__ tet_dof, const double* __restrict__ That,
+                           const double* __restrict__ mu, const double* __restrict__ e_k,
+                           const double* __restrict__ e_km1, const double* __restrict__ e_km2,
+                           double* __restrict__ grad) {
+    for (int64_t K = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; K < n_tets; K += (int64_t)gridDim.x * blockDim.x) {
+        double m[6], v[6];
+#pragma unroll
+        for (int p = 0; p < 6; ++p) {
+            const int d = tet_dof[6 * K + p];
+            m[p] = d >= 0 ? mu[d] : 0.0;
+            v[p] = d >= 0 ? e_k[d] - 2.0 * e_km1[d] + e_km2[d] : 0.0;
+        }
+        const double* Tk = That + 36 * K;
+        double acc = 0.0;
+#pragma unroll
+        for (int p = 0; p < 6; ++p) {
+            double r = 0.0;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) r += Tk[6 * p + q] * v[q];
+            acc += m[p] * r;
+        }
+        grad[K] -= acc;
+    }
+}
+
+// *acc -= a . b (deterministic grid reduction; the last block updates *acc)
+__global__ void __launch_bounds__(kThreads) k_dot_sub(int64_t n, const double* __restrict__ a,
+                                                      const double* __restrict__ b, double* acc, PcgScalars* sc,
+                                                      double* __restrict__ partials) {
+    double v[1] = {0.0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v[0] += a[i] * b[i];
+    if (grid_sum<1>(v, partials, &sc->counter[4])) *acc -= v[0];
+}
+
+// seed += 2 w P^T P e over all probes (one thread, fixed order; at most a few
+// hundred probes x 18 weights)
+__global__ void k_probe_seed(int n_probe, const int32_t* __restrict__ pd, const double* __restrict__ pw,
+                             const double* __restrict__ e, double weight, double* __restrict__ seed) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    for (int k = 0; k < n_probe; ++k)
+        for (int c = 0; c < 3; ++c) {
+            double v = 0.0;
+            for (int le = 0; le < 6; ++le) v += e[pd[6 * k + le]] * pw[18 * k + 3 * le + c];
+            for (int le = 0; le < 6; ++le) seed[pd[6 * k + le]] += 2.0 * weight * v * pw[18 * k + 3 * le + c];
+        }
+}
+
 __global__ void k_probe(int n_probe, const int32_t* __restrict__ pd, const double* __restrict__ pw,
                         const double* __restrict__ e, double* __restrict__ out) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -855,11 +905,11 @@ int launch_factor_finish(const dd_handle* h, void* stream) {
     return (int)cudaGetLastError();
 }
 
-int launch_rhs(const dd_handle* h, const double* e_n, const double* d2g, double dt, void* stream) {
+int launch_rhs(const dd_handle* h, const double* e_n, const double* src, double src_sign, double dt, void* stream) {
     const int64_t nl = h->sub_ptr.back();
     const int blocks = (int)std::min<int64_t>((nl * 8 + kThreads - 1) / kThreads, 152 * 16);
-    k_rhs<<<blocks, kThreads, 0, S(stream)>>>(nl, h->d.row_ptr, h->d.col_dof, h->d.Sval, e_n, d2g, h->d.slot_dof,
-                                              h->d.slot_own, -dt * dt, h->d.b);
+    k_rhs<<<blocks, kThreads, 0, S(stream)>>>(nl, h->d.row_ptr, h->d.col_dof, h->d.Sval, e_n, src, src_sign,
+                                              h->d.slot_dof, h->d.slot_own, -dt * dt, h->d.b);
     return (int)cudaGetLastError();
 }
 
@@ -983,6 +1033,26 @@ int launch_advance(const dd_handle* h, const double* e_n, const double* e_nm1, c
                    void* stream) {
     const int64_t nd = h->n_dof;
     k_advance<<<reduce_blocks(nd), kThreads, 0, S(stream)>>>(nd, e_n, e_nm1, delta, e_np1);
+    return (int)cudaGetLastError();
+}
+
+int launch_grad_eps(const dd_handle* h, const double* mu, const double* e_k, const double* e_km1, const double* e_km2,
+                    double* grad_eps, void* stream) {
+    const int64_t nt = h->n_tets;
+    k_grad_eps<<<(unsigned)std::min<int64_t>((nt + kThreads - 1) / kThreads, 152 * 32), kThreads, 0, S(stream)>>>(
+        nt, h->d.tet_dof, h->d.That, mu, e_k, e_km1, e_km2, grad_eps);
+    return (int)cudaGetLastError();
+}
+
+int launch_dot_sub(const dd_handle* h, const double* a, const double* b, double* acc, void* stream) {
+    const int64_t nd = h->n_dof;
+    k_dot_sub<<<reduce_blocks(nd), kThreads, 0, S(stream)>>>(nd, a, b, acc, h->d.sc, h->d.partials);
+    return (int)cudaGetLastError();
+}
+
+int launch_probe_seed(const dd_handle* h, const double* e, double weight, double* seed, void* stream) {
+    if (h->n_probe == 0) return 0;
+    k_probe_seed<<<1, 32, 0, S(stream)>>>(h->n_probe, h->d.probe_dof, h->d.probe_w, e, weight, seed);
     return (int)cudaGetLastError();
 }
 

@@ -20,7 +20,8 @@ DD_ERR_NO_CONVERGENCE, DD_ERR_NONFINITE, DD_ERR_TIMEOUT, DD_ERR_CUDA, DD_ERR_STA
 DD_FP64, DD_MIXED = 0, 1
 
 SYMBOLS = ["dd_setup", "dd_set_params", "dd_get_sizes", "dd_get_maps", "dd_set_probes", "dd_bind_workspace",
-           "dd_factor", "dd_step", "dd_schur_apply", "dd_schur_apply_static", "dd_probe", "dd_get_state", "dd_set_state", "dd_profile",
+           "dd_factor", "dd_step", "dd_schur_apply", "dd_schur_apply_static", "dd_probe", "dd_adjoint_reset",
+           "dd_adjoint_step", "dd_probe_seed", "dd_get_state", "dd_set_state", "dd_profile",
            "dd_destroy", "dd_last_error"]
 N_STAGES = 9
 STAGES = ["rhs", "local_solve", "iface_apply", "coarse", "corner", "recover", "vector", "refine", "factor"]
@@ -78,6 +79,9 @@ def load_library(path: str = LIB_PATH):
         "dd_get_state": (C.c_int, [vp, vp, vp, C.POINTER(i64), vp]),
         "dd_set_state": (C.c_int, [vp, vp, vp, i64, vp]),
         "dd_profile": (C.c_int, [vp, C.c_int, C.POINTER(dd_profile_stats), vp]),
+        "dd_adjoint_reset": (C.c_int, [vp, vp]),
+        "dd_adjoint_step": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp, C.POINTER(dd_stats), vp]),
+        "dd_probe_seed": (C.c_int, [vp, vp, C.c_double, vp, vp]),
         "dd_destroy": (None, [vp]),
         "dd_last_error": (C.c_char_p, [vp]),
     }
@@ -211,6 +215,23 @@ def dd_set_state(h, e_n, e_nm1, step, stream=None):
     _check(h, lib().dd_set_state(h, _ptr(e_n), _ptr(e_nm1), int(step), _stream(stream)))
 
 
+def dd_adjoint_reset(h, stream=None):
+    _check(h, lib().dd_adjoint_reset(h, _stream(stream)))
+
+
+def dd_adjoint_step(h, seed, e_k=None, e_km1=None, e_km2=None, d2g_hat=None, grad_eps=None, grad_amp=None,
+                    mu_out=None, stats=True, stream=None):
+    st = dd_stats()
+    rc = lib().dd_adjoint_step(h, _ptr(seed), _ptr(e_k), _ptr(e_km1), _ptr(e_km2), _ptr(d2g_hat), _ptr(grad_eps),
+                               _ptr(grad_amp), _ptr(mu_out), C.byref(st) if stats else None, _stream(stream))
+    _check(h, rc)
+    return dict(rc=rc, iters=st.iters, refinements=st.refinements, resid=st.resid, status=st.status)
+
+
+def dd_probe_seed(h, e, weight, seed, stream=None):
+    _check(h, lib().dd_probe_seed(h, _ptr(e), float(weight), _ptr(seed), _stream(stream)))
+
+
 def dd_profile(h, enable=-1, read=True, stream=None):
     """enable: 1 reset+start, 0 stop, -1 unchanged.  Returns per-stage dict when read."""
     st = dd_profile_stats()
@@ -234,6 +255,7 @@ class FieldSolver:
 
     def __init__(self, xyz, tets, part, n_sub, eps=None, mu=1.0, params=None, probes=None, device="cuda"):
         self.h = dd_setup(xyz, tets, part, n_sub, eps, mu, params)
+        self.n_tets = len(tets)
         self.sizes = dd_get_sizes(self.h)
         self.n_dof = self.sizes.n_dof
         self.n_lambda = self.sizes.n_lambda
