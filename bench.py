@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--only", choices=["fp64", "mixed"], default=None, help="time one precision only")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-profile", action="store_true", help="skip the per-stage event-profiled pass")
+    ap.add_argument("--eager", action="store_true", help="time eager launches instead of the CUDA-graph step")
+    ap.add_argument("--chunk", type=int, default=2, help="CG iterations per graph WHILE-body launch")
     ap.add_argument("--cavity", type=int, nargs=2, metavar=("N", "K"), default=None,
                     help="profiling case: unit PEC cavity of N^3 cubes in K^3 subdomains instead of --config "
                          "(dt = the 48^3 cavity's dt scaled by 48/N)")
@@ -254,8 +256,14 @@ def run_ours(args, rank, world, local):
         return ms, np.array(its), np.array(refs), prof, e_last.clone()
 
     clocks = Clocks(local)
-    p64 = D.make_params(precision=D.DD_FP64, tol=args.tol64)
-    p32 = D.make_params(precision=D.DD_MIXED, tol=args.tol32, refine_tol=args.refine_tol, max_refine=6)
+    g = 0 if args.eager else 1
+    ch = 8 if args.eager else args.chunk
+    p64 = D.make_params(precision=D.DD_FP64, tol=args.tol64, use_graph=g, chunk=ch)
+    p32 = D.make_params(precision=D.DD_MIXED, tol=args.tol32, refine_tol=args.refine_tol, max_refine=6, use_graph=g,
+                        chunk=ch)
+    # event profiling needs eager launches (events are recorded around every launch)
+    p64e = D.make_params(precision=D.DD_FP64, tol=args.tol64)
+    p32e = D.make_params(precision=D.DD_MIXED, tol=args.tol32, refine_tol=args.refine_tol, max_refine=6)
     nan = float("nan")
     ms64 = ms32 = nan
     it64 = it32 = ref32 = np.zeros(1)
@@ -268,11 +276,13 @@ def run_ours(args, rank, world, local):
         ms32, it32, ref32, prof32, e32 = run_steps(p32, False, clocks)
     rel = float(torch.linalg.norm(e32 - e64) / torch.linalg.norm(e64)) if e32 is not None and e64 is not None else nan
     # per-stage breakdown: a second pass over the same steps with CUDA events around every launch
+    launches64 = prof64["total_launches"] if prof64 else None
+    launches32 = prof32["total_launches"] if prof32 else None
     if not args.no_profile:
         if args.only in (None, "fp64"):
-            prof64 = run_steps(p64, True)[3]
+            prof64 = run_steps(p64e, True)[3]
         if args.only in (None, "mixed"):
-            prof32 = run_steps(p32, True)[3]
+            prof32 = run_steps(p32e, True)[3]
 
     # end-to-end: per step, H2D of the source from pinned host memory, the C-ABI step, D2H of e^{n+1}
     ms_e2e = nan
@@ -308,7 +318,7 @@ def run_ours(args, rank, world, local):
     ms64, ms32, ms_e2e = allmax(ms64), allmax(ms32), allmax(ms_e2e)
     sizes = fs.sizes
     res = dict(fs=fs, K=K, ms64=ms64, ms32=ms32, ms_e2e=ms_e2e, it64=it64, it32=it32, ref32=ref32, prof64=prof64,
-               prof32=prof32, rel=rel, t_setup=t_setup, t_factor=t_factor, clocks=clocks.summary(), sizes=sizes,
+               prof32=prof32, rel=rel, launches64=launches64, launches32=launches32, t_setup=t_setup, t_factor=t_factor, clocks=clocks.summary(), sizes=sizes,
                workload=w, dt=dt)
     return res
 
@@ -430,7 +440,8 @@ def main():
                                 f"{sizes.n_corner} corners, Gaussian z-line pulse, dt=2xCFL={r['dt']:.6g}"),
                    "l2_policy": "inputs larger than L2 (dense subdomain operators "
                                 f"{sizes.dense_bytes_fp64 / 1e9:.1f} GB FP64 + half that FP32), no flush",
-                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                   "stage_profile": "separate eager pass over the same steps with CUDA events per launch"},
         "mixed": {"steps_per_s": v32, "ms_per_step": r["ms32"] / K, "iters_per_step": float(np.mean(r["it32"])),
                   "refinements_per_step": float(np.mean(r["ref32"])), "inner_tol": args.tol32,
                   "refine_tol": args.refine_tol, "stages": st32},
@@ -446,7 +457,8 @@ def main():
         "cpu_baseline": cb,
         "e2e": {"value": world * K / (r["ms_e2e"] / 1e3), "unit": "steps/s",
                 "h2d_bytes_per_step": int(sizes.n_dof * 8), "d2h_bytes_per_step": int(sizes.n_dof * 8)},
-        "gpu_launches": int(prof_head["total_launches"]) if prof_head else None,
+        "gpu_launches": int(r["launches32"] if head == "mixed" else r["launches64"]),
+        "launch_mode": "eager" if args.eager else f"CUDA graph per step (CG WHILE node, {args.chunk} it/body)",
         "clocks": r["clocks"],
     }
     print(json.dumps(_clean(line)), flush=True)

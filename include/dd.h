@@ -85,7 +85,15 @@ typedef struct {
  * refine_tol DD_MIXED only: stop refining a step when the FP64 residual of the
  *            step's linear system satisfies ||r||_2 <= refine_tol * ||b||_2.
  * max_refine DD_MIXED only: cap on FP32 correction solves per step.
- * chunk      CG iterations issued between two convergence checks. */
+ * chunk      CG iterations issued between two convergence checks (host
+ *            polls in eager mode; iterations per WHILE-body launch in graph mode).
+ * use_graph  1 = dd_step runs as a CUDA graph captured once per time-level
+ *            phase (rebuilt after dd_factor / dd_set_params): the CG loop is a
+ *            conditional WHILE node whose condition the CG kernels set, and
+ *            every further mixed-precision refinement pass is a conditional IF
+ *            node, so a step needs no host round trip unless stats are
+ *            requested.  The step's source is copied into the workspace before
+ *            each launch.  0 = eager launches with host convergence polling. */
 typedef struct {
     int precision;
     double tol;
@@ -95,6 +103,7 @@ typedef struct {
     double refine_tol;
     int max_refine;
     int chunk;
+    int use_graph;
 } dd_params;
 
 /* Sizes of a set-up problem. */
@@ -155,7 +164,7 @@ typedef struct {
  * matrices, multiplicities, local numbering, B_r / B_c, local CSR matrices.
  * part [n_tets] (host) gives the subdomain 0..n_sub-1 of every tet.
  * params may be NULL (defaults: FP64, tol 1e-12, max_it 500, Jacobi, warm
- * start, refine_tol 1e-12, max_refine 4, chunk 8).  On success *out owns a new
+ * start, refine_tol 1e-12, max_refine 4, chunk 8, eager launches).  On success *out owns a new
  * handle (free with dd_destroy).  Errors: DD_ERR_ARG, DD_ERR_MESH,
  * DD_ERR_PARTITION.  No GPU work is done. */
 int dd_setup(const dd_mesh* mesh, const int32_t* part, int32_t n_sub, const dd_params* params,

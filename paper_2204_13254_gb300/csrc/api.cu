@@ -16,6 +16,14 @@ int cuda_fail(dd_handle* h, int code, const char* what) {
     return DD_ERR_CUDA;
 }
 
+void drop_graphs(dd_handle* h) {
+    for (int k = 0; k < 3; ++k)
+        if (h->gexec[k]) {
+            cudaGraphExecDestroy((cudaGraphExec_t)h->gexec[k]);
+            h->gexec[k] = nullptr;
+        }
+}
+
 #define CK(h, expr, what)                                     \
     do {                                                      \
         int rc_ = (expr);                                     \
@@ -32,6 +40,7 @@ dd_params default_params() {
     p.refine_tol = 1e-12;
     p.max_refine = 4;
     p.chunk = 8;
+    p.use_graph = 0;
     return p;
 }
 
@@ -212,6 +221,7 @@ size_t dd_workspace_layout(dd_handle* h, bool assign) {
     L.take(d.xC, nc);
     L.take(d.delta, nd);
     L.take(d.delta_k, nd);
+    L.take(d.src_in, nd);
     L.take(d.sc, 1);
     L.take(d.partials, 3 * kMaxPartials);
     L.take(d.status, 4);
@@ -326,7 +336,46 @@ void count_cg_work(dd_handle* h, int prec, int n) {
 // (subassembled; DD_MIXED also needs the FP32 shadow d.bf), leaving x in d.x
 // (r slots) and x_c in d.xC.  Returns a DD status; iteration count and the
 // final relative interface residual in *it_out / *res_out.
-int dd_solve(dd_handle* h, int prec, double tol, bool warm, int* it_out, double* res_out, cudaStream_t s) {
+// Graph capture helpers: add a conditional node at the current end of stream s's
+// capture and return its body graph; later work captured on s depends on it.
+int add_conditional(dd_handle* h, cudaStream_t s, cudaGraphConditionalHandle hc, cudaGraphConditionalNodeType type,
+                    cudaGraph_t* body) {
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    CK(h, (int)cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &nd), "capture info");
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = hc;
+    p.conditional.type = type;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(h, (int)cudaGraphAddNode(&node, g, deps, nullptr, nd, &p), "add conditional node");
+    *body = p.conditional.phGraph_out[0];
+    CK(h, (int)cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies), "deps");
+    return DD_OK;
+}
+
+int create_handle(dd_handle* h, cudaStream_t s, cudaGraphConditionalHandle* hc) {
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g;
+    CK(h, (int)cudaStreamGetCaptureInfo(s, &st, nullptr, &g, nullptr, nullptr, nullptr), "capture info");
+    CK(h, (int)cudaGraphConditionalHandleCreate(hc, g, 0, cudaGraphCondAssignDefault), "conditional handle");
+    return DD_OK;
+}
+
+cudaStream_t capture_stream(dd_handle* h, int depth) {
+    if (!h->gstream[depth]) {
+        cudaStream_t cs;
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+        h->gstream[depth] = (void*)cs;
+    }
+    return (cudaStream_t)h->gstream[depth];
+}
+
+int dd_solve(dd_handle* h, int prec, double tol, bool warm, int* it_out, double* res_out, cudaStream_t s,
+             int adaptive = 0, int depth = 0) {
     const bool has_c = !h->corner_dof.empty();
     const bool has_l = !h->mult_dof.empty();
     const Vecs V = vecs(h, prec);
@@ -363,16 +412,56 @@ int dd_solve(dd_handle* h, int prec, double tol, bool warm, int* it_out, double*
     int iters = 0;
     double res = 0.0;
     if (has_l) {
-        const bool use_warm = warm && h->lam_valid;
+        // a captured graph always takes the warm start; dd_step zeroes lambda before
+        // launching it when the multipliers are not valid (same values as a cold start)
+        const bool use_warm = warm && (h->lam_valid || h->capturing);
         if (use_warm) {
             CK(h, apply_schur_w(h, prec, X_LAMBDA, h->d.lam, nullptr, V.lamf, nullptr, false, s), "apply lambda0");
         } else {
             CK(h, (int)cudaMemsetAsync(h->d.lam, 0, nlb, s), "memset");
             CK(h, (int)cudaMemsetAsync(h->d.lamf, 0, sizeof(float) * h->mult_dof.size(), s), "memset");
         }
+        if (h->capturing) {
+            // CG loop as a conditional WHILE node; the CG kernels set its condition
+            cudaGraphConditionalHandle hc;
+            int rc = create_handle(h, s, &hc);
+            if (rc) return rc;
+            {
+                Prof P(h, ST_VEC, s, 1);
+                CK(h, launch_pcg_init(h, use_warm ? 1 : 0, tol, V.wf, V.zf, V.pf, (unsigned long long)hc, adaptive, s),
+                   "pcg init");
+            }
+            cudaGraph_t body;
+            rc = add_conditional(h, s, hc, cudaGraphCondTypeWhile, &body);
+            if (rc) return rc;
+            cudaStream_t bs = capture_stream(h, depth + 1);
+            if (!bs) return h->fail(DD_ERR_CUDA, "capture stream");
+            CK(h, (int)cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed),
+               "capture body");
+            const int64_t l0 = h->total_launches;
+            int brc = DD_OK;
+            for (int k = 0; k < h->prm.chunk && brc == DD_OK; ++k) {
+                brc = apply_schur_w(h, prec, X_PCG, h->d.z, h->d.p, V.zf, V.pf, true, bs);
+                if (brc) break;
+                Prof P(h, ST_VEC, bs, 2);
+                brc = launch_pcg_alpha(h, V.wf, V.pf, bs);
+                if (!brc) brc = launch_pcg_update(h, V.zf, V.lamf, (unsigned long long)hc, bs);
+            }
+            cudaGraph_t out_body;
+            const int erc = (int)cudaStreamEndCapture(bs, &out_body);
+            if (brc) return brc > 0 && brc < 100 ? brc : cuda_fail(h, brc, "capture body");
+            CK(h, erc, "end body capture");
+            h->g_kernels_iter = (h->total_launches - l0) / std::max(1, h->prm.chunk);
+            h->total_launches = l0;
+            {
+                Prof P(h, ST_VEC, s, 1);
+                CK(h, launch_solve_end(h, s), "solve end");
+            }
+            h->lam_valid = true;
+        } else {
         {
             Prof P(h, ST_VEC, s, 1);
-            CK(h, launch_pcg_init(h, use_warm ? 1 : 0, tol, V.wf, V.zf, V.pf, s), "pcg init");
+            CK(h, launch_pcg_init(h, use_warm ? 1 : 0, tol, V.wf, V.zf, V.pf, 0ull, 0, s), "pcg init");
         }
         PcgScalars hs;
         CK(h, read_scalars(h, &hs, s), "pcg scalars");
@@ -382,7 +471,7 @@ int dd_solve(dd_handle* h, int prec, double tol, bool warm, int* it_out, double*
                 CK(h, apply_schur_w(h, prec, X_PCG, h->d.z, h->d.p, V.zf, V.pf, true, s), "apply");
                 Prof P(h, ST_VEC, s, 2);
                 CK(h, launch_pcg_alpha(h, V.wf, V.pf, s), "pcg alpha");
-                CK(h, launch_pcg_update(h, V.zf, V.lamf, s), "pcg update");
+                CK(h, launch_pcg_update(h, V.zf, V.lamf, 0ull, s), "pcg update");
             }
             CK(h, read_scalars(h, &hs, s), "pcg scalars");
         }
@@ -392,6 +481,7 @@ int dd_solve(dd_handle* h, int prec, double tol, bool warm, int* it_out, double*
         if (hs.status != DD_OK) status = hs.status;
         else if (!hs.done) status = DD_ERR_NO_CONVERGENCE;
         h->lam_valid = true;
+        }
     }
     // x_c = K~cc^-1 (f~_c + F_rc^T lambda)                           Eq. F1uc
     if (has_c) {
@@ -451,7 +541,9 @@ int dd_set_params(dd_handle* h, const dd_params* params) {
     if (!h || !params) return DD_ERR_ARG;
     int rc = check_params(h, *params);
     if (rc) return rc;
+    if (h->capturing) return h->fail(DD_ERR_STATE, "dd_set_params during capture");
     h->prm = *params;
+    drop_graphs(h);
     return DD_OK;
 }
 
@@ -508,6 +600,7 @@ int dd_bind_workspace(dd_handle* h, void* dev, size_t bytes, void* stream) {
     if ((reinterpret_cast<uintptr_t>(dev) & 255) != 0) return h->fail(DD_ERR_ARG, "workspace must be 256-byte aligned");
     const size_t need = dd_workspace_layout(h, false);
     if (bytes < need) return h->fail(DD_ERR_ARG, "workspace too small: need " + std::to_string(need) + " bytes");
+    drop_graphs(h);
     h->ws = static_cast<char*>(dev);
     h->ws_bytes = bytes;
     dd_workspace_layout(h, true);
@@ -561,6 +654,7 @@ int dd_factor(dd_handle* h, double dt, void* stream) {
     if (!(dt > 0.0) || !std::isfinite(dt)) return h->fail(DD_ERR_ARG, "dt must be positive");
     cudaStream_t s = (cudaStream_t)stream;
     h->factored = false;
+    drop_graphs(h);
     CK(h, (int)cudaMemsetAsync(h->d.status, 0, 4, s), "memset");
     {
         Prof P(h, ST_FACTOR, s, 2);
@@ -686,6 +780,199 @@ int advance(dd_handle* h, const double* u_n, const double* u_nm1, double* u_np1,
     return status;
 }
 
+// ---- graph mode ---------------------------------------------------------------
+
+// Mixed-precision refinement passes k >= 2 as nested conditional IF nodes:
+// the condition of each pass is set by the residual kernel at the end of the
+// previous pass (it defaults to 0 at every launch).
+int refine_chain(dd_handle* h, int k, int depth, cudaStream_t s, const double* u_n, const double* u_nm1) {
+    cudaGraphConditionalHandle hc;
+    int rc = create_handle(h, s, &hc);
+    if (rc) return rc;
+    {
+        Prof P(h, ST_VEC, s, 1);
+        CK(h, launch_refine_cond(h, (unsigned long long)hc, s), "refine cond");
+    }
+    cudaGraph_t body;
+    rc = add_conditional(h, s, hc, cudaGraphCondTypeIf, &body);
+    if (rc) return rc;
+    cudaStream_t bs = capture_stream(h, depth + 1);
+    if (!bs) return h->fail(DD_ERR_CUDA, "capture stream");
+    CK(h, (int)cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed), "capture if");
+    const int64_t l0 = h->total_launches;
+    int brc = DD_OK;
+    {
+        const size_t nm = h->mult_dof.size();
+        if (nm) {  // later passes start cold, as in eager mode
+            brc = (int)cudaMemsetAsync(h->d.lam, 0, sizeof(double) * nm, bs);
+            if (!brc) brc = (int)cudaMemsetAsync(h->d.lamf, 0, sizeof(float) * nm, bs);
+            if (brc) brc = cuda_fail(h, brc, "memset");
+        }
+        int it = 0;
+        double r = 0.0;
+        if (!brc) brc = dd_solve(h, DD_MIXED, h->prm.tol, false, &it, &r, bs, 1, depth + 1);
+        if (!brc) {
+            Prof P(h, ST_VEC, bs, 1);
+            brc = launch_writeback(h, u_n, u_nm1, h->d.delta_k, h->d.delta, 0, nullptr, bs);
+            if (brc) brc = cuda_fail(h, brc, "writeback");
+        }
+        if (!brc) {
+            Prof P(h, ST_REFINE, bs, 2, h->bytes_per_launch[ST_REFINE]);
+            brc = launch_residual_local(h, bs);
+            if (!brc) brc = launch_assembled_norm(h, 0, h->d.bf, bs);
+            if (brc) brc = cuda_fail(h, brc, "residual");
+        }
+        if (!brc && k + 1 < h->prm.max_refine) brc = refine_chain(h, k + 1, depth + 1, bs, u_n, u_nm1);
+    }
+    cudaGraph_t out_body;
+    const int erc = (int)cudaStreamEndCapture(bs, &out_body);
+    if (brc) return brc;
+    CK(h, erc, "end if capture");
+    if (k == 1) h->g_kernels_pass = h->total_launches - l0;
+    h->total_launches = l0;
+    return DD_OK;
+}
+
+// The whole step from (u_n, u_nm1) into u_np1, captured on stream s; the source is d.src_in.
+int step_body_graph(dd_handle* h, const double* u_n, const double* u_nm1, double* u_np1, cudaStream_t s) {
+    {
+        Prof P(h, ST_VEC, s, 1);
+        CK(h, launch_step_begin(h, s), "step begin");
+    }
+    {
+        Prof P(h, ST_RHS, s, 1, h->bytes_per_launch[ST_RHS]);
+        CK(h, launch_rhs(h, u_n, h->d.src_in, -1.0, h->dt, s), "rhs");
+    }
+    int it = 0;
+    double r = 0.0;
+    if (h->prm.precision == DD_FP64) {
+        int rc = dd_solve(h, DD_FP64, h->prm.tol, h->prm.warm_start != 0, &it, &r, s, 0, 0);
+        if (rc) return rc;
+        Prof P(h, ST_VEC, s, 1);
+        CK(h, launch_writeback(h, u_n, u_nm1, nullptr, nullptr, 1, u_np1, s), "writeback");
+        return DD_OK;
+    }
+    {
+        Prof P(h, ST_REFINE, s, 1);
+        CK(h, launch_assembled_norm(h, 1, h->d.bf, s), "norm b");
+    }
+    int rc = dd_solve(h, DD_MIXED, h->prm.tol, h->prm.warm_start != 0, &it, &r, s, 0, 0);
+    if (rc) return rc;
+    {
+        Prof P(h, ST_VEC, s, 1);
+        CK(h, launch_writeback(h, u_n, u_nm1, h->d.delta_k, h->d.delta, 1, nullptr, s), "writeback");
+    }
+    {
+        Prof P(h, ST_REFINE, s, 2, h->bytes_per_launch[ST_REFINE]);
+        CK(h, launch_residual_local(h, s), "residual");
+        CK(h, launch_assembled_norm(h, 0, h->d.bf, s), "norm r");
+    }
+    const size_t nm = h->mult_dof.size();
+    if (nm) {  // keep the first pass's multipliers as the next step's warm start
+        CK(h, (int)cudaMemcpyAsync(h->d.lam_scratch, h->d.lam, sizeof(double) * nm, cudaMemcpyDeviceToDevice, s), "save");
+        CK(h, (int)cudaMemcpyAsync(h->d.lamf_scratch, h->d.lamf, sizeof(float) * nm, cudaMemcpyDeviceToDevice, s), "save");
+    }
+    if (h->prm.max_refine > 1) {
+        rc = refine_chain(h, 1, 0, s, u_n, u_nm1);
+        if (rc) return rc;
+    }
+    {
+        Prof P(h, ST_VEC, s, 1);
+        CK(h, launch_refine_cond(h, 0ull, s), "refine final");
+    }
+    if (nm) {
+        CK(h, (int)cudaMemcpyAsync(h->d.lam, h->d.lam_scratch, sizeof(double) * nm, cudaMemcpyDeviceToDevice, s), "restore");
+        CK(h, (int)cudaMemcpyAsync(h->d.lamf, h->d.lamf_scratch, sizeof(float) * nm, cudaMemcpyDeviceToDevice, s), "restore");
+    }
+    Prof P(h, ST_VEC, s, 1);
+    CK(h, launch_advance(h, u_n, u_nm1, h->d.delta, u_np1, s), "advance");
+    return DD_OK;
+}
+
+// Capture the step of time-level phase `phase` (e[phase] = e^n) into h->gexec[phase].
+int capture_step(dd_handle* h, int phase) {
+    cudaStream_t cs = capture_stream(h, 0);
+    if (!cs) return h->fail(DD_ERR_CUDA, "capture stream");
+    const bool prof_saved = h->prof_on;
+    const int64_t l0 = h->total_launches;
+    int64_t lk[DD_N_STAGES], wk[DD_N_STAGES];
+    double bk[DD_N_STAGES];
+    for (int k = 0; k < DD_N_STAGES; ++k) {
+        lk[k] = h->launches[k];
+        wk[k] = h->work[k];
+        bk[k] = h->work_bytes[k];
+    }
+    h->prof_on = false;
+    h->capturing = true;
+    const bool lam_valid = h->lam_valid;
+    int rc = (int)cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+    if (rc) {
+        h->capturing = false;
+        h->prof_on = prof_saved;
+        return cuda_fail(h, rc, "begin capture");
+    }
+    rc = step_body_graph(h, h->d.e[phase], h->d.e[(phase + 2) % 3], h->d.e[(phase + 1) % 3], cs);
+    cudaGraph_t g = nullptr;
+    const int erc = (int)cudaStreamEndCapture(cs, &g);
+    h->capturing = false;
+    h->prof_on = prof_saved;
+    h->lam_valid = lam_valid;
+    h->g_kernels_main = h->total_launches - l0;
+    h->total_launches = l0;
+    for (int k = 0; k < DD_N_STAGES; ++k) {  // capture is not execution
+        h->launches[k] = lk[k];
+        h->work[k] = wk[k];
+        h->work_bytes[k] = bk[k];
+    }
+    if (rc || erc) {
+        if (g) cudaGraphDestroy(g);
+        return rc ? rc : cuda_fail(h, erc, "end capture");
+    }
+    cudaGraphExec_t ex;
+    rc = (int)cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (rc) return cuda_fail(h, rc, "graph instantiate");
+    h->gexec[phase] = (void*)ex;
+    return DD_OK;
+}
+
+int dd_step_graph(dd_handle* h, const double* d2g, double* e_out, dd_stats* stats, cudaStream_t s) {
+    const int phase = h->cur;
+    if (!h->gexec[phase]) {
+        int rc = capture_step(h, phase);
+        if (rc) return rc;
+    }
+    const size_t nb = sizeof(double) * h->n_dof;
+    if (d2g) CK(h, (int)cudaMemcpyAsync(h->d.src_in, d2g, nb, cudaMemcpyDeviceToDevice, s), "source copy");
+    else CK(h, (int)cudaMemsetAsync(h->d.src_in, 0, nb, s), "source clear");
+    if (!h->lam_valid && !h->mult_dof.empty()) {
+        CK(h, (int)cudaMemsetAsync(h->d.lam, 0, sizeof(double) * h->mult_dof.size(), s), "memset");
+        CK(h, (int)cudaMemsetAsync(h->d.lamf, 0, sizeof(float) * h->mult_dof.size(), s), "memset");
+    }
+    CK(h, (int)cudaGraphLaunch((cudaGraphExec_t)h->gexec[phase], s), "graph launch");
+    h->lam_valid = true;
+    double* e_np1 = h->d.e[(phase + 1) % 3];
+    h->cur = (phase + 1) % 3;
+    h->step += 1;
+    if (e_out) CK(h, (int)cudaMemcpyAsync(e_out, e_np1, nb, cudaMemcpyDeviceToDevice, s), "e_out");
+    int status = DD_OK;
+    if (stats) {
+        PcgScalars hs;
+        CK(h, read_scalars(h, &hs, s), "scalars");
+        stats->iters = hs.it_total;
+        stats->refinements = h->prm.precision == DD_MIXED ? hs.refinements : 0;
+        stats->resid = h->prm.precision == DD_MIXED ? (hs.norm_b2 > 0 ? std::sqrt(hs.norm_r2 / hs.norm_b2) : 0.0)
+                                                     : (hs.gg > 0 ? std::sqrt(hs.rr / hs.gg) : 0.0);
+        status = hs.step_status;
+        stats->status = status;
+        h->total_launches += h->g_kernels_main + h->g_kernels_iter * (int64_t)hs.it_total +
+                             h->g_kernels_pass * (int64_t)std::max(0, hs.refinements - 1);
+        if (status == DD_ERR_NO_CONVERGENCE) h->err = "interface CG or refinement did not converge";
+        if (status == DD_ERR_NONFINITE) h->err = "non-finite residual";
+    }
+    return status;
+}
+
 // Swap the interface multipliers (warm start) between the forward and the
 // adjoint march, which share the factors but not their CG history.
 void swap_lambda(dd_handle* h) {
@@ -700,6 +987,7 @@ int dd_step(dd_handle* h, const double* d2g, double* e_out, dd_stats* stats, voi
     if (!h) return DD_ERR_ARG;
     if (!h->factored) return h->fail(DD_ERR_STATE, "dd_step before dd_factor");
     cudaStream_t s = (cudaStream_t)stream;
+    if (h->prm.use_graph) return dd_step_graph(h, d2g, e_out, stats, s);
     const double* e_n = h->d.e[h->cur];
     const double* e_nm1 = h->d.e[(h->cur + 2) % 3];
     double* e_np1 = h->d.e[(h->cur + 1) % 3];
@@ -857,6 +1145,9 @@ int dd_profile(dd_handle* h, int enable, dd_profile_stats* out, void* stream) {
 
 void dd_destroy(dd_handle* h) {
     if (!h) return;
+    drop_graphs(h);
+    for (void* st : h->gstream)
+        if (st) cudaStreamDestroy((cudaStream_t)st);
     for (void* e : h->ev_pool) cudaEventDestroy((cudaEvent_t)e);
     delete h;
 }

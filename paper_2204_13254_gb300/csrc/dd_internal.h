@@ -83,6 +83,10 @@ struct PcgScalars {
     int32_t pad;
     double norm_b2;   // mixed mode: ||b||^2 of the step system
     double norm_r2;   // mixed mode: ||r||^2 of the current FP64 residual
+    int32_t it_total;     // graph mode: CG iterations of the whole step
+    int32_t refinements;  // graph mode: solves of the whole step
+    int32_t step_status;  // graph mode: DD status of the whole step
+    int32_t pad2;
     uint32_t counter[8];  // last-block counters of the grid reductions
 };
 
@@ -155,6 +159,7 @@ struct DevPtrs {
     // global vectors (n_dof)
     double* delta = nullptr;         // assembled correction of the step
     double* delta_k = nullptr;       // assembled correction of one refinement
+    double* src_in = nullptr;        // graph mode: the step's source, copied in before each launch
     double* res = nullptr;           // assembled FP64 residual
     // scalars
     PcgScalars* sc = nullptr;
@@ -224,6 +229,14 @@ struct dd_handle {
     bool lam_valid = false;
     bool lam_adj_valid = false;
 
+    // CUDA-graph mode (dd_params.use_graph): one executable graph per time-level phase
+    void* gexec[3] = {nullptr, nullptr, nullptr};   // cudaGraphExec_t
+    void* gstream[8] = {};                          // private capture streams, one per nesting depth
+    bool capturing = false;
+    int64_t g_kernels_main = 0;      // kernels outside conditional bodies
+    int64_t g_kernels_iter = 0;      // kernels per CG iteration (WHILE body)
+    int64_t g_kernels_pass = 0;      // kernels per extra refinement pass outside its WHILE body
+
     // profiling (dd_profile)
     bool prof_on = false;
     std::vector<void*> ev_pool;            // cudaEvent_t
@@ -272,9 +285,13 @@ int launch_corner_gather(const dd_handle* h, const double* w, const float* wf, c
                          bool check_done, void* stream);
 int launch_jump(const dd_handle* h, const double* w, const float* wf, const double* base, double sign, double* out,
                 void* stream);
-int launch_pcg_init(const dd_handle* h, int have_q, double tol, const float* wf, float* zf, float* pf, void* stream);
+int launch_pcg_init(const dd_handle* h, int have_q, double tol, const float* wf, float* zf, float* pf,
+                    unsigned long long cond, int adaptive, void* stream);
+int launch_step_begin(const dd_handle* h, void* stream);
+int launch_solve_end(const dd_handle* h, void* stream);
+int launch_refine_cond(const dd_handle* h, unsigned long long cond, void* stream);
 int launch_pcg_alpha(const dd_handle* h, const float* wf, float* pf, void* stream);
-int launch_pcg_update(const dd_handle* h, float* zf, float* lamf, void* stream);
+int launch_pcg_update(const dd_handle* h, float* zf, float* lamf, unsigned long long cond, void* stream);
 int launch_writeback(const dd_handle* h, const double* e_n, const double* e_nm1, double* delta_k, double* delta_acc,
                      int first, double* e_np1, void* stream);
 int launch_advance(const dd_handle* h, const double* e_n, const double* e_nm1, const double* delta, double* e_np1,

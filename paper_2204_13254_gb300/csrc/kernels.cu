@@ -645,7 +645,8 @@ __global__ void __launch_bounds__(kThreads) k_pcg_init(int64_t n_lambda, const i
                                                        double* __restrict__ r, double* __restrict__ z,
                                                        double* __restrict__ p, float* __restrict__ zf,
                                                        float* __restrict__ pf, PcgScalars* sc,
-                                                       double* __restrict__ partials) {
+                                                       double* __restrict__ partials, unsigned long long cond,
+                                                       int adaptive, double refine_tol) {
     double v[3] = {0.0, 0.0, 0.0};
     for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < n_lambda; m += (int64_t)gridDim.x * blockDim.x) {
         const double q = have_q ? (wval(w, wf, mult_slot[2 * m]) - wval(w, wf, mult_slot[2 * m + 1])) : 0.0;
@@ -666,13 +667,19 @@ __global__ void __launch_bounds__(kThreads) k_pcg_init(int64_t n_lambda, const i
         sc->rz = v[0];
         sc->gg = v[1];
         sc->rr = v[2];
-        sc->tol2 = tol * tol * v[1];
+        double t = tol;
+        if (adaptive) {  // a later refinement pass only has to cut the current step residual to refine_tol
+            const double resid = sc->norm_b2 > 0.0 ? sqrt(sc->norm_r2 / sc->norm_b2) : 0.0;
+            if (resid > 0.0) t = fmin(0.1, fmax(tol, 0.3 * refine_tol / resid));
+        }
+        sc->tol2 = t * t * v[1];
         sc->beta = 0.0;
         sc->alpha = 0.0;
         sc->it = 0;
         const bool finite = isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]);
         sc->status = finite ? DD_OK : DD_ERR_NONFINITE;
         sc->done = (!finite || v[2] <= sc->tol2) ? 1 : 0;
+        if (cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, sc->done ? 0u : 1u);
     }
 }
 
@@ -705,7 +712,8 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(int64_t n_lambda, const
                                                          double* __restrict__ lam, double* __restrict__ r,
                                                          double* __restrict__ z, float* __restrict__ zf,
                                                          float* __restrict__ lamf, PcgScalars* sc,
-                                                         double* __restrict__ partials) {
+                                                         double* __restrict__ partials, unsigned long long cond,
+                                                         int max_it) {
     if (sc->done) return;
     const double alpha = sc->alpha;
     double v[2] = {0.0, 0.0};
@@ -735,6 +743,36 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(int64_t n_lambda, const
         }
         sc->beta = v[1] / sc->rz;
         sc->rz = v[1];
+        sc->it_total += 1;
+        if (cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, (!sc->done && sc->it < max_it) ? 1u : 0u);
+    }
+}
+
+// graph mode: per-step counters
+__global__ void k_step_begin(PcgScalars* sc) {
+    sc->it_total = 0;
+    sc->refinements = 0;
+    sc->step_status = DD_OK;
+}
+
+// graph mode: end of one DD solve (status of the CG loop)
+__global__ void k_solve_end(PcgScalars* sc) {
+    sc->refinements += 1;
+    if (sc->status != DD_OK) sc->step_status = sc->status;
+    else if (!sc->done && sc->step_status == DD_OK) sc->step_status = DD_ERR_NO_CONVERGENCE;
+}
+
+// graph mode: after an FP64 residual, run the next refinement pass (cond = 1) while
+// the relative step residual exceeds refine_tol; cond == 0 only records the outcome
+// of the last pass.
+__global__ void k_refine_cond(PcgScalars* sc, unsigned long long cond, double refine_tol) {
+    const double resid = sc->norm_b2 > 0.0 ? sqrt(sc->norm_r2 / sc->norm_b2) : 0.0;
+    const bool finite = isfinite(resid);
+    if (!finite) sc->step_status = DD_ERR_NONFINITE;
+    if (cond) {
+        cudaGraphSetConditional((cudaGraphConditionalHandle)cond, (finite && resid > refine_tol) ? 1u : 0u);
+    } else if (finite && resid > refine_tol && sc->step_status == DD_OK) {
+        sc->step_status = DD_ERR_NO_CONVERGENCE;
     }
 }
 
@@ -998,11 +1036,28 @@ int launch_jump(const dd_handle* h, const double* w, const float* wf, const doub
     return (int)cudaGetLastError();
 }
 
-int launch_pcg_init(const dd_handle* h, int have_q, double tol, const float* wf, float* zf, float* pf, void* stream) {
+int launch_pcg_init(const dd_handle* h, int have_q, double tol, const float* wf, float* zf, float* pf,
+                    unsigned long long cond, int adaptive, void* stream) {
     const int64_t nl = (int64_t)h->mult_dof.size();
     k_pcg_init<<<reduce_blocks(nl), kThreads, 0, S(stream)>>>(nl, h->d.mult_slot, h->d.w, wf, have_q, h->d.g,
                                                               h->prm.precond ? h->d.dinv : nullptr, tol, h->d.r, h->d.z,
-                                                              h->d.p, zf, pf, h->d.sc, h->d.partials);
+                                                              h->d.p, zf, pf, h->d.sc, h->d.partials, cond, adaptive,
+                                                              h->prm.refine_tol);
+    return (int)cudaGetLastError();
+}
+
+int launch_step_begin(const dd_handle* h, void* stream) {
+    k_step_begin<<<1, 1, 0, S(stream)>>>(h->d.sc);
+    return (int)cudaGetLastError();
+}
+
+int launch_solve_end(const dd_handle* h, void* stream) {
+    k_solve_end<<<1, 1, 0, S(stream)>>>(h->d.sc);
+    return (int)cudaGetLastError();
+}
+
+int launch_refine_cond(const dd_handle* h, unsigned long long cond, void* stream) {
+    k_refine_cond<<<1, 1, 0, S(stream)>>>(h->d.sc, cond, h->prm.refine_tol);
     return (int)cudaGetLastError();
 }
 
@@ -1013,11 +1068,11 @@ int launch_pcg_alpha(const dd_handle* h, const float* wf, float* pf, void* strea
     return (int)cudaGetLastError();
 }
 
-int launch_pcg_update(const dd_handle* h, float* zf, float* lamf, void* stream) {
+int launch_pcg_update(const dd_handle* h, float* zf, float* lamf, unsigned long long cond, void* stream) {
     const int64_t nl = (int64_t)h->mult_dof.size();
     k_pcg_update<<<reduce_blocks(nl), kThreads, 0, S(stream)>>>(nl, h->d.p, h->d.q, h->prm.precond ? h->d.dinv : nullptr,
                                                                 h->d.lam, h->d.r, h->d.z, zf, lamf, h->d.sc,
-                                                                h->d.partials);
+                                                                h->d.partials, cond, h->prm.max_it);
     return (int)cudaGetLastError();
 }
 
