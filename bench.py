@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-profile", action="store_true", help="skip the per-stage event-profiled pass")
     ap.add_argument("--eager", action="store_true", help="time eager launches instead of the CUDA-graph step")
     ap.add_argument("--chunk", type=int, default=2, help="CG iterations per graph WHILE-body launch")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default GEMV tiles")
     ap.add_argument("--cavity", type=int, nargs=2, metavar=("N", "K"), default=None,
                     help="profiling case: unit PEC cavity of N^3 cubes in K^3 subdomains instead of --config "
                          "(dt = the 48^3 cavity's dt scaled by 48/N)")
@@ -211,6 +212,10 @@ def run_ours(args, rank, world, local):
     fs.factor(dt)
     torch.cuda.synchronize()
     t_factor = time.perf_counter() - t0
+    t_tune, tiles = 0.0, None
+    if not args.no_autotune:
+        t_tune = D.dd_autotune(fs.h, None)
+        tiles = D.dd_get_tiles(fs.h)
     n = fs.n_dof
     dofs = torch.tensor(fs.dof_of_pairs(w.source_pairs), device=dev)
     d2g = w.d2G(dt, Wu + K)
@@ -319,7 +324,7 @@ def run_ours(args, rank, world, local):
     sizes = fs.sizes
     res = dict(fs=fs, K=K, ms64=ms64, ms32=ms32, ms_e2e=ms_e2e, it64=it64, it32=it32, ref32=ref32, prof64=prof64,
                prof32=prof32, rel=rel, launches64=launches64, launches32=launches32, t_setup=t_setup, t_factor=t_factor, clocks=clocks.summary(), sizes=sizes,
-               workload=w, dt=dt)
+               workload=w, dt=dt, t_tune=t_tune, tiles=tiles)
     return res
 
 
@@ -449,7 +454,8 @@ def main():
                  "tol": args.tol64, "stages": st64},
         "speedup_mixed_vs_fp64": v32 / v64,
         "rel_err_mixed_vs_fp64": r["rel"],
-        "setup_s": r["t_setup"], "factor_s": r["t_factor"],
+        "setup_s": r["t_setup"], "factor_s": r["t_factor"], "autotune_s": r["t_tune"],
+        "gemv_tiles": r["tiles"],
         "roofline": {"bound": "hbm", "kernel": f"k_gemv<{'float' if head == 'mixed' else 'double'}> ({dom})",
                      "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,

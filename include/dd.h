@@ -294,6 +294,24 @@ typedef struct {
  * while enabled. */
 int dd_profile(dd_handle* h, int enable, dd_profile_stats* out, void* stream);
 
+/* Tile autotuner for the batched subdomain GEMVs (the per-step hot kernels).
+ * For each GEMV kind (local solve, corner rows, corner coupling, recovery,
+ * coarse, interface rows) and each precision it times every candidate tile --
+ * lanes per matrix row in {8, 16, 32} x rows per CTA in {8, 16, 32, 64, 128} --
+ * on the factored operators with CUDA events (1 warm-up + 3 timed launches)
+ * and keeps the fastest.  cache_path (host string, may be NULL): a text file of
+ * "key precision kind lanes rows" lines keyed by device name and problem sizes;
+ * a complete entry is reused without timing, new results are appended.
+ * Requires dd_factor; results are bitwise unaffected only up to the order of
+ * floating-point sums inside a row (lanes per row changes it).  seconds (host,
+ * may be NULL) receives the wall time.  Synchronises `stream`. */
+int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* stream);
+
+/* Current tiles: lpr[p*6 + k], rows[p*6 + k] for precision p (0 FP64, 1 FP32)
+ * and GEMV kind k (0 local, 1 corner rows, 2 corner coupling, 3 recovery,
+ * 4 coarse, 5 interface rows); host int32[12] each. */
+int dd_get_tiles(const dd_handle* h, int32_t* lpr, int32_t* rows);
+
 void dd_destroy(dd_handle* h);
 const char* dd_last_error(const dd_handle* h);
 

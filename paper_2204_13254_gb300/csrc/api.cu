@@ -5,7 +5,11 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <chrono>
+#include <fstream>
+#include <map>
 #include <new>
+#include <sstream>
 
 #include "dd_internal.h"
 
@@ -146,6 +150,15 @@ struct Layout {
     }
 };
 
+// Task lists must fit the capacity reserved in the workspace layout.
+int upload_tasks(dd_handle* h, int p, int m, cudaStream_t s) {
+    if (h->tasks[p][m].size() > h->task_cap[m]) return h->fail(DD_ERR_STATE, "GEMV task list exceeds its capacity");
+    if (h->tasks[p][m].empty()) return DD_OK;
+    const int rc = (int)cudaMemcpyAsync(h->d.tasks[p][m], h->tasks[p][m].data(), sizeof(GemvTask) * h->tasks[p][m].size(),
+                                        cudaMemcpyHostToDevice, s);
+    return rc ? DD_ERR_CUDA : DD_OK;
+}
+
 template <typename T>
 int upload(T* dst, const std::vector<T>& src, cudaStream_t s) {
     if (src.empty()) return 0;
@@ -179,7 +192,8 @@ size_t dd_workspace_layout(dd_handle* h, bool assign) {
     L.take(d.Tval, nnz);
     L.take(d.Sval, nnz);
     L.take(d.Aval, nnz);
-    for (int m = 0; m < GEMV_NMODES; ++m) L.take(d.tasks[m], h->tasks[m].size());
+    for (int p = 0; p < 2; ++p)
+        for (int m = 0; m < GEMV_NMODES; ++m) L.take(d.tasks[p][m], h->task_cap[m]);
     L.take(d.probe_dof, 6 * kMaxProbes);
     L.take(d.probe_w, 18 * kMaxProbes);
     L.take(d.M64, (size_t)h->dense_elems);
@@ -625,7 +639,11 @@ int dd_bind_workspace(dd_handle* h, void* dev, size_t bytes, void* stream) {
     CK(h, upload(h->d.col_dof, h->col_dof, s), "upload");
     CK(h, upload(h->d.Tval, h->Tval, s), "upload");
     CK(h, upload(h->d.Sval, h->Sval, s), "upload");
-    for (int m = 0; m < GEMV_NMODES; ++m) CK(h, upload(h->d.tasks[m], h->tasks[m], s), "upload");
+    for (int p = 0; p < 2; ++p)
+        for (int m = 0; m < GEMV_NMODES; ++m) {
+            const int urc = upload_tasks(h, p, m, s);
+            if (urc) return urc == DD_ERR_CUDA ? h->fail(DD_ERR_CUDA, "upload tasks") : urc;
+        }
     {
         std::vector<int32_t> td(h->tet_dof.size());
         for (size_t i = 0; i < td.size(); ++i) td[i] = (int32_t)h->tet_dof[i];
@@ -1105,6 +1123,127 @@ int dd_set_state(dd_handle* h, const double* e_n, const double* e_nm1, int64_t s
     CK(h, (int)cudaMemcpyAsync(h->d.e[2], e_nm1, nb, cudaMemcpyDeviceToDevice, s), "copy");
     h->step = step;
     h->lam_valid = false;
+    return DD_OK;
+}
+
+int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* stream) {
+    if (!h) return DD_ERR_ARG;
+    if (!h->factored) return h->fail(DD_ERR_STATE, "dd_autotune before dd_factor");
+    if (h->capturing) return h->fail(DD_ERR_STATE, "dd_autotune during capture");
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0;
+    CK(h, (int)cudaGetDevice(&dev), "device");
+    cudaDeviceProp prop;
+    CK(h, (int)cudaGetDeviceProperties(&prop, dev), "device properties");
+    std::string key = std::string(prop.name) + "|" + std::to_string(h->n_sub) + "|" + std::to_string(h->n_dof) + "|" +
+                      std::to_string(h->sub_ptr.back()) + "|" + std::to_string(h->corner_dof.size()) + "|" +
+                      std::to_string(h->max_ns);
+    for (char& c : key)
+        if (c == ' ' || c == '\t') c = '_';
+    std::map<std::pair<int, int>, TileCfg> found;
+    if (cache_path && *cache_path) {
+        std::ifstream f(cache_path);
+        std::string line;
+        while (std::getline(f, line)) {
+            std::istringstream is(line);
+            std::string k;
+            int p, m, lpr, rows;
+            if ((is >> k >> p >> m >> lpr >> rows) && k == key && p >= 0 && p < 2 && m >= 0 && m < GEMV_NMODES &&
+                (lpr == 8 || lpr == 16 || lpr == 32) && rows >= kMinRowsPerTask)
+                found[{p, m}] = TileCfg{lpr, rows};
+        }
+    }
+    const bool cached = found.size() == (size_t)(2 * GEMV_NMODES);
+    cudaEvent_t e0, e1;
+    CK(h, (int)cudaEventCreate(&e0), "event");
+    CK(h, (int)cudaEventCreate(&e1), "event");
+    const auto t_start = std::chrono::steady_clock::now();
+    int rc = DD_OK;
+    const size_t nl = (size_t)h->sub_ptr.back(), nc = h->corner_dof.size();
+    if (!cached) {
+        // time every candidate tile on the real operators (inputs zero: timing only)
+        rc = (int)cudaMemsetAsync(h->d.b, 0, sizeof(double) * nl, s);
+        if (!rc) rc = (int)cudaMemsetAsync(h->d.bf, 0, sizeof(float) * nl, s);
+        if (!rc && nc) rc = (int)cudaMemsetAsync(h->d.uC, 0, sizeof(double) * nc, s);
+        if (!rc && nc) rc = (int)cudaMemsetAsync(h->d.uCf, 0, sizeof(float) * nc, s);
+        const int lprs[3] = {8, 16, 32};
+        const int rowss[5] = {8, 16, 32, 64, 128};
+        for (int p = 0; p < 2 && !rc; ++p) {
+            const int prec = p == 0 ? DD_FP64 : DD_MIXED;
+            for (int m = 0; m < GEMV_NMODES && !rc; ++m) {
+                if (h->tasks[p][m].empty()) {
+                    found[{p, m}] = h->tile[p][m];
+                    continue;
+                }
+                const bool co = m == GEMV_COARSE;
+                XSrc xs{};
+                xs.kind = X_FLAT;
+                xs.v = co ? h->d.uC : h->d.b;
+                xs.vf = co ? h->d.uCf : h->d.bf;
+                GemvOut go = p == 0 ? GemvOut{co ? h->d.vC : h->d.x, nullptr, nullptr, nullptr, 1.0}
+                                    : GemvOut{nullptr, nullptr, co ? h->d.vCf : h->d.wf, nullptr, 1.0};
+                float best = 1e30f;
+                TileCfg bt = h->tile[p][m];
+                for (int li = 0; li < 3 && !rc; ++li)
+                    for (int ri = 0; ri < 5 && !rc; ++ri) {
+                        h->tile[p][m] = TileCfg{lprs[li], rowss[ri]};
+                        build_tasks(h, m, rowss[ri], h->tasks[p][m]);
+                        const int urc = upload_tasks(h, p, m, s);
+                        if (urc) {
+                            cudaEventDestroy(e0);
+                            cudaEventDestroy(e1);
+                            return urc == DD_ERR_CUDA ? h->fail(DD_ERR_CUDA, "upload tasks") : urc;
+                        }
+                        for (int it = 0; it < 4 && !rc; ++it) {
+                            if (it == 1) rc = (int)cudaEventRecord(e0, s);
+                            if (!rc) rc = launch_gemv(h, m, prec, xs, go, false, s);
+                        }
+                        if (!rc) rc = (int)cudaEventRecord(e1, s);
+                        if (!rc) rc = (int)cudaEventSynchronize(e1);
+                        float ms = 0.f;
+                        if (!rc) rc = (int)cudaEventElapsedTime(&ms, e0, e1);
+                        h->launches[ST_FACTOR] += 4;
+                        h->total_launches += 4;
+                        if (!rc && ms < best) {
+                            best = ms;
+                            bt = h->tile[p][m];
+                        }
+                    }
+                found[{p, m}] = bt;
+            }
+        }
+        if (!rc && cache_path && *cache_path) {
+            std::ofstream f(cache_path, std::ios::app);
+            for (const auto& kv : found)
+                f << key << "\t" << kv.first.first << "\t" << kv.first.second << "\t" << kv.second.lpr << "\t"
+                  << kv.second.rows << "\n";
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return cuda_fail(h, rc, "autotune");
+    for (int p = 0; p < 2; ++p)
+        for (int m = 0; m < GEMV_NMODES; ++m) {
+            h->tile[p][m] = found[{p, m}];
+            build_tasks(h, m, h->tile[p][m].rows, h->tasks[p][m]);
+            const int urc = upload_tasks(h, p, m, s);
+            if (urc) return urc == DD_ERR_CUDA ? h->fail(DD_ERR_CUDA, "upload tasks") : urc;
+        }
+    CK(h, (int)cudaStreamSynchronize(s), "sync");
+    drop_graphs(h);
+    h->tuned = true;
+    if (seconds)
+        *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    return DD_OK;
+}
+
+int dd_get_tiles(const dd_handle* h, int32_t* lpr, int32_t* rows) {
+    if (!h || !lpr || !rows) return DD_ERR_ARG;
+    for (int p = 0; p < 2; ++p)
+        for (int m = 0; m < GEMV_NMODES; ++m) {
+            lpr[p * GEMV_NMODES + m] = h->tile[p][m].lpr;
+            rows[p * GEMV_NMODES + m] = h->tile[p][m].rows;
+        }
     return DD_OK;
 }
 

@@ -68,6 +68,13 @@ struct GemvOut {
     double alpha;
 };
 
+// Tile shape of a batched GEMV launch: lanes cooperating on one row and rows
+// handled by one CTA.  Defaults below; dd_autotune replaces them by measurement.
+struct TileCfg {
+    int32_t lpr;
+    int32_t rows;
+};
+
 // Device scalars of the interface CG (one struct in the workspace).
 struct PcgScalars {
     double rz;        // r . z
@@ -111,7 +118,7 @@ struct DevPtrs {
     double* Tval = nullptr;
     double* Sval = nullptr;
     double* Aval = nullptr;          // T + dt^2/4 S (filled by dd_factor)
-    GemvTask* tasks[GEMV_NMODES] = {};
+    GemvTask* tasks[2][GEMV_NMODES] = {};   // [0] FP64 tiles, [1] FP32 tiles
     int32_t* probe_dof = nullptr;
     double* probe_w = nullptr;
     // dense operators
@@ -209,7 +216,10 @@ struct dd_handle {
     int64_t dense_elems = 0;
     int32_t ldc = 0;                 // leading dimension of K~cc
     int32_t max_nr = 0, max_ns = 0;
-    std::vector<GemvTask> tasks[GEMV_NMODES];
+    std::vector<GemvTask> tasks[2][GEMV_NMODES];   // per precision (tile shapes may differ)
+    size_t task_cap[GEMV_NMODES] = {};             // device capacity: tasks at the smallest row count
+    TileCfg tile[2][GEMV_NMODES];                  // lanes per row and rows per CTA, per precision and mode
+    bool tuned = false;
 
     // probes
     int32_t n_probe = 0;
@@ -257,13 +267,19 @@ struct dd_handle {
 };
 
 constexpr int kNB = 32;              // pivot block of the dense elimination
-// rows per CTA of the batched GEMV, per mode (LOCAL, SCHUR, CORNER, RECOVER, COARSE)
+// default tile shapes per mode (LOCAL, SCHUR_C, CORNER, RECOVER, COARSE, SCHUR_G):
+// rows per CTA, and lanes per row for FP32 and FP64 (8 lanes for FP64 keeps the
+// FP64 reduction adds off GB300's narrow FP64 pipe)
 constexpr int kRowsPerMode[GEMV_NMODES] = {32, 32, 64, 32, 8, 64};
+constexpr int kLprF32[GEMV_NMODES] = {32, 16, 8, 16, 32, 16};
+constexpr int kLprF64[GEMV_NMODES] = {8, 8, 8, 8, 32, 8};
+constexpr int kMinRowsPerTask = 8;    // smallest rows per CTA of any default or candidate tile (sets task capacity)
 constexpr int kMaxPartials = 4096;   // block partials of the grid reductions
 
 // setup.cpp
 int dd_build_host(dd_handle* h, const dd_mesh* mesh, const int32_t* part, int32_t n_sub);
 int dd_locate_probes(dd_handle* h, int32_t n, const double* xyz);
+void build_tasks(const dd_handle* h, int mode, int rows, std::vector<GemvTask>& out);
 size_t dd_workspace_layout(dd_handle* h, bool assign);
 
 // kernels.cu launchers (return a cudaError_t value; 0 = success)

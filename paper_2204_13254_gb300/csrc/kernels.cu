@@ -976,13 +976,14 @@ int run_gemv(unsigned nb, size_t smem, cudaStream_t st, const GemvTask* tasks, c
 }
 
 int launch_gemv(const dd_handle* h, int mode, int prec, XSrc xs, GemvOut go, bool check_done, void* stream) {
-    const auto& tl = h->tasks[mode];
+    const int pi = prec == DD_MIXED ? 1 : 0;
+    const auto& tl = h->tasks[pi][mode];
     if (tl.empty()) return 0;
     xs.slot_mult = h->d.slot_mult;
     xs.slot_corner = h->d.slot_corner;
     xs.sc = h->d.sc;
     const MatDesc* mats = mode == GEMV_COARSE ? h->d.coarse_desc : h->d.mats;
-    const GemvTask* tasks = h->d.tasks[mode];
+    const GemvTask* tasks = h->d.tasks[pi][mode];
     const int maxcol = mode == GEMV_COARSE ? (int)h->corner_dof.size() : h->max_ns;
     const size_t elt = prec == DD_MIXED ? sizeof(float) : sizeof(double);
     size_t smem = (size_t)(maxcol + 4) * elt;   // staged extent rounds the segment out to 16-byte boundaries
@@ -993,21 +994,21 @@ int launch_gemv(const dd_handle* h, int mode, int prec, XSrc xs, GemvOut go, boo
     }
     const int32_t* done = check_done ? &h->d.sc->done : nullptr;
     const unsigned nb = (unsigned)tl.size();
-    // lanes per row: long rows 32, medium rows 16, the 72-wide corner block 8; FP64
-    // uses 8 except on the 7056-long coarse rows (fewer FP64 reduction adds)
-    static const int kLprF32[GEMV_NMODES] = {32, 16, 8, 16, 32, 16};
-    static const int kLprF64[GEMV_NMODES] = {8, 8, 8, 8, 32, 8};
+    const int lpr = h->tile[pi][mode].lpr;
     if (prec == DD_MIXED) {
         const float* M = mode == GEMV_COARSE ? h->d.K32 : h->d.M32;
-        switch (kLprF32[mode]) {
+        switch (lpr) {
             case 8: return run_gemv<float, 8>(nb, smem, S(stream), tasks, mats, M, mode, xs, go, staged, done);
             case 16: return run_gemv<float, 16>(nb, smem, S(stream), tasks, mats, M, mode, xs, go, staged, done);
             default: return run_gemv<float, 32>(nb, smem, S(stream), tasks, mats, M, mode, xs, go, staged, done);
         }
     }
     const double* M = mode == GEMV_COARSE ? h->d.K64 : h->d.M64;
-    if (kLprF64[mode] == 32) return run_gemv<double, 32>(nb, smem, S(stream), tasks, mats, M, mode, xs, go, staged, done);
-    return run_gemv<double, 8>(nb, smem, S(stream), tasks, mats, M, mode, xs, go, staged, done);
+    switch (lpr) {
+        case 8: return run_gemv<double, 8>(nb, smem, S(stream), tasks, mats, M, mode, xs, go, staged, done);
+        case 16: return run_gemv<double, 16>(nb, smem, S(stream), tasks, mats, M, mode, xs, go, staged, done);
+        default: return run_gemv<double, 32>(nb, smem, S(stream), tasks, mats, M, mode, xs, go, staged, done);
+    }
 }
 
 int launch_iface_rhs(const dd_handle* h, float* fCf, void* stream) {

@@ -371,29 +371,39 @@ int dd_build_host(dd_handle* h, const dd_mesh* mesh, const int32_t* part, int32_
     h->dense_elems = moff;
     h->ldc = (int32_t)((nc + 3) / 4 * 4);
 
-    // ---- batched GEMV task lists ------------------------------------------------
+    // ---- batched GEMV task lists (default tiles; dd_autotune may change them) ------
     for (int mode = 0; mode < GEMV_NMODES; ++mode) {
-        auto& tl = h->tasks[mode];
-        tl.clear();
-        if (mode == GEMV_COARSE) {
-            const int rp = kRowsPerMode[mode];
-            for (int64_t r0 = 0; r0 < nc; r0 += rp)
-                tl.push_back({0, (int32_t)r0, (int32_t)std::min<int64_t>(nc, r0 + rp), 0});
-            continue;
-        }
-        for (int s = 0; s < n_sub; ++s) {
-            const MatDesc& md = h->mats[s];
-            int32_t r0 = 0, r1 = 0;
-            if (mode == GEMV_LOCAL) { r0 = 0; r1 = md.ns; }
-            if (mode == GEMV_SCHUR_C) { r0 = md.nr; r1 = md.ns; }
-            if (mode == GEMV_CORNER) { r0 = md.nI; r1 = md.nr; }
-            if (mode == GEMV_RECOVER) { r0 = 0; r1 = md.nr; }
-            if (mode == GEMV_SCHUR_G) { r0 = md.nI; r1 = md.nr; }
-            const int rp = kRowsPerMode[mode];
-            for (int32_t a = r0; a < r1; a += rp) tl.push_back({s, a, std::min(r1, a + rp), 0});
+        std::vector<GemvTask> cap;
+        build_tasks(h, mode, kMinRowsPerTask, cap);
+        h->task_cap[mode] = cap.size();
+        for (int p = 0; p < 2; ++p) {
+            h->tile[p][mode] = TileCfg{p == 0 ? kLprF64[mode] : kLprF32[mode], kRowsPerMode[mode]};
+            build_tasks(h, mode, kRowsPerMode[mode], h->tasks[p][mode]);
         }
     }
     return DD_OK;
+}
+
+// CTA tasks of a batched GEMV: the mode's row range of every subdomain (or of
+// the coarse matrix) cut into chunks of `rows` rows.
+void build_tasks(const dd_handle* h, int mode, int rows, std::vector<GemvTask>& tl) {
+    tl.clear();
+    if (mode == GEMV_COARSE) {
+        const int64_t nc = (int64_t)h->corner_dof.size();
+        for (int64_t r0 = 0; r0 < nc; r0 += rows)
+            tl.push_back({0, (int32_t)r0, (int32_t)std::min<int64_t>(nc, r0 + rows), 0});
+        return;
+    }
+    for (int s = 0; s < h->n_sub; ++s) {
+        const MatDesc& md = h->mats[s];
+        int32_t r0 = 0, r1 = 0;
+        if (mode == GEMV_LOCAL) { r0 = 0; r1 = md.ns; }
+        if (mode == GEMV_SCHUR_C) { r0 = md.nr; r1 = md.ns; }
+        if (mode == GEMV_CORNER) { r0 = md.nI; r1 = md.nr; }
+        if (mode == GEMV_RECOVER) { r0 = 0; r1 = md.nr; }
+        if (mode == GEMV_SCHUR_G) { r0 = md.nI; r1 = md.nr; }
+        for (int32_t a = r0; a < r1; a += rows) tl.push_back({s, a, std::min(r1, a + rows), 0});
+    }
 }
 
 int dd_locate_probes(dd_handle* h, int32_t n, const double* p) {

@@ -21,7 +21,7 @@ DD_FP64, DD_MIXED = 0, 1
 
 SYMBOLS = ["dd_setup", "dd_set_params", "dd_get_sizes", "dd_get_maps", "dd_set_probes", "dd_bind_workspace",
            "dd_factor", "dd_step", "dd_schur_apply", "dd_schur_apply_static", "dd_probe", "dd_adjoint_reset",
-           "dd_adjoint_step", "dd_probe_seed", "dd_get_state", "dd_set_state", "dd_profile",
+           "dd_adjoint_step", "dd_probe_seed", "dd_autotune", "dd_get_tiles", "dd_get_state", "dd_set_state", "dd_profile",
            "dd_destroy", "dd_last_error"]
 N_STAGES = 9
 STAGES = ["rhs", "local_solve", "iface_apply", "coarse", "corner", "recover", "vector", "refine", "factor"]
@@ -83,6 +83,8 @@ def load_library(path: str = LIB_PATH):
         "dd_adjoint_reset": (C.c_int, [vp, vp]),
         "dd_adjoint_step": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp, C.POINTER(dd_stats), vp]),
         "dd_probe_seed": (C.c_int, [vp, vp, C.c_double, vp, vp]),
+        "dd_autotune": (C.c_int, [vp, C.c_char_p, C.POINTER(C.c_double), vp]),
+        "dd_get_tiles": (C.c_int, [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
         "dd_destroy": (None, [vp]),
         "dd_last_error": (C.c_char_p, [vp]),
     }
@@ -231,6 +233,23 @@ def dd_adjoint_step(h, seed, e_k=None, e_km1=None, e_km2=None, d2g_hat=None, gra
 
 def dd_probe_seed(h, e, weight, seed, stream=None):
     _check(h, lib().dd_probe_seed(h, _ptr(e), float(weight), _ptr(seed), _stream(stream)))
+
+
+GEMV_KINDS = ["local", "corner_rows", "corner_coupling", "recover", "coarse", "iface_rows"]
+
+
+def dd_autotune(h, cache_path=None, stream=None):
+    """Time candidate GEMV tiles on the factored operators; returns wall seconds."""
+    secs = C.c_double()
+    _check(h, lib().dd_autotune(h, cache_path.encode() if cache_path else None, C.byref(secs), _stream(stream)))
+    return secs.value
+
+
+def dd_get_tiles(h):
+    lpr = (C.c_int32 * 12)()
+    rows = (C.c_int32 * 12)()
+    _check(h, lib().dd_get_tiles(h, lpr, rows))
+    return {("fp64", "fp32")[p]: {GEMV_KINDS[k]: (lpr[6 * p + k], rows[6 * p + k]) for k in range(6)} for p in range(2)}
 
 
 def dd_profile(h, enable=-1, read=True, stream=None):
