@@ -328,6 +328,13 @@ def run_ours(args, rank, world, local):
     return res
 
 
+def aggregate_replicas(ms_local, steps, world, reduce_max):
+    """Whole-job rate of `world` independent replicas: every rank timed `steps`
+    steps in ms_local; the job takes the slowest rank's time (max over ranks)."""
+    ms = reduce_max(ms_local)
+    return ms, world * steps / (ms / 1e3)
+
+
 def stage_table(prof, K):
     out = {}
     if not prof:
@@ -417,9 +424,10 @@ def main():
     sizes = r["sizes"]
     w = r["workload"]
     ms_head = r["ms32"] if head == "mixed" else r["ms64"]
-    value = world * K / (ms_head / 1e3)
-    v64 = world * K / (r["ms64"] / 1e3)
-    v32 = world * K / (r["ms32"] / 1e3)
+    same = lambda x: x          # times were already max-reduced over ranks in run_ours
+    value = aggregate_replicas(ms_head, K, world, same)[1]
+    v64 = aggregate_replicas(r["ms64"], K, world, same)[1]
+    v32 = aggregate_replicas(r["ms32"], K, world, same)[1]
     cb = None
     if world == 1 and not args.no_cpu_baseline and not args.cavity:
         try:
@@ -461,7 +469,7 @@ def main():
                      "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs" + ("" if peak_kind == "measured" else " (no MEASURED_PEAKS.json)")},
         "cpu_baseline": cb,
-        "e2e": {"value": world * K / (r["ms_e2e"] / 1e3), "unit": "steps/s",
+        "e2e": {"value": aggregate_replicas(r["ms_e2e"], K, world, same)[1], "unit": "steps/s",
                 "h2d_bytes_per_step": int(sizes.n_dof * 8), "d2h_bytes_per_step": int(sizes.n_dof * 8)},
         "gpu_launches": int(r["launches32"] if head == "mixed" else r["launches64"]),
         "launch_mode": "eager" if args.eager else f"CUDA graph per step (CG WHILE node, {args.chunk} it/body)",

@@ -24,7 +24,7 @@ GOLD = os.path.join(os.path.dirname(__file__), "golden")
 DT = json.load(open(os.path.join(GOLD, "cfl_dt.json")))
 
 
-def run_and_check(cfg, n_steps, runs):
+def run_and_check(cfg, n_steps, runs, autotune=False):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     w = W.config(cfg)
@@ -38,6 +38,8 @@ def run_and_check(cfg, n_steps, runs):
     d2g = w.d2G(dt, n_steps)
     fs = D.FieldSolver(w.xyz, w.tets, w.part, w.n_sub, w.eps, w.mu).bind()
     fs.factor(dt)
+    if autotune:
+        D.dd_autotune(fs.h, None)
     dofs = fs.dof_of_pairs(w.source_pairs)
     sv = torch.zeros(fs.n_dof, dtype=torch.float64, device="cuda")
     out = torch.empty_like(sv)
@@ -76,3 +78,12 @@ def test_config4_cavity48_fp64_and_mixed():
 
 def test_config3_jittered_rcb300_fp64():
     run_and_check(3, 12, [("fp64", D.make_params(tol=1e-12), 1e-11)])
+
+
+def test_config4_bench_launch_configuration():
+    """The configuration bench.py times: autotuned tiles, CUDA-graph steps, both precisions."""
+    res = run_and_check(4, 30, [("fp64", D.make_params(tol=1e-10, use_graph=1, chunk=2), 1e-9),
+                                ("mixed", D.make_params(precision=D.DD_MIXED, tol=1e-5, refine_tol=1e-10,
+                                                        max_refine=6, use_graph=1, chunk=2), 1e-9)], autotune=True)
+    f64, f32 = res["fp64"][2], res["mixed"][2]
+    assert np.linalg.norm(f32[-1] - f64[-1]) / np.linalg.norm(f64[-1]) <= 1e-8
