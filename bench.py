@@ -203,9 +203,13 @@ def run_ours(args, rank, world, local):
         w = W.config(cfg)
         dt = load_dt(cfg)
     K, Wu = args.steps, args.warmup
+    pic = cfg == 2 and not args.cavity      # config 2: the timed step is the whole PIC cycle
     t0 = time.perf_counter()
     fs = D.FieldSolver(w.xyz, w.tets, w.part, w.n_sub, w.eps, w.mu,
-                       D.make_params(precision=D.DD_FP64, tol=args.tol64), device=dev).bind()
+                       D.make_params(precision=D.DD_FP64, tol=args.tol64), device=dev)
+    if pic:
+        fs.set_beam(*W.beam(w, 100000, w.steps * dt, seed=0))
+    fs.bind()
     t_setup = time.perf_counter() - t0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -230,12 +234,20 @@ def run_ours(args, rank, world, local):
         if world > 1:
             torch.distributed.barrier()
 
+    def one_step(k, stats):
+        if pic:
+            return fs.pic_step(stats=stats)
+        return fs.step(D2G[k], stats=stats)
+
     def run_steps(params, profile, clocks=None):
         """W warm-up steps, then K timed steps (CUDA events on the launch stream)."""
         fs.set_params(params)
-        fs.set_state(zero, zero, 0)
+        if pic:
+            fs.factor(dt)                        # restarts fields and particles
+        else:
+            fs.set_state(zero, zero, 0)
         for k in range(Wu):
-            fs.step(D2G[k], stats=True)
+            one_step(k, True)
         barrier()
         torch.cuda.synchronize()
         fs.profile(enable=1, read=False)          # reset the launch counters
@@ -247,7 +259,7 @@ def run_ours(args, rank, world, local):
         ev0.record(stream)
         its, refs = [], []
         for k in range(K):
-            st = fs.step(D2G[Wu + k], stats=True)
+            st = one_step(Wu + k, True)
             its.append(st["iters"])
             refs.append(st["refinements"])
         ev1.record(stream)
@@ -291,7 +303,7 @@ def run_ours(args, rank, world, local):
 
     # end-to-end: per step, H2D of the source from pinned host memory, the C-ABI step, D2H of e^{n+1}
     ms_e2e = nan
-    if not args.no_e2e:
+    if not args.no_e2e and not pic:
         host_src = torch.zeros((K, n), dtype=torch.float64).pin_memory()
         host_src.copy_(D2G[Wu:].cpu())
         host_e = torch.empty(n, dtype=torch.float64).pin_memory()
@@ -324,7 +336,7 @@ def run_ours(args, rank, world, local):
     sizes = fs.sizes
     res = dict(fs=fs, K=K, ms64=ms64, ms32=ms32, ms_e2e=ms_e2e, it64=it64, it32=it32, ref32=ref32, prof64=prof64,
                prof32=prof32, rel=rel, launches64=launches64, launches32=launches32, t_setup=t_setup, t_factor=t_factor, clocks=clocks.summary(), sizes=sizes,
-               workload=w, dt=dt, t_tune=t_tune, tiles=tiles)
+               workload=w, dt=dt, t_tune=t_tune, tiles=tiles, pic=pic)
     return res
 
 
@@ -429,7 +441,7 @@ def main():
     v64 = aggregate_replicas(r["ms64"], K, world, same)[1]
     v32 = aggregate_replicas(r["ms32"], K, world, same)[1]
     cb = None
-    if world == 1 and not args.no_cpu_baseline and not args.cavity:
+    if world == 1 and not args.no_cpu_baseline and not args.cavity and not r["pic"]:
         try:
             its = r["it32"] if head == "mixed" else r["it64"]
             cb = cpu_baseline(args.config, r["dt"], float(np.mean(its)), w.n_sub)
@@ -448,7 +460,8 @@ def main():
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms_head / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if head == "mixed" else "f64", "data": "synthetic",
-        "config": {"workload": (f"{w.name}: PEC box {w.dims[0]}x{w.dims[1]}x{w.dims[2]} Kuhn cubes, {len(w.tets)} tets, "
+        "config": {"workload": ("PIC cycle (1e5-particle beam push + Whitney deposition + DD field solve + Faraday), "
+                                if r["pic"] else "") + (f"{w.name}: PEC box {w.dims[0]}x{w.dims[1]}x{w.dims[2]} Kuhn cubes, {len(w.tets)} tets, "
                                 f"{sizes.n_dof} edge dofs, {w.n_sub} subdomains, {sizes.n_lambda} multipliers, "
                                 f"{sizes.n_corner} corners, Gaussian z-line pulse, dt=2xCFL={r['dt']:.6g}"),
                    "l2_policy": "inputs larger than L2 (dense subdomain operators "

@@ -235,6 +235,45 @@ int dd_adjoint_step(dd_handle* h, const double* seed, const double* e_k, const d
  * probe set (device [n_dof] e and seed; seed is overwritten). */
 int dd_probe_seed(dd_handle* h, const double* e, double weight, double* seed, void* stream);
 
+/* ---- particle-in-cell coupling (Sec. II PIC cycle) --------------------
+ * Macro-particles enter through the mesh boundary at given times and move on
+ * straight segments within a step.  Per step (dd_pic_step):
+ *  1. push: Boris with E(x^n) from the edge field e^n (Whitney 1-forms) and
+ *     B(x^n) from the face fluxes b^n (Whitney 2-forms); a particle injected
+ *     during the step moves without a push from its injection time;
+ *  2. deposit: q * int W_e . dl along the path, cut at every face crossed
+ *     (exact; conserves charge per particle), into dep^{n+1/2}; a path that
+ *     reaches a wall stops there;
+ *  3. field step: dd_step with d2g = dep^{n+1/2} - dep^{n-1/2} (the second
+ *     difference of the integrated current g);
+ *  4. Faraday: b^{n+1} = b^n - dt/2 * C (e^{n+1} + e^n), C the discrete curl.
+ * Deposition uses FP64 atomic adds (summation order is not fixed). */
+typedef struct {
+    int64_t n_particles;
+    const double* x_inj;   /* host [n*3] injection points (on the mesh boundary) */
+    const double* v_inj;   /* host [n*3] velocity from injection on */
+    const double* t_inj;   /* host [n] injection times (t >= 0) */
+    double q;              /* macro-particle charge */
+    double qm;             /* charge / mass */
+} dd_beam;
+
+/* Host set-up of the particle data: faces, tet adjacency, the boundary tet of
+ * every injection point.  Call after dd_setup and before dd_bind_workspace
+ * (the workspace size grows with the particles).  Errors: DD_ERR_ARG when an
+ * injection point is not on the mesh boundary. */
+int dd_set_beam(dd_handle* h, const dd_beam* beam);
+
+/* One PIC cycle at t_n = step * dt (see above).  stats as dd_step; a particle
+ * crossing more than 64 tets in one step sets DD_ERR_ARG. */
+int dd_pic_step(dd_handle* h, dd_stats* stats, void* stream);
+
+/* Particle state and integrated current (device outputs, any may be NULL):
+ * x [n*3] positions, status [n] (0 waiting, 1 in flight, 2 stopped at a wall),
+ * G [n_dof] integrated current g^n, b [n_faces] face fluxes.  Sizes: n_faces
+ * is returned in *n_faces (host, may be NULL). */
+int dd_pic_state(const dd_handle* h, double* x, int32_t* status, double* G, double* b, int64_t* n_faces,
+                 void* stream);
+
 /* Apply the Schur-complement interface operator of Eq. f1schur,
  * out = (F_rr + F_rc K~cc^-1 F_rc^T) lam, in FP64 with the factors of the last
  * dd_factor.  lam, out: device [n_lambda]. */

@@ -208,6 +208,28 @@ size_t dd_workspace_layout(dd_handle* h, bool assign) {
     L.take(d.lamf_adj, nm);
     L.take(d.tet_dof, 6 * (size_t)h->n_tets);
     L.take(d.That, 36 * (size_t)h->n_tets);
+    {
+        const size_t np = (size_t)h->n_particles, nt = h->n_particles ? (size_t)h->n_tets : 0,
+                     nfc = h->n_particles ? (size_t)h->n_faces : 0, ndp = h->n_particles ? nd : 0;
+        L.take(d.px, 3 * np);
+        L.take(d.pv, 3 * np);
+        L.take(d.pt, np);
+        L.take(d.ptet, np);
+        L.take(d.pstat, np);
+        L.take(d.tets_dev, 4 * nt);
+        L.take(d.tgrad, 12 * nt);
+        L.take(d.tx0, 3 * nt);
+        L.take(d.tface, 4 * nt);
+        L.take(d.tnbr, 4 * nt);
+        L.take(d.face_nodes, 3 * nfc);
+        L.take(d.face_edge, 3 * nfc);
+        L.take(d.bflux, nfc);
+        L.take(d.dep[0], ndp);
+        L.take(d.dep[1], ndp);
+        L.take(d.Gcum, ndp);
+        L.take(d.d2g_pic, ndp);
+        L.take(d.pic_err, 4);
+    }
     L.take(d.b, nl);
     L.take(d.y, nl);
     L.take(d.w, nl);
@@ -531,6 +553,11 @@ int dd_solve(dd_handle* h, int prec, double tol, bool warm, int* it_out, double*
 
 extern "C" {
 
+namespace {
+int reset_particles(dd_handle* h, cudaStream_t s);
+int upload_pic_mesh(dd_handle* h, cudaStream_t s);
+}  // namespace
+
 int dd_setup(const dd_mesh* mesh, const int32_t* part, int32_t n_sub, const dd_params* params, dd_handle** out) {
     if (!out) return DD_ERR_ARG;
     *out = nullptr;
@@ -651,6 +678,10 @@ int dd_bind_workspace(dd_handle* h, void* dev, size_t bytes, void* stream) {
         CK(h, (int)cudaStreamSynchronize(s), "sync");   // td is a local
     }
     CK(h, upload(h->d.That, h->That, s), "upload");
+    {
+        const int prc = upload_pic_mesh(h, s);
+        if (prc) return prc;
+    }
     if (h->n_probe) {
         CK(h, upload(h->d.probe_dof, h->probe_dof, s), "upload");
         CK(h, upload(h->d.probe_w, h->probe_w, s), "upload");
@@ -706,6 +737,11 @@ int dd_factor(dd_handle* h, double dt, void* stream) {
     for (int k = 0; k < 3; ++k) CK(h, (int)cudaMemsetAsync(h->d.e[k], 0, sizeof(double) * nd, s), "memset");
     CK(h, (int)cudaStreamSynchronize(s), "sync");
     for (int k = 0; k < 3; ++k) CK(h, (int)cudaMemsetAsync(h->d.mu[k], 0, sizeof(double) * nd, s), "memset");
+    CK(h, (int)cudaStreamSynchronize(s), "sync");
+    {
+        const int prc = reset_particles(h, s);
+        if (prc) return prc;
+    }
     CK(h, (int)cudaStreamSynchronize(s), "sync");
     h->dt = dt;
     h->step = 0;
@@ -1123,6 +1159,96 @@ int dd_set_state(dd_handle* h, const double* e_n, const double* e_nm1, int64_t s
     CK(h, (int)cudaMemcpyAsync(h->d.e[2], e_nm1, nb, cudaMemcpyDeviceToDevice, s), "copy");
     h->step = step;
     h->lam_valid = false;
+    return DD_OK;
+}
+
+namespace {
+
+// Particles back at their injection data, fields of the PIC coupling zeroed.
+int reset_particles(dd_handle* h, cudaStream_t s) {
+    if (!h->n_particles) return DD_OK;
+    const size_t np = (size_t)h->n_particles, nd = (size_t)h->n_dof;
+    CK(h, upload(h->d.px, h->p_x, s), "upload");
+    CK(h, upload(h->d.pv, h->p_v, s), "upload");
+    CK(h, upload(h->d.pt, h->p_t, s), "upload");
+    CK(h, upload(h->d.ptet, h->p_tet, s), "upload");
+    CK(h, (int)cudaMemsetAsync(h->d.pstat, 0, sizeof(int32_t) * np, s), "memset");
+    CK(h, (int)cudaMemsetAsync(h->d.bflux, 0, sizeof(double) * (size_t)h->n_faces, s), "memset");
+    for (int k = 0; k < 2; ++k) CK(h, (int)cudaMemsetAsync(h->d.dep[k], 0, sizeof(double) * nd, s), "memset");
+    CK(h, (int)cudaMemsetAsync(h->d.Gcum, 0, sizeof(double) * nd, s), "memset");
+    CK(h, (int)cudaMemsetAsync(h->d.pic_err, 0, 4, s), "memset");
+    h->dep_cur = 0;
+    return DD_OK;
+}
+
+int upload_pic_mesh(dd_handle* h, cudaStream_t s) {
+    if (!h->n_particles) return DD_OK;
+    std::vector<double> x0(3 * (size_t)h->n_tets);
+    for (int64_t t = 0; t < h->n_tets; ++t)
+        for (int c = 0; c < 3; ++c) x0[3 * t + c] = h->xyz[3 * (int64_t)h->tets[4 * t] + c];
+    CK(h, upload(h->d.tets_dev, h->tets, s), "upload");
+    CK(h, upload(h->d.tgrad, h->grad, s), "upload");
+    CK(h, upload(h->d.tx0, x0, s), "upload");
+    CK(h, upload(h->d.tface, h->tet_face, s), "upload");
+    CK(h, upload(h->d.tnbr, h->tet_nbr, s), "upload");
+    CK(h, upload(h->d.face_nodes, h->face_nodes, s), "upload");
+    CK(h, upload(h->d.face_edge, h->face_edge, s), "upload");
+    CK(h, (int)cudaStreamSynchronize(s), "sync");   // x0 is a local
+    return reset_particles(h, s);
+}
+
+}  // namespace
+
+int dd_set_beam(dd_handle* h, const dd_beam* beam) {
+    if (!h || !beam || beam->n_particles < 0 || (beam->n_particles > 0 && (!beam->x_inj || !beam->v_inj || !beam->t_inj)))
+        return h ? h->fail(DD_ERR_ARG, "bad beam") : DD_ERR_ARG;
+    if (h->bound) return h->fail(DD_ERR_STATE, "dd_set_beam after dd_bind_workspace");
+    return dd_build_beam(h, beam);
+}
+
+int dd_pic_step(dd_handle* h, dd_stats* stats, void* stream) {
+    if (!h) return DD_ERR_ARG;
+    if (!h->factored) return h->fail(DD_ERR_STATE, "dd_pic_step before dd_factor");
+    if (!h->n_particles) return h->fail(DD_ERR_STATE, "dd_pic_step without dd_set_beam");
+    cudaStream_t s = (cudaStream_t)stream;
+    const double t_n = (double)h->step * h->dt;
+    double* dn = h->d.dep[h->dep_cur];
+    const double* dold = h->d.dep[1 - h->dep_cur];
+    const double* e_n = h->d.e[h->cur];
+    CK(h, (int)cudaMemsetAsync(dn, 0, sizeof(double) * (size_t)h->n_dof, s), "memset");
+    {
+        Prof P(h, ST_VEC, s, 2);
+        CK(h, launch_pic_move(h, t_n, h->dt, e_n, dn, s), "pic move");
+        CK(h, launch_pic_source(h, dn, dold, s), "pic source");
+    }
+    const int rc = dd_step(h, h->d.d2g_pic, nullptr, stats, stream);
+    if (rc != DD_OK && rc != DD_ERR_NO_CONVERGENCE) return rc;
+    {
+        Prof P(h, ST_VEC, s, 1);
+        CK(h, launch_faraday(h, h->d.e[h->cur], e_n, h->dt, s), "faraday");
+    }
+    h->dep_cur = 1 - h->dep_cur;
+    if (stats) {
+        int32_t err = 0;
+        CK(h, (int)cudaMemcpyAsync(&err, h->d.pic_err, 4, cudaMemcpyDeviceToHost, s), "pic err");
+        CK(h, (int)cudaStreamSynchronize(s), "sync");
+        if (err) return h->fail(DD_ERR_ARG, "a particle crossed more than 64 tets in one step");
+    }
+    return rc;
+}
+
+int dd_pic_state(const dd_handle* hc, double* x, int32_t* status, double* G, double* b, int64_t* n_faces, void* stream) {
+    dd_handle* h = const_cast<dd_handle*>(hc);
+    if (!h) return DD_ERR_ARG;
+    if (n_faces) *n_faces = h->n_faces;
+    if (!h->n_particles) return (x || status || G || b) ? h->fail(DD_ERR_STATE, "no beam") : DD_OK;
+    if (!h->bound) return h->fail(DD_ERR_STATE, "no workspace bound");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t np = (size_t)h->n_particles;
+    if (x) CK(h, (int)cudaMemcpyAsync(x, h->d.px, 3 * np * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+    if (status) CK(h, (int)cudaMemcpyAsync(status, h->d.pstat, np * sizeof(int32_t), cudaMemcpyDeviceToDevice, s), "copy");
+    if (G) CK(h, (int)cudaMemcpyAsync(G, h->d.Gcum, (size_t)h->n_dof * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+    if (b) CK(h, (int)cudaMemcpyAsync(b, h->d.bflux, (size_t)h->n_faces * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
     return DD_OK;
 }
 

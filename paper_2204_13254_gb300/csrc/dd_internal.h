@@ -128,6 +128,25 @@ struct DevPtrs {
     float* K32 = nullptr;
     double* Pinv = nullptr;          // [n_sub+1][NB*NB] pivot-block inverses while factoring
     double* dinv = nullptr;          // [n_lambda] inverse Jacobi diagonal
+    // particles (dd_set_beam): state, per-tet geometry and faces
+    double* px = nullptr;            // [n_p*3] positions
+    double* pv = nullptr;            // [n_p*3] velocities
+    double* pt = nullptr;            // [n_p] injection times
+    int32_t* ptet = nullptr;         // [n_p] current tet
+    int32_t* pstat = nullptr;        // [n_p] 0 waiting, 1 in flight, 2 stopped at a wall
+    int32_t* tets_dev = nullptr;     // [n_tets*4] node ids
+    double* tgrad = nullptr;         // [n_tets*12] barycentric gradients
+    double* tx0 = nullptr;           // [n_tets*3] coordinates of local vertex 0
+    int32_t* tface = nullptr;        // [n_tets*4] face opposite each local vertex
+    int32_t* tnbr = nullptr;         // [n_tets*4] neighbour across that face, -1 on the wall
+    int32_t* face_nodes = nullptr;   // [n_faces*3] sorted node triple
+    int32_t* face_edge = nullptr;    // [n_faces*3] dofs of edges (a,b), (b,c), (a,c); -1 on the wall
+    double* bflux = nullptr;         // [n_faces] magnetic flux (Whitney 2-form dofs)
+    double* dep[2] = {nullptr, nullptr};  // [n_dof] deposited integrated current of this / the previous step
+    double* Gcum = nullptr;          // [n_dof] integrated current g^n (sum of deposits)
+    double* d2g_pic = nullptr;       // [n_dof] source second difference of the PIC step
+    int32_t* pic_err = nullptr;      // traversal overflow flag
+
     // time levels (ring of 3) of the forward and the adjoint march
     double* e[3] = {nullptr, nullptr, nullptr};
     double* mu[3] = {nullptr, nullptr, nullptr};
@@ -221,6 +240,15 @@ struct dd_handle {
     TileCfg tile[2][GEMV_NMODES];                  // lanes per row and rows per CTA, per precision and mode
     bool tuned = false;
 
+    // particles (dd_set_beam)
+    int64_t n_particles = 0;
+    double pq = 0.0, pqm = 0.0;
+    std::vector<double> p_x, p_v, p_t;
+    std::vector<int32_t> p_tet;
+    int64_t n_faces = 0;
+    std::vector<int32_t> face_nodes, face_edge, tet_face, tet_nbr;
+    int dep_cur = 0;
+
     // probes
     int32_t n_probe = 0;
     std::vector<int32_t> probe_dof;  // 6 per probe
@@ -280,6 +308,7 @@ constexpr int kMaxPartials = 4096;   // block partials of the grid reductions
 int dd_build_host(dd_handle* h, const dd_mesh* mesh, const int32_t* part, int32_t n_sub);
 int dd_locate_probes(dd_handle* h, int32_t n, const double* xyz);
 void build_tasks(const dd_handle* h, int mode, int rows, std::vector<GemvTask>& out);
+int dd_build_beam(dd_handle* h, const dd_beam* beam);
 size_t dd_workspace_layout(dd_handle* h, bool assign);
 
 // kernels.cu launchers (return a cudaError_t value; 0 = success)
@@ -313,6 +342,9 @@ int launch_writeback(const dd_handle* h, const double* e_n, const double* e_nm1,
 int launch_advance(const dd_handle* h, const double* e_n, const double* e_nm1, const double* delta, double* e_np1,
                    void* stream);
 int launch_probe(const dd_handle* h, const double* e, double* out, void* stream);
+int launch_pic_move(const dd_handle* h, double t_n, double dt, const double* e_n, double* dep, void* stream);
+int launch_pic_source(const dd_handle* h, const double* dep_new, const double* dep_old, void* stream);
+int launch_faraday(const dd_handle* h, const double* e_np1, const double* e_n, double dt, void* stream);
 
 // GEMV x-source kinds (see kernels.cu)
 enum : int { X_FLAT = 0, X_LAMBDA = 1, X_PCG = 2, X_CORNER = 3, X_RECOVER = 4, X_COARSE = 5, X_PCG_CV = 6,

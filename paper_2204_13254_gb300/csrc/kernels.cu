@@ -879,6 +879,166 @@ __global__ void k_probe_seed(int n_probe, const int32_t* __restrict__ pd, const 
         }
 }
 
+// ----------------------------------------------------------------------------
+// Particle-in-cell coupling
+// ----------------------------------------------------------------------------
+
+__constant__ int c_edge_a[6] = {0, 0, 0, 1, 1, 2};
+__constant__ int c_edge_b[6] = {1, 2, 3, 2, 3, 3};
+
+__device__ __forceinline__ void bary(const double* __restrict__ tgrad, const double* __restrict__ tx0, int t,
+                                     const double* x, double* l) {
+    const double* g = tgrad + 12 * (int64_t)t;
+    const double dx = x[0] - tx0[3 * t], dy = x[1] - tx0[3 * t + 1], dz = x[2] - tx0[3 * t + 2];
+    l[1] = g[3] * dx + g[4] * dy + g[5] * dz;
+    l[2] = g[6] * dx + g[7] * dy + g[8] * dz;
+    l[3] = g[9] * dx + g[10] * dy + g[11] * dz;
+    l[0] = 1.0 - l[1] - l[2] - l[3];
+}
+
+__device__ __forceinline__ void cross3d(const double* a, const double* b, double* c) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// One thread per macro-particle: Boris push with E (Whitney 1-forms of e^n) and
+// B (Whitney 2-forms of the face fluxes) at x^n, then the straight path over the
+// step, cut at every face crossed, depositing q * int W_e . dl on the tet's edges.
+__global__ void k_pic_move(int64_t n_p, double t_n, double dt, double q, double qm, double* __restrict__ px,
+                           double* __restrict__ pv, const double* __restrict__ pt, int32_t* __restrict__ ptet,
+                           int32_t* __restrict__ pstat, const int32_t* __restrict__ tets,
+                           const double* __restrict__ tgrad, const double* __restrict__ tx0,
+                           const int32_t* __restrict__ tet_dof, const int32_t* __restrict__ tface,
+                           const int32_t* __restrict__ tnbr, const int32_t* __restrict__ face_nodes,
+                           const double* __restrict__ e, const double* __restrict__ bflux, double* __restrict__ dep,
+                           int32_t* __restrict__ err) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_p) return;
+    const int st = pstat[i];
+    if (st == 2) return;
+    const double t1 = t_n + dt;
+    double x[3] = {px[3 * i], px[3 * i + 1], px[3 * i + 2]};
+    double v[3] = {pv[3 * i], pv[3 * i + 1], pv[3 * i + 2]};
+    int t = ptet[i];
+    double tau;
+    if (st == 0) {
+        if (pt[i] > t1) return;
+        tau = t1 - fmax(pt[i], t_n);  // injected during this step: no push
+    } else {
+        double l[4];
+        bary(tgrad, tx0, t, x, l);
+        const double* g = tgrad + 12 * (int64_t)t;
+        const int32_t* nd = tets + 4 * (int64_t)t;
+        double E[3] = {0.0, 0.0, 0.0}, B[3] = {0.0, 0.0, 0.0};
+        for (int k = 0; k < 6; ++k) {
+            const int d = tet_dof[6 * (int64_t)t + k];
+            if (d < 0) continue;
+            const int a = c_edge_a[k], b = c_edge_b[k];
+            const double w = (nd[a] < nd[b] ? 1.0 : -1.0) * e[d];
+            for (int c = 0; c < 3; ++c) E[c] += w * (l[a] * g[3 * b + c] - l[b] * g[3 * a + c]);
+        }
+        for (int f = 0; f < 4; ++f) {
+            const int fid = tface[4 * (int64_t)t + f];
+            int lv[3];
+            for (int j = 0; j < 3; ++j) {
+                const int node = face_nodes[3 * (int64_t)fid + j];
+                lv[j] = nd[0] == node ? 0 : nd[1] == node ? 1 : nd[2] == node ? 2 : 3;
+            }
+            double c1[3], c2[3], c3[3];
+            cross3d(g + 3 * lv[1], g + 3 * lv[2], c1);
+            cross3d(g + 3 * lv[2], g + 3 * lv[0], c2);
+            cross3d(g + 3 * lv[0], g + 3 * lv[1], c3);
+            const double w = 2.0 * bflux[fid];
+            for (int c = 0; c < 3; ++c) B[c] += w * (l[lv[0]] * c1[c] + l[lv[1]] * c2[c] + l[lv[2]] * c3[c]);
+        }
+        // Boris
+        const double h = 0.5 * qm * dt;
+        double vm[3], tv[3], vp[3], sv[3], c[3];
+        for (int k = 0; k < 3; ++k) {
+            vm[k] = v[k] + h * E[k];
+            tv[k] = h * B[k];
+        }
+        cross3d(vm, tv, c);
+        for (int k = 0; k < 3; ++k) vp[k] = vm[k] + c[k];
+        const double tt = tv[0] * tv[0] + tv[1] * tv[1] + tv[2] * tv[2];
+        for (int k = 0; k < 3; ++k) sv[k] = 2.0 * tv[k] / (1.0 + tt);
+        cross3d(vp, sv, c);
+        for (int k = 0; k < 3; ++k) v[k] = vm[k] + c[k] + h * E[k];
+        tau = dt;
+    }
+    double p0[3] = {x[0], x[1], x[2]};
+    const double p1[3] = {x[0] + tau * v[0], x[1] + tau * v[1], x[2] + tau * v[2]};
+    int status = 1;
+    int it = 0;
+    for (; it < 64; ++it) {
+        double l0[4], l1[4];
+        bary(tgrad, tx0, t, p0, l0);
+        bary(tgrad, tx0, t, p1, l1);
+        double s_exit = 1.0;
+        int k_exit = -1;
+        for (int k = 0; k < 4; ++k)
+            if (l1[k] < 0.0 && l1[k] < l0[k]) {
+                const double s = fmax(l0[k], 0.0) / (l0[k] - l1[k]);
+                if (s < s_exit) {
+                    s_exit = s;
+                    k_exit = k;
+                }
+            }
+        double le[4], pe[3];
+        for (int k = 0; k < 4; ++k) le[k] = k_exit < 0 ? l1[k] : l0[k] + s_exit * (l1[k] - l0[k]);
+        for (int c = 0; c < 3; ++c) pe[c] = k_exit < 0 ? p1[c] : p0[c] + s_exit * (p1[c] - p0[c]);
+        const int32_t* nd = tets + 4 * (int64_t)t;
+        for (int k = 0; k < 6; ++k) {
+            const int d = tet_dof[6 * (int64_t)t + k];
+            if (d < 0) continue;
+            const int a = c_edge_a[k], b = c_edge_b[k];
+            const double sg = nd[a] < nd[b] ? 1.0 : -1.0;
+            atomicAdd(dep + d, q * sg * (l0[a] * le[b] - l0[b] * le[a]));
+        }
+        for (int c = 0; c < 3; ++c) p0[c] = pe[c];
+        if (k_exit < 0) break;
+        const int nb = tnbr[4 * (int64_t)t + k_exit];
+        if (nb < 0) {
+            status = 2;  // reached a wall
+            break;
+        }
+        t = nb;
+    }
+    if (it == 64) atomicExch(err, 1);
+    px[3 * i] = p0[0];
+    px[3 * i + 1] = p0[1];
+    px[3 * i + 2] = p0[2];
+    pv[3 * i] = v[0];
+    pv[3 * i + 1] = v[1];
+    pv[3 * i + 2] = v[2];
+    ptet[i] = t;
+    pstat[i] = status;
+}
+
+// d2g = dep^{n+1/2} - dep^{n-1/2};  G += dep^{n+1/2}
+__global__ void k_pic_source(int64_t n, const double* __restrict__ dn, const double* __restrict__ dold,
+                             double* __restrict__ d2g, double* __restrict__ G) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        d2g[k] = dn[k] - dold[k];
+        G[k] += dn[k];
+    }
+}
+
+// b -= dt/2 * C (e1 + e0), (C e)_f = e_ab + e_bc - e_ac on the sorted face (a,b,c)
+__global__ void k_faraday(int64_t nf, const int32_t* __restrict__ fe, const double* __restrict__ e1,
+                          const double* __restrict__ e0, double* __restrict__ b, double hdt) {
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
+        double c = 0.0;
+        const double sg[3] = {1.0, 1.0, -1.0};
+        for (int j = 0; j < 3; ++j) {
+            const int d = fe[3 * f + j];
+            if (d >= 0) c += sg[j] * (e1[d] + e0[d]);
+        }
+        b[f] -= hdt * c;
+    }
+}
+
 __global__ void k_probe(int n_probe, const int32_t* __restrict__ pd, const double* __restrict__ pw,
                         const double* __restrict__ e, double* __restrict__ out) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1109,6 +1269,27 @@ int launch_dot_sub(const dd_handle* h, const double* a, const double* b, double*
 int launch_probe_seed(const dd_handle* h, const double* e, double weight, double* seed, void* stream) {
     if (h->n_probe == 0) return 0;
     k_probe_seed<<<1, 32, 0, S(stream)>>>(h->n_probe, h->d.probe_dof, h->d.probe_w, e, weight, seed);
+    return (int)cudaGetLastError();
+}
+
+int launch_pic_move(const dd_handle* h, double t_n, double dt, const double* e_n, double* dep, void* stream) {
+    const int64_t np = h->n_particles;
+    if (np == 0) return 0;
+    k_pic_move<<<(unsigned)((np + 127) / 128), 128, 0, S(stream)>>>(
+        np, t_n, dt, h->pq, h->pqm, h->d.px, h->d.pv, h->d.pt, h->d.ptet, h->d.pstat, h->d.tets_dev, h->d.tgrad,
+        h->d.tx0, h->d.tet_dof, h->d.tface, h->d.tnbr, h->d.face_nodes, e_n, h->d.bflux, dep, h->d.pic_err);
+    return (int)cudaGetLastError();
+}
+
+int launch_pic_source(const dd_handle* h, const double* dep_new, const double* dep_old, void* stream) {
+    const int64_t nd = h->n_dof;
+    k_pic_source<<<reduce_blocks(nd), kThreads, 0, S(stream)>>>(nd, dep_new, dep_old, h->d.d2g_pic, h->d.Gcum);
+    return (int)cudaGetLastError();
+}
+
+int launch_faraday(const dd_handle* h, const double* e_np1, const double* e_n, double dt, void* stream) {
+    const int64_t nf = h->n_faces;
+    k_faraday<<<reduce_blocks(nf), kThreads, 0, S(stream)>>>(nf, h->d.face_edge, e_np1, e_n, h->d.bflux, 0.5 * dt);
     return (int)cudaGetLastError();
 }
 

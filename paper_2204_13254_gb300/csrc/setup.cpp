@@ -441,3 +441,111 @@ int dd_locate_probes(dd_handle* h, int32_t n, const double* p) {
     h->n_probe = n;
     return DD_OK;
 }
+
+// Particle set-up: faces (sorted node triples), the face opposite each local
+// vertex of every tet, tet adjacency across faces, the discrete curl's edge
+// list per face, and the boundary tet holding each injection point.
+int dd_build_beam(dd_handle* h, const dd_beam* beam) {
+    const int64_t T = h->n_tets, N = h->n_nodes, np = beam->n_particles;
+    // faces
+    std::vector<std::pair<Tri, int64_t>> fl(4 * T);
+    for (int64_t t = 0; t < T; ++t)
+        for (int f = 0; f < 4; ++f) {
+            int64_t v[3] = {h->tets[4 * t + kFace[f][0]], h->tets[4 * t + kFace[f][1]], h->tets[4 * t + kFace[f][2]]};
+            std::sort(v, v + 3);
+            fl[4 * t + f] = {Tri{v[0], v[1], v[2]}, 4 * t + f};
+        }
+    std::sort(fl.begin(), fl.end(), [](const auto& a, const auto& b) {
+        return a.first < b.first || (a.first == b.first && a.second < b.second);
+    });
+    h->tet_face.assign(4 * T, -1);
+    h->tet_nbr.assign(4 * T, -1);
+    h->face_nodes.clear();
+    int64_t nf = 0;
+    for (size_t i = 0; i < fl.size();) {
+        size_t j = i + 1;
+        while (j < fl.size() && fl[j].first == fl[i].first) ++j;
+        h->face_nodes.push_back((int32_t)fl[i].first.a);
+        h->face_nodes.push_back((int32_t)fl[i].first.b);
+        h->face_nodes.push_back((int32_t)fl[i].first.c);
+        for (size_t k = i; k < j; ++k) h->tet_face[fl[k].second] = (int32_t)nf;
+        if (j - i == 2) {
+            h->tet_nbr[fl[i].second] = (int32_t)(fl[i + 1].second / 4);
+            h->tet_nbr[fl[i + 1].second] = (int32_t)(fl[i].second / 4);
+        }
+        ++nf;
+        i = j;
+    }
+    h->n_faces = nf;
+    // discrete curl: dofs of edges (a,b), (b,c), (a,c) of every sorted face
+    std::vector<int64_t> key(h->n_edges);
+    for (int64_t e = 0; e < h->n_edges; ++e) key[e] = h->edges[2 * e] * N + h->edges[2 * e + 1];
+    std::vector<int64_t> edge_dof(h->n_edges, -1);
+    for (int64_t d = 0; d < h->n_dof; ++d) edge_dof[h->dof_edge[d]] = d;
+    auto dof_of = [&](int64_t a, int64_t b) {
+        const int64_t e = std::lower_bound(key.begin(), key.end(), a * N + b) - key.begin();
+        return (int32_t)edge_dof[e];
+    };
+    h->face_edge.resize(3 * nf);
+    for (int64_t f = 0; f < nf; ++f) {
+        const int64_t a = h->face_nodes[3 * f], b = h->face_nodes[3 * f + 1], c = h->face_nodes[3 * f + 2];
+        h->face_edge[3 * f] = dof_of(a, b);
+        h->face_edge[3 * f + 1] = dof_of(b, c);
+        h->face_edge[3 * f + 2] = dof_of(a, c);
+    }
+    // injection tets: candidates are the tets with a wall face, binned on a coarse grid
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int64_t i = 0; i < N; ++i)
+        for (int c = 0; c < 3; ++c) {
+            lo[c] = std::min(lo[c], h->xyz[3 * i + c]);
+            hi[c] = std::max(hi[c], h->xyz[3 * i + c]);
+        }
+    const int G = 32;
+    auto cell = [&](double x, int c) {
+        const double w = (hi[c] - lo[c]) > 0 ? (hi[c] - lo[c]) : 1.0;
+        return std::min(G - 1, std::max(0, (int)((x - lo[c]) / w * G)));
+    };
+    std::vector<std::vector<int32_t>> bins((size_t)G * G * G);
+    for (int64_t t = 0; t < T; ++t) {
+        bool wall = false;
+        for (int f = 0; f < 4; ++f) wall |= h->tet_nbr[4 * t + f] < 0;
+        if (!wall) continue;
+        double tl[3] = {1e300, 1e300, 1e300}, th[3] = {-1e300, -1e300, -1e300};
+        for (int v = 0; v < 4; ++v)
+            for (int c = 0; c < 3; ++c) {
+                const double x = h->xyz[3 * (int64_t)h->tets[4 * t + v] + c];
+                tl[c] = std::min(tl[c], x);
+                th[c] = std::max(th[c], x);
+            }
+        for (int i = cell(tl[0] - 1e-9, 0); i <= cell(th[0] + 1e-9, 0); ++i)
+            for (int j = cell(tl[1] - 1e-9, 1); j <= cell(th[1] + 1e-9, 1); ++j)
+                for (int k = cell(tl[2] - 1e-9, 2); k <= cell(th[2] + 1e-9, 2); ++k)
+                    bins[((size_t)i * G + j) * G + k].push_back((int32_t)t);   // tets visited in id order
+    }
+    h->p_x.assign(beam->x_inj, beam->x_inj + 3 * np);
+    h->p_v.assign(beam->v_inj, beam->v_inj + 3 * np);
+    h->p_t.assign(beam->t_inj, beam->t_inj + np);
+    h->p_tet.assign(np, -1);
+    for (int64_t p = 0; p < np; ++p) {
+        const double* x = &h->p_x[3 * p];
+        if (!(h->p_t[p] >= 0.0)) return h->fail(DD_ERR_ARG, "negative injection time");
+        const auto& cand = bins[((size_t)cell(x[0], 0) * G + cell(x[1], 1)) * G + cell(x[2], 2)];
+        for (int32_t t : cand) {
+            const double* g = &h->grad[12 * (int64_t)t];
+            const double* x0 = &h->xyz[3 * (int64_t)h->tets[4 * (int64_t)t]];
+            const double dx[3] = {x[0] - x0[0], x[1] - x0[1], x[2] - x0[2]};
+            const double l1 = dot3(g + 3, dx), l2 = dot3(g + 6, dx), l3 = dot3(g + 9, dx);
+            const double l0 = 1.0 - l1 - l2 - l3;
+            if (l0 >= -1e-12 && l1 >= -1e-12 && l2 >= -1e-12 && l3 >= -1e-12) {
+                h->p_tet[p] = t;
+                break;
+            }
+        }
+        if (h->p_tet[p] < 0)
+            return h->fail(DD_ERR_ARG, "injection point " + std::to_string(p) + " is not on the mesh boundary");
+    }
+    h->n_particles = np;
+    h->pq = beam->q;
+    h->pqm = beam->qm;
+    return DD_OK;
+}

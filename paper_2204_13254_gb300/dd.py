@@ -21,7 +21,8 @@ DD_FP64, DD_MIXED = 0, 1
 
 SYMBOLS = ["dd_setup", "dd_set_params", "dd_get_sizes", "dd_get_maps", "dd_set_probes", "dd_bind_workspace",
            "dd_factor", "dd_step", "dd_schur_apply", "dd_schur_apply_static", "dd_probe", "dd_adjoint_reset",
-           "dd_adjoint_step", "dd_probe_seed", "dd_autotune", "dd_get_tiles", "dd_get_state", "dd_set_state", "dd_profile",
+           "dd_adjoint_step", "dd_probe_seed", "dd_autotune", "dd_get_tiles", "dd_set_beam", "dd_pic_step",
+           "dd_pic_state", "dd_get_state", "dd_set_state", "dd_profile",
            "dd_destroy", "dd_last_error"]
 N_STAGES = 9
 STAGES = ["rhs", "local_solve", "iface_apply", "coarse", "corner", "recover", "vector", "refine", "factor"]
@@ -55,6 +56,11 @@ class dd_stats(C.Structure):
     _fields_ = [("iters", C.c_int), ("refinements", C.c_int), ("resid", C.c_double), ("status", C.c_int)]
 
 
+class dd_beam(C.Structure):
+    _fields_ = [("n_particles", C.c_int64), ("x_inj", C.POINTER(C.c_double)), ("v_inj", C.POINTER(C.c_double)),
+                ("t_inj", C.POINTER(C.c_double)), ("q", C.c_double), ("qm", C.c_double)]
+
+
 class dd_profile_stats(C.Structure):
     _fields_ = [("launches", C.c_int64 * N_STAGES), ("work", C.c_int64 * N_STAGES), ("ms", C.c_double * N_STAGES),
                 ("bytes", C.c_double * N_STAGES), ("total_launches", C.c_int64)]
@@ -85,6 +91,9 @@ def load_library(path: str = LIB_PATH):
         "dd_probe_seed": (C.c_int, [vp, vp, C.c_double, vp, vp]),
         "dd_autotune": (C.c_int, [vp, C.c_char_p, C.POINTER(C.c_double), vp]),
         "dd_get_tiles": (C.c_int, [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+        "dd_set_beam": (C.c_int, [vp, C.POINTER(dd_beam)]),
+        "dd_pic_step": (C.c_int, [vp, C.POINTER(dd_stats), vp]),
+        "dd_pic_state": (C.c_int, [vp, vp, vp, vp, vp, C.POINTER(C.c_int64), vp]),
         "dd_destroy": (None, [vp]),
         "dd_last_error": (C.c_char_p, [vp]),
     }
@@ -235,6 +244,27 @@ def dd_probe_seed(h, e, weight, seed, stream=None):
     _check(h, lib().dd_probe_seed(h, _ptr(e), float(weight), _ptr(seed), _stream(stream)))
 
 
+def dd_set_beam(h, x_inj, v_inj, t_inj, q, qm):
+    x = np.ascontiguousarray(x_inj, dtype=np.float64).reshape(-1, 3)
+    v = np.ascontiguousarray(v_inj, dtype=np.float64).reshape(-1, 3)
+    t = np.ascontiguousarray(t_inj, dtype=np.float64)
+    dp = C.POINTER(C.c_double)
+    b = dd_beam(len(x), x.ctypes.data_as(dp), v.ctypes.data_as(dp), t.ctypes.data_as(dp), float(q), float(qm))
+    _check(h, lib().dd_set_beam(h, C.byref(b)))
+
+
+def dd_pic_step(h, stats=True, stream=None):
+    st = dd_stats()
+    _check(h, lib().dd_pic_step(h, C.byref(st) if stats else None, _stream(stream)))
+    return dict(iters=st.iters, refinements=st.refinements, resid=st.resid, status=st.status)
+
+
+def dd_pic_state(h, x=None, status=None, G=None, b=None, stream=None):
+    nf = C.c_int64()
+    _check(h, lib().dd_pic_state(h, _ptr(x), _ptr(status), _ptr(G), _ptr(b), C.byref(nf), _stream(stream)))
+    return nf.value
+
+
 GEMV_KINDS = ["local", "corner_rows", "corner_coupling", "recover", "coarse", "iface_rows"]
 
 
@@ -322,6 +352,26 @@ class FieldSolver:
         out = torch.empty_like(lam)
         dd_schur_apply(self.h, lam, out)
         return out
+
+    def set_beam(self, x_inj, v_inj, t_inj, q, qm):
+        """Particles for dd_pic_step (before bind())."""
+        dd_set_beam(self.h, x_inj, v_inj, t_inj, q, qm)
+        self.n_particles = len(np.asarray(t_inj))
+        self.sizes = dd_get_sizes(self.h)
+        return self
+
+    def pic_step(self, stats=True):
+        return dd_pic_step(self.h, stats)
+
+    def pic_state(self):
+        import torch
+        nf = dd_pic_state(self.h)
+        x = torch.empty(3 * self.n_particles, dtype=torch.float64, device=self.device)
+        st = torch.empty(self.n_particles, dtype=torch.int32, device=self.device)
+        G = torch.empty(self.n_dof, dtype=torch.float64, device=self.device)
+        b = torch.empty(nf, dtype=torch.float64, device=self.device)
+        dd_pic_state(self.h, x, st, G, b)
+        return x.view(-1, 3), st, G, b
 
     def probe(self):
         import torch

@@ -236,6 +236,21 @@ def box(nx, ny, nz, kx, ky, kz, L=(1.0, 1.0, 1.0), steps=200, probes=None, eps=N
                     probes=np.asarray(probes, dtype=np.float64), dims=(nx, ny, nz), L=tuple(L))
 
 
+def beam(w: Workload, n_particles: int, t_max: float, speed: float = 0.1, sigma: float = 0.05, q: float = -1e-6,
+         qm: float = -1.0, seed: int = 0, clip: float = 0.45):
+    """Electron-like beam entering through the z = 0 wall on the axis x = y = L/2.
+
+    Transverse offsets ~ N(0, sigma^2) clipped to +-clip, velocity (0, 0, speed),
+    injection times ~ U[0, t_max) (seeded).  Returns (x_inj, v_inj, t_inj, q, qm).
+    """
+    rng = np.random.default_rng(seed)
+    off = np.clip(rng.normal(0.0, sigma, size=(n_particles, 2)), -clip, clip)
+    x = np.column_stack([w.L[0] / 2 + off[:, 0], w.L[1] / 2 + off[:, 1], np.zeros(n_particles)])
+    v = np.tile([0.0, 0.0, speed], (n_particles, 1))
+    t = rng.uniform(0.0, t_max, size=n_particles)
+    return x, v, t, q, qm
+
+
 PROBES_ADJOINT = np.array([[0.2, 0.3, 0.4], [0.7, 0.6, 0.3], [0.4, 0.8, 0.7], [0.6, 0.25, 0.8]])
 
 
