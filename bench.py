@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--eager", action="store_true", help="time eager launches instead of the CUDA-graph step")
     ap.add_argument("--chunk", type=int, default=2, help="CG iterations per graph WHILE-body launch")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default GEMV tiles")
+    ap.add_argument("--warm", type=int, default=1, help="interface-CG warm start: 1 previous step, 2 extrapolated")
     ap.add_argument("--cavity", type=int, nargs=2, metavar=("N", "K"), default=None,
                     help="profiling case: unit PEC cavity of N^3 cubes in K^3 subdomains instead of --config "
                          "(dt = the 48^3 cavity's dt scaled by 48/N)")
@@ -275,12 +276,13 @@ def run_ours(args, rank, world, local):
     clocks = Clocks(local)
     g = 0 if args.eager else 1
     ch = 8 if args.eager else args.chunk
-    p64 = D.make_params(precision=D.DD_FP64, tol=args.tol64, use_graph=g, chunk=ch)
+    p64 = D.make_params(precision=D.DD_FP64, tol=args.tol64, use_graph=g, chunk=ch, warm_start=args.warm)
     p32 = D.make_params(precision=D.DD_MIXED, tol=args.tol32, refine_tol=args.refine_tol, max_refine=6, use_graph=g,
-                        chunk=ch)
+                        chunk=ch, warm_start=args.warm)
     # event profiling needs eager launches (events are recorded around every launch)
-    p64e = D.make_params(precision=D.DD_FP64, tol=args.tol64)
-    p32e = D.make_params(precision=D.DD_MIXED, tol=args.tol32, refine_tol=args.refine_tol, max_refine=6)
+    p64e = D.make_params(precision=D.DD_FP64, tol=args.tol64, warm_start=args.warm)
+    p32e = D.make_params(precision=D.DD_MIXED, tol=args.tol32, refine_tol=args.refine_tol, max_refine=6,
+                         warm_start=args.warm)
     nan = float("nan")
     ms64 = ms32 = nan
     it64 = it32 = ref32 = np.zeros(1)
@@ -486,6 +488,7 @@ def main():
                 "h2d_bytes_per_step": int(sizes.n_dof * 8), "d2h_bytes_per_step": int(sizes.n_dof * 8)},
         "gpu_launches": int(r["launches32"] if head == "mixed" else r["launches64"]),
         "launch_mode": "eager" if args.eager else f"CUDA graph per step (CG WHILE node, {args.chunk} it/body)",
+        "warm_start": {1: "previous step's multipliers", 2: "extrapolated multipliers 2l(n-1)-l(n-2)"}.get(args.warm, args.warm),
         "clocks": r["clocks"],
     }
     print(json.dumps(_clean(line)), flush=True)

@@ -81,7 +81,10 @@ typedef struct {
  * max_it     CG iteration cap per solve.
  * precond    0 = none, 1 = Jacobi (diagonal of F_rr; the paper's diagonal
  *            preconditioner of Sec. III-C).
- * warm_start 1 = start each interface solve from the previous multipliers.
+ * warm_start 1 = start each interface solve from the previous multipliers;
+ *            2 = start the first solve of a step from the linear extrapolation
+ *            2 lambda^{n-1} - lambda^{n-2} of the previous steps' multipliers
+ *            (once two steps of history exist; the adjoint march uses 1).
  * refine_tol DD_MIXED only: stop refining a step when the FP64 residual of the
  *            step's linear system satisfies ||r||_2 <= refine_tol * ||b||_2.
  * max_refine DD_MIXED only: cap on FP32 correction solves per step.

@@ -206,6 +206,8 @@ size_t dd_workspace_layout(dd_handle* h, bool assign) {
     for (int k = 0; k < 3; ++k) L.take(d.mu[k], nd);
     L.take(d.lam_adj, nm);
     L.take(d.lamf_adj, nm);
+    L.take(d.lam_prev, nm);
+    L.take(d.lam_prev_adj, nm);
     L.take(d.tet_dof, 6 * (size_t)h->n_tets);
     L.take(d.That, 36 * (size_t)h->n_tets);
     {
@@ -743,6 +745,8 @@ int dd_factor(dd_handle* h, double dt, void* stream) {
         if (prc) return prc;
     }
     CK(h, (int)cudaStreamSynchronize(s), "sync");
+    CK(h, (int)cudaMemsetAsync(&h->d.sc->lam_levels, 0, sizeof(int32_t), s), "memset");
+    CK(h, (int)cudaStreamSynchronize(s), "sync");
     h->dt = dt;
     h->step = 0;
     h->cur = 0;
@@ -755,6 +759,21 @@ int dd_factor(dd_handle* h, double dt, void* stream) {
 
 namespace {
 
+// warm_start 2: before the first solve of a step, lambda_0 = 2 lambda^{n-1} -
+// lambda^{n-2} once two levels of history exist (a device counter), so that
+// eager and graph launches extrapolate on the same steps.
+int extrapolate_lambda(dd_handle* h, int prec, cudaStream_t s) {
+    if (h->prm.warm_start != 2 || h->mult_dof.empty()) return DD_OK;
+    const size_t nm = h->mult_dof.size();
+    if (!h->lam_valid && !h->capturing) {
+        CK(h, (int)cudaMemsetAsync(h->d.lam, 0, sizeof(double) * nm, s), "memset");
+        CK(h, (int)cudaMemsetAsync(h->d.lamf, 0, sizeof(float) * nm, s), "memset");
+    }
+    Prof P(h, ST_VEC, s, 2);
+    CK(h, launch_extrapolate(h, prec == DD_MIXED ? h->d.lamf : nullptr, s), "extrapolate");
+    return DD_OK;
+}
+
 // One level of the Newmark recurrence from (u_n, u_nm1) into u_np1:
 // A delta = -dt^2 S u_n + src_sign * src (subassembled, source on the owner),
 // u_np1 = 2 u_n - u_nm1 + delta.  Used by the forward step (src = d2g, sign -1)
@@ -766,6 +785,10 @@ int advance(dd_handle* h, const double* u_n, const double* u_nm1, double* u_np1,
     {
         Prof P(h, ST_RHS, s, 1, h->bytes_per_launch[ST_RHS]);
         CK(h, launch_rhs(h, u_n, src, src_sign, h->dt, s), "rhs");
+    }
+    {
+        const int xrc = extrapolate_lambda(h, h->prm.precision, s);
+        if (xrc) return xrc;
     }
     if (h->prm.precision == DD_FP64) {
         status = dd_solve(h, DD_FP64, h->prm.tol, h->prm.warm_start != 0, &iters, &resid, s);
@@ -899,6 +922,10 @@ int step_body_graph(dd_handle* h, const double* u_n, const double* u_nm1, double
     }
     int it = 0;
     double r = 0.0;
+    {
+        const int xrc = extrapolate_lambda(h, h->prm.precision, s);
+        if (xrc) return xrc;
+    }
     if (h->prm.precision == DD_FP64) {
         int rc = dd_solve(h, DD_FP64, h->prm.tol, h->prm.warm_start != 0, &it, &r, s, 0, 0);
         if (rc) return rc;
@@ -1032,6 +1059,7 @@ int dd_step_graph(dd_handle* h, const double* d2g, double* e_out, dd_stats* stat
 void swap_lambda(dd_handle* h) {
     std::swap(h->d.lam, h->d.lam_adj);
     std::swap(h->d.lamf, h->d.lamf_adj);
+    std::swap(h->d.lam_prev, h->d.lam_prev_adj);
     std::swap(h->lam_valid, h->lam_adj_valid);
 }
 
@@ -1086,7 +1114,10 @@ int dd_adjoint_step(dd_handle* h, const double* seed, const double* e_k, const d
     double resid = 0.0;
     // A mu^k = B mu^{k+1} - A mu^{k+2} + seed   (A, B symmetric: same factors as the forward march)
     swap_lambda(h);
+    const int ws = h->prm.warm_start;
+    h->prm.warm_start = std::min(ws, 1);   // the extrapolation history belongs to the forward march
     const int status = advance(h, mu_k1, mu_k2, mu_k, seed, +1.0, &iters, &refinements, &resid, s);
+    h->prm.warm_start = ws;
     swap_lambda(h);
     if (status != DD_OK && status != DD_ERR_NO_CONVERGENCE) return status;
     h->cur_adj = (h->cur_adj + 1) % 3;
@@ -1157,6 +1188,7 @@ int dd_set_state(dd_handle* h, const double* e_n, const double* e_nm1, int64_t s
     h->cur = 0;
     CK(h, (int)cudaMemcpyAsync(h->d.e[0], e_n, nb, cudaMemcpyDeviceToDevice, s), "copy");
     CK(h, (int)cudaMemcpyAsync(h->d.e[2], e_nm1, nb, cudaMemcpyDeviceToDevice, s), "copy");
+    CK(h, (int)cudaMemsetAsync(&h->d.sc->lam_levels, 0, sizeof(int32_t), s), "memset");
     h->step = step;
     h->lam_valid = false;
     return DD_OK;

@@ -90,6 +90,8 @@ struct PcgScalars {
     int32_t pad;
     double norm_b2;   // mixed mode: ||b||^2 of the step system
     double norm_r2;   // mixed mode: ||r||^2 of the current FP64 residual
+    int32_t lam_levels;   // warm_start 2: multiplier history levels available (0, 1, 2)
+    int32_t pad3;
     int32_t it_total;     // graph mode: CG iterations of the whole step
     int32_t refinements;  // graph mode: solves of the whole step
     int32_t step_status;  // graph mode: DD status of the whole step
@@ -151,6 +153,8 @@ struct DevPtrs {
     double* e[3] = {nullptr, nullptr, nullptr};
     double* mu[3] = {nullptr, nullptr, nullptr};
     double* lam_adj = nullptr;       // adjoint multipliers (warm start), swapped with lam
+    double* lam_prev = nullptr;      // multipliers of the step before (warm_start 2 extrapolation)
+    double* lam_prev_adj = nullptr;
     float* lamf_adj = nullptr;
     int32_t* tet_dof = nullptr;      // [n_tets*6] dof of each tet edge, -1 on the PEC wall
     double* That = nullptr;          // [n_tets*36] unit-eps oriented element mass matrices
@@ -333,6 +337,7 @@ int launch_jump(const dd_handle* h, const double* w, const float* wf, const doub
 int launch_pcg_init(const dd_handle* h, int have_q, double tol, const float* wf, float* zf, float* pf,
                     unsigned long long cond, int adaptive, void* stream);
 int launch_step_begin(const dd_handle* h, void* stream);
+int launch_extrapolate(const dd_handle* h, float* lamf, void* stream);
 int launch_solve_end(const dd_handle* h, void* stream);
 int launch_refine_cond(const dd_handle* h, unsigned long long cond, void* stream);
 int launch_pcg_alpha(const dd_handle* h, const float* wf, float* pf, void* stream);

@@ -748,6 +748,26 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(int64_t n_lambda, const
     }
 }
 
+// warm_start 2: lambda <- 2 lambda - lambda_prev (linear extrapolation in time of the
+// previous two steps' multipliers) once two levels exist; lambda_prev <- old lambda.
+__global__ void k_extrapolate(int64_t n, double* __restrict__ lam, double* __restrict__ prev, float* __restrict__ lamf,
+                              PcgScalars* sc) {
+    const int levels = sc->lam_levels;
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < n; m += (int64_t)gridDim.x * blockDim.x) {
+        const double l = lam[m];
+        if (levels >= 2) {
+            const double x = 2.0 * l - prev[m];
+            lam[m] = x;
+            if (lamf) lamf[m] = (float)x;
+        }
+        prev[m] = l;
+    }
+}
+
+__global__ void k_levels_inc(PcgScalars* sc) {
+    if (sc->lam_levels < 2) sc->lam_levels += 1;
+}
+
 // graph mode: per-step counters
 __global__ void k_step_begin(PcgScalars* sc) {
     sc->it_total = 0;
@@ -1204,6 +1224,14 @@ int launch_pcg_init(const dd_handle* h, int have_q, double tol, const float* wf,
                                                               h->prm.precond ? h->d.dinv : nullptr, tol, h->d.r, h->d.z,
                                                               h->d.p, zf, pf, h->d.sc, h->d.partials, cond, adaptive,
                                                               h->prm.refine_tol);
+    return (int)cudaGetLastError();
+}
+
+int launch_extrapolate(const dd_handle* h, float* lamf, void* stream) {
+    const int64_t nl = (int64_t)h->mult_dof.size();
+    if (nl == 0) return 0;
+    k_extrapolate<<<reduce_blocks(nl), kThreads, 0, S(stream)>>>(nl, h->d.lam, h->d.lam_prev, lamf, h->d.sc);
+    k_levels_inc<<<1, 1, 0, S(stream)>>>(h->d.sc);
     return (int)cudaGetLastError();
 }
 

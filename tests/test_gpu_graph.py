@@ -33,13 +33,13 @@ def march(w, dt, n, prm, stats=True):
     return np.array(F), S
 
 
-@pytest.mark.parametrize("prec", [D.DD_FP64, D.DD_MIXED])
-def test_graph_equals_eager(prec):
+@pytest.mark.parametrize("prec,warm", [(D.DD_FP64, 1), (D.DD_MIXED, 1), (D.DD_FP64, 2), (D.DD_MIXED, 2)])
+def test_graph_equals_eager(prec, warm):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     w = W.config(1)
     dt = json.load(open(os.path.join(GOLD, "cfl_dt.json")))["config1"]["dt"]
-    kw = dict(precision=prec, tol=1e-12 if prec == D.DD_FP64 else 1e-6, refine_tol=1e-12, max_refine=5)
+    kw = dict(precision=prec, tol=1e-12 if prec == D.DD_FP64 else 1e-6, refine_tol=1e-12, max_refine=5, warm_start=warm)
     Fe, Se = march(w, dt, 40, D.make_params(**kw, chunk=8, use_graph=0))
     Fg, Sg = march(w, dt, 40, D.make_params(**kw, chunk=2, use_graph=1))
     assert np.array_equal(Fe, Fg)

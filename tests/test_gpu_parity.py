@@ -218,3 +218,19 @@ def test_error_status_without_fault():
     fs.set_params(D.make_params(tol=1e-12))
     assert fs.step(src)["status"] == 0
     fs.close()
+
+
+@pytest.mark.parametrize("prec", [D.DD_FP64, D.DD_MIXED])
+def test_extrapolated_warm_start_matches_oracle(prec):
+    """warm_start 2 (lambda_0 = 2 lambda^{n-1} - lambda^{n-2}) changes only the CG start."""
+    need_gpu()
+    w = W.config(1)
+    dt = DT["config1"]["dt"]
+    n = 200
+    _, _, _, _, ref = oracle_run(w, dt, n)
+    prm = D.make_params(precision=prec, tol=1e-13 if prec == D.DD_FP64 else 1e-6, refine_tol=1e-12, max_refine=6,
+                        warm_start=2)
+    fs, f, _, stats = gpu_run(w, dt, n, prm, probes=False)
+    err = rel_err(f, ref["fields"])
+    assert err[2:].max() <= (1e-10 if prec == D.DD_FP64 else 1e-8), err.max()
+    fs.close()
