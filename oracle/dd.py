@@ -24,6 +24,14 @@ subdomain of a tet is given).  Readings of the paper used here:
   preconditioner) is taken as CG, the Schur system being symmetric positive
   definite, with the Jacobi preconditioner diag(F_rr); it stops when
   ||r_k|| <= tol ||rhs||.
+* The coupled variant (end of Sec. III-A; Fig. fetiIter) solves Eqs. F1lr and
+  F1uc together for u = [lambda; x_c]:
+      [ F_rr     F_rc ] [lambda]   [d_r ]
+      [ -F_rc^T  K~cc ] [x_c   ] = [f~_c]
+  with restarted GMRES (oracle.gmres) and the diagonal preconditioner
+  diag(F_rr) (+) diag(K~cc).  The matrix is not symmetric; its symmetric part
+  is blockdiag(F_rr, K~cc), positive definite, so GMRES(m) converges.  The warm
+  start is the previous step's [lambda; x_c].
 * The local right-hand side L^(i) is the subassembled Newmark right side
   B^(i) e^n - A^(i) e^{n-1} on the (consistent) local copies of the fields,
   plus the source on the lowest-id subdomain that owns the edge.  The global
@@ -33,6 +41,8 @@ from __future__ import annotations
 
 import numpy as np
 import scipy.linalg as sla
+
+from .gmres import gmres
 
 
 class DDMaps:
@@ -124,7 +134,9 @@ class DDSolver:
                 s, li = maps.mult_sub[k, side], maps.mult_loc[k, side]
                 u = np.zeros(maps.nr[s]); u[li] = 1.0
                 self.diag[k] += sla.cho_solve(self.chol[s], u)[li]
+        self.diag_c = np.diag(self.Acc_tilde).copy()
         self.lam = np.zeros(maps.n_lambda)
+        self.xc = np.zeros(maps.n_corner)
 
     # -- Boolean maps ---------------------------------------------------------
     def Br_T(self, lam, s):
@@ -184,12 +196,27 @@ class DDSolver:
             out = out + self.F_rc(self.Kcc_solve(self.F_rcT(lam)))
         return out
 
-    # -- one solve ------------------------------------------------------------
-    def solve(self, b_local, tol=1e-14, max_it=1000, warm=True):
-        """Solve the torn system for local right-hand sides b_local[s] (length n_s).
+    def coupled_apply(self, u):
+        """[F_rr lambda + F_rc x_c ; -F_rc^T lambda + K~cc x_c]   (Eqs. F1lr, F1uc)."""
+        nl = self.maps.n_lambda
+        lam, xc = u[:nl], u[nl:]
+        top = self.F_rr(lam) + self.F_rc(xc)
+        bottom = self.Acc_tilde @ xc - self.F_rcT(lam)
+        return np.concatenate([top, bottom])
 
-        Returns (x_local list, lambda, x_c, iterations, final relative residual).
-        """
+    def recover(self, b_local, lam, x_c):
+        """x_r = A_rr^-1 (b_r - A_rc B_c x_c - B_r^T lambda) per subdomain   (Eq. rF1)."""
+        m = self.maps
+        x = []
+        for s in range(m.n_sub):
+            nr = m.nr[s]
+            xc_s = x_c[m.corner_of_local[s]]
+            xr = self.Arr_solve(s, b_local[s][:nr] - self.A[s][:nr, nr:] @ xc_s - self.Br_T(lam, s))
+            x.append(np.concatenate([xr, xc_s]))
+        return x
+
+    def rhs_parts(self, b_local):
+        """d_r = sum B_r A_rr^-1 b_r and f~_c = sum B_c^T (b_c - A_cr A_rr^-1 b_r)."""
         m = self.maps
         y = []
         fc_parts = []
@@ -198,8 +225,37 @@ class DDSolver:
             ys = self.Arr_solve(s, b_local[s][:nr])
             y.append(ys)
             fc_parts.append(b_local[s][nr:] - self.A[s][nr:, :nr] @ ys)
-        d_r = self.Br_sum(y)
-        f_c = self.Bc_sum(fc_parts)
+        return self.Br_sum(y), self.Bc_sum(fc_parts)
+
+    def solve_coupled(self, b_local, tol=1e-6, max_it=1000, warm=True, restart=20):
+        """Coupled solve of Eqs. F1lr + F1uc by GMRES(restart) with the diagonal preconditioner.
+
+        Returns (x_local list, lambda, x_c, iterations, relative residual estimate)."""
+        m = self.maps
+        d_r, f_c = self.rhs_parts(b_local)
+        b = np.concatenate([d_r, f_c])
+        x0 = np.concatenate([self.lam, self.xc]) if warm else np.zeros(len(b))
+        dinv = np.concatenate([1.0 / self.diag, 1.0 / self.diag_c])
+        it, res = 0, 0.0
+        u = x0
+        if len(b):
+            u, it, res, _ = gmres(self.coupled_apply, b, x0, dinv, tol, restart, max_it)
+        lam, x_c = u[:m.n_lambda].copy(), u[m.n_lambda:].copy()
+        self.lam, self.xc = lam, x_c
+        return self.recover(b_local, lam, x_c), lam, x_c, it, res
+
+    # -- one solve ------------------------------------------------------------
+    def solve(self, b_local, tol=1e-14, max_it=1000, warm=True, solver="cg", restart=20):
+        """Solve the torn system for local right-hand sides b_local[s] (length n_s).
+
+        solver "cg": Schur form (Eq. f1schur) with Jacobi CG; "gmres": coupled
+        form (Eqs. F1lr + F1uc) with GMRES(restart).
+        Returns (x_local list, lambda, x_c, iterations, final relative residual).
+        """
+        if solver == "gmres":
+            return self.solve_coupled(b_local, tol, max_it, warm, restart)
+        m = self.maps
+        d_r, f_c = self.rhs_parts(b_local)
         rhs = d_r - (self.F_rc(self.Kcc_solve(f_c)) if m.n_corner else 0.0)
         lam = self.lam.copy() if warm else np.zeros(m.n_lambda)
         r = rhs - self.schur_apply(lam)
@@ -223,12 +279,8 @@ class DDSolver:
                 rz = rz_new
         self.lam = lam
         x_c = self.Kcc_solve(f_c + self.F_rcT(lam)) if m.n_corner else np.zeros(0)
-        x = []
-        for s in range(m.n_sub):
-            nr = m.nr[s]
-            xc_s = x_c[m.corner_of_local[s]]
-            xr = self.Arr_solve(s, b_local[s][:nr] - self.A[s][:nr, nr:] @ xc_s - self.Br_T(lam, s))
-            x.append(np.concatenate([xr, xc_s]))
+        self.xc = x_c
+        x = self.recover(b_local, lam, x_c)
         res = np.linalg.norm(rhs - self.schur_apply(lam)) / nrm0 if nrm0 > 0 else 0.0
         return x, lam, x_c, it, res
 
@@ -253,23 +305,23 @@ class DDSolver:
         return out
 
 
-def run(space, maps, dt, src, d2g, n_steps, tol=1e-14, P=None, keep=False):
+def run(space, maps, dt, src, d2g, n_steps, tol=1e-14, P=None, keep=False, solver="cg", restart=20):
     """Newmark march with every step solved by the CPU MFETI-DP1 solver."""
-    solver = DDSolver(space, maps, dt)
+    dd = DDSolver(space, maps, dt)
     e_nm1 = np.zeros(space.n)
     e_n = np.zeros(space.n)
     its, probes, fields = [], [], []
     for k in range(n_steps):
-        b = solver.newmark_rhs(e_n, e_nm1, d2g[k] * src)
-        x, lam, xc, it, res = solver.solve(b, tol=tol)
-        e_np1 = solver.gather_global(x)
+        b = dd.newmark_rhs(e_n, e_nm1, d2g[k] * src)
+        x, lam, xc, it, res = dd.solve(b, tol=tol, solver=solver, restart=restart)
+        e_np1 = dd.gather_global(x)
         e_nm1, e_n = e_n, e_np1
         its.append(it)
         if P is not None:
             probes.append(P @ e_n)
         if keep:
             fields.append(e_n.copy())
-    out = dict(e_n=e_n, e_nm1=e_nm1, iters=np.array(its), solver=solver)
+    out = dict(e_n=e_n, e_nm1=e_nm1, iters=np.array(its), solver=dd)
     if P is not None:
         out["probes"] = np.array(probes)
     if keep:
