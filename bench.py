@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--chunk", type=int, default=2, help="CG iterations per graph WHILE-body launch")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default GEMV tiles")
     ap.add_argument("--warm", type=int, default=1, help="interface-CG warm start: 1 previous step, 2 extrapolated")
+    ap.add_argument("--no-gmres", action="store_true",
+                    help="skip the coupled-GMRES(20) vs Schur-CG comparison at the paper's tolerance 1e-6")
     ap.add_argument("--cavity", type=int, nargs=2, metavar=("N", "K"), default=None,
                     help="profiling case: unit PEC cavity of N^3 cubes in K^3 subdomains instead of --config "
                          "(dt = the 48^3 cavity's dt scaled by 48/N)")
@@ -294,6 +296,21 @@ def run_ours(args, rank, world, local):
     if args.only in (None, "mixed"):
         ms32, it32, ref32, prof32, e32 = run_steps(p32, False, clocks)
     rel = float(torch.linalg.norm(e32 - e64) / torch.linalg.norm(e64)) if e32 is not None and e64 is not None else nan
+    # the paper's coupled solve (Eqs. F1lr + F1uc, GMRES(20), tol 1e-6, diagonal preconditioner)
+    # beside the Schur CG at the same tolerance, both FP64, same launch mode
+    gm = None
+    if not args.no_gmres and not pic:
+        tol_p = 1e-6
+        pg = D.make_params(precision=D.DD_FP64, tol=tol_p, use_graph=g, chunk=ch, solver=D.DD_SOLVER_COUPLED_GMRES,
+                           restart=20)
+        pc = D.make_params(precision=D.DD_FP64, tol=tol_p, use_graph=g, chunk=ch)
+        msg, itg, _, profg, eg = run_steps(pg, False)
+        msc, itc, _, _, ec = run_steps(pc, False)
+        gm = {"tol": tol_p, "restart": 20,
+              "gmres": {"steps_per_s": K * 1e3 / msg, "ms_per_step": msg / K, "iters_per_step": float(np.mean(itg)),
+                        "gpu_launches": int(profg["total_launches"])},
+              "schur_cg": {"steps_per_s": K * 1e3 / msc, "ms_per_step": msc / K, "iters_per_step": float(np.mean(itc))},
+              "rel_diff_fields": float(torch.linalg.norm(eg - ec) / torch.linalg.norm(ec))}
     # per-stage breakdown: a second pass over the same steps with CUDA events around every launch
     launches64 = prof64["total_launches"] if prof64 else None
     launches32 = prof32["total_launches"] if prof32 else None
@@ -338,7 +355,7 @@ def run_ours(args, rank, world, local):
     sizes = fs.sizes
     res = dict(fs=fs, K=K, ms64=ms64, ms32=ms32, ms_e2e=ms_e2e, it64=it64, it32=it32, ref32=ref32, prof64=prof64,
                prof32=prof32, rel=rel, launches64=launches64, launches32=launches32, t_setup=t_setup, t_factor=t_factor, clocks=clocks.summary(), sizes=sizes,
-               workload=w, dt=dt, t_tune=t_tune, tiles=tiles, pic=pic)
+               workload=w, dt=dt, t_tune=t_tune, tiles=tiles, pic=pic, gmres=gm)
     return res
 
 
@@ -476,6 +493,7 @@ def main():
         "fp64": {"steps_per_s": v64, "ms_per_step": r["ms64"] / K, "iters_per_step": float(np.mean(r["it64"])),
                  "tol": args.tol64, "stages": st64},
         "speedup_mixed_vs_fp64": v32 / v64,
+        "coupled_gmres_vs_schur_cg": r["gmres"],
         "rel_err_mixed_vs_fp64": r["rel"],
         "setup_s": r["t_setup"], "factor_s": r["t_factor"], "autotune_s": r["t_tune"],
         "gemv_tiles": r["tiles"],

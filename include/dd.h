@@ -58,6 +58,12 @@ extern "C" {
 #define DD_FP64 0   /* every per-step operation in FP64                                   */
 #define DD_MIXED 1  /* FP32 local/interface/coarse application, FP64 residual refinement  */
 
+/* Interface solvers (dd_params.solver). */
+#define DD_SOLVER_SCHUR_CG 0       /* Eq. f1schur (symmetric positive definite) by Jacobi CG       */
+#define DD_SOLVER_COUPLED_GMRES 1  /* Eqs. F1lr + F1uc together by restarted GMRES (Sec. III-A end,
+                                      Sec. IV, Fig. fetiIter)                                      */
+#define DD_MAX_RESTART 32          /* largest GMRES restart length                                */
+
 typedef struct dd_handle dd_handle;
 
 /* Tetrahedral mesh (host arrays, copied during dd_setup).
@@ -76,11 +82,13 @@ typedef struct {
 } dd_mesh;
 
 /* Solver parameters.
- * tol        relative residual of the interface CG (Eq. f1schur):
- *            stop when ||r_k||_2 <= tol * ||rhs||_2.
- * max_it     CG iteration cap per solve.
+ * tol        relative residual of the interface solve: stop when
+ *            ||r_k||_2 <= tol * ||rhs||_2 (CG: Eq. f1schur; GMRES: the
+ *            coupled system, r = [d_r; f~_c] - M [lambda; x_c]).
+ * max_it     iteration cap per solve (CG iterations / GMRES Arnoldi steps).
  * precond    0 = none, 1 = Jacobi (diagonal of F_rr; the paper's diagonal
- *            preconditioner of Sec. III-C).
+ *            preconditioner of Sec. III-C; for the coupled GMRES the diagonal
+ *            of the coupled matrix, diag(F_rr) and diag(K~cc)).
  * warm_start 1 = start each interface solve from the previous multipliers;
  *            2 = start the first solve of a step from the linear extrapolation
  *            2 lambda^{n-1} - lambda^{n-2} of the previous steps' multipliers
@@ -96,7 +104,17 @@ typedef struct {
  *            every further mixed-precision refinement pass is a conditional IF
  *            node, so a step needs no host round trip unless stats are
  *            requested.  The step's source is copied into the workspace before
- *            each launch.  0 = eager launches with host convergence polling. */
+ *            each launch.  0 = eager launches with host convergence polling.
+ * solver     DD_SOLVER_SCHUR_CG (default) or DD_SOLVER_COUPLED_GMRES: the
+ *            coupled equations F1lr and F1uc,
+ *                [ F_rr     F_rc ] [lambda]   [d_r ]
+ *                [ -F_rc^T  K~cc ] [x_c   ] = [f~_c],
+ *            solved by GMRES(restart) with right preconditioning (the
+ *            residual tested is the unpreconditioned one), classical
+ *            Gram-Schmidt applied twice, Givens rotations; warm start from
+ *            the previous solve's [lambda; x_c].  DD_FP64 and warm_start 0/1
+ *            only (DD_ERR_ARG otherwise).  K~cc^-1 is not used by this solver.
+ * restart    GMRES restart length m, 1..DD_MAX_RESTART (the paper: 20). */
 typedef struct {
     int precision;
     double tol;
@@ -107,6 +125,8 @@ typedef struct {
     int max_refine;
     int chunk;
     int use_graph;
+    int solver;
+    int restart;
 } dd_params;
 
 /* Sizes of a set-up problem. */
@@ -152,10 +172,11 @@ typedef struct {
     int32_t* owner;
 } dd_maps;
 
-/* Per-call statistics (host struct).  iters = interface CG iterations summed
- * over the solves of the call; refinements = FP32 correction solves
- * (DD_MIXED); resid = final relative residual (interface CG for DD_FP64, step
- * system for DD_MIXED); status = DD_OK or the error the call returned. */
+/* Per-call statistics (host struct).  iters = interface CG iterations (GMRES:
+ * Arnoldi steps) summed over the solves of the call; refinements = FP32
+ * correction solves (DD_MIXED); resid = final relative residual (interface
+ * solve for DD_FP64 -- for GMRES the Givens residual estimate --, step system
+ * for DD_MIXED); status = DD_OK or the error the call returned. */
 typedef struct {
     int iters;
     int refinements;
@@ -281,6 +302,16 @@ int dd_pic_state(const dd_handle* h, double* x, int32_t* status, double* G, doub
  * out = (F_rr + F_rc K~cc^-1 F_rc^T) lam, in FP64 with the factors of the last
  * dd_factor.  lam, out: device [n_lambda]. */
 int dd_schur_apply(dd_handle* h, const double* lam, double* out, void* stream);
+
+/* Apply the coupled operator of Eqs. F1lr + F1uc in FP64 with the factors of
+ * the last dd_factor:
+ *   out[0:n_lambda]          = F_rr u_l + F_rc u_c
+ *   out[n_lambda:+n_corner]  = -F_rc^T u_l + K~cc u_c
+ * with u_l = u[0:n_lambda], u_c = u[n_lambda:n_lambda+n_corner].
+ * u, out: device [n_lambda + n_corner], not overlapping.  Uses the handle's
+ * workspace (not reentrant on one handle).  Errors: DD_ERR_ARG, DD_ERR_STATE
+ * (not factored), DD_ERR_CUDA. */
+int dd_coupled_apply(dd_handle* h, const double* u, double* out, void* stream);
 
 /* Same result as dd_schur_apply, for callers that must not allocate device
  * memory (for example code running inside a fixed memory pool, a callback

@@ -45,6 +45,8 @@ dd_params default_params() {
     p.max_refine = 4;
     p.chunk = 8;
     p.use_graph = 0;
+    p.solver = DD_SOLVER_SCHUR_CG;
+    p.restart = 20;
     return p;
 }
 
@@ -52,6 +54,13 @@ int check_params(dd_handle* h, const dd_params& p) {
     if (p.precision != DD_FP64 && p.precision != DD_MIXED) return h->fail(DD_ERR_ARG, "precision must be DD_FP64 or DD_MIXED");
     if (!(p.tol > 0.0) || p.max_it < 1 || p.chunk < 1 || p.max_refine < 1 || !(p.refine_tol > 0.0))
         return h->fail(DD_ERR_ARG, "tol, refine_tol must be > 0 and max_it, chunk, max_refine >= 1");
+    if (p.solver != DD_SOLVER_SCHUR_CG && p.solver != DD_SOLVER_COUPLED_GMRES)
+        return h->fail(DD_ERR_ARG, "solver must be DD_SOLVER_SCHUR_CG or DD_SOLVER_COUPLED_GMRES");
+    if (p.solver == DD_SOLVER_COUPLED_GMRES) {
+        if (p.restart < 1 || p.restart > kMaxRestart) return h->fail(DD_ERR_ARG, "restart must be in 1..DD_MAX_RESTART");
+        if (p.precision != DD_FP64) return h->fail(DD_ERR_ARG, "the coupled GMRES solver runs in DD_FP64 only");
+        if (p.warm_start == 2) return h->fail(DD_ERR_ARG, "warm_start 2 applies to the Schur CG only");
+    }
     return DD_OK;
 }
 
@@ -125,6 +134,7 @@ void compute_stage_bytes(dd_handle* h) {
                     case GEMV_SCHUR_C: r0 = md.nr; r1 = md.ns; c0 = md.nI; c1 = md.nr; break;
                     case GEMV_CORNER: r0 = md.nI; r1 = md.nr; c0 = md.nr; c1 = md.ns; break;
                     case GEMV_SCHUR_G: r0 = md.nI; r1 = md.nr; c0 = md.nI; c1 = md.ns; break;
+                    case GEMV_COUPLED: r0 = md.nI; r1 = md.ns; c0 = md.nI; c1 = md.ns; break;
                     default: r0 = 0; r1 = md.nr; c0 = md.nI; c1 = md.ns; break;
                 }
                 elems += (double)(r1 - r0) * (double)(c1 - c0);
@@ -257,6 +267,18 @@ size_t dd_workspace_layout(dd_handle* h, bool assign) {
     L.take(d.uC, nc);
     L.take(d.vC, nc);
     L.take(d.xC, nc);
+    L.take(d.xC_adj, nc);
+    L.take(d.dinvC, nc);
+    {
+        const int64_t nu = (int64_t)(nm + nc);
+        h->gm_ldv = (nu + 31) / 32 * 32;
+        h->gm_blocks = (int32_t)std::max<int64_t>(1, (nu + kGmChunk - 1) / kGmChunk);
+        L.take(d.Vk, (size_t)(kMaxRestart + 1) * (size_t)h->gm_ldv);
+        L.take(d.tu, (size_t)nu);
+        L.take(d.zu, (size_t)nu);
+        L.take(d.gs, 1);
+        L.take(d.gpart, (size_t)(kMaxRestart + 1) * (size_t)h->gm_blocks);
+    }
     L.take(d.delta, nd);
     L.take(d.delta_k, nd);
     L.take(d.src_in, nd);
@@ -412,6 +434,159 @@ cudaStream_t capture_stream(dd_handle* h, int depth) {
     return (cudaStream_t)h->gstream[depth];
 }
 
+// Read the control words of the coupled GMRES back (synchronises the stream).
+int read_gm(dd_handle* h, GmresScalars* out, cudaStream_t s) {
+    int rc = (int)cudaMemcpyAsync(out, h->d.gs, kGmCtrlBytes, cudaMemcpyDeviceToHost, s);
+    if (rc) return rc;
+    return (int)cudaStreamSynchronize(s);
+}
+
+// Coupled solve of Eqs. F1lr + F1uc (FP64) by restarted GMRES with right
+// diagonal preconditioning: u = [lambda; x_c] from b = [d_r; f~_c] (in d.g,
+// d.fC), left in d.lam and d.xC.  Eager mode polls the control words after
+// every cycle start and every `chunk` Arnoldi steps; graph mode captures the
+// restart cycles as a conditional WHILE node whose body holds the cycle start,
+// a nested WHILE node over the Arnoldi steps and the update of u.
+int gmres_solve(dd_handle* h, double tol, bool warm, int* it_out, double* res_out, cudaStream_t s, int depth) {
+    const size_t nm = h->mult_dof.size(), nc = h->corner_dof.size();
+    *it_out = 0;
+    *res_out = 0.0;
+    if (nm + nc == 0) return DD_OK;
+    const bool use_warm = warm && (h->lam_valid || h->capturing);
+    if (!use_warm) {
+        if (nm) CK(h, (int)cudaMemsetAsync(h->d.lam, 0, sizeof(double) * nm, s), "memset");
+        if (nc) CK(h, (int)cudaMemsetAsync(h->d.xC, 0, sizeof(double) * nc, s), "memset");
+    }
+    // x = [B_r^T u_l ; -u_c] over the [Gamma | c] columns of every local matrix
+    const XSrc xs_x = xsrc(X_LAMBDA_CV, h->d.lam, nullptr, nullptr, nullptr, h->d.xC, nullptr);
+    const XSrc xs_z = xsrc(X_LAMBDA_CV, h->d.zu, nullptr, nullptr, nullptr, h->d.zu + nm, nullptr);
+    const GemvOut go = gout(h->d.w, nullptr, nullptr, nullptr, 1.0);
+    const double mbc = mb(h, GEMV_COUPLED, DD_FP64);
+    const int32_t* skip = &h->d.gs->skip;
+    auto cycle_start = [&](cudaStream_t st, int have_q, unsigned long long cond_inner) -> int {
+        if (have_q) {
+            Prof P(h, ST_SCHUR, st, 1, mbc);
+            CK(h, launch_gemv(h, GEMV_COUPLED, DD_FP64, xs_x, go, false, st), "coupled operator on x");
+        }
+        Prof P(h, ST_VEC, st, 2);
+        CK(h, launch_gm_start(h, have_q, cond_inner, st), "gmres start");
+        CK(h, launch_gm_normalize(h, st), "gmres normalize");
+        return DD_OK;
+    };
+    // one Arnoldi step; its full-work count is added once the step count is known
+    auto arnoldi = [&](cudaStream_t st, unsigned long long cond_inner) -> int {
+        {
+            Prof P(h, ST_SCHUR, st, 1);
+            CK(h, launch_gemv(h, GEMV_COUPLED, DD_FP64, xs_z, go, false, st, skip), "coupled operator");
+        }
+        Prof P(h, ST_VEC, st, 4);
+        CK(h, launch_gm_pass(h, 0, 0ull, st), "gmres pass 0");
+        CK(h, launch_gm_pass(h, 1, 0ull, st), "gmres pass 1");
+        CK(h, launch_gm_pass(h, 2, cond_inner, st), "gmres pass 2");
+        CK(h, launch_gm_normalize(h, st), "gmres normalize");
+        return DD_OK;
+    };
+    if (h->capturing) {
+        cudaGraphConditionalHandle ho;
+        int rc = create_handle(h, s, &ho);
+        if (rc) return rc;
+        {
+            Prof P(h, ST_VEC, s, 1);
+            CK(h, launch_gm_init(h, tol, h->prm.max_it, h->prm.restart, (unsigned long long)ho, s), "gmres init");
+        }
+        cudaGraph_t body;
+        rc = add_conditional(h, s, ho, cudaGraphCondTypeWhile, &body);
+        if (rc) return rc;
+        cudaStream_t bo = capture_stream(h, depth + 1);
+        if (!bo) return h->fail(DD_ERR_CUDA, "capture stream");
+        CK(h, (int)cudaStreamBeginCaptureToGraph(bo, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed),
+           "capture cycle");
+        const int64_t l0 = h->total_launches;
+        cudaGraphConditionalHandle hi;
+        int brc = create_handle(h, bo, &hi);
+        if (!brc) brc = cycle_start(bo, 1, (unsigned long long)hi);
+        cudaGraph_t ibody;
+        if (!brc) brc = add_conditional(h, bo, hi, cudaGraphCondTypeWhile, &ibody);
+        if (!brc) {
+            cudaStream_t bi = capture_stream(h, depth + 2);
+            if (!bi) {
+                brc = h->fail(DD_ERR_CUDA, "capture stream");
+            } else {
+                const int crc = (int)cudaStreamBeginCaptureToGraph(bi, ibody, nullptr, nullptr, 0,
+                                                                   cudaStreamCaptureModeRelaxed);
+                if (crc) {
+                    brc = cuda_fail(h, crc, "capture arnoldi");
+                } else {
+                    const int64_t l1 = h->total_launches;
+                    for (int k = 0; k < h->prm.chunk && !brc; ++k) brc = arnoldi(bi, (unsigned long long)hi);
+                    cudaGraph_t out;
+                    const int erc = (int)cudaStreamEndCapture(bi, &out);
+                    if (!brc && erc) brc = cuda_fail(h, erc, "end arnoldi capture");
+                    h->g_kernels_iter = (h->total_launches - l1) / std::max(1, h->prm.chunk);
+                    h->total_launches = l1;
+                }
+            }
+        }
+        if (!brc) {
+            Prof P(h, ST_VEC, bo, 1);
+            const int urc = launch_gm_update(h, (unsigned long long)ho, bo);
+            if (urc) brc = cuda_fail(h, urc, "gmres update");
+        }
+        cudaGraph_t out_body;
+        const int erc = (int)cudaStreamEndCapture(bo, &out_body);
+        if (brc) return brc;
+        CK(h, erc, "end cycle capture");
+        h->g_kernels_cycle = h->total_launches - l0;
+        h->total_launches = l0;
+        {
+            Prof P(h, ST_VEC, s, 1);
+            CK(h, launch_solve_end(h, s), "solve end");
+        }
+        h->lam_valid = true;
+        return DD_OK;
+    }
+    {
+        Prof P(h, ST_VEC, s, 1);
+        CK(h, launch_gm_init(h, tol, h->prm.max_it, h->prm.restart, 0ull, s), "gmres init");
+    }
+    GmresScalars c;
+    bool first = true;
+    for (;;) {
+        const int have_q = (!first || use_warm) ? 1 : 0;
+        first = false;
+        int rc = cycle_start(s, have_q, 0ull);
+        if (rc) return rc;
+        CK(h, read_gm(h, &c, s), "gmres scalars");
+        while (!c.cycle_end) {
+            const int it0 = c.it;
+            for (int k = 0; k < h->prm.chunk; ++k) {
+                rc = arnoldi(s, 0ull);
+                if (rc) return rc;
+            }
+            CK(h, read_gm(h, &c, s), "gmres scalars");
+            h->work[ST_SCHUR] += c.it - it0;
+            h->work_bytes[ST_SCHUR] += (c.it - it0) * mbc;
+        }
+        {
+            Prof P(h, ST_VEC, s, 1);
+            CK(h, launch_gm_update(h, 0ull, s), "gmres update");
+        }
+        if (c.final) break;
+    }
+    h->lam_valid = true;
+    *it_out = c.it;
+    *res_out = c.bnorm > 0 ? c.resid / c.bnorm : 0.0;
+    if (c.status != DD_OK) {
+        h->err = "non-finite GMRES residual";
+        return c.status;
+    }
+    if (!c.converged) {
+        h->err = "coupled GMRES did not converge";
+        return DD_ERR_NO_CONVERGENCE;
+    }
+    return DD_OK;
+}
+
 int dd_solve(dd_handle* h, int prec, double tol, bool warm, int* it_out, double* res_out, cudaStream_t s,
              int adaptive = 0, int depth = 0) {
     const bool has_c = !h->corner_dof.empty();
@@ -428,6 +603,19 @@ int dd_solve(dd_handle* h, int prec, double tol, bool warm, int* it_out, double*
     {
         Prof P(h, ST_VEC, s, 1);
         CK(h, launch_iface_rhs(h, V.fCf, s), "iface rhs");
+    }
+    if (h->prm.solver == DD_SOLVER_COUPLED_GMRES) {
+        // [lambda; x_c] from the coupled Eqs. F1lr + F1uc, then x_r      Eq. rF1
+        const int status = gmres_solve(h, tol, warm, it_out, res_out, s, depth);
+        if (status != DD_OK && status != DD_ERR_NO_CONVERGENCE) return status;
+        const std::string msg = h->err;
+        {
+            Prof P(h, ST_RECOVER, s, 1, mb(h, GEMV_RECOVER, prec));
+            CK(h, launch_gemv(h, GEMV_RECOVER, prec, xsrc(X_RECOVER, h->d.lam, h->d.xC, nullptr, nullptr),
+                              gout(h->d.x, h->d.y, nullptr, nullptr, 1.0), false, s), "recover");
+        }
+        h->err = msg;
+        return status;
     }
     if (has_c && has_l) {
         // g = d_r - F_rc K~cc^-1 f~_c                                Eq. f1schur
@@ -691,6 +879,7 @@ int dd_bind_workspace(dd_handle* h, void* dev, size_t bytes, void* stream) {
     for (int k = 0; k < 3; ++k) CK(h, (int)cudaMemsetAsync(h->d.e[k], 0, sizeof(double) * nd, s), "memset");
     for (int k = 0; k < 3; ++k) CK(h, (int)cudaMemsetAsync(h->d.mu[k], 0, sizeof(double) * nd, s), "memset");
     CK(h, (int)cudaMemsetAsync(h->d.sc, 0, sizeof(PcgScalars), s), "memset");
+    CK(h, (int)cudaMemsetAsync(h->d.gs, 0, sizeof(GmresScalars), s), "memset");
     CK(h, (int)cudaMemsetAsync(h->d.status, 0, 16, s), "memset");
     CK(h, (int)cudaStreamSynchronize(s), "sync");
     h->bound = true;
@@ -730,6 +919,7 @@ int dd_factor(dd_handle* h, double dt, void* stream) {
     {
         Prof P(h, ST_FACTOR, s, 3);
         CK(h, launch_factor_finish(h, s), "factor finish");
+        CK(h, launch_corner_diag(h, s), "coarse diagonal");
     }
     int32_t st = 0;
     CK(h, (int)cudaMemcpyAsync(&st, h->d.status, 4, cudaMemcpyDeviceToHost, s), "status");
@@ -1030,6 +1220,8 @@ int dd_step_graph(dd_handle* h, const double* d2g, double* e_out, dd_stats* stat
         CK(h, (int)cudaMemsetAsync(h->d.lam, 0, sizeof(double) * h->mult_dof.size(), s), "memset");
         CK(h, (int)cudaMemsetAsync(h->d.lamf, 0, sizeof(float) * h->mult_dof.size(), s), "memset");
     }
+    if (!h->lam_valid && h->prm.solver == DD_SOLVER_COUPLED_GMRES && !h->corner_dof.empty())
+        CK(h, (int)cudaMemsetAsync(h->d.xC, 0, sizeof(double) * h->corner_dof.size(), s), "memset");
     CK(h, (int)cudaGraphLaunch((cudaGraphExec_t)h->gexec[phase], s), "graph launch");
     h->lam_valid = true;
     double* e_np1 = h->d.e[(phase + 1) % 3];
@@ -1047,7 +1239,8 @@ int dd_step_graph(dd_handle* h, const double* d2g, double* e_out, dd_stats* stat
         status = hs.step_status;
         stats->status = status;
         h->total_launches += h->g_kernels_main + h->g_kernels_iter * (int64_t)hs.it_total +
-                             h->g_kernels_pass * (int64_t)std::max(0, hs.refinements - 1);
+                             h->g_kernels_pass * (int64_t)std::max(0, hs.refinements - 1) +
+                             h->g_kernels_cycle * (int64_t)hs.cycles;
         if (status == DD_ERR_NO_CONVERGENCE) h->err = "interface CG or refinement did not converge";
         if (status == DD_ERR_NONFINITE) h->err = "non-finite residual";
     }
@@ -1060,6 +1253,7 @@ void swap_lambda(dd_handle* h) {
     std::swap(h->d.lam, h->d.lam_adj);
     std::swap(h->d.lamf, h->d.lamf_adj);
     std::swap(h->d.lam_prev, h->d.lam_prev_adj);
+    std::swap(h->d.xC, h->d.xC_adj);
     std::swap(h->lam_valid, h->lam_adj_valid);
 }
 
@@ -1157,6 +1351,22 @@ int dd_schur_apply(dd_handle* h, const double* lam, double* out, void* stream) {
     CK(h, apply_schur_w(h, DD_FP64, X_LAMBDA, lam, nullptr, nullptr, nullptr, false, s), "apply");
     Prof P(h, ST_VEC, s, 1);
     CK(h, launch_jump(h, h->d.w, nullptr, nullptr, 1.0, out, s), "jump");
+    return DD_OK;
+}
+
+int dd_coupled_apply(dd_handle* h, const double* u, double* out, void* stream) {
+    if (!h || !u || !out) return DD_ERR_ARG;
+    if (!h->factored) return h->fail(DD_ERR_STATE, "dd_coupled_apply before dd_factor");
+    const size_t nm = h->mult_dof.size(), nc = h->corner_dof.size();
+    if (nm + nc == 0) return DD_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    {
+        Prof P(h, ST_SCHUR, s, 1, mb(h, GEMV_COUPLED, DD_FP64));
+        CK(h, launch_gemv(h, GEMV_COUPLED, DD_FP64, xsrc(X_LAMBDA_CV, u, nullptr, nullptr, nullptr, u + nm, nullptr),
+                          gout(h->d.w, nullptr, nullptr, nullptr, 1.0), false, s), "coupled operator");
+    }
+    Prof P(h, ST_VEC, s, 1);
+    CK(h, launch_gm_combine(h, out, s), "combine");
     return DD_OK;
 }
 

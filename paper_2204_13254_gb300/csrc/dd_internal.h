@@ -1,6 +1,7 @@
 // Internal declarations shared by the host setup, the kernels and the C ABI.
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -35,7 +36,8 @@ enum GemvMode : int {
     GEMV_RECOVER = 3,  // rows [0,nr)  cols [nI,ns): x_r from y, lambda, x_c               (Eq. rF1)
     GEMV_COARSE = 4,   // the dense K~cc^-1 (single matrix)
     GEMV_SCHUR_G = 5,  // rows [nI,nr) cols [nI,ns): F_rr and F_rc pieces in one pass       (Eq. f1schur)
-    GEMV_NMODES = 6
+    GEMV_COUPLED = 6,  // rows [nI,ns) cols [nI,ns): F_rr, F_rc, F_rc^T and K~cc pieces   (Eqs. F1lr, F1uc)
+    GEMV_NMODES = 7
 };
 
 // Source of the x vector of a batched GEMV (staged in shared memory per CTA).
@@ -95,9 +97,41 @@ struct PcgScalars {
     int32_t it_total;     // graph mode: CG iterations of the whole step
     int32_t refinements;  // graph mode: solves of the whole step
     int32_t step_status;  // graph mode: DD status of the whole step
-    int32_t pad2;
+    int32_t cycles;       // graph mode: GMRES restart cycles of the whole step
     uint32_t counter[8];  // last-block counters of the grid reductions
 };
+
+constexpr int kMaxRestart = DD_MAX_RESTART;
+constexpr int kGmElems = 4;                          // vector elements per thread in the GMRES kernels
+constexpr int kGmChunk = kGmElems * 256;             // elements per block
+
+// Device state of the restarted GMRES of the coupled system (one struct in the
+// workspace).  The control words come first: eager mode reads them back.
+struct GmresScalars {
+    int32_t j;          // Arnoldi column being built in the current cycle
+    int32_t it;         // Arnoldi steps of this solve
+    int32_t k;          // columns of the cycle that just ended (update x with y[0..k))
+    int32_t cycle_end;  // the current cycle has ended (inner loop stops)
+    int32_t final;      // the solve ends after the pending update (converged, budget spent or non-finite)
+    int32_t converged;
+    int32_t status;     // DD_OK / DD_ERR_NONFINITE
+    int32_t skip;       // cycle_end: per-step kernels exit at once
+    double bnorm;       // ||b||
+    double tol;         // relative tolerance of the solve
+    double thr;         // tol * ||b||
+    double beta;        // ||r_0|| of the cycle
+    double hnext;       // norm of the vector to normalise next (beta, then H[j+1][j])
+    double resid;       // |g_{j+1}| after the last step
+    int32_t max_it, m, cycles, pad;
+    uint32_t counter[4];
+    double g[kMaxRestart + 1];
+    double cs[kMaxRestart], sn[kMaxRestart];
+    double y[kMaxRestart];
+    double h1[kMaxRestart + 1];   // first Gram-Schmidt projection of the current column
+    double h2[kMaxRestart + 1];   // second projection
+    double H[kMaxRestart * (kMaxRestart + 1)];   // column j at H[j * (kMaxRestart + 1)], rotated in place
+};
+constexpr size_t kGmCtrlBytes = offsetof(GmresScalars, max_it);
 
 struct DevPtrs {
     // maps (slot = flat local index over all subdomains)
@@ -178,6 +212,14 @@ struct DevPtrs {
     double* uC = nullptr;
     double* vC = nullptr;
     double* xC = nullptr;
+    double* xC_adj = nullptr;        // adjoint march's corner solution (coupled GMRES warm start)
+    double* dinvC = nullptr;         // [n_corner] inverse diagonal of K~cc
+    // coupled GMRES vectors (n_u = n_lambda + n_corner, leading dimension gm_ldv)
+    double* Vk = nullptr;            // [(kMaxRestart+1) * gm_ldv] Krylov basis
+    double* tu = nullptr;            // [n_u] Arnoldi work vector
+    double* zu = nullptr;            // [n_u] D^-1 v_j, the operator's input
+    GmresScalars* gs = nullptr;
+    double* gpart = nullptr;         // [(kMaxRestart+1) * gm_blocks] block partials
     float* fCf = nullptr;
     float* uCf = nullptr;
     float* vCf = nullptr;
@@ -278,6 +320,9 @@ struct dd_handle {
     int64_t g_kernels_main = 0;      // kernels outside conditional bodies
     int64_t g_kernels_iter = 0;      // kernels per CG iteration (WHILE body)
     int64_t g_kernels_pass = 0;      // kernels per extra refinement pass outside its WHILE body
+    int64_t g_kernels_cycle = 0;     // kernels per GMRES restart cycle outside its inner WHILE body
+    int64_t gm_ldv = 0;              // leading dimension of the GMRES basis
+    int32_t gm_blocks = 1;           // blocks of the GMRES vector kernels
 
     // profiling (dd_profile)
     bool prof_on = false;
@@ -299,12 +344,12 @@ struct dd_handle {
 };
 
 constexpr int kNB = 32;              // pivot block of the dense elimination
-// default tile shapes per mode (LOCAL, SCHUR_C, CORNER, RECOVER, COARSE, SCHUR_G):
+// default tile shapes per mode (LOCAL, SCHUR_C, CORNER, RECOVER, COARSE, SCHUR_G, COUPLED):
 // rows per CTA, and lanes per row for FP32 and FP64 (8 lanes for FP64 keeps the
 // FP64 reduction adds off GB300's narrow FP64 pipe)
-constexpr int kRowsPerMode[GEMV_NMODES] = {32, 32, 64, 32, 8, 64};
-constexpr int kLprF32[GEMV_NMODES] = {32, 16, 8, 16, 32, 16};
-constexpr int kLprF64[GEMV_NMODES] = {8, 8, 8, 8, 32, 8};
+constexpr int kRowsPerMode[GEMV_NMODES] = {32, 32, 64, 32, 8, 64, 64};
+constexpr int kLprF32[GEMV_NMODES] = {32, 16, 8, 16, 32, 16, 16};
+constexpr int kLprF64[GEMV_NMODES] = {8, 8, 8, 8, 32, 8, 8};
 constexpr int kMinRowsPerTask = 8;    // smallest rows per CTA of any default or candidate tile (sets task capacity)
 constexpr int kMaxPartials = 4096;   // block partials of the grid reductions
 
@@ -328,7 +373,8 @@ int launch_dot_sub(const dd_handle* h, const double* a, const double* b, double*
 int launch_probe_seed(const dd_handle* h, const double* e, double weight, double* seed, void* stream);
 int launch_residual_local(const dd_handle* h, void* stream);
 int launch_assembled_norm(const dd_handle* h, int set_b, float* bf, void* stream);
-int launch_gemv(const dd_handle* h, int mode, int prec, XSrc xs, GemvOut go, bool check_done, void* stream);
+int launch_gemv(const dd_handle* h, int mode, int prec, XSrc xs, GemvOut go, bool check_done, void* stream,
+                const int32_t* skip_flag = nullptr);
 int launch_iface_rhs(const dd_handle* h, float* fCf, void* stream);
 int launch_corner_gather(const dd_handle* h, const double* w, const float* wf, const double* add, double* uC, float* uCf,
                          bool check_done, void* stream);
@@ -350,6 +396,15 @@ int launch_probe(const dd_handle* h, const double* e, double* out, void* stream)
 int launch_pic_move(const dd_handle* h, double t_n, double dt, const double* e_n, double* dep, void* stream);
 int launch_pic_source(const dd_handle* h, const double* dep_new, const double* dep_old, void* stream);
 int launch_faraday(const dd_handle* h, const double* e_np1, const double* e_n, double dt, void* stream);
+
+// gmres.cu: coupled-system GMRES (u = [lambda; x_c])
+int launch_corner_diag(const dd_handle* h, void* stream);
+int launch_gm_init(const dd_handle* h, double tol, int max_it, int m, unsigned long long cond_outer, void* stream);
+int launch_gm_start(const dd_handle* h, int have_q, unsigned long long cond_inner, void* stream);
+int launch_gm_normalize(const dd_handle* h, void* stream);
+int launch_gm_pass(const dd_handle* h, int phase, unsigned long long cond_inner, void* stream);
+int launch_gm_update(const dd_handle* h, unsigned long long cond_outer, void* stream);
+int launch_gm_combine(const dd_handle* h, double* out, void* stream);
 
 // GEMV x-source kinds (see kernels.cu)
 enum : int { X_FLAT = 0, X_LAMBDA = 1, X_PCG = 2, X_CORNER = 3, X_RECOVER = 4, X_COARSE = 5, X_PCG_CV = 6,

@@ -1,0 +1,449 @@
+// Restarted GMRES on the coupled MFETI-DP1 system of Eqs. F1lr + F1uc (sm_103a).
+//
+// Unknown u = [lambda; x_c] (n_u = n_lambda + n_corner), right-hand side
+// b = [d_r; f~_c], operator
+//     M u = [ F_rr u_l + F_rc u_c ; -F_rc^T u_l + K~cc u_c ].
+// One application of M is one batched GEMV over the rows and columns
+// [Gamma | c] of every swept local matrix (GEMV_COUPLED, x = [B_r^T u_l; -u_c])
+// followed by the jump over the multipliers and the negated corner assembly,
+// which the first Gram-Schmidt kernel below performs while it reads the
+// output.  Preconditioning is on the right with D = diag(M) (the paper's
+// diagonal preconditioner): the basis vectors v_j are scaled by D^-1 before
+// they enter the GEMV, and x += D^-1 V y at the end of a cycle, so the
+// residual tested is the unpreconditioned b - M x.
+//
+// One Arnoldi step = GEMV + three vector kernels + one normalisation:
+//   pass 0: t = M D^-1 v_j (combine),        h1 = V^T t
+//   pass 1: t -= V h1,                        h2 = V^T t   (classical Gram-Schmidt, twice)
+//   pass 2: t -= V h2, ||t|| -> H[j+1][j]; the last block applies the stored
+//           Givens rotations to column j, makes the new one, updates the
+//           least-squares residual |g_{j+1}| and decides the end of the cycle
+//           (converged, m steps, budget spent, breakdown); at the end it
+//           back-substitutes y = R^-1 g.
+//   normalise: v_{j+1} = t / H[j+1][j], z = D^-1 v_{j+1}.
+// Multi-dot products are block partials reduced in fixed block order by the
+// last block to finish (atomic ticket, no spinning): results do not depend on
+// scheduling.
+#include <cuda_runtime.h>
+
+#include "dd_internal.h"
+
+namespace {
+
+inline cudaStream_t S(void* s) { return (cudaStream_t)s; }
+
+constexpr int kT = 256;
+constexpr int kWarps = kT / 32;
+constexpr int kM1 = kMaxRestart + 1;
+
+__device__ __forceinline__ double wsum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// (M u)_i from the GEMV output w per slot: jump over multiplier i, or minus the
+// assembly over the copies of corner i - n_lambda.
+__device__ __forceinline__ double combine(int64_t i, int64_t nl, const int64_t* __restrict__ ms,
+                                          const int64_t* __restrict__ cp, const int64_t* __restrict__ cs,
+                                          const double* __restrict__ w) {
+    if (i < nl) return w[ms[2 * i]] - w[ms[2 * i + 1]];
+    const int64_t c = i - nl;
+    double s = 0.0;
+    for (int64_t k = cp[c]; k < cp[c + 1]; ++k) s += w[cs[k]];
+    return -s;
+}
+
+__device__ __forceinline__ double dinv_at(int64_t i, int64_t nl, const double* __restrict__ dl,
+                                          const double* __restrict__ dc) {
+    if (i < nl) return dl ? dl[i] : 1.0;
+    return dc ? dc[i - nl] : 1.0;
+}
+
+// Ticket of a multi-block reduction: every writer thread has fenced its partials
+// before the barrier; true in every thread of the last block.
+__device__ bool last_block(uint32_t* counter) {
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+// Sum of partials[k * nb + b] over b in fixed order (lanes stride the blocks,
+// then a fixed shuffle tree); valid in lane 0.
+__device__ __forceinline__ double reduce_partials(const double* partials, int k, int nb) {
+    double s = 0.0;
+    for (int b = threadIdx.x & 31; b < nb; b += 32) s += ((volatile const double*)partials)[(int64_t)k * nb + b];
+    return wsum(s);
+}
+
+// Block sum of one value (all threads call); result in thread 0.
+__device__ double block_sum1(double v) {
+    __shared__ double red[kWarps];
+    v = wsum(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kWarps; ++w) s += red[w];
+    return s;
+}
+
+// K~cc diagonal: sum over the copies of each corner of the local Schur
+// complement's diagonal (the corner block of the swept M_s), inverted.
+__global__ void k_corner_diag(int64_t nc, const int64_t* __restrict__ cp, const int64_t* __restrict__ cs,
+                              const int32_t* __restrict__ slot_sub, const MatDesc* __restrict__ mats,
+                              const double* __restrict__ M, double* __restrict__ dinvC) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int64_t k = cp[c]; k < cp[c + 1]; ++k) {
+            const int64_t slot = cs[k];
+            const MatDesc md = mats[slot_sub[slot]];
+            const int64_t row = slot - md.voff;
+            s += M[md.moff + row * md.ld + row];
+        }
+        dinvC[c] = 1.0 / s;
+    }
+}
+
+__global__ void k_gm_init(GmresScalars* gs, double tol, int max_it, int m, unsigned long long cond) {
+    gs->it = 0;
+    gs->final = 0;
+    gs->converged = 0;
+    gs->status = DD_OK;
+    gs->cycle_end = 0;
+    gs->skip = 0;
+    gs->k = 0;
+    gs->j = 0;
+    gs->tol = tol;
+    gs->max_it = max_it;
+    gs->m = m;
+    gs->cycles = 0;
+    if (cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, 1u);
+}
+
+// Start of a cycle: t = b - M x (have_q: w holds the GEMV of x), beta = ||t||,
+// ||b||; decides whether the solve is already over.
+__global__ void __launch_bounds__(kT) k_gm_start(int64_t nl, int64_t nc, const int64_t* __restrict__ ms,
+                                                 const int64_t* __restrict__ cp, const int64_t* __restrict__ cs,
+                                                 const double* __restrict__ w, int have_q,
+                                                 const double* __restrict__ g, const double* __restrict__ fC,
+                                                 double* __restrict__ tu, GmresScalars* gs, PcgScalars* sc,
+                                                 double* __restrict__ partials, unsigned long long cond) {
+    const int64_t nu = nl + nc;
+    double rr = 0.0, bb = 0.0;
+#pragma unroll
+    for (int e = 0; e < kGmElems; ++e) {
+        const int64_t i = (int64_t)blockIdx.x * kGmChunk + e * kT + threadIdx.x;
+        if (i < nu) {
+            const double b = i < nl ? g[i] : fC[i - nl];
+            const double r = b - (have_q ? combine(i, nl, ms, cp, cs, w) : 0.0);
+            tu[i] = r;
+            rr += r * r;
+            bb += b * b;
+        }
+    }
+    rr = block_sum1(rr);
+    bb = block_sum1(bb);
+    const int nb = gridDim.x;
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = rr;
+        partials[nb + blockIdx.x] = bb;
+    }
+    if (!last_block(&gs->counter[0])) return;
+    double tot[2];
+    for (int k = 0; k < 2; ++k) tot[k] = __shfl_sync(0xffffffffu, reduce_partials(partials, k, nb), 0);
+    if (threadIdx.x == 0) {
+        gs->counter[0] = 0u;
+        const double beta = sqrt(tot[0]);
+        gs->bnorm = sqrt(tot[1]);
+        gs->thr = gs->tol * gs->bnorm;
+        gs->beta = beta;
+        gs->hnext = beta;
+        gs->resid = beta;
+        gs->g[0] = beta;
+        gs->j = 0;
+        gs->k = 0;
+        gs->cycles += 1;
+        sc->cycles += 1;
+        int end = 0;
+        if (!isfinite(beta) || !isfinite(gs->bnorm)) {
+            gs->status = DD_ERR_NONFINITE;
+            end = 1;
+        } else if (beta <= gs->thr) {
+            gs->converged = 1;
+            end = 1;
+        } else if (gs->it >= gs->max_it) {
+            end = 1;
+        }
+        gs->final = end;
+        gs->cycle_end = end;
+        gs->skip = end;
+        if (cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, end ? 0u : 1u);
+    }
+}
+
+// v_j = t / hnext, z = D^-1 v_j
+__global__ void k_gm_normalize(int64_t nl, int64_t nc, double* __restrict__ V, int64_t ldv,
+                               const double* __restrict__ tu, const double* __restrict__ dl,
+                               const double* __restrict__ dc, double* __restrict__ zu, const GmresScalars* gs) {
+    if (gs->skip) return;
+    const int64_t nu = nl + nc;
+    double* vj = V + (int64_t)gs->j * ldv;
+    const double inv = 1.0 / gs->hnext;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nu; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = tu[i] * inv;
+        vj[i] = v;
+        zu[i] = dinv_at(i, nl, dl, dc) * v;
+    }
+}
+
+// Gram-Schmidt passes of Arnoldi column j (see the file comment).
+template <int PHASE>
+__global__ void __launch_bounds__(kT) k_gm_pass(int64_t nl, int64_t nc, const int64_t* __restrict__ ms,
+                                                const int64_t* __restrict__ cp, const int64_t* __restrict__ cs,
+                                                const double* __restrict__ w, const double* __restrict__ V,
+                                                int64_t ldv, double* __restrict__ tu, GmresScalars* gs,
+                                                PcgScalars* sc, double* __restrict__ partials,
+                                                unsigned long long cond) {
+    if (gs->skip) return;
+    __shared__ double coef[kM1];
+    __shared__ double red[kM1][kWarps];
+    const int64_t nu = nl + nc;
+    const int j = gs->j;
+    const int nv = j + 1;
+    const int nb = gridDim.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (PHASE > 0 && threadIdx.x < nv) coef[threadIdx.x] = PHASE == 1 ? gs->h1[threadIdx.x] : gs->h2[threadIdx.x];
+    __syncthreads();
+    double t[kGmElems];
+#pragma unroll
+    for (int e = 0; e < kGmElems; ++e) {
+        const int64_t i = (int64_t)blockIdx.x * kGmChunk + e * kT + threadIdx.x;
+        t[e] = 0.0;
+        if (i < nu) {
+            double v;
+            if (PHASE == 0) {
+                v = combine(i, nl, ms, cp, cs, w);
+            } else {
+                v = tu[i];
+                for (int k = 0; k < nv; ++k) v -= coef[k] * V[(int64_t)k * ldv + i];
+            }
+            tu[i] = v;
+            t[e] = v;
+        }
+    }
+    if (PHASE < 2) {
+        // partial dots with v_0 .. v_j
+        for (int k = 0; k < nv; ++k) {
+            double p = 0.0;
+#pragma unroll
+            for (int e = 0; e < kGmElems; ++e) {
+                const int64_t i = (int64_t)blockIdx.x * kGmChunk + e * kT + threadIdx.x;
+                if (i < nu) p += t[e] * V[(int64_t)k * ldv + i];
+            }
+            p = wsum(p);
+            if (lane == 0) red[k][warp] = p;
+        }
+        __syncthreads();
+        if (threadIdx.x < nv) {
+            double s = 0.0;
+            for (int q = 0; q < kWarps; ++q) s += red[threadIdx.x][q];
+            partials[(int64_t)threadIdx.x * nb + blockIdx.x] = s;
+            __threadfence();
+        }
+        if (!last_block(&gs->counter[1 + PHASE])) return;
+        for (int k = warp; k < nv; k += kWarps) {
+            const double s = reduce_partials(partials, k, nb);
+            if (lane == 0) {
+                if (PHASE == 0) {
+                    gs->h1[k] = s;
+                } else {
+                    gs->h2[k] = s;
+                    gs->H[(int64_t)j * kM1 + k] = gs->h1[k] + s;
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) gs->counter[1 + PHASE] = 0u;
+        return;
+    }
+    // PHASE 2: ||t||, Givens, end of cycle
+    double p = 0.0;
+#pragma unroll
+    for (int e = 0; e < kGmElems; ++e) p += t[e] * t[e];
+    p = block_sum1(p);
+    if (threadIdx.x == 0) partials[blockIdx.x] = p;
+    if (!last_block(&gs->counter[3])) return;
+    const double tot = __shfl_sync(0xffffffffu, reduce_partials(partials, 0, nb), 0);
+    if (threadIdx.x != 0) return;
+    gs->counter[3] = 0u;
+    double* col = gs->H + (int64_t)j * kM1;
+    const double hsub = sqrt(tot);
+    col[j + 1] = hsub;
+    for (int i = 0; i < j; ++i) {
+        const double a = col[i], b = col[i + 1];
+        col[i] = gs->cs[i] * a + gs->sn[i] * b;
+        col[i + 1] = -gs->sn[i] * a + gs->cs[i] * b;
+    }
+    double c = 1.0, s = 0.0;
+    {
+        const double a = col[j], b = col[j + 1];
+        const double r = hypot(a, b);
+        if (r != 0.0) {
+            c = a / r;
+            s = b / r;
+        }
+    }
+    col[j] = c * col[j] + s * col[j + 1];
+    col[j + 1] = 0.0;
+    gs->cs[j] = c;
+    gs->sn[j] = s;
+    gs->g[j + 1] = -s * gs->g[j];
+    gs->g[j] = c * gs->g[j];
+    gs->it += 1;
+    sc->it_total += 1;
+    const double resid = fabs(gs->g[j + 1]);
+    gs->resid = resid;
+    const bool finite = isfinite(resid) && isfinite(hsub) && isfinite(col[j]);
+    const bool conv = finite && resid <= gs->thr;
+    const bool out_of_budget = gs->it >= gs->max_it;
+    const bool end = !finite || conv || out_of_budget || j + 1 == gs->m || hsub == 0.0;
+    if (!finite) gs->status = DD_ERR_NONFINITE;
+    if (end) {
+        const int k = finite ? j + 1 : 0;
+        for (int i = k - 1; i >= 0; --i) {
+            double v = gs->g[i];
+            for (int l = i + 1; l < k; ++l) v -= gs->H[(int64_t)l * kM1 + i] * gs->y[l];
+            gs->y[i] = v / gs->H[(int64_t)i * kM1 + i];
+        }
+        gs->k = k;
+        gs->converged = conv ? 1 : 0;
+        gs->final = (!finite || conv || out_of_budget) ? 1 : 0;
+        gs->cycle_end = 1;
+        gs->skip = 1;
+    } else {
+        gs->j = j + 1;
+        gs->hnext = hsub;
+    }
+    if (cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, end ? 0u : 1u);
+}
+
+// End of a cycle: x += D^-1 V y (x = [lambda; x_c] in place); at the end of the
+// solve, publish its outcome in the CG scalars (step statistics, solve end).
+__global__ void k_gm_update(int64_t nl, int64_t nc, const double* __restrict__ V, int64_t ldv,
+                            const double* __restrict__ dl, const double* __restrict__ dc, double* __restrict__ lam,
+                            double* __restrict__ xC, const GmresScalars* gs, PcgScalars* sc,
+                            unsigned long long cond) {
+    __shared__ double y[kMaxRestart];
+    const int k = gs->k;
+    if (threadIdx.x < k) y[threadIdx.x] = gs->y[threadIdx.x];
+    __syncthreads();
+    const int64_t nu = nl + nc;
+    if (k > 0) {
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nu; i += (int64_t)gridDim.x * blockDim.x) {
+            double v = 0.0;
+            for (int q = 0; q < k; ++q) v += y[q] * V[(int64_t)q * ldv + i];
+            v *= dinv_at(i, nl, dl, dc);
+            if (i < nl) lam[i] += v;
+            else xC[i - nl] += v;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (gs->final) {
+            sc->status = gs->status;
+            sc->done = gs->converged;
+            sc->it = gs->it;
+            sc->rr = gs->resid * gs->resid;
+            sc->gg = gs->bnorm * gs->bnorm;
+        }
+        if (cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, gs->final ? 0u : 1u);
+    }
+}
+
+__global__ void k_gm_combine(int64_t nl, int64_t nc, const int64_t* __restrict__ ms, const int64_t* __restrict__ cp,
+                             const int64_t* __restrict__ cs, const double* __restrict__ w, double* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nl + nc; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = combine(i, nl, ms, cp, cs, w);
+}
+
+int vec_blocks(int64_t n) {
+    int64_t b = (n + kT - 1) / kT;
+    if (b > 2 * 152) b = 2 * 152;
+    return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+int launch_corner_diag(const dd_handle* h, void* stream) {
+    const int64_t nc = (int64_t)h->corner_dof.size();
+    if (nc == 0) return 0;
+    k_corner_diag<<<vec_blocks(nc), kT, 0, S(stream)>>>(nc, h->d.corner_ptr, h->d.corner_slot, h->d.slot_sub, h->d.mats,
+                                                       h->d.M64, h->d.dinvC);
+    return (int)cudaGetLastError();
+}
+
+int launch_gm_init(const dd_handle* h, double tol, int max_it, int m, unsigned long long cond_outer, void* stream) {
+    k_gm_init<<<1, 1, 0, S(stream)>>>(h->d.gs, tol, max_it, m, cond_outer);
+    return (int)cudaGetLastError();
+}
+
+int launch_gm_start(const dd_handle* h, int have_q, unsigned long long cond_inner, void* stream) {
+    const int64_t nl = (int64_t)h->mult_dof.size(), nc = (int64_t)h->corner_dof.size();
+    k_gm_start<<<h->gm_blocks, kT, 0, S(stream)>>>(nl, nc, h->d.mult_slot, h->d.corner_ptr, h->d.corner_slot, h->d.w,
+                                                   have_q, h->d.g, h->d.fC, h->d.tu, h->d.gs, h->d.sc, h->d.gpart,
+                                                   cond_inner);
+    return (int)cudaGetLastError();
+}
+
+int launch_gm_normalize(const dd_handle* h, void* stream) {
+    const int64_t nl = (int64_t)h->mult_dof.size(), nc = (int64_t)h->corner_dof.size();
+    const bool pc = h->prm.precond != 0;
+    k_gm_normalize<<<vec_blocks(nl + nc), kT, 0, S(stream)>>>(nl, nc, h->d.Vk, h->gm_ldv, h->d.tu,
+                                                               pc ? h->d.dinv : nullptr, pc ? h->d.dinvC : nullptr,
+                                                               h->d.zu, h->d.gs);
+    return (int)cudaGetLastError();
+}
+
+int launch_gm_pass(const dd_handle* h, int phase, unsigned long long cond_inner, void* stream) {
+    const int64_t nl = (int64_t)h->mult_dof.size(), nc = (int64_t)h->corner_dof.size();
+    const DevPtrs& d = h->d;
+    switch (phase) {
+        case 0:
+            k_gm_pass<0><<<h->gm_blocks, kT, 0, S(stream)>>>(nl, nc, d.mult_slot, d.corner_ptr, d.corner_slot, d.w,
+                                                             d.Vk, h->gm_ldv, d.tu, d.gs, d.sc, d.gpart, 0ull);
+            break;
+        case 1:
+            k_gm_pass<1><<<h->gm_blocks, kT, 0, S(stream)>>>(nl, nc, d.mult_slot, d.corner_ptr, d.corner_slot, d.w,
+                                                             d.Vk, h->gm_ldv, d.tu, d.gs, d.sc, d.gpart, 0ull);
+            break;
+        default:
+            k_gm_pass<2><<<h->gm_blocks, kT, 0, S(stream)>>>(nl, nc, d.mult_slot, d.corner_ptr, d.corner_slot, d.w,
+                                                             d.Vk, h->gm_ldv, d.tu, d.gs, d.sc, d.gpart, cond_inner);
+            break;
+    }
+    return (int)cudaGetLastError();
+}
+
+int launch_gm_update(const dd_handle* h, unsigned long long cond_outer, void* stream) {
+    const int64_t nl = (int64_t)h->mult_dof.size(), nc = (int64_t)h->corner_dof.size();
+    const bool pc = h->prm.precond != 0;
+    k_gm_update<<<vec_blocks(nl + nc), kT, 0, S(stream)>>>(nl, nc, h->d.Vk, h->gm_ldv, pc ? h->d.dinv : nullptr,
+                                                            pc ? h->d.dinvC : nullptr, h->d.lam, h->d.xC, h->d.gs,
+                                                            h->d.sc, cond_outer);
+    return (int)cudaGetLastError();
+}
+
+int launch_gm_combine(const dd_handle* h, double* out, void* stream) {
+    const int64_t nl = (int64_t)h->mult_dof.size(), nc = (int64_t)h->corner_dof.size();
+    if (nl + nc == 0) return 0;
+    k_gm_combine<<<vec_blocks(nl + nc), kT, 0, S(stream)>>>(nl, nc, h->d.mult_slot, h->d.corner_ptr, h->d.corner_slot,
+                                                             h->d.w, out);
+    return (int)cudaGetLastError();
+}

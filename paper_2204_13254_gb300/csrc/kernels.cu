@@ -13,6 +13,7 @@
 //        F_rr / F_rc^T pieces on lambda        rows [nI,ns) cols [nI,nr)
 //        F_rc pieces on the corner vector      rows [nI,nr) cols [nr,ns)
 //        recovery x_r (Eq. rF1)                rows [0,nr)  cols [nI,ns)
+//        coupled operator (Eqs. F1lr, F1uc)    rows [nI,ns) cols [nI,ns)
 //  * Interface vectors are indexed by multiplier, corner vectors by corner.
 //
 // All reductions are deterministic: each block writes a partial sum and the
@@ -520,6 +521,7 @@ __global__ void __launch_bounds__(kThreads) k_gemv(const GemvTask* __restrict__ 
         case GEMV_CORNER: c0 = md.nr; c1 = md.ns; break;
         case GEMV_RECOVER: c0 = md.nI; c1 = md.ns; break;
         case GEMV_SCHUR_G: c0 = md.nI; c1 = md.ns; break;
+        case GEMV_COUPLED: c0 = md.nI; c1 = md.ns; break;
         default: c0 = 0; c1 = md.ns; break;
     }
     const TM beta = (xs.kind == X_PCG || xs.kind == X_PCG_CV) ? (TM)xs.sc->beta : (TM)0;
@@ -772,6 +774,7 @@ __global__ void k_levels_inc(PcgScalars* sc) {
 __global__ void k_step_begin(PcgScalars* sc) {
     sc->it_total = 0;
     sc->refinements = 0;
+    sc->cycles = 0;
     sc->step_status = DD_OK;
 }
 
@@ -1155,7 +1158,8 @@ int run_gemv(unsigned nb, size_t smem, cudaStream_t st, const GemvTask* tasks, c
     return (int)cudaGetLastError();
 }
 
-int launch_gemv(const dd_handle* h, int mode, int prec, XSrc xs, GemvOut go, bool check_done, void* stream) {
+int launch_gemv(const dd_handle* h, int mode, int prec, XSrc xs, GemvOut go, bool check_done, void* stream,
+                const int32_t* skip_flag) {
     const int pi = prec == DD_MIXED ? 1 : 0;
     const auto& tl = h->tasks[pi][mode];
     if (tl.empty()) return 0;
@@ -1172,7 +1176,7 @@ int launch_gemv(const dd_handle* h, int mode, int prec, XSrc xs, GemvOut go, boo
         staged = 0;
         smem = 0;
     }
-    const int32_t* done = check_done ? &h->d.sc->done : nullptr;
+    const int32_t* done = check_done ? &h->d.sc->done : skip_flag;
     const unsigned nb = (unsigned)tl.size();
     const int lpr = h->tile[pi][mode].lpr;
     if (prec == DD_MIXED) {

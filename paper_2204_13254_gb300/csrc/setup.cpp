@@ -402,6 +402,7 @@ void build_tasks(const dd_handle* h, int mode, int rows, std::vector<GemvTask>& 
         if (mode == GEMV_CORNER) { r0 = md.nI; r1 = md.nr; }
         if (mode == GEMV_RECOVER) { r0 = 0; r1 = md.nr; }
         if (mode == GEMV_SCHUR_G) { r0 = md.nI; r1 = md.nr; }
+        if (mode == GEMV_COUPLED) { r0 = md.nI; r1 = md.ns; }
         for (int32_t a = r0; a < r1; a += rows) tl.push_back({s, a, std::min(r1, a + rows), 0});
     }
 }

@@ -18,9 +18,11 @@ LIB_PATH = os.path.join(_HERE, "libdd.so")
 DD_OK, DD_ERR_ARG, DD_ERR_MESH, DD_ERR_PARTITION, DD_ERR_NOT_SPD = 0, 1, 2, 3, 4
 DD_ERR_NO_CONVERGENCE, DD_ERR_NONFINITE, DD_ERR_TIMEOUT, DD_ERR_CUDA, DD_ERR_STATE = 5, 6, 7, 8, 9
 DD_FP64, DD_MIXED = 0, 1
+DD_SOLVER_SCHUR_CG, DD_SOLVER_COUPLED_GMRES = 0, 1
+DD_MAX_RESTART = 32
 
 SYMBOLS = ["dd_setup", "dd_set_params", "dd_get_sizes", "dd_get_maps", "dd_set_probes", "dd_bind_workspace",
-           "dd_factor", "dd_step", "dd_schur_apply", "dd_schur_apply_static", "dd_probe", "dd_adjoint_reset",
+           "dd_factor", "dd_step", "dd_schur_apply", "dd_schur_apply_static", "dd_coupled_apply", "dd_probe", "dd_adjoint_reset",
            "dd_adjoint_step", "dd_probe_seed", "dd_autotune", "dd_get_tiles", "dd_set_beam", "dd_pic_step",
            "dd_pic_state", "dd_get_state", "dd_set_state", "dd_profile",
            "dd_destroy", "dd_last_error"]
@@ -36,7 +38,7 @@ class dd_mesh(C.Structure):
 class dd_params(C.Structure):
     _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("max_it", C.c_int), ("precond", C.c_int),
                 ("warm_start", C.c_int), ("refine_tol", C.c_double), ("max_refine", C.c_int), ("chunk", C.c_int),
-                ("use_graph", C.c_int)]
+                ("use_graph", C.c_int), ("solver", C.c_int), ("restart", C.c_int)]
 
 
 class dd_sizes(C.Structure):
@@ -82,6 +84,7 @@ def load_library(path: str = LIB_PATH):
         "dd_step": (C.c_int, [vp, vp, vp, C.POINTER(dd_stats), vp]),
         "dd_schur_apply": (C.c_int, [vp, vp, vp, vp]),
         "dd_schur_apply_static": (C.c_int, [vp, vp, vp, vp]),
+        "dd_coupled_apply": (C.c_int, [vp, vp, vp, vp]),
         "dd_probe": (C.c_int, [vp, vp, vp]),
         "dd_get_state": (C.c_int, [vp, vp, vp, C.POINTER(i64), vp]),
         "dd_set_state": (C.c_int, [vp, vp, vp, i64, vp]),
@@ -131,8 +134,9 @@ def _stream(stream=None):
 
 
 def make_params(precision=DD_FP64, tol=1e-12, max_it=500, precond=1, warm_start=1, refine_tol=1e-12, max_refine=4,
-                chunk=8, use_graph=0):
-    return dd_params(precision, tol, max_it, precond, warm_start, refine_tol, max_refine, chunk, use_graph)
+                chunk=8, use_graph=0, solver=DD_SOLVER_SCHUR_CG, restart=20):
+    return dd_params(precision, tol, max_it, precond, warm_start, refine_tol, max_refine, chunk, use_graph, solver,
+                     restart)
 
 
 # ---- C-ABI-named wrappers ------------------------------------------------------
@@ -213,6 +217,11 @@ def dd_schur_apply_static(h, lam, out, stream=None):
     _check(h, lib().dd_schur_apply_static(h, _ptr(lam), _ptr(out), _stream(stream)))
 
 
+def dd_coupled_apply(h, u, out, stream=None):
+    """out = [F_rr u_l + F_rc u_c ; -F_rc^T u_l + K~cc u_c] (Eqs. F1lr + F1uc), u = [u_l; u_c]."""
+    _check(h, lib().dd_coupled_apply(h, _ptr(u), _ptr(out), _stream(stream)))
+
+
 def dd_probe(h, out, stream=None):
     _check(h, lib().dd_probe(h, _ptr(out), _stream(stream)))
 
@@ -265,7 +274,7 @@ def dd_pic_state(h, x=None, status=None, G=None, b=None, stream=None):
     return nf.value
 
 
-GEMV_KINDS = ["local", "corner_rows", "corner_coupling", "recover", "coarse", "iface_rows"]
+GEMV_KINDS = ["local", "corner_rows", "corner_coupling", "recover", "coarse", "iface_rows", "coupled"]
 
 
 def dd_autotune(h, cache_path=None, stream=None):
@@ -276,10 +285,12 @@ def dd_autotune(h, cache_path=None, stream=None):
 
 
 def dd_get_tiles(h):
-    lpr = (C.c_int32 * 12)()
-    rows = (C.c_int32 * 12)()
+    nk = len(GEMV_KINDS)
+    lpr = (C.c_int32 * (2 * nk))()
+    rows = (C.c_int32 * (2 * nk))()
     _check(h, lib().dd_get_tiles(h, lpr, rows))
-    return {("fp64", "fp32")[p]: {GEMV_KINDS[k]: (lpr[6 * p + k], rows[6 * p + k]) for k in range(6)} for p in range(2)}
+    return {("fp64", "fp32")[p]: {GEMV_KINDS[k]: (lpr[nk * p + k], rows[nk * p + k]) for k in range(nk)}
+            for p in range(2)}
 
 
 def dd_profile(h, enable=-1, read=True, stream=None):
@@ -351,6 +362,12 @@ class FieldSolver:
         import torch
         out = torch.empty_like(lam)
         dd_schur_apply(self.h, lam, out)
+        return out
+
+    def coupled_apply(self, u):
+        import torch
+        out = torch.empty_like(u)
+        dd_coupled_apply(self.h, u, out)
         return out
 
     def set_beam(self, x_inj, v_inj, t_inj, q, qm):
