@@ -2,8 +2,12 @@
 """Benchmark of the MFETI-DP1 Maxwell field-solve time step on GB300.
 
 One "step" is one implicit Newmark time step of the edge-element wave
-equation solved by MFETI-DP1 (right-hand side SpMV, local solves, interface
-CG with the corner coarse problem, recovery): every stage of the hot path.
+equation solved by MFETI-DP1 (right-hand side SpMV, local solves, the
+interface solve, recovery): every stage of the hot path.  The interface solve
+is the coupled system of Eqs. F1lr + F1uc by GMRES(20) with the diagonal
+preconditioner (the paper's Fig. fetiIter setting; --solver gmres, default)
+or the Schur complement of Eq. f1schur by Jacobi CG (--solver cg); the line
+also times the other solver and both at the paper's tolerance 1e-6.
 
 Default workload: the mixed-precision configuration -- a PEC unit cube of
 48^3 Kuhn cubes (663,552 tets, 753,552 interior edge unknowns) torn into
@@ -58,6 +62,8 @@ def parse():
     ap.add_argument("--chunk", type=int, default=2, help="CG iterations per graph WHILE-body launch")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default GEMV tiles")
     ap.add_argument("--warm", type=int, default=1, help="interface-CG warm start: 1 previous step, 2 extrapolated")
+    ap.add_argument("--solver", choices=["cg", "gmres"], default="gmres",
+                    help="interface solver of the headline runs: Schur CG (Eq. f1schur) or coupled GMRES(20)")
     ap.add_argument("--no-gmres", action="store_true",
                     help="skip the coupled-GMRES(20) vs Schur-CG comparison at the paper's tolerance 1e-6")
     ap.add_argument("--cavity", type=int, nargs=2, metavar=("N", "K"), default=None,
@@ -278,13 +284,15 @@ def run_ours(args, rank, world, local):
     clocks = Clocks(local)
     g = 0 if args.eager else 1
     ch = 8 if args.eager else args.chunk
-    p64 = D.make_params(precision=D.DD_FP64, tol=args.tol64, use_graph=g, chunk=ch, warm_start=args.warm)
+    solver_of = {"cg": D.DD_SOLVER_SCHUR_CG, "gmres": D.DD_SOLVER_COUPLED_GMRES}
+    sv = solver_of[args.solver]
+    p64 = D.make_params(precision=D.DD_FP64, tol=args.tol64, use_graph=g, chunk=ch, warm_start=args.warm, solver=sv)
     p32 = D.make_params(precision=D.DD_MIXED, tol=args.tol32, refine_tol=args.refine_tol, max_refine=6, use_graph=g,
-                        chunk=ch, warm_start=args.warm)
+                        chunk=ch, warm_start=args.warm, solver=sv)
     # event profiling needs eager launches (events are recorded around every launch)
-    p64e = D.make_params(precision=D.DD_FP64, tol=args.tol64, warm_start=args.warm)
+    p64e = D.make_params(precision=D.DD_FP64, tol=args.tol64, warm_start=args.warm, solver=sv)
     p32e = D.make_params(precision=D.DD_MIXED, tol=args.tol32, refine_tol=args.refine_tol, max_refine=6,
-                         warm_start=args.warm)
+                         warm_start=args.warm, solver=sv)
     nan = float("nan")
     ms64 = ms32 = nan
     it64 = it32 = ref32 = np.zeros(1)
@@ -311,6 +319,16 @@ def run_ours(args, rank, world, local):
                         "gpu_launches": int(profg["total_launches"])},
               "schur_cg": {"steps_per_s": K * 1e3 / msc, "ms_per_step": msc / K, "iters_per_step": float(np.mean(itc))},
               "rel_diff_fields": float(torch.linalg.norm(eg - ec) / torch.linalg.norm(ec))}
+        # the other solver at the headline's mixed-precision settings
+        other = "gmres" if args.solver == "cg" else "cg"
+        po = D.make_params(precision=D.DD_MIXED, tol=args.tol32, refine_tol=args.refine_tol, max_refine=6,
+                           use_graph=g, chunk=ch, warm_start=1, solver=solver_of[other])
+        mso, ito, refo, profo, eo = run_steps(po, False)
+        gm[f"mixed_{other}"] = {"steps_per_s": K * 1e3 / mso, "ms_per_step": mso / K,
+                                "iters_per_step": float(np.mean(ito)), "refinements_per_step": float(np.mean(refo)),
+                                "gpu_launches": int(profo["total_launches"]),
+                                "rel_err_vs_fp64": (float(torch.linalg.norm(eo - e64) / torch.linalg.norm(e64))
+                                                    if e64 is not None else None)}
     # per-stage breakdown: a second pass over the same steps with CUDA events around every launch
     launches64 = prof64["total_launches"] if prof64 else None
     launches32 = prof32["total_launches"] if prof32 else None
@@ -505,7 +523,9 @@ def main():
         "e2e": {"value": aggregate_replicas(r["ms_e2e"], K, world, same)[1], "unit": "steps/s",
                 "h2d_bytes_per_step": int(sizes.n_dof * 8), "d2h_bytes_per_step": int(sizes.n_dof * 8)},
         "gpu_launches": int(r["launches32"] if head == "mixed" else r["launches64"]),
-        "launch_mode": "eager" if args.eager else f"CUDA graph per step (CG WHILE node, {args.chunk} it/body)",
+        "launch_mode": "eager" if args.eager else f"CUDA graph per step (Krylov loop as WHILE node, {args.chunk} it/body)",
+        "interface_solver": {"cg": "Schur complement (Eq. f1schur), Jacobi CG",
+                             "gmres": "coupled Eqs. F1lr + F1uc, GMRES(20), diagonal preconditioner"}[args.solver],
         "warm_start": {1: "previous step's multipliers", 2: "extrapolated multipliers 2l(n-1)-l(n-2)"}.get(args.warm, args.warm),
         "clocks": r["clocks"],
     }

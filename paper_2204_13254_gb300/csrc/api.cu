@@ -58,7 +58,6 @@ int check_params(dd_handle* h, const dd_params& p) {
         return h->fail(DD_ERR_ARG, "solver must be DD_SOLVER_SCHUR_CG or DD_SOLVER_COUPLED_GMRES");
     if (p.solver == DD_SOLVER_COUPLED_GMRES) {
         if (p.restart < 1 || p.restart > kMaxRestart) return h->fail(DD_ERR_ARG, "restart must be in 1..DD_MAX_RESTART");
-        if (p.precision != DD_FP64) return h->fail(DD_ERR_ARG, "the coupled GMRES solver runs in DD_FP64 only");
         if (p.warm_start == 2) return h->fail(DD_ERR_ARG, "warm_start 2 applies to the Schur CG only");
     }
     return DD_OK;
@@ -268,6 +267,9 @@ size_t dd_workspace_layout(dd_handle* h, bool assign) {
     L.take(d.vC, nc);
     L.take(d.xC, nc);
     L.take(d.xC_adj, nc);
+    L.take(d.xCf_adj, nc);
+    L.take(d.xC_scratch, nc);
+    L.take(d.xCf_scratch, nc);
     L.take(d.dinvC, nc);
     {
         const int64_t nu = (int64_t)(nm + nc);
@@ -276,6 +278,7 @@ size_t dd_workspace_layout(dd_handle* h, bool assign) {
         L.take(d.Vk, (size_t)(kMaxRestart + 1) * (size_t)h->gm_ldv);
         L.take(d.tu, (size_t)nu);
         L.take(d.zu, (size_t)nu);
+        L.take(d.zuf, (size_t)nu);
         L.take(d.gs, 1);
         L.take(d.gpart, (size_t)(kMaxRestart + 1) * (size_t)h->gm_blocks);
     }
@@ -426,6 +429,7 @@ int create_handle(dd_handle* h, cudaStream_t s, cudaGraphConditionalHandle* hc) 
 }
 
 cudaStream_t capture_stream(dd_handle* h, int depth) {
+    if (depth < 0 || depth >= (int)(sizeof(h->gstream) / sizeof(h->gstream[0]))) return nullptr;
     if (!h->gstream[depth]) {
         cudaStream_t cs;
         if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
@@ -441,49 +445,55 @@ int read_gm(dd_handle* h, GmresScalars* out, cudaStream_t s) {
     return (int)cudaStreamSynchronize(s);
 }
 
-// Coupled solve of Eqs. F1lr + F1uc (FP64) by restarted GMRES with right
-// diagonal preconditioning: u = [lambda; x_c] from b = [d_r; f~_c] (in d.g,
-// d.fC), left in d.lam and d.xC.  Eager mode polls the control words after
-// every cycle start and every `chunk` Arnoldi steps; graph mode captures the
-// restart cycles as a conditional WHILE node whose body holds the cycle start,
-// a nested WHILE node over the Arnoldi steps and the update of u.
-int gmres_solve(dd_handle* h, double tol, bool warm, int* it_out, double* res_out, cudaStream_t s, int depth) {
+// Coupled solve of Eqs. F1lr + F1uc by restarted GMRES with right diagonal
+// preconditioning: u = [lambda; x_c] from b = [d_r; f~_c] (in d.g, d.fC), left
+// in d.lam and d.xC (DD_MIXED: FP32 GEMVs on FP32 shadows, FP64 Krylov vectors
+// and least-squares problem).  Eager mode polls the control words after every
+// cycle start and every `chunk` Arnoldi steps; graph mode captures the restart
+// cycles as a conditional WHILE node whose body holds the cycle start, a nested
+// WHILE node over the Arnoldi steps and the update of u.
+int gmres_solve(dd_handle* h, int prec, double tol, bool warm, int* it_out, double* res_out, cudaStream_t s,
+                int depth, int adaptive) {
     const size_t nm = h->mult_dof.size(), nc = h->corner_dof.size();
     *it_out = 0;
     *res_out = 0.0;
     if (nm + nc == 0) return DD_OK;
+    const Vecs V = vecs(h, prec);
     const bool use_warm = warm && (h->lam_valid || h->capturing);
     if (!use_warm) {
         if (nm) CK(h, (int)cudaMemsetAsync(h->d.lam, 0, sizeof(double) * nm, s), "memset");
         if (nc) CK(h, (int)cudaMemsetAsync(h->d.xC, 0, sizeof(double) * nc, s), "memset");
+        if (V.f32 && nm) CK(h, (int)cudaMemsetAsync(V.lamf, 0, sizeof(float) * nm, s), "memset");
+        if (V.f32 && nc) CK(h, (int)cudaMemsetAsync(V.xCf, 0, sizeof(float) * nc, s), "memset");
     }
+    float* zuf = V.f32 ? h->d.zuf : nullptr;
     // x = [B_r^T u_l ; -u_c] over the [Gamma | c] columns of every local matrix
-    const XSrc xs_x = xsrc(X_LAMBDA_CV, h->d.lam, nullptr, nullptr, nullptr, h->d.xC, nullptr);
-    const XSrc xs_z = xsrc(X_LAMBDA_CV, h->d.zu, nullptr, nullptr, nullptr, h->d.zu + nm, nullptr);
-    const GemvOut go = gout(h->d.w, nullptr, nullptr, nullptr, 1.0);
-    const double mbc = mb(h, GEMV_COUPLED, DD_FP64);
+    const XSrc xs_x = xsrc(X_LAMBDA_CV, h->d.lam, nullptr, V.lamf, nullptr, h->d.xC, V.xCf);
+    const XSrc xs_z = xsrc(X_LAMBDA_CV, h->d.zu, nullptr, zuf, nullptr, h->d.zu + nm, zuf ? zuf + nm : nullptr);
+    const GemvOut go = V.f32 ? gout(nullptr, nullptr, V.wf, nullptr, 1.0) : gout(h->d.w, nullptr, nullptr, nullptr, 1.0);
+    const double mbc = mb(h, GEMV_COUPLED, prec);
     const int32_t* skip = &h->d.gs->skip;
     auto cycle_start = [&](cudaStream_t st, int have_q, unsigned long long cond_inner) -> int {
         if (have_q) {
             Prof P(h, ST_SCHUR, st, 1, mbc);
-            CK(h, launch_gemv(h, GEMV_COUPLED, DD_FP64, xs_x, go, false, st), "coupled operator on x");
+            CK(h, launch_gemv(h, GEMV_COUPLED, prec, xs_x, go, false, st), "coupled operator on x");
         }
         Prof P(h, ST_VEC, st, 2);
-        CK(h, launch_gm_start(h, have_q, cond_inner, st), "gmres start");
-        CK(h, launch_gm_normalize(h, st), "gmres normalize");
+        CK(h, launch_gm_start(h, have_q, V.wf, cond_inner, st), "gmres start");
+        CK(h, launch_gm_normalize(h, zuf, st), "gmres normalize");
         return DD_OK;
     };
     // one Arnoldi step; its full-work count is added once the step count is known
     auto arnoldi = [&](cudaStream_t st, unsigned long long cond_inner) -> int {
         {
             Prof P(h, ST_SCHUR, st, 1);
-            CK(h, launch_gemv(h, GEMV_COUPLED, DD_FP64, xs_z, go, false, st, skip), "coupled operator");
+            CK(h, launch_gemv(h, GEMV_COUPLED, prec, xs_z, go, false, st, skip), "coupled operator");
         }
         Prof P(h, ST_VEC, st, 4);
-        CK(h, launch_gm_pass(h, 0, 0ull, st), "gmres pass 0");
-        CK(h, launch_gm_pass(h, 1, 0ull, st), "gmres pass 1");
-        CK(h, launch_gm_pass(h, 2, cond_inner, st), "gmres pass 2");
-        CK(h, launch_gm_normalize(h, st), "gmres normalize");
+        CK(h, launch_gm_pass(h, 0, V.wf, 0ull, st), "gmres pass 0");
+        CK(h, launch_gm_pass(h, 1, V.wf, 0ull, st), "gmres pass 1");
+        CK(h, launch_gm_pass(h, 2, V.wf, cond_inner, st), "gmres pass 2");
+        CK(h, launch_gm_normalize(h, zuf, st), "gmres normalize");
         return DD_OK;
     };
     if (h->capturing) {
@@ -492,7 +502,8 @@ int gmres_solve(dd_handle* h, double tol, bool warm, int* it_out, double* res_ou
         if (rc) return rc;
         {
             Prof P(h, ST_VEC, s, 1);
-            CK(h, launch_gm_init(h, tol, h->prm.max_it, h->prm.restart, (unsigned long long)ho, s), "gmres init");
+            CK(h, launch_gm_init(h, tol, h->prm.max_it, h->prm.restart, adaptive, (unsigned long long)ho, s),
+               "gmres init");
         }
         cudaGraph_t body;
         rc = add_conditional(h, s, ho, cudaGraphCondTypeWhile, &body);
@@ -529,7 +540,7 @@ int gmres_solve(dd_handle* h, double tol, bool warm, int* it_out, double* res_ou
         }
         if (!brc) {
             Prof P(h, ST_VEC, bo, 1);
-            const int urc = launch_gm_update(h, (unsigned long long)ho, bo);
+            const int urc = launch_gm_update(h, V.lamf, V.xCf, (unsigned long long)ho, bo);
             if (urc) brc = cuda_fail(h, urc, "gmres update");
         }
         cudaGraph_t out_body;
@@ -547,7 +558,7 @@ int gmres_solve(dd_handle* h, double tol, bool warm, int* it_out, double* res_ou
     }
     {
         Prof P(h, ST_VEC, s, 1);
-        CK(h, launch_gm_init(h, tol, h->prm.max_it, h->prm.restart, 0ull, s), "gmres init");
+        CK(h, launch_gm_init(h, tol, h->prm.max_it, h->prm.restart, 0, 0ull, s), "gmres init");
     }
     GmresScalars c;
     bool first = true;
@@ -569,7 +580,7 @@ int gmres_solve(dd_handle* h, double tol, bool warm, int* it_out, double* res_ou
         }
         {
             Prof P(h, ST_VEC, s, 1);
-            CK(h, launch_gm_update(h, 0ull, s), "gmres update");
+            CK(h, launch_gm_update(h, V.lamf, V.xCf, 0ull, s), "gmres update");
         }
         if (c.final) break;
     }
@@ -606,12 +617,12 @@ int dd_solve(dd_handle* h, int prec, double tol, bool warm, int* it_out, double*
     }
     if (h->prm.solver == DD_SOLVER_COUPLED_GMRES) {
         // [lambda; x_c] from the coupled Eqs. F1lr + F1uc, then x_r      Eq. rF1
-        const int status = gmres_solve(h, tol, warm, it_out, res_out, s, depth);
+        const int status = gmres_solve(h, prec, tol, warm, it_out, res_out, s, depth, adaptive);
         if (status != DD_OK && status != DD_ERR_NO_CONVERGENCE) return status;
         const std::string msg = h->err;
         {
             Prof P(h, ST_RECOVER, s, 1, mb(h, GEMV_RECOVER, prec));
-            CK(h, launch_gemv(h, GEMV_RECOVER, prec, xsrc(X_RECOVER, h->d.lam, h->d.xC, nullptr, nullptr),
+            CK(h, launch_gemv(h, GEMV_RECOVER, prec, xsrc(X_RECOVER, h->d.lam, h->d.xC, V.lamf, V.xCf),
                               gout(h->d.x, h->d.y, nullptr, nullptr, 1.0), false, s), "recover");
         }
         h->err = msg;
@@ -964,6 +975,25 @@ int extrapolate_lambda(dd_handle* h, int prec, cudaStream_t s) {
     return DD_OK;
 }
 
+// Mixed refinement: the first pass's interface solution (lambda and, for the
+// coupled GMRES, x_c) is the next step's warm start; the later passes solve for
+// corrections.  save: copy it aside after the first pass; !save: put it back.
+int keep_first_pass(dd_handle* h, bool save, cudaStream_t s) {
+    const size_t nm = h->mult_dof.size(), nc = h->corner_dof.size();
+    auto cp = [&](void* a, void* b, size_t n) -> int {
+        if (!n) return DD_OK;
+        CK(h, (int)cudaMemcpyAsync(save ? b : a, save ? a : b, n, cudaMemcpyDeviceToDevice, s), "warm-start copy");
+        return DD_OK;
+    };
+    int rc = cp(h->d.lam, h->d.lam_scratch, sizeof(double) * nm);
+    if (!rc) rc = cp(h->d.lamf, h->d.lamf_scratch, sizeof(float) * nm);
+    if (!rc && h->prm.solver == DD_SOLVER_COUPLED_GMRES) {
+        rc = cp(h->d.xC, h->d.xC_scratch, sizeof(double) * nc);
+        if (!rc) rc = cp(h->d.xCf, h->d.xCf_scratch, sizeof(float) * nc);
+    }
+    return rc;
+}
+
 // One level of the Newmark recurrence from (u_n, u_nm1) into u_np1:
 // A delta = -dt^2 S u_n + src_sign * src (subassembled, source on the owner),
 // u_np1 = 2 u_n - u_nm1 + delta.  Used by the forward step (src = d2g, sign -1)
@@ -994,11 +1024,9 @@ int advance(dd_handle* h, const double* u_n, const double* u_nm1, double* u_np1,
         PcgScalars hs;
         for (int k = 0; k < h->prm.max_refine; ++k) {
             const bool warm = (k == 0) && h->prm.warm_start != 0;
-            if (k == 1 && !h->mult_dof.empty()) {
-                CK(h, (int)cudaMemcpyAsync(h->d.lam_scratch, h->d.lam, sizeof(double) * h->mult_dof.size(),
-                                           cudaMemcpyDeviceToDevice, s), "save lambda");
-                CK(h, (int)cudaMemcpyAsync(h->d.lamf_scratch, h->d.lamf, sizeof(float) * h->mult_dof.size(),
-                                           cudaMemcpyDeviceToDevice, s), "save lambda");
+            if (k == 1) {
+                const int xrc = keep_first_pass(h, true, s);
+                if (xrc) return xrc;
             }
             int it = 0;
             double r = 0.0;
@@ -1028,11 +1056,9 @@ int advance(dd_handle* h, const double* u_n, const double* u_nm1, double* u_np1,
             if (resid <= h->prm.refine_tol) break;
             if (k + 1 == h->prm.max_refine) status = DD_ERR_NO_CONVERGENCE;
         }
-        if (refinements > 1 && !h->mult_dof.empty()) {
-            CK(h, (int)cudaMemcpyAsync(h->d.lam, h->d.lam_scratch, sizeof(double) * h->mult_dof.size(),
-                                       cudaMemcpyDeviceToDevice, s), "restore lambda");
-            CK(h, (int)cudaMemcpyAsync(h->d.lamf, h->d.lamf_scratch, sizeof(float) * h->mult_dof.size(),
-                                       cudaMemcpyDeviceToDevice, s), "restore lambda");
+        if (refinements > 1) {
+            const int xrc = keep_first_pass(h, false, s);
+            if (xrc) return xrc;
         }
         if (status == DD_ERR_NONFINITE) return status;
         {
@@ -1138,11 +1164,8 @@ int step_body_graph(dd_handle* h, const double* u_n, const double* u_nm1, double
         CK(h, launch_residual_local(h, s), "residual");
         CK(h, launch_assembled_norm(h, 0, h->d.bf, s), "norm r");
     }
-    const size_t nm = h->mult_dof.size();
-    if (nm) {  // keep the first pass's multipliers as the next step's warm start
-        CK(h, (int)cudaMemcpyAsync(h->d.lam_scratch, h->d.lam, sizeof(double) * nm, cudaMemcpyDeviceToDevice, s), "save");
-        CK(h, (int)cudaMemcpyAsync(h->d.lamf_scratch, h->d.lamf, sizeof(float) * nm, cudaMemcpyDeviceToDevice, s), "save");
-    }
+    rc = keep_first_pass(h, true, s);   // the first pass's solution is the next step's warm start
+    if (rc) return rc;
     if (h->prm.max_refine > 1) {
         rc = refine_chain(h, 1, 0, s, u_n, u_nm1);
         if (rc) return rc;
@@ -1151,10 +1174,8 @@ int step_body_graph(dd_handle* h, const double* u_n, const double* u_nm1, double
         Prof P(h, ST_VEC, s, 1);
         CK(h, launch_refine_cond(h, 0ull, s), "refine final");
     }
-    if (nm) {
-        CK(h, (int)cudaMemcpyAsync(h->d.lam, h->d.lam_scratch, sizeof(double) * nm, cudaMemcpyDeviceToDevice, s), "restore");
-        CK(h, (int)cudaMemcpyAsync(h->d.lamf, h->d.lamf_scratch, sizeof(float) * nm, cudaMemcpyDeviceToDevice, s), "restore");
-    }
+    rc = keep_first_pass(h, false, s);
+    if (rc) return rc;
     Prof P(h, ST_VEC, s, 1);
     CK(h, launch_advance(h, u_n, u_nm1, h->d.delta, u_np1, s), "advance");
     return DD_OK;
@@ -1220,8 +1241,10 @@ int dd_step_graph(dd_handle* h, const double* d2g, double* e_out, dd_stats* stat
         CK(h, (int)cudaMemsetAsync(h->d.lam, 0, sizeof(double) * h->mult_dof.size(), s), "memset");
         CK(h, (int)cudaMemsetAsync(h->d.lamf, 0, sizeof(float) * h->mult_dof.size(), s), "memset");
     }
-    if (!h->lam_valid && h->prm.solver == DD_SOLVER_COUPLED_GMRES && !h->corner_dof.empty())
+    if (!h->lam_valid && h->prm.solver == DD_SOLVER_COUPLED_GMRES && !h->corner_dof.empty()) {
         CK(h, (int)cudaMemsetAsync(h->d.xC, 0, sizeof(double) * h->corner_dof.size(), s), "memset");
+        CK(h, (int)cudaMemsetAsync(h->d.xCf, 0, sizeof(float) * h->corner_dof.size(), s), "memset");
+    }
     CK(h, (int)cudaGraphLaunch((cudaGraphExec_t)h->gexec[phase], s), "graph launch");
     h->lam_valid = true;
     double* e_np1 = h->d.e[(phase + 1) % 3];
@@ -1254,6 +1277,7 @@ void swap_lambda(dd_handle* h) {
     std::swap(h->d.lamf, h->d.lamf_adj);
     std::swap(h->d.lam_prev, h->d.lam_prev_adj);
     std::swap(h->d.xC, h->d.xC_adj);
+    std::swap(h->d.xCf, h->d.xCf_adj);
     std::swap(h->lam_valid, h->lam_adj_valid);
 }
 

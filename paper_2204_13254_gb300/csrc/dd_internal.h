@@ -213,11 +213,15 @@ struct DevPtrs {
     double* vC = nullptr;
     double* xC = nullptr;
     double* xC_adj = nullptr;        // adjoint march's corner solution (coupled GMRES warm start)
+    float* xCf_adj = nullptr;
     double* dinvC = nullptr;         // [n_corner] inverse diagonal of K~cc
     // coupled GMRES vectors (n_u = n_lambda + n_corner, leading dimension gm_ldv)
     double* Vk = nullptr;            // [(kMaxRestart+1) * gm_ldv] Krylov basis
     double* tu = nullptr;            // [n_u] Arnoldi work vector
     double* zu = nullptr;            // [n_u] D^-1 v_j, the operator's input
+    float* zuf = nullptr;            // [n_u] FP32 shadow of zu (DD_MIXED)
+    double* xC_scratch = nullptr;    // [n_corner] first-pass corner solution kept across refinement passes
+    float* xCf_scratch = nullptr;
     GmresScalars* gs = nullptr;
     double* gpart = nullptr;         // [(kMaxRestart+1) * gm_blocks] block partials
     float* fCf = nullptr;
@@ -315,7 +319,7 @@ struct dd_handle {
 
     // CUDA-graph mode (dd_params.use_graph): one executable graph per time-level phase
     void* gexec[3] = {nullptr, nullptr, nullptr};   // cudaGraphExec_t
-    void* gstream[8] = {};                          // private capture streams, one per nesting depth
+    void* gstream[16] = {};                         // private capture streams, one per nesting depth
     bool capturing = false;
     int64_t g_kernels_main = 0;      // kernels outside conditional bodies
     int64_t g_kernels_iter = 0;      // kernels per CG iteration (WHILE body)
@@ -399,11 +403,13 @@ int launch_faraday(const dd_handle* h, const double* e_np1, const double* e_n, d
 
 // gmres.cu: coupled-system GMRES (u = [lambda; x_c])
 int launch_corner_diag(const dd_handle* h, void* stream);
-int launch_gm_init(const dd_handle* h, double tol, int max_it, int m, unsigned long long cond_outer, void* stream);
-int launch_gm_start(const dd_handle* h, int have_q, unsigned long long cond_inner, void* stream);
-int launch_gm_normalize(const dd_handle* h, void* stream);
-int launch_gm_pass(const dd_handle* h, int phase, unsigned long long cond_inner, void* stream);
-int launch_gm_update(const dd_handle* h, unsigned long long cond_outer, void* stream);
+// wf: FP32 GEMV output (DD_MIXED) or null; zuf/lamf/xCf: FP32 shadows to write (DD_MIXED) or null
+int launch_gm_init(const dd_handle* h, double tol, int max_it, int m, int adaptive, unsigned long long cond_outer,
+                   void* stream);
+int launch_gm_start(const dd_handle* h, int have_q, const float* wf, unsigned long long cond_inner, void* stream);
+int launch_gm_normalize(const dd_handle* h, float* zuf, void* stream);
+int launch_gm_pass(const dd_handle* h, int phase, const float* wf, unsigned long long cond_inner, void* stream);
+int launch_gm_update(const dd_handle* h, float* lamf, float* xCf, unsigned long long cond_outer, void* stream);
 int launch_gm_combine(const dd_handle* h, double* out, void* stream);
 
 // GEMV x-source kinds (see kernels.cu)

@@ -12,6 +12,9 @@
 // they enter the GEMV, and x += D^-1 V y at the end of a cycle, so the
 // residual tested is the unpreconditioned b - M x.
 //
+// In DD_MIXED the Krylov vectors (basis, work vector) are FP32, the
+// least-squares problem and the iterate FP64.
+//
 // One Arnoldi step = GEMV + three vector kernels + one normalisation:
 //   pass 0: t = M D^-1 v_j (combine),        h1 = V^T t
 //   pass 1: t -= V h1,                        h2 = V^T t   (classical Gram-Schmidt, twice)
@@ -41,16 +44,25 @@ __device__ __forceinline__ double wsum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
+__device__ __forceinline__ float wsum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
 
-// (M u)_i from the GEMV output w per slot: jump over multiplier i, or minus the
-// assembly over the copies of corner i - n_lambda.
+__device__ __forceinline__ double wv(const double* __restrict__ w, const float* __restrict__ wf, int64_t slot) {
+    return wf ? (double)wf[slot] : w[slot];
+}
+
+// (M u)_i from the GEMV output per slot (w, or its FP32 form wf): jump over
+// multiplier i, or minus the assembly over the copies of corner i - n_lambda.
 __device__ __forceinline__ double combine(int64_t i, int64_t nl, const int64_t* __restrict__ ms,
                                           const int64_t* __restrict__ cp, const int64_t* __restrict__ cs,
-                                          const double* __restrict__ w) {
-    if (i < nl) return w[ms[2 * i]] - w[ms[2 * i + 1]];
+                                          const double* __restrict__ w, const float* __restrict__ wf) {
+    if (i < nl) return wv(w, wf, ms[2 * i]) - wv(w, wf, ms[2 * i + 1]);
     const int64_t c = i - nl;
     double s = 0.0;
-    for (int64_t k = cp[c]; k < cp[c + 1]; ++k) s += w[cs[k]];
+    for (int64_t k = cp[c]; k < cp[c + 1]; ++k) s += wv(w, wf, cs[k]);
     return -s;
 }
 
@@ -112,7 +124,14 @@ __global__ void k_corner_diag(int64_t nc, const int64_t* __restrict__ cp, const 
     }
 }
 
-__global__ void k_gm_init(GmresScalars* gs, double tol, int max_it, int m, unsigned long long cond) {
+// adaptive: a later mixed-precision refinement pass only has to cut the current
+// step residual (relative to ||b||) to refine_tol, with a 3x margin.
+__global__ void k_gm_init(GmresScalars* gs, const PcgScalars* sc, double tol, double refine_tol, int adaptive,
+                          int max_it, int m, unsigned long long cond) {
+    if (adaptive) {
+        const double resid = sc->norm_b2 > 0.0 ? sqrt(sc->norm_r2 / sc->norm_b2) : 0.0;
+        if (resid > 0.0) tol = fmin(0.1, fmax(tol, 0.3 * refine_tol / resid));
+    }
     gs->it = 0;
     gs->final = 0;
     gs->converged = 0;
@@ -129,12 +148,17 @@ __global__ void k_gm_init(GmresScalars* gs, double tol, int max_it, int m, unsig
 }
 
 // Start of a cycle: t = b - M x (have_q: w holds the GEMV of x), beta = ||t||,
-// ||b||; decides whether the solve is already over.
+// ||b||; decides whether the solve is already over.  VT: type of the Krylov
+// vectors (double; float for the FP32 inner solves of DD_MIXED, whose tolerance
+// is far above FP32 rounding -- GB300's FP64 rate would otherwise make the
+// Gram-Schmidt arithmetic a sizeable part of the step).
+template <typename VT>
 __global__ void __launch_bounds__(kT) k_gm_start(int64_t nl, int64_t nc, const int64_t* __restrict__ ms,
                                                  const int64_t* __restrict__ cp, const int64_t* __restrict__ cs,
-                                                 const double* __restrict__ w, int have_q,
+                                                 const double* __restrict__ w, const float* __restrict__ wf,
+                                                 int have_q,
                                                  const double* __restrict__ g, const double* __restrict__ fC,
-                                                 double* __restrict__ tu, GmresScalars* gs, PcgScalars* sc,
+                                                 VT* __restrict__ tu, GmresScalars* gs, PcgScalars* sc,
                                                  double* __restrict__ partials, unsigned long long cond) {
     const int64_t nu = nl + nc;
     double rr = 0.0, bb = 0.0;
@@ -143,9 +167,9 @@ __global__ void __launch_bounds__(kT) k_gm_start(int64_t nl, int64_t nc, const i
         const int64_t i = (int64_t)blockIdx.x * kGmChunk + e * kT + threadIdx.x;
         if (i < nu) {
             const double b = i < nl ? g[i] : fC[i - nl];
-            const double r = b - (have_q ? combine(i, nl, ms, cp, cs, w) : 0.0);
+            const VT r = (VT)(b - (have_q ? combine(i, nl, ms, cp, cs, w, wf) : 0.0));
             tu[i] = r;
-            rr += r * r;
+            rr += (double)r * (double)r;
             bb += b * b;
         }
     }
@@ -189,48 +213,52 @@ __global__ void __launch_bounds__(kT) k_gm_start(int64_t nl, int64_t nc, const i
     }
 }
 
-// v_j = t / hnext, z = D^-1 v_j
-__global__ void k_gm_normalize(int64_t nl, int64_t nc, double* __restrict__ V, int64_t ldv,
-                               const double* __restrict__ tu, const double* __restrict__ dl,
-                               const double* __restrict__ dc, double* __restrict__ zu, const GmresScalars* gs) {
+// v_j = t / hnext, z = D^-1 v_j: FP64 z for the FP64 GEMV, FP32 z for the FP32 one
+template <typename VT>
+__global__ void k_gm_normalize(int64_t nl, int64_t nc, VT* __restrict__ V, int64_t ldv, const VT* __restrict__ tu,
+                               const double* __restrict__ dl, const double* __restrict__ dc, double* __restrict__ zu,
+                               float* __restrict__ zuf, const GmresScalars* gs) {
     if (gs->skip) return;
     const int64_t nu = nl + nc;
-    double* vj = V + (int64_t)gs->j * ldv;
-    const double inv = 1.0 / gs->hnext;
+    VT* vj = V + (int64_t)gs->j * ldv;
+    const VT inv = (VT)(1.0 / gs->hnext);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nu; i += (int64_t)gridDim.x * blockDim.x) {
-        const double v = tu[i] * inv;
+        const VT v = tu[i] * inv;
+        const VT z = (VT)dinv_at(i, nl, dl, dc) * v;
         vj[i] = v;
-        zu[i] = dinv_at(i, nl, dl, dc) * v;
+        if (zu) zu[i] = (double)z;
+        if (zuf) zuf[i] = (float)z;
     }
 }
 
 // Gram-Schmidt passes of Arnoldi column j (see the file comment).
-template <int PHASE>
+template <int PHASE, typename VT>
 __global__ void __launch_bounds__(kT) k_gm_pass(int64_t nl, int64_t nc, const int64_t* __restrict__ ms,
                                                 const int64_t* __restrict__ cp, const int64_t* __restrict__ cs,
-                                                const double* __restrict__ w, const double* __restrict__ V,
-                                                int64_t ldv, double* __restrict__ tu, GmresScalars* gs,
+                                                const double* __restrict__ w, const float* __restrict__ wf,
+                                                const VT* __restrict__ V, int64_t ldv,
+                                                VT* __restrict__ tu, GmresScalars* gs,
                                                 PcgScalars* sc, double* __restrict__ partials,
                                                 unsigned long long cond) {
     if (gs->skip) return;
-    __shared__ double coef[kM1];
+    __shared__ VT coef[kM1];
     __shared__ double red[kM1][kWarps];
     const int64_t nu = nl + nc;
     const int j = gs->j;
     const int nv = j + 1;
     const int nb = gridDim.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (PHASE > 0 && threadIdx.x < nv) coef[threadIdx.x] = PHASE == 1 ? gs->h1[threadIdx.x] : gs->h2[threadIdx.x];
+    if (PHASE > 0 && threadIdx.x < nv) coef[threadIdx.x] = (VT)(PHASE == 1 ? gs->h1[threadIdx.x] : gs->h2[threadIdx.x]);
     __syncthreads();
-    double t[kGmElems];
+    VT t[kGmElems];
 #pragma unroll
     for (int e = 0; e < kGmElems; ++e) {
         const int64_t i = (int64_t)blockIdx.x * kGmChunk + e * kT + threadIdx.x;
-        t[e] = 0.0;
+        t[e] = (VT)0;
         if (i < nu) {
-            double v;
+            VT v;
             if (PHASE == 0) {
-                v = combine(i, nl, ms, cp, cs, w);
+                v = (VT)combine(i, nl, ms, cp, cs, w, wf);
             } else {
                 v = tu[i];
                 for (int k = 0; k < nv; ++k) v -= coef[k] * V[(int64_t)k * ldv + i];
@@ -242,14 +270,14 @@ __global__ void __launch_bounds__(kT) k_gm_pass(int64_t nl, int64_t nc, const in
     if (PHASE < 2) {
         // partial dots with v_0 .. v_j
         for (int k = 0; k < nv; ++k) {
-            double p = 0.0;
+            VT p = (VT)0;
 #pragma unroll
             for (int e = 0; e < kGmElems; ++e) {
                 const int64_t i = (int64_t)blockIdx.x * kGmChunk + e * kT + threadIdx.x;
                 if (i < nu) p += t[e] * V[(int64_t)k * ldv + i];
             }
             p = wsum(p);
-            if (lane == 0) red[k][warp] = p;
+            if (lane == 0) red[k][warp] = (double)p;
         }
         __syncthreads();
         if (threadIdx.x < nv) {
@@ -275,10 +303,10 @@ __global__ void __launch_bounds__(kT) k_gm_pass(int64_t nl, int64_t nc, const in
         return;
     }
     // PHASE 2: ||t||, Givens, end of cycle
-    double p = 0.0;
+    VT pt = (VT)0;
 #pragma unroll
-    for (int e = 0; e < kGmElems; ++e) p += t[e] * t[e];
-    p = block_sum1(p);
+    for (int e = 0; e < kGmElems; ++e) pt += t[e] * t[e];
+    const double p = block_sum1((double)pt);
     if (threadIdx.x == 0) partials[blockIdx.x] = p;
     if (!last_block(&gs->counter[3])) return;
     const double tot = __shfl_sync(0xffffffffu, reduce_partials(partials, 0, nb), 0);
@@ -337,22 +365,30 @@ __global__ void __launch_bounds__(kT) k_gm_pass(int64_t nl, int64_t nc, const in
 
 // End of a cycle: x += D^-1 V y (x = [lambda; x_c] in place); at the end of the
 // solve, publish its outcome in the CG scalars (step statistics, solve end).
-__global__ void k_gm_update(int64_t nl, int64_t nc, const double* __restrict__ V, int64_t ldv,
+template <typename VT>
+__global__ void k_gm_update(int64_t nl, int64_t nc, const VT* __restrict__ V, int64_t ldv,
                             const double* __restrict__ dl, const double* __restrict__ dc, double* __restrict__ lam,
-                            double* __restrict__ xC, const GmresScalars* gs, PcgScalars* sc,
-                            unsigned long long cond) {
-    __shared__ double y[kMaxRestart];
+                            double* __restrict__ xC, float* __restrict__ lamf, float* __restrict__ xCf,
+                            const GmresScalars* gs, PcgScalars* sc, unsigned long long cond) {
+    __shared__ VT y[kMaxRestart];
     const int k = gs->k;
-    if (threadIdx.x < k) y[threadIdx.x] = gs->y[threadIdx.x];
+    if (threadIdx.x < k) y[threadIdx.x] = (VT)gs->y[threadIdx.x];
     __syncthreads();
     const int64_t nu = nl + nc;
     if (k > 0) {
         for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nu; i += (int64_t)gridDim.x * blockDim.x) {
-            double v = 0.0;
-            for (int q = 0; q < k; ++q) v += y[q] * V[(int64_t)q * ldv + i];
-            v *= dinv_at(i, nl, dl, dc);
-            if (i < nl) lam[i] += v;
-            else xC[i - nl] += v;
+            VT vs = (VT)0;
+            for (int q = 0; q < k; ++q) vs += y[q] * V[(int64_t)q * ldv + i];
+            const double v = (double)vs * dinv_at(i, nl, dl, dc);
+            if (i < nl) {
+                const double x = lam[i] + v;
+                lam[i] = x;
+                if (lamf) lamf[i] = (float)x;
+            } else {
+                const double x = xC[i - nl] + v;
+                xC[i - nl] = x;
+                if (xCf) xCf[i - nl] = (float)x;
+            }
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -370,7 +406,7 @@ __global__ void k_gm_update(int64_t nl, int64_t nc, const double* __restrict__ V
 __global__ void k_gm_combine(int64_t nl, int64_t nc, const int64_t* __restrict__ ms, const int64_t* __restrict__ cp,
                              const int64_t* __restrict__ cs, const double* __restrict__ w, double* __restrict__ out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nl + nc; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = combine(i, nl, ms, cp, cs, w);
+        out[i] = combine(i, nl, ms, cp, cs, w, nullptr);
 }
 
 int vec_blocks(int64_t n) {
@@ -389,54 +425,77 @@ int launch_corner_diag(const dd_handle* h, void* stream) {
     return (int)cudaGetLastError();
 }
 
-int launch_gm_init(const dd_handle* h, double tol, int max_it, int m, unsigned long long cond_outer, void* stream) {
-    k_gm_init<<<1, 1, 0, S(stream)>>>(h->d.gs, tol, max_it, m, cond_outer);
+int launch_gm_init(const dd_handle* h, double tol, int max_it, int m, int adaptive, unsigned long long cond_outer,
+                   void* stream) {
+    k_gm_init<<<1, 1, 0, S(stream)>>>(h->d.gs, h->d.sc, tol, h->prm.refine_tol, adaptive, max_it, m, cond_outer);
     return (int)cudaGetLastError();
 }
 
-int launch_gm_start(const dd_handle* h, int have_q, unsigned long long cond_inner, void* stream) {
+int launch_gm_start(const dd_handle* h, int have_q, const float* wf, unsigned long long cond_inner, void* stream) {
     const int64_t nl = (int64_t)h->mult_dof.size(), nc = (int64_t)h->corner_dof.size();
-    k_gm_start<<<h->gm_blocks, kT, 0, S(stream)>>>(nl, nc, h->d.mult_slot, h->d.corner_ptr, h->d.corner_slot, h->d.w,
-                                                   have_q, h->d.g, h->d.fC, h->d.tu, h->d.gs, h->d.sc, h->d.gpart,
-                                                   cond_inner);
+    if (wf)
+        k_gm_start<float><<<h->gm_blocks, kT, 0, S(stream)>>>(
+            nl, nc, h->d.mult_slot, h->d.corner_ptr, h->d.corner_slot, h->d.w, wf, have_q, h->d.g, h->d.fC,
+            reinterpret_cast<float*>(h->d.tu), h->d.gs, h->d.sc, h->d.gpart, cond_inner);
+    else
+        k_gm_start<double><<<h->gm_blocks, kT, 0, S(stream)>>>(nl, nc, h->d.mult_slot, h->d.corner_ptr,
+                                                               h->d.corner_slot, h->d.w, nullptr, have_q, h->d.g,
+                                                               h->d.fC, h->d.tu, h->d.gs, h->d.sc, h->d.gpart,
+                                                               cond_inner);
     return (int)cudaGetLastError();
 }
 
-int launch_gm_normalize(const dd_handle* h, void* stream) {
+int launch_gm_normalize(const dd_handle* h, float* zuf, void* stream) {
     const int64_t nl = (int64_t)h->mult_dof.size(), nc = (int64_t)h->corner_dof.size();
     const bool pc = h->prm.precond != 0;
-    k_gm_normalize<<<vec_blocks(nl + nc), kT, 0, S(stream)>>>(nl, nc, h->d.Vk, h->gm_ldv, h->d.tu,
-                                                               pc ? h->d.dinv : nullptr, pc ? h->d.dinvC : nullptr,
-                                                               h->d.zu, h->d.gs);
+    const double* dl = pc ? h->d.dinv : nullptr;
+    const double* dc = pc ? h->d.dinvC : nullptr;
+    if (zuf)
+        k_gm_normalize<float><<<vec_blocks(nl + nc), kT, 0, S(stream)>>>(
+            nl, nc, reinterpret_cast<float*>(h->d.Vk), h->gm_ldv, reinterpret_cast<const float*>(h->d.tu), dl, dc,
+            nullptr, zuf, h->d.gs);
+    else
+        k_gm_normalize<double><<<vec_blocks(nl + nc), kT, 0, S(stream)>>>(nl, nc, h->d.Vk, h->gm_ldv, h->d.tu, dl, dc,
+                                                                           h->d.zu, nullptr, h->d.gs);
     return (int)cudaGetLastError();
 }
 
-int launch_gm_pass(const dd_handle* h, int phase, unsigned long long cond_inner, void* stream) {
+template <int PHASE, typename VT>
+void run_pass(const dd_handle* h, const float* wf, unsigned long long cond, cudaStream_t st) {
     const int64_t nl = (int64_t)h->mult_dof.size(), nc = (int64_t)h->corner_dof.size();
     const DevPtrs& d = h->d;
-    switch (phase) {
-        case 0:
-            k_gm_pass<0><<<h->gm_blocks, kT, 0, S(stream)>>>(nl, nc, d.mult_slot, d.corner_ptr, d.corner_slot, d.w,
-                                                             d.Vk, h->gm_ldv, d.tu, d.gs, d.sc, d.gpart, 0ull);
-            break;
-        case 1:
-            k_gm_pass<1><<<h->gm_blocks, kT, 0, S(stream)>>>(nl, nc, d.mult_slot, d.corner_ptr, d.corner_slot, d.w,
-                                                             d.Vk, h->gm_ldv, d.tu, d.gs, d.sc, d.gpart, 0ull);
-            break;
-        default:
-            k_gm_pass<2><<<h->gm_blocks, kT, 0, S(stream)>>>(nl, nc, d.mult_slot, d.corner_ptr, d.corner_slot, d.w,
-                                                             d.Vk, h->gm_ldv, d.tu, d.gs, d.sc, d.gpart, cond_inner);
-            break;
+    k_gm_pass<PHASE, VT><<<h->gm_blocks, kT, 0, st>>>(nl, nc, d.mult_slot, d.corner_ptr, d.corner_slot, d.w, wf,
+                                                      reinterpret_cast<const VT*>(d.Vk), h->gm_ldv,
+                                                      reinterpret_cast<VT*>(d.tu), d.gs, d.sc, d.gpart, cond);
+}
+
+int launch_gm_pass(const dd_handle* h, int phase, const float* wf, unsigned long long cond_inner, void* stream) {
+    const cudaStream_t st = S(stream);
+    if (wf) {
+        if (phase == 0) run_pass<0, float>(h, wf, 0ull, st);
+        else if (phase == 1) run_pass<1, float>(h, wf, 0ull, st);
+        else run_pass<2, float>(h, wf, cond_inner, st);
+    } else {
+        if (phase == 0) run_pass<0, double>(h, nullptr, 0ull, st);
+        else if (phase == 1) run_pass<1, double>(h, nullptr, 0ull, st);
+        else run_pass<2, double>(h, nullptr, cond_inner, st);
     }
     return (int)cudaGetLastError();
 }
 
-int launch_gm_update(const dd_handle* h, unsigned long long cond_outer, void* stream) {
+int launch_gm_update(const dd_handle* h, float* lamf, float* xCf, unsigned long long cond_outer, void* stream) {
     const int64_t nl = (int64_t)h->mult_dof.size(), nc = (int64_t)h->corner_dof.size();
     const bool pc = h->prm.precond != 0;
-    k_gm_update<<<vec_blocks(nl + nc), kT, 0, S(stream)>>>(nl, nc, h->d.Vk, h->gm_ldv, pc ? h->d.dinv : nullptr,
-                                                            pc ? h->d.dinvC : nullptr, h->d.lam, h->d.xC, h->d.gs,
-                                                            h->d.sc, cond_outer);
+    const double* dl = pc ? h->d.dinv : nullptr;
+    const double* dc = pc ? h->d.dinvC : nullptr;
+    if (lamf)
+        k_gm_update<float><<<vec_blocks(nl + nc), kT, 0, S(stream)>>>(
+            nl, nc, reinterpret_cast<const float*>(h->d.Vk), h->gm_ldv, dl, dc, h->d.lam, h->d.xC, lamf, xCf, h->d.gs,
+            h->d.sc, cond_outer);
+    else
+        k_gm_update<double><<<vec_blocks(nl + nc), kT, 0, S(stream)>>>(nl, nc, h->d.Vk, h->gm_ldv, dl, dc, h->d.lam,
+                                                                        h->d.xC, nullptr, nullptr, h->d.gs, h->d.sc,
+                                                                        cond_outer);
     return (int)cudaGetLastError();
 }
 
