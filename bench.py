@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--warm", type=int, default=1, help="interface-CG warm start: 1 previous step, 2 extrapolated")
     ap.add_argument("--solver", choices=["cg", "gmres"], default="gmres",
                     help="interface solver of the headline runs: Schur CG (Eq. f1schur) or coupled GMRES(20)")
+    ap.add_argument("--no-sym", action="store_true",
+                    help="DD_MIXED GEMVs on the dense FP32 copy instead of the packed symmetric tiles")
     ap.add_argument("--no-gmres", action="store_true",
                     help="skip the coupled-GMRES(20) vs Schur-CG comparison at the paper's tolerance 1e-6")
     ap.add_argument("--cavity", type=int, nargs=2, metavar=("N", "K"), default=None,
@@ -286,13 +288,14 @@ def run_ours(args, rank, world, local):
     ch = 8 if args.eager else args.chunk
     solver_of = {"cg": D.DD_SOLVER_SCHUR_CG, "gmres": D.DD_SOLVER_COUPLED_GMRES}
     sv = solver_of[args.solver]
+    sym = 0 if args.no_sym else 1
     p64 = D.make_params(precision=D.DD_FP64, tol=args.tol64, use_graph=g, chunk=ch, warm_start=args.warm, solver=sv)
     p32 = D.make_params(precision=D.DD_MIXED, tol=args.tol32, refine_tol=args.refine_tol, max_refine=6, use_graph=g,
-                        chunk=ch, warm_start=args.warm, solver=sv)
+                        chunk=ch, warm_start=args.warm, solver=sv, sym_fp32=sym)
     # event profiling needs eager launches (events are recorded around every launch)
     p64e = D.make_params(precision=D.DD_FP64, tol=args.tol64, warm_start=args.warm, solver=sv)
     p32e = D.make_params(precision=D.DD_MIXED, tol=args.tol32, refine_tol=args.refine_tol, max_refine=6,
-                         warm_start=args.warm, solver=sv)
+                         warm_start=args.warm, solver=sv, sym_fp32=sym)
     nan = float("nan")
     ms64 = ms32 = nan
     it64 = it32 = ref32 = np.zeros(1)
@@ -322,7 +325,7 @@ def run_ours(args, rank, world, local):
         # the other solver at the headline's mixed-precision settings
         other = "gmres" if args.solver == "cg" else "cg"
         po = D.make_params(precision=D.DD_MIXED, tol=args.tol32, refine_tol=args.refine_tol, max_refine=6,
-                           use_graph=g, chunk=ch, warm_start=1, solver=solver_of[other])
+                           use_graph=g, chunk=ch, warm_start=1, solver=solver_of[other], sym_fp32=sym)
         mso, ito, refo, profo, eo = run_steps(po, False)
         gm[f"mixed_{other}"] = {"steps_per_s": K * 1e3 / mso, "ms_per_step": mso / K,
                                 "iters_per_step": float(np.mean(ito)), "refinements_per_step": float(np.mean(refo)),
@@ -524,6 +527,7 @@ def main():
                 "h2d_bytes_per_step": int(sizes.n_dof * 8), "d2h_bytes_per_step": int(sizes.n_dof * 8)},
         "gpu_launches": int(r["launches32"] if head == "mixed" else r["launches64"]),
         "launch_mode": "eager" if args.eager else f"CUDA graph per step (Krylov loop as WHILE node, {args.chunk} it/body)",
+        "fp32_storage": "dense" if args.no_sym else "packed symmetric 64x64 tiles (local solve, interface rows, coupled operator)",
         "interface_solver": {"cg": "Schur complement (Eq. f1schur), Jacobi CG",
                              "gmres": "coupled Eqs. F1lr + F1uc, GMRES(20), diagonal preconditioner"}[args.solver],
         "warm_start": {1: "previous step's multipliers", 2: "extrapolated multipliers 2l(n-1)-l(n-2)"}.get(args.warm, args.warm),

@@ -114,7 +114,12 @@ typedef struct {
  *            Gram-Schmidt applied twice, Givens rotations; warm start from
  *            the previous solve's [lambda; x_c].  DD_FP64 and warm_start 0/1
  *            only (DD_ERR_ARG otherwise).  K~cc^-1 is not used by this solver.
- * restart    GMRES restart length m, 1..DD_MAX_RESTART (the paper: 20). */
+ * restart    GMRES restart length m, 1..DD_MAX_RESTART (the paper: 20).
+ * sym_fp32   DD_MIXED: 1 = the FP32 GEMVs over symmetric blocks (local solve,
+ *            interface rows, coupled operator) read packed lower-triangular
+ *            FP32 tiles (the swept local matrix is J times a symmetric matrix,
+ *            J = diag(I_r, -I_c)), about 60 % of the dense bytes; 0 = the
+ *            dense FP32 copy.  Results differ by FP32 rounding only. */
 typedef struct {
     int precision;
     double tol;
@@ -127,6 +132,7 @@ typedef struct {
     int use_graph;
     int solver;
     int restart;
+    int sym_fp32;
 } dd_params;
 
 /* Sizes of a set-up problem. */

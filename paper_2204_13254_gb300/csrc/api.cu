@@ -47,6 +47,7 @@ dd_params default_params() {
     p.use_graph = 0;
     p.solver = DD_SOLVER_SCHUR_CG;
     p.restart = 20;
+    p.sym_fp32 = 1;
     return p;
 }
 
@@ -54,6 +55,7 @@ int check_params(dd_handle* h, const dd_params& p) {
     if (p.precision != DD_FP64 && p.precision != DD_MIXED) return h->fail(DD_ERR_ARG, "precision must be DD_FP64 or DD_MIXED");
     if (!(p.tol > 0.0) || p.max_it < 1 || p.chunk < 1 || p.max_refine < 1 || !(p.refine_tol > 0.0))
         return h->fail(DD_ERR_ARG, "tol, refine_tol must be > 0 and max_it, chunk, max_refine >= 1");
+    if (p.sym_fp32 != 0 && p.sym_fp32 != 1) return h->fail(DD_ERR_ARG, "sym_fp32 must be 0 or 1");
     if (p.solver != DD_SOLVER_SCHUR_CG && p.solver != DD_SOLVER_COUPLED_GMRES)
         return h->fail(DD_ERR_ARG, "solver must be DD_SOLVER_SCHUR_CG or DD_SOLVER_COUPLED_GMRES");
     if (p.solver == DD_SOLVER_COUPLED_GMRES) {
@@ -109,7 +111,9 @@ struct Prof {
 
 // algorithmic bytes of one full GEMV launch of `mode` at precision `prec`
 double mb(const dd_handle* h, int mode, int prec) {
-    return prec == DD_MIXED ? h->mode_bytes32[mode] : h->mode_bytes[mode];
+    if (prec != DD_MIXED) return h->mode_bytes[mode];
+    if (h->prm.sym_fp32 && h->sym_ok && h->mode_bytes_sym[mode] > 0.0) return h->mode_bytes_sym[mode];
+    return h->mode_bytes32[mode];
 }
 
 // Algorithmic bytes of one full launch: matrix elements read at the launch's
@@ -207,6 +211,12 @@ size_t dd_workspace_layout(dd_handle* h, bool assign) {
     L.take(d.probe_w, 18 * kMaxProbes);
     L.take(d.M64, (size_t)h->dense_elems);
     L.take(d.M32, (size_t)h->dense_elems);
+    L.take(d.Msym, (size_t)h->sym_elems);
+    L.take(d.symd, (size_t)h->n_sub);
+    for (int m = 0; m < GEMV_NMODES; ++m) {
+        int rm, cm;
+        if (sym_masks(m, &rm, &cm)) L.take(d.sym_rng[m], (size_t)h->n_sub * kSymCLMax * 2);
+    }
     L.take(d.K64, nc * (size_t)h->ldc);
     L.take(d.K32, nc * (size_t)h->ldc);
     L.take(d.Pinv, (size_t)(h->n_sub + 1) * kNB * kNB);
@@ -866,6 +876,9 @@ int dd_bind_workspace(dd_handle* h, void* dev, size_t bytes, void* stream) {
     CK(h, upload(h->d.col_loc, h->col_loc, s), "upload");
     CK(h, upload(h->d.col_dof, h->col_dof, s), "upload");
     CK(h, upload(h->d.Tval, h->Tval, s), "upload");
+    CK(h, upload(h->d.symd, h->sym, s), "upload");
+    for (int m = 0; m < GEMV_NMODES; ++m)
+        if (!h->sym_rng[m].empty()) CK(h, upload(h->d.sym_rng[m], h->sym_rng[m], s), "upload");
     CK(h, upload(h->d.Sval, h->Sval, s), "upload");
     for (int p = 0; p < 2; ++p)
         for (int m = 0; m < GEMV_NMODES; ++m) {
@@ -931,6 +944,10 @@ int dd_factor(dd_handle* h, double dt, void* stream) {
         Prof P(h, ST_FACTOR, s, 3);
         CK(h, launch_factor_finish(h, s), "factor finish");
         CK(h, launch_corner_diag(h, s), "coarse diagonal");
+    }
+    {
+        Prof P(h, ST_FACTOR, s, 1);
+        CK(h, launch_sym_pack(h, s), "packed symmetric tiles");
     }
     int32_t st = 0;
     CK(h, (int)cudaMemcpyAsync(&st, h->d.status, 4, cudaMemcpyDeviceToHost, s), "status");
@@ -1533,19 +1550,26 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
     for (char& c : key)
         if (c == ' ' || c == '\t') c = '_';
     std::map<std::pair<int, int>, TileCfg> found;
+    std::map<int, int> found_cl;   // packed symmetric modes: CTAs per subdomain (cache lines "key 2 mode cl 0")
+    int n_sym = 0;
+    for (int m = 0; m < GEMV_NMODES; ++m) {
+        int rm, cm;
+        if (sym_masks(m, &rm, &cm)) ++n_sym;
+    }
     if (cache_path && *cache_path) {
         std::ifstream f(cache_path);
         std::string line;
         while (std::getline(f, line)) {
             std::istringstream is(line);
             std::string k;
-            int p, m, lpr, rows;
-            if ((is >> k >> p >> m >> lpr >> rows) && k == key && p >= 0 && p < 2 && m >= 0 && m < GEMV_NMODES &&
-                (lpr == 8 || lpr == 16 || lpr == 32) && rows >= kMinRowsPerTask)
+            int p, m, lpr, rows, rm, cm;
+            if (!(is >> k >> p >> m >> lpr >> rows) || k != key || m < 0 || m >= GEMV_NMODES) continue;
+            if (p >= 0 && p < 2 && (lpr == 8 || lpr == 16 || lpr == 32) && rows >= kMinRowsPerTask)
                 found[{p, m}] = TileCfg{lpr, rows};
+            if (p == 2 && sym_masks(m, &rm, &cm) && (lpr == 1 || lpr == 2 || lpr == 4 || lpr == 8)) found_cl[m] = lpr;
         }
     }
-    const bool cached = found.size() == (size_t)(2 * GEMV_NMODES);
+    const bool cached = found.size() == (size_t)(2 * GEMV_NMODES) && found_cl.size() == (size_t)n_sym;
     cudaEvent_t e0, e1;
     CK(h, (int)cudaEventCreate(&e0), "event");
     CK(h, (int)cudaEventCreate(&e1), "event");
@@ -1563,8 +1587,47 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
         for (int p = 0; p < 2 && !rc; ++p) {
             const int prec = p == 0 ? DD_FP64 : DD_MIXED;
             for (int m = 0; m < GEMV_NMODES && !rc; ++m) {
+                int rm, cm;
+                const bool sym_saved = h->prm.sym_fp32 != 0;
+                if (p == 1 && h->sym_ok && sym_masks(m, &rm, &cm)) {
+                    // packed symmetric tiles: time 1, 2, 4 and 8 CTAs per subdomain
+                    h->prm.sym_fp32 = 1;
+                    XSrc xs{};
+                    xs.kind = X_FLAT;
+                    xs.v = h->d.b;
+                    xs.vf = h->d.bf;
+                    const GemvOut go{nullptr, nullptr, h->d.wf, nullptr, 1.0};
+                    float best = 1e30f;
+                    int bcl = h->sym_cl[m];
+                    for (int cl : {1, 2, 4, 8}) {
+                        sym_ranges(h, m, cl);
+                        rc = upload(h->d.sym_rng[m], h->sym_rng[m], s);
+                        for (int it = 0; it < 4 && !rc; ++it) {
+                            if (it == 1) rc = (int)cudaEventRecord(e0, s);
+                            if (!rc) rc = launch_gemv(h, m, DD_MIXED, xs, go, false, s);
+                        }
+                        if (!rc) rc = (int)cudaEventRecord(e1, s);
+                        if (!rc) rc = (int)cudaEventSynchronize(e1);
+                        float ms = 0.f;
+                        if (!rc) rc = (int)cudaEventElapsedTime(&ms, e0, e1);
+                        h->launches[ST_FACTOR] += 4;
+                        h->total_launches += 4;
+                        if (rc) break;
+                        if (ms < best) {
+                            best = ms;
+                            bcl = cl;
+                        }
+                    }
+                    found_cl[m] = bcl;
+                    if (rc) {
+                        h->prm.sym_fp32 = sym_saved ? 1 : 0;
+                        break;
+                    }
+                }
+                h->prm.sym_fp32 = 0;   // the dense tiles below time the dense kernel
                 if (h->tasks[p][m].empty()) {
                     found[{p, m}] = h->tile[p][m];
+                    h->prm.sym_fp32 = sym_saved ? 1 : 0;
                     continue;
                 }
                 const bool co = m == GEMV_COARSE;
@@ -1602,6 +1665,7 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
                         }
                     }
                 found[{p, m}] = bt;
+                h->prm.sym_fp32 = sym_saved ? 1 : 0;
             }
         }
         if (!rc && cache_path && *cache_path) {
@@ -1609,6 +1673,7 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
             for (const auto& kv : found)
                 f << key << "\t" << kv.first.first << "\t" << kv.first.second << "\t" << kv.second.lpr << "\t"
                   << kv.second.rows << "\n";
+            for (const auto& kv : found_cl) f << key << "\t2\t" << kv.first << "\t" << kv.second << "\t0\n";
         }
     }
     cudaEventDestroy(e0);
@@ -1621,6 +1686,10 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
             const int urc = upload_tasks(h, p, m, s);
             if (urc) return urc == DD_ERR_CUDA ? h->fail(DD_ERR_CUDA, "upload tasks") : urc;
         }
+    for (const auto& kv : found_cl) {
+        sym_ranges(h, kv.first, kv.second);
+        CK(h, upload(h->d.sym_rng[kv.first], h->sym_rng[kv.first], s), "upload ranges");
+    }
     CK(h, (int)cudaStreamSynchronize(s), "sync");
     drop_graphs(h);
     h->tuned = true;

@@ -20,6 +20,58 @@ struct MatDesc {
     int32_t ns;     // r + corner
 };
 
+#ifdef __CUDACC__
+#define DD_HD __host__ __device__
+#else
+#define DD_HD
+#endif
+
+// Packed symmetric FP32 storage of the swept local matrices (DD_MIXED GEMVs).
+// M_s = J S_s with S_s symmetric and J = diag(I_r, -I_c) (A_rr^-1 and the
+// corner Schur complement are symmetric, M_s[c][r] = -M_s[r][c]^T), so
+// M_s[i][j] = J_i J_j M_s[j][i] and the lower triangle determines M_s.  Each
+// group (interior I, interface Gamma, corner c) is padded to whole
+// kSymT x kSymT tiles; the tiles of the lower triangle (tile row a >= tile
+// column b) are stored one after the other in row order (a(a+1)/2 + b),
+// row-major inside a tile, zeros in the padding; diagonal tiles are stored
+// whole.
+constexpr int kSymT = 64;
+constexpr int kSymTile = kSymT * kSymT;
+constexpr int kSymCLMax = 8;       // most CTAs per subdomain (one thread-block cluster)
+constexpr int kSymStages = 4;      // TMA ring depth (tiles in flight per CTA)
+
+struct SymDesc {
+    int64_t toff;     // float offset of tile (0, 0) in the packed buffer
+    int64_t voff;     // first slot of the subdomain
+    int32_t n[3];     // nI, nGamma, nc
+    int32_t t0[4];    // first tile of each group; t0[3] = tiles per side
+};
+
+DD_HD inline int sym_group(const int32_t* t0, int a) { return a < t0[1] ? 0 : (a < t0[2] ? 1 : 2); }
+
+// Row and column groups (bit 0 I, bit 1 Gamma, bit 2 c) of the GEMV modes that
+// use the packed storage; false for the others.
+DD_HD inline bool sym_masks(int mode, int* rmask, int* cmask) {
+    switch (mode) {
+        case 0: *rmask = 7; *cmask = 3; return true;   // GEMV_LOCAL:   rows all, cols r
+        case 5: *rmask = 2; *cmask = 6; return true;   // GEMV_SCHUR_G: rows Gamma, cols Gamma c
+        case 6: *rmask = 6; *cmask = 6; return true;   // GEMV_COUPLED: rows Gamma c, cols Gamma c
+        default: return false;
+    }
+}
+
+// What stored tile (a, b), b <= a, contributes to y[R] = M[R, C] x[C]:
+// bit 0 direct (rows of a, columns of b), bit 1 mirrored (rows of b, columns
+// of a: the transposed tile), bit 2 the mirrored tile enters with sign -1.
+DD_HD inline int sym_tile_flags(const int32_t* t0, int a, int b, int rmask, int cmask) {
+    const int ga = sym_group(t0, a), gb = sym_group(t0, b);
+    int f = 0;
+    if (((rmask >> ga) & 1) && ((cmask >> gb) & 1)) f |= 1;
+    if (a != b && ((rmask >> gb) & 1) && ((cmask >> ga) & 1)) f |= 2;
+    if ((ga == 2) != (gb == 2)) f |= 4;
+    return f;
+}
+
 // One CTA of a batched GEMV: rows [row0, row1) of matrix `mat`.
 struct GemvTask {
     int32_t mat;
@@ -89,7 +141,7 @@ struct PcgScalars {
     int32_t it;       // iterations done
     int32_t done;     // 1 when converged (kernels become no-ops)
     int32_t status;   // DD_OK / DD_ERR_NONFINITE
-    int32_t pad;
+    int32_t wait_err; // nonzero once a bounded TMA wait of the packed-tile GEMV gave up
     double norm_b2;   // mixed mode: ||b||^2 of the step system
     double norm_r2;   // mixed mode: ||r||^2 of the current FP64 residual
     int32_t lam_levels;   // warm_start 2: multiplier history levels available (0, 1, 2)
@@ -160,6 +212,9 @@ struct DevPtrs {
     // dense operators
     double* M64 = nullptr;           // per-subdomain swept matrices
     float* M32 = nullptr;            // FP32 copy
+    float* Msym = nullptr;           // packed symmetric FP32 tiles (see SymDesc)
+    SymDesc* symd = nullptr;         // [n_sub]
+    int32_t* sym_rng[GEMV_NMODES] = {};   // [n_sub * kSymCLMax * 2] tile-row range of every CTA
     double* K64 = nullptr;           // K~cc^-1, n_corner x ldc
     float* K32 = nullptr;
     double* Pinv = nullptr;          // [n_sub+1][NB*NB] pivot-block inverses while factoring
@@ -286,6 +341,13 @@ struct dd_handle {
     int32_t ldc = 0;                 // leading dimension of K~cc
     int32_t max_nr = 0, max_ns = 0;
     std::vector<GemvTask> tasks[2][GEMV_NMODES];   // per precision (tile shapes may differ)
+    std::vector<SymDesc> sym;                      // packed symmetric storage per subdomain
+    int64_t sym_elems = 0;
+    int32_t sym_np_max = 0;                        // largest padded side (floats)
+    std::vector<int32_t> sym_rng[GEMV_NMODES];
+    int32_t sym_cl[GEMV_NMODES] = {4, 1, 1, 1, 1, 2, 2};   // CTAs per subdomain of each packed mode
+    int32_t sym_max_tiles = 0;                     // largest tile count of one subdomain
+    bool sym_ok = false;                           // the packed GEMV's shared memory fits one CTA
     size_t task_cap[GEMV_NMODES] = {};             // device capacity: tasks at the smallest row count
     TileCfg tile[2][GEMV_NMODES];                  // lanes per row and rows per CTA, per precision and mode
     bool tuned = false;
@@ -340,6 +402,7 @@ struct dd_handle {
     double bytes_per_launch[DD_N_STAGES] = {};  // algorithmic bytes of one full launch (RHS, refinement)
     double mode_bytes[GEMV_NMODES] = {};        // algorithmic bytes of one GEMV launch, FP64 matrices
     double mode_bytes32[GEMV_NMODES] = {};      // same with FP32 matrices
+    double mode_bytes_sym[GEMV_NMODES] = {};    // same with the packed symmetric FP32 tiles
 
     int fail(int code, const std::string& msg) {
         err = msg;
@@ -400,6 +463,13 @@ int launch_probe(const dd_handle* h, const double* e, double* out, void* stream)
 int launch_pic_move(const dd_handle* h, double t_n, double dt, const double* e_n, double* dep, void* stream);
 int launch_pic_source(const dd_handle* h, const double* dep_new, const double* dep_old, void* stream);
 int launch_faraday(const dd_handle* h, const double* e_np1, const double* e_n, double dt, void* stream);
+
+// symgemv.cu: packed symmetric FP32 storage and its GEMV
+void build_sym(dd_handle* h);
+void sym_ranges(dd_handle* h, int mode, int cl);
+int launch_sym_pack(const dd_handle* h, void* stream);
+int launch_symgemv(const dd_handle* h, int mode, XSrc xs, GemvOut go, const int32_t* skip, void* stream);
+size_t sym_smem_bytes(const dd_handle* h);
 
 // gmres.cu: coupled-system GMRES (u = [lambda; x_c])
 int launch_corner_diag(const dd_handle* h, void* stream);

@@ -371,6 +371,9 @@ int dd_build_host(dd_handle* h, const dd_mesh* mesh, const int32_t* part, int32_
     h->dense_elems = moff;
     h->ldc = (int32_t)((nc + 3) / 4 * 4);
 
+    build_sym(h);
+    h->sym_ok = sym_smem_bytes(h) <= 227 * 1024;
+
     // ---- batched GEMV task lists (default tiles; dd_autotune may change them) ------
     for (int mode = 0; mode < GEMV_NMODES; ++mode) {
         std::vector<GemvTask> cap;

@@ -38,7 +38,7 @@ class dd_mesh(C.Structure):
 class dd_params(C.Structure):
     _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("max_it", C.c_int), ("precond", C.c_int),
                 ("warm_start", C.c_int), ("refine_tol", C.c_double), ("max_refine", C.c_int), ("chunk", C.c_int),
-                ("use_graph", C.c_int), ("solver", C.c_int), ("restart", C.c_int)]
+                ("use_graph", C.c_int), ("solver", C.c_int), ("restart", C.c_int), ("sym_fp32", C.c_int)]
 
 
 class dd_sizes(C.Structure):
@@ -134,9 +134,9 @@ def _stream(stream=None):
 
 
 def make_params(precision=DD_FP64, tol=1e-12, max_it=500, precond=1, warm_start=1, refine_tol=1e-12, max_refine=4,
-                chunk=8, use_graph=0, solver=DD_SOLVER_SCHUR_CG, restart=20):
+                chunk=8, use_graph=0, solver=DD_SOLVER_SCHUR_CG, restart=20, sym_fp32=1):
     return dd_params(precision, tol, max_it, precond, warm_start, refine_tol, max_refine, chunk, use_graph, solver,
-                     restart)
+                     restart, sym_fp32)
 
 
 # ---- C-ABI-named wrappers ------------------------------------------------------

@@ -234,3 +234,38 @@ def test_extrapolated_warm_start_matches_oracle(prec):
     err = rel_err(f, ref["fields"])
     assert err[2:].max() <= (1e-10 if prec == D.DD_FP64 else 1e-8), err.max()
     fs.close()
+
+
+@pytest.mark.parametrize("solver", [D.DD_SOLVER_SCHUR_CG, D.DD_SOLVER_COUPLED_GMRES])
+def test_packed_symmetric_fp32_tiles(solver):
+    """DD_MIXED with the packed lower-triangular FP32 tiles (sym_fp32 = 1) and with
+    the dense FP32 copy (0), on a jittered RCB split whose group sizes are not
+    multiples of the tile edge: both within 1e-8 of the monolithic fields, with
+    about the same iteration counts, and the packed path deterministic."""
+    need_gpu()
+    nx, ny, nz = 10, 8, 8
+    L = (1.2, 1.0, 1.0)
+    xyz, tets = W.kuhn_box(nx, ny, nz, *L)
+    xyz, rng = W.jitter_nodes(xyz, L[0] / nx, L, 0.2, seed=9)
+    part = W.rcb_partition(W.tet_centroids(xyz, tets), 6, rng.uniform(0.6, 1.4, size=6))
+    w = W.Workload("ragged", xyz, tets, part, 6, rng.uniform(1, 4, size=len(tets)), 1.0, 30,
+                   W.z_line_node_pairs(nx, ny, nz, 5, 4))
+    space = fem.EdgeSpace(xyz, tets, w.eps)
+    T, S = space.assemble()
+    dt = 2.0 * newmark.cfl_dt(T, S)
+    n = 30
+    _, _, _, _, ref = oracle_run(w, dt, n)
+    runs = {}
+    for sym in (1, 0, 1):
+        prm = D.make_params(precision=D.DD_MIXED, tol=1e-5, refine_tol=1e-12, max_refine=6, solver=solver,
+                            sym_fp32=sym)
+        fs, f, _, stats = gpu_run(w, dt, n, prm, probes=False)
+        fs.close()
+        assert all(s["status"] == 0 for s in stats)
+        assert rel_err(f, ref["fields"])[2:].max() <= 1e-8, (sym, rel_err(f, ref["fields"]).max())
+        its = np.array([s["iters"] for s in stats])
+        if sym in runs:
+            assert np.array_equal(runs[sym][0], f)           # deterministic
+        else:
+            runs[sym] = (f, its)
+    assert np.all(np.abs(runs[1][1] - runs[0][1]) <= 3), (runs[1][1], runs[0][1])
