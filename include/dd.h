@@ -386,10 +386,15 @@ int dd_profile(dd_handle* h, int enable, dd_profile_stats* out, void* stream);
  * may be NULL) receives the wall time.  Synchronises `stream`. */
 int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* stream);
 
-/* Current tiles: lpr[p*6 + k], rows[p*6 + k] for precision p (0 FP64, 1 FP32)
+/* Current tiles: lpr[p*7 + k], rows[p*7 + k] for precision p (0 FP64, 1 FP32)
  * and GEMV kind k (0 local, 1 corner rows, 2 corner coupling, 3 recovery,
- * 4 coarse, 5 interface rows); host int32[12] each. */
+ * 4 coarse, 5 interface rows, 6 coupled operator) of the dense kernel; host
+ * int32[14] each.  Kinds 0, 5 and 6 run in DD_MIXED on the packed symmetric
+ * tiles when sym_fp32 = 1: cl[k] CTAs (one cluster) per subdomain and a TMA
+ * ring of st[k] tiles (host int32[7] each, 0 for the other kinds; either
+ * pointer may be NULL). */
 int dd_get_tiles(const dd_handle* h, int32_t* lpr, int32_t* rows);
+int dd_get_sym_config(const dd_handle* h, int32_t* cl, int32_t* st);
 
 void dd_destroy(dd_handle* h);
 const char* dd_last_error(const dd_handle* h);

@@ -1550,7 +1550,8 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
     for (char& c : key)
         if (c == ' ' || c == '\t') c = '_';
     std::map<std::pair<int, int>, TileCfg> found;
-    std::map<int, int> found_cl;   // packed symmetric modes: CTAs per subdomain (cache lines "key 2 mode cl 0")
+    std::map<int, std::pair<int, int>> found_cl;   // packed symmetric modes: (CTAs per subdomain, ring depth),
+                                                   // cache lines "key 2 mode cl st"
     int n_sym = 0;
     for (int m = 0; m < GEMV_NMODES; ++m) {
         int rm, cm;
@@ -1566,7 +1567,9 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
             if (!(is >> k >> p >> m >> lpr >> rows) || k != key || m < 0 || m >= GEMV_NMODES) continue;
             if (p >= 0 && p < 2 && (lpr == 8 || lpr == 16 || lpr == 32) && rows >= kMinRowsPerTask)
                 found[{p, m}] = TileCfg{lpr, rows};
-            if (p == 2 && sym_masks(m, &rm, &cm) && (lpr == 1 || lpr == 2 || lpr == 4 || lpr == 8)) found_cl[m] = lpr;
+            if (p == 2 && sym_masks(m, &rm, &cm) && (lpr == 1 || lpr == 2 || lpr == 4 || lpr == 8) && rows >= 2 &&
+                rows <= kSymStages)
+                found_cl[m] = {lpr, rows};
         }
     }
     const bool cached = found.size() == (size_t)(2 * GEMV_NMODES) && found_cl.size() == (size_t)n_sym;
@@ -1590,7 +1593,7 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
                 int rm, cm;
                 const bool sym_saved = h->prm.sym_fp32 != 0;
                 if (p == 1 && h->sym_ok && sym_masks(m, &rm, &cm)) {
-                    // packed symmetric tiles: time 1, 2, 4 and 8 CTAs per subdomain
+                    // packed symmetric tiles: time 1, 2, 4 and 8 CTAs per subdomain with rings of 2, 3 and 4 tiles
                     h->prm.sym_fp32 = 1;
                     XSrc xs{};
                     xs.kind = X_FLAT;
@@ -1598,8 +1601,10 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
                     xs.vf = h->d.bf;
                     const GemvOut go{nullptr, nullptr, h->d.wf, nullptr, 1.0};
                     float best = 1e30f;
-                    int bcl = h->sym_cl[m];
-                    for (int cl : {1, 2, 4, 8}) {
+                    std::pair<int, int> bcl{h->sym_cl[m], h->sym_st[m]};
+                    for (int cand = 0; cand < 12 && !rc; ++cand) {
+                        const int cl = 1 << (cand / 3), st = 2 + cand % 3;
+                        h->sym_st[m] = st;
                         sym_ranges(h, m, cl);
                         rc = upload(h->d.sym_rng[m], h->sym_rng[m], s);
                         for (int it = 0; it < 4 && !rc; ++it) {
@@ -1615,7 +1620,7 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
                         if (rc) break;
                         if (ms < best) {
                             best = ms;
-                            bcl = cl;
+                            bcl = {cl, st};
                         }
                     }
                     found_cl[m] = bcl;
@@ -1673,7 +1678,8 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
             for (const auto& kv : found)
                 f << key << "\t" << kv.first.first << "\t" << kv.first.second << "\t" << kv.second.lpr << "\t"
                   << kv.second.rows << "\n";
-            for (const auto& kv : found_cl) f << key << "\t2\t" << kv.first << "\t" << kv.second << "\t0\n";
+            for (const auto& kv : found_cl)
+                f << key << "\t2\t" << kv.first << "\t" << kv.second.first << "\t" << kv.second.second << "\n";
         }
     }
     cudaEventDestroy(e0);
@@ -1687,7 +1693,8 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
             if (urc) return urc == DD_ERR_CUDA ? h->fail(DD_ERR_CUDA, "upload tasks") : urc;
         }
     for (const auto& kv : found_cl) {
-        sym_ranges(h, kv.first, kv.second);
+        h->sym_st[kv.first] = kv.second.second;
+        sym_ranges(h, kv.first, kv.second.first);
         CK(h, upload(h->d.sym_rng[kv.first], h->sym_rng[kv.first], s), "upload ranges");
     }
     CK(h, (int)cudaStreamSynchronize(s), "sync");
@@ -1705,6 +1712,17 @@ int dd_get_tiles(const dd_handle* h, int32_t* lpr, int32_t* rows) {
             lpr[p * GEMV_NMODES + m] = h->tile[p][m].lpr;
             rows[p * GEMV_NMODES + m] = h->tile[p][m].rows;
         }
+    return DD_OK;
+}
+
+int dd_get_sym_config(const dd_handle* h, int32_t* cl, int32_t* st) {
+    if (!h) return DD_ERR_ARG;
+    for (int m = 0; m < GEMV_NMODES; ++m) {
+        int rm, cmk;
+        const bool on = sym_masks(m, &rm, &cmk);
+        if (cl) cl[m] = on ? h->sym_cl[m] : 0;
+        if (st) st[m] = on ? h->sym_st[m] : 0;
+    }
     return DD_OK;
 }
 

@@ -38,7 +38,7 @@ struct MatDesc {
 constexpr int kSymT = 64;
 constexpr int kSymTile = kSymT * kSymT;
 constexpr int kSymCLMax = 8;       // most CTAs per subdomain (one thread-block cluster)
-constexpr int kSymStages = 4;      // TMA ring depth (tiles in flight per CTA)
+constexpr int kSymStages = 4;      // deepest TMA ring (tiles in flight per CTA)
 
 struct SymDesc {
     int64_t toff;     // float offset of tile (0, 0) in the packed buffer
@@ -346,6 +346,7 @@ struct dd_handle {
     int32_t sym_np_max = 0;                        // largest padded side (floats)
     std::vector<int32_t> sym_rng[GEMV_NMODES];
     int32_t sym_cl[GEMV_NMODES] = {4, 1, 1, 1, 1, 2, 2};   // CTAs per subdomain of each packed mode
+    int32_t sym_st[GEMV_NMODES] = {4, 4, 4, 4, 4, 4, 4};   // TMA ring depth of each packed mode
     int32_t sym_max_tiles = 0;                     // largest tile count of one subdomain
     bool sym_ok = false;                           // the packed GEMV's shared memory fits one CTA
     size_t task_cap[GEMV_NMODES] = {};             // device capacity: tasks at the smallest row count

@@ -10,10 +10,10 @@
 // tile is read from HBM once for both roles, about 60 % of the dense bytes of
 // the local solve, the interface rows and the coupled operator.
 //
-// Work split: the cl CTAs of a cluster (1..kSymCLMax, per mode, chosen by
-// dd_autotune) share one subdomain by ranges of
+// Work split: the cl CTAs of a cluster (1..kSymCLMax; per mode, like the ring
+// depth st <= kSymStages, chosen by dd_autotune) share one subdomain by ranges of
 // tile rows (balanced on the host by tile count).  Each CTA streams its tiles
-// through a kSymStages-deep ring of shared-memory buffers filled by
+// through an st-deep ring of shared-memory buffers filled by
 // cp.async.bulk (one 16 KB copy per tile, completion on an mbarrier) issued by
 // one thread, and accumulates its partial y over the subdomain's whole padded
 // index range in shared memory:
@@ -124,23 +124,23 @@ __device__ __forceinline__ float wsumf(float v) {
 }
 
 // Shared-memory layout of k_symgemv (floats unless noted), span = the padded
-// index range the mode touches (from its first group on):
-//   ring [kSymStages][kSymTile] | x [span] | y [span] | red [2][4][64] | rowred [8][16] | bars (u64) [kSymStages]
-__host__ __device__ inline size_t sym_smem(int span) {
-    size_t f = (size_t)kSymStages * kSymTile + 2 * (size_t)span + 2 * 4 * 64 + 8 * 16;
+// index range the mode touches (from its first group on), st = ring depth:
+//   ring [st][kSymTile] | x [span] | y [span] | red [2][4][64] | rowred [8][16] | bars (u64) [kSymStages]
+__host__ __device__ inline size_t sym_smem(int span, int st) {
+    size_t f = (size_t)st * kSymTile + 2 * (size_t)span + 2 * 4 * 64 + 8 * 16;
     return f * sizeof(float) + kSymStages * sizeof(uint64_t);
 }
 
 __host__ __device__ inline int lowest_group(int mask) { return (mask & 1) ? 0 : ((mask & 2) ? 1 : 2); }
 
 __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ descs, const int32_t* __restrict__ ranges,
-                                                const float* __restrict__ Msym, int span_max, int cl, int rmask,
-                                                int cmask, XSrc xs, GemvOut go, const int32_t* __restrict__ skip,
-                                                int32_t* __restrict__ err) {
+                                                const float* __restrict__ Msym, int span_max, int cl, int st,
+                                                int rmask, int cmask, XSrc xs, GemvOut go,
+                                                const int32_t* __restrict__ skip, int32_t* __restrict__ err) {
     if (skip && *skip) return;   // the same word for every CTA of the grid
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float* ring = reinterpret_cast<float*>(smem_raw);
-    float* xsh = ring + kSymStages * kSymTile;   // index p - p_lo
+    float* xsh = ring + st * kSymTile;   // index p - p_lo
     float* ysh = xsh + span_max;
     float* red = ysh + span_max;        // [2][4][64]
     float* rowred = red + 2 * 4 * 64;   // [8][16]
@@ -157,13 +157,13 @@ __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ desc
     const int p_lo = G.first(lowest_group(rmask | cmask)) * kSymT;
     const int r_lo = G.first(lowest_group(rmask)) * kSymT;
 
-    // producer (thread 0): barriers, then the first kSymStages tiles, in flight
-    // while the CTA stages x
+    // producer (thread 0): barriers, then the first st tiles, in flight while
+    // the CTA stages x
     int pa = a0, pb = 0, pf = 0, issued = 0;
     if (tid == 0) {
-        for (int s = 0; s < kSymStages; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < st; ++s) mbar_init(&bars[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        for (int s = 0; s < kSymStages && G.next(rmask, cmask, a1, pa, pb, pf); ++s, ++pb, ++issued)
+        for (int s = 0; s < st && G.next(rmask, cmask, a1, pa, pb, pf); ++s, ++pb, ++issued)
             load_tile(ring + s * kSymTile, tiles + ((int64_t)pa * (pa + 1) / 2 + pb) * kSymTile, &bars[s]);
     }
     // x over the column groups (padded index space from p_lo), y = 0
@@ -209,8 +209,8 @@ __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ desc
                 xa[r] = xsh[ca * kSymT + rg * 16 + r - p_lo];
             }
         }
-        const int s = k % kSymStages;
-        const bool ok = mbar_wait(&bars[s], (uint32_t)(k / kSymStages) & 1u);
+        const int s = k % st;
+        const bool ok = mbar_wait(&bars[s], (uint32_t)(k / st) & 1u);
         const float* T = ring + s * kSymTile + rg * 16 * kSymT + j;
         const float xb = (cf & 1) ? xsh[cb * kSymT + j - p_lo] : 0.0f;
         float c0 = 0.0f, c1 = 0.0f;
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ desc
     }
     if (!bad && cur >= 0) flush(cur);
     if (bad && tid == 0) {
-        for (int q = k; q < issued; ++q) mbar_wait(&bars[q % kSymStages], (uint32_t)(q / kSymStages) & 1u);
+        for (int q = k; q < issued; ++q) mbar_wait(&bars[q % st], (uint32_t)(q / st) & 1u);
         atomicExch(err, 1);
     }
 
@@ -298,7 +298,7 @@ __global__ void k_sym_pack(const SymDesc* __restrict__ descs, const MatDesc* __r
 
 }  // namespace
 
-size_t sym_smem_bytes(const dd_handle* h) { return sym_smem(h->sym_np_max); }
+size_t sym_smem_bytes(const dd_handle* h) { return sym_smem(h->sym_np_max, kSymStages); }
 
 // Padded index range a mode touches in the largest subdomain (from its first group on).
 int sym_span(const dd_handle* h, int mode) {
@@ -398,9 +398,10 @@ int launch_symgemv(const dd_handle* h, int mode, XSrc xs, GemvOut go, const int3
     xs.slot_corner = h->d.slot_corner;
     xs.sc = h->d.sc;
     const int span = sym_span(h, mode);
-    const size_t smem = sym_smem(span);
+    const int st = h->sym_st[mode];
+    const size_t smem = sym_smem(span, st);
     cudaError_t e = cudaFuncSetAttribute(k_symgemv, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sym_smem(h->sym_np_max));
+                                         (int)sym_smem(h->sym_np_max, kSymStages));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_symgemv, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
@@ -419,6 +420,6 @@ int launch_symgemv(const dd_handle* h, int mode, XSrc xs, GemvOut go, const int3
     cfg.attrs = at;
     cfg.numAttrs = 1;
     return (int)cudaLaunchKernelEx(&cfg, k_symgemv, (const SymDesc*)h->d.symd, (const int32_t*)h->d.sym_rng[mode],
-                                   (const float*)h->d.Msym, span, cl, rmask, cmask, xs, go, skip,
+                                   (const float*)h->d.Msym, span, cl, st, rmask, cmask, xs, go, skip,
                                    &h->d.sc->wait_err);
 }

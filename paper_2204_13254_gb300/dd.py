@@ -23,7 +23,8 @@ DD_MAX_RESTART = 32
 
 SYMBOLS = ["dd_setup", "dd_set_params", "dd_get_sizes", "dd_get_maps", "dd_set_probes", "dd_bind_workspace",
            "dd_factor", "dd_step", "dd_schur_apply", "dd_schur_apply_static", "dd_coupled_apply", "dd_probe", "dd_adjoint_reset",
-           "dd_adjoint_step", "dd_probe_seed", "dd_autotune", "dd_get_tiles", "dd_set_beam", "dd_pic_step",
+           "dd_adjoint_step", "dd_probe_seed", "dd_autotune", "dd_get_tiles", "dd_get_sym_config", "dd_set_beam",
+           "dd_pic_step",
            "dd_pic_state", "dd_get_state", "dd_set_state", "dd_profile",
            "dd_destroy", "dd_last_error"]
 N_STAGES = 9
@@ -94,6 +95,7 @@ def load_library(path: str = LIB_PATH):
         "dd_probe_seed": (C.c_int, [vp, vp, C.c_double, vp, vp]),
         "dd_autotune": (C.c_int, [vp, C.c_char_p, C.POINTER(C.c_double), vp]),
         "dd_get_tiles": (C.c_int, [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+        "dd_get_sym_config": (C.c_int, [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
         "dd_set_beam": (C.c_int, [vp, C.POINTER(dd_beam)]),
         "dd_pic_step": (C.c_int, [vp, C.POINTER(dd_stats), vp]),
         "dd_pic_state": (C.c_int, [vp, vp, vp, vp, vp, C.POINTER(C.c_int64), vp]),
@@ -291,6 +293,15 @@ def dd_get_tiles(h):
     _check(h, lib().dd_get_tiles(h, lpr, rows))
     return {("fp64", "fp32")[p]: {GEMV_KINDS[k]: (lpr[nk * p + k], rows[nk * p + k]) for k in range(nk)}
             for p in range(2)}
+
+
+def dd_get_sym_config(h):
+    """Packed symmetric GEMV kinds: {kind: (CTAs per subdomain, TMA ring depth)}."""
+    nk = len(GEMV_KINDS)
+    cl = (C.c_int32 * nk)()
+    st = (C.c_int32 * nk)()
+    _check(h, lib().dd_get_sym_config(h, cl, st))
+    return {GEMV_KINDS[k]: (cl[k], st[k]) for k in range(nk) if cl[k]}
 
 
 def dd_profile(h, enable=-1, read=True, stream=None):

@@ -49,5 +49,5 @@ def test_autotune_results_and_cache(tmp_path):
         assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
         D.dd_autotune(fs.h, cache)               # complete cache entry: tiles read back, no timing
         assert D.dd_get_tiles(fs.h) == tiles
-        assert sum(1 for _ in open(cache)) == 2 * len(D.GEMV_KINDS) + 3      # + cluster sizes of the 3 packed modes
+        assert sum(1 for _ in open(cache)) == 2 * len(D.GEMV_KINDS) + 3      # + packed-mode cluster sizes and ring depths
         fs.close()
