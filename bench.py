@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--eager", action="store_true", help="time eager launches instead of the CUDA-graph step")
     ap.add_argument("--chunk", type=int, default=2, help="CG iterations per graph WHILE-body launch")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default GEMV tiles")
+    ap.add_argument("--tune-cache", default=None,
+                    help="autotuner cache file: read when it holds this problem, else written after timing "
+                         "(lets a profiled run reuse the tiles of an unprofiled one)")
     ap.add_argument("--warm", type=int, default=1, help="interface-CG warm start: 1 previous step, 2 extrapolated")
     ap.add_argument("--solver", choices=["cg", "gmres"], default="gmres",
                     help="interface solver of the headline runs: Schur CG (Eq. f1schur) or coupled GMRES(20)")
@@ -229,7 +232,7 @@ def run_ours(args, rank, world, local):
     t_factor = time.perf_counter() - t0
     t_tune, tiles = 0.0, None
     if not args.no_autotune:
-        t_tune = D.dd_autotune(fs.h, None)
+        t_tune = D.dd_autotune(fs.h, args.tune_cache)
         tiles = D.dd_get_tiles(fs.h)
         tiles["packed_fp32 (CTAs per subdomain, ring depth)"] = D.dd_get_sym_config(fs.h)
     n = fs.n_dof
