@@ -522,7 +522,9 @@ def main():
         "rel_err_mixed_vs_fp64": r["rel"],
         "setup_s": r["t_setup"], "factor_s": r["t_factor"], "autotune_s": r["t_tune"],
         "gemv_tiles": r["tiles"],
-        "roofline": {"bound": "hbm", "kernel": f"k_gemv<{'float' if head == 'mixed' else 'double'}> ({dom})",
+        "roofline": {"bound": "hbm", "kernel": (f"k_symgemv (packed FP32 tiles, {dom})"
+                                                if head == "mixed" and not args.no_sym and dom in ("local_solve", "iface_apply")
+                                                else f"k_gemv<{'float' if head == 'mixed' else 'double'}> ({dom})"),
                      "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs" + ("" if peak_kind == "measured" else " (no MEASURED_PEAKS.json)")},
