@@ -32,7 +32,7 @@ struct MatDesc {
 // M_s[i][j] = J_i J_j M_s[j][i] and the lower triangle determines M_s.  Each
 // group (interior I, interface Gamma, corner c) is padded to whole
 // kSymT x kSymT tiles; the tiles of the lower triangle (tile row a >= tile
-// column b) are stored one after the other in row order (a(a+1)/2 + b),
+// column b) are stored one after the other in the order of sym_tile_index,
 // row-major inside a tile, zeros in the padding; diagonal tiles are stored
 // whole.
 constexpr int kSymT = 64;
@@ -48,6 +48,21 @@ struct SymDesc {
 };
 
 DD_HD inline int sym_group(const int32_t* t0, int a) { return a < t0[1] ? 0 : (a < t0[2] ? 1 : 2); }
+
+// Storage position of lower tile (a, b) inside its subdomain, t1 = first tile of
+// Gamma, nt = tiles per side: first the lower triangle of the [Gamma|c] block
+// (row order; everything the interface rows and the coupled operator read is
+// one contiguous run), then the [Gamma|c] x I rectangle (row order), then the
+// lower triangle of the I block.
+DD_HD inline int64_t sym_tile_index(int a, int b, int t1, int nt) {
+    const int64_t m = nt - t1;
+    if (b >= t1) {
+        const int64_t x = a - t1;
+        return x * (x + 1) / 2 + (b - t1);
+    }
+    if (a >= t1) return m * (m + 1) / 2 + (int64_t)(a - t1) * t1 + b;
+    return m * (m + 1) / 2 + m * t1 + (int64_t)a * (a + 1) / 2 + b;
+}
 
 // Row and column groups (bit 0 I, bit 1 Gamma, bit 2 c) of the GEMV modes that
 // use the packed storage; false for the others.
@@ -347,6 +362,7 @@ struct dd_handle {
     std::vector<int32_t> sym_rng[GEMV_NMODES];
     int32_t sym_cl[GEMV_NMODES] = {4, 1, 1, 1, 1, 2, 2};   // CTAs per subdomain of each packed mode
     int32_t sym_st[GEMV_NMODES] = {4, 4, 4, 4, 4, 4, 4};   // TMA ring depth of each packed mode
+    int32_t sym_nl[GEMV_NMODES] = {};                      // longest tile list of one CTA (shared memory)
     int32_t sym_max_tiles = 0;                     // largest tile count of one subdomain
     bool sym_ok = false;                           // the packed GEMV's shared memory fits one CTA
     size_t task_cap[GEMV_NMODES] = {};             // device capacity: tasks at the smallest row count

@@ -17,12 +17,14 @@
 // cp.async.bulk (one 16 KB copy per tile, completion on an mbarrier) issued by
 // one thread, and accumulates its partial y over the subdomain's whole padded
 // index range in shared memory:
-//  * thread (rg, j) = (tid / 64, tid % 64) reads rows 16 rg .. 16 rg + 15 of
-//    column j of the tile (consecutive threads, consecutive words: no bank
+//  * 128 threads; thread (rg, cq) = (tid / 16, tid % 16) reads rows
+//    8 rg .. 8 rg + 7, columns 4 cq .. 4 cq + 3 of the tile with 16-byte
+//    loads (a half-warp reads 256 contiguous bytes of one row: no bank
 //    conflicts);
 //  * direct role: per-thread row partials stay in registers across the tile
-//    row and are reduced (shuffles, then two warps) when the tile row ends;
-//  * transposed role: the 16-row column partials of the four row groups are
+//    row and are reduced over the half-warp (fixed shuffle tree) when the
+//    tile row ends;
+//  * transposed role: the 8-row column partials of the eight row groups are
 //    added in fixed order once per tile.
 // The cluster then sums the cl partial vectors through distributed shared
 // memory in rank order.  All sums have a fixed order: results are
@@ -41,7 +43,7 @@ namespace cg = cooperative_groups;
 
 namespace {
 
-constexpr int kT = 256;
+constexpr int kT = 128;             // threads per CTA: 8 row groups x 16 column quads of a tile
 constexpr uint32_t kTileBytes = kSymTile * sizeof(float);
 constexpr unsigned kWaitLimit = 1u << 20;   // polls of one mbarrier wait before it gives up (well under a second)
 
@@ -117,19 +119,17 @@ struct Groups {
     }
 };
 
-__device__ __forceinline__ float wsumf(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+// Shared-memory layout of k_symgemv (floats unless noted), span = the padded
+// index range the mode touches (from its first group on), st = ring depth,
+// nl = longest tile list of one CTA:
+//   ring [st][kSymTile] | x [span] | y [span] | red [2][8][64] | bars (u64) [kSymStages] | tile list (u32) [nl]
+__host__ __device__ inline size_t sym_smem(int span, int st, int nl) {
+    size_t f = (size_t)st * kSymTile + 2 * (size_t)span + 2 * 8 * 64;
+    return f * sizeof(float) + kSymStages * sizeof(uint64_t) + (size_t)nl * sizeof(uint32_t);
 }
 
-// Shared-memory layout of k_symgemv (floats unless noted), span = the padded
-// index range the mode touches (from its first group on), st = ring depth:
-//   ring [st][kSymTile] | x [span] | y [span] | red [2][4][64] | rowred [8][16] | bars (u64) [kSymStages]
-__host__ __device__ inline size_t sym_smem(int span, int st) {
-    size_t f = (size_t)st * kSymTile + 2 * (size_t)span + 2 * 4 * 64 + 8 * 16;
-    return f * sizeof(float) + kSymStages * sizeof(uint64_t);
-}
+// tile list entry: a << 16 | b << 3 | flags (a, b < 8192)
+__device__ __forceinline__ uint32_t tile_entry(int a, int b, int f) { return ((uint32_t)a << 16) | ((uint32_t)b << 3) | f; }
 
 __host__ __device__ inline int lowest_group(int mask) { return (mask & 1) ? 0 : ((mask & 2) ? 1 : 2); }
 
@@ -137,17 +137,18 @@ __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ desc
                                                 const float* __restrict__ Msym, int span_max, int cl, int st,
                                                 int rmask, int cmask, XSrc xs, GemvOut go,
                                                 const int32_t* __restrict__ skip, int32_t* __restrict__ err) {
+    // (ranges/list capacity: the host sizes the list region for the longest range of this mode)
     if (skip && *skip) return;   // the same word for every CTA of the grid
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float* ring = reinterpret_cast<float*>(smem_raw);
     float* xsh = ring + st * kSymTile;   // index p - p_lo
     float* ysh = xsh + span_max;
-    float* red = ysh + span_max;        // [2][4][64]
-    float* rowred = red + 2 * 4 * 64;   // [8][16]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(rowred + 8 * 16);
+    float* red = ysh + span_max;        // [2][8][64] transposed-role partials, double-buffered
+    uint64_t* bars = reinterpret_cast<uint64_t*>(red + 2 * 8 * 64);
+    uint32_t* tl = reinterpret_cast<uint32_t*>(bars + kSymStages);
 
     cg::cluster_group cluster = cg::this_cluster();
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     const int sub = blockIdx.x / cl;
     const SymDesc sd = descs[sub];
     const Groups G{sd.t0[1], sd.t0[2], sd.t0[3], sd.n[0], sd.n[1], sd.n[2]};
@@ -157,14 +158,21 @@ __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ desc
     const int p_lo = G.first(lowest_group(rmask | cmask)) * kSymT;
     const int r_lo = G.first(lowest_group(rmask)) * kSymT;
 
-    // producer (thread 0): barriers, then the first st tiles, in flight while
-    // the CTA stages x
-    int pa = a0, pb = 0, pf = 0, issued = 0;
+    // thread 0: barriers, the first st tiles (in flight while the CTA stages x),
+    // then the CTA's whole tile list
+    __shared__ int n_tiles;
+    int issued = 0;
     if (tid == 0) {
         for (int s = 0; s < st; ++s) mbar_init(&bars[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        int pa = a0, pb = 0, pf = 0;
         for (int s = 0; s < st && G.next(rmask, cmask, a1, pa, pb, pf); ++s, ++pb, ++issued)
-            load_tile(ring + s * kSymTile, tiles + ((int64_t)pa * (pa + 1) / 2 + pb) * kSymTile, &bars[s]);
+            load_tile(ring + s * kSymTile, tiles + sym_tile_index(pa, pb, G.t1, G.nt) * kSymTile, &bars[s]);
+        int n = 0;
+        pa = a0;
+        pb = 0;
+        while (G.next(rmask, cmask, a1, pa, pb, pf)) tl[n++] = tile_entry(pa, pb++, pf);
+        n_tiles = n;
     }
     // x over the column groups (padded index space from p_lo), y = 0
     const float beta = (xs.kind == X_PCG || xs.kind == X_PCG_CV) ? (float)xs.sc->beta : 0.0f;
@@ -181,68 +189,78 @@ __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ desc
     }
     __syncthreads();
 
-    const int rg = tid >> 6, j = tid & 63;
-    float acc[16], xa[16];
-    int ca = a0, cb = 0, cf = 0, cur = -1, k = 0;
+    // thread (rg, cq): rows 8 rg .. 8 rg + 7 and columns 4 cq .. 4 cq + 3 of a tile
+    // (16-byte shared loads; a half-warp covers one row group)
+    const int rg = tid >> 4, cq = tid & 15;
+    const int nt_cta = n_tiles;
+    float acc[8], xa[8];
+    int cur = -1, k = 0, slot = 0;
+    uint32_t phase = 0;
     bool bad = false;
-    // per-thread row partials of tile row `row` -> y (both warps of each row group)
+    // direct-role row partials of tile row `row` -> y: sum over the 16 column
+    // quads (one half-warp, fixed shuffle tree), lane cq == r adds row r.  No
+    // barrier: only this half-warp writes these rows before the next tile's barrier.
     auto flush = [&](int row) {
 #pragma unroll
-        for (int r = 0; r < 16; ++r) {
-            const float v = wsumf(acc[r]);
-            if (lane == 0) rowred[warp * 16 + r] = v;
+        for (int r = 0; r < 8; ++r) {
+            float v = acc[r];
+#pragma unroll
+            for (int o = 1; o < 16; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (cq == r) ysh[row * kSymT + rg * 8 + r - p_lo] += v;
         }
-        __syncthreads();
-        if (tid < 64) {
-            const int w0 = (tid >> 4) * 2;
-            ysh[row * kSymT + tid - p_lo] += rowred[w0 * 16 + (tid & 15)] + rowred[(w0 + 1) * 16 + (tid & 15)];
-        }
-        __syncthreads();
     };
-    while (G.next(rmask, cmask, a1, ca, cb, cf)) {
+    for (; k < nt_cta; ++k) {
+        const uint32_t e = tl[k];
+        const int ca = (int)(e >> 16), cb = (int)((e >> 3) & 0x1fff), cf = (int)(e & 7);
         if (ca != cur) {
             if (cur >= 0) flush(cur);
             cur = ca;
 #pragma unroll
-            for (int r = 0; r < 16; ++r) {
+            for (int r = 0; r < 8; ++r) {
                 acc[r] = 0.0f;
-                xa[r] = xsh[ca * kSymT + rg * 16 + r - p_lo];
+                xa[r] = xsh[ca * kSymT + rg * 8 + r - p_lo];
             }
         }
-        const int s = k % st;
-        const bool ok = mbar_wait(&bars[s], (uint32_t)(k / st) & 1u);
-        const float* T = ring + s * kSymTile + rg * 16 * kSymT + j;
-        const float xb = (cf & 1) ? xsh[cb * kSymT + j - p_lo] : 0.0f;
-        float c0 = 0.0f, c1 = 0.0f;
+        const bool ok = mbar_wait(&bars[slot], phase);
+        const float4* T = reinterpret_cast<const float4*>(ring + slot * kSymTile) + rg * 8 * (kSymT / 4) + cq;
+        const float4 xb = (cf & 1) ? *reinterpret_cast<const float4*>(xsh + cb * kSymT + 4 * cq - p_lo)
+                                   : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        float4 col = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if (ok) {
 #pragma unroll
-            for (int r = 0; r < 16; r += 2) {
-                const float m0 = T[r * kSymT], m1 = T[(r + 1) * kSymT];
-                acc[r] = fmaf(m0, xb, acc[r]);
-                acc[r + 1] = fmaf(m1, xb, acc[r + 1]);
-                c0 = fmaf(m0, xa[r], c0);
-                c1 = fmaf(m1, xa[r + 1], c1);
+            for (int r = 0; r < 8; ++r) {
+                const float4 m = T[r * (kSymT / 4)];
+                acc[r] = fmaf(m.x, xb.x, fmaf(m.y, xb.y, fmaf(m.z, xb.z, fmaf(m.w, xb.w, acc[r]))));
+                col.x = fmaf(m.x, xa[r], col.x);
+                col.y = fmaf(m.y, xa[r], col.y);
+                col.z = fmaf(m.z, xa[r], col.z);
+                col.w = fmaf(m.w, xa[r], col.w);
             }
         }
-        float* rd = red + (k & 1) * 4 * 64;
-        rd[rg * 64 + j] = c0 + c1;
-        bad = __syncthreads_or(!ok) != 0;   // also: every thread is done with ring slot s
+        float* rd = red + (k & 1) * 8 * 64;
+        *reinterpret_cast<float4*>(rd + rg * 64 + 4 * cq) = col;
+        bad = __syncthreads_or(!ok) != 0;   // also: every thread is done with ring slot `slot`
         if (bad) break;
-        if (tid == 0 && G.next(rmask, cmask, a1, pa, pb, pf)) {
-            load_tile(ring + s * kSymTile, tiles + ((int64_t)pa * (pa + 1) / 2 + pb) * kSymTile, &bars[s]);
-            ++pb;
+        if (tid == 0 && k + st < nt_cta) {
+            const uint32_t en = tl[k + st];
+            const int na = (int)(en >> 16), nb = (int)((en >> 3) & 0x1fff);
+            load_tile(ring + slot * kSymTile, tiles + sym_tile_index(na, nb, G.t1, G.nt) * kSymTile, &bars[slot]);
             ++issued;
         }
-        if ((cf & 2) && tid < 64) {
-            const float sum = ((rd[tid] + rd[64 + tid]) + rd[128 + tid]) + rd[192 + tid];
+        if ((cf & 2) && tid < 64) {   // transposed role: column tid of the tile, 8 row groups in order
+            float sum = rd[tid];
+#pragma unroll
+            for (int q = 1; q < 8; ++q) sum += rd[q * 64 + tid];
             ysh[cb * kSymT + tid - p_lo] += (cf & 4) ? -sum : sum;
         }
-        ++k;
-        ++cb;
+        if (++slot == st) {
+            slot = 0;
+            phase ^= 1u;
+        }
     }
     if (!bad && cur >= 0) flush(cur);
     if (bad && tid == 0) {
-        for (int q = k; q < issued; ++q) mbar_wait(&bars[q % st], (uint32_t)(q / st) & 1u);
+        for (int q = k; q < issued; ++q) mbar_wait(&bars[q % st], (uint32_t)(q / st) & 1u);   // k: the tile that failed
         atomicExch(err, 1);
     }
 
@@ -285,7 +303,7 @@ __global__ void k_sym_pack(const SymDesc* __restrict__ descs, const MatDesc* __r
     const MatDesc md = mats[blockIdx.y];
     const int gstart[3] = {0, sd.n[0], sd.n[0] + sd.n[1]};
     const int ga = sym_group(sd.t0, a), gb = sym_group(sd.t0, b);
-    float* out = Msym + sd.toff + kt * kSymTile;
+    float* out = Msym + sd.toff + sym_tile_index(a, b, sd.t0[1], nt) * kSymTile;
     for (int e = threadIdx.x; e < kSymTile; e += blockDim.x) {
         const int qi = (a - sd.t0[ga]) * kSymT + e / kSymT;
         const int qj = (b - sd.t0[gb]) * kSymT + e % kSymT;
@@ -298,7 +316,7 @@ __global__ void k_sym_pack(const SymDesc* __restrict__ descs, const MatDesc* __r
 
 }  // namespace
 
-size_t sym_smem_bytes(const dd_handle* h) { return sym_smem(h->sym_np_max, kSymStages); }
+size_t sym_smem_bytes(const dd_handle* h) { return sym_smem(h->sym_np_max, kSymStages, h->sym_max_tiles); }
 
 // Padded index range a mode touches in the largest subdomain (from its first group on).
 int sym_span(const dd_handle* h, int mode) {
@@ -357,6 +375,7 @@ void sym_ranges(dd_handle* h, int mode, int cl) {
     int rmask, cmask;
     h->sym_rng[mode].clear();
     h->sym_cl[mode] = cl;
+    h->sym_nl[mode] = 0;
     if (!sym_masks(mode, &rmask, &cmask)) return;
     for (const SymDesc& sd : h->sym) {
         const int nt = sd.t0[3];
@@ -380,6 +399,9 @@ void sym_ranges(dd_handle* h, int mode, int cl) {
             }
             h->sym_rng[mode].push_back(begin);
             h->sym_rng[mode].push_back(a);
+            int64_t n = 0;
+            for (int q = begin; q < a; ++q) n += per_row[q];
+            h->sym_nl[mode] = std::max<int32_t>(h->sym_nl[mode], (int32_t)n);
         }
     }
 }
@@ -399,9 +421,9 @@ int launch_symgemv(const dd_handle* h, int mode, XSrc xs, GemvOut go, const int3
     xs.sc = h->d.sc;
     const int span = sym_span(h, mode);
     const int st = h->sym_st[mode];
-    const size_t smem = sym_smem(span, st);
+    const size_t smem = sym_smem(span, st, h->sym_nl[mode]);
     cudaError_t e = cudaFuncSetAttribute(k_symgemv, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sym_smem(h->sym_np_max, kSymStages));
+                                         (int)sym_smem_bytes(h));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_symgemv, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
