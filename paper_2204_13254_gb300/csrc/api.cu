@@ -499,10 +499,9 @@ int gmres_solve(dd_handle* h, int prec, double tol, bool warm, int* it_out, doub
             Prof P(h, ST_SCHUR, st, 1);
             CK(h, launch_gemv(h, GEMV_COUPLED, prec, xs_z, go, false, st, skip), "coupled operator");
         }
-        Prof P(h, ST_VEC, st, 4);
+        Prof P(h, ST_VEC, st, 3);
         CK(h, launch_gm_pass(h, 0, V.wf, 0ull, st), "gmres pass 0");
-        CK(h, launch_gm_pass(h, 1, V.wf, 0ull, st), "gmres pass 1");
-        CK(h, launch_gm_pass(h, 2, V.wf, cond_inner, st), "gmres pass 2");
+        CK(h, launch_gm_pass(h, 1, V.wf, cond_inner, st), "gmres pass 1");
         CK(h, launch_gm_normalize(h, zuf, st), "gmres normalize");
         return DD_OK;
     };

@@ -189,7 +189,8 @@ struct GmresScalars {
     double beta;        // ||r_0|| of the cycle
     double hnext;       // norm of the vector to normalise next (beta, then H[j+1][j])
     double resid;       // |g_{j+1}| after the last step
-    int32_t max_it, m, cycles, pad;
+    int32_t max_it, m, cycles;
+    int32_t nh2;        // terms of the second projection k_gm_normalize applies (0 at a cycle start)
     uint32_t counter[4];
     double g[kMaxRestart + 1];
     double cs[kMaxRestart], sn[kMaxRestart];

@@ -15,15 +15,16 @@
 // In DD_MIXED the Krylov vectors (basis, work vector) are FP32, the
 // least-squares problem and the iterate FP64.
 //
-// One Arnoldi step = GEMV + three vector kernels + one normalisation:
+// One Arnoldi step = GEMV + two Gram-Schmidt kernels + one normalisation
+// (classical Gram-Schmidt applied twice):
 //   pass 0: t = M D^-1 v_j (combine),        h1 = V^T t
-//   pass 1: t -= V h1,                        h2 = V^T t   (classical Gram-Schmidt, twice)
-//   pass 2: t -= V h2, ||t|| -> H[j+1][j]; the last block applies the stored
-//           Givens rotations to column j, makes the new one, updates the
+//   pass 1: t1 = t - V h1, h2 = V^T t1, ||t1||^2; H[j+1][j] = ||t1 - V h2|| =
+//           sqrt(||t1||^2 - ||h2||^2); the last block applies the stored Givens
+//           rotations to column j, makes the new one, updates the
 //           least-squares residual |g_{j+1}| and decides the end of the cycle
 //           (converged, m steps, budget spent, breakdown); at the end it
 //           back-substitutes y = R^-1 g.
-//   normalise: v_{j+1} = t / H[j+1][j], z = D^-1 v_{j+1}.
+//   normalise: v_{j+1} = (t1 - V h2) / H[j+1][j], z = D^-1 v_{j+1}.
 // Multi-dot products are block partials reduced in fixed block order by the
 // last block to finish (atomic ticket, no spinning): results do not depend on
 // scheduling.
@@ -194,6 +195,7 @@ __global__ void __launch_bounds__(kT) k_gm_start(int64_t nl, int64_t nc, const i
         gs->g[0] = beta;
         gs->j = 0;
         gs->k = 0;
+        gs->nh2 = 0;
         gs->cycles += 1;
         sc->cycles += 1;
         int end = 0;
@@ -213,17 +215,25 @@ __global__ void __launch_bounds__(kT) k_gm_start(int64_t nl, int64_t nc, const i
     }
 }
 
-// v_j = t / hnext, z = D^-1 v_j: FP64 z for the FP64 GEMV, FP32 z for the FP32 one
+// v_j = (t - sum_k h2_k v_k) / hnext (the second Gram-Schmidt projection of the
+// previous column, nh2 terms, none at a cycle start), z = D^-1 v_j: FP64 z for
+// the FP64 GEMV, FP32 z for the FP32 one
 template <typename VT>
 __global__ void k_gm_normalize(int64_t nl, int64_t nc, VT* __restrict__ V, int64_t ldv, const VT* __restrict__ tu,
                                const double* __restrict__ dl, const double* __restrict__ dc, double* __restrict__ zu,
                                float* __restrict__ zuf, const GmresScalars* gs) {
     if (gs->skip) return;
+    __shared__ VT coef[kM1];
+    const int nh2 = gs->nh2;
+    if (threadIdx.x < nh2) coef[threadIdx.x] = (VT)gs->h2[threadIdx.x];
+    __syncthreads();
     const int64_t nu = nl + nc;
     VT* vj = V + (int64_t)gs->j * ldv;
     const VT inv = (VT)(1.0 / gs->hnext);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nu; i += (int64_t)gridDim.x * blockDim.x) {
-        const VT v = tu[i] * inv;
+        VT t = tu[i];
+        for (int k = 0; k < nh2; ++k) t -= coef[k] * V[(int64_t)k * ldv + i];
+        const VT v = t * inv;
         const VT z = (VT)dinv_at(i, nl, dl, dc) * v;
         vj[i] = v;
         if (zu) zu[i] = (double)z;
@@ -232,6 +242,12 @@ __global__ void k_gm_normalize(int64_t nl, int64_t nc, VT* __restrict__ V, int64
 }
 
 // Gram-Schmidt passes of Arnoldi column j (see the file comment).
+//   PHASE 0: t = combine(w), h1 = V^T t.
+//   PHASE 1: t1 = t - V h1, h2 = V^T t1 and ||t1||^2; the last block takes
+//            H[:, j] = h1 + h2 and H[j+1][j] = ||t1 - V h2|| = sqrt(||t1||^2 -
+//            ||h2||^2) (V orthonormal; h2 is the small reorthogonalisation
+//            correction, applied to the vector by k_gm_normalize), then the
+//            Givens rotations and the end-of-cycle logic.
 template <int PHASE, typename VT>
 __global__ void __launch_bounds__(kT) k_gm_pass(int64_t nl, int64_t nc, const int64_t* __restrict__ ms,
                                                 const int64_t* __restrict__ cp, const int64_t* __restrict__ cs,
@@ -242,13 +258,15 @@ __global__ void __launch_bounds__(kT) k_gm_pass(int64_t nl, int64_t nc, const in
                                                 unsigned long long cond) {
     if (gs->skip) return;
     __shared__ VT coef[kM1];
-    __shared__ double red[kM1][kWarps];
+    __shared__ double red[kM1 + 1][kWarps];
+    __shared__ double tot[kM1 + 1];
     const int64_t nu = nl + nc;
     const int j = gs->j;
     const int nv = j + 1;
+    const int nsum = PHASE == 0 ? nv : nv + 1;   // PHASE 1 adds ||t1||^2 as sum nv
     const int nb = gridDim.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (PHASE > 0 && threadIdx.x < nv) coef[threadIdx.x] = (VT)(PHASE == 1 ? gs->h1[threadIdx.x] : gs->h2[threadIdx.x]);
+    if (PHASE == 1 && threadIdx.x < nv) coef[threadIdx.x] = (VT)gs->h1[threadIdx.x];
     __syncthreads();
     VT t[kGmElems];
 #pragma unroll
@@ -267,53 +285,45 @@ __global__ void __launch_bounds__(kT) k_gm_pass(int64_t nl, int64_t nc, const in
             t[e] = v;
         }
     }
-    if (PHASE < 2) {
-        // partial dots with v_0 .. v_j
-        for (int k = 0; k < nv; ++k) {
-            VT p = (VT)0;
+    // partial dots with v_0 .. v_j (and ||t||^2 in PHASE 1)
+    for (int k = 0; k < nsum; ++k) {
+        VT p = (VT)0;
 #pragma unroll
-            for (int e = 0; e < kGmElems; ++e) {
-                const int64_t i = (int64_t)blockIdx.x * kGmChunk + e * kT + threadIdx.x;
-                if (i < nu) p += t[e] * V[(int64_t)k * ldv + i];
-            }
-            p = wsum(p);
-            if (lane == 0) red[k][warp] = (double)p;
+        for (int e = 0; e < kGmElems; ++e) {
+            const int64_t i = (int64_t)blockIdx.x * kGmChunk + e * kT + threadIdx.x;
+            if (i < nu) p += t[e] * (k < nv ? V[(int64_t)k * ldv + i] : t[e]);
         }
-        __syncthreads();
-        if (threadIdx.x < nv) {
-            double s = 0.0;
-            for (int q = 0; q < kWarps; ++q) s += red[threadIdx.x][q];
-            partials[(int64_t)threadIdx.x * nb + blockIdx.x] = s;
-            __threadfence();
-        }
-        if (!last_block(&gs->counter[1 + PHASE])) return;
-        for (int k = warp; k < nv; k += kWarps) {
-            const double s = reduce_partials(partials, k, nb);
-            if (lane == 0) {
-                if (PHASE == 0) {
-                    gs->h1[k] = s;
-                } else {
-                    gs->h2[k] = s;
-                    gs->H[(int64_t)j * kM1 + k] = gs->h1[k] + s;
-                }
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) gs->counter[1 + PHASE] = 0u;
+        p = wsum(p);
+        if (lane == 0) red[k][warp] = (double)p;
+    }
+    __syncthreads();
+    if (threadIdx.x < nsum) {
+        double s = 0.0;
+        for (int q = 0; q < kWarps; ++q) s += red[threadIdx.x][q];
+        partials[(int64_t)threadIdx.x * nb + blockIdx.x] = s;
+        __threadfence();
+    }
+    if (!last_block(&gs->counter[1 + PHASE])) return;
+    for (int k = warp; k < nsum; k += kWarps) {
+        const double s = reduce_partials(partials, k, nb);
+        if (lane == 0) tot[k] = s;
+    }
+    __syncthreads();
+    if (PHASE == 0) {
+        if (threadIdx.x < nv) gs->h1[threadIdx.x] = tot[threadIdx.x];
+        if (threadIdx.x == 0) gs->counter[1] = 0u;
         return;
     }
-    // PHASE 2: ||t||, Givens, end of cycle
-    VT pt = (VT)0;
-#pragma unroll
-    for (int e = 0; e < kGmElems; ++e) pt += t[e] * t[e];
-    const double p = block_sum1((double)pt);
-    if (threadIdx.x == 0) partials[blockIdx.x] = p;
-    if (!last_block(&gs->counter[3])) return;
-    const double tot = __shfl_sync(0xffffffffu, reduce_partials(partials, 0, nb), 0);
     if (threadIdx.x != 0) return;
-    gs->counter[3] = 0u;
+    gs->counter[2] = 0u;
     double* col = gs->H + (int64_t)j * kM1;
-    const double hsub = sqrt(tot);
+    double h2sq = 0.0;
+    for (int k = 0; k < nv; ++k) {
+        gs->h2[k] = tot[k];
+        col[k] = gs->h1[k] + tot[k];
+        h2sq += tot[k] * tot[k];
+    }
+    const double hsub = sqrt(fmax(tot[nv] - h2sq, 0.0));
     col[j + 1] = hsub;
     for (int i = 0; i < j; ++i) {
         const double a = col[i], b = col[i + 1];
@@ -357,6 +367,7 @@ __global__ void __launch_bounds__(kT) k_gm_pass(int64_t nl, int64_t nc, const in
         gs->cycle_end = 1;
         gs->skip = 1;
     } else {
+        gs->nh2 = nv;
         gs->j = j + 1;
         gs->hnext = hsub;
     }
@@ -473,12 +484,10 @@ int launch_gm_pass(const dd_handle* h, int phase, const float* wf, unsigned long
     const cudaStream_t st = S(stream);
     if (wf) {
         if (phase == 0) run_pass<0, float>(h, wf, 0ull, st);
-        else if (phase == 1) run_pass<1, float>(h, wf, 0ull, st);
-        else run_pass<2, float>(h, wf, cond_inner, st);
+        else run_pass<1, float>(h, wf, cond_inner, st);
     } else {
         if (phase == 0) run_pass<0, double>(h, nullptr, 0ull, st);
-        else if (phase == 1) run_pass<1, double>(h, nullptr, 0ull, st);
-        else run_pass<2, double>(h, nullptr, cond_inner, st);
+        else run_pass<1, double>(h, nullptr, cond_inner, st);
     }
     return (int)cudaGetLastError();
 }
