@@ -390,11 +390,13 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
  * and GEMV kind k (0 local, 1 corner rows, 2 corner coupling, 3 recovery,
  * 4 coarse, 5 interface rows, 6 coupled operator) of the dense kernel; host
  * int32[14] each.  Kinds 0, 5 and 6 run in DD_MIXED on the packed symmetric
- * tiles when sym_fp32 = 1: cl[k] CTAs (one cluster) per subdomain and a TMA
- * ring of st[k] tiles (host int32[7] each, 0 for the other kinds; either
- * pointer may be NULL). */
+ * tiles when sym_fp32 = 1: cl[k] CTAs (one cluster) per subdomain, a TMA ring
+ * of st[k] tiles, and the tiles of subdomains 0 .. keep[k]-1 copied with an
+ * L2 evict_last policy (the rest evict_first) so that they stay in L2 across
+ * the launches of a Krylov solve (host int32[7] each, 0 for the other kinds;
+ * any pointer may be NULL). */
 int dd_get_tiles(const dd_handle* h, int32_t* lpr, int32_t* rows);
-int dd_get_sym_config(const dd_handle* h, int32_t* cl, int32_t* st);
+int dd_get_sym_config(const dd_handle* h, int32_t* cl, int32_t* st, int32_t* keep);
 
 void dd_destroy(dd_handle* h);
 const char* dd_last_error(const dd_handle* h);

@@ -1549,8 +1549,11 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
     for (char& c : key)
         if (c == ' ' || c == '\t') c = '_';
     std::map<std::pair<int, int>, TileCfg> found;
-    std::map<int, std::pair<int, int>> found_cl;   // packed symmetric modes: (CTAs per subdomain, ring depth),
-                                                   // cache lines "key 2 mode cl st"
+    struct SymCfg {
+        int cl, st, keep;
+    };
+    std::map<int, SymCfg> found_cl;   // packed symmetric modes: CTAs per subdomain, ring depth, subdomains kept
+                                      // in L2; cache lines "key 2 mode cl st keep"
     int n_sym = 0;
     for (int m = 0; m < GEMV_NMODES; ++m) {
         int rm, cm;
@@ -1566,9 +1569,10 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
             if (!(is >> k >> p >> m >> lpr >> rows) || k != key || m < 0 || m >= GEMV_NMODES) continue;
             if (p >= 0 && p < 2 && (lpr == 8 || lpr == 16 || lpr == 32) && rows >= kMinRowsPerTask)
                 found[{p, m}] = TileCfg{lpr, rows};
+            int keep = 0;
             if (p == 2 && sym_masks(m, &rm, &cm) && (lpr == 1 || lpr == 2 || lpr == 4 || lpr == 8) && rows >= 2 &&
-                rows <= kSymStages)
-                found_cl[m] = {lpr, rows};
+                rows <= kSymStages && (is >> keep) && keep >= 0 && keep <= h->n_sub)
+                found_cl[m] = SymCfg{lpr, rows, keep};
         }
     }
     const bool cached = found.size() == (size_t)(2 * GEMV_NMODES) && found_cl.size() == (size_t)n_sym;
@@ -1599,11 +1603,24 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
                     xs.v = h->d.b;
                     xs.vf = h->d.bf;
                     const GemvOut go{nullptr, nullptr, h->d.wf, nullptr, 1.0};
+                    // then, for the kinds a Krylov solve repeats, how many subdomains' tiles to keep in
+                    // L2 (evict_last) across launches: 0, 32, 64 or 96 MB worth
                     float best = 1e30f;
-                    std::pair<int, int> bcl{h->sym_cl[m], h->sym_st[m]};
-                    for (int cand = 0; cand < 12 && !rc; ++cand) {
-                        const int cl = 1 << (cand / 3), st = 2 + cand % 3;
+                    SymCfg bcl{h->sym_cl[m], h->sym_st[m], 0};
+                    const bool repeated = m != GEMV_LOCAL;
+                    const double per_sub = h->mode_bytes_sym[m] / std::max(1, h->n_sub);
+                    for (int cand = 0; cand < 12 + (repeated ? 3 : 0) && !rc; ++cand) {
+                        int cl, st, keep = 0;
+                        if (cand < 12) {
+                            cl = 1 << (cand / 3);
+                            st = 2 + cand % 3;
+                        } else {
+                            cl = bcl.cl;
+                            st = bcl.st;
+                            keep = std::min(h->n_sub, (int)((cand - 11) * 32.0e6 / std::max(1.0, per_sub)));
+                        }
                         h->sym_st[m] = st;
+                        h->sym_keep[m] = keep;
                         sym_ranges(h, m, cl);
                         rc = upload(h->d.sym_rng[m], h->sym_rng[m], s);
                         for (int it = 0; it < 4 && !rc; ++it) {
@@ -1619,7 +1636,7 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
                         if (rc) break;
                         if (ms < best) {
                             best = ms;
-                            bcl = {cl, st};
+                            bcl = SymCfg{cl, st, keep};
                         }
                     }
                     found_cl[m] = bcl;
@@ -1678,7 +1695,8 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
                 f << key << "\t" << kv.first.first << "\t" << kv.first.second << "\t" << kv.second.lpr << "\t"
                   << kv.second.rows << "\n";
             for (const auto& kv : found_cl)
-                f << key << "\t2\t" << kv.first << "\t" << kv.second.first << "\t" << kv.second.second << "\n";
+                f << key << "\t2\t" << kv.first << "\t" << kv.second.cl << "\t" << kv.second.st << "\t"
+                  << kv.second.keep << "\n";
         }
     }
     cudaEventDestroy(e0);
@@ -1692,8 +1710,9 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
             if (urc) return urc == DD_ERR_CUDA ? h->fail(DD_ERR_CUDA, "upload tasks") : urc;
         }
     for (const auto& kv : found_cl) {
-        h->sym_st[kv.first] = kv.second.second;
-        sym_ranges(h, kv.first, kv.second.first);
+        h->sym_st[kv.first] = kv.second.st;
+        h->sym_keep[kv.first] = kv.second.keep;
+        sym_ranges(h, kv.first, kv.second.cl);
         CK(h, upload(h->d.sym_rng[kv.first], h->sym_rng[kv.first], s), "upload ranges");
     }
     CK(h, (int)cudaStreamSynchronize(s), "sync");
@@ -1714,13 +1733,14 @@ int dd_get_tiles(const dd_handle* h, int32_t* lpr, int32_t* rows) {
     return DD_OK;
 }
 
-int dd_get_sym_config(const dd_handle* h, int32_t* cl, int32_t* st) {
+int dd_get_sym_config(const dd_handle* h, int32_t* cl, int32_t* st, int32_t* keep) {
     if (!h) return DD_ERR_ARG;
     for (int m = 0; m < GEMV_NMODES; ++m) {
         int rm, cmk;
         const bool on = sym_masks(m, &rm, &cmk);
         if (cl) cl[m] = on ? h->sym_cl[m] : 0;
         if (st) st[m] = on ? h->sym_st[m] : 0;
+        if (keep) keep[m] = on ? h->sym_keep[m] : 0;
     }
     return DD_OK;
 }

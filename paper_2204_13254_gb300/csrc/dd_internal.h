@@ -364,6 +364,7 @@ struct dd_handle {
     int32_t sym_cl[GEMV_NMODES] = {4, 1, 1, 1, 1, 2, 2};   // CTAs per subdomain of each packed mode
     int32_t sym_st[GEMV_NMODES] = {4, 4, 4, 4, 4, 4, 4};   // TMA ring depth of each packed mode
     int32_t sym_nl[GEMV_NMODES] = {};                      // longest tile list of one CTA (shared memory)
+    int32_t sym_keep[GEMV_NMODES] = {};                    // subdomains whose tiles are kept in L2 (evict_last)
     int32_t sym_max_tiles = 0;                     // largest tile count of one subdomain
     bool sym_ok = false;                           // the packed GEMV's shared memory fits one CTA
     size_t task_cap[GEMV_NMODES] = {};             // device capacity: tasks at the smallest row count

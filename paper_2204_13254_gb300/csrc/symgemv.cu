@@ -55,13 +55,24 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
+// L2 policies for the tile copies: evict_last keeps a subset of the operator
+// resident in L2 across the launches of one Krylov solve, evict_first streams
+// the rest past it.
+__device__ __forceinline__ uint64_t l2_policy(bool keep) {
+    uint64_t pol;
+    if (keep) asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    else asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
 // One 16 KB tile global -> shared, completing on `bar` (which expects the bytes).
-__device__ __forceinline__ void load_tile(float* dst, const float* src, uint64_t* bar) {
+__device__ __forceinline__ void load_tile(float* dst, const float* src, uint64_t* bar, uint64_t pol) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(kTileBytes)
                  : "memory");
     asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
-        "l"(src), "r"(kTileBytes), "r"(smem_u32(bar))
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(kTileBytes), "r"(smem_u32(bar)), "l"(pol)
         : "memory");
 }
 
@@ -135,7 +146,7 @@ __host__ __device__ inline int lowest_group(int mask) { return (mask & 1) ? 0 : 
 
 __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ descs, const int32_t* __restrict__ ranges,
                                                 const float* __restrict__ Msym, int span_max, int cl, int st,
-                                                int rmask, int cmask, XSrc xs, GemvOut go,
+                                                int rmask, int cmask, int keep, XSrc xs, GemvOut go,
                                                 const int32_t* __restrict__ skip, int32_t* __restrict__ err) {
     // (ranges/list capacity: the host sizes the list region for the longest range of this mode)
     if (skip && *skip) return;   // the same word for every CTA of the grid
@@ -162,12 +173,13 @@ __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ desc
     // then the CTA's whole tile list
     __shared__ int n_tiles;
     int issued = 0;
+    const uint64_t pol = l2_policy(sub < keep);   // subdomains below `keep` stay in L2
     if (tid == 0) {
         for (int s = 0; s < st; ++s) mbar_init(&bars[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         int pa = a0, pb = 0, pf = 0;
         for (int s = 0; s < st && G.next(rmask, cmask, a1, pa, pb, pf); ++s, ++pb, ++issued)
-            load_tile(ring + s * kSymTile, tiles + sym_tile_index(pa, pb, G.t1, G.nt) * kSymTile, &bars[s]);
+            load_tile(ring + s * kSymTile, tiles + sym_tile_index(pa, pb, G.t1, G.nt) * kSymTile, &bars[s], pol);
         int n = 0;
         pa = a0;
         pb = 0;
@@ -244,7 +256,7 @@ __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ desc
         if (tid == 0 && k + st < nt_cta) {
             const uint32_t en = tl[k + st];
             const int na = (int)(en >> 16), nb = (int)((en >> 3) & 0x1fff);
-            load_tile(ring + slot * kSymTile, tiles + sym_tile_index(na, nb, G.t1, G.nt) * kSymTile, &bars[slot]);
+            load_tile(ring + slot * kSymTile, tiles + sym_tile_index(na, nb, G.t1, G.nt) * kSymTile, &bars[slot], pol);
             ++issued;
         }
         if ((cf & 2) && tid < 64) {   // transposed role: column tid of the tile, 8 row groups in order
@@ -442,6 +454,6 @@ int launch_symgemv(const dd_handle* h, int mode, XSrc xs, GemvOut go, const int3
     cfg.attrs = at;
     cfg.numAttrs = 1;
     return (int)cudaLaunchKernelEx(&cfg, k_symgemv, (const SymDesc*)h->d.symd, (const int32_t*)h->d.sym_rng[mode],
-                                   (const float*)h->d.Msym, span, cl, st, rmask, cmask, xs, go, skip,
+                                   (const float*)h->d.Msym, span, cl, st, rmask, cmask, h->sym_keep[mode], xs, go, skip,
                                    &h->d.sc->wait_err);
 }

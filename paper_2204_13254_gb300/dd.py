@@ -95,7 +95,7 @@ def load_library(path: str = LIB_PATH):
         "dd_probe_seed": (C.c_int, [vp, vp, C.c_double, vp, vp]),
         "dd_autotune": (C.c_int, [vp, C.c_char_p, C.POINTER(C.c_double), vp]),
         "dd_get_tiles": (C.c_int, [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
-        "dd_get_sym_config": (C.c_int, [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+        "dd_get_sym_config": (C.c_int, [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
         "dd_set_beam": (C.c_int, [vp, C.POINTER(dd_beam)]),
         "dd_pic_step": (C.c_int, [vp, C.POINTER(dd_stats), vp]),
         "dd_pic_state": (C.c_int, [vp, vp, vp, vp, vp, C.POINTER(C.c_int64), vp]),
@@ -296,12 +296,13 @@ def dd_get_tiles(h):
 
 
 def dd_get_sym_config(h):
-    """Packed symmetric GEMV kinds: {kind: (CTAs per subdomain, TMA ring depth)}."""
+    """Packed symmetric GEMV kinds: {kind: (CTAs per subdomain, TMA ring depth, subdomains kept in L2)}."""
     nk = len(GEMV_KINDS)
     cl = (C.c_int32 * nk)()
     st = (C.c_int32 * nk)()
-    _check(h, lib().dd_get_sym_config(h, cl, st))
-    return {GEMV_KINDS[k]: (cl[k], st[k]) for k in range(nk) if cl[k]}
+    keep = (C.c_int32 * nk)()
+    _check(h, lib().dd_get_sym_config(h, cl, st, keep))
+    return {GEMV_KINDS[k]: (cl[k], st[k], keep[k]) for k in range(nk) if cl[k]}
 
 
 def dd_profile(h, enable=-1, read=True, stream=None):
