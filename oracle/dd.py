@@ -41,6 +41,7 @@ from __future__ import annotations
 
 import numpy as np
 import scipy.linalg as sla
+import scipy.sparse as sp
 
 from .gmres import gmres
 
@@ -324,6 +325,206 @@ def run(space, maps, dt, src, d2g, n_steps, tol=1e-14, P=None, keep=False, solve
     out = dict(e_n=e_n, e_nm1=e_nm1, iters=np.array(its), solver=dd)
     if P is not None:
         out["probes"] = np.array(probes)
+    if keep:
+        out["fields"] = np.array(fields)
+    return out
+
+
+def interface_mass(space, maps, part):
+    """Tangential Whitney mass M_T of the interface faces on the multiplier edges (sparse
+    n_lambda x n_lambda).  An entry couples two multiplier edges of one interface face;
+    both edges then join the same pair of subdomains, so M_T is block diagonal by pair."""
+    from .fem import face_tangential_mass, interface_faces
+    faces, _ = interface_faces(space.tets, part)
+    n = int(space.tets.max()) + 1
+    ekey = space.edges[:, 0] * n + space.edges[:, 1]
+    def dof(a, b):
+        return space.edge_to_dof[np.searchsorted(ekey, a * n + b)]
+    fd = np.stack([dof(faces[:, 0], faces[:, 1]), dof(faces[:, 1], faces[:, 2]),
+                   dof(faces[:, 0], faces[:, 2])], axis=1)                      # [F,3], -1 on the PEC wall
+    midx = -np.ones(space.n, dtype=np.int64)
+    midx[maps.mult_dof] = np.arange(maps.n_lambda)
+    fm = np.where(fd >= 0, midx[np.maximum(fd, 0)], -1)
+    Mf = face_tangential_mass(space.xyz[faces])
+    r = np.broadcast_to(fm[:, :, None], Mf.shape)
+    c = np.broadcast_to(fm[:, None, :], Mf.shape)
+    ok = (r >= 0) & (c >= 0)
+    M = sp.csr_matrix((Mf[ok], (r[ok], c[ok])), shape=(maps.n_lambda, maps.n_lambda))
+    M.sum_duplicates()
+    return M
+
+
+class DP2Solver:
+    """CPU MFETI-DP2 solve of A x = b (Sec. III-B), re-derived for the edge-only step system.
+
+    Readings (the paper's DP2 is written for its mixed E/B system with face unknowns):
+    * The Robin transmission condition Lambda = n x H - eta^-1 n x n x E becomes, in
+      the Newmark step matrix A = T + dt^2/4 S, the interface term R^(s) = alpha M_T^(s)
+      added to every local matrix on its interface (m = 2) edges, M_T the tangential
+      Whitney mass of the interface faces; alpha = dt / (2 eta) with eta = 1 (the
+      admittance term is a first time derivative; Newmark's gamma = 1/2 gives dt/2).
+      Any alpha > 0 gives the monolithic solution at convergence.
+    * One multiplier per interface edge and side: (A^(s) + R^(s)) x^(s) = b^(s) +
+      lambda^(s) (unsigned, on the side's own interface edges), corners primal as in
+      DP1.  Transmission (Eq. f2imp1): lambda^(1) + lambda^(2) = (R^(1) + R^(2)) x^(2)
+      and = (R^(1) + R^(2)) x^(1), so that at convergence the traces agree and the
+      interface rows of the subassembled system hold; R^(1) + R^(2) = 2 alpha M_T on
+      the pair's edges.
+    * Coupled system for u = [lambda^(s1); lambda^(s2); x_c] (s1 < s2 the multiplier's
+      subdomains), solved by restarted GMRES with the diagonal preconditioner
+      [1; 1; diag(K~cc)] (the lambda-lambda diagonal of the coupled matrix is 1).
+    """
+
+    def __init__(self, space, maps: DDMaps, dt, part, alpha=None):
+        self.space, self.maps, self.dt = space, maps, float(dt)
+        self.alpha = 0.5 * self.dt if alpha is None else float(alpha)
+        self.M = interface_mass(space, maps, part)
+        m = maps
+        self.A, self.B, self.Ahat, self.chol = [], [], [], []
+        self.Acc_tilde = np.zeros((m.n_corner, m.n_corner))
+        Md = self.M.toarray() if m.n_lambda <= 20000 else None
+        for s in range(m.n_sub):
+            loc = m.local[s]
+            dof_map = -np.ones(space.n, dtype=np.int64)
+            dof_map[loc] = np.arange(len(loc))
+            Ts, Ss = space.assemble(m.tets_of[s], dof_map, len(loc))
+            As = (Ts + (dt * dt / 4.0) * Ss).toarray()
+            self.A.append(As)
+            self.B.append((2.0 * Ts - (dt * dt / 2.0) * Ss).toarray())
+            # R^(s) = alpha M_T on the multipliers that involve s, at their local positions
+            ks, ls = [], []
+            for side in range(2):
+                sel = np.flatnonzero(m.mult_sub[:, side] == s)
+                ks.append(sel)
+                ls.append(m.mult_loc[sel, side])
+            k = np.concatenate(ks)
+            l = np.concatenate(ls)
+            Ah = As.copy()
+            sub = Md[np.ix_(k, k)] if Md is not None else self.M[k][:, k].toarray()
+            Ah[np.ix_(l, l)] += self.alpha * sub
+            self.Ahat.append(Ah)
+            nr = m.nr[s]
+            cf = sla.cho_factor(Ah[:nr, :nr], lower=True)
+            self.chol.append(cf)
+            Arc = Ah[:nr, nr:]
+            ci = m.corner_of_local[s]
+            self.Acc_tilde[np.ix_(ci, ci)] += Ah[nr:, nr:] - Arc.T @ sla.cho_solve(cf, Arc)
+        self.diag_c = np.diag(self.Acc_tilde).copy()
+        self.u = np.zeros(2 * m.n_lambda + m.n_corner)
+
+    # -- maps ----------------------------------------------------------------------
+    def local_z(self, lam1, lam2, s):
+        """lambda^(s) on the local r-vector of s (unsigned, the side's own multipliers)."""
+        m = self.maps
+        z = np.zeros(m.nr[s])
+        sel = m.mult_sub[:, 0] == s
+        z[m.mult_loc[sel, 0]] += lam1[sel]
+        sel = m.mult_sub[:, 1] == s
+        z[m.mult_loc[sel, 1]] += lam2[sel]
+        return z
+
+    def traces(self, xr):
+        """(t1, t2): the interface values of the multiplier edges in s1 and in s2."""
+        m = self.maps
+        off = np.concatenate([[0], np.cumsum([len(v) for v in xr])])
+        flat = np.concatenate(xr)
+        return (flat[off[m.mult_sub[:, 0]] + m.mult_loc[:, 0]],
+                flat[off[m.mult_sub[:, 1]] + m.mult_loc[:, 1]])
+
+    def Bc_sum(self, xc):
+        out = np.zeros(self.maps.n_corner)
+        for s in range(self.maps.n_sub):
+            np.add.at(out, self.maps.corner_of_local[s], xc[s])
+        return out
+
+    def split(self, u):
+        nl = self.maps.n_lambda
+        return u[:nl], u[nl:2 * nl], u[2 * nl:]
+
+    # -- coupled operator (Eq. f2imp1 with Eq. F2un) ----------------------------------
+    def coupled_apply(self, u):
+        m = self.maps
+        lam1, lam2, xc = self.split(u)
+        xr, cpart = [], []
+        for s in range(m.n_sub):
+            nr = m.nr[s]
+            z = self.local_z(lam1, lam2, s)
+            x = sla.cho_solve(self.chol[s], z - self.Ahat[s][:nr, nr:] @ xc[m.corner_of_local[s]])
+            xr.append(x)
+            cpart.append(self.Ahat[s][nr:, :nr] @ sla.cho_solve(self.chol[s], z))
+        t1, t2 = self.traces(xr)
+        two_a_M = 2.0 * self.alpha * self.M
+        y1 = lam1 + lam2 - two_a_M @ t2
+        y2 = lam1 + lam2 - two_a_M @ t1
+        yc = self.Acc_tilde @ xc + self.Bc_sum(cpart)      # lambda enters the local problems with +
+        return np.concatenate([y1, y2, yc])
+
+    def rhs(self, b_local):
+        m = self.maps
+        y0, fc = [], []
+        for s in range(m.n_sub):
+            nr = m.nr[s]
+            y = sla.cho_solve(self.chol[s], b_local[s][:nr])
+            y0.append(y)
+            fc.append(b_local[s][nr:] - self.Ahat[s][nr:, :nr] @ y)
+        t1, t2 = self.traces(y0)
+        two_a_M = 2.0 * self.alpha * self.M
+        return np.concatenate([two_a_M @ t2, two_a_M @ t1, self.Bc_sum(fc)]), y0
+
+    def solve(self, b_local, tol=1e-12, max_it=2000, warm=True, restart=20):
+        """Returns (x_local list, u = [lambda1; lambda2; x_c], iterations, residual estimate)."""
+        m = self.maps
+        b, y0 = self.rhs(b_local)
+        dinv = np.concatenate([np.ones(2 * m.n_lambda), 1.0 / self.diag_c])
+        x0 = self.u.copy() if warm else np.zeros(len(b))
+        u, it, res = x0, 0, 0.0
+        if len(b):
+            u, it, res, _ = gmres(self.coupled_apply, b, x0, dinv, tol, restart, max_it)
+        self.u = u.copy()
+        lam1, lam2, xc = self.split(u)
+        x = []
+        for s in range(m.n_sub):
+            nr = m.nr[s]
+            xc_s = xc[m.corner_of_local[s]]
+            z = self.local_z(lam1, lam2, s)
+            xr = y0[s] + sla.cho_solve(self.chol[s], z - self.Ahat[s][:nr, nr:] @ xc_s)
+            x.append(np.concatenate([xr, xc_s]))
+        return x, u, it, res
+
+    def gather_global(self, x_local):
+        e = np.zeros(self.space.n)
+        for s in range(self.maps.n_sub - 1, -1, -1):
+            e[self.maps.local[s]] = x_local[s]
+        return e
+
+    def newmark_rhs(self, e_n, e_nm1, src_vec):
+        """Subassembled L^(s) = B^(s) e^n - A^(s) e^{n-1} - (source on the owner), unmodified A."""
+        m = self.maps
+        out = []
+        for s in range(m.n_sub):
+            loc = m.local[s]
+            b = self.B[s] @ e_n[loc] - self.A[s] @ e_nm1[loc]
+            own = m.owner[loc] == s
+            b[own] -= src_vec[loc[own]]
+            out.append(b)
+        return out
+
+
+def run_dp2(space, maps, part, dt, src, d2g, n_steps, tol=1e-12, keep=False, restart=20, alpha=None):
+    """Newmark march with every step solved by the CPU MFETI-DP2 solver."""
+    dd = DP2Solver(space, maps, dt, part, alpha)
+    e_nm1 = np.zeros(space.n)
+    e_n = np.zeros(space.n)
+    its, fields = [], []
+    for k in range(n_steps):
+        b = dd.newmark_rhs(e_n, e_nm1, d2g[k] * src)
+        x, u, it, res = dd.solve(b, tol=tol, restart=restart)
+        e_np1 = dd.gather_global(x)
+        e_nm1, e_n = e_n, e_np1
+        its.append(it)
+        if keep:
+            fields.append(e_n.copy())
+    out = dict(e_n=e_n, iters=np.array(its), solver=dd)
     if keep:
         out["fields"] = np.array(fields)
     return out

@@ -108,6 +108,62 @@ def element_matrices(X):
     return T, S, vol
 
 
+def face_tangential_mass(P):
+    """Tangential Whitney mass 3x3 of triangles P [...,3,3] (node rows sorted by global id).
+
+    Edges in the order (0,1), (1,2), (0,2), each oriented from its lower to its
+    higher node.  The tangential trace of the 3-D Whitney function of an edge of
+    the face is the 2-D Whitney function l_a g_b - l_b g_a of the triangle (g:
+    surface gradients of its barycentrics), so
+    M[p,q] = int_face (n x W_p).(n x W_q) = int_face W_p,t . W_q,t, integrated
+    exactly with int l_a l_c = area (1 + delta_ac) / 12.
+    """
+    P = np.asarray(P, dtype=np.float64)
+    E1 = P[..., 1, :] - P[..., 0, :]
+    E2 = P[..., 2, :] - P[..., 0, :]
+    G = np.stack([np.stack([(E1 * E1).sum(-1), (E1 * E2).sum(-1)], -1),
+                  np.stack([(E1 * E2).sum(-1), (E2 * E2).sum(-1)], -1)], -2)
+    Gi = np.linalg.inv(G)
+    g = np.zeros(P.shape[:-2] + (3, 3))
+    g[..., 1, :] = Gi[..., 0, 0, None] * E1 + Gi[..., 0, 1, None] * E2
+    g[..., 2, :] = Gi[..., 1, 0, None] * E1 + Gi[..., 1, 1, None] * E2
+    g[..., 0, :] = -g[..., 1, :] - g[..., 2, :]
+    area = 0.5 * np.linalg.norm(np.cross(E1, E2), axis=-1)
+    Ml = area[..., None, None] * (np.ones((3, 3)) + np.eye(3)) / 12.0
+    GG = g @ np.swapaxes(g, -1, -2)
+    fe = [(0, 1), (1, 2), (0, 2)]
+    M = np.zeros(P.shape[:-2] + (3, 3))
+    for p_, (a, b) in enumerate(fe):
+        for q_, (c, d) in enumerate(fe):
+            M[..., p_, q_] = (Ml[..., a, c] * GG[..., b, d] - Ml[..., a, d] * GG[..., b, c]
+                              - Ml[..., b, c] * GG[..., a, d] + Ml[..., b, d] * GG[..., a, c])
+    return M
+
+
+def interface_faces(tets, part):
+    """Triangles shared by two tets of different subdomains: (sorted node triples [F,3],
+    subdomain pairs [F,2] with the lower id first)."""
+    tets = np.asarray(tets, dtype=np.int64)
+    part = np.asarray(part, dtype=np.int64)
+    T = len(tets)
+    f = np.concatenate([np.sort(tets[:, list(fc)], axis=1) for fc in LOCAL_FACES], axis=0)
+    owner = np.tile(np.arange(T), 4)
+    uf, inv, cnt = np.unique(f, axis=0, return_inverse=True, return_counts=True)
+    first = -np.ones(len(uf), dtype=np.int64)
+    second = -np.ones(len(uf), dtype=np.int64)
+    for r, u in enumerate(inv):
+        if first[u] < 0:
+            first[u] = owner[r]
+        else:
+            second[u] = owner[r]
+    shared = (cnt == 2)
+    sa, sb = part[first[shared]], part[second[shared]]
+    keep = sa != sb
+    faces = uf[shared][keep]
+    pairs = np.stack([np.minimum(sa, sb)[keep], np.maximum(sa, sb)[keep]], axis=1)
+    return faces, pairs
+
+
 def whitney_at(X, lam):
     """Values [6,3] of the six local Whitney functions at barycentric point lam [4]."""
     g, _ = barycentric_gradients(X)
