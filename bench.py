@@ -69,6 +69,8 @@ def parse():
                     help="interface solver of the headline runs: Schur CG (Eq. f1schur) or coupled GMRES(20)")
     ap.add_argument("--no-sym", action="store_true",
                     help="DD_MIXED GEMVs on the dense FP32 copy instead of the packed symmetric tiles")
+    ap.add_argument("--no-dp2", action="store_true",
+                    help="skip the MFETI-DP2 runs (its own factorisation; coupled GMRES(20), FP64 at tol 1e-6 and mixed)")
     ap.add_argument("--no-gmres", action="store_true",
                     help="skip the coupled-GMRES(20) vs Schur-CG comparison at the paper's tolerance 1e-6")
     ap.add_argument("--cavity", type=int, nargs=2, metavar=("N", "K"), default=None,
@@ -369,6 +371,31 @@ def run_ours(args, rank, world, local):
         barrier()
         ms_e2e = ev0.elapsed_time(ev1)
 
+    # MFETI-DP2 (Sec. III-B): refactor with the Robin term, FP64 at the paper's tolerance and
+    # the headline's mixed settings; last, so that the runs above keep the DP1 factorisation
+    dp2 = None
+    if not args.no_dp2 and not pic:
+        pd = D.make_params(precision=D.DD_FP64, tol=1e-6, use_graph=g, chunk=ch,
+                           solver=D.DD_SOLVER_COUPLED_GMRES, scheme=D.DD_SCHEME_DP2, restart=20)
+        fs.set_params(pd)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fs.factor(dt)
+        torch.cuda.synchronize()
+        t_f2 = time.perf_counter() - t0
+        msd, itd, _, _, ed = run_steps(pd, False)
+        pm = D.make_params(precision=D.DD_MIXED, tol=args.tol32, refine_tol=args.refine_tol, max_refine=6,
+                           use_graph=g, chunk=ch, solver=D.DD_SOLVER_COUPLED_GMRES, scheme=D.DD_SCHEME_DP2,
+                           restart=20, sym_fp32=sym)
+        msm, itm, refm, _, em = run_steps(pm, False)
+        dp2 = {"factor_s": t_f2,
+               "fp64_tol_1e-6": {"steps_per_s": K * 1e3 / msd, "ms_per_step": msd / K,
+                                 "iters_per_step": float(np.mean(itd))},
+               "mixed": {"steps_per_s": K * 1e3 / msm, "ms_per_step": msm / K, "iters_per_step": float(np.mean(itm)),
+                         "refinements_per_step": float(np.mean(refm)),
+                         "rel_err_vs_fp64_dp1": (float(torch.linalg.norm(em - e64) / torch.linalg.norm(e64))
+                                                 if e64 is not None else None)}}
+
     def allmax(x):
         if world == 1:
             return x
@@ -380,7 +407,7 @@ def run_ours(args, rank, world, local):
     sizes = fs.sizes
     res = dict(fs=fs, K=K, ms64=ms64, ms32=ms32, ms_e2e=ms_e2e, it64=it64, it32=it32, ref32=ref32, prof64=prof64,
                prof32=prof32, rel=rel, launches64=launches64, launches32=launches32, t_setup=t_setup, t_factor=t_factor, clocks=clocks.summary(), sizes=sizes,
-               workload=w, dt=dt, t_tune=t_tune, tiles=tiles, pic=pic, gmres=gm)
+               workload=w, dt=dt, t_tune=t_tune, tiles=tiles, pic=pic, gmres=gm, dp2=dp2)
     return res
 
 
@@ -519,6 +546,7 @@ def main():
                  "tol": args.tol64, "stages": st64},
         "speedup_mixed_vs_fp64": v32 / v64,
         "coupled_gmres_vs_schur_cg": r["gmres"],
+        "mfeti_dp2": r["dp2"],
         "rel_err_mixed_vs_fp64": r["rel"],
         "setup_s": r["t_setup"], "factor_s": r["t_factor"], "autotune_s": r["t_tune"],
         "gemv_tiles": r["tiles"],

@@ -64,6 +64,11 @@ extern "C" {
                                       Sec. IV, Fig. fetiIter)                                      */
 #define DD_MAX_RESTART 32          /* largest GMRES restart length                                */
 
+/* Domain-decomposition schemes (dd_params.scheme). */
+#define DD_SCHEME_DP1 0  /* MFETI-DP1 (Sec. III-A): one multiplier per interface edge         */
+#define DD_SCHEME_DP2 1  /* MFETI-DP2 (Sec. III-B), edge-only reading: Robin term alpha*M_T on
+                            every local interface, one multiplier per interface edge and side */
+
 typedef struct dd_handle dd_handle;
 
 /* Tetrahedral mesh (host arrays, copied during dd_setup).
@@ -115,6 +120,21 @@ typedef struct {
  *            the previous solve's [lambda; x_c].  DD_FP64 and warm_start 0/1
  *            only (DD_ERR_ARG otherwise).  K~cc^-1 is not used by this solver.
  * restart    GMRES restart length m, 1..DD_MAX_RESTART (the paper: 20).
+ * scheme     DD_SCHEME_DP1 (default) or DD_SCHEME_DP2.  DP2 (Sec. III-B, read for
+ *            the edge-only step system A = T + dt^2/4 S): every local matrix
+ *            gets the Robin term R = robin_alpha * M_T on its interface edges
+ *            (M_T: tangential Whitney mass of the interface faces, restricted
+ *            to the multiplier edges); each interface edge carries one
+ *            multiplier per side, (A^(s) + R^(s)) x^(s) = b^(s) + lambda^(s), with
+ *            the transmission conditions lambda^(1) + lambda^(2) =
+ *            2 alpha M_T x^(2) = 2 alpha M_T x^(1) (Eq. f2imp1); corners stay
+ *            primal.  Solved as the coupled system for [lambda^(1); lambda^(2);
+ *            x_c] by GMRES (DD_SOLVER_COUPLED_GMRES required, DD_ERR_ARG
+ *            otherwise) with the diagonal preconditioner [1; 1; diag(K~cc)].
+ *            The scheme and alpha are fixed by dd_factor: a step with another
+ *            scheme than the factorisation returns DD_ERR_STATE.
+ * robin_alpha DP2 Robin coefficient; <= 0 selects dt / 2 (the admittance of
+ *            vacuum, eta = 1, times Newmark's dt/2).
  * sym_fp32   DD_MIXED: 1 = the FP32 GEMVs over symmetric blocks (local solve,
  *            interface rows, coupled operator) read packed lower-triangular
  *            FP32 tiles (the swept local matrix is J times a symmetric matrix,
@@ -133,6 +153,8 @@ typedef struct {
     int solver;
     int restart;
     int sym_fp32;
+    int scheme;
+    double robin_alpha;
 } dd_params;
 
 /* Sizes of a set-up problem. */
@@ -318,6 +340,22 @@ int dd_schur_apply(dd_handle* h, const double* lam, double* out, void* stream);
  * workspace (not reentrant on one handle).  Errors: DD_ERR_ARG, DD_ERR_STATE
  * (not factored), DD_ERR_CUDA. */
 int dd_coupled_apply(dd_handle* h, const double* u, double* out, void* stream);
+
+/* With the DP2 factorisation (scheme DD_SCHEME_DP2 at dd_factor) the coupled
+ * operator of Eqs. f2imp1 + F2un instead, u = [l1; l2; x_c] (device
+ * [2 n_lambda + n_corner]):
+ *   out[0:nl]        = l1 + l2 - 2 alpha M_T t2(u)
+ *   out[nl:2nl]      = l1 + l2 - 2 alpha M_T t1(u)
+ *   out[2nl:]        = K~cc x_c + sum_s B_c A_cr (A+R)_rr^-1 lambda^(s)
+ * with t_side(u) the interface traces (A+R)_rr^-1 (lambda^(s) - A_rc x_c) of
+ * the multiplier edges in the subdomain of that side.  Errors as
+ * dd_coupled_apply (DD_ERR_STATE if the factorisation is DP1). */
+int dd_dp2_apply(dd_handle* h, const double* u, double* out, void* stream);
+
+/* Interface tangential mass M_T on the multiplier edges (host CSR, n_lambda
+ * rows; column = multiplier index).  *nnz (host) receives the number of
+ * entries; ptr [n_lambda+1], col [nnz], val [nnz] may each be NULL. */
+int dd_get_interface_mass(const dd_handle* h, int64_t* nnz, int64_t* ptr, int32_t* col, double* val);
 
 /* Same result as dd_schur_apply, for callers that must not allocate device
  * memory (for example code running inside a fixed memory pool, a callback

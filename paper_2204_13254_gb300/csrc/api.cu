@@ -48,6 +48,8 @@ dd_params default_params() {
     p.solver = DD_SOLVER_SCHUR_CG;
     p.restart = 20;
     p.sym_fp32 = 1;
+    p.scheme = DD_SCHEME_DP1;
+    p.robin_alpha = 0.0;
     return p;
 }
 
@@ -56,6 +58,11 @@ int check_params(dd_handle* h, const dd_params& p) {
     if (!(p.tol > 0.0) || p.max_it < 1 || p.chunk < 1 || p.max_refine < 1 || !(p.refine_tol > 0.0))
         return h->fail(DD_ERR_ARG, "tol, refine_tol must be > 0 and max_it, chunk, max_refine >= 1");
     if (p.sym_fp32 != 0 && p.sym_fp32 != 1) return h->fail(DD_ERR_ARG, "sym_fp32 must be 0 or 1");
+    if (p.scheme != DD_SCHEME_DP1 && p.scheme != DD_SCHEME_DP2)
+        return h->fail(DD_ERR_ARG, "scheme must be DD_SCHEME_DP1 or DD_SCHEME_DP2");
+    if (p.scheme == DD_SCHEME_DP2 && p.solver != DD_SOLVER_COUPLED_GMRES)
+        return h->fail(DD_ERR_ARG, "MFETI-DP2 is solved by the coupled GMRES (its system is not symmetric)");
+    if (!std::isfinite(p.robin_alpha)) return h->fail(DD_ERR_ARG, "robin_alpha must be finite");
     if (p.solver != DD_SOLVER_SCHUR_CG && p.solver != DD_SOLVER_COUPLED_GMRES)
         return h->fail(DD_ERR_ARG, "solver must be DD_SOLVER_SCHUR_CG or DD_SOLVER_COUPLED_GMRES");
     if (p.solver == DD_SOLVER_COUPLED_GMRES) {
@@ -224,6 +231,16 @@ size_t dd_workspace_layout(dd_handle* h, bool assign) {
     for (int k = 0; k < 3; ++k) L.take(d.e[k], nd);
     for (int k = 0; k < 3; ++k) L.take(d.mu[k], nd);
     L.take(d.lam_adj, nm);
+    L.take(d.lam2, nm);
+    L.take(d.lam2f, nm);
+    L.take(d.lam2_adj, nm);
+    L.take(d.lam2f_adj, nm);
+    L.take(d.lam2_scratch, nm);
+    L.take(d.lam2f_scratch, nm);
+    L.take(d.g2, nm);
+    L.take(d.mt_ptr, nm + 1);
+    L.take(d.mt_col, h->mt_col.size());
+    L.take(d.mt_val, h->mt_val.size());
     L.take(d.lamf_adj, nm);
     L.take(d.lam_prev, nm);
     L.take(d.lam_prev_adj, nm);
@@ -282,7 +299,7 @@ size_t dd_workspace_layout(dd_handle* h, bool assign) {
     L.take(d.xCf_scratch, nc);
     L.take(d.dinvC, nc);
     {
-        const int64_t nu = (int64_t)(nm + nc);
+        const int64_t nu = (int64_t)(2 * nm + nc);   // MFETI-DP2 has two multiplier blocks
         h->gm_ldv = (nu + 31) / 32 * 32;
         h->gm_blocks = (int32_t)std::max<int64_t>(1, (nu + kGmChunk - 1) / kGmChunk);
         L.take(d.Vk, (size_t)(kMaxRestart + 1) * (size_t)h->gm_ldv);
@@ -462,6 +479,40 @@ int read_gm(dd_handle* h, GmresScalars* out, cudaStream_t s) {
 // cycle start and every `chunk` Arnoldi steps; graph mode captures the restart
 // cycles as a conditional WHILE node whose body holds the cycle start, a nested
 // WHILE node over the Arnoldi steps and the update of u.
+// The coupled solve's unknown in blocks (DP1: [lambda; x_c]; DP2: [lambda^(s1);
+// lambda^(s2); x_c]), right-hand side [g; (g2;) fC], diagonal preconditioner.
+UView uview(const dd_handle* h, int prec) {
+    const DevPtrs& d = h->d;
+    const bool f32 = prec == DD_MIXED;
+    const bool dp2 = h->factored_scheme == DD_SCHEME_DP2;
+    const bool pc = h->prm.precond != 0;
+    UView U;
+    U.n1 = (int64_t)h->mult_dof.size();
+    U.n2 = dp2 ? U.n1 : 0;
+    U.nc = (int64_t)h->corner_dof.size();
+    U.b1 = d.g;
+    U.b2 = dp2 ? d.g2 : nullptr;
+    U.bc = d.fC;
+    U.x1 = d.lam;
+    U.x2 = dp2 ? d.lam2 : nullptr;
+    U.xc = d.xC;
+    U.x1f = f32 ? d.lamf : nullptr;
+    U.x2f = (f32 && dp2) ? d.lam2f : nullptr;
+    U.xcf = f32 ? d.xCf : nullptr;
+    U.d1 = (pc && !dp2) ? d.dinv : nullptr;   // DP2: the multiplier blocks have unit diagonal
+    U.dc = pc ? d.dinvC : nullptr;
+    U.ms = d.mult_slot;
+    U.cp = d.corner_ptr;
+    U.cs = d.corner_slot;
+    if (dp2) {
+        U.mtp = d.mt_ptr;
+        U.mtc = d.mt_col;
+        U.mtv = d.mt_val;
+        U.two_alpha = 2.0 * h->factored_alpha;
+    }
+    return U;
+}
+
 int gmres_solve(dd_handle* h, int prec, double tol, bool warm, int* it_out, double* res_out, cudaStream_t s,
                 int depth, int adaptive) {
     const size_t nm = h->mult_dof.size(), nc = h->corner_dof.size();
@@ -469,17 +520,26 @@ int gmres_solve(dd_handle* h, int prec, double tol, bool warm, int* it_out, doub
     *res_out = 0.0;
     if (nm + nc == 0) return DD_OK;
     const Vecs V = vecs(h, prec);
+    const UView U = uview(h, prec);
+    const bool dp2 = U.n2 > 0;
     const bool use_warm = warm && (h->lam_valid || h->capturing);
     if (!use_warm) {
         if (nm) CK(h, (int)cudaMemsetAsync(h->d.lam, 0, sizeof(double) * nm, s), "memset");
         if (nc) CK(h, (int)cudaMemsetAsync(h->d.xC, 0, sizeof(double) * nc, s), "memset");
         if (V.f32 && nm) CK(h, (int)cudaMemsetAsync(V.lamf, 0, sizeof(float) * nm, s), "memset");
         if (V.f32 && nc) CK(h, (int)cudaMemsetAsync(V.xCf, 0, sizeof(float) * nc, s), "memset");
+        if (dp2) CK(h, (int)cudaMemsetAsync(h->d.lam2, 0, sizeof(double) * nm, s), "memset");
+        if (dp2 && V.f32) CK(h, (int)cudaMemsetAsync(h->d.lam2f, 0, sizeof(float) * nm, s), "memset");
     }
     float* zuf = V.f32 ? h->d.zuf : nullptr;
-    // x = [B_r^T u_l ; -u_c] over the [Gamma | c] columns of every local matrix
-    const XSrc xs_x = xsrc(X_LAMBDA_CV, h->d.lam, nullptr, V.lamf, nullptr, h->d.xC, V.xCf);
-    const XSrc xs_z = xsrc(X_LAMBDA_CV, h->d.zu, nullptr, zuf, nullptr, h->d.zu + nm, zuf ? zuf + nm : nullptr);
+    // DP1: x = [B_r^T u_l ; -u_c] over the [Gamma | c] columns of every local matrix;
+    // DP2: x = [lambda^(s) (the subdomain's own side) ; +u_c]
+    const int64_t o2 = (int64_t)(dp2 ? 2 * nm : nm);   // offset of the corner block in u
+    const XSrc xs_x = dp2 ? xsrc(X_SIDE_CP, h->d.lam, h->d.lam2, V.lamf, V.f32 ? h->d.lam2f : nullptr, h->d.xC, V.xCf)
+                          : xsrc(X_LAMBDA_CV, h->d.lam, nullptr, V.lamf, nullptr, h->d.xC, V.xCf);
+    const XSrc xs_z = dp2 ? xsrc(X_SIDE_CP, h->d.zu, h->d.zu + nm, zuf, zuf ? zuf + nm : nullptr, h->d.zu + o2,
+                                 zuf ? zuf + o2 : nullptr)
+                          : xsrc(X_LAMBDA_CV, h->d.zu, nullptr, zuf, nullptr, h->d.zu + nm, zuf ? zuf + nm : nullptr);
     const GemvOut go = V.f32 ? gout(nullptr, nullptr, V.wf, nullptr, 1.0) : gout(h->d.w, nullptr, nullptr, nullptr, 1.0);
     const double mbc = mb(h, GEMV_COUPLED, prec);
     const int32_t* skip = &h->d.gs->skip;
@@ -489,8 +549,8 @@ int gmres_solve(dd_handle* h, int prec, double tol, bool warm, int* it_out, doub
             CK(h, launch_gemv(h, GEMV_COUPLED, prec, xs_x, go, false, st), "coupled operator on x");
         }
         Prof P(h, ST_VEC, st, 2);
-        CK(h, launch_gm_start(h, have_q, V.wf, cond_inner, st), "gmres start");
-        CK(h, launch_gm_normalize(h, zuf, st), "gmres normalize");
+        CK(h, launch_gm_start(h, U, have_q, V.wf, cond_inner, st), "gmres start");
+        CK(h, launch_gm_normalize(h, U, zuf, st), "gmres normalize");
         return DD_OK;
     };
     // one Arnoldi step; its full-work count is added once the step count is known
@@ -500,9 +560,9 @@ int gmres_solve(dd_handle* h, int prec, double tol, bool warm, int* it_out, doub
             CK(h, launch_gemv(h, GEMV_COUPLED, prec, xs_z, go, false, st, skip), "coupled operator");
         }
         Prof P(h, ST_VEC, st, 3);
-        CK(h, launch_gm_pass(h, 0, V.wf, 0ull, st), "gmres pass 0");
-        CK(h, launch_gm_pass(h, 1, V.wf, cond_inner, st), "gmres pass 1");
-        CK(h, launch_gm_normalize(h, zuf, st), "gmres normalize");
+        CK(h, launch_gm_pass(h, U, 0, V.wf, zuf, 0ull, st), "gmres pass 0");
+        CK(h, launch_gm_pass(h, U, 1, V.wf, zuf, cond_inner, st), "gmres pass 1");
+        CK(h, launch_gm_normalize(h, U, zuf, st), "gmres normalize");
         return DD_OK;
     };
     if (h->capturing) {
@@ -549,7 +609,7 @@ int gmres_solve(dd_handle* h, int prec, double tol, bool warm, int* it_out, doub
         }
         if (!brc) {
             Prof P(h, ST_VEC, bo, 1);
-            const int urc = launch_gm_update(h, V.lamf, V.xCf, (unsigned long long)ho, bo);
+            const int urc = launch_gm_update(h, U, (unsigned long long)ho, bo);
             if (urc) brc = cuda_fail(h, urc, "gmres update");
         }
         cudaGraph_t out_body;
@@ -589,7 +649,7 @@ int gmres_solve(dd_handle* h, int prec, double tol, bool warm, int* it_out, doub
         }
         {
             Prof P(h, ST_VEC, s, 1);
-            CK(h, launch_gm_update(h, V.lamf, V.xCf, 0ull, s), "gmres update");
+            CK(h, launch_gm_update(h, U, 0ull, s), "gmres update");
         }
         if (c.final) break;
     }
@@ -609,6 +669,8 @@ int gmres_solve(dd_handle* h, int prec, double tol, bool warm, int* it_out, doub
 
 int dd_solve(dd_handle* h, int prec, double tol, bool warm, int* it_out, double* res_out, cudaStream_t s,
              int adaptive = 0, int depth = 0) {
+    if (h->prm.scheme != h->factored_scheme)
+        return h->fail(DD_ERR_STATE, "the scheme changed since dd_factor: factor again");
     const bool has_c = !h->corner_dof.empty();
     const bool has_l = !h->mult_dof.empty();
     const Vecs V = vecs(h, prec);
@@ -625,14 +687,22 @@ int dd_solve(dd_handle* h, int prec, double tol, bool warm, int* it_out, double*
         CK(h, launch_iface_rhs(h, V.fCf, s), "iface rhs");
     }
     if (h->prm.solver == DD_SOLVER_COUPLED_GMRES) {
-        // [lambda; x_c] from the coupled Eqs. F1lr + F1uc, then x_r      Eq. rF1
+        const bool dp2 = h->factored_scheme == DD_SCHEME_DP2;
+        if (dp2) {   // b1 = 2 alpha M_T t2(y), b2 = 2 alpha M_T t1(y)            Eqs. f2imp1
+            Prof P(h, ST_VEC, s, 1);
+            CK(h, launch_dp2_rhs(h, uview(h, prec), s), "dp2 rhs");
+        }
+        // [lambda; x_c] from the coupled Eqs. F1lr + F1uc (DP2: f2imp1 + F2un), then x_r   Eq. rF1 / IF2
         const int status = gmres_solve(h, prec, tol, warm, it_out, res_out, s, depth, adaptive);
         if (status != DD_OK && status != DD_ERR_NO_CONVERGENCE) return status;
         const std::string msg = h->err;
         {
             Prof P(h, ST_RECOVER, s, 1, mb(h, GEMV_RECOVER, prec));
-            CK(h, launch_gemv(h, GEMV_RECOVER, prec, xsrc(X_RECOVER, h->d.lam, h->d.xC, V.lamf, V.xCf),
-                              gout(h->d.x, h->d.y, nullptr, nullptr, 1.0), false, s), "recover");
+            const XSrc xr = dp2 ? xsrc(X_SIDE_CP, h->d.lam, h->d.lam2, V.lamf, V.f32 ? h->d.lam2f : nullptr, h->d.xC,
+                                       V.xCf)
+                                : xsrc(X_RECOVER, h->d.lam, h->d.xC, V.lamf, V.xCf);
+            CK(h, launch_gemv(h, GEMV_RECOVER, prec, xr, gout(h->d.x, h->d.y, nullptr, nullptr, 1.0), false, s),
+               "recover");
         }
         h->err = msg;
         return status;
@@ -876,6 +946,9 @@ int dd_bind_workspace(dd_handle* h, void* dev, size_t bytes, void* stream) {
     CK(h, upload(h->d.col_dof, h->col_dof, s), "upload");
     CK(h, upload(h->d.Tval, h->Tval, s), "upload");
     CK(h, upload(h->d.symd, h->sym, s), "upload");
+    CK(h, upload(h->d.mt_ptr, h->mt_ptr, s), "upload");
+    CK(h, upload(h->d.mt_col, h->mt_col, s), "upload");
+    CK(h, upload(h->d.mt_val, h->mt_val, s), "upload");
     for (int m = 0; m < GEMV_NMODES; ++m)
         if (!h->sym_rng[m].empty()) CK(h, upload(h->d.sym_rng[m], h->sym_rng[m], s), "upload");
     CK(h, upload(h->d.Sval, h->Sval, s), "upload");
@@ -924,6 +997,11 @@ int dd_factor(dd_handle* h, double dt, void* stream) {
         CK(h, launch_csr_combine(h, dt * dt / 4.0, s), "A = T + dt^2/4 S");
         CK(h, launch_dense_assemble(h, s), "dense assemble");
     }
+    const double alpha = h->prm.robin_alpha > 0.0 ? h->prm.robin_alpha : 0.5 * dt;
+    if (h->prm.scheme == DD_SCHEME_DP2) {
+        Prof P(h, ST_FACTOR, s, 1);
+        CK(h, launch_robin_add(h, alpha, s), "Robin term");
+    }
     for (int k0 = 0; k0 < h->max_nr; k0 += kNB) {
         Prof P(h, ST_FACTOR, s, 3);
         CK(h, launch_sweep(h, false, k0, s), "local elimination");
@@ -970,6 +1048,8 @@ int dd_factor(dd_handle* h, double dt, void* stream) {
     h->cur_adj = 0;
     h->lam_valid = false;
     h->lam_adj_valid = false;
+    h->factored_scheme = h->prm.scheme;
+    h->factored_alpha = alpha;
     h->factored = true;
     return DD_OK;
 }
@@ -1006,6 +1086,10 @@ int keep_first_pass(dd_handle* h, bool save, cudaStream_t s) {
     if (!rc && h->prm.solver == DD_SOLVER_COUPLED_GMRES) {
         rc = cp(h->d.xC, h->d.xC_scratch, sizeof(double) * nc);
         if (!rc) rc = cp(h->d.xCf, h->d.xCf_scratch, sizeof(float) * nc);
+    }
+    if (!rc && h->factored_scheme == DD_SCHEME_DP2) {
+        rc = cp(h->d.lam2, h->d.lam2_scratch, sizeof(double) * nm);
+        if (!rc) rc = cp(h->d.lam2f, h->d.lam2f_scratch, sizeof(float) * nm);
     }
     return rc;
 }
@@ -1261,6 +1345,10 @@ int dd_step_graph(dd_handle* h, const double* d2g, double* e_out, dd_stats* stat
         CK(h, (int)cudaMemsetAsync(h->d.xC, 0, sizeof(double) * h->corner_dof.size(), s), "memset");
         CK(h, (int)cudaMemsetAsync(h->d.xCf, 0, sizeof(float) * h->corner_dof.size(), s), "memset");
     }
+    if (!h->lam_valid && h->factored_scheme == DD_SCHEME_DP2 && !h->mult_dof.empty()) {
+        CK(h, (int)cudaMemsetAsync(h->d.lam2, 0, sizeof(double) * h->mult_dof.size(), s), "memset");
+        CK(h, (int)cudaMemsetAsync(h->d.lam2f, 0, sizeof(float) * h->mult_dof.size(), s), "memset");
+    }
     CK(h, (int)cudaGraphLaunch((cudaGraphExec_t)h->gexec[phase], s), "graph launch");
     h->lam_valid = true;
     double* e_np1 = h->d.e[(phase + 1) % 3];
@@ -1294,6 +1382,8 @@ void swap_lambda(dd_handle* h) {
     std::swap(h->d.lam_prev, h->d.lam_prev_adj);
     std::swap(h->d.xC, h->d.xC_adj);
     std::swap(h->d.xCf, h->d.xCf_adj);
+    std::swap(h->d.lam2, h->d.lam2_adj);
+    std::swap(h->d.lam2f, h->d.lam2f_adj);
     std::swap(h->lam_valid, h->lam_adj_valid);
 }
 
@@ -1386,6 +1476,7 @@ int dd_probe_seed(dd_handle* h, const double* e, double weight, double* seed, vo
 int dd_schur_apply(dd_handle* h, const double* lam, double* out, void* stream) {
     if (!h || !lam || !out) return DD_ERR_ARG;
     if (!h->factored) return h->fail(DD_ERR_STATE, "dd_schur_apply before dd_factor");
+    if (h->factored_scheme != DD_SCHEME_DP1) return h->fail(DD_ERR_STATE, "dd_schur_apply needs the DP1 factorisation");
     if (h->mult_dof.empty()) return DD_OK;
     cudaStream_t s = (cudaStream_t)stream;
     CK(h, apply_schur_w(h, DD_FP64, X_LAMBDA, lam, nullptr, nullptr, nullptr, false, s), "apply");
@@ -1397,6 +1488,7 @@ int dd_schur_apply(dd_handle* h, const double* lam, double* out, void* stream) {
 int dd_coupled_apply(dd_handle* h, const double* u, double* out, void* stream) {
     if (!h || !u || !out) return DD_ERR_ARG;
     if (!h->factored) return h->fail(DD_ERR_STATE, "dd_coupled_apply before dd_factor");
+    if (h->factored_scheme != DD_SCHEME_DP1) return h->fail(DD_ERR_STATE, "dd_coupled_apply needs the DP1 factorisation");
     const size_t nm = h->mult_dof.size(), nc = h->corner_dof.size();
     if (nm + nc == 0) return DD_OK;
     cudaStream_t s = (cudaStream_t)stream;
@@ -1406,7 +1498,34 @@ int dd_coupled_apply(dd_handle* h, const double* u, double* out, void* stream) {
                           gout(h->d.w, nullptr, nullptr, nullptr, 1.0), false, s), "coupled operator");
     }
     Prof P(h, ST_VEC, s, 1);
-    CK(h, launch_gm_combine(h, out, s), "combine");
+    CK(h, launch_gm_combine(h, uview(h, DD_FP64), u, out, s), "combine");
+    return DD_OK;
+}
+
+int dd_dp2_apply(dd_handle* h, const double* u, double* out, void* stream) {
+    if (!h || !u || !out) return DD_ERR_ARG;
+    if (!h->factored) return h->fail(DD_ERR_STATE, "dd_dp2_apply before dd_factor");
+    if (h->factored_scheme != DD_SCHEME_DP2) return h->fail(DD_ERR_STATE, "dd_dp2_apply needs the DP2 factorisation");
+    const size_t nm = h->mult_dof.size(), nc = h->corner_dof.size();
+    if (nm + nc == 0) return DD_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    {
+        Prof P(h, ST_SCHUR, s, 1, mb(h, GEMV_COUPLED, DD_FP64));
+        CK(h, launch_gemv(h, GEMV_COUPLED, DD_FP64,
+                          xsrc(X_SIDE_CP, u, u + nm, nullptr, nullptr, u + 2 * nm, nullptr),
+                          gout(h->d.w, nullptr, nullptr, nullptr, 1.0), false, s), "DP2 operator");
+    }
+    Prof P(h, ST_VEC, s, 1);
+    CK(h, launch_gm_combine(h, uview(h, DD_FP64), u, out, s), "combine");
+    return DD_OK;
+}
+
+int dd_get_interface_mass(const dd_handle* h, int64_t* nnz, int64_t* ptr, int32_t* col, double* val) {
+    if (!h || !nnz) return DD_ERR_ARG;
+    *nnz = (int64_t)h->mt_col.size();
+    if (ptr && !h->mt_ptr.empty()) std::memcpy(ptr, h->mt_ptr.data(), sizeof(int64_t) * h->mt_ptr.size());
+    if (col && !h->mt_col.empty()) std::memcpy(col, h->mt_col.data(), sizeof(int32_t) * h->mt_col.size());
+    if (val && !h->mt_val.empty()) std::memcpy(val, h->mt_val.data(), sizeof(double) * h->mt_val.size());
     return DD_OK;
 }
 

@@ -112,7 +112,9 @@ enum GemvMode : int {
 // (B_r^T (z + beta p))_j with z = v, p = v2; X_CORNER x_j = v[corner(slot)];
 // X_RECOVER interface slot -(B_r^T v)_j, corner slot v2[corner(slot)];
 // X_COARSE x_j = v[j]; X_PCG_CV / X_LAMBDA_CV: interface slots as X_PCG /
-// X_LAMBDA, corner slots -v3[corner(slot)].  k_gemv<double> reads v/v2, k_gemv<float> reads the
+// X_LAMBDA, corner slots -v3[corner(slot)]; X_SIDE_CP (MFETI-DP2) interface
+// slots v[m] in the first subdomain of multiplier m and v2[m] in the second
+// (unsigned), corner slots +v3[corner(slot)].  k_gemv<double> reads v/v2, k_gemv<float> reads the
 // FP32 shadows vf/v2f so that it executes no FP64 instruction.
 struct XSrc {
     int kind;
@@ -201,6 +203,32 @@ struct GmresScalars {
 };
 constexpr size_t kGmCtrlBytes = offsetof(GmresScalars, max_it);
 
+// The unknown of a coupled solve in three blocks, u = [u1 (n1); u2 (n2); uc (nc)]:
+// MFETI-DP1 u1 = lambda, n2 = 0; MFETI-DP2 u1, u2 = the multipliers of the first
+// and of the second subdomain of every interface edge.  Also what turns the
+// output w (per slot) of the [Gamma|c]-row GEMV into (M u).
+struct UView {
+    int64_t n1 = 0, n2 = 0, nc = 0;
+    const double* b1 = nullptr;   // right-hand side blocks
+    const double* b2 = nullptr;
+    const double* bc = nullptr;
+    double* x1 = nullptr;         // iterate blocks
+    double* x2 = nullptr;
+    double* xc = nullptr;
+    float* x1f = nullptr;         // their FP32 shadows (DD_MIXED) or null
+    float* x2f = nullptr;
+    float* xcf = nullptr;
+    const double* d1 = nullptr;   // inverse diagonal of block 1 (null: 1); block 2 has 1
+    const double* dc = nullptr;   // inverse diagonal of the corner block (null: 1)
+    const int64_t* ms = nullptr;  // mult_slot, corner_ptr, corner_slot
+    const int64_t* cp = nullptr;
+    const int64_t* cs = nullptr;
+    const int64_t* mtp = nullptr; // MFETI-DP2: interface tangential mass (CSR over multipliers); null for DP1
+    const int32_t* mtc = nullptr;
+    const double* mtv = nullptr;
+    double two_alpha = 0.0;
+};
+
 struct DevPtrs {
     // maps (slot = flat local index over all subdomains)
     MatDesc* mats = nullptr;
@@ -258,6 +286,16 @@ struct DevPtrs {
     double* e[3] = {nullptr, nullptr, nullptr};
     double* mu[3] = {nullptr, nullptr, nullptr};
     double* lam_adj = nullptr;       // adjoint multipliers (warm start), swapped with lam
+    double* lam2 = nullptr;          // MFETI-DP2: multipliers of the second subdomain of each interface edge
+    float* lam2f = nullptr;
+    double* lam2_adj = nullptr;
+    float* lam2f_adj = nullptr;
+    double* lam2_scratch = nullptr;  // first refinement pass's second block (next step's warm start)
+    float* lam2f_scratch = nullptr;
+    double* g2 = nullptr;            // MFETI-DP2: right-hand side of the second multiplier block
+    int64_t* mt_ptr = nullptr;       // MFETI-DP2: interface tangential mass, CSR over multipliers
+    int32_t* mt_col = nullptr;
+    double* mt_val = nullptr;
     double* lam_prev = nullptr;      // multipliers of the step before (warm_start 2 extrapolation)
     double* lam_prev_adj = nullptr;
     float* lamf_adj = nullptr;
@@ -352,6 +390,9 @@ struct dd_handle {
     std::vector<int64_t> row_ptr;
     std::vector<int32_t> col_loc, col_dof;
     std::vector<double> Tval, Sval;
+    std::vector<int64_t> mt_ptr;     // MFETI-DP2: interface tangential mass, CSR over multipliers
+    std::vector<int32_t> mt_col;
+    std::vector<double> mt_val;
     std::vector<MatDesc> mats;
     int64_t dense_elems = 0;
     int32_t ldc = 0;                 // leading dimension of K~cc
@@ -397,6 +438,8 @@ struct dd_handle {
     int cur_adj = 0;                 // mu[cur_adj] = mu^{k+1}, mu[(cur_adj+2)%3] = mu^{k+2}
     bool lam_valid = false;
     bool lam_adj_valid = false;
+    int factored_scheme = DD_SCHEME_DP1;   // scheme of the last dd_factor
+    double factored_alpha = 0.0;           // its Robin coefficient (DP2)
 
     // CUDA-graph mode (dd_params.use_graph): one executable graph per time-level phase
     void* gexec[3] = {nullptr, nullptr, nullptr};   // cudaGraphExec_t
@@ -492,17 +535,21 @@ size_t sym_smem_bytes(const dd_handle* h);
 
 // gmres.cu: coupled-system GMRES (u = [lambda; x_c])
 int launch_corner_diag(const dd_handle* h, void* stream);
-// wf: FP32 GEMV output (DD_MIXED) or null; zuf/lamf/xCf: FP32 shadows to write (DD_MIXED) or null
+// wf: FP32 GEMV output (DD_MIXED) or null; zuf: FP32 operator input to write (DD_MIXED) or null
 int launch_gm_init(const dd_handle* h, double tol, int max_it, int m, int adaptive, unsigned long long cond_outer,
                    void* stream);
-int launch_gm_start(const dd_handle* h, int have_q, const float* wf, unsigned long long cond_inner, void* stream);
-int launch_gm_normalize(const dd_handle* h, float* zuf, void* stream);
-int launch_gm_pass(const dd_handle* h, int phase, const float* wf, unsigned long long cond_inner, void* stream);
-int launch_gm_update(const dd_handle* h, float* lamf, float* xCf, unsigned long long cond_outer, void* stream);
-int launch_gm_combine(const dd_handle* h, double* out, void* stream);
+int launch_gm_start(const dd_handle* h, const UView& U, int have_q, const float* wf, unsigned long long cond_inner,
+                    void* stream);
+int launch_gm_normalize(const dd_handle* h, const UView& U, float* zuf, void* stream);
+int launch_gm_pass(const dd_handle* h, const UView& U, int phase, const float* wf, const float* zuf,
+                   unsigned long long cond_inner, void* stream);
+int launch_gm_update(const dd_handle* h, const UView& U, unsigned long long cond_outer, void* stream);
+int launch_gm_combine(const dd_handle* h, const UView& U, const double* in, double* out, void* stream);
+int launch_dp2_rhs(const dd_handle* h, const UView& U, void* stream);
+int launch_robin_add(const dd_handle* h, double alpha, void* stream);
 
 // GEMV x-source kinds (see kernels.cu)
 enum : int { X_FLAT = 0, X_LAMBDA = 1, X_PCG = 2, X_CORNER = 3, X_RECOVER = 4, X_COARSE = 5, X_PCG_CV = 6,
-             X_LAMBDA_CV = 7 };
+             X_LAMBDA_CV = 7, X_SIDE_CP = 8 };
 
 constexpr int kMaxProbes = 256;

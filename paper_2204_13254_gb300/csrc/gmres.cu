@@ -55,22 +55,56 @@ __device__ __forceinline__ double wv(const double* __restrict__ w, const float* 
     return wf ? (double)wf[slot] : w[slot];
 }
 
-// (M u)_i from the GEMV output per slot (w, or its FP32 form wf): jump over
-// multiplier i, or minus the assembly over the copies of corner i - n_lambda.
-__device__ __forceinline__ double combine(int64_t i, int64_t nl, const int64_t* __restrict__ ms,
-                                          const int64_t* __restrict__ cp, const int64_t* __restrict__ cs,
-                                          const double* __restrict__ w, const float* __restrict__ wf) {
-    if (i < nl) return wv(w, wf, ms[2 * i]) - wv(w, wf, ms[2 * i + 1]);
-    const int64_t c = i - nl;
+// Input of the operator in its two multiplier blocks (DP2 needs u1 + u2): FP32
+// (DD_MIXED operator input) or FP64.
+struct UIn {
+    const double* d1;
+    const double* d2;
+    const float* f1;
+    const float* f2;
+    __device__ __forceinline__ double sum(int64_t k) const {
+        return f1 ? (double)f1[k] + (double)f2[k] : d1[k] + d2[k];
+    }
+};
+
+// (M u)_i from the GEMV output per slot (w, or its FP32 form wf).
+// MFETI-DP1: jump over multiplier i; minus the assembly over the copies of a corner.
+// MFETI-DP2: u1_k + u2_k - 2 alpha (M_T t)_k with t the interface traces of the
+// other side (side 2 for block 1, side 1 for block 2); plus the assembly over
+// the copies of a corner (the multipliers enter the local problems with +).
+__device__ __forceinline__ double combine(int64_t i, const UView& U, const double* __restrict__ w,
+                                          const float* __restrict__ wf, const UIn& in) {
+    if (!U.mtp) {
+        if (i < U.n1) return wv(w, wf, U.ms[2 * i]) - wv(w, wf, U.ms[2 * i + 1]);
+        const int64_t c = i - U.n1;
+        double s = 0.0;
+        for (int64_t k = U.cp[c]; k < U.cp[c + 1]; ++k) s += wv(w, wf, U.cs[k]);
+        return -s;
+    }
+    if (i < U.n1 + U.n2) {
+        const bool first = i < U.n1;
+        const int64_t k = first ? i : i - U.n1;
+        const int other = first ? 1 : 0;
+        double acc = 0.0;
+        for (int64_t p = U.mtp[k]; p < U.mtp[k + 1]; ++p) acc += U.mtv[p] * wv(w, wf, U.ms[2 * (int64_t)U.mtc[p] + other]);
+        return in.sum(k) - U.two_alpha * acc;
+    }
+    const int64_t c = i - U.n1 - U.n2;
     double s = 0.0;
-    for (int64_t k = cp[c]; k < cp[c + 1]; ++k) s += wv(w, wf, cs[k]);
-    return -s;
+    for (int64_t k = U.cp[c]; k < U.cp[c + 1]; ++k) s += wv(w, wf, U.cs[k]);
+    return s;
 }
 
-__device__ __forceinline__ double dinv_at(int64_t i, int64_t nl, const double* __restrict__ dl,
-                                          const double* __restrict__ dc) {
-    if (i < nl) return dl ? dl[i] : 1.0;
-    return dc ? dc[i - nl] : 1.0;
+__device__ __forceinline__ double dinv_at(int64_t i, const UView& U) {
+    if (i < U.n1) return U.d1 ? U.d1[i] : 1.0;
+    if (i < U.n1 + U.n2) return 1.0;
+    return U.dc ? U.dc[i - U.n1 - U.n2] : 1.0;
+}
+
+__device__ __forceinline__ double b_at(int64_t i, const UView& U) {
+    if (i < U.n1) return U.b1[i];
+    if (i < U.n1 + U.n2) return U.b2[i - U.n1];
+    return U.bc[i - U.n1 - U.n2];
 }
 
 // Ticket of a multi-block reduction: every writer thread has fenced its partials
@@ -154,21 +188,18 @@ __global__ void k_gm_init(GmresScalars* gs, const PcgScalars* sc, double tol, do
 // is far above FP32 rounding -- GB300's FP64 rate would otherwise make the
 // Gram-Schmidt arithmetic a sizeable part of the step).
 template <typename VT>
-__global__ void __launch_bounds__(kT) k_gm_start(int64_t nl, int64_t nc, const int64_t* __restrict__ ms,
-                                                 const int64_t* __restrict__ cp, const int64_t* __restrict__ cs,
-                                                 const double* __restrict__ w, const float* __restrict__ wf,
-                                                 int have_q,
-                                                 const double* __restrict__ g, const double* __restrict__ fC,
-                                                 VT* __restrict__ tu, GmresScalars* gs, PcgScalars* sc,
+__global__ void __launch_bounds__(kT) k_gm_start(UView U, const double* __restrict__ w, const float* __restrict__ wf,
+                                                 int have_q, VT* __restrict__ tu, GmresScalars* gs, PcgScalars* sc,
                                                  double* __restrict__ partials, unsigned long long cond) {
-    const int64_t nu = nl + nc;
+    const int64_t nu = U.n1 + U.n2 + U.nc;
+    const UIn in{U.x1, U.n2 ? U.x2 : U.x1, nullptr, nullptr};
     double rr = 0.0, bb = 0.0;
 #pragma unroll
     for (int e = 0; e < kGmElems; ++e) {
         const int64_t i = (int64_t)blockIdx.x * kGmChunk + e * kT + threadIdx.x;
         if (i < nu) {
-            const double b = i < nl ? g[i] : fC[i - nl];
-            const VT r = (VT)(b - (have_q ? combine(i, nl, ms, cp, cs, w, wf) : 0.0));
+            const double b = b_at(i, U);
+            const VT r = (VT)(b - (have_q ? combine(i, U, w, wf, in) : 0.0));
             tu[i] = r;
             rr += (double)r * (double)r;
             bb += b * b;
@@ -219,22 +250,21 @@ __global__ void __launch_bounds__(kT) k_gm_start(int64_t nl, int64_t nc, const i
 // previous column, nh2 terms, none at a cycle start), z = D^-1 v_j: FP64 z for
 // the FP64 GEMV, FP32 z for the FP32 one
 template <typename VT>
-__global__ void k_gm_normalize(int64_t nl, int64_t nc, VT* __restrict__ V, int64_t ldv, const VT* __restrict__ tu,
-                               const double* __restrict__ dl, const double* __restrict__ dc, double* __restrict__ zu,
-                               float* __restrict__ zuf, const GmresScalars* gs) {
+__global__ void k_gm_normalize(UView U, VT* __restrict__ V, int64_t ldv, const VT* __restrict__ tu,
+                               double* __restrict__ zu, float* __restrict__ zuf, const GmresScalars* gs) {
     if (gs->skip) return;
     __shared__ VT coef[kM1];
     const int nh2 = gs->nh2;
     if (threadIdx.x < nh2) coef[threadIdx.x] = (VT)gs->h2[threadIdx.x];
     __syncthreads();
-    const int64_t nu = nl + nc;
+    const int64_t nu = U.n1 + U.n2 + U.nc;
     VT* vj = V + (int64_t)gs->j * ldv;
     const VT inv = (VT)(1.0 / gs->hnext);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nu; i += (int64_t)gridDim.x * blockDim.x) {
         VT t = tu[i];
         for (int k = 0; k < nh2; ++k) t -= coef[k] * V[(int64_t)k * ldv + i];
         const VT v = t * inv;
-        const VT z = (VT)dinv_at(i, nl, dl, dc) * v;
+        const VT z = (VT)dinv_at(i, U) * v;
         vj[i] = v;
         if (zu) zu[i] = (double)z;
         if (zuf) zuf[i] = (float)z;
@@ -249,10 +279,8 @@ __global__ void k_gm_normalize(int64_t nl, int64_t nc, VT* __restrict__ V, int64
 //            correction, applied to the vector by k_gm_normalize), then the
 //            Givens rotations and the end-of-cycle logic.
 template <int PHASE, typename VT>
-__global__ void __launch_bounds__(kT) k_gm_pass(int64_t nl, int64_t nc, const int64_t* __restrict__ ms,
-                                                const int64_t* __restrict__ cp, const int64_t* __restrict__ cs,
-                                                const double* __restrict__ w, const float* __restrict__ wf,
-                                                const VT* __restrict__ V, int64_t ldv,
+__global__ void __launch_bounds__(kT) k_gm_pass(UView U, const double* __restrict__ w, const float* __restrict__ wf,
+                                                UIn in, const VT* __restrict__ V, int64_t ldv,
                                                 VT* __restrict__ tu, GmresScalars* gs,
                                                 PcgScalars* sc, double* __restrict__ partials,
                                                 unsigned long long cond) {
@@ -260,7 +288,7 @@ __global__ void __launch_bounds__(kT) k_gm_pass(int64_t nl, int64_t nc, const in
     __shared__ VT coef[kM1];
     __shared__ double red[kM1 + 1][kWarps];
     __shared__ double tot[kM1 + 1];
-    const int64_t nu = nl + nc;
+    const int64_t nu = U.n1 + U.n2 + U.nc;
     const int j = gs->j;
     const int nv = j + 1;
     const int nsum = PHASE == 0 ? nv : nv + 1;   // PHASE 1 adds ||t1||^2 as sum nv
@@ -276,7 +304,7 @@ __global__ void __launch_bounds__(kT) k_gm_pass(int64_t nl, int64_t nc, const in
         if (i < nu) {
             VT v;
             if (PHASE == 0) {
-                v = (VT)combine(i, nl, ms, cp, cs, w, wf);
+                v = (VT)combine(i, U, w, wf, in);
             } else {
                 v = tu[i];
                 for (int k = 0; k < nv; ++k) v -= coef[k] * V[(int64_t)k * ldv + i];
@@ -377,29 +405,37 @@ __global__ void __launch_bounds__(kT) k_gm_pass(int64_t nl, int64_t nc, const in
 // End of a cycle: x += D^-1 V y (x = [lambda; x_c] in place); at the end of the
 // solve, publish its outcome in the CG scalars (step statistics, solve end).
 template <typename VT>
-__global__ void k_gm_update(int64_t nl, int64_t nc, const VT* __restrict__ V, int64_t ldv,
-                            const double* __restrict__ dl, const double* __restrict__ dc, double* __restrict__ lam,
-                            double* __restrict__ xC, float* __restrict__ lamf, float* __restrict__ xCf,
-                            const GmresScalars* gs, PcgScalars* sc, unsigned long long cond) {
+__global__ void k_gm_update(UView U, const VT* __restrict__ V, int64_t ldv, const GmresScalars* gs, PcgScalars* sc,
+                            unsigned long long cond) {
     __shared__ VT y[kMaxRestart];
     const int k = gs->k;
     if (threadIdx.x < k) y[threadIdx.x] = (VT)gs->y[threadIdx.x];
     __syncthreads();
-    const int64_t nu = nl + nc;
+    const int64_t nu = U.n1 + U.n2 + U.nc;
     if (k > 0) {
         for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nu; i += (int64_t)gridDim.x * blockDim.x) {
             VT vs = (VT)0;
             for (int q = 0; q < k; ++q) vs += y[q] * V[(int64_t)q * ldv + i];
-            const double v = (double)vs * dinv_at(i, nl, dl, dc);
-            if (i < nl) {
-                const double x = lam[i] + v;
-                lam[i] = x;
-                if (lamf) lamf[i] = (float)x;
+            const double v = (double)vs * dinv_at(i, U);
+            double* x;
+            float* xf;
+            int64_t o;
+            if (i < U.n1) {
+                x = U.x1;
+                xf = U.x1f;
+                o = i;
+            } else if (i < U.n1 + U.n2) {
+                x = U.x2;
+                xf = U.x2f;
+                o = i - U.n1;
             } else {
-                const double x = xC[i - nl] + v;
-                xC[i - nl] = x;
-                if (xCf) xCf[i - nl] = (float)x;
+                x = U.xc;
+                xf = U.xcf;
+                o = i - U.n1 - U.n2;
             }
+            const double nx = x[o] + v;
+            x[o] = nx;
+            if (xf) xf[o] = (float)nx;
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -414,10 +450,45 @@ __global__ void k_gm_update(int64_t nl, int64_t nc, const VT* __restrict__ V, in
     }
 }
 
-__global__ void k_gm_combine(int64_t nl, int64_t nc, const int64_t* __restrict__ ms, const int64_t* __restrict__ cp,
-                             const int64_t* __restrict__ cs, const double* __restrict__ w, double* __restrict__ out) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nl + nc; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = combine(i, nl, ms, cp, cs, w, nullptr);
+__global__ void k_gm_combine(UView U, const double* __restrict__ w, const double* __restrict__ in,
+                             double* __restrict__ out) {
+    const UIn ui{in, U.n2 ? in + U.n1 : in, nullptr, nullptr};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < U.n1 + U.n2 + U.nc;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = combine(i, U, w, nullptr, ui);
+}
+
+// MFETI-DP2 right-hand side of the multiplier blocks from y = (A+R)_rr^-1 b_r (per
+// slot): b1_k = 2 alpha (M_T t2)_k, b2_k = 2 alpha (M_T t1)_k (traces of the other side).
+__global__ void k_dp2_rhs(UView U, const double* __restrict__ y, double* __restrict__ b1, double* __restrict__ b2) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < U.n1; k += (int64_t)gridDim.x * blockDim.x) {
+        double a1 = 0.0, a2 = 0.0;
+        for (int64_t p = U.mtp[k]; p < U.mtp[k + 1]; ++p) {
+            const int64_t l = U.mtc[p];
+            a1 += U.mtv[p] * y[U.ms[2 * l + 1]];
+            a2 += U.mtv[p] * y[U.ms[2 * l]];
+        }
+        b1[k] = U.two_alpha * a1;
+        b2[k] = U.two_alpha * a2;
+    }
+}
+
+// MFETI-DP2 Robin term: M_s[i][j] += alpha (M_T)_kl at the slots of multipliers k, l
+// in each of their two subdomains (before the local elimination).  Every (k, l)
+// entry is distinct, so no two threads write the same matrix element.
+__global__ void k_robin_add(int64_t nl, const int64_t* __restrict__ mtp, const int32_t* __restrict__ mtc,
+                            const double* __restrict__ mtv, const int64_t* __restrict__ ms,
+                            const int32_t* __restrict__ slot_sub, const MatDesc* __restrict__ mats, double alpha,
+                            double* __restrict__ M) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nl; k += (int64_t)gridDim.x * blockDim.x)
+        for (int64_t p = mtp[k]; p < mtp[k + 1]; ++p) {
+            const int64_t l = mtc[p];
+            for (int side = 0; side < 2; ++side) {
+                const int64_t sk = ms[2 * k + side], sl = ms[2 * l + side];
+                const MatDesc md = mats[slot_sub[sk]];
+                M[md.moff + (sk - md.voff) * md.ld + (sl - md.voff)] += alpha * mtv[p];
+            }
+        }
 }
 
 int vec_blocks(int64_t n) {
@@ -442,76 +513,78 @@ int launch_gm_init(const dd_handle* h, double tol, int max_it, int m, int adapti
     return (int)cudaGetLastError();
 }
 
-int launch_gm_start(const dd_handle* h, int have_q, const float* wf, unsigned long long cond_inner, void* stream) {
-    const int64_t nl = (int64_t)h->mult_dof.size(), nc = (int64_t)h->corner_dof.size();
+int launch_gm_start(const dd_handle* h, const UView& U, int have_q, const float* wf, unsigned long long cond_inner,
+                    void* stream) {
     if (wf)
-        k_gm_start<float><<<h->gm_blocks, kT, 0, S(stream)>>>(
-            nl, nc, h->d.mult_slot, h->d.corner_ptr, h->d.corner_slot, h->d.w, wf, have_q, h->d.g, h->d.fC,
-            reinterpret_cast<float*>(h->d.tu), h->d.gs, h->d.sc, h->d.gpart, cond_inner);
+        k_gm_start<float><<<h->gm_blocks, kT, 0, S(stream)>>>(U, h->d.w, wf, have_q, reinterpret_cast<float*>(h->d.tu),
+                                                              h->d.gs, h->d.sc, h->d.gpart, cond_inner);
     else
-        k_gm_start<double><<<h->gm_blocks, kT, 0, S(stream)>>>(nl, nc, h->d.mult_slot, h->d.corner_ptr,
-                                                               h->d.corner_slot, h->d.w, nullptr, have_q, h->d.g,
-                                                               h->d.fC, h->d.tu, h->d.gs, h->d.sc, h->d.gpart,
-                                                               cond_inner);
+        k_gm_start<double><<<h->gm_blocks, kT, 0, S(stream)>>>(U, h->d.w, nullptr, have_q, h->d.tu, h->d.gs, h->d.sc,
+                                                               h->d.gpart, cond_inner);
     return (int)cudaGetLastError();
 }
 
-int launch_gm_normalize(const dd_handle* h, float* zuf, void* stream) {
-    const int64_t nl = (int64_t)h->mult_dof.size(), nc = (int64_t)h->corner_dof.size();
-    const bool pc = h->prm.precond != 0;
-    const double* dl = pc ? h->d.dinv : nullptr;
-    const double* dc = pc ? h->d.dinvC : nullptr;
+int launch_gm_normalize(const dd_handle* h, const UView& U, float* zuf, void* stream) {
+    const int64_t nu = U.n1 + U.n2 + U.nc;
     if (zuf)
-        k_gm_normalize<float><<<vec_blocks(nl + nc), kT, 0, S(stream)>>>(
-            nl, nc, reinterpret_cast<float*>(h->d.Vk), h->gm_ldv, reinterpret_cast<const float*>(h->d.tu), dl, dc,
-            nullptr, zuf, h->d.gs);
+        k_gm_normalize<float><<<vec_blocks(nu), kT, 0, S(stream)>>>(U, reinterpret_cast<float*>(h->d.Vk), h->gm_ldv,
+                                                                   reinterpret_cast<const float*>(h->d.tu), nullptr,
+                                                                   zuf, h->d.gs);
     else
-        k_gm_normalize<double><<<vec_blocks(nl + nc), kT, 0, S(stream)>>>(nl, nc, h->d.Vk, h->gm_ldv, h->d.tu, dl, dc,
-                                                                           h->d.zu, nullptr, h->d.gs);
+        k_gm_normalize<double><<<vec_blocks(nu), kT, 0, S(stream)>>>(U, h->d.Vk, h->gm_ldv, h->d.tu, h->d.zu, nullptr,
+                                                                    h->d.gs);
     return (int)cudaGetLastError();
 }
 
 template <int PHASE, typename VT>
-void run_pass(const dd_handle* h, const float* wf, unsigned long long cond, cudaStream_t st) {
-    const int64_t nl = (int64_t)h->mult_dof.size(), nc = (int64_t)h->corner_dof.size();
+void run_pass(const dd_handle* h, const UView& U, const float* wf, const float* zuf, unsigned long long cond,
+              cudaStream_t st) {
     const DevPtrs& d = h->d;
-    k_gm_pass<PHASE, VT><<<h->gm_blocks, kT, 0, st>>>(nl, nc, d.mult_slot, d.corner_ptr, d.corner_slot, d.w, wf,
-                                                      reinterpret_cast<const VT*>(d.Vk), h->gm_ldv,
+    const UIn in{d.zu, U.n2 ? d.zu + U.n1 : d.zu, zuf, (zuf && U.n2) ? zuf + U.n1 : zuf};
+    k_gm_pass<PHASE, VT><<<h->gm_blocks, kT, 0, st>>>(U, d.w, wf, in, reinterpret_cast<const VT*>(d.Vk), h->gm_ldv,
                                                       reinterpret_cast<VT*>(d.tu), d.gs, d.sc, d.gpart, cond);
 }
 
-int launch_gm_pass(const dd_handle* h, int phase, const float* wf, unsigned long long cond_inner, void* stream) {
+int launch_gm_pass(const dd_handle* h, const UView& U, int phase, const float* wf, const float* zuf,
+                   unsigned long long cond_inner, void* stream) {
     const cudaStream_t st = S(stream);
     if (wf) {
-        if (phase == 0) run_pass<0, float>(h, wf, 0ull, st);
-        else run_pass<1, float>(h, wf, cond_inner, st);
+        if (phase == 0) run_pass<0, float>(h, U, wf, zuf, 0ull, st);
+        else run_pass<1, float>(h, U, wf, zuf, cond_inner, st);
     } else {
-        if (phase == 0) run_pass<0, double>(h, nullptr, 0ull, st);
-        else run_pass<1, double>(h, nullptr, cond_inner, st);
+        if (phase == 0) run_pass<0, double>(h, U, nullptr, nullptr, 0ull, st);
+        else run_pass<1, double>(h, U, nullptr, nullptr, cond_inner, st);
     }
     return (int)cudaGetLastError();
 }
 
-int launch_gm_update(const dd_handle* h, float* lamf, float* xCf, unsigned long long cond_outer, void* stream) {
-    const int64_t nl = (int64_t)h->mult_dof.size(), nc = (int64_t)h->corner_dof.size();
-    const bool pc = h->prm.precond != 0;
-    const double* dl = pc ? h->d.dinv : nullptr;
-    const double* dc = pc ? h->d.dinvC : nullptr;
-    if (lamf)
-        k_gm_update<float><<<vec_blocks(nl + nc), kT, 0, S(stream)>>>(
-            nl, nc, reinterpret_cast<const float*>(h->d.Vk), h->gm_ldv, dl, dc, h->d.lam, h->d.xC, lamf, xCf, h->d.gs,
-            h->d.sc, cond_outer);
+int launch_gm_update(const dd_handle* h, const UView& U, unsigned long long cond_outer, void* stream) {
+    const int64_t nu = U.n1 + U.n2 + U.nc;
+    if (U.x1f || U.xcf)
+        k_gm_update<float><<<vec_blocks(nu), kT, 0, S(stream)>>>(U, reinterpret_cast<const float*>(h->d.Vk), h->gm_ldv,
+                                                                h->d.gs, h->d.sc, cond_outer);
     else
-        k_gm_update<double><<<vec_blocks(nl + nc), kT, 0, S(stream)>>>(nl, nc, h->d.Vk, h->gm_ldv, dl, dc, h->d.lam,
-                                                                        h->d.xC, nullptr, nullptr, h->d.gs, h->d.sc,
-                                                                        cond_outer);
+        k_gm_update<double><<<vec_blocks(nu), kT, 0, S(stream)>>>(U, h->d.Vk, h->gm_ldv, h->d.gs, h->d.sc, cond_outer);
     return (int)cudaGetLastError();
 }
 
-int launch_gm_combine(const dd_handle* h, double* out, void* stream) {
-    const int64_t nl = (int64_t)h->mult_dof.size(), nc = (int64_t)h->corner_dof.size();
-    if (nl + nc == 0) return 0;
-    k_gm_combine<<<vec_blocks(nl + nc), kT, 0, S(stream)>>>(nl, nc, h->d.mult_slot, h->d.corner_ptr, h->d.corner_slot,
-                                                             h->d.w, out);
+int launch_gm_combine(const dd_handle* h, const UView& U, const double* in, double* out, void* stream) {
+    const int64_t nu = U.n1 + U.n2 + U.nc;
+    if (nu == 0) return 0;
+    k_gm_combine<<<vec_blocks(nu), kT, 0, S(stream)>>>(U, h->d.w, in, out);
+    return (int)cudaGetLastError();
+}
+
+int launch_dp2_rhs(const dd_handle* h, const UView& U, void* stream) {
+    if (U.n1 == 0) return 0;
+    k_dp2_rhs<<<vec_blocks(U.n1), kT, 0, S(stream)>>>(U, h->d.y, h->d.g, h->d.g2);
+    return (int)cudaGetLastError();
+}
+
+int launch_robin_add(const dd_handle* h, double alpha, void* stream) {
+    const int64_t nl = (int64_t)h->mult_dof.size();
+    if (nl == 0) return 0;
+    k_robin_add<<<vec_blocks(nl), kT, 0, S(stream)>>>(nl, h->d.mt_ptr, h->d.mt_col, h->d.mt_val, h->d.mult_slot,
+                                                     h->d.slot_sub, h->d.mats, alpha, h->d.M64);
     return (int)cudaGetLastError();
 }

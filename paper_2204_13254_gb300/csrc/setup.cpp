@@ -26,6 +26,41 @@ inline void cross3(const double* a, const double* b, double* c) {
 }
 inline double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
 
+// Tangential Whitney mass of a triangle (nodes p[0..2], ids increasing) over its
+// edges (0,1), (1,2), (0,2), each oriented low -> high: the tangential trace of
+// a 3-D Whitney function is the 2-D one l_a g_b - l_b g_a (g: surface gradients
+// of the triangle's barycentrics, g_k = sum_j (G^-1)_kj E_j with E_j = p_j - p_0,
+// G the 2x2 metric), integrated with int l_a l_c = area (1 + delta_ac) / 12.
+void face_mass(const double* p0, const double* p1, const double* p2, double M[9]) {
+    double E1[3], E2[3];
+    for (int c = 0; c < 3; ++c) {
+        E1[c] = p1[c] - p0[c];
+        E2[c] = p2[c] - p0[c];
+    }
+    const double g11 = dot3(E1, E1), g12 = dot3(E1, E2), g22 = dot3(E2, E2);
+    const double det = g11 * g22 - g12 * g12;
+    const double i11 = g22 / det, i12 = -g12 / det, i22 = g11 / det;
+    double g[3][3];
+    for (int c = 0; c < 3; ++c) {
+        g[1][c] = i11 * E1[c] + i12 * E2[c];
+        g[2][c] = i12 * E1[c] + i22 * E2[c];
+        g[0][c] = -g[1][c] - g[2][c];
+    }
+    const double area = 0.5 * std::sqrt(det);
+    double gg[3][3], ll[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            gg[a][b] = dot3(g[a], g[b]);
+            ll[a][b] = area * (a == b ? 2.0 : 1.0) / 12.0;
+        }
+    const int fe[3][2] = {{0, 1}, {1, 2}, {0, 2}};
+    for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q) {
+            const int a = fe[p][0], b = fe[p][1], c = fe[q][0], d = fe[q][1];
+            M[3 * p + q] = ll[a][c] * gg[b][d] - ll[a][d] * gg[b][c] - ll[b][c] * gg[a][d] + ll[b][d] * gg[a][c];
+        }
+}
+
 // Barycentric gradients g[4][3] and |volume| of a tet.  With d_i = X_i - X_0 and
 // det = d1 . (d2 x d3): grad l1 = d2 x d3 / det, grad l2 = d3 x d1 / det,
 // grad l3 = d1 x d2 / det, grad l0 = -(sum).  Returns the signed det.
@@ -370,6 +405,62 @@ int dd_build_host(dd_handle* h, const dd_mesh* mesh, const int32_t* part, int32_
     for (int64_t i = 0; i < n_local; ++i) h->row_ptr[i + 1] += h->row_ptr[i];
     h->dense_elems = moff;
     h->ldc = (int32_t)((nc + 3) / 4 * 4);
+
+    // ---- interface tangential mass on the multiplier edges (MFETI-DP2) ---------
+    // faces shared by tets of two subdomains; CSR over multipliers (block diagonal
+    // by subdomain pair: the edges of such a face join exactly that pair)
+    {
+        struct FaceOwner {
+            int64_t a, b, c;
+            int32_t s;
+            bool operator<(const FaceOwner& o) const {
+                return a != o.a ? a < o.a : (b != o.b ? b < o.b : (c != o.c ? c < o.c : s < o.s));
+            }
+        };
+        std::vector<FaceOwner> fo(4 * T);
+        for (int64_t t = 0; t < T; ++t)
+            for (int f = 0; f < 4; ++f) {
+                int64_t v[3] = {h->tets[4 * t + kFace[f][0]], h->tets[4 * t + kFace[f][1]], h->tets[4 * t + kFace[f][2]]};
+                std::sort(v, v + 3);
+                fo[4 * t + f] = {v[0], v[1], v[2], h->part[t]};
+            }
+        std::sort(fo.begin(), fo.end());
+        struct MT {
+            int64_t k, l;
+            double v;
+        };
+        std::vector<MT> mt;
+        for (size_t i = 0; i + 1 < fo.size(); ++i) {
+            const FaceOwner& x = fo[i];
+            const FaceOwner& y = fo[i + 1];
+            if (x.a != y.a || x.b != y.b || x.c != y.c || x.s == y.s) continue;
+            const int64_t ev[3] = {edge_id(x.a, x.b), edge_id(x.b, x.c), edge_id(x.a, x.c)};
+            int64_t mk[3];
+            for (int e = 0; e < 3; ++e) {
+                const int64_t d = edge_dof[ev[e]];
+                mk[e] = d >= 0 ? mult_idx[d] : -1;
+            }
+            double M[9];
+            face_mass(&h->xyz[3 * x.a], &h->xyz[3 * x.b], &h->xyz[3 * x.c], M);
+            for (int p = 0; p < 3; ++p)
+                for (int q = 0; q < 3; ++q)
+                    if (mk[p] >= 0 && mk[q] >= 0) mt.push_back({mk[p], mk[q], M[3 * p + q]});
+        }
+        std::sort(mt.begin(), mt.end(), [](const MT& u, const MT& v) { return u.k != v.k ? u.k < v.k : u.l < v.l; });
+        h->mt_ptr.assign(nl + 1, 0);
+        h->mt_col.clear();
+        h->mt_val.clear();
+        for (size_t i = 0; i < mt.size();) {
+            size_t j = i;
+            double v = 0.0;
+            while (j < mt.size() && mt[j].k == mt[i].k && mt[j].l == mt[i].l) v += mt[j++].v;
+            h->mt_col.push_back((int32_t)mt[i].l);
+            h->mt_val.push_back(v);
+            ++h->mt_ptr[mt[i].k + 1];
+            i = j;
+        }
+        for (int64_t k = 0; k < nl; ++k) h->mt_ptr[k + 1] += h->mt_ptr[k];
+    }
 
     build_sym(h);
     h->sym_ok = sym_smem_bytes(h) <= 227 * 1024;

@@ -58,6 +58,8 @@ extern "C" int dd_schur_apply_static(dd_handle* h, const double* lam, double* ou
                                        " scratch doubles (local unknowns + 2 x corners, each rounded up to 32); the "
                                        "static limit is " + std::to_string(kStaticScratchDoubles));
     if (!h->factored) return h->fail(DD_ERR_STATE, "dd_schur_apply_static before dd_factor");
+    if (h->factored_scheme != DD_SCHEME_DP1)
+        return h->fail(DD_ERR_STATE, "dd_schur_apply_static needs the DP1 factorisation");
     if (h->mult_dof.empty()) return DD_OK;
     int dev = 0;
     cudaError_t rc = cudaGetDevice(&dev);

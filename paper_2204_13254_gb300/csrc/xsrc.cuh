@@ -45,6 +45,14 @@ __device__ __forceinline__ double xsrc_value(const XSrc& xs, int64_t slot, int64
             }
             return m > 0 ? xs.v[m - 1] : -xs.v[-m - 1];
         }
+        case X_SIDE_CP: {
+            const int m = xs.slot_mult[slot];
+            if (m == 0) {
+                const int c = xs.slot_corner[slot];
+                return c >= 0 ? xs.v3[c] : 0.0;
+            }
+            return m > 0 ? xs.v[m - 1] : xs.v2[-m - 1];
+        }
         default: return xs.v[j];
     }
 }
@@ -89,6 +97,14 @@ __device__ __forceinline__ float xsrc_value_f(const XSrc& xs, int64_t slot, int6
                 return c >= 0 ? -xs.v3f[c] : 0.0f;
             }
             return m > 0 ? xs.vf[m - 1] : -xs.vf[-m - 1];
+        }
+        case X_SIDE_CP: {
+            const int m = xs.slot_mult[slot];
+            if (m == 0) {
+                const int c = xs.slot_corner[slot];
+                return c >= 0 ? xs.v3f[c] : 0.0f;
+            }
+            return m > 0 ? xs.vf[m - 1] : xs.v2f[-m - 1];
         }
         default: return xs.vf[j];
     }

@@ -20,9 +20,11 @@ DD_ERR_NO_CONVERGENCE, DD_ERR_NONFINITE, DD_ERR_TIMEOUT, DD_ERR_CUDA, DD_ERR_STA
 DD_FP64, DD_MIXED = 0, 1
 DD_SOLVER_SCHUR_CG, DD_SOLVER_COUPLED_GMRES = 0, 1
 DD_MAX_RESTART = 32
+DD_SCHEME_DP1, DD_SCHEME_DP2 = 0, 1
 
 SYMBOLS = ["dd_setup", "dd_set_params", "dd_get_sizes", "dd_get_maps", "dd_set_probes", "dd_bind_workspace",
-           "dd_factor", "dd_step", "dd_schur_apply", "dd_schur_apply_static", "dd_coupled_apply", "dd_probe", "dd_adjoint_reset",
+           "dd_factor", "dd_step", "dd_schur_apply", "dd_schur_apply_static", "dd_coupled_apply", "dd_dp2_apply",
+           "dd_get_interface_mass", "dd_probe", "dd_adjoint_reset",
            "dd_adjoint_step", "dd_probe_seed", "dd_autotune", "dd_get_tiles", "dd_get_sym_config", "dd_set_beam",
            "dd_pic_step",
            "dd_pic_state", "dd_get_state", "dd_set_state", "dd_profile",
@@ -39,7 +41,8 @@ class dd_mesh(C.Structure):
 class dd_params(C.Structure):
     _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("max_it", C.c_int), ("precond", C.c_int),
                 ("warm_start", C.c_int), ("refine_tol", C.c_double), ("max_refine", C.c_int), ("chunk", C.c_int),
-                ("use_graph", C.c_int), ("solver", C.c_int), ("restart", C.c_int), ("sym_fp32", C.c_int)]
+                ("use_graph", C.c_int), ("solver", C.c_int), ("restart", C.c_int), ("sym_fp32", C.c_int),
+                ("scheme", C.c_int), ("robin_alpha", C.c_double)]
 
 
 class dd_sizes(C.Structure):
@@ -86,6 +89,8 @@ def load_library(path: str = LIB_PATH):
         "dd_schur_apply": (C.c_int, [vp, vp, vp, vp]),
         "dd_schur_apply_static": (C.c_int, [vp, vp, vp, vp]),
         "dd_coupled_apply": (C.c_int, [vp, vp, vp, vp]),
+        "dd_dp2_apply": (C.c_int, [vp, vp, vp, vp]),
+        "dd_get_interface_mass": (C.c_int, [vp, C.POINTER(i64), vp, vp, vp]),
         "dd_probe": (C.c_int, [vp, vp, vp]),
         "dd_get_state": (C.c_int, [vp, vp, vp, C.POINTER(i64), vp]),
         "dd_set_state": (C.c_int, [vp, vp, vp, i64, vp]),
@@ -136,9 +141,10 @@ def _stream(stream=None):
 
 
 def make_params(precision=DD_FP64, tol=1e-12, max_it=500, precond=1, warm_start=1, refine_tol=1e-12, max_refine=4,
-                chunk=8, use_graph=0, solver=DD_SOLVER_SCHUR_CG, restart=20, sym_fp32=1):
+                chunk=8, use_graph=0, solver=DD_SOLVER_SCHUR_CG, restart=20, sym_fp32=1, scheme=DD_SCHEME_DP1,
+                robin_alpha=0.0):
     return dd_params(precision, tol, max_it, precond, warm_start, refine_tol, max_refine, chunk, use_graph, solver,
-                     restart, sym_fp32)
+                     restart, sym_fp32, scheme, robin_alpha)
 
 
 # ---- C-ABI-named wrappers ------------------------------------------------------
@@ -222,6 +228,23 @@ def dd_schur_apply_static(h, lam, out, stream=None):
 def dd_coupled_apply(h, u, out, stream=None):
     """out = [F_rr u_l + F_rc u_c ; -F_rc^T u_l + K~cc u_c] (Eqs. F1lr + F1uc), u = [u_l; u_c]."""
     _check(h, lib().dd_coupled_apply(h, _ptr(u), _ptr(out), _stream(stream)))
+
+
+def dd_dp2_apply(h, u, out, stream=None):
+    """out = DP2 coupled operator (Eqs. f2imp1 + F2un) applied to u = [l1; l2; x_c]."""
+    _check(h, lib().dd_dp2_apply(h, _ptr(u), _ptr(out), _stream(stream)))
+
+
+def dd_get_interface_mass(h):
+    """Host CSR (ptr, col, val) of the interface tangential mass on the multiplier edges."""
+    nnz = C.c_int64()
+    _check(h, lib().dd_get_interface_mass(h, C.byref(nnz), None, None, None))
+    s = dd_get_sizes(h)
+    ptr = np.zeros(s.n_lambda + 1, np.int64)
+    col = np.zeros(max(nnz.value, 1), np.int32)
+    val = np.zeros(max(nnz.value, 1), np.float64)
+    _check(h, lib().dd_get_interface_mass(h, C.byref(nnz), ptr.ctypes.data, col.ctypes.data, val.ctypes.data))
+    return ptr, col[:nnz.value], val[:nnz.value]
 
 
 def dd_probe(h, out, stream=None):
