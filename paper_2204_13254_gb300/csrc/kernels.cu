@@ -338,20 +338,32 @@ __global__ void k_rhs(int64_t n_local, const int64_t* __restrict__ row_ptr, cons
 
 // b <- b - A^(s) delta|_s (subassembled FP64 residual of the step system) and
 // the assembled residual norm: res[d] = sum over copies of the new b.
+// b -= A delta per slot row (local CSR, ~15 entries a row): 4 lanes per row, 8 rows
+// per warp, every lane's loads issued before its adds (streaming loads of the
+// matrix, delta gathered through L1/L2).
 __global__ void k_residual_local(int64_t n_local, const int64_t* __restrict__ row_ptr,
                                  const int32_t* __restrict__ col_dof, const double* __restrict__ A,
                                  const double* __restrict__ delta, double* __restrict__ b) {
-    const int lane8 = threadIdx.x & 7;
+    const int lane4 = threadIdx.x & 3;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t w0 = warp * 4; w0 < n_local; w0 += nwarp * 4) {
-        const int64_t i = w0 + ((threadIdx.x & 31) >> 3);
+    for (int64_t w0 = warp * 8; w0 < n_local; w0 += nwarp * 8) {
+        const int64_t i = w0 + ((threadIdx.x & 31) >> 2);
         double s = 0.0;
-        if (i < n_local)
-            for (int64_t k = row_ptr[i] + lane8; k < row_ptr[i + 1]; k += 8) s += A[k] * delta[col_dof[k]];
-#pragma unroll
-        for (int o = 4; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, 8);
-        if (lane8 == 0 && i < n_local) b[i] -= s;
+        if (i < n_local) {
+            const int64_t k1 = row_ptr[i + 1];
+            int64_t k = row_ptr[i] + lane4;
+            for (; k + 12 < k1; k += 16) {
+                const double a0 = __ldcs(A + k), a1 = __ldcs(A + k + 4), a2 = __ldcs(A + k + 8), a3 = __ldcs(A + k + 12);
+                const int32_t c0 = __ldcs(col_dof + k), c1 = __ldcs(col_dof + k + 4), c2 = __ldcs(col_dof + k + 8),
+                              c3 = __ldcs(col_dof + k + 12);
+                s += a0 * delta[c0] + a1 * delta[c1] + a2 * delta[c2] + a3 * delta[c3];
+            }
+            for (; k < k1; k += 4) s += __ldcs(A + k) * delta[__ldcs(col_dof + k)];
+        }
+        s += __shfl_xor_sync(0xffffffffu, s, 2, 4);
+        s += __shfl_xor_sync(0xffffffffu, s, 1, 4);
+        if (lane4 == 0 && i < n_local) b[i] -= s;
     }
 }
 
@@ -1049,7 +1061,7 @@ int launch_rhs(const dd_handle* h, const double* e_n, const double* src, double 
 
 int launch_residual_local(const dd_handle* h, void* stream) {
     const int64_t nl = h->sub_ptr.back();
-    const int blocks = (int)std::min<int64_t>((nl * 8 + kThreads - 1) / kThreads, 152 * 16);
+    const int blocks = (int)std::min<int64_t>((nl * 4 + kThreads - 1) / kThreads, 152 * 16);
     k_residual_local<<<blocks, kThreads, 0, S(stream)>>>(nl, h->d.row_ptr, h->d.col_dof, h->d.Aval, h->d.delta_k,
                                                          h->d.b);
     return (int)cudaGetLastError();

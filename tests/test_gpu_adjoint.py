@@ -39,7 +39,7 @@ def gpu_grad(eps, amp, prob, steps, checkpoint=100):
     a = torch.tensor(amp, dtype=torch.float64, requires_grad=True)
     J = A.probe_objective(e, a, prob, steps, checkpoint)
     J.backward()
-    return float(J), e.grad.cpu().numpy(), float(a.grad)
+    return float(J.detach()), e.grad.cpu().numpy(), float(a.grad)
 
 
 def test_adjoint_matches_oracle_adjoint():
