@@ -236,7 +236,7 @@ def run_ours(args, rank, world, local):
     if not args.no_autotune:
         t_tune = D.dd_autotune(fs.h, args.tune_cache)
         tiles = D.dd_get_tiles(fs.h)
-        tiles["packed_fp32 (CTAs per subdomain, ring depth, subdomains kept in L2)"] = D.dd_get_sym_config(fs.h)
+        tiles["packed_fp32 (CTAs per subdomain, ring depth, subdomains kept in L2, warp-specialised)"] = D.dd_get_sym_config(fs.h)
     n = fs.n_dof
     dofs = torch.tensor(fs.dof_of_pairs(w.source_pairs), device=dev)
     d2g = w.d2G(dt, Wu + K)

@@ -222,7 +222,10 @@ size_t dd_workspace_layout(dd_handle* h, bool assign) {
     L.take(d.symd, (size_t)h->n_sub);
     for (int m = 0; m < GEMV_NMODES; ++m) {
         int rm, cm;
-        if (sym_masks(m, &rm, &cm)) L.take(d.sym_rng[m], (size_t)h->n_sub * kSymCLMax * 2);
+        if (sym_masks(m, &rm, &cm)) {
+            L.take(d.sym_rng[m], (size_t)h->n_sub * kSymCLMax * 3);
+            L.take(d.sym_tl[m], std::max<size_t>(1, h->sym_tl[m].size()));
+        }
     }
     L.take(d.K64, nc * (size_t)h->ldc);
     L.take(d.K32, nc * (size_t)h->ldc);
@@ -949,8 +952,10 @@ int dd_bind_workspace(dd_handle* h, void* dev, size_t bytes, void* stream) {
     CK(h, upload(h->d.mt_ptr, h->mt_ptr, s), "upload");
     CK(h, upload(h->d.mt_col, h->mt_col, s), "upload");
     CK(h, upload(h->d.mt_val, h->mt_val, s), "upload");
-    for (int m = 0; m < GEMV_NMODES; ++m)
+    for (int m = 0; m < GEMV_NMODES; ++m) {
         if (!h->sym_rng[m].empty()) CK(h, upload(h->d.sym_rng[m], h->sym_rng[m], s), "upload");
+        if (!h->sym_tl[m].empty()) CK(h, upload(h->d.sym_tl[m], h->sym_tl[m], s), "upload");
+    }
     CK(h, upload(h->d.Sval, h->Sval, s), "upload");
     for (int p = 0; p < 2; ++p)
         for (int m = 0; m < GEMV_NMODES; ++m) {
@@ -1669,10 +1674,10 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
         if (c == ' ' || c == '\t') c = '_';
     std::map<std::pair<int, int>, TileCfg> found;
     struct SymCfg {
-        int cl, st, keep;
+        int cl, st, keep, ws;
     };
     std::map<int, SymCfg> found_cl;   // packed symmetric modes: CTAs per subdomain, ring depth, subdomains kept
-                                      // in L2; cache lines "key 2 mode cl st keep"
+                                      // in L2, kernel form; cache lines "key 2 mode cl st keep ws"
     int n_sym = 0;
     for (int m = 0; m < GEMV_NMODES; ++m) {
         int rm, cm;
@@ -1688,10 +1693,10 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
             if (!(is >> k >> p >> m >> lpr >> rows) || k != key || m < 0 || m >= GEMV_NMODES) continue;
             if (p >= 0 && p < 2 && (lpr == 8 || lpr == 16 || lpr == 32) && rows >= kMinRowsPerTask)
                 found[{p, m}] = TileCfg{lpr, rows};
-            int keep = 0;
+            int keep = 0, ws = 0;
             if (p == 2 && sym_masks(m, &rm, &cm) && (lpr == 1 || lpr == 2 || lpr == 4 || lpr == 8) && rows >= 2 &&
-                rows <= kSymStages && (is >> keep) && keep >= 0 && keep <= h->n_sub)
-                found_cl[m] = SymCfg{lpr, rows, keep};
+                rows <= kSymStages && (is >> keep >> ws) && keep >= 0 && keep <= h->n_sub && (ws == 0 || ws == 1))
+                found_cl[m] = SymCfg{lpr, rows, keep, ws};
         }
     }
     const bool cached = found.size() == (size_t)(2 * GEMV_NMODES) && found_cl.size() == (size_t)n_sym;
@@ -1715,7 +1720,8 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
                 int rm, cm;
                 const bool sym_saved = h->prm.sym_fp32 != 0;
                 if (p == 1 && h->sym_ok && sym_masks(m, &rm, &cm)) {
-                    // packed symmetric tiles: time 1, 2, 4 and 8 CTAs per subdomain with rings of 2, 3 and 4 tiles
+                    // packed symmetric tiles: time both kernel forms with 1, 2, 4 and 8 CTAs per subdomain and
+                    // rings of 2, 3 and 4 tiles
                     h->prm.sym_fp32 = 1;
                     XSrc xs{};
                     xs.kind = X_FLAT;
@@ -1725,21 +1731,24 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
                     // then, for the kinds a Krylov solve repeats, how many subdomains' tiles to keep in
                     // L2 (evict_last) across launches: 0, 32, 64 or 96 MB worth
                     float best = 1e30f;
-                    SymCfg bcl{h->sym_cl[m], h->sym_st[m], 0};
+                    SymCfg bcl{h->sym_cl[m], h->sym_st[m], 0, 0};
                     const bool repeated = m != GEMV_LOCAL;
                     const double per_sub = h->mode_bytes_sym[m] / std::max(1, h->n_sub);
-                    for (int cand = 0; cand < 12 + (repeated ? 3 : 0) && !rc; ++cand) {
-                        int cl, st, keep = 0;
-                        if (cand < 12) {
-                            cl = 1 << (cand / 3);
+                    for (int cand = 0; cand < 24 + (repeated ? 3 : 0) && !rc; ++cand) {
+                        int cl, st, keep = 0, ws;
+                        if (cand < 24) {
+                            ws = cand / 12;
+                            cl = 1 << ((cand % 12) / 3);
                             st = 2 + cand % 3;
                         } else {
                             cl = bcl.cl;
                             st = bcl.st;
-                            keep = std::min(h->n_sub, (int)((cand - 11) * 32.0e6 / std::max(1.0, per_sub)));
+                            ws = bcl.ws;
+                            keep = std::min(h->n_sub, (int)((cand - 23) * 32.0e6 / std::max(1.0, per_sub)));
                         }
                         h->sym_st[m] = st;
                         h->sym_keep[m] = keep;
+                        h->sym_ws[m] = ws;
                         sym_ranges(h, m, cl);
                         rc = upload(h->d.sym_rng[m], h->sym_rng[m], s);
                         for (int it = 0; it < 4 && !rc; ++it) {
@@ -1755,7 +1764,7 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
                         if (rc) break;
                         if (ms < best) {
                             best = ms;
-                            bcl = SymCfg{cl, st, keep};
+                            bcl = SymCfg{cl, st, keep, ws};
                         }
                     }
                     found_cl[m] = bcl;
@@ -1815,7 +1824,7 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
                   << kv.second.rows << "\n";
             for (const auto& kv : found_cl)
                 f << key << "\t2\t" << kv.first << "\t" << kv.second.cl << "\t" << kv.second.st << "\t"
-                  << kv.second.keep << "\n";
+                  << kv.second.keep << "\t" << kv.second.ws << "\n";
         }
     }
     cudaEventDestroy(e0);
@@ -1831,6 +1840,7 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
     for (const auto& kv : found_cl) {
         h->sym_st[kv.first] = kv.second.st;
         h->sym_keep[kv.first] = kv.second.keep;
+        h->sym_ws[kv.first] = kv.second.ws;
         sym_ranges(h, kv.first, kv.second.cl);
         CK(h, upload(h->d.sym_rng[kv.first], h->sym_rng[kv.first], s), "upload ranges");
     }
@@ -1852,7 +1862,7 @@ int dd_get_tiles(const dd_handle* h, int32_t* lpr, int32_t* rows) {
     return DD_OK;
 }
 
-int dd_get_sym_config(const dd_handle* h, int32_t* cl, int32_t* st, int32_t* keep) {
+int dd_get_sym_config(const dd_handle* h, int32_t* cl, int32_t* st, int32_t* keep, int32_t* ws) {
     if (!h) return DD_ERR_ARG;
     for (int m = 0; m < GEMV_NMODES; ++m) {
         int rm, cmk;
@@ -1860,7 +1870,29 @@ int dd_get_sym_config(const dd_handle* h, int32_t* cl, int32_t* st, int32_t* kee
         if (cl) cl[m] = on ? h->sym_cl[m] : 0;
         if (st) st[m] = on ? h->sym_st[m] : 0;
         if (keep) keep[m] = on ? h->sym_keep[m] : 0;
+        if (ws) ws[m] = on ? h->sym_ws[m] : 0;
     }
+    return DD_OK;
+}
+
+int dd_set_sym_config(dd_handle* h, int32_t kind, int32_t cl, int32_t st, int32_t keep, int32_t ws, void* stream) {
+    if (!h) return DD_ERR_ARG;
+    int rm, cm;
+    if (kind < 0 || kind >= GEMV_NMODES || !sym_masks(kind, &rm, &cm))
+        return h->fail(DD_ERR_ARG, "dd_set_sym_config: not a packed GEMV kind");
+    if (!(cl == 1 || cl == 2 || cl == 4 || cl == 8) || st < 2 || st > kSymStages || keep < 0 || keep > h->n_sub ||
+        !(ws == 0 || ws == 1))
+        return h->fail(DD_ERR_ARG, "dd_set_sym_config: cl in {1,2,4,8}, 2 <= st <= 4, 0 <= keep <= n_sub, ws in {0,1}");
+    if (!h->bound) return h->fail(DD_ERR_STATE, "dd_set_sym_config before dd_bind_workspace");
+    if (h->capturing) return h->fail(DD_ERR_STATE, "dd_set_sym_config during capture");
+    cudaStream_t s = (cudaStream_t)stream;
+    h->sym_st[kind] = st;
+    h->sym_keep[kind] = keep;
+    h->sym_ws[kind] = ws;
+    sym_ranges(h, kind, cl);
+    CK(h, upload(h->d.sym_rng[kind], h->sym_rng[kind], s), "upload ranges");
+    CK(h, (int)cudaStreamSynchronize(s), "sync");
+    drop_graphs(h);
     return DD_OK;
 }
 

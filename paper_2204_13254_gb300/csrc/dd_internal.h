@@ -258,7 +258,8 @@ struct DevPtrs {
     float* M32 = nullptr;            // FP32 copy
     float* Msym = nullptr;           // packed symmetric FP32 tiles (see SymDesc)
     SymDesc* symd = nullptr;         // [n_sub]
-    int32_t* sym_rng[GEMV_NMODES] = {};   // [n_sub * kSymCLMax * 2] tile-row range of every CTA
+    int32_t* sym_rng[GEMV_NMODES] = {};   // [n_sub * kSymCLMax * 3] (list offset, tile count, end tile row) per CTA
+    uint32_t* sym_tl[GEMV_NMODES] = {};   // tiles of each packed mode, every subdomain in row order
     double* K64 = nullptr;           // K~cc^-1, n_corner x ldc
     float* K32 = nullptr;
     double* Pinv = nullptr;          // [n_sub+1][NB*NB] pivot-block inverses while factoring
@@ -402,10 +403,13 @@ struct dd_handle {
     int64_t sym_elems = 0;
     int32_t sym_np_max = 0;                        // largest padded side (floats)
     std::vector<int32_t> sym_rng[GEMV_NMODES];
+    std::vector<uint32_t> sym_tl[GEMV_NMODES];     // tile list of each packed mode (a << 16 | b << 3 | flags)
+    std::vector<int64_t> sym_tl_off[GEMV_NMODES];  // start of each subdomain's run in sym_tl (n_sub + 1)
     int32_t sym_cl[GEMV_NMODES] = {4, 1, 1, 1, 1, 2, 2};   // CTAs per subdomain of each packed mode
     int32_t sym_st[GEMV_NMODES] = {4, 4, 4, 4, 4, 4, 4};   // TMA ring depth of each packed mode
     int32_t sym_nl[GEMV_NMODES] = {};                      // longest tile list of one CTA (shared memory)
     int32_t sym_keep[GEMV_NMODES] = {};                    // subdomains whose tiles are kept in L2 (evict_last)
+    int32_t sym_ws[GEMV_NMODES] = {};                      // 1: warp-specialised packed kernel, 0: CTA-synchronous
     int32_t sym_max_tiles = 0;                     // largest tile count of one subdomain
     bool sym_ok = false;                           // the packed GEMV's shared memory fits one CTA
     size_t task_cap[GEMV_NMODES] = {};             // device capacity: tasks at the smallest row count

@@ -39,6 +39,9 @@ inline cudaStream_t S(void* s) { return (cudaStream_t)s; }
 constexpr int kT = 256;
 constexpr int kWarps = kT / 32;
 constexpr int kM1 = kMaxRestart + 1;
+constexpr int kE = kGmElems;       // vector elements per thread
+constexpr int kKB = 8;             // basis vectors loaded per batch
+static_assert(kGmChunk == kE * kT, "block chunk of the Krylov vector kernels");
 
 __device__ __forceinline__ double wsum(double v) {
 #pragma unroll
@@ -95,6 +98,54 @@ __device__ __forceinline__ double combine(int64_t i, const UView& U, const doubl
     return s;
 }
 
+// combine() of MFETI-DP1 for the kE elements i0 + e kT of one thread: the index
+// loads of all of them first, then their value loads (corner copies four at a
+// time), so that a thread waits for a few round trips instead of one per load.
+// Same sums in the same order as combine().
+template <int E, typename VT>
+__device__ __forceinline__ void combine_dp1(int64_t i0, int stride, const UView& U, const double* __restrict__ w,
+                                            const float* __restrict__ wf, VT* t) {
+    const int64_t nu = U.n1 + U.nc;
+    int64_t a[E], b[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int64_t i = i0 + (int64_t)e * stride;
+        const int64_t* base = i < U.n1 ? U.ms + 2 * i : U.cp + (i - U.n1);
+        a[e] = i < nu ? base[0] : 0;
+        b[e] = i < nu ? base[1] : 0;
+    }
+    double va[E], vb[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const bool mult = i0 + (int64_t)e * stride < U.n1;
+        va[e] = mult ? wv(w, wf, a[e]) : 0.0;
+        vb[e] = mult ? wv(w, wf, b[e]) : 0.0;
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int64_t i = i0 + (int64_t)e * stride;
+        if (i < U.n1) {
+            t[e] = (VT)(va[e] - vb[e]);
+        } else if (i < nu) {
+            double sum = 0.0;
+            for (int64_t k0 = a[e]; k0 < b[e]; k0 += 4) {
+                int64_t sl[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) sl[q] = k0 + q < b[e] ? U.cs[k0 + q] : -1;
+                double v[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[q] = sl[q] >= 0 ? wv(w, wf, sl[q]) : 0.0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (sl[q] >= 0) sum += v[q];
+            }
+            t[e] = (VT)(-sum);
+        } else {
+            t[e] = (VT)0;
+        }
+    }
+}
+
 __device__ __forceinline__ double dinv_at(int64_t i, const UView& U) {
     if (i < U.n1) return U.d1 ? U.d1[i] : 1.0;
     if (i < U.n1 + U.n2) return 1.0;
@@ -121,12 +172,26 @@ __device__ bool last_block(uint32_t* counter) {
     return last;
 }
 
-// Sum of partials[k * nb + b] over b in fixed order (lanes stride the blocks,
-// then a fixed shuffle tree); valid in lane 0.
-__device__ __forceinline__ double reduce_partials(const double* partials, int k, int nb) {
-    double s = 0.0;
-    for (int b = threadIdx.x & 31; b < nb; b += 32) s += ((volatile const double*)partials)[(int64_t)k * nb + b];
-    return wsum(s);
+// tot[k] = sum over b of partials[k * nb + b] for k < nsum, by the whole block:
+// 8 threads per k (b = segment mod 8, up to 8 loads in flight per thread), the
+// segments combined by a fixed shuffle tree; fixed order for a given nb.  L2
+// loads: the partials were written by other blocks of this launch.
+__device__ __forceinline__ void reduce_partials_all(const double* partials, int nsum, int nb, double* tot) {
+    const int seg = threadIdx.x & 7;
+    for (int k = threadIdx.x >> 3; k - (int)(threadIdx.x >> 3) < nsum; k += kT / 8) {
+        const bool own = k < nsum;
+        const double* p = partials + (int64_t)(own ? k : 0) * nb;
+        double s = 0.0;
+        for (int b0 = seg; b0 < nb; b0 += 64) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = (own && b0 + 8 * u < nb) ? __ldcg(p + b0 + 8 * u) : 0.0;
+            s += ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+        }
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (own && seg == 0) tot[k] = s;
+    }
 }
 
 // Block sum of one value (all threads call); result in thread 0.
@@ -213,8 +278,9 @@ __global__ void __launch_bounds__(kT) k_gm_start(UView U, const double* __restri
         partials[nb + blockIdx.x] = bb;
     }
     if (!last_block(&gs->counter[0])) return;
-    double tot[2];
-    for (int k = 0; k < 2; ++k) tot[k] = __shfl_sync(0xffffffffu, reduce_partials(partials, k, nb), 0);
+    __shared__ double tot[2];
+    reduce_partials_all(partials, 2, nb, tot);
+    __syncthreads();
     if (threadIdx.x == 0) {
         gs->counter[0] = 0u;
         const double beta = sqrt(tot[0]);
@@ -248,22 +314,42 @@ __global__ void __launch_bounds__(kT) k_gm_start(UView U, const double* __restri
 
 // v_j = (t - sum_k h2_k v_k) / hnext (the second Gram-Schmidt projection of the
 // previous column, nh2 terms, none at a cycle start), z = D^-1 v_j: FP64 z for
-// the FP64 GEMV, FP32 z for the FP32 one
+// the FP64 GEMV, FP32 z for the FP32 one.  The basis entries of a thread's
+// elements are loaded kKB vectors at a time, all in flight before any is used.
 template <typename VT>
-__global__ void k_gm_normalize(UView U, VT* __restrict__ V, int64_t ldv, const VT* __restrict__ tu,
-                               double* __restrict__ zu, float* __restrict__ zuf, const GmresScalars* gs) {
+__global__ void __launch_bounds__(kT) k_gm_normalize(UView U, VT* __restrict__ V, int64_t ldv, const VT* __restrict__ tu,
+                                                     double* __restrict__ zu, float* __restrict__ zuf,
+                                                     const GmresScalars* gs) {
     if (gs->skip) return;
     __shared__ VT coef[kM1];
     const int nh2 = gs->nh2;
     if (threadIdx.x < nh2) coef[threadIdx.x] = (VT)gs->h2[threadIdx.x];
-    __syncthreads();
     const int64_t nu = U.n1 + U.n2 + U.nc;
-    VT* vj = V + (int64_t)gs->j * ldv;
+    const int64_t i0 = (int64_t)blockIdx.x * kGmChunk + threadIdx.x;
+    VT t[kE];
+#pragma unroll
+    for (int e = 0; e < kE; ++e) t[e] = i0 + e * kT < nu ? tu[i0 + e * kT] : (VT)0;
+    __syncthreads();
+    for (int k0 = 0; k0 < nh2; k0 += kKB) {
+        VT vv[kKB][kE];
+#pragma unroll
+        for (int q = 0; q < kKB; ++q)
+#pragma unroll
+            for (int e = 0; e < kE; ++e)
+                vv[q][e] = (k0 + q < nh2 && i0 + e * kT < nu) ? V[(int64_t)(k0 + q) * ldv + i0 + e * kT] : (VT)0;
+#pragma unroll
+        for (int q = 0; q < kKB; ++q)
+            if (k0 + q < nh2)
+#pragma unroll
+                for (int e = 0; e < kE; ++e) t[e] -= coef[k0 + q] * vv[q][e];
+    }
     const VT inv = (VT)(1.0 / gs->hnext);
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nu; i += (int64_t)gridDim.x * blockDim.x) {
-        VT t = tu[i];
-        for (int k = 0; k < nh2; ++k) t -= coef[k] * V[(int64_t)k * ldv + i];
-        const VT v = t * inv;
+    VT* vj = V + (int64_t)gs->j * ldv;
+#pragma unroll
+    for (int e = 0; e < kE; ++e) {
+        const int64_t i = i0 + e * kT;
+        if (i >= nu) continue;
+        const VT v = t[e] * inv;
         const VT z = (VT)dinv_at(i, U) * v;
         vj[i] = v;
         if (zu) zu[i] = (double)z;
@@ -295,34 +381,62 @@ __global__ void __launch_bounds__(kT) k_gm_pass(UView U, const double* __restric
     const int nb = gridDim.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (PHASE == 1 && threadIdx.x < nv) coef[threadIdx.x] = (VT)gs->h1[threadIdx.x];
-    __syncthreads();
-    VT t[kGmElems];
+    const int64_t i0 = (int64_t)blockIdx.x * kGmChunk + threadIdx.x;
+    VT t[kE];
+    if (PHASE == 0 && !U.mtp) {
+        combine_dp1<kE, VT>(i0, kT, U, w, wf, t);
+    } else {
 #pragma unroll
-    for (int e = 0; e < kGmElems; ++e) {
-        const int64_t i = (int64_t)blockIdx.x * kGmChunk + e * kT + threadIdx.x;
-        t[e] = (VT)0;
-        if (i < nu) {
-            VT v;
-            if (PHASE == 0) {
-                v = (VT)combine(i, U, w, wf, in);
-            } else {
-                v = tu[i];
-                for (int k = 0; k < nv; ++k) v -= coef[k] * V[(int64_t)k * ldv + i];
-            }
-            tu[i] = v;
-            t[e] = v;
+        for (int e = 0; e < kE; ++e) {
+            const int64_t i = i0 + e * kT;
+            t[e] = (VT)0;
+            if (i < nu) t[e] = PHASE == 0 ? (VT)combine(i, U, w, wf, in) : tu[i];
         }
     }
+    __syncthreads();   // coef
+    if (PHASE == 1) {   // t1 = t - V h1, kKB basis vectors per batch of loads
+        for (int k0 = 0; k0 < nv; k0 += kKB) {
+            VT vv[kKB][kE];
+#pragma unroll
+            for (int q = 0; q < kKB; ++q)
+#pragma unroll
+                for (int e = 0; e < kE; ++e)
+                    vv[q][e] = (k0 + q < nv && i0 + e * kT < nu) ? V[(int64_t)(k0 + q) * ldv + i0 + e * kT] : (VT)0;
+#pragma unroll
+            for (int q = 0; q < kKB; ++q)
+                if (k0 + q < nv)
+#pragma unroll
+                    for (int e = 0; e < kE; ++e) t[e] -= coef[k0 + q] * vv[q][e];
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < kE; ++e)
+        if (i0 + e * kT < nu) tu[i0 + e * kT] = t[e];
     // partial dots with v_0 .. v_j (and ||t||^2 in PHASE 1)
-    for (int k = 0; k < nsum; ++k) {
+    for (int k0 = 0; k0 < nv; k0 += kKB) {
+        VT vv[kKB][kE];
+#pragma unroll
+        for (int q = 0; q < kKB; ++q)
+#pragma unroll
+            for (int e = 0; e < kE; ++e)
+                vv[q][e] = (k0 + q < nv && i0 + e * kT < nu) ? V[(int64_t)(k0 + q) * ldv + i0 + e * kT] : (VT)0;
+#pragma unroll
+        for (int q = 0; q < kKB; ++q) {
+            if (k0 + q < nv) {
+                VT p = (VT)0;
+#pragma unroll
+                for (int e = 0; e < kE; ++e) p += t[e] * vv[q][e];
+                p = wsum(p);
+                if (lane == 0) red[k0 + q][warp] = (double)p;
+            }
+        }
+    }
+    if (PHASE == 1) {
         VT p = (VT)0;
 #pragma unroll
-        for (int e = 0; e < kGmElems; ++e) {
-            const int64_t i = (int64_t)blockIdx.x * kGmChunk + e * kT + threadIdx.x;
-            if (i < nu) p += t[e] * (k < nv ? V[(int64_t)k * ldv + i] : t[e]);
-        }
+        for (int e = 0; e < kE; ++e) p += t[e] * t[e];
         p = wsum(p);
-        if (lane == 0) red[k][warp] = (double)p;
+        if (lane == 0) red[nv][warp] = (double)p;
     }
     __syncthreads();
     if (threadIdx.x < nsum) {
@@ -332,111 +446,150 @@ __global__ void __launch_bounds__(kT) k_gm_pass(UView U, const double* __restric
         __threadfence();
     }
     if (!last_block(&gs->counter[1 + PHASE])) return;
-    for (int k = warp; k < nsum; k += kWarps) {
-        const double s = reduce_partials(partials, k, nb);
-        if (lane == 0) tot[k] = s;
-    }
+    reduce_partials_all(partials, nsum, nb, tot);
     __syncthreads();
     if (PHASE == 0) {
         if (threadIdx.x < nv) gs->h1[threadIdx.x] = tot[threadIdx.x];
         if (threadIdx.x == 0) gs->counter[1] = 0u;
         return;
     }
-    if (threadIdx.x != 0) return;
-    gs->counter[2] = 0u;
-    double* col = gs->H + (int64_t)j * kM1;
-    double h2sq = 0.0;
-    for (int k = 0; k < nv; ++k) {
-        gs->h2[k] = tot[k];
-        col[k] = gs->h1[k] + tot[k];
-        h2sq += tot[k] * tot[k];
+    // Column j of H, its Givens rotations and, at a cycle end, y = R^-1 g: on
+    // shared-memory copies of H, the rotations and g that the whole block loads
+    // at once (one thread working through global memory would wait for every
+    // load in turn).  Same arithmetic in the same order as the sequential
+    // definition.
+    __shared__ double sH[kMaxRestart * kM1];   // columns 0 .. j
+    __shared__ double scs[kMaxRestart], ssn[kMaxRestart], sg[kM1], sy[kMaxRestart];
+    __shared__ int s_end, s_k;
+    const int tid = threadIdx.x;
+    for (int p = tid; p < j * kM1; p += kT) sH[p] = gs->H[p];
+    if (tid < j) {
+        scs[tid] = gs->cs[tid];
+        ssn[tid] = gs->sn[tid];
     }
-    const double hsub = sqrt(fmax(tot[nv] - h2sq, 0.0));
-    col[j + 1] = hsub;
-    for (int i = 0; i < j; ++i) {
-        const double a = col[i], b = col[i + 1];
-        col[i] = gs->cs[i] * a + gs->sn[i] * b;
-        col[i + 1] = -gs->sn[i] * a + gs->cs[i] * b;
+    if (tid <= j) sg[tid] = gs->g[tid];
+    if (tid < nv) {
+        gs->h2[tid] = tot[tid];
+        sH[j * kM1 + tid] = gs->h1[tid] + tot[tid];
     }
-    double c = 1.0, s = 0.0;
-    {
-        const double a = col[j], b = col[j + 1];
-        const double r = hypot(a, b);
-        if (r != 0.0) {
-            c = a / r;
-            s = b / r;
+    const int it = gs->it + 1, max_it = gs->max_it, m = gs->m;
+    const double thr = gs->thr;
+    __syncthreads();
+    double* col = sH + j * kM1;
+    if (tid == 0) {
+        double h2sq = 0.0;
+        for (int k = 0; k < nv; ++k) h2sq += tot[k] * tot[k];
+        const double hsub = sqrt(fmax(tot[nv] - h2sq, 0.0));
+        col[j + 1] = hsub;
+        for (int i = 0; i < j; ++i) {
+            const double a = col[i], b = col[i + 1];
+            col[i] = scs[i] * a + ssn[i] * b;
+            col[i + 1] = -ssn[i] * a + scs[i] * b;
         }
-    }
-    col[j] = c * col[j] + s * col[j + 1];
-    col[j + 1] = 0.0;
-    gs->cs[j] = c;
-    gs->sn[j] = s;
-    gs->g[j + 1] = -s * gs->g[j];
-    gs->g[j] = c * gs->g[j];
-    gs->it += 1;
-    sc->it_total += 1;
-    const double resid = fabs(gs->g[j + 1]);
-    gs->resid = resid;
-    const bool finite = isfinite(resid) && isfinite(hsub) && isfinite(col[j]);
-    const bool conv = finite && resid <= gs->thr;
-    const bool out_of_budget = gs->it >= gs->max_it;
-    const bool end = !finite || conv || out_of_budget || j + 1 == gs->m || hsub == 0.0;
-    if (!finite) gs->status = DD_ERR_NONFINITE;
-    if (end) {
-        const int k = finite ? j + 1 : 0;
-        for (int i = k - 1; i >= 0; --i) {
-            double v = gs->g[i];
-            for (int l = i + 1; l < k; ++l) v -= gs->H[(int64_t)l * kM1 + i] * gs->y[l];
-            gs->y[i] = v / gs->H[(int64_t)i * kM1 + i];
+        double c = 1.0, s = 0.0;
+        {
+            const double a = col[j], b = col[j + 1];
+            const double r = hypot(a, b);
+            if (r != 0.0) {
+                c = a / r;
+                s = b / r;
+            }
         }
-        gs->k = k;
-        gs->converged = conv ? 1 : 0;
-        gs->final = (!finite || conv || out_of_budget) ? 1 : 0;
-        gs->cycle_end = 1;
-        gs->skip = 1;
-    } else {
-        gs->nh2 = nv;
-        gs->j = j + 1;
-        gs->hnext = hsub;
+        col[j] = c * col[j] + s * col[j + 1];
+        col[j + 1] = 0.0;
+        gs->cs[j] = c;
+        gs->sn[j] = s;
+        sg[j + 1] = -s * sg[j];
+        sg[j] = c * sg[j];
+        gs->g[j + 1] = sg[j + 1];
+        gs->g[j] = sg[j];
+        gs->it = it;
+        sc->it_total += 1;
+        const double resid = fabs(sg[j + 1]);
+        gs->resid = resid;
+        const bool finite = isfinite(resid) && isfinite(hsub) && isfinite(col[j]);
+        const bool conv = finite && resid <= thr;
+        const bool out_of_budget = it >= max_it;
+        const bool end = !finite || conv || out_of_budget || j + 1 == m || hsub == 0.0;
+        if (!finite) gs->status = DD_ERR_NONFINITE;
+        gs->counter[2] = 0u;
+        s_end = end ? 1 : 0;
+        s_k = finite ? j + 1 : 0;
+        if (end) {
+            const int k = s_k;
+            for (int i = k - 1; i >= 0; --i) {
+                double v = sg[i];
+                for (int l = i + 1; l < k; ++l) v -= sH[l * kM1 + i] * sy[l];
+                sy[i] = v / sH[i * kM1 + i];
+            }
+            gs->k = k;
+            gs->converged = conv ? 1 : 0;
+            gs->final = (!finite || conv || out_of_budget) ? 1 : 0;
+            gs->cycle_end = 1;
+            gs->skip = 1;
+        } else {
+            gs->nh2 = nv;
+            gs->j = j + 1;
+            gs->hnext = hsub;
+        }
+        if (cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, end ? 0u : 1u);
     }
-    if (cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, end ? 0u : 1u);
+    __syncthreads();
+    if (tid <= j + 1) gs->H[(int64_t)j * kM1 + tid] = col[tid];
+    if (s_end && tid < s_k) gs->y[tid] = sy[tid];
 }
 
 // End of a cycle: x += D^-1 V y (x = [lambda; x_c] in place); at the end of the
 // solve, publish its outcome in the CG scalars (step statistics, solve end).
 template <typename VT>
-__global__ void k_gm_update(UView U, const VT* __restrict__ V, int64_t ldv, const GmresScalars* gs, PcgScalars* sc,
-                            unsigned long long cond) {
+__global__ void __launch_bounds__(kT) k_gm_update(UView U, const VT* __restrict__ V, int64_t ldv,
+                                                  const GmresScalars* gs, PcgScalars* sc, unsigned long long cond) {
     __shared__ VT y[kMaxRestart];
     const int k = gs->k;
     if (threadIdx.x < k) y[threadIdx.x] = (VT)gs->y[threadIdx.x];
     __syncthreads();
     const int64_t nu = U.n1 + U.n2 + U.nc;
-    if (k > 0) {
-        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nu; i += (int64_t)gridDim.x * blockDim.x) {
-            VT vs = (VT)0;
-            for (int q = 0; q < k; ++q) vs += y[q] * V[(int64_t)q * ldv + i];
-            const double v = (double)vs * dinv_at(i, U);
-            double* x;
-            float* xf;
-            int64_t o;
-            if (i < U.n1) {
-                x = U.x1;
-                xf = U.x1f;
-                o = i;
-            } else if (i < U.n1 + U.n2) {
-                x = U.x2;
-                xf = U.x2f;
-                o = i - U.n1;
-            } else {
-                x = U.xc;
-                xf = U.xcf;
-                o = i - U.n1 - U.n2;
-            }
-            const double nx = x[o] + v;
-            x[o] = nx;
-            if (xf) xf[o] = (float)nx;
+    const int64_t i0 = (int64_t)blockIdx.x * kGmChunk + threadIdx.x;
+    VT vs[kE];
+#pragma unroll
+    for (int e = 0; e < kE; ++e) vs[e] = (VT)0;
+    for (int q0 = 0; q0 < k; q0 += kKB) {
+        VT vv[kKB][kE];
+#pragma unroll
+        for (int q = 0; q < kKB; ++q)
+#pragma unroll
+            for (int e = 0; e < kE; ++e)
+                vv[q][e] = (q0 + q < k && i0 + e * kT < nu) ? V[(int64_t)(q0 + q) * ldv + i0 + e * kT] : (VT)0;
+#pragma unroll
+        for (int q = 0; q < kKB; ++q)
+            if (q0 + q < k)
+#pragma unroll
+                for (int e = 0; e < kE; ++e) vs[e] += y[q0 + q] * vv[q][e];
+    }
+#pragma unroll
+    for (int e = 0; e < kE; ++e) {
+        const int64_t i = i0 + e * kT;
+        if (k == 0 || i >= nu) continue;
+        const double v = (double)vs[e] * dinv_at(i, U);
+        double* x;
+        float* xf;
+        int64_t o;
+        if (i < U.n1) {
+            x = U.x1;
+            xf = U.x1f;
+            o = i;
+        } else if (i < U.n1 + U.n2) {
+            x = U.x2;
+            xf = U.x2f;
+            o = i - U.n1;
+        } else {
+            x = U.xc;
+            xf = U.xcf;
+            o = i - U.n1 - U.n2;
         }
+        const double nx = x[o] + v;
+        x[o] = nx;
+        if (xf) xf[o] = (float)nx;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         if (gs->final) {
@@ -525,13 +678,12 @@ int launch_gm_start(const dd_handle* h, const UView& U, int have_q, const float*
 }
 
 int launch_gm_normalize(const dd_handle* h, const UView& U, float* zuf, void* stream) {
-    const int64_t nu = U.n1 + U.n2 + U.nc;
     if (zuf)
-        k_gm_normalize<float><<<vec_blocks(nu), kT, 0, S(stream)>>>(U, reinterpret_cast<float*>(h->d.Vk), h->gm_ldv,
+        k_gm_normalize<float><<<h->gm_blocks, kT, 0, S(stream)>>>(U, reinterpret_cast<float*>(h->d.Vk), h->gm_ldv,
                                                                    reinterpret_cast<const float*>(h->d.tu), nullptr,
                                                                    zuf, h->d.gs);
     else
-        k_gm_normalize<double><<<vec_blocks(nu), kT, 0, S(stream)>>>(U, h->d.Vk, h->gm_ldv, h->d.tu, h->d.zu, nullptr,
+        k_gm_normalize<double><<<h->gm_blocks, kT, 0, S(stream)>>>(U, h->d.Vk, h->gm_ldv, h->d.tu, h->d.zu, nullptr,
                                                                     h->d.gs);
     return (int)cudaGetLastError();
 }
@@ -559,12 +711,11 @@ int launch_gm_pass(const dd_handle* h, const UView& U, int phase, const float* w
 }
 
 int launch_gm_update(const dd_handle* h, const UView& U, unsigned long long cond_outer, void* stream) {
-    const int64_t nu = U.n1 + U.n2 + U.nc;
     if (U.x1f || U.xcf)
-        k_gm_update<float><<<vec_blocks(nu), kT, 0, S(stream)>>>(U, reinterpret_cast<const float*>(h->d.Vk), h->gm_ldv,
+        k_gm_update<float><<<h->gm_blocks, kT, 0, S(stream)>>>(U, reinterpret_cast<const float*>(h->d.Vk), h->gm_ldv,
                                                                 h->d.gs, h->d.sc, cond_outer);
     else
-        k_gm_update<double><<<vec_blocks(nu), kT, 0, S(stream)>>>(U, h->d.Vk, h->gm_ldv, h->d.gs, h->d.sc, cond_outer);
+        k_gm_update<double><<<h->gm_blocks, kT, 0, S(stream)>>>(U, h->d.Vk, h->gm_ldv, h->d.gs, h->d.sc, cond_outer);
     return (int)cudaGetLastError();
 }
 

@@ -12,7 +12,10 @@
 //
 // Work split: the cl CTAs of a cluster (1..kSymCLMax; per mode, like the ring
 // depth st <= kSymStages, chosen by dd_autotune) share one subdomain by ranges of
-// tile rows (balanced on the host by tile count).  Each CTA streams its tiles
+// tile rows (balanced on the host by tile count).  The tiles a mode needs are
+// listed once on the host (row order, per subdomain); a CTA copies its run of
+// that list to shared memory and stages only the x entries its tile rows read,
+// issuing the index loads of eight entries before their value loads.  It streams its tiles
 // through an st-deep ring of shared-memory buffers filled by
 // cp.async.bulk (one 16 KB copy per tile, completion on an mbarrier) issued by
 // one thread, and accumulates its partial y over the subdomain's whole padded
@@ -100,55 +103,105 @@ struct Groups {
     int n0, n1, n2;   // group sizes
     __device__ __forceinline__ int of(int a) const { return (a >= t1) + (a >= t2); }
     __device__ __forceinline__ int first(int g) const { return g == 0 ? 0 : (g == 1 ? t1 : t2); }
-    __device__ __forceinline__ int end(int g) const { return g == 0 ? t1 : (g == 1 ? t2 : nt); }
     __device__ __forceinline__ int size(int g) const { return g == 0 ? n0 : (g == 1 ? n1 : n2); }
     __device__ __forceinline__ int start(int g) const { return g == 0 ? 0 : (g == 1 ? n0 : n0 + n1); }
-    // flags of tile (a, b) as sym_tile_flags
-    __device__ __forceinline__ int flags(int a, int b, int rmask, int cmask) const {
-        const int ga = of(a), gb = of(b);
-        int f = 0;
-        if (((rmask >> ga) & 1) && ((cmask >> gb) & 1)) f |= 1;
-        if (a != b && ((rmask >> gb) & 1) && ((cmask >> ga) & 1)) f |= 2;
-        if ((ga == 2) != (gb == 2)) f |= 4;
-        return f;
-    }
-    // Next tile (a, b) at or after the iterator position, in row order over tile
-    // rows [.., a1), that contributes to the mode; flags in f.  Flags depend
-    // only on the groups of a and b (and on a == b), so a group that
-    // contributes nothing is skipped whole.
-    __device__ __forceinline__ bool next(int rmask, int cmask, int a1, int& a, int& b, int& f) const {
-        for (; a < a1; ++a, b = 0) {
-            while (b <= a) {
-                f = flags(a, b, rmask, cmask);
-                if (f & 3) return true;
-                int nb = end(of(b));
-                if (nb > a) nb = a;   // the diagonal tile has flags of its own
-                b = nb > b ? nb : b + 1;
-            }
-        }
-        return false;
-    }
 };
 
-// Shared-memory layout of k_symgemv (floats unless noted), span = the padded
-// index range the mode touches (from its first group on), st = ring depth,
-// nl = longest tile list of one CTA:
-//   ring [st][kSymTile] | x [span] | y [span] | red [2][8][64] | bars (u64) [kSymStages] | tile list (u32) [nl]
+// Shared-memory layouts (floats unless noted), span = the padded index range
+// the mode touches (from its first group on), st = ring depth, nl = longest
+// tile list of one CTA:
+//   k_symgemv:    ring [st][kSymTile] | x [span] | y [span] | red [2][8][64] | bars (u64) [kSymStages] | tiles (u32) [nl]
+//   k_symgemv_ws: ring [st][kSymTile] | x [span] | y [4][span] | full, empty (u64) [kSymStages] | tiles (u32) [nl]
 __host__ __device__ inline size_t sym_smem(int span, int st, int nl) {
     size_t f = (size_t)st * kSymTile + 2 * (size_t)span + 2 * 8 * 64;
     return f * sizeof(float) + kSymStages * sizeof(uint64_t) + (size_t)nl * sizeof(uint32_t);
 }
+__host__ __device__ inline size_t sym_smem_ws(int span, int st, int nl) {
+    size_t f = (size_t)st * kSymTile + 5 * (size_t)span;
+    return f * sizeof(float) + 2 * kSymStages * sizeof(uint64_t) + (size_t)nl * sizeof(uint32_t);
+}
 
 // tile list entry: a << 16 | b << 3 | flags (a, b < 8192)
-__device__ __forceinline__ uint32_t tile_entry(int a, int b, int f) { return ((uint32_t)a << 16) | ((uint32_t)b << 3) | f; }
+__host__ __device__ __forceinline__ uint32_t tile_entry(int a, int b, int f) { return ((uint32_t)a << 16) | ((uint32_t)b << 3) | f; }
+__device__ __forceinline__ int64_t entry_tile(uint32_t e, const Groups& G) {
+    return sym_tile_index((int)(e >> 16), (int)((e >> 3) & 0x1fff), G.t1, G.nt);
+}
 
 __host__ __device__ inline int lowest_group(int mask) { return (mask & 1) ? 0 : ((mask & 2) ? 1 : 2); }
 
+// x over the column groups of tile rows < a_end (the only ones the CTA reads),
+// eight entries per thread per pass: their index loads, then their value loads.
+__device__ __forceinline__ void stage_x(const XSrc& xs, const SymDesc& sd, const Groups& G, int cmask, int p_lo,
+                                        int p_end, float* xsh, int tid, int nthr) {
+    const float beta = (xs.kind == X_PCG || xs.kind == X_PCG_CV) ? (float)xs.sc->beta : 0.0f;
+    constexpr int kStage = 8;
+    for (int p0 = p_lo + tid; p0 < p_end; p0 += nthr * kStage) {
+        int mm[kStage], cc[kStage], ll[kStage];
+#pragma unroll
+        for (int u = 0; u < kStage; ++u) {
+            const int p = p0 + u * nthr;
+            const int g = G.of(p / kSymT);
+            const int q = p - G.first(g) * kSymT;
+            const bool need = p < p_end && ((cmask >> g) & 1) && q < G.size(g);
+            ll[u] = need ? G.start(g) + q : -1;
+            mm[u] = need ? xs.slot_mult[sd.voff + ll[u]] : 0;
+            cc[u] = need ? xs.slot_corner[sd.voff + ll[u]] : -1;
+        }
+        float vv[kStage];
+#pragma unroll
+        for (int u = 0; u < kStage; ++u) {
+            const XRef r = ll[u] >= 0 ? xsrc_ref_f(xs, mm[u], cc[u], sd.voff + ll[u], ll[u])
+                                      : XRef{nullptr, nullptr, 0, 1.0f};
+            vv[u] = xref_value(r, beta);
+        }
+#pragma unroll
+        for (int u = 0; u < kStage; ++u) {
+            const int p = p0 + u * nthr;
+            if (p < p_end) xsh[p - p_lo] = vv[u];
+        }
+    }
+}
+
+// y[R] = sum over the cluster's partial vectors ysh (rank order); this CTA
+// stores every cl-th chunk of rows.  Both cluster barriers are taken by every CTA.
+__device__ __forceinline__ void cluster_store(cg::cluster_group& cluster, const float* ysh, const SymDesc& sd,
+                                              const Groups& G, int rmask, int r_lo, int p_lo, int np, int cl,
+                                              const GemvOut& go, int tid, int nthr) {
+    cluster.sync();
+    const int rank = (int)cluster.block_rank();
+    for (int p = r_lo + rank * nthr + tid; p < np; p += cl * nthr) {
+        const int g = G.of(p / kSymT);
+        const int q = p - G.first(g) * kSymT;
+        if (!((rmask >> g) & 1) || q >= G.size(g)) continue;
+        float part[kSymCLMax];
+#pragma unroll
+        for (int c = 0; c < kSymCLMax; ++c)
+            part[c] = c < cl ? cluster.map_shared_rank(const_cast<float*>(ysh), c)[p - p_lo] : 0.0f;
+        float v = 0.0f;
+#pragma unroll
+        for (int c = 0; c < kSymCLMax; ++c)
+            if (c < cl) v += part[c];
+        const int64_t o = sd.voff + G.start(g) + q;
+        if (go.out32) {
+            float w = (float)go.alpha * v;
+            if (go.base32) w += go.base32[o];
+            go.out32[o] = w;
+        }
+        if (go.out) {
+            double w = (double)v;
+            if (go.alpha != 1.0) w *= go.alpha;
+            if (go.base) w += go.base[o];
+            go.out[o] = w;
+        }
+    }
+    cluster.sync();   // no CTA leaves while another reads its shared memory
+}
+
+// CTA-synchronous form: 128 threads consume every tile together, one barrier per tile.
 __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ descs, const int32_t* __restrict__ ranges,
-                                                const float* __restrict__ Msym, int span_max, int cl, int st,
-                                                int rmask, int cmask, int keep, XSrc xs, GemvOut go,
-                                                const int32_t* __restrict__ skip, int32_t* __restrict__ err) {
-    // (ranges/list capacity: the host sizes the list region for the longest range of this mode)
+                                                const uint32_t* __restrict__ tlist, const float* __restrict__ Msym,
+                                                int span_max, int cl, int st, int rmask, int cmask, int keep, XSrc xs,
+                                                GemvOut go, const int32_t* __restrict__ skip, int32_t* __restrict__ err) {
     if (skip && *skip) return;   // the same word for every CTA of the grid
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float* ring = reinterpret_cast<float*>(smem_raw);
@@ -164,47 +217,31 @@ __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ desc
     const SymDesc sd = descs[sub];
     const Groups G{sd.t0[1], sd.t0[2], sd.t0[3], sd.n[0], sd.n[1], sd.n[2]};
     const int np = G.nt * kSymT;
-    const int a0 = ranges[2 * blockIdx.x], a1 = ranges[2 * blockIdx.x + 1];
+    // this CTA's run of the mode's tile list and the end of its tile rows
+    const uint32_t* lst = tlist + ranges[3 * blockIdx.x];
+    const int nt_cta = ranges[3 * blockIdx.x + 1];
+    const int a_end = ranges[3 * blockIdx.x + 2];
     const float* tiles = Msym + sd.toff;
     const int p_lo = G.first(lowest_group(rmask | cmask)) * kSymT;
     const int r_lo = G.first(lowest_group(rmask)) * kSymT;
 
-    // thread 0: barriers, the first st tiles (in flight while the CTA stages x),
-    // then the CTA's whole tile list
-    __shared__ int n_tiles;
+    // thread 0: barriers and the first st tiles (in flight while the CTA stages x)
     int issued = 0;
     const uint64_t pol = l2_policy(sub < keep);   // subdomains below `keep` stay in L2
     if (tid == 0) {
         for (int s = 0; s < st; ++s) mbar_init(&bars[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        int pa = a0, pb = 0, pf = 0;
-        for (int s = 0; s < st && G.next(rmask, cmask, a1, pa, pb, pf); ++s, ++pb, ++issued)
-            load_tile(ring + s * kSymTile, tiles + sym_tile_index(pa, pb, G.t1, G.nt) * kSymTile, &bars[s], pol);
-        int n = 0;
-        pa = a0;
-        pb = 0;
-        while (G.next(rmask, cmask, a1, pa, pb, pf)) tl[n++] = tile_entry(pa, pb++, pf);
-        n_tiles = n;
+        for (int s = 0; s < st && s < nt_cta; ++s, ++issued)
+            load_tile(ring + s * kSymTile, tiles + entry_tile(lst[s], G) * kSymTile, &bars[s], pol);
     }
-    // x over the column groups (padded index space from p_lo), y = 0
-    const float beta = (xs.kind == X_PCG || xs.kind == X_PCG_CV) ? (float)xs.sc->beta : 0.0f;
-    for (int p = p_lo + tid; p < np; p += kT) {
-        const int g = G.of(p / kSymT);
-        const int q = p - G.first(g) * kSymT;
-        float v = 0.0f;
-        if (((cmask >> g) & 1) && q < G.size(g)) {
-            const int l = G.start(g) + q;
-            v = xsrc_value_f(xs, sd.voff + l, l, beta);
-        }
-        xsh[p - p_lo] = v;
-        ysh[p - p_lo] = 0.0f;
-    }
+    for (int k = tid; k < nt_cta; k += kT) tl[k] = lst[k];
+    for (int p = p_lo + tid; p < np; p += kT) ysh[p - p_lo] = 0.0f;
+    stage_x(xs, sd, G, cmask, p_lo, min(np, a_end * kSymT), xsh, tid, kT);
     __syncthreads();
 
     // thread (rg, cq): rows 8 rg .. 8 rg + 7 and columns 4 cq .. 4 cq + 3 of a tile
     // (16-byte shared loads; a half-warp covers one row group)
     const int rg = tid >> 4, cq = tid & 15;
-    const int nt_cta = n_tiles;
     float acc[8], xa[8];
     int cur = -1, k = 0, slot = 0;
     uint32_t phase = 0;
@@ -255,8 +292,7 @@ __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ desc
         if (bad) break;
         if (tid == 0 && k + st < nt_cta) {
             const uint32_t en = tl[k + st];
-            const int na = (int)(en >> 16), nb = (int)((en >> 3) & 0x1fff);
-            load_tile(ring + slot * kSymTile, tiles + sym_tile_index(na, nb, G.t1, G.nt) * kSymTile, &bars[slot], pol);
+            load_tile(ring + slot * kSymTile, tiles + entry_tile(en, G) * kSymTile, &bars[slot], pol);
             ++issued;
         }
         if ((cf & 2) && tid < 64) {   // transposed role: column tid of the tile, 8 row groups in order
@@ -276,29 +312,186 @@ __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ desc
         atomicExch(err, 1);
     }
 
-    // y[R] = sum over the cluster's partial vectors, rank order; this CTA stores every cl-th row
-    cluster.sync();
-    const int rank = (int)cluster.block_rank();
-    for (int p = r_lo + rank * kT + tid; p < np; p += cl * kT) {
-        const int g = G.of(p / kSymT);
-        const int q = p - G.first(g) * kSymT;
-        if (!((rmask >> g) & 1) || q >= G.size(g)) continue;
-        float v = 0.0f;
-        for (int c = 0; c < cl; ++c) v += cluster.map_shared_rank(ysh, c)[p - p_lo];
-        const int64_t o = sd.voff + G.start(g) + q;
-        if (go.out32) {
-            float w = (float)go.alpha * v;
-            if (go.base32) w += go.base32[o];
-            go.out32[o] = w;
-        }
-        if (go.out) {
-            double w = (double)v;
-            if (go.alpha != 1.0) w *= go.alpha;
-            if (go.base) w += go.base[o];
-            go.out[o] = w;
-        }
+    cluster_store(cluster, ysh, sd, G, rmask, r_lo, p_lo, np, cl, go, tid, kT);
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait that also gives up once another role has aborted.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, const volatile int* abort) {
+    for (unsigned k = 0; k < kWaitLimit; ++k) {
+        if (mbar_test(bar, parity)) return true;
+        if ((k & 255u) == 255u && *abort) return false;
     }
-    cluster.sync();   // no CTA leaves while another reads its shared memory
+    return false;
+}
+
+// Warp-specialised form: warp 4 (one elected lane) refills the ring as soon as
+// the four consumer warps have released a slot (an `empty` mbarrier per slot,
+// four arrivals); each consumer warp reads rows 16 w .. 16 w + 15 of every tile
+// (the same thread layout as k_symgemv) and keeps its own copy of the partial
+// y, so no barrier spans the CTA between tiles: the direct-role row sums are
+// warp-local as before, and the transposed-role column sums of the warp's two
+// row groups combine with one shuffle.  The four copies are added in warp order
+// at the end (deterministic).
+constexpr int kTW = kT + 32;
+
+__global__ void __launch_bounds__(kTW) k_symgemv_ws(const SymDesc* __restrict__ descs,
+                                                    const int32_t* __restrict__ ranges,
+                                                    const uint32_t* __restrict__ tlist, const float* __restrict__ Msym,
+                                                    int span_max, int cl, int st, int rmask, int cmask, int keep,
+                                                    XSrc xs, GemvOut go, const int32_t* __restrict__ skip,
+                                                    int32_t* __restrict__ err) {
+    if (skip && *skip) return;   // the same word for every CTA of the grid
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float* ring = reinterpret_cast<float*>(smem_raw);
+    float* xsh = ring + st * kSymTile;   // index p - p_lo
+    float* yw = xsh + span_max;          // [4][span_max]: one partial y per consumer warp
+    uint64_t* full = reinterpret_cast<uint64_t*>(yw + 4 * span_max);
+    uint64_t* empty = full + kSymStages;
+    uint32_t* tl = reinterpret_cast<uint32_t*>(empty + kSymStages);
+    __shared__ int abort_flag;
+
+    cg::cluster_group cluster = cg::this_cluster();
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int sub = blockIdx.x / cl;
+    const SymDesc sd = descs[sub];
+    const Groups G{sd.t0[1], sd.t0[2], sd.t0[3], sd.n[0], sd.n[1], sd.n[2]};
+    const int np = G.nt * kSymT;
+    const uint32_t* lst = tlist + ranges[3 * blockIdx.x];
+    const int nt_cta = ranges[3 * blockIdx.x + 1];
+    const int a_end = ranges[3 * blockIdx.x + 2];
+    const float* tiles = Msym + sd.toff;
+    const int p_lo = G.first(lowest_group(rmask | cmask)) * kSymT;
+    const int r_lo = G.first(lowest_group(rmask)) * kSymT;
+    const int span = np - p_lo;
+
+    int issued = 0;   // producer lane only
+    const uint64_t pol = l2_policy(sub < keep);
+    if (tid == kT) {
+        for (int s = 0; s < st; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 4);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_flag = 0;
+        for (int s = 0; s < st && s < nt_cta; ++s, ++issued)
+            load_tile(ring + s * kSymTile, tiles + entry_tile(lst[s], G) * kSymTile, &full[s], pol);
+    }
+    for (int k = tid; k < nt_cta; k += kTW) tl[k] = lst[k];
+    for (int p = tid; p < 4 * span; p += kTW) yw[(p / span) * span_max + p % span] = 0.0f;
+    stage_x(xs, sd, G, cmask, p_lo, min(np, a_end * kSymT), xsh, tid, kTW);
+    __syncthreads();
+
+    if (warp == 4) {
+        if (lane == 0) {
+            for (int k = st; k < nt_cta; ++k) {
+                const int s = k % st;
+                const uint32_t use = (uint32_t)(k / st);   // >= 1: the slot's previous tile was k - st
+                if (!mbar_wait_or_abort(&empty[s], (use - 1u) & 1u, &abort_flag)) {
+                    abort_flag = 1;
+                    break;
+                }
+                load_tile(ring + s * kSymTile, tiles + entry_tile(tl[k], G) * kSymTile, &full[s], pol);
+                ++issued;
+            }
+        }
+    } else {
+        const int rg = tid >> 4, cq = tid & 15;
+        float* yc = yw + warp * span_max;   // this warp's copy (index p - p_lo)
+        float acc[8], xa[8];
+        int cur = -1, slot = 0;
+        uint32_t phase = 0;
+        bool bad = false;
+        auto flush = [&](int row) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                float v = acc[r];
+#pragma unroll
+                for (int o = 1; o < 16; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (cq == r) yc[row * kSymT + rg * 8 + r - p_lo] += v;
+            }
+            __syncwarp();
+        };
+        for (int k = 0; k < nt_cta; ++k) {
+            const uint32_t e = tl[k];
+            const int ca = (int)(e >> 16), cb = (int)((e >> 3) & 0x1fff), cf = (int)(e & 7);
+            if (ca != cur) {
+                if (cur >= 0) flush(cur);
+                cur = ca;
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    acc[r] = 0.0f;
+                    xa[r] = xsh[ca * kSymT + rg * 8 + r - p_lo];
+                }
+            }
+            const bool ok = __all_sync(0xffffffffu, mbar_wait_or_abort(&full[slot], phase, &abort_flag));
+            if (!ok) {
+                if (lane == 0) abort_flag = 1;
+                bad = true;
+                break;
+            }
+            const float4* T = reinterpret_cast<const float4*>(ring + slot * kSymTile) + rg * 8 * (kSymT / 4) + cq;
+            const float4 xb = (cf & 1) ? *reinterpret_cast<const float4*>(xsh + cb * kSymT + 4 * cq - p_lo)
+                                       : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            float4 col = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const float4 m = T[r * (kSymT / 4)];
+                acc[r] = fmaf(m.x, xb.x, fmaf(m.y, xb.y, fmaf(m.z, xb.z, fmaf(m.w, xb.w, acc[r]))));
+                col.x = fmaf(m.x, xa[r], col.x);
+                col.y = fmaf(m.y, xa[r], col.y);
+                col.z = fmaf(m.z, xa[r], col.z);
+                col.w = fmaf(m.w, xa[r], col.w);
+            }
+            __syncwarp();   // every lane is done with the slot
+            if (lane == 0) mbar_arrive(&empty[slot]);
+            if (cf & 2) {   // transposed role: the warp's 16 rows of column 4 cq .. 4 cq + 3, row group order
+                col.x += __shfl_xor_sync(0xffffffffu, col.x, 16);
+                col.y += __shfl_xor_sync(0xffffffffu, col.y, 16);
+                col.z += __shfl_xor_sync(0xffffffffu, col.z, 16);
+                col.w += __shfl_xor_sync(0xffffffffu, col.w, 16);
+                if (lane < 16) {
+                    float4* yp = reinterpret_cast<float4*>(yc + cb * kSymT + 4 * cq - p_lo);
+                    float4 yv = *yp;
+                    if (cf & 4) {
+                        yv.x -= col.x;
+                        yv.y -= col.y;
+                        yv.z -= col.z;
+                        yv.w -= col.w;
+                    } else {
+                        yv.x += col.x;
+                        yv.y += col.y;
+                        yv.z += col.z;
+                        yv.w += col.w;
+                    }
+                    *yp = yv;
+                }
+                __syncwarp();
+            }
+            if (++slot == st) {
+                slot = 0;
+                phase ^= 1u;
+            }
+        }
+        if (!bad && cur >= 0) flush(cur);
+    }
+    __syncthreads();
+    if (abort_flag) {   // drain the copies still in flight (the last one of each slot), then report
+        if (tid == kT) {
+            for (int q = issued > st ? issued - st : 0; q < issued; ++q)
+                mbar_wait(&full[q % st], (uint32_t)(q / st) & 1u);
+            atomicExch(err, 1);
+        }
+        __syncthreads();
+    }
+    // the four warp copies, added in warp order into copy 0
+    for (int p = tid; p < span; p += kTW)
+        yw[p] = ((yw[p] + yw[span_max + p]) + yw[2 * span_max + p]) + yw[3 * span_max + p];
+    cluster_store(cluster, yw, sd, G, rmask, r_lo, p_lo, np, cl, go, tid, kTW);
 }
 
 // Pack: tile (a, b) of subdomain blockIdx.y from the swept FP64 matrix.
@@ -328,7 +521,10 @@ __global__ void k_sym_pack(const SymDesc* __restrict__ descs, const MatDesc* __r
 
 }  // namespace
 
-size_t sym_smem_bytes(const dd_handle* h) { return sym_smem(h->sym_np_max, kSymStages, h->sym_max_tiles); }
+size_t sym_smem_bytes(const dd_handle* h) {
+    return std::max(sym_smem(h->sym_np_max, kSymStages, h->sym_max_tiles),
+                    sym_smem_ws(h->sym_np_max, kSymStages, h->sym_max_tiles));
+}
 
 // Padded index range a mode touches in the largest subdomain (from its first group on).
 int sym_span(const dd_handle* h, int mode) {
@@ -376,20 +572,35 @@ void build_sym(dd_handle* h) {
             }
         }
         h->mode_bytes_sym[mode] = bytes;
+        // the mode's tiles of every subdomain in row order (what the kernel streams)
+        std::vector<uint32_t>& tl = h->sym_tl[mode];
+        std::vector<int64_t>& off = h->sym_tl_off[mode];
+        tl.clear();
+        off.assign(1, 0);
+        for (const SymDesc& sd : h->sym) {
+            for (int a = 0; a < sd.t0[3]; ++a)
+                for (int b = 0; b <= a; ++b) {
+                    const int f = sym_tile_flags(sd.t0, a, b, rmask, cmask);
+                    if (f & 3) tl.push_back(tile_entry(a, b, f));
+                }
+            off.push_back((int64_t)tl.size());
+        }
         sym_ranges(h, mode, h->sym_cl[mode]);
     }
 }
 
-// Tile-row range of each of the cl CTAs of every subdomain for `mode`:
-// contiguous ranges, CTA c ending where the running tile count comes closest
-// to (c + 1) / cl of the subdomain's total.
+// Work of each of the cl CTAs of every subdomain for `mode`: contiguous tile-row
+// ranges, CTA c ending where the running tile count comes closest to (c + 1) / cl
+// of the subdomain's total; stored as (first entry in the mode's tile list, tile
+// count, end tile row).
 void sym_ranges(dd_handle* h, int mode, int cl) {
     int rmask, cmask;
     h->sym_rng[mode].clear();
     h->sym_cl[mode] = cl;
     h->sym_nl[mode] = 0;
     if (!sym_masks(mode, &rmask, &cmask)) return;
-    for (const SymDesc& sd : h->sym) {
+    for (int s = 0; s < h->n_sub; ++s) {
+        const SymDesc& sd = h->sym[s];
         const int nt = sd.t0[3];
         std::vector<int64_t> per_row(nt, 0);
         int64_t total = 0;
@@ -399,7 +610,7 @@ void sym_ranges(dd_handle* h, int mode, int cl) {
             total += per_row[a];
         }
         int a = 0;
-        int64_t run = 0;
+        int64_t run = 0, first = h->sym_tl_off[mode][s];
         for (int c = 0; c < cl; ++c) {
             const int begin = a;
             if (c == cl - 1) {
@@ -409,10 +620,12 @@ void sym_ranges(dd_handle* h, int mode, int cl) {
                 while (a < nt && run + per_row[a] <= target) run += per_row[a++];
                 if (a < nt && target - run > run + per_row[a] - target) run += per_row[a++];
             }
-            h->sym_rng[mode].push_back(begin);
-            h->sym_rng[mode].push_back(a);
             int64_t n = 0;
             for (int q = begin; q < a; ++q) n += per_row[q];
+            h->sym_rng[mode].push_back((int32_t)first);
+            h->sym_rng[mode].push_back((int32_t)n);
+            h->sym_rng[mode].push_back(a);
+            first += n;
             h->sym_nl[mode] = std::max<int32_t>(h->sym_nl[mode], (int32_t)n);
         }
     }
@@ -433,17 +646,18 @@ int launch_symgemv(const dd_handle* h, int mode, XSrc xs, GemvOut go, const int3
     xs.sc = h->d.sc;
     const int span = sym_span(h, mode);
     const int st = h->sym_st[mode];
-    const size_t smem = sym_smem(span, st, h->sym_nl[mode]);
-    cudaError_t e = cudaFuncSetAttribute(k_symgemv, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sym_smem_bytes(h));
+    const bool ws = h->sym_ws[mode] != 0;
+    const size_t smem = ws ? sym_smem_ws(span, st, h->sym_nl[mode]) : sym_smem(span, st, h->sym_nl[mode]);
+    auto kern = ws ? k_symgemv_ws : k_symgemv;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sym_smem_bytes(h));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_symgemv, cudaFuncAttributePreferredSharedMemoryCarveout,
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return (int)e;
     const int cl = h->sym_cl[mode];
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(h->n_sub * cl));
-    cfg.blockDim = dim3(kT);
+    cfg.blockDim = dim3(ws ? kTW : kT);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = S(stream);
     cudaLaunchAttribute at[1];
@@ -453,7 +667,7 @@ int launch_symgemv(const dd_handle* h, int mode, XSrc xs, GemvOut go, const int3
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return (int)cudaLaunchKernelEx(&cfg, k_symgemv, (const SymDesc*)h->d.symd, (const int32_t*)h->d.sym_rng[mode],
-                                   (const float*)h->d.Msym, span, cl, st, rmask, cmask, h->sym_keep[mode], xs, go, skip,
-                                   &h->d.sc->wait_err);
+    return (int)cudaLaunchKernelEx(&cfg, kern, (const SymDesc*)h->d.symd, (const int32_t*)h->d.sym_rng[mode],
+                                   (const uint32_t*)h->d.sym_tl[mode], (const float*)h->d.Msym, span, cl, st, rmask,
+                                   cmask, h->sym_keep[mode], xs, go, skip, &h->d.sc->wait_err);
 }

@@ -110,4 +110,47 @@ __device__ __forceinline__ float xsrc_value_f(const XSrc& xs, int64_t slot, int6
     }
 }
 
+// Where the FP32 value of one slot comes from, from its pre-loaded slot_mult (m)
+// and slot_corner (c) entries: value = sgn * (a[i] + beta * b[i]) (b may be
+// null), 0 when a is null.  Lets a caller issue the index loads of several
+// slots, then their value loads, without a dependent chain per slot; the
+// values equal xsrc_value_f's bit for bit (the sign is a multiplication by +-1).
+struct XRef {
+    const float* a;
+    const float* b;
+    int64_t i;
+    float sgn;
+};
+
+__device__ __forceinline__ XRef xsrc_ref_f(const XSrc& xs, int m, int c, int64_t slot, int64_t j) {
+    const XRef none{nullptr, nullptr, 0, 1.0f};
+    const int mi = (m > 0 ? m : -m) - 1;
+    const float ms = m > 0 ? 1.0f : -1.0f;
+    switch (xs.kind) {
+        case X_FLAT: return {xs.vf, nullptr, slot, 1.0f};
+        case X_LAMBDA: return m != 0 ? XRef{xs.vf, nullptr, mi, ms} : none;
+        case X_PCG: return m != 0 ? XRef{xs.vf, xs.v2f, mi, ms} : none;
+        case X_CORNER: return c >= 0 ? XRef{xs.vf, nullptr, c, 1.0f} : none;
+        case X_RECOVER:
+            if (m != 0) return {xs.vf, nullptr, mi, -ms};
+            return c >= 0 ? XRef{xs.v2f, nullptr, c, 1.0f} : none;
+        case X_PCG_CV:
+            if (m != 0) return {xs.vf, xs.v2f, mi, ms};
+            return c >= 0 ? XRef{xs.v3f, nullptr, c, -1.0f} : none;
+        case X_LAMBDA_CV:
+            if (m != 0) return {xs.vf, nullptr, mi, ms};
+            return c >= 0 ? XRef{xs.v3f, nullptr, c, -1.0f} : none;
+        case X_SIDE_CP:
+            if (m != 0) return m > 0 ? XRef{xs.vf, nullptr, mi, 1.0f} : XRef{xs.v2f, nullptr, mi, 1.0f};
+            return c >= 0 ? XRef{xs.v3f, nullptr, c, 1.0f} : none;
+        default: return {xs.vf, nullptr, j, 1.0f};
+    }
+}
+
+__device__ __forceinline__ float xref_value(const XRef& r, float beta) {
+    if (!r.a) return 0.0f;
+    const float v = r.b ? fmaf(beta, r.b[r.i], r.a[r.i]) : r.a[r.i];
+    return r.sgn * v;
+}
+
 }  // namespace

@@ -24,11 +24,9 @@ DD_SCHEME_DP1, DD_SCHEME_DP2 = 0, 1
 
 SYMBOLS = ["dd_setup", "dd_set_params", "dd_get_sizes", "dd_get_maps", "dd_set_probes", "dd_bind_workspace",
            "dd_factor", "dd_step", "dd_schur_apply", "dd_schur_apply_static", "dd_coupled_apply", "dd_dp2_apply",
-           "dd_get_interface_mass", "dd_probe", "dd_adjoint_reset",
-           "dd_adjoint_step", "dd_probe_seed", "dd_autotune", "dd_get_tiles", "dd_get_sym_config", "dd_set_beam",
-           "dd_pic_step",
-           "dd_pic_state", "dd_get_state", "dd_set_state", "dd_profile",
-           "dd_destroy", "dd_last_error"]
+           "dd_get_interface_mass", "dd_probe", "dd_adjoint_reset", "dd_adjoint_step", "dd_probe_seed", "dd_autotune",
+           "dd_get_tiles", "dd_get_sym_config", "dd_set_sym_config", "dd_set_beam", "dd_pic_step", "dd_pic_state",
+           "dd_get_state", "dd_set_state", "dd_profile", "dd_destroy", "dd_last_error"]
 N_STAGES = 9
 STAGES = ["rhs", "local_solve", "iface_apply", "coarse", "corner", "recover", "vector", "refine", "factor"]
 
@@ -100,7 +98,9 @@ def load_library(path: str = LIB_PATH):
         "dd_probe_seed": (C.c_int, [vp, vp, C.c_double, vp, vp]),
         "dd_autotune": (C.c_int, [vp, C.c_char_p, C.POINTER(C.c_double), vp]),
         "dd_get_tiles": (C.c_int, [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
-        "dd_get_sym_config": (C.c_int, [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+        "dd_get_sym_config": (C.c_int, [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                        C.POINTER(C.c_int32)]),
+        "dd_set_sym_config": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, vp]),
         "dd_set_beam": (C.c_int, [vp, C.POINTER(dd_beam)]),
         "dd_pic_step": (C.c_int, [vp, C.POINTER(dd_stats), vp]),
         "dd_pic_state": (C.c_int, [vp, vp, vp, vp, vp, C.POINTER(C.c_int64), vp]),
@@ -319,13 +319,20 @@ def dd_get_tiles(h):
 
 
 def dd_get_sym_config(h):
-    """Packed symmetric GEMV kinds: {kind: (CTAs per subdomain, TMA ring depth, subdomains kept in L2)}."""
+    """Packed symmetric GEMV kinds: {kind: (CTAs per subdomain, TMA ring depth, subdomains kept in L2,
+    kernel form: 1 warp-specialised, 0 CTA-synchronous)}."""
     nk = len(GEMV_KINDS)
     cl = (C.c_int32 * nk)()
     st = (C.c_int32 * nk)()
     keep = (C.c_int32 * nk)()
-    _check(h, lib().dd_get_sym_config(h, cl, st, keep))
-    return {GEMV_KINDS[k]: (cl[k], st[k], keep[k]) for k in range(nk) if cl[k]}
+    ws = (C.c_int32 * nk)()
+    _check(h, lib().dd_get_sym_config(h, cl, st, keep, ws))
+    return {GEMV_KINDS[k]: (cl[k], st[k], keep[k], ws[k]) for k in range(nk) if cl[k]}
+
+
+def dd_set_sym_config(h, kind, cl, st, keep=0, ws=0):
+    """Pins the packed-tile launch of GEMV kind `kind` ("local", "iface_rows" or "coupled")."""
+    _check(h, lib().dd_set_sym_config(h, GEMV_KINDS.index(kind), cl, st, keep, ws, _stream()))
 
 
 def dd_profile(h, enable=-1, read=True, stream=None):

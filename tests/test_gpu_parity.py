@@ -40,10 +40,12 @@ def oracle_run(w, dt, n, keep=True):
     return space, T, S, src, out
 
 
-def gpu_run(w, dt, n, params, keep=True, probes=True):
+def gpu_run(w, dt, n, params, keep=True, probes=True, after_factor=None):
     fs = D.FieldSolver(w.xyz, w.tets, w.part, w.n_sub, w.eps, w.mu, params,
                        probes=w.probes if probes and len(w.probes) else None).bind()
     fs.factor(dt)
+    if after_factor:
+        after_factor(fs)
     dofs = fs.dof_of_pairs(w.source_pairs)
     src = torch.zeros(fs.n_dof, dtype=torch.float64, device="cuda")
     d2g = w.d2G(dt, n)
@@ -236,12 +238,18 @@ def test_extrapolated_warm_start_matches_oracle(prec):
     fs.close()
 
 
+PACKED_KINDS = ("local", "iface_rows", "coupled")
+
+
 @pytest.mark.parametrize("solver", [D.DD_SOLVER_SCHUR_CG, D.DD_SOLVER_COUPLED_GMRES])
 def test_packed_symmetric_fp32_tiles(solver):
     """DD_MIXED with the packed lower-triangular FP32 tiles (sym_fp32 = 1) and with
     the dense FP32 copy (0), on a jittered RCB split whose group sizes are not
-    multiples of the tile edge: both within 1e-8 of the monolithic fields, with
-    about the same iteration counts, and the packed path deterministic."""
+    multiples of the tile edge: within 1e-8 of the monolithic fields, with about
+    the same iteration counts, and the packed path deterministic -- for both
+    kernel forms (CTA-synchronous, warp-specialised) over cluster sizes 1..8,
+    ring depths 2..4 and L2-kept subdomain counts (clusters of 8 leave some CTAs
+    of these small subdomains without tiles)."""
     need_gpu()
     nx, ny, nz = 10, 8, 8
     L = (1.2, 1.0, 1.0)
@@ -255,19 +263,49 @@ def test_packed_symmetric_fp32_tiles(solver):
     dt = 2.0 * newmark.cfl_dt(T, S)
     n = 30
     _, _, _, _, ref = oracle_run(w, dt, n)
+
+    def pin(cl, st, keep, ws):
+        def f(fs):
+            for kind in PACKED_KINDS:
+                D.dd_set_sym_config(fs.h, kind, cl, st, keep, ws)
+            cfg = D.dd_get_sym_config(fs.h)
+            assert all(cfg[k] == (cl, st, keep, ws) for k in PACKED_KINDS), cfg
+        return f
+
+    cases = [("dense", 0, None), ("packed", 1, None), ("packed", 1, None),
+             ("ws 2x3 keep 2", 1, pin(2, 3, 2, 1)), ("ws 1x2", 1, pin(1, 2, 0, 1)),
+             ("ws 8x4 keep 6", 1, pin(8, 4, 6, 1)), ("ws 8x4 keep 6", 1, pin(8, 4, 6, 1)),
+             ("sync 8x4 keep 3", 1, pin(8, 4, 3, 0))]
     runs = {}
-    for sym in (1, 0, 1):
+    for name, sym, hook in cases:
         prm = D.make_params(precision=D.DD_MIXED, tol=1e-5, refine_tol=1e-12, max_refine=6, solver=solver,
                             sym_fp32=sym)
-        fs, f, _, stats = gpu_run(w, dt, n, prm, probes=False)
+        fs, f, _, stats = gpu_run(w, dt, n, prm, probes=False, after_factor=hook)
         fs.close()
-        assert all(s["status"] == 0 for s in stats)
-        assert rel_err(f, ref["fields"])[2:].max() <= 1e-8, (sym, rel_err(f, ref["fields"]).max())
+        assert all(s["status"] == 0 for s in stats), name
+        assert rel_err(f, ref["fields"])[2:].max() <= 1e-8, (name, rel_err(f, ref["fields"]).max())
         its = np.array([s["iters"] for s in stats])
-        if sym in runs:
-            assert np.array_equal(runs[sym][0], f)           # deterministic
+        if name in runs:
+            assert np.array_equal(runs[name][0], f), name          # deterministic
         else:
-            runs[sym] = (f, its)
-    # the first steps (tiny right-hand sides) are the most rounding-sensitive
-    assert np.all(np.abs(runs[1][1][2:] - runs[0][1][2:]) <= 3), (runs[1][1], runs[0][1])
-    assert abs(runs[1][1].sum() - runs[0][1].sum()) <= 0.05 * runs[0][1].sum()
+            runs[name] = (f, its)
+    dense = runs["dense"][1]
+    for name, (f, its) in runs.items():
+        # the first steps (tiny right-hand sides) are the most rounding-sensitive
+        assert np.all(np.abs(its[2:] - dense[2:]) <= 3), (name, its, dense)
+        assert abs(its.sum() - dense.sum()) <= 0.05 * dense.sum(), (name, its, dense)
+
+
+def test_sym_config_rejects_bad_values():
+    need_gpu()
+    w = W.config(1)
+    fs = D.FieldSolver(w.xyz, w.tets, w.part, w.n_sub, w.eps, w.mu,
+                       D.make_params(precision=D.DD_MIXED, tol=1e-5)).bind()
+    fs.factor(DT["config1"]["dt"])
+    for args in [("corner_rows", 1, 2, 0, 0), ("local", 3, 2, 0, 0), ("local", 1, 5, 0, 0), ("local", 1, 1, 0, 0),
+                 ("local", 1, 2, w.n_sub + 1, 0), ("local", 1, 2, 0, 2)]:
+        with pytest.raises(RuntimeError):
+            D.dd_set_sym_config(fs.h, *args)
+    D.dd_set_sym_config(fs.h, "coupled", 2, 4, 1, 1)
+    assert D.dd_get_sym_config(fs.h)["coupled"] == (2, 4, 1, 1)
+    fs.close()
