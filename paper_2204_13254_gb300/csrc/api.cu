@@ -203,6 +203,7 @@ size_t dd_workspace_layout(dd_handle* h, bool assign) {
     L.take(d.mult_slot, 2 * nm);
     L.take(d.corner_ptr, nc + 1);
     L.take(d.corner_slot, h->corner_slot.size());
+    L.take(d.slot_upos, h->slot_upos.size());
     L.take(d.owner_slot, nd);
     L.take(d.copy_ptr, nd + 1);
     L.take(d.copy_slot, nl);
@@ -370,6 +371,14 @@ XSrc xsrc(int kind, const double* v, const double* v2, const float* vf, const fl
 // (out32) and, where a double consumer exists, the double output too.
 GemvOut gout(double* out, const double* base, float* out32, const float* base32, double alpha) {
     return GemvOut{out, base, out32, base32, alpha};
+}
+
+// Output of the coupled operator's GEMV, in the order the GMRES combine reads:
+// both sides of every multiplier, then the corner copies.
+GemvOut gout_coupled(const dd_handle* h, double* out, float* out32) {
+    GemvOut go = gout(out, nullptr, out32, nullptr, 1.0);
+    go.pos = h->d.slot_upos;
+    return go;
 }
 
 // w <- interface operator pieces for x-source (kind, v, v2) of Eq. f1schur:
@@ -543,7 +552,7 @@ int gmres_solve(dd_handle* h, int prec, double tol, bool warm, int* it_out, doub
     const XSrc xs_z = dp2 ? xsrc(X_SIDE_CP, h->d.zu, h->d.zu + nm, zuf, zuf ? zuf + nm : nullptr, h->d.zu + o2,
                                  zuf ? zuf + o2 : nullptr)
                           : xsrc(X_LAMBDA_CV, h->d.zu, nullptr, zuf, nullptr, h->d.zu + nm, zuf ? zuf + nm : nullptr);
-    const GemvOut go = V.f32 ? gout(nullptr, nullptr, V.wf, nullptr, 1.0) : gout(h->d.w, nullptr, nullptr, nullptr, 1.0);
+    const GemvOut go = V.f32 ? gout_coupled(h, nullptr, V.wf) : gout_coupled(h, h->d.w, nullptr);
     const double mbc = mb(h, GEMV_COUPLED, prec);
     const int32_t* skip = &h->d.gs->skip;
     auto cycle_start = [&](cudaStream_t st, int have_q, unsigned long long cond_inner) -> int {
@@ -939,6 +948,7 @@ int dd_bind_workspace(dd_handle* h, void* dev, size_t bytes, void* stream) {
     CK(h, upload(h->d.slot_sub, h->slot_sub, s), "upload");
     CK(h, upload(h->d.slot_own, h->slot_own, s), "upload");
     CK(h, upload(h->d.mult_slot, h->mult_slot, s), "upload");
+    CK(h, upload(h->d.slot_upos, h->slot_upos, s), "upload");
     CK(h, upload(h->d.corner_ptr, h->corner_ptr, s), "upload");
     CK(h, upload(h->d.corner_slot, h->corner_slot, s), "upload");
     CK(h, upload(h->d.owner_slot, h->owner_slot, s), "upload");
@@ -1500,7 +1510,7 @@ int dd_coupled_apply(dd_handle* h, const double* u, double* out, void* stream) {
     {
         Prof P(h, ST_SCHUR, s, 1, mb(h, GEMV_COUPLED, DD_FP64));
         CK(h, launch_gemv(h, GEMV_COUPLED, DD_FP64, xsrc(X_LAMBDA_CV, u, nullptr, nullptr, nullptr, u + nm, nullptr),
-                          gout(h->d.w, nullptr, nullptr, nullptr, 1.0), false, s), "coupled operator");
+                          gout_coupled(h, h->d.w, nullptr), false, s), "coupled operator");
     }
     Prof P(h, ST_VEC, s, 1);
     CK(h, launch_gm_combine(h, uview(h, DD_FP64), u, out, s), "combine");
@@ -1518,7 +1528,7 @@ int dd_dp2_apply(dd_handle* h, const double* u, double* out, void* stream) {
         Prof P(h, ST_SCHUR, s, 1, mb(h, GEMV_COUPLED, DD_FP64));
         CK(h, launch_gemv(h, GEMV_COUPLED, DD_FP64,
                           xsrc(X_SIDE_CP, u, u + nm, nullptr, nullptr, u + 2 * nm, nullptr),
-                          gout(h->d.w, nullptr, nullptr, nullptr, 1.0), false, s), "DP2 operator");
+                          gout_coupled(h, h->d.w, nullptr), false, s), "DP2 operator");
     }
     Prof P(h, ST_VEC, s, 1);
     CK(h, launch_gm_combine(h, uview(h, DD_FP64), u, out, s), "combine");

@@ -130,13 +130,15 @@ struct XSrc {
 };
 
 // Output of a batched GEMV: out[voff+row] = base + alpha * (M x)_row, written in
-// FP64 (out/base) and/or FP32 (out32/base32; FP32 arithmetic).
+// FP64 (out/base) and/or FP32 (out32/base32; FP32 arithmetic).  pos (may be
+// null; then base is null too): the row of slot o is written at out[pos[o]].
 struct GemvOut {
     double* out;
     const double* base;
     float* out32;
     const float* base32;
     double alpha;
+    const int32_t* pos = nullptr;
 };
 
 // Tile shape of a batched GEMV launch: lanes cooperating on one row and rows
@@ -243,6 +245,8 @@ struct DevPtrs {
     int64_t* mult_slot = nullptr;    // [n_lambda*2] slots of s1 and s2
     int64_t* corner_ptr = nullptr;   // [n_corner+1]
     int64_t* corner_slot = nullptr;  // copies of every corner, by subdomain
+    int32_t* slot_upos = nullptr;    // [n_local] where the coupled operator writes a slot's row: 2 m + side for
+                                     // multiplier m, 2 n_lambda + k for corner copy k, -1 for interior slots
     int64_t* owner_slot = nullptr;   // [n_dof] slot in the owner subdomain
     int64_t* row_ptr = nullptr;      // local CSR over slots [n_local+1]
     int32_t* col_loc = nullptr;      // local column index
@@ -386,6 +390,7 @@ struct dd_handle {
     std::vector<int32_t> slot_mult, slot_corner, slot_dof;
     std::vector<uint8_t> slot_own;
     std::vector<int64_t> mult_slot, corner_ptr, corner_slot, owner_slot;
+    std::vector<int32_t> slot_upos;
     std::vector<int32_t> slot_sub;
     std::vector<int64_t> copy_ptr, copy_slot;
     std::vector<int64_t> row_ptr;

@@ -70,18 +70,21 @@ struct UIn {
     }
 };
 
-// (M u)_i from the GEMV output per slot (w, or its FP32 form wf).
+// (M u)_i from the coupled operator's GEMV output w (or its FP32 form wf),
+// stored as both sides of every multiplier (w[2 m + side]) followed by the
+// copies of every corner (w[2 n1 + k], k in [cp[c], cp[c+1])).
 // MFETI-DP1: jump over multiplier i; minus the assembly over the copies of a corner.
 // MFETI-DP2: u1_k + u2_k - 2 alpha (M_T t)_k with t the interface traces of the
 // other side (side 2 for block 1, side 1 for block 2); plus the assembly over
 // the copies of a corner (the multipliers enter the local problems with +).
 __device__ __forceinline__ double combine(int64_t i, const UView& U, const double* __restrict__ w,
                                           const float* __restrict__ wf, const UIn& in) {
+    const int64_t wc = 2 * U.n1;   // first corner copy
     if (!U.mtp) {
-        if (i < U.n1) return wv(w, wf, U.ms[2 * i]) - wv(w, wf, U.ms[2 * i + 1]);
+        if (i < U.n1) return wv(w, wf, 2 * i) - wv(w, wf, 2 * i + 1);
         const int64_t c = i - U.n1;
         double s = 0.0;
-        for (int64_t k = U.cp[c]; k < U.cp[c + 1]; ++k) s += wv(w, wf, U.cs[k]);
+        for (int64_t k = U.cp[c]; k < U.cp[c + 1]; ++k) s += wv(w, wf, wc + k);
         return -s;
     }
     if (i < U.n1 + U.n2) {
@@ -89,37 +92,32 @@ __device__ __forceinline__ double combine(int64_t i, const UView& U, const doubl
         const int64_t k = first ? i : i - U.n1;
         const int other = first ? 1 : 0;
         double acc = 0.0;
-        for (int64_t p = U.mtp[k]; p < U.mtp[k + 1]; ++p) acc += U.mtv[p] * wv(w, wf, U.ms[2 * (int64_t)U.mtc[p] + other]);
+        for (int64_t p = U.mtp[k]; p < U.mtp[k + 1]; ++p) acc += U.mtv[p] * wv(w, wf, 2 * (int64_t)U.mtc[p] + other);
         return in.sum(k) - U.two_alpha * acc;
     }
     const int64_t c = i - U.n1 - U.n2;
     double s = 0.0;
-    for (int64_t k = U.cp[c]; k < U.cp[c + 1]; ++k) s += wv(w, wf, U.cs[k]);
+    for (int64_t k = U.cp[c]; k < U.cp[c + 1]; ++k) s += wv(w, wf, wc + k);
     return s;
 }
 
-// combine() of MFETI-DP1 for the kE elements i0 + e kT of one thread: the index
-// loads of all of them first, then their value loads (corner copies four at a
-// time), so that a thread waits for a few round trips instead of one per load.
-// Same sums in the same order as combine().
+// combine() of MFETI-DP1 for the E elements i0 + e stride of one thread: the
+// multiplier pairs are adjacent in w; a corner's copies are contiguous and
+// loaded four at a time.  Same sums in the same order as combine().
 template <int E, typename VT>
 __device__ __forceinline__ void combine_dp1(int64_t i0, int stride, const UView& U, const double* __restrict__ w,
                                             const float* __restrict__ wf, VT* t) {
-    const int64_t nu = U.n1 + U.nc;
-    int64_t a[E], b[E];
+    const int64_t nu = U.n1 + U.nc, wc = 2 * U.n1;
+    double va[E], vb[E];
+    int64_t k0[E], k1[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const int64_t i = i0 + (int64_t)e * stride;
-        const int64_t* base = i < U.n1 ? U.ms + 2 * i : U.cp + (i - U.n1);
-        a[e] = i < nu ? base[0] : 0;
-        b[e] = i < nu ? base[1] : 0;
-    }
-    double va[E], vb[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const bool mult = i0 + (int64_t)e * stride < U.n1;
-        va[e] = mult ? wv(w, wf, a[e]) : 0.0;
-        vb[e] = mult ? wv(w, wf, b[e]) : 0.0;
+        const bool mult = i < U.n1, corner = !mult && i < nu;
+        va[e] = mult ? wv(w, wf, 2 * i) : 0.0;
+        vb[e] = mult ? wv(w, wf, 2 * i + 1) : 0.0;
+        k0[e] = corner ? U.cp[i - U.n1] : 0;
+        k1[e] = corner ? U.cp[i - U.n1 + 1] : 0;
     }
 #pragma unroll
     for (int e = 0; e < E; ++e) {
@@ -128,16 +126,13 @@ __device__ __forceinline__ void combine_dp1(int64_t i0, int stride, const UView&
             t[e] = (VT)(va[e] - vb[e]);
         } else if (i < nu) {
             double sum = 0.0;
-            for (int64_t k0 = a[e]; k0 < b[e]; k0 += 4) {
-                int64_t sl[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) sl[q] = k0 + q < b[e] ? U.cs[k0 + q] : -1;
+            for (int64_t k = k0[e]; k < k1[e]; k += 4) {
                 double v[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) v[q] = sl[q] >= 0 ? wv(w, wf, sl[q]) : 0.0;
+                for (int q = 0; q < 4; ++q) v[q] = k + q < k1[e] ? wv(w, wf, wc + k + q) : 0.0;
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
-                    if (sl[q] >= 0) sum += v[q];
+                    if (k + q < k1[e]) sum += v[q];
             }
             t[e] = (VT)(-sum);
         } else {

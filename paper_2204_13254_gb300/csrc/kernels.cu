@@ -384,16 +384,17 @@ __device__ __forceinline__ float stage_value<float>(const XSrc& xs, int64_t slot
 
 template <typename TM>
 __device__ __forceinline__ void gemv_store(const GemvOut& go, int64_t o, TM acc, TM alpha_t) {
+    const int64_t oo = go.pos ? (int64_t)go.pos[o] : o;
     if (go.out32) {
         float v = (float)alpha_t * (float)acc;
         if (go.base32) v += go.base32[o];
-        go.out32[o] = v;
+        go.out32[oo] = v;
     }
     if (go.out) {
         double v = (double)acc;
         if (go.alpha != 1.0) v *= go.alpha;
         if (go.base) v += go.base[o];
-        go.out[o] = v;
+        go.out[oo] = v;
     }
 }
 

@@ -337,6 +337,10 @@ int dd_build_host(dd_handle* h, const dd_mesh* mesh, const int32_t* part, int32_
         for (int64_t i = 0; i < n_local; ++i)  // subdomain order
             if (h->slot_corner[i] >= 0) h->corner_slot[fill[h->slot_corner[i]]++] = i;
     }
+    // coupled-operator output order: the two sides of every multiplier, then the corner copies
+    h->slot_upos.assign(n_local, -1);
+    for (int64_t k = 0; k < 2 * nl; ++k) h->slot_upos[h->mult_slot[k]] = (int32_t)k;
+    for (int64_t k = 0; k < h->corner_ptr[nc]; ++k) h->slot_upos[h->corner_slot[k]] = (int32_t)(2 * nl + k);
 
     // ---- subassembled local CSR (rows = slots, per subdomain) -----------------
     std::vector<std::vector<int64_t>> tets_of(n_sub);

@@ -182,16 +182,17 @@ __device__ __forceinline__ void cluster_store(cg::cluster_group& cluster, const 
         for (int c = 0; c < kSymCLMax; ++c)
             if (c < cl) v += part[c];
         const int64_t o = sd.voff + G.start(g) + q;
+        const int64_t oo = go.pos ? (int64_t)go.pos[o] : o;
         if (go.out32) {
             float w = (float)go.alpha * v;
             if (go.base32) w += go.base32[o];
-            go.out32[o] = w;
+            go.out32[oo] = w;
         }
         if (go.out) {
             double w = (double)v;
             if (go.alpha != 1.0) w *= go.alpha;
             if (go.base) w += go.base[o];
-            go.out[o] = w;
+            go.out[oo] = w;
         }
     }
     cluster.sync();   // no CTA leaves while another reads its shared memory
