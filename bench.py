@@ -69,6 +69,8 @@ def parse():
                     help="interface solver of the headline runs: Schur CG (Eq. f1schur) or coupled GMRES(20)")
     ap.add_argument("--no-sym", action="store_true",
                     help="DD_MIXED GEMVs on the dense FP32 copy instead of the packed symmetric tiles")
+    ap.add_argument("--ensemble", type=int, default=4,
+                    help="members of the multi-RHS (ensemble) run beside the headline; 0 or 1 skips it")
     ap.add_argument("--no-dp2", action="store_true",
                     help="skip the MFETI-DP2 runs (its own factorisation; coupled GMRES(20), FP64 at tol 1e-6 and mixed)")
     ap.add_argument("--no-gmres", action="store_true",
@@ -396,6 +398,59 @@ def run_ours(args, rank, world, local):
                          "rel_err_vs_fp64_dp1": (float(torch.linalg.norm(em - e64) / torch.linalg.norm(e64))
                                                  if e64 is not None else None)}}
 
+    # multi-RHS batching: R members (the headline source at amplitudes 1, -1/2, 2, 1/4, ...) marched
+    # together with one copy of the factored operators, headline mixed settings, coupled GMRES
+    ens = None
+    if args.ensemble > 1 and not pic:
+        R = args.ensemble
+        pe = D.make_params(precision=D.DD_MIXED, tol=args.tol32, refine_tol=args.refine_tol, max_refine=6,
+                           use_graph=g, chunk=ch, solver=D.DD_SOLVER_COUPLED_GMRES, sym_fp32=sym, members=R)
+        t0 = time.perf_counter()
+        fe = D.FieldSolver(w.xyz, w.tets, w.part, w.n_sub, w.eps, w.mu, pe, device=dev).bind()
+        t_se = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fe.factor(dt)
+        torch.cuda.synchronize()
+        t_fe = time.perf_counter() - t0
+        if not args.no_autotune:
+            D.dd_autotune(fe.h, args.tune_cache)
+        amps = [[1.0, -0.5, 2.0, 0.25][r % 4] * (1 + r // 4) for r in range(R)]
+        ne = fe.n_dof
+        De = torch.zeros((Wu + K, ne), dtype=torch.float64, device=dev)
+        for r in range(R):
+            de = torch.tensor(fe.dof_of_pairs(w.source_pairs, member=r), device=dev)
+            for k in range(Wu + K):
+                De[k, de] = amps[r] * float(d2g[k])
+        for k in range(Wu):
+            fe.step(De[k], stats=True)
+        barrier()
+        torch.cuda.synchronize()
+        fe.profile(enable=1, read=False)
+        fe.profile(enable=0, read=False)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        ite, rfe = [], []
+        for k in range(K):
+            st = fe.step(De[Wu + k], stats=True)
+            ite.append(st["iters"])
+            rfe.append(st["refinements"])
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        mse = ev0.elapsed_time(ev1)
+        pe_prof = fe.profile(enable=0, read=True)
+        ee, _, _ = fe.get_state()
+        ee = ee.view(R, -1)
+        ens = {"members": R, "amplitudes": amps, "member_steps_per_s": R * K * 1e3 / mse, "ms_per_step": mse / K,
+               "iters_per_step": float(np.mean(ite)), "refinements_per_step": float(np.mean(rfe)),
+               "gpu_launches": int(pe_prof["total_launches"]), "setup_s": t_se, "factor_s": t_fe,
+               "operator_bytes_fp64": int(fe.sizes.dense_bytes_fp64),
+               "rel_err_member0_vs_single_mixed": (float(torch.linalg.norm(ee[0] - e32) / torch.linalg.norm(e32))
+                                                   if e32 is not None and args.solver == "gmres" else None)}
+        fe.close()
+        del De
+
     def allmax(x):
         if world == 1:
             return x
@@ -407,7 +462,7 @@ def run_ours(args, rank, world, local):
     sizes = fs.sizes
     res = dict(fs=fs, K=K, ms64=ms64, ms32=ms32, ms_e2e=ms_e2e, it64=it64, it32=it32, ref32=ref32, prof64=prof64,
                prof32=prof32, rel=rel, launches64=launches64, launches32=launches32, t_setup=t_setup, t_factor=t_factor, clocks=clocks.summary(), sizes=sizes,
-               workload=w, dt=dt, t_tune=t_tune, tiles=tiles, pic=pic, gmres=gm, dp2=dp2)
+               workload=w, dt=dt, t_tune=t_tune, tiles=tiles, pic=pic, gmres=gm, dp2=dp2, ens=ens)
     return res
 
 
@@ -547,6 +602,8 @@ def main():
         "speedup_mixed_vs_fp64": v32 / v64,
         "coupled_gmres_vs_schur_cg": r["gmres"],
         "mfeti_dp2": r["dp2"],
+        "ensemble": (dict(r["ens"], member_steps_vs_single=r["ens"]["member_steps_per_s"] / v32)
+                     if r["ens"] else None),
         "rel_err_mixed_vs_fp64": r["rel"],
         "setup_s": r["t_setup"], "factor_s": r["t_factor"], "autotune_s": r["t_tune"],
         "gemv_tiles": r["tiles"],

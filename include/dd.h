@@ -139,7 +139,24 @@ typedef struct {
  *            interface rows, coupled operator) read packed lower-triangular
  *            FP32 tiles (the swept local matrix is J times a symmetric matrix,
  *            J = diag(I_r, -I_c)), about 60 % of the dense bytes; 0 = the
- *            dense FP32 copy.  Results differ by FP32 rounding only. */
+ *            dense FP32 copy.  Results differ by FP32 rounding only.
+ * members    Ensemble size R, 1..64 (fixed by dd_setup; dd_set_params must keep
+ *            it).  R > 1 marches R independent field problems on the same mesh,
+ *            materials and dt at once (multi-RHS batching): member r is copy r
+ *            of the mesh -- node ids offset by r * n_nodes, subdomain ids by
+ *            r * n_sub -- so its dofs, multipliers and corners follow those of
+ *            member r - 1, and every vector (source, fields, multipliers) holds
+ *            the R members one after the other.  The factored local operators
+ *            are computed and stored once and read by every member: the GEMVs
+ *            visit the R copies of a subdomain together, so that one read from
+ *            HBM serves them through L2.  The members' interface systems are
+ *            solved as one block-diagonal system: one Krylov iteration serves
+ *            all members and the stopping tests use the norms of the stacked
+ *            vectors (members of very different magnitude are solved to the
+ *            same absolute, not relative, accuracy).  R > 1 needs
+ *            DD_SOLVER_COUPLED_GMRES (the Schur CG would need the dense inverse
+ *            of the stacked coarse problem; DD_ERR_ARG otherwise); probes, the
+ *            PIC cycle, the adjoint and dd_schur_apply return DD_ERR_STATE. */
 typedef struct {
     int precision;
     double tol;
@@ -155,6 +172,7 @@ typedef struct {
     int sym_fp32;
     int scheme;
     double robin_alpha;
+    int members;
 } dd_params;
 
 /* Sizes of a set-up problem. */
@@ -169,7 +187,8 @@ typedef struct {
     int32_t max_nr;         /* largest local r block                          */
     int32_t max_ns;         /* largest local system (r + c)                   */
     size_t workspace_bytes; /* bytes dd_bind_workspace needs                  */
-    int64_t dense_bytes_fp64; /* bytes of the per-subdomain dense operators   */
+    int64_t dense_bytes_fp64; /* bytes of the per-subdomain dense operators (stored once for all members) */
+    int32_t members;        /* ensemble size R: n_dof, n_sub, n_lambda, ... count all members */
 } dd_sizes;
 
 /* Tearing maps, written to caller-allocated host arrays (any may be NULL).

@@ -50,6 +50,7 @@ dd_params default_params() {
     p.sym_fp32 = 1;
     p.scheme = DD_SCHEME_DP1;
     p.robin_alpha = 0.0;
+    p.members = 1;
     return p;
 }
 
@@ -69,6 +70,11 @@ int check_params(dd_handle* h, const dd_params& p) {
         if (p.restart < 1 || p.restart > kMaxRestart) return h->fail(DD_ERR_ARG, "restart must be in 1..DD_MAX_RESTART");
         if (p.warm_start == 2) return h->fail(DD_ERR_ARG, "warm_start 2 applies to the Schur CG only");
     }
+    if (p.members < 1 || p.members > kMaxMembers) return h->fail(DD_ERR_ARG, "members must be in 1..64");
+    if (p.members > 1 && p.solver != DD_SOLVER_COUPLED_GMRES)
+        return h->fail(DD_ERR_ARG, "an ensemble (members > 1) is solved by the coupled GMRES");
+    if (h->members > 0 && p.members != h->members)
+        return h->fail(DD_ERR_ARG, "members is fixed by dd_setup");
     return DD_OK;
 }
 
@@ -224,7 +230,7 @@ size_t dd_workspace_layout(dd_handle* h, bool assign) {
     for (int m = 0; m < GEMV_NMODES; ++m) {
         int rm, cm;
         if (sym_masks(m, &rm, &cm)) {
-            L.take(d.sym_rng[m], (size_t)h->n_sub * kSymCLMax * 3);
+            L.take(d.sym_rng[m], (size_t)h->n_sub * kSymCLMax * 4);
             L.take(d.sym_tl[m], std::max<size_t>(1, h->sym_tl[m].size()));
         }
     }
@@ -861,7 +867,27 @@ int dd_setup(const dd_mesh* mesh, const int32_t* part, int32_t n_sub, const dd_p
     int rc = check_params(h, h->prm);
     if (rc == DD_OK) {
         try {
-            rc = dd_build_host(h, mesh, part, n_sub);
+            const int R = h->prm.members;
+            h->members = R;
+            h->n_sub_real = n_sub;
+            if (R == 1) {
+                rc = dd_build_host(h, mesh, part, n_sub);
+            } else {
+                // member r = copy r of the mesh: node ids + r N, subdomain ids + r n_sub
+                const int64_t N = mesh->n_nodes, T = mesh->n_tets;
+                std::vector<double> xyz((size_t)(R * 3 * N)), eps;
+                std::vector<int32_t> tets((size_t)(R * 4 * T)), prt((size_t)(R * T));
+                if (mesh->eps) eps.resize((size_t)(R * T));
+                for (int r = 0; r < R; ++r) {
+                    std::copy(mesh->xyz, mesh->xyz + 3 * N, xyz.begin() + r * 3 * N);
+                    for (int64_t k = 0; k < 4 * T; ++k) tets[r * 4 * T + k] = mesh->tets[k] + (int32_t)(r * N);
+                    for (int64_t t = 0; t < T; ++t) prt[r * T + t] = part[t] + r * n_sub;
+                    if (mesh->eps) std::copy(mesh->eps, mesh->eps + T, eps.begin() + r * T);
+                }
+                if ((int64_t)R * N > INT32_MAX) rc = h->fail(DD_ERR_ARG, "ensemble mesh too large");
+                dd_mesh rep{R * N, R * T, xyz.data(), tets.data(), mesh->eps ? eps.data() : nullptr, mesh->mu};
+                if (rc == DD_OK) rc = dd_build_host(h, &rep, prt.data(), R * n_sub);
+            }
         } catch (const std::exception& ex) {
             rc = h->fail(DD_ERR_ARG, std::string("setup failed: ") + ex.what());
         }
@@ -893,6 +919,7 @@ int dd_get_sizes(const dd_handle* h, dd_sizes* o) {
     o->max_ns = h->max_ns;
     o->workspace_bytes = h->sub_ptr.empty() ? 0 : dd_workspace_layout(const_cast<dd_handle*>(h), false);
     o->dense_bytes_fp64 = h->dense_elems * 8;
+    o->members = h->members;
     return DD_OK;
 }
 
@@ -918,6 +945,7 @@ int dd_get_maps(const dd_handle* h, dd_maps* m) {
 
 int dd_set_probes(dd_handle* h, int32_t n, const double* xyz) {
     if (!h || n < 0 || n > kMaxProbes || (n > 0 && !xyz)) return h ? h->fail(DD_ERR_ARG, "bad probe list") : DD_ERR_ARG;
+    if (n > 0 && h->members > 1) return h->fail(DD_ERR_STATE, "probes are not available for an ensemble (members > 1)");
     int rc = dd_locate_probes(h, n, xyz);
     if (rc) return rc;
     if (h->bound && n > 0) {
@@ -1022,7 +1050,7 @@ int dd_factor(dd_handle* h, double dt, void* stream) {
         CK(h, launch_sweep(h, false, k0, s), "local elimination");
     }
     const int nc = (int)h->corner_dof.size();
-    if (nc) {
+    if (nc && h->ldc) {
         {
             Prof P(h, ST_FACTOR, s, 1);
             CK(h, launch_coarse_assemble(h, s), "coarse assemble");
@@ -1431,6 +1459,7 @@ int dd_step(dd_handle* h, const double* d2g, double* e_out, dd_stats* stats, voi
 
 int dd_adjoint_reset(dd_handle* h, void* stream) {
     if (!h) return DD_ERR_ARG;
+    if (h->members > 1) return h->fail(DD_ERR_STATE, "the adjoint is not available for an ensemble (members > 1)");
     if (!h->bound) return h->fail(DD_ERR_STATE, "no workspace bound");
     cudaStream_t s = (cudaStream_t)stream;
     for (int k = 0; k < 3; ++k) CK(h, (int)cudaMemsetAsync(h->d.mu[k], 0, sizeof(double) * h->n_dof, s), "memset");
@@ -1443,6 +1472,7 @@ int dd_adjoint_step(dd_handle* h, const double* seed, const double* e_k, const d
                     const double* d2g_hat, double* grad_eps, double* grad_amp, double* mu_out, dd_stats* stats,
                     void* stream) {
     if (!h || !seed) return DD_ERR_ARG;
+    if (h->members > 1) return h->fail(DD_ERR_STATE, "the adjoint is not available for an ensemble (members > 1)");
     if (!h->factored) return h->fail(DD_ERR_STATE, "dd_adjoint_step before dd_factor");
     if (grad_eps && (!e_k || !e_km1 || !e_km2)) return h->fail(DD_ERR_ARG, "grad_eps needs e_k, e_km1, e_km2");
     cudaStream_t s = (cudaStream_t)stream;
@@ -1480,6 +1510,7 @@ int dd_adjoint_step(dd_handle* h, const double* seed, const double* e_k, const d
 
 int dd_probe_seed(dd_handle* h, const double* e, double weight, double* seed, void* stream) {
     if (!h || !e || !seed) return DD_ERR_ARG;
+    if (h->members > 1) return h->fail(DD_ERR_STATE, "dd_probe_seed is not available for an ensemble (members > 1)");
     if (!h->bound) return h->fail(DD_ERR_STATE, "no workspace bound");
     cudaStream_t s = (cudaStream_t)stream;
     CK(h, (int)cudaMemsetAsync(seed, 0, sizeof(double) * h->n_dof, s), "memset");
@@ -1490,6 +1521,7 @@ int dd_probe_seed(dd_handle* h, const double* e, double weight, double* seed, vo
 
 int dd_schur_apply(dd_handle* h, const double* lam, double* out, void* stream) {
     if (!h || !lam || !out) return DD_ERR_ARG;
+    if (h->members > 1) return h->fail(DD_ERR_STATE, "dd_schur_apply is not available for an ensemble (members > 1)");
     if (!h->factored) return h->fail(DD_ERR_STATE, "dd_schur_apply before dd_factor");
     if (h->factored_scheme != DD_SCHEME_DP1) return h->fail(DD_ERR_STATE, "dd_schur_apply needs the DP1 factorisation");
     if (h->mult_dof.empty()) return DD_OK;
@@ -1619,6 +1651,7 @@ int dd_set_beam(dd_handle* h, const dd_beam* beam) {
     if (!h || !beam || beam->n_particles < 0 || (beam->n_particles > 0 && (!beam->x_inj || !beam->v_inj || !beam->t_inj)))
         return h ? h->fail(DD_ERR_ARG, "bad beam") : DD_ERR_ARG;
     if (h->bound) return h->fail(DD_ERR_STATE, "dd_set_beam after dd_bind_workspace");
+    if (h->members > 1) return h->fail(DD_ERR_STATE, "the PIC cycle is not available for an ensemble (members > 1)");
     return dd_build_beam(h, beam);
 }
 

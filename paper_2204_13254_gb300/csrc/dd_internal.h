@@ -173,6 +173,7 @@ struct PcgScalars {
 };
 
 constexpr int kMaxRestart = DD_MAX_RESTART;
+constexpr int kMaxMembers = 64;   // ensemble size limit
 constexpr int kGmElems = 4;                          // vector elements per thread in the GMRES kernels
 constexpr int kGmChunk = kGmElems * 256;             // elements per block
 
@@ -262,7 +263,7 @@ struct DevPtrs {
     float* M32 = nullptr;            // FP32 copy
     float* Msym = nullptr;           // packed symmetric FP32 tiles (see SymDesc)
     SymDesc* symd = nullptr;         // [n_sub]
-    int32_t* sym_rng[GEMV_NMODES] = {};   // [n_sub * kSymCLMax * 3] (list offset, tile count, end tile row) per CTA
+    int32_t* sym_rng[GEMV_NMODES] = {};   // [n_sub * kSymCLMax * 4] (list offset, tile count, end tile row, subdomain) per CTA
     uint32_t* sym_tl[GEMV_NMODES] = {};   // tiles of each packed mode, every subdomain in row order
     double* K64 = nullptr;           // K~cc^-1, n_corner x ldc
     float* K32 = nullptr;
@@ -391,6 +392,8 @@ struct dd_handle {
     std::vector<uint8_t> slot_own;
     std::vector<int64_t> mult_slot, corner_ptr, corner_slot, owner_slot;
     std::vector<int32_t> slot_upos;
+    int32_t members = 0;           // ensemble size R (set by dd_setup)
+    int32_t n_sub_real = 0;        // subdomains of one member: the ones whose operators are stored (0 .. n_sub_real-1)
     std::vector<int32_t> slot_sub;
     std::vector<int64_t> copy_ptr, copy_slot;
     std::vector<int64_t> row_ptr;

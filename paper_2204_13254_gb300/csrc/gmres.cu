@@ -728,7 +728,8 @@ int launch_dp2_rhs(const dd_handle* h, const UView& U, void* stream) {
 }
 
 int launch_robin_add(const dd_handle* h, double alpha, void* stream) {
-    const int64_t nl = (int64_t)h->mult_dof.size();
+    // member 0's multipliers (the first 1/R of them) touch every stored matrix once
+    const int64_t nl = (int64_t)h->mult_dof.size() / std::max(1, h->members);
     if (nl == 0) return 0;
     k_robin_add<<<vec_blocks(nl), kT, 0, S(stream)>>>(nl, h->d.mt_ptr, h->d.mt_col, h->d.mt_val, h->d.mult_slot,
                                                      h->d.slot_sub, h->d.mats, alpha, h->d.M64);

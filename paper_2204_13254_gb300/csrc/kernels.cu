@@ -1012,7 +1012,7 @@ int launch_csr_combine(const dd_handle* h, double ca, void* stream) {
 
 int launch_dense_assemble(const dd_handle* h, void* stream) {
     CU_TRY(cudaMemsetAsync(h->d.M64, 0, sizeof(double) * (size_t)h->dense_elems, S(stream)));
-    const int64_t nl = h->sub_ptr.back();
+    const int64_t nl = h->sub_ptr[h->n_sub_real];   // stored subdomains only (ensemble copies share them)
     k_dense_assemble<<<reduce_blocks(nl), kThreads, 0, S(stream)>>>(nl, h->d.row_ptr, h->d.col_loc, h->d.Aval,
                                                                      h->d.slot_sub, h->d.mats, h->d.M64);
     return (int)cudaGetLastError();
@@ -1021,7 +1021,7 @@ int launch_dense_assemble(const dd_handle* h, void* stream) {
 int launch_sweep(const dd_handle* h, bool coarse, int k0, void* stream) {
     const MatDesc* mats = coarse ? h->d.coarse_desc : h->d.mats;
     double* M = coarse ? h->d.K64 : h->d.M64;
-    const int nm = coarse ? 1 : h->n_sub;
+    const int nm = coarse ? 1 : h->n_sub_real;
     const int nmax = coarse ? (int)h->corner_dof.size() : h->max_ns;
     double* Pinv = coarse ? h->d.Pinv + (size_t)h->n_sub * kNB * kNB : h->d.Pinv;
     k_sweep_pivot<<<nm, kThreads, 0, S(stream)>>>(mats, M, k0, Pinv, h->d.status);
@@ -1034,7 +1034,7 @@ int launch_sweep(const dd_handle* h, bool coarse, int k0, void* stream) {
 
 int launch_coarse_assemble(const dd_handle* h, void* stream) {
     const int64_t nc = (int64_t)h->corner_dof.size();
-    if (nc == 0) return 0;
+    if (nc == 0 || h->ldc == 0) return 0;
     k_coarse_assemble<<<(unsigned)nc, kThreads, 0, S(stream)>>>(nc, h->ldc, h->d.corner_ptr, h->d.corner_slot,
                                                                 h->d.slot_sub, h->d.slot_corner, h->d.mats, h->d.M64,
                                                                 h->d.K64);

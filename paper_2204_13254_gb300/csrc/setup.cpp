@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstring>
 #include <numeric>
+#include <stdexcept>
 
 #include "dd_internal.h"
 
@@ -401,14 +402,21 @@ int dd_build_host(dd_handle* h, const dd_mesh* mesh, const int32_t* part, int32_
         md.nr = h->nI[s] + h->nG[s];
         md.ns = ns;
         md.ld = (ns + 3) / 4 * 4;
-        moff += (int64_t)ns * md.ld;
+        if (s < h->n_sub_real) {
+            moff += (int64_t)ns * md.ld;
+        } else {   // ensemble copy: the same local matrix as member 0's subdomain
+            const MatDesc& m0 = h->mats[s % h->n_sub_real];
+            if (m0.ns != md.ns || m0.nI != md.nI || m0.nr != md.nr) throw std::runtime_error("ensemble copy differs");
+            md.moff = m0.moff;
+        }
         h->mats[s] = md;
         h->max_nr = std::max(h->max_nr, md.nr);
         h->max_ns = std::max(h->max_ns, md.ns);
     }
     for (int64_t i = 0; i < n_local; ++i) h->row_ptr[i + 1] += h->row_ptr[i];
     h->dense_elems = moff;
-    h->ldc = (int32_t)((nc + 3) / 4 * 4);
+    // the dense K~cc^-1 serves the Schur CG only; an ensemble (coupled GMRES) has none
+    h->ldc = h->members > 1 ? 0 : (int32_t)((nc + 3) / 4 * 4);
 
     // ---- interface tangential mass on the multiplier edges (MFETI-DP2) ---------
     // faces shared by tets of two subdomains; CSR over multipliers (block diagonal
@@ -487,12 +495,16 @@ int dd_build_host(dd_handle* h, const dd_mesh* mesh, const int32_t* part, int32_
 void build_tasks(const dd_handle* h, int mode, int rows, std::vector<GemvTask>& tl) {
     tl.clear();
     if (mode == GEMV_COARSE) {
+        if (h->ldc == 0) return;   // no dense K~cc^-1 (ensemble)
         const int64_t nc = (int64_t)h->corner_dof.size();
         for (int64_t r0 = 0; r0 < nc; r0 += rows)
             tl.push_back({0, (int32_t)r0, (int32_t)std::min<int64_t>(nc, r0 + rows), 0});
         return;
     }
-    for (int s = 0; s < h->n_sub; ++s) {
+    // ensemble: the copies of a subdomain one after the other (they read the same matrix)
+    const int R = std::max(1, h->members), nsr = h->n_sub / R;
+    for (int q = 0; q < h->n_sub; ++q) {
+        const int s = (q % R) * nsr + q / R;
         const MatDesc& md = h->mats[s];
         int32_t r0 = 0, r1 = 0;
         if (mode == GEMV_LOCAL) { r0 = 0; r1 = md.ns; }

@@ -50,6 +50,8 @@ size_t round32(size_t n) { return (n + 31) / 32 * 32; }
 
 extern "C" int dd_schur_apply_static(dd_handle* h, const double* lam, double* out, void* stream) {
     if (!h || !lam || !out) return DD_ERR_ARG;
+    if (h->members > 1)
+        return h->fail(DD_ERR_STATE, "dd_schur_apply_static is not available for an ensemble (members > 1)");
     const size_t n_local = h->sub_ptr.empty() ? 0 : (size_t)h->sub_ptr.back();
     const size_t nc = h->corner_dof.size();
     const size_t need = round32(n_local) + 2 * round32(nc);

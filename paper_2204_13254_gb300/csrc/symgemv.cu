@@ -201,8 +201,8 @@ __device__ __forceinline__ void cluster_store(cg::cluster_group& cluster, const 
 // CTA-synchronous form: 128 threads consume every tile together, one barrier per tile.
 __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ descs, const int32_t* __restrict__ ranges,
                                                 const uint32_t* __restrict__ tlist, const float* __restrict__ Msym,
-                                                int span_max, int cl, int st, int rmask, int cmask, int keep, XSrc xs,
-                                                GemvOut go, const int32_t* __restrict__ skip, int32_t* __restrict__ err) {
+                                                int span_max, int cl, int st, int rmask, int cmask, int keep, int n_real,
+                                                XSrc xs, GemvOut go, const int32_t* __restrict__ skip, int32_t* __restrict__ err) {
     if (skip && *skip) return;   // the same word for every CTA of the grid
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float* ring = reinterpret_cast<float*>(smem_raw);
@@ -214,21 +214,21 @@ __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ desc
 
     cg::cluster_group cluster = cg::this_cluster();
     const int tid = threadIdx.x;
-    const int sub = blockIdx.x / cl;
+    const int sub = ranges[4 * blockIdx.x + 3];
     const SymDesc sd = descs[sub];
     const Groups G{sd.t0[1], sd.t0[2], sd.t0[3], sd.n[0], sd.n[1], sd.n[2]};
     const int np = G.nt * kSymT;
     // this CTA's run of the mode's tile list and the end of its tile rows
-    const uint32_t* lst = tlist + ranges[3 * blockIdx.x];
-    const int nt_cta = ranges[3 * blockIdx.x + 1];
-    const int a_end = ranges[3 * blockIdx.x + 2];
+    const uint32_t* lst = tlist + ranges[4 * blockIdx.x];
+    const int nt_cta = ranges[4 * blockIdx.x + 1];
+    const int a_end = ranges[4 * blockIdx.x + 2];
     const float* tiles = Msym + sd.toff;
     const int p_lo = G.first(lowest_group(rmask | cmask)) * kSymT;
     const int r_lo = G.first(lowest_group(rmask)) * kSymT;
 
     // thread 0: barriers and the first st tiles (in flight while the CTA stages x)
     int issued = 0;
-    const uint64_t pol = l2_policy(sub < keep);   // subdomains below `keep` stay in L2
+    const uint64_t pol = l2_policy(sub % n_real < keep);   // stored subdomains below `keep` stay in L2
     if (tid == 0) {
         for (int s = 0; s < st; ++s) mbar_init(&bars[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(kTW) k_symgemv_ws(const SymDesc* __restrict__ 
                                                     const int32_t* __restrict__ ranges,
                                                     const uint32_t* __restrict__ tlist, const float* __restrict__ Msym,
                                                     int span_max, int cl, int st, int rmask, int cmask, int keep,
-                                                    XSrc xs, GemvOut go, const int32_t* __restrict__ skip,
+                                                    int n_real, XSrc xs, GemvOut go, const int32_t* __restrict__ skip,
                                                     int32_t* __restrict__ err) {
     if (skip && *skip) return;   // the same word for every CTA of the grid
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -358,20 +358,20 @@ __global__ void __launch_bounds__(kTW) k_symgemv_ws(const SymDesc* __restrict__ 
     cg::cluster_group cluster = cg::this_cluster();
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int sub = blockIdx.x / cl;
+    const int sub = ranges[4 * blockIdx.x + 3];
     const SymDesc sd = descs[sub];
     const Groups G{sd.t0[1], sd.t0[2], sd.t0[3], sd.n[0], sd.n[1], sd.n[2]};
     const int np = G.nt * kSymT;
-    const uint32_t* lst = tlist + ranges[3 * blockIdx.x];
-    const int nt_cta = ranges[3 * blockIdx.x + 1];
-    const int a_end = ranges[3 * blockIdx.x + 2];
+    const uint32_t* lst = tlist + ranges[4 * blockIdx.x];
+    const int nt_cta = ranges[4 * blockIdx.x + 1];
+    const int a_end = ranges[4 * blockIdx.x + 2];
     const float* tiles = Msym + sd.toff;
     const int p_lo = G.first(lowest_group(rmask | cmask)) * kSymT;
     const int r_lo = G.first(lowest_group(rmask)) * kSymT;
     const int span = np - p_lo;
 
     int issued = 0;   // producer lane only
-    const uint64_t pol = l2_policy(sub < keep);
+    const uint64_t pol = l2_policy(sub % n_real < keep);
     if (tid == kT) {
         for (int s = 0; s < st; ++s) {
             mbar_init(&full[s], 1);
@@ -553,6 +553,10 @@ void build_sym(dd_handle* h) {
         for (int g = 0; g < 3; ++g) sd.t0[g + 1] = sd.t0[g] + (sd.n[g] + kSymT - 1) / kSymT;
         const int nt = sd.t0[3];
         const int64_t ntl = (int64_t)nt * (nt + 1) / 2;
+        if (s >= h->n_sub_real) {   // ensemble copy: member 0's tiles
+            sd.toff = h->sym[s % h->n_sub_real].toff;
+            continue;
+        }
         toff += ntl * kSymTile;
         h->sym_np_max = std::max(h->sym_np_max, nt * kSymT);
         h->sym_max_tiles = std::max<int32_t>(h->sym_max_tiles, (int32_t)ntl);
@@ -573,12 +577,14 @@ void build_sym(dd_handle* h) {
             }
         }
         h->mode_bytes_sym[mode] = bytes;
-        // the mode's tiles of every subdomain in row order (what the kernel streams)
+        // the mode's tiles of every stored subdomain in row order (what the kernel
+        // streams; ensemble copies share member 0's list)
         std::vector<uint32_t>& tl = h->sym_tl[mode];
         std::vector<int64_t>& off = h->sym_tl_off[mode];
         tl.clear();
         off.assign(1, 0);
-        for (const SymDesc& sd : h->sym) {
+        for (int s = 0; s < h->n_sub_real; ++s) {
+            const SymDesc& sd = h->sym[s];
             for (int a = 0; a < sd.t0[3]; ++a)
                 for (int b = 0; b <= a; ++b) {
                     const int f = sym_tile_flags(sd.t0, a, b, rmask, cmask);
@@ -593,15 +599,18 @@ void build_sym(dd_handle* h) {
 // Work of each of the cl CTAs of every subdomain for `mode`: contiguous tile-row
 // ranges, CTA c ending where the running tile count comes closest to (c + 1) / cl
 // of the subdomain's total; stored as (first entry in the mode's tile list, tile
-// count, end tile row).
+// count, end tile row, subdomain).  Ensemble copies of a subdomain follow each
+// other (they stream the same tiles, which L2 then serves).
 void sym_ranges(dd_handle* h, int mode, int cl) {
     int rmask, cmask;
     h->sym_rng[mode].clear();
     h->sym_cl[mode] = cl;
     h->sym_nl[mode] = 0;
     if (!sym_masks(mode, &rmask, &cmask)) return;
-    for (int s = 0; s < h->n_sub; ++s) {
-        const SymDesc& sd = h->sym[s];
+    const int R = std::max(1, h->members);
+    for (int q = 0; q < h->n_sub; ++q) {
+        const int s0 = q / R, sub = (q % R) * h->n_sub_real + s0;
+        const SymDesc& sd = h->sym[s0];
         const int nt = sd.t0[3];
         std::vector<int64_t> per_row(nt, 0);
         int64_t total = 0;
@@ -611,7 +620,7 @@ void sym_ranges(dd_handle* h, int mode, int cl) {
             total += per_row[a];
         }
         int a = 0;
-        int64_t run = 0, first = h->sym_tl_off[mode][s];
+        int64_t run = 0, first = h->sym_tl_off[mode][s0];
         for (int c = 0; c < cl; ++c) {
             const int begin = a;
             if (c == cl - 1) {
@@ -625,7 +634,8 @@ void sym_ranges(dd_handle* h, int mode, int cl) {
             for (int q = begin; q < a; ++q) n += per_row[q];
             h->sym_rng[mode].push_back((int32_t)first);
             h->sym_rng[mode].push_back((int32_t)n);
-            h->sym_rng[mode].push_back(a);
+            h->sym_rng[mode].push_back(n ? a : 0);
+            h->sym_rng[mode].push_back(sub);
             first += n;
             h->sym_nl[mode] = std::max<int32_t>(h->sym_nl[mode], (int32_t)n);
         }
@@ -634,7 +644,7 @@ void sym_ranges(dd_handle* h, int mode, int cl) {
 
 int launch_sym_pack(const dd_handle* h, void* stream) {
     if (h->n_sub == 0 || h->sym_max_tiles == 0) return 0;
-    k_sym_pack<<<dim3((unsigned)h->sym_max_tiles, (unsigned)h->n_sub), kT, 0, S(stream)>>>(h->d.symd, h->d.mats,
+    k_sym_pack<<<dim3((unsigned)h->sym_max_tiles, (unsigned)h->n_sub_real), kT, 0, S(stream)>>>(h->d.symd, h->d.mats,
                                                                                            h->d.M64, h->d.Msym);
     return (int)cudaGetLastError();
 }
@@ -670,5 +680,6 @@ int launch_symgemv(const dd_handle* h, int mode, XSrc xs, GemvOut go, const int3
     cfg.numAttrs = 1;
     return (int)cudaLaunchKernelEx(&cfg, kern, (const SymDesc*)h->d.symd, (const int32_t*)h->d.sym_rng[mode],
                                    (const uint32_t*)h->d.sym_tl[mode], (const float*)h->d.Msym, span, cl, st, rmask,
-                                   cmask, h->sym_keep[mode], xs, go, skip, &h->d.sc->wait_err);
+                                   cmask, h->sym_keep[mode], std::max(1, h->n_sub_real), xs, go, skip,
+                                   &h->d.sc->wait_err);
 }

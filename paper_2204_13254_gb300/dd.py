@@ -40,13 +40,14 @@ class dd_params(C.Structure):
     _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("max_it", C.c_int), ("precond", C.c_int),
                 ("warm_start", C.c_int), ("refine_tol", C.c_double), ("max_refine", C.c_int), ("chunk", C.c_int),
                 ("use_graph", C.c_int), ("solver", C.c_int), ("restart", C.c_int), ("sym_fp32", C.c_int),
-                ("scheme", C.c_int), ("robin_alpha", C.c_double)]
+                ("scheme", C.c_int), ("robin_alpha", C.c_double), ("members", C.c_int)]
 
 
 class dd_sizes(C.Structure):
     _fields_ = [("n_edges", C.c_int64), ("n_dof", C.c_int64), ("n_sub", C.c_int32), ("n_lambda", C.c_int64),
                 ("n_corner", C.c_int64), ("n_local", C.c_int64), ("nnz_local", C.c_int64), ("max_nr", C.c_int32),
-                ("max_ns", C.c_int32), ("workspace_bytes", C.c_size_t), ("dense_bytes_fp64", C.c_int64)]
+                ("max_ns", C.c_int32), ("workspace_bytes", C.c_size_t), ("dense_bytes_fp64", C.c_int64),
+                ("members", C.c_int32)]
 
 
 class dd_maps(C.Structure):
@@ -142,9 +143,9 @@ def _stream(stream=None):
 
 def make_params(precision=DD_FP64, tol=1e-12, max_it=500, precond=1, warm_start=1, refine_tol=1e-12, max_refine=4,
                 chunk=8, use_graph=0, solver=DD_SOLVER_SCHUR_CG, restart=20, sym_fp32=1, scheme=DD_SCHEME_DP1,
-                robin_alpha=0.0):
+                robin_alpha=0.0, members=1):
     return dd_params(precision, tol, max_it, precond, warm_start, refine_tol, max_refine, chunk, use_graph, solver,
-                     restart, sym_fp32, scheme, robin_alpha)
+                     restart, sym_fp32, scheme, robin_alpha, members)
 
 
 # ---- C-ABI-named wrappers ------------------------------------------------------
@@ -362,6 +363,9 @@ class FieldSolver:
         self.sizes = dd_get_sizes(self.h)
         self.n_dof = self.sizes.n_dof
         self.n_lambda = self.sizes.n_lambda
+        self.members = self.sizes.members          # ensemble size: member r owns dofs [r, r + 1) * n_dof_member
+        self.n_dof_member = self.n_dof // self.members
+        self.n_nodes = len(xyz)
         if probes is not None:
             dd_set_probes(self.h, probes)
         self.n_probe = 0 if probes is None else len(np.asarray(probes).reshape(-1, 3))
@@ -380,13 +384,15 @@ class FieldSolver:
     def maps(self):
         return dd_get_maps(self.h)
 
-    def dof_of_pairs(self, pairs):
-        """dof ids of node pairs (lo, hi) -- host marshalling for source vectors."""
+    def dof_of_pairs(self, pairs, member=0):
+        """dof ids of node pairs (lo, hi) of ensemble member `member` -- host
+        marshalling for source vectors."""
+        pairs = np.asarray(pairs) + member * self.n_nodes
         m = self.maps()
         edges = m["edges"][m["dof_edge"]]
         n = int(max(edges.max(), np.max(pairs))) + 1
         keys = edges[:, 0] * n + edges[:, 1]
-        pk = np.asarray(pairs)[:, 0] * n + np.asarray(pairs)[:, 1]
+        pk = pairs[:, 0] * n + pairs[:, 1]
         pos = np.searchsorted(keys, pk)
         assert np.all(keys[pos] == pk), "pair is not an interior edge"
         return pos

@@ -132,3 +132,40 @@ def test_interface_mass_matches_oracle():
         got = sp.csr_matrix((val, col, ptr), shape=ref.shape)
         assert got.nnz == ref.nnz
         assert abs(got - ref).max() <= 1e-15 * abs(ref).max()
+
+
+def test_ensemble_setup_shares_the_operators(built):
+    """members = R: R copies of the tearing maps (member r = mesh copy r, node ids
+    + r N), every count R times the single problem's, the dense operators
+    stored once, and the Schur CG refused (it would need the stacked K~cc^-1)."""
+    w = W.config(1)
+    R = 3
+    one = D.dd_setup(w.xyz, w.tets, w.part, w.n_sub, params=D.make_params(solver=D.DD_SOLVER_COUPLED_GMRES))
+    ens = D.dd_setup(w.xyz, w.tets, w.part, w.n_sub,
+                     params=D.make_params(solver=D.DD_SOLVER_COUPLED_GMRES, members=R))
+    try:
+        s1, sR = D.dd_get_sizes(one), D.dd_get_sizes(ens)
+        assert s1.members == 1 and sR.members == R
+        for f in ("n_edges", "n_dof", "n_sub", "n_lambda", "n_corner", "n_local", "nnz_local"):
+            assert getattr(sR, f) == R * getattr(s1, f), f
+        assert sR.dense_bytes_fp64 == s1.dense_bytes_fp64
+        assert sR.workspace_bytes < R * s1.workspace_bytes
+        m1, mR = D.dd_get_maps(one), D.dd_get_maps(ens)
+        N = len(w.xyz)
+        e1 = m1["edges"][m1["dof_edge"]]
+        eR = mR["edges"][mR["dof_edge"]].reshape(R, -1, 2)
+        for r in range(R):
+            assert np.array_equal(eR[r], e1 + r * N)
+        ns1 = np.diff(m1["sub_ptr"])
+        assert np.array_equal(np.diff(mR["sub_ptr"]), np.tile(ns1, R))
+        ms = mR["mult_sub"].reshape(R, -1, 2)
+        for r in range(R):
+            assert np.array_equal(ms[r], m1["mult_sub"].reshape(-1, 2) + r * w.n_sub)
+    finally:
+        D.dd_destroy(one)
+        D.dd_destroy(ens)
+    for bad in (D.make_params(members=R), D.make_params(solver=D.DD_SOLVER_COUPLED_GMRES, members=0),
+                D.make_params(solver=D.DD_SOLVER_COUPLED_GMRES, members=65)):
+        with pytest.raises(D.DDError) as e:
+            D.dd_setup(w.xyz, w.tets, w.part, w.n_sub, params=bad)
+        assert e.value.code == D.DD_ERR_ARG
