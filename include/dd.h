@@ -450,20 +450,22 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
  * tiles when sym_fp32 = 1: cl[k] CTAs (one cluster) per subdomain, a TMA ring
  * of st[k] tiles, and the tiles of subdomains 0 .. keep[k]-1 copied with an
  * L2 evict_last policy (the rest evict_first) so that they stay in L2 across
- * the launches of a Krylov solve; ws[k] = 1 when the kind runs the
- * warp-specialised kernel (a producer warp refills the ring as the four
- * consumer warps release slots, each consumer warp keeping its own partial y),
- * 0 for the CTA-synchronous one (host int32[7] each, 0 for the other kinds;
- * any pointer may be NULL). */
+ * the launches of a Krylov solve; ws[k] is the kernel form: 0 the
+ * CTA-synchronous kernel, 1 the warp-specialised one (a producer warp refills
+ * the ring as the four consumer warps release slots, each consumer warp keeping
+ * its own partial y), 2 (ensembles) one CTA applying every tile it loads to the
+ * x of 2 or 4 ensemble copies of its subdomain (host int32[7] each, 0 for the
+ * other kinds; any pointer may be NULL). */
 int dd_get_tiles(const dd_handle* h, int32_t* lpr, int32_t* rows);
 int dd_get_sym_config(const dd_handle* h, int32_t* cl, int32_t* st, int32_t* keep, int32_t* ws);
 
 /* Sets the packed-tile launch of GEMV kind `kind` (0, 5 or 6) to cl CTAs per
- * subdomain (1, 2, 4 or 8), a ring of st tiles (2..4), keep subdomains in L2
- * (0..n_sub) and kernel form ws (1 warp-specialised, 0 CTA-synchronous), as
+ * subdomain (1, 2, 4 or 8), a ring of st tiles (2..4), keep stored subdomains
+ * in L2 (0..n_sub) and kernel form ws (0, 1 or 2 as in dd_get_sym_config), as
  * dd_autotune would (its next run may change it again).  Results differ from
  * another setting only in the order of FP32 sums.  DD_ERR_ARG for other kinds
- * or values, DD_ERR_STATE before dd_bind_workspace or during a capture.
+ * or values (or form 2 when its shared memory exceeds a CTA's), DD_ERR_STATE
+ * before dd_bind_workspace or during a capture.
  * Synchronises `stream`; drops captured step graphs. */
 int dd_set_sym_config(dd_handle* h, int32_t kind, int32_t cl, int32_t st, int32_t keep, int32_t ws, void* stream);
 

@@ -230,7 +230,7 @@ size_t dd_workspace_layout(dd_handle* h, bool assign) {
     for (int m = 0; m < GEMV_NMODES; ++m) {
         int rm, cm;
         if (sym_masks(m, &rm, &cm)) {
-            L.take(d.sym_rng[m], (size_t)h->n_sub * kSymCLMax * 4);
+            L.take(d.sym_rng[m], (size_t)h->n_sub * kSymCLMax * kSymRng);
             L.take(d.sym_tl[m], std::max<size_t>(1, h->sym_tl[m].size()));
         }
     }
@@ -1738,7 +1738,7 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
                 found[{p, m}] = TileCfg{lpr, rows};
             int keep = 0, ws = 0;
             if (p == 2 && sym_masks(m, &rm, &cm) && (lpr == 1 || lpr == 2 || lpr == 4 || lpr == 8) && rows >= 2 &&
-                rows <= kSymStages && (is >> keep >> ws) && keep >= 0 && keep <= h->n_sub && (ws == 0 || ws == 1))
+                rows <= kSymStages && (is >> keep >> ws) && keep >= 0 && keep <= h->n_sub && ws >= 0 && ws <= 2)
                 found_cl[m] = SymCfg{lpr, rows, keep, ws};
         }
     }
@@ -1777,9 +1777,13 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
                     SymCfg bcl{h->sym_cl[m], h->sym_st[m], 0, 0};
                     const bool repeated = m != GEMV_LOCAL;
                     const double per_sub = h->mode_bytes_sym[m] / std::max(1, h->n_sub);
-                    for (int cand = 0; cand < 24 + (repeated ? 3 : 0) && !rc; ++cand) {
+                    // kernel forms: CTA-synchronous, warp-specialised and, for an ensemble whose
+                    // shared memory allows it, the copies of a subdomain in one CTA
+                    const bool form2 = h->members > 1 && sym_smem_bytes_nr(h, h->members <= 2 ? 2 : 4) <= 227 * 1024;
+                    const int nsweep = 12 * (form2 ? 3 : 2);
+                    for (int cand = 0; cand < nsweep + (repeated ? 3 : 0) && !rc; ++cand) {
                         int cl, st, keep = 0, ws;
-                        if (cand < 24) {
+                        if (cand < nsweep) {
                             ws = cand / 12;
                             cl = 1 << ((cand % 12) / 3);
                             st = 2 + cand % 3;
@@ -1787,7 +1791,7 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
                             cl = bcl.cl;
                             st = bcl.st;
                             ws = bcl.ws;
-                            keep = std::min(h->n_sub, (int)((cand - 23) * 32.0e6 / std::max(1.0, per_sub)));
+                            keep = std::min(h->n_sub, (int)((cand - nsweep + 1) * 32.0e6 / std::max(1.0, per_sub)));
                         }
                         h->sym_st[m] = st;
                         h->sym_keep[m] = keep;
@@ -1924,8 +1928,10 @@ int dd_set_sym_config(dd_handle* h, int32_t kind, int32_t cl, int32_t st, int32_
     if (kind < 0 || kind >= GEMV_NMODES || !sym_masks(kind, &rm, &cm))
         return h->fail(DD_ERR_ARG, "dd_set_sym_config: not a packed GEMV kind");
     if (!(cl == 1 || cl == 2 || cl == 4 || cl == 8) || st < 2 || st > kSymStages || keep < 0 || keep > h->n_sub ||
-        !(ws == 0 || ws == 1))
-        return h->fail(DD_ERR_ARG, "dd_set_sym_config: cl in {1,2,4,8}, 2 <= st <= 4, 0 <= keep <= n_sub, ws in {0,1}");
+        ws < 0 || ws > 2)
+        return h->fail(DD_ERR_ARG, "dd_set_sym_config: cl in {1,2,4,8}, 2 <= st <= 4, 0 <= keep <= n_sub, ws in {0,1,2}");
+    if (ws == 2 && sym_smem_bytes_nr(h, h->members <= 2 ? 2 : 4) > 227 * 1024)
+        return h->fail(DD_ERR_ARG, "dd_set_sym_config: the ensemble form needs more shared memory than a CTA has");
     if (!h->bound) return h->fail(DD_ERR_STATE, "dd_set_sym_config before dd_bind_workspace");
     if (h->capturing) return h->fail(DD_ERR_STATE, "dd_set_sym_config during capture");
     cudaStream_t s = (cudaStream_t)stream;

@@ -174,6 +174,7 @@ struct PcgScalars {
 
 constexpr int kMaxRestart = DD_MAX_RESTART;
 constexpr int kMaxMembers = 64;   // ensemble size limit
+constexpr int kSymRng = 5;        // ints per CTA in a packed GEMV work table
 constexpr int kGmElems = 4;                          // vector elements per thread in the GMRES kernels
 constexpr int kGmChunk = kGmElems * 256;             // elements per block
 
@@ -263,7 +264,8 @@ struct DevPtrs {
     float* M32 = nullptr;            // FP32 copy
     float* Msym = nullptr;           // packed symmetric FP32 tiles (see SymDesc)
     SymDesc* symd = nullptr;         // [n_sub]
-    int32_t* sym_rng[GEMV_NMODES] = {};   // [n_sub * kSymCLMax * 4] (list offset, tile count, end tile row, subdomain) per CTA
+    int32_t* sym_rng[GEMV_NMODES] = {};   // [n_sub * kSymCLMax * kSymRng] (list offset, tile count, end tile row,
+                                          // subdomain, ensemble members served) per CTA
     uint32_t* sym_tl[GEMV_NMODES] = {};   // tiles of each packed mode, every subdomain in row order
     double* K64 = nullptr;           // K~cc^-1, n_corner x ldc
     float* K32 = nullptr;
@@ -417,7 +419,8 @@ struct dd_handle {
     int32_t sym_st[GEMV_NMODES] = {4, 4, 4, 4, 4, 4, 4};   // TMA ring depth of each packed mode
     int32_t sym_nl[GEMV_NMODES] = {};                      // longest tile list of one CTA (shared memory)
     int32_t sym_keep[GEMV_NMODES] = {};                    // subdomains whose tiles are kept in L2 (evict_last)
-    int32_t sym_ws[GEMV_NMODES] = {};                      // 1: warp-specialised packed kernel, 0: CTA-synchronous
+    int32_t sym_ws[GEMV_NMODES] = {};                      // packed kernel form: 0 CTA-synchronous, 1 warp-specialised,
+                                                           // 2 ensemble copies of a subdomain in one CTA
     int32_t sym_max_tiles = 0;                     // largest tile count of one subdomain
     bool sym_ok = false;                           // the packed GEMV's shared memory fits one CTA
     size_t task_cap[GEMV_NMODES] = {};             // device capacity: tasks at the smallest row count
@@ -544,6 +547,8 @@ void sym_ranges(dd_handle* h, int mode, int cl);
 int launch_sym_pack(const dd_handle* h, void* stream);
 int launch_symgemv(const dd_handle* h, int mode, XSrc xs, GemvOut go, const int32_t* skip, void* stream);
 size_t sym_smem_bytes(const dd_handle* h);
+size_t sym_smem_bytes_nr(const dd_handle* h, int nr);
+int sym_members_per_cta(const dd_handle* h, int mode);
 
 // gmres.cu: coupled-system GMRES (u = [lambda; x_c])
 int launch_corner_diag(const dd_handle* h, void* stream);

@@ -38,13 +38,9 @@ namespace {
 inline cudaStream_t S(void* s) { return (cudaStream_t)s; }
 
 constexpr int kThreads = 256;
+constexpr unsigned kLocalSplit = 4;   // CTAs per subdomain of the local-CSR kernels
 
 __device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-__device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
@@ -310,61 +306,101 @@ __global__ void k_to_fp32(int64_t n, const double* __restrict__ a, float* __rest
 // Step: right-hand side (Newmark increment form)
 // ----------------------------------------------------------------------------
 
-// b_s = -dt^2 S^(s) e^n|_s + src_sign * (owner ? src : 0), one 8-lane group per slot row
+// b_s = -dt^2 S^(s) e^n|_s + src_sign * (owner ? src : 0) on every slot of s
 // (forward: src = d2g, sign -1; adjoint: src = seed, sign +1).
 // With e^{n+1} = 2e^n - e^{n-1} + delta, the recurrence becomes A delta = b.
-__global__ void k_rhs(int64_t n_local, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col_dof,
-                      const double* __restrict__ Sv, const double* __restrict__ e_n, const double* __restrict__ d2g,
-                      double src_sign, const int32_t* __restrict__ slot_dof, const uint8_t* __restrict__ slot_own,
-                      double mdt2, double* __restrict__ b) {
-    // each warp owns 4 consecutive rows (8 lanes per row); the loop is warp-uniform
-    const int lane8 = threadIdx.x & 7;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t w0 = warp * 4; w0 < n_local; w0 += nwarp * 4) {
-        const int64_t i = w0 + ((threadIdx.x & 31) >> 3);
-        double s = 0.0;
-        if (i < n_local)
-            for (int64_t k = row_ptr[i] + lane8; k < row_ptr[i + 1]; k += 8) s += Sv[k] * e_n[col_dof[k]];
+// The FP64 residual of a mixed-precision refinement pass is b^(s) -= A^(s) delta|_s.
+
+// A CTA of subdomain blockIdx.x: the global vector v at the subdomain's ns dofs into
+// shared memory (vl[l] = v[slot_dof[voff + l]]), eight slots per thread per
+// pass (their index loads, then their value loads), so that the rows below read
+// it through the local column index instead of gathering one global entry per
+// matrix element.
+__device__ __forceinline__ void stage_local(const double* __restrict__ v, const int32_t* __restrict__ slot_dof,
+                                            int64_t voff, int ns, double* vl) {
+    constexpr int kU = 8;
+    for (int l0 = threadIdx.x; l0 < ns; l0 += blockDim.x * kU) {
+        int d[kU];
 #pragma unroll
-        for (int o = 4; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, 8);
-        if (lane8 == 0 && i < n_local) {
-            double v = mdt2 * s;
-            if (d2g && slot_own[i]) v += src_sign * d2g[slot_dof[i]];
-            b[i] = v;
+        for (int u = 0; u < kU; ++u) {
+            const int l = l0 + u * blockDim.x;
+            d[u] = l < ns ? slot_dof[voff + l] : 0;
+        }
+        double x[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) x[u] = l0 + u * (int)blockDim.x < ns ? v[d[u]] : 0.0;
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int l = l0 + u * blockDim.x;
+            if (l < ns) vl[l] = x[u];
         }
     }
 }
 
-// b <- b - A^(s) delta|_s (subassembled FP64 residual of the step system) and
-// the assembled residual norm: res[d] = sum over copies of the new b.
-// b -= A delta per slot row (local CSR, ~15 entries a row): 4 lanes per row, 8 rows
-// per warp, every lane's loads issued before its adds (streaming loads of the
-// matrix, delta gathered through L1/L2).
-__global__ void k_residual_local(int64_t n_local, const int64_t* __restrict__ row_ptr,
-                                 const int32_t* __restrict__ col_dof, const double* __restrict__ A,
-                                 const double* __restrict__ delta, double* __restrict__ b) {
+// Row sums of one subdomain's local CSR against the staged vector (its rows split
+// over gridDim.y CTAs, each staging the whole vector): 4 lanes per row, 8 rows per warp, the matrix streamed (every lane's loads issued before
+// its adds); fn(i, s) receives slot i's sum in lane 0 of its quad.
+template <typename Fn>
+__device__ __forceinline__ void local_rows(const MatDesc& md, const int64_t* __restrict__ row_ptr,
+                                           const int32_t* __restrict__ col_loc, const double* __restrict__ A,
+                                           const double* vl, Fn fn) {
     const int lane4 = threadIdx.x & 3;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t w0 = warp * 8; w0 < n_local; w0 += nwarp * 8) {
-        const int64_t i = w0 + ((threadIdx.x & 31) >> 2);
+    const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    // this CTA's share of the rows: part blockIdx.y of gridDim.y
+    const int ra = (int)((int64_t)md.ns * blockIdx.y / gridDim.y), rb = (int)((int64_t)md.ns * (blockIdx.y + 1) / gridDim.y);
+    for (int r0 = ra + warp * 8; r0 < rb; r0 += nwarp * 8) {
+        const int r = r0 + ((threadIdx.x & 31) >> 2);
+        const int64_t i = md.voff + r;
         double s = 0.0;
-        if (i < n_local) {
+        if (r < rb) {
             const int64_t k1 = row_ptr[i + 1];
             int64_t k = row_ptr[i] + lane4;
             for (; k + 12 < k1; k += 16) {
                 const double a0 = __ldcs(A + k), a1 = __ldcs(A + k + 4), a2 = __ldcs(A + k + 8), a3 = __ldcs(A + k + 12);
-                const int32_t c0 = __ldcs(col_dof + k), c1 = __ldcs(col_dof + k + 4), c2 = __ldcs(col_dof + k + 8),
-                              c3 = __ldcs(col_dof + k + 12);
-                s += a0 * delta[c0] + a1 * delta[c1] + a2 * delta[c2] + a3 * delta[c3];
+                const int32_t c0 = __ldcs(col_loc + k), c1 = __ldcs(col_loc + k + 4), c2 = __ldcs(col_loc + k + 8),
+                              c3 = __ldcs(col_loc + k + 12);
+                s += a0 * vl[c0] + a1 * vl[c1] + a2 * vl[c2] + a3 * vl[c3];
             }
-            for (; k < k1; k += 4) s += __ldcs(A + k) * delta[__ldcs(col_dof + k)];
+            for (; k < k1; k += 4) s += __ldcs(A + k) * vl[__ldcs(col_loc + k)];
         }
         s += __shfl_xor_sync(0xffffffffu, s, 2, 4);
         s += __shfl_xor_sync(0xffffffffu, s, 1, 4);
-        if (lane4 == 0 && i < n_local) b[i] -= s;
+        if (lane4 == 0 && r < rb) fn(i, s);
     }
+}
+
+// b^(s) = -dt^2 S^(s) e^n|_s + src_sign * d2g on the owned copies (the increment
+// form's right-hand side), kLocalSplit CTAs per subdomain.
+__global__ void __launch_bounds__(kThreads) k_rhs_sub(const MatDesc* __restrict__ mats,
+                                                     const int64_t* __restrict__ row_ptr,
+                                                     const int32_t* __restrict__ col_loc, const double* __restrict__ Sv,
+                                                     const double* __restrict__ e_n, const double* __restrict__ d2g,
+                                                     double src_sign, const int32_t* __restrict__ slot_dof,
+                                                     const uint8_t* __restrict__ slot_own, double mdt2,
+                                                     double* __restrict__ b) {
+    extern __shared__ double vl[];
+    const MatDesc md = mats[blockIdx.x];
+    stage_local(e_n, slot_dof, md.voff, md.ns, vl);
+    __syncthreads();
+    local_rows(md, row_ptr, col_loc, Sv, vl, [&](int64_t i, double s) {
+        double v = mdt2 * s;
+        if (d2g && slot_own[i]) v += src_sign * d2g[slot_dof[i]];
+        b[i] = v;
+    });
+}
+
+// b^(s) -= A^(s) delta|_s (the subassembled FP64 residual of the step system), kLocalSplit CTAs per subdomain.
+__global__ void __launch_bounds__(kThreads) k_residual_sub(const MatDesc* __restrict__ mats,
+                                                          const int64_t* __restrict__ row_ptr,
+                                                          const int32_t* __restrict__ col_loc,
+                                                          const double* __restrict__ A,
+                                                          const int32_t* __restrict__ slot_dof,
+                                                          const double* __restrict__ delta, double* __restrict__ b) {
+    extern __shared__ double vl[];
+    const MatDesc md = mats[blockIdx.x];
+    stage_local(delta, slot_dof, md.voff, md.ns, vl);
+    __syncthreads();
+    local_rows(md, row_ptr, col_loc, A, vl, [&](int64_t i, double s) { b[i] -= s; });
 }
 
 // ----------------------------------------------------------------------------
@@ -1053,18 +1089,17 @@ int launch_factor_finish(const dd_handle* h, void* stream) {
 }
 
 int launch_rhs(const dd_handle* h, const double* e_n, const double* src, double src_sign, double dt, void* stream) {
-    const int64_t nl = h->sub_ptr.back();
-    const int blocks = (int)std::min<int64_t>((nl * 8 + kThreads - 1) / kThreads, 152 * 16);
-    k_rhs<<<blocks, kThreads, 0, S(stream)>>>(nl, h->d.row_ptr, h->d.col_dof, h->d.Sval, e_n, src, src_sign,
-                                              h->d.slot_dof, h->d.slot_own, -dt * dt, h->d.b);
+    if (h->n_sub == 0) return 0;
+    k_rhs_sub<<<dim3((unsigned)h->n_sub, kLocalSplit), kThreads, sizeof(double) * (size_t)h->max_ns, S(stream)>>>(
+        h->d.mats, h->d.row_ptr, h->d.col_loc, h->d.Sval, e_n, src, src_sign, h->d.slot_dof, h->d.slot_own, -dt * dt,
+        h->d.b);
     return (int)cudaGetLastError();
 }
 
 int launch_residual_local(const dd_handle* h, void* stream) {
-    const int64_t nl = h->sub_ptr.back();
-    const int blocks = (int)std::min<int64_t>((nl * 4 + kThreads - 1) / kThreads, 152 * 16);
-    k_residual_local<<<blocks, kThreads, 0, S(stream)>>>(nl, h->d.row_ptr, h->d.col_dof, h->d.Aval, h->d.delta_k,
-                                                         h->d.b);
+    if (h->n_sub == 0) return 0;
+    k_residual_sub<<<dim3((unsigned)h->n_sub, kLocalSplit), kThreads, sizeof(double) * (size_t)h->max_ns, S(stream)>>>(
+        h->d.mats, h->d.row_ptr, h->d.col_loc, h->d.Aval, h->d.slot_dof, h->d.delta_k, h->d.b);
     return (int)cudaGetLastError();
 }
 

@@ -110,10 +110,11 @@ struct Groups {
 // Shared-memory layouts (floats unless noted), span = the padded index range
 // the mode touches (from its first group on), st = ring depth, nl = longest
 // tile list of one CTA:
-//   k_symgemv:    ring [st][kSymTile] | x [span] | y [span] | red [2][8][64] | bars (u64) [kSymStages] | tiles (u32) [nl]
+//   k_symgemv<NR>: ring [st][kSymTile] | x [NR][span] | y [NR][span] | red [2][NR][8][64] |
+//                  bars (u64) [kSymStages] | tiles (u32) [nl]
 //   k_symgemv_ws: ring [st][kSymTile] | x [span] | y [4][span] | full, empty (u64) [kSymStages] | tiles (u32) [nl]
-__host__ __device__ inline size_t sym_smem(int span, int st, int nl) {
-    size_t f = (size_t)st * kSymTile + 2 * (size_t)span + 2 * 8 * 64;
+__host__ __device__ inline size_t sym_smem(int span, int st, int nl, int nr = 1) {
+    size_t f = (size_t)st * kSymTile + 2 * (size_t)nr * span + 2 * (size_t)nr * 8 * 64;
     return f * sizeof(float) + kSymStages * sizeof(uint64_t) + (size_t)nl * sizeof(uint32_t);
 }
 __host__ __device__ inline size_t sym_smem_ws(int span, int st, int nl) {
@@ -198,7 +199,11 @@ __device__ __forceinline__ void cluster_store(cg::cluster_group& cluster, const 
     cluster.sync();   // no CTA leaves while another reads its shared memory
 }
 
-// CTA-synchronous form: 128 threads consume every tile together, one barrier per tile.
+// CTA-synchronous form: 128 threads consume every tile together, one barrier per
+// tile.  NR > 1 (ensembles): the CTA serves the nmem <= NR ensemble copies sub,
+// sub + n_real, ... of one stored subdomain, applying every tile it loads to each
+// member's x (one TMA copy and one pass over shared memory per tile for all of them).
+template <int NR>
 __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ descs, const int32_t* __restrict__ ranges,
                                                 const uint32_t* __restrict__ tlist, const float* __restrict__ Msym,
                                                 int span_max, int cl, int st, int rmask, int cmask, int keep, int n_real,
@@ -206,22 +211,23 @@ __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ desc
     if (skip && *skip) return;   // the same word for every CTA of the grid
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float* ring = reinterpret_cast<float*>(smem_raw);
-    float* xsh = ring + st * kSymTile;   // index p - p_lo
-    float* ysh = xsh + span_max;
-    float* red = ysh + span_max;        // [2][8][64] transposed-role partials, double-buffered
-    uint64_t* bars = reinterpret_cast<uint64_t*>(red + 2 * 8 * 64);
+    float* xsh = ring + st * kSymTile;   // [NR][span_max], index p - p_lo
+    float* ysh = xsh + NR * span_max;    // [NR][span_max]
+    float* red = ysh + NR * span_max;    // [2][NR][8][64] transposed-role partials, double-buffered
+    uint64_t* bars = reinterpret_cast<uint64_t*>(red + 2 * NR * 8 * 64);
     uint32_t* tl = reinterpret_cast<uint32_t*>(bars + kSymStages);
 
     cg::cluster_group cluster = cg::this_cluster();
     const int tid = threadIdx.x;
-    const int sub = ranges[4 * blockIdx.x + 3];
+    const int32_t* rg5 = ranges + kSymRng * blockIdx.x;
+    const int sub = rg5[3], nmem = rg5[4];
     const SymDesc sd = descs[sub];
     const Groups G{sd.t0[1], sd.t0[2], sd.t0[3], sd.n[0], sd.n[1], sd.n[2]};
     const int np = G.nt * kSymT;
     // this CTA's run of the mode's tile list and the end of its tile rows
-    const uint32_t* lst = tlist + ranges[4 * blockIdx.x];
-    const int nt_cta = ranges[4 * blockIdx.x + 1];
-    const int a_end = ranges[4 * blockIdx.x + 2];
+    const uint32_t* lst = tlist + rg5[0];
+    const int nt_cta = rg5[1];
+    const int a_end = rg5[2];
     const float* tiles = Msym + sd.toff;
     const int p_lo = G.first(lowest_group(rmask | cmask)) * kSymT;
     const int r_lo = G.first(lowest_group(rmask)) * kSymT;
@@ -236,14 +242,22 @@ __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ desc
             load_tile(ring + s * kSymTile, tiles + entry_tile(lst[s], G) * kSymTile, &bars[s], pol);
     }
     for (int k = tid; k < nt_cta; k += kT) tl[k] = lst[k];
-    for (int p = p_lo + tid; p < np; p += kT) ysh[p - p_lo] = 0.0f;
-    stage_x(xs, sd, G, cmask, p_lo, min(np, a_end * kSymT), xsh, tid, kT);
+    const int p_end = min(np, a_end * kSymT);
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+        for (int p = p_lo + tid; p < np; p += kT) ysh[q * span_max + p - p_lo] = 0.0f;
+        if (q < nmem) {
+            stage_x(xs, descs[sub + q * n_real], G, cmask, p_lo, p_end, xsh + q * span_max, tid, kT);
+        } else {   // an empty member slot of the group reads zeros
+            for (int p = p_lo + tid; p < p_end; p += kT) xsh[q * span_max + p - p_lo] = 0.0f;
+        }
+    }
     __syncthreads();
 
     // thread (rg, cq): rows 8 rg .. 8 rg + 7 and columns 4 cq .. 4 cq + 3 of a tile
     // (16-byte shared loads; a half-warp covers one row group)
     const int rg = tid >> 4, cq = tid & 15;
-    float acc[8], xa[8];
+    float acc[NR][8], xa[NR][8];
     int cur = -1, k = 0, slot = 0;
     uint32_t phase = 0;
     bool bad = false;
@@ -252,12 +266,14 @@ __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ desc
     // barrier: only this half-warp writes these rows before the next tile's barrier.
     auto flush = [&](int row) {
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            float v = acc[r];
+        for (int q = 0; q < NR; ++q)
 #pragma unroll
-            for (int o = 1; o < 16; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (cq == r) ysh[row * kSymT + rg * 8 + r - p_lo] += v;
-        }
+            for (int r = 0; r < 8; ++r) {
+                float v = acc[q][r];
+#pragma unroll
+                for (int o = 1; o < 16; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (cq == r) ysh[q * span_max + row * kSymT + rg * 8 + r - p_lo] += v;
+            }
     };
     for (; k < nt_cta; ++k) {
         const uint32_t e = tl[k];
@@ -266,29 +282,39 @@ __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ desc
             if (cur >= 0) flush(cur);
             cur = ca;
 #pragma unroll
-            for (int r = 0; r < 8; ++r) {
-                acc[r] = 0.0f;
-                xa[r] = xsh[ca * kSymT + rg * 8 + r - p_lo];
-            }
+            for (int q = 0; q < NR; ++q)
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    acc[q][r] = 0.0f;
+                    xa[q][r] = xsh[q * span_max + ca * kSymT + rg * 8 + r - p_lo];
+                }
         }
         const bool ok = mbar_wait(&bars[slot], phase);
         const float4* T = reinterpret_cast<const float4*>(ring + slot * kSymTile) + rg * 8 * (kSymT / 4) + cq;
-        const float4 xb = (cf & 1) ? *reinterpret_cast<const float4*>(xsh + cb * kSymT + 4 * cq - p_lo)
-                                   : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        float4 col = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        float4 xb[NR], col[NR];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+            xb[q] = (cf & 1) ? *reinterpret_cast<const float4*>(xsh + q * span_max + cb * kSymT + 4 * cq - p_lo)
+                             : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            col[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
         if (ok) {
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
                 const float4 m = T[r * (kSymT / 4)];
-                acc[r] = fmaf(m.x, xb.x, fmaf(m.y, xb.y, fmaf(m.z, xb.z, fmaf(m.w, xb.w, acc[r]))));
-                col.x = fmaf(m.x, xa[r], col.x);
-                col.y = fmaf(m.y, xa[r], col.y);
-                col.z = fmaf(m.z, xa[r], col.z);
-                col.w = fmaf(m.w, xa[r], col.w);
+#pragma unroll
+                for (int q = 0; q < NR; ++q) {
+                    acc[q][r] = fmaf(m.x, xb[q].x, fmaf(m.y, xb[q].y, fmaf(m.z, xb[q].z, fmaf(m.w, xb[q].w, acc[q][r]))));
+                    col[q].x = fmaf(m.x, xa[q][r], col[q].x);
+                    col[q].y = fmaf(m.y, xa[q][r], col[q].y);
+                    col[q].z = fmaf(m.z, xa[q][r], col[q].z);
+                    col[q].w = fmaf(m.w, xa[q][r], col[q].w);
+                }
             }
         }
-        float* rd = red + (k & 1) * 8 * 64;
-        *reinterpret_cast<float4*>(rd + rg * 64 + 4 * cq) = col;
+        float* rd = red + (k & 1) * NR * 8 * 64;
+#pragma unroll
+        for (int q = 0; q < NR; ++q) *reinterpret_cast<float4*>(rd + q * 512 + rg * 64 + 4 * cq) = col[q];
         bad = __syncthreads_or(!ok) != 0;   // also: every thread is done with ring slot `slot`
         if (bad) break;
         if (tid == 0 && k + st < nt_cta) {
@@ -296,11 +322,14 @@ __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ desc
             load_tile(ring + slot * kSymTile, tiles + entry_tile(en, G) * kSymTile, &bars[slot], pol);
             ++issued;
         }
-        if ((cf & 2) && tid < 64) {   // transposed role: column tid of the tile, 8 row groups in order
-            float sum = rd[tid];
+        if (cf & 2) {   // transposed role: column c of the tile for member q, 8 row groups in order
+            for (int t = tid; t < 64 * NR; t += kT) {
+                const int q = t >> 6, c = t & 63;
+                float sum = rd[q * 512 + c];
 #pragma unroll
-            for (int q = 1; q < 8; ++q) sum += rd[q * 64 + tid];
-            ysh[cb * kSymT + tid - p_lo] += (cf & 4) ? -sum : sum;
+                for (int g = 1; g < 8; ++g) sum += rd[q * 512 + g * 64 + c];
+                ysh[q * span_max + cb * kSymT + c - p_lo] += (cf & 4) ? -sum : sum;
+            }
         }
         if (++slot == st) {
             slot = 0;
@@ -313,7 +342,8 @@ __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ desc
         atomicExch(err, 1);
     }
 
-    cluster_store(cluster, ysh, sd, G, rmask, r_lo, p_lo, np, cl, go, tid, kT);
+    for (int q = 0; q < nmem; ++q)
+        cluster_store(cluster, ysh + q * span_max, descs[sub + q * n_real], G, rmask, r_lo, p_lo, np, cl, go, tid, kT);
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -358,13 +388,13 @@ __global__ void __launch_bounds__(kTW) k_symgemv_ws(const SymDesc* __restrict__ 
     cg::cluster_group cluster = cg::this_cluster();
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int sub = ranges[4 * blockIdx.x + 3];
+    const int sub = ranges[kSymRng * blockIdx.x + 3];
     const SymDesc sd = descs[sub];
     const Groups G{sd.t0[1], sd.t0[2], sd.t0[3], sd.n[0], sd.n[1], sd.n[2]};
     const int np = G.nt * kSymT;
-    const uint32_t* lst = tlist + ranges[4 * blockIdx.x];
-    const int nt_cta = ranges[4 * blockIdx.x + 1];
-    const int a_end = ranges[4 * blockIdx.x + 2];
+    const uint32_t* lst = tlist + ranges[kSymRng * blockIdx.x];
+    const int nt_cta = ranges[kSymRng * blockIdx.x + 1];
+    const int a_end = ranges[kSymRng * blockIdx.x + 2];
     const float* tiles = Msym + sd.toff;
     const int p_lo = G.first(lowest_group(rmask | cmask)) * kSymT;
     const int r_lo = G.first(lowest_group(rmask)) * kSymT;
@@ -522,6 +552,16 @@ __global__ void k_sym_pack(const SymDesc* __restrict__ descs, const MatDesc* __r
 
 }  // namespace
 
+// Ensemble copies of a subdomain served by one CTA: 1 for the single-member
+// forms, 2 or 4 for the ensemble form.
+int sym_members_per_cta(const dd_handle* h, int mode) {
+    if (h->sym_ws[mode] != 2) return 1;
+    return h->members <= 2 ? 2 : 4;
+}
+
+// Shared memory of the ensemble form with nr members per CTA at the deepest ring.
+size_t sym_smem_bytes_nr(const dd_handle* h, int nr) { return sym_smem(h->sym_np_max, kSymStages, h->sym_max_tiles, nr); }
+
 size_t sym_smem_bytes(const dd_handle* h) {
     return std::max(sym_smem(h->sym_np_max, kSymStages, h->sym_max_tiles),
                     sym_smem_ws(h->sym_np_max, kSymStages, h->sym_max_tiles));
@@ -608,8 +648,8 @@ void sym_ranges(dd_handle* h, int mode, int cl) {
     h->sym_nl[mode] = 0;
     if (!sym_masks(mode, &rmask, &cmask)) return;
     const int R = std::max(1, h->members);
-    for (int q = 0; q < h->n_sub; ++q) {
-        const int s0 = q / R, sub = (q % R) * h->n_sub_real + s0;
+    const int per = sym_members_per_cta(h, mode);   // ensemble copies served by one CTA
+    for (int s0 = 0; s0 < h->n_sub_real; ++s0) {
         const SymDesc& sd = h->sym[s0];
         const int nt = sd.t0[3];
         std::vector<int64_t> per_row(nt, 0);
@@ -619,25 +659,29 @@ void sym_ranges(dd_handle* h, int mode, int cl) {
                 if (sym_tile_flags(sd.t0, a, b, rmask, cmask) & 3) ++per_row[a];
             total += per_row[a];
         }
-        int a = 0;
-        int64_t run = 0, first = h->sym_tl_off[mode][s0];
-        for (int c = 0; c < cl; ++c) {
-            const int begin = a;
-            if (c == cl - 1) {
-                a = nt;
-            } else {
-                const int64_t target = total * (c + 1) / cl;
-                while (a < nt && run + per_row[a] <= target) run += per_row[a++];
-                if (a < nt && target - run > run + per_row[a] - target) run += per_row[a++];
+        for (int m0 = 0; m0 < R; m0 += per) {
+            const int nmem = std::min(per, R - m0), sub = m0 * h->n_sub_real + s0;
+            int a = 0;
+            int64_t run = 0, first = h->sym_tl_off[mode][s0];
+            for (int c = 0; c < cl; ++c) {
+                const int begin = a;
+                if (c == cl - 1) {
+                    a = nt;
+                } else {
+                    const int64_t target = total * (c + 1) / cl;
+                    while (a < nt && run + per_row[a] <= target) run += per_row[a++];
+                    if (a < nt && target - run > run + per_row[a] - target) run += per_row[a++];
+                }
+                int64_t n = 0;
+                for (int q = begin; q < a; ++q) n += per_row[q];
+                h->sym_rng[mode].push_back((int32_t)first);
+                h->sym_rng[mode].push_back((int32_t)n);
+                h->sym_rng[mode].push_back(n ? a : 0);
+                h->sym_rng[mode].push_back(sub);
+                h->sym_rng[mode].push_back(nmem);
+                first += n;
+                h->sym_nl[mode] = std::max<int32_t>(h->sym_nl[mode], (int32_t)n);
             }
-            int64_t n = 0;
-            for (int q = begin; q < a; ++q) n += per_row[q];
-            h->sym_rng[mode].push_back((int32_t)first);
-            h->sym_rng[mode].push_back((int32_t)n);
-            h->sym_rng[mode].push_back(n ? a : 0);
-            h->sym_rng[mode].push_back(sub);
-            first += n;
-            h->sym_nl[mode] = std::max<int32_t>(h->sym_nl[mode], (int32_t)n);
         }
     }
 }
@@ -657,17 +701,21 @@ int launch_symgemv(const dd_handle* h, int mode, XSrc xs, GemvOut go, const int3
     xs.sc = h->d.sc;
     const int span = sym_span(h, mode);
     const int st = h->sym_st[mode];
-    const bool ws = h->sym_ws[mode] != 0;
-    const size_t smem = ws ? sym_smem_ws(span, st, h->sym_nl[mode]) : sym_smem(span, st, h->sym_nl[mode]);
-    auto kern = ws ? k_symgemv_ws : k_symgemv;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sym_smem_bytes(h));
+    const int form = h->sym_ws[mode];
+    const int nr = sym_members_per_cta(h, mode);
+    const bool ws = form == 1;
+    const size_t smem = ws ? sym_smem_ws(span, st, h->sym_nl[mode]) : sym_smem(span, st, h->sym_nl[mode], nr);
+    auto kern = ws ? k_symgemv_ws : (nr == 4 ? k_symgemv<4> : (nr == 2 ? k_symgemv<2> : k_symgemv<1>));
+    const size_t cap = nr > 1 ? sym_smem_bytes_nr(h, nr) : sym_smem_bytes(h);
+    if (cap > 227 * 1024) return (int)cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return (int)e;
     const int cl = h->sym_cl[mode];
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(h->n_sub * cl));
+    cfg.gridDim = dim3((unsigned)(h->sym_rng[mode].size() / kSymRng));
     cfg.blockDim = dim3(ws ? kTW : kT);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = S(stream);

@@ -47,9 +47,11 @@ def oracle_member(w, dt, n, pairs, amp):
     return newmark.run(T, S, dt, src, w.d2G(dt, n), n, keep=True)["fields"]
 
 
-def run_ensemble(w, dt, n, prm, sources):
+def run_ensemble(w, dt, n, prm, sources, after_factor=None):
     fs = D.FieldSolver(w.xyz, w.tets, w.part, w.n_sub, w.eps, w.mu, prm).bind()
     fs.factor(dt)
+    if after_factor:
+        after_factor(fs)
     R, nd = fs.members, fs.n_dof_member
     assert R == len(sources)
     d2g = w.d2G(dt, n)
@@ -120,6 +122,30 @@ def test_ensemble_ragged_rcb_mixed():
     for r, (pairs, amp) in enumerate(sources):
         err = rel_err(f[:, r], oracle_member(w, dt, n, pairs, amp))
         assert err[2:].max() <= 1e-8, (r, err.max())
+
+
+@pytest.mark.parametrize("form", [(2, 1, 2, 0), (2, 2, 3, 2), (2, 8, 4, 1), (0, 2, 3, 1), (1, 1, 4, 0)])
+def test_packed_kernel_forms_for_ensembles(form):
+    """Each packed-tile kernel form (ws, cl, st, keep) pinned for every packed kind:
+    form 2 serves the copies of a subdomain from one CTA (3 members: a group of 4
+    with one empty slot); every member matches its oracle."""
+    need_gpu()
+    ws, cl, st, keep = form
+    w = W.config(1)
+    dt = DT["config1"]["dt"]
+    n = 30
+    sources = member_sources(w, w.dims)
+
+    def pin(fs):
+        for kind in ("local", "iface_rows", "coupled"):
+            D.dd_set_sym_config(fs.h, kind, cl, st, keep, ws)
+
+    prm = D.make_params(precision=D.DD_MIXED, tol=1e-5, refine_tol=1e-12, max_refine=8, solver=G, members=3)
+    f, stats = run_ensemble(w, dt, n, prm, sources, after_factor=pin)
+    assert all(s["status"] == 0 for s in stats)
+    for r, (pairs, amp) in enumerate(sources):
+        err = rel_err(f[:, r], oracle_member(w, dt, n, pairs, amp))
+        assert err[2:].max() <= 1e-8, (form, r, err.max())
 
 
 def test_silent_member_stays_zero_and_the_other_matches_the_single_problem():
