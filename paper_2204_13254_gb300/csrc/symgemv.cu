@@ -639,8 +639,8 @@ void build_sym(dd_handle* h) {
 // Work of each of the cl CTAs of every subdomain for `mode`: contiguous tile-row
 // ranges, CTA c ending where the running tile count comes closest to (c + 1) / cl
 // of the subdomain's total; stored as (first entry in the mode's tile list, tile
-// count, end tile row, subdomain).  Ensemble copies of a subdomain follow each
-// other (they stream the same tiles, which L2 then serves).
+// count, end tile row, subdomain, members served).  Ensemble copies of a
+// subdomain follow each other (they stream the same tiles, which L2 then serves).
 void sym_ranges(dd_handle* h, int mode, int cl) {
     int rmask, cmask;
     h->sym_rng[mode].clear();
@@ -684,6 +684,21 @@ void sym_ranges(dd_handle* h, int mode, int cl) {
             }
         }
     }
+    // Largest clusters first (longest CTA tile list, stable): when the grid is larger than
+    // one wave, the short clusters fill the slots the long ones leave at the end.
+    std::vector<int32_t>& rng = h->sym_rng[mode];
+    const size_t per_cluster = (size_t)cl * kSymRng, ncl = rng.size() / per_cluster;
+    std::vector<int32_t> longest(ncl, 0);
+    std::vector<size_t> order(ncl);
+    for (size_t q = 0; q < ncl; ++q) {
+        order[q] = q;
+        for (int c = 0; c < cl; ++c) longest[q] = std::max(longest[q], rng[q * per_cluster + c * kSymRng + 1]);
+    }
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return longest[x] > longest[y]; });
+    std::vector<int32_t> sorted;
+    sorted.reserve(rng.size());
+    for (size_t q : order) sorted.insert(sorted.end(), rng.begin() + q * per_cluster, rng.begin() + (q + 1) * per_cluster);
+    rng.swap(sorted);
 }
 
 int launch_sym_pack(const dd_handle* h, void* stream) {
