@@ -207,6 +207,14 @@ def cpu_baseline(cfg, dt, full_iters, n_sub_full, n_steps=6):
 # GPU leg
 # ----------------------------------------------------------------------------
 
+def packed_kernel(tiles, stage, solver):
+    """Name of the packed-tile kernel form the tuner chose for a stage's GEMV kind."""
+    cfg = next((v for k, v in (tiles or {}).items() if k.startswith("packed")), {})
+    kind = "local" if stage == "local_solve" else ("coupled" if solver == "gmres" else "iface_rows")
+    ws = cfg.get(kind, (0, 0, 0, 0))[3]
+    return {0: "k_symgemv<1>", 1: "k_symgemv_ws", 2: "k_symgemv<NR>"}.get(ws, "k_symgemv")
+
+
 def run_ours(args, rank, world, local):
     import torch
     from paper_2204_13254_gb300 import dd as D
@@ -607,7 +615,7 @@ def main():
         "rel_err_mixed_vs_fp64": r["rel"],
         "setup_s": r["t_setup"], "factor_s": r["t_factor"], "autotune_s": r["t_tune"],
         "gemv_tiles": r["tiles"],
-        "roofline": {"bound": "hbm", "kernel": (f"k_symgemv (packed FP32 tiles, {dom})"
+        "roofline": {"bound": "hbm", "kernel": (f"{packed_kernel(r['tiles'], dom, args.solver)} (packed FP32 tiles, {dom})"
                                                 if head == "mixed" and not args.no_sym and dom in ("local_solve", "iface_apply")
                                                 else f"k_gemv<{'float' if head == 'mixed' else 'double'}> ({dom})"),
                      "achieved": achieved, "peak": peak,
