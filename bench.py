@@ -626,7 +626,7 @@ def main():
                 "h2d_bytes_per_step": int(sizes.n_dof * 8), "d2h_bytes_per_step": int(sizes.n_dof * 8)},
         "gpu_launches": int(r["launches32"] if head == "mixed" else r["launches64"]),
         "launch_mode": "eager" if args.eager else f"CUDA graph per step (Krylov loop as WHILE node, {args.chunk} it/body)",
-        "fp32_storage": "dense" if args.no_sym else "packed symmetric 64x64 tiles (local solve, interface rows, coupled operator)",
+        "fp32_storage": "dense" if args.no_sym else "packed symmetric 64x64 tiles (local solve, interface rows, coupled operator; the recovery too for ensembles)",
         "interface_solver": {"cg": "Schur complement (Eq. f1schur), Jacobi CG",
                              "gmres": "coupled Eqs. F1lr + F1uc, GMRES(20), diagonal preconditioner"}[args.solver],
         "warm_start": {1: "previous step's multipliers", 2: "extrapolated multipliers 2l(n-1)-l(n-2)"}.get(args.warm, args.warm),

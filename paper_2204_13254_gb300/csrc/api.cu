@@ -125,7 +125,7 @@ struct Prof {
 // algorithmic bytes of one full GEMV launch of `mode` at precision `prec`
 double mb(const dd_handle* h, int mode, int prec) {
     if (prec != DD_MIXED) return h->mode_bytes[mode];
-    if (h->prm.sym_fp32 && h->sym_ok && h->mode_bytes_sym[mode] > 0.0) return h->mode_bytes_sym[mode];
+    if (h->prm.sym_fp32 && h->sym_ok && sym_active(h, mode) && h->mode_bytes_sym[mode] > 0.0) return h->mode_bytes_sym[mode];
     return h->mode_bytes32[mode];
 }
 
@@ -1723,8 +1723,7 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
                                       // in L2, kernel form; cache lines "key 2 mode cl st keep ws"
     int n_sym = 0;
     for (int m = 0; m < GEMV_NMODES; ++m) {
-        int rm, cm;
-        if (sym_masks(m, &rm, &cm)) ++n_sym;
+        if (sym_active(h, m)) ++n_sym;
     }
     if (cache_path && *cache_path) {
         std::ifstream f(cache_path);
@@ -1732,12 +1731,12 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
         while (std::getline(f, line)) {
             std::istringstream is(line);
             std::string k;
-            int p, m, lpr, rows, rm, cm;
+            int p, m, lpr, rows;
             if (!(is >> k >> p >> m >> lpr >> rows) || k != key || m < 0 || m >= GEMV_NMODES) continue;
             if (p >= 0 && p < 2 && (lpr == 8 || lpr == 16 || lpr == 32) && rows >= kMinRowsPerTask)
                 found[{p, m}] = TileCfg{lpr, rows};
             int keep = 0, ws = 0;
-            if (p == 2 && sym_masks(m, &rm, &cm) && (lpr == 1 || lpr == 2 || lpr == 4 || lpr == 8) && rows >= 2 &&
+            if (p == 2 && sym_active(h, m) && (lpr == 1 || lpr == 2 || lpr == 4 || lpr == 8) && rows >= 2 &&
                 rows <= kSymStages && (is >> keep >> ws) && keep >= 0 && keep <= h->n_sub && ws >= 0 && ws <= 2)
                 found_cl[m] = SymCfg{lpr, rows, keep, ws};
         }
@@ -1760,9 +1759,8 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
         for (int p = 0; p < 2 && !rc; ++p) {
             const int prec = p == 0 ? DD_FP64 : DD_MIXED;
             for (int m = 0; m < GEMV_NMODES && !rc; ++m) {
-                int rm, cm;
                 const bool sym_saved = h->prm.sym_fp32 != 0;
-                if (p == 1 && h->sym_ok && sym_masks(m, &rm, &cm)) {
+                if (p == 1 && h->sym_ok && sym_active(h, m)) {
                     // packed symmetric tiles: time both kernel forms with 1, 2, 4 and 8 CTAs per subdomain and
                     // rings of 2, 3 and 4 tiles
                     h->prm.sym_fp32 = 1;
@@ -1912,8 +1910,7 @@ int dd_get_tiles(const dd_handle* h, int32_t* lpr, int32_t* rows) {
 int dd_get_sym_config(const dd_handle* h, int32_t* cl, int32_t* st, int32_t* keep, int32_t* ws) {
     if (!h) return DD_ERR_ARG;
     for (int m = 0; m < GEMV_NMODES; ++m) {
-        int rm, cmk;
-        const bool on = sym_masks(m, &rm, &cmk);
+        const bool on = sym_active(h, m);
         if (cl) cl[m] = on ? h->sym_cl[m] : 0;
         if (st) st[m] = on ? h->sym_st[m] : 0;
         if (keep) keep[m] = on ? h->sym_keep[m] : 0;
@@ -1924,8 +1921,7 @@ int dd_get_sym_config(const dd_handle* h, int32_t* cl, int32_t* st, int32_t* kee
 
 int dd_set_sym_config(dd_handle* h, int32_t kind, int32_t cl, int32_t st, int32_t keep, int32_t ws, void* stream) {
     if (!h) return DD_ERR_ARG;
-    int rm, cm;
-    if (kind < 0 || kind >= GEMV_NMODES || !sym_masks(kind, &rm, &cm))
+    if (kind < 0 || kind >= GEMV_NMODES || !sym_active(h, kind))
         return h->fail(DD_ERR_ARG, "dd_set_sym_config: not a packed GEMV kind");
     if (!(cl == 1 || cl == 2 || cl == 4 || cl == 8) || st < 2 || st > kSymStages || keep < 0 || keep > h->n_sub ||
         ws < 0 || ws > 2)

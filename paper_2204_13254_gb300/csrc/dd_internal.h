@@ -69,6 +69,7 @@ DD_HD inline int64_t sym_tile_index(int a, int b, int t1, int nt) {
 DD_HD inline bool sym_masks(int mode, int* rmask, int* cmask) {
     switch (mode) {
         case 0: *rmask = 7; *cmask = 3; return true;   // GEMV_LOCAL:   rows all, cols r
+        case 3: *rmask = 3; *cmask = 6; return true;   // GEMV_RECOVER: rows r, cols Gamma c (ensembles only)
         case 5: *rmask = 2; *cmask = 6; return true;   // GEMV_SCHUR_G: rows Gamma, cols Gamma c
         case 6: *rmask = 6; *cmask = 6; return true;   // GEMV_COUPLED: rows Gamma c, cols Gamma c
         default: return false;
@@ -547,6 +548,9 @@ void sym_ranges(dd_handle* h, int mode, int cl);
 int launch_sym_pack(const dd_handle* h, void* stream);
 int launch_symgemv(const dd_handle* h, int mode, XSrc xs, GemvOut go, const int32_t* skip, void* stream);
 size_t sym_smem_bytes(const dd_handle* h);
+// Packed kinds in use: the recovery reads the packed tiles only for an ensemble (its I x [Gamma|c]
+// rectangle has no symmetric twin, so one problem gains almost nothing; an ensemble shares the reads).
+bool sym_active(const dd_handle* h, int mode);
 size_t sym_smem_bytes_nr(const dd_handle* h, int nr);
 int sym_members_per_cta(const dd_handle* h, int mode);
 

@@ -1140,7 +1140,7 @@ int launch_gemv(const dd_handle* h, int mode, int prec, XSrc xs, GemvOut go, boo
     const int32_t* done = check_done ? &h->d.sc->done : skip_flag;
     {
         int rm, cm;
-        if (prec == DD_MIXED && h->prm.sym_fp32 && h->sym_ok && sym_masks(mode, &rm, &cm))
+        if (prec == DD_MIXED && h->prm.sym_fp32 && h->sym_ok && sym_active(h, mode))
             return launch_symgemv(h, mode, xs, go, done, stream);
     }
     const unsigned nb = (unsigned)tl.size();

@@ -552,6 +552,11 @@ __global__ void k_sym_pack(const SymDesc* __restrict__ descs, const MatDesc* __r
 
 }  // namespace
 
+bool sym_active(const dd_handle* h, int mode) {
+    int rm, cm;
+    return sym_masks(mode, &rm, &cm) && (mode != GEMV_RECOVER || h->members > 1);
+}
+
 // Ensemble copies of a subdomain served by one CTA: 1 for the single-member
 // forms, 2 or 4 for the ensemble form.
 int sym_members_per_cta(const dd_handle* h, int mode) {

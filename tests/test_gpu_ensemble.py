@@ -126,9 +126,10 @@ def test_ensemble_ragged_rcb_mixed():
 
 @pytest.mark.parametrize("form", [(2, 1, 2, 0), (2, 2, 3, 2), (2, 8, 4, 1), (0, 2, 3, 1), (1, 1, 4, 0)])
 def test_packed_kernel_forms_for_ensembles(form):
-    """Each packed-tile kernel form (ws, cl, st, keep) pinned for every packed kind:
-    form 2 serves the copies of a subdomain from one CTA (3 members: a group of 4
-    with one empty slot); every member matches its oracle."""
+    """Each packed-tile kernel form (ws, cl, st, keep) pinned for every packed kind
+    (for an ensemble the recovery reads the packed tiles too): form 2 serves the
+    copies of a subdomain from one CTA (3 members: a group of 4 with one empty
+    slot); every member matches its oracle."""
     need_gpu()
     ws, cl, st, keep = form
     w = W.config(1)
@@ -137,8 +138,9 @@ def test_packed_kernel_forms_for_ensembles(form):
     sources = member_sources(w, w.dims)
 
     def pin(fs):
-        for kind in ("local", "iface_rows", "coupled"):
+        for kind in ("local", "recover", "iface_rows", "coupled"):   # the recovery is packed for ensembles
             D.dd_set_sym_config(fs.h, kind, cl, st, keep, ws)
+        assert set(D.dd_get_sym_config(fs.h)) == {"local", "recover", "iface_rows", "coupled"}
 
     prm = D.make_params(precision=D.DD_MIXED, tol=1e-5, refine_tol=1e-12, max_refine=8, solver=G, members=3)
     f, stats = run_ensemble(w, dt, n, prm, sources, after_factor=pin)
