@@ -97,7 +97,8 @@ typedef struct {
  * warm_start 1 = start each interface solve from the previous multipliers;
  *            2 = start the first solve of a step from the linear extrapolation
  *            2 lambda^{n-1} - lambda^{n-2} of the previous steps' multipliers
- *            (once two steps of history exist; the adjoint march uses 1).
+ *            (the coupled GMRES: of [lambda; x_c], DP2 [lambda^(1); lambda^(2);
+ *            x_c]) once two steps of history exist; the adjoint march uses 1.
  * refine_tol DD_MIXED only: stop refining a step when the FP64 residual of the
  *            step's linear system satisfies ||r||_2 <= refine_tol * ||b||_2.
  * max_refine DD_MIXED only: cap on FP32 correction solves per step.
@@ -117,8 +118,9 @@ typedef struct {
  *            solved by GMRES(restart) with right preconditioning (the
  *            residual tested is the unpreconditioned one), classical
  *            Gram-Schmidt applied twice, Givens rotations; warm start from
- *            the previous solve's [lambda; x_c].  DD_FP64 and warm_start 0/1
- *            only (DD_ERR_ARG otherwise).  K~cc^-1 is not used by this solver.
+ *            the previous solve's [lambda; x_c] (warm_start 2: extrapolated).
+ *            DD_FP64 or DD_MIXED (FP32 Krylov vectors inside the FP64
+ *            refinement).  K~cc^-1 is not used by this solver.
  * restart    GMRES restart length m, 1..DD_MAX_RESTART (the paper: 20).
  * scheme     DD_SCHEME_DP1 (default) or DD_SCHEME_DP2.  DP2 (Sec. III-B, read for
  *            the edge-only step system A = T + dt^2/4 S): every local matrix

@@ -59,6 +59,7 @@ int check_params(dd_handle* h, const dd_params& p) {
     if (!(p.tol > 0.0) || p.max_it < 1 || p.chunk < 1 || p.max_refine < 1 || !(p.refine_tol > 0.0))
         return h->fail(DD_ERR_ARG, "tol, refine_tol must be > 0 and max_it, chunk, max_refine >= 1");
     if (p.sym_fp32 != 0 && p.sym_fp32 != 1) return h->fail(DD_ERR_ARG, "sym_fp32 must be 0 or 1");
+    if (p.warm_start < 0 || p.warm_start > 2) return h->fail(DD_ERR_ARG, "warm_start must be 0, 1 or 2");
     if (p.scheme != DD_SCHEME_DP1 && p.scheme != DD_SCHEME_DP2)
         return h->fail(DD_ERR_ARG, "scheme must be DD_SCHEME_DP1 or DD_SCHEME_DP2");
     if (p.scheme == DD_SCHEME_DP2 && p.solver != DD_SOLVER_COUPLED_GMRES)
@@ -68,7 +69,6 @@ int check_params(dd_handle* h, const dd_params& p) {
         return h->fail(DD_ERR_ARG, "solver must be DD_SOLVER_SCHUR_CG or DD_SOLVER_COUPLED_GMRES");
     if (p.solver == DD_SOLVER_COUPLED_GMRES) {
         if (p.restart < 1 || p.restart > kMaxRestart) return h->fail(DD_ERR_ARG, "restart must be in 1..DD_MAX_RESTART");
-        if (p.warm_start == 2) return h->fail(DD_ERR_ARG, "warm_start 2 applies to the Schur CG only");
     }
     if (p.members < 1 || p.members > kMaxMembers) return h->fail(DD_ERR_ARG, "members must be in 1..64");
     if (p.members > 1 && p.solver != DD_SOLVER_COUPLED_GMRES)
@@ -254,6 +254,10 @@ size_t dd_workspace_layout(dd_handle* h, bool assign) {
     L.take(d.lamf_adj, nm);
     L.take(d.lam_prev, nm);
     L.take(d.lam_prev_adj, nm);
+    L.take(d.xC_prev, nc);
+    L.take(d.xC_prev_adj, nc);
+    L.take(d.lam2_prev, nm);
+    L.take(d.lam2_prev_adj, nm);
     L.take(d.tet_dof, 6 * (size_t)h->n_tets);
     L.take(d.That, 36 * (size_t)h->n_tets);
     {
@@ -1104,13 +1108,22 @@ namespace {
 // eager and graph launches extrapolate on the same steps.
 int extrapolate_lambda(dd_handle* h, int prec, cudaStream_t s) {
     if (h->prm.warm_start != 2 || h->mult_dof.empty()) return DD_OK;
-    const size_t nm = h->mult_dof.size();
+    const size_t nm = h->mult_dof.size(), nc = h->corner_dof.size();
+    const bool gm = h->prm.solver == DD_SOLVER_COUPLED_GMRES, dp2 = h->factored_scheme == DD_SCHEME_DP2;
     if (!h->lam_valid && !h->capturing) {
         CK(h, (int)cudaMemsetAsync(h->d.lam, 0, sizeof(double) * nm, s), "memset");
         CK(h, (int)cudaMemsetAsync(h->d.lamf, 0, sizeof(float) * nm, s), "memset");
+        if (gm && nc) {
+            CK(h, (int)cudaMemsetAsync(h->d.xC, 0, sizeof(double) * nc, s), "memset");
+            CK(h, (int)cudaMemsetAsync(h->d.xCf, 0, sizeof(float) * nc, s), "memset");
+        }
+        if (dp2) {
+            CK(h, (int)cudaMemsetAsync(h->d.lam2, 0, sizeof(double) * nm, s), "memset");
+            CK(h, (int)cudaMemsetAsync(h->d.lam2f, 0, sizeof(float) * nm, s), "memset");
+        }
     }
-    Prof P(h, ST_VEC, s, 2);
-    CK(h, launch_extrapolate(h, prec == DD_MIXED ? h->d.lamf : nullptr, s), "extrapolate");
+    Prof P(h, ST_VEC, s, 2 + (gm && nc ? 1 : 0) + (dp2 ? 1 : 0));
+    CK(h, launch_extrapolate(h, prec == DD_MIXED, s), "extrapolate");
     return DD_OK;
 }
 
@@ -1423,6 +1436,8 @@ void swap_lambda(dd_handle* h) {
     std::swap(h->d.lam, h->d.lam_adj);
     std::swap(h->d.lamf, h->d.lamf_adj);
     std::swap(h->d.lam_prev, h->d.lam_prev_adj);
+    std::swap(h->d.xC_prev, h->d.xC_prev_adj);
+    std::swap(h->d.lam2_prev, h->d.lam2_prev_adj);
     std::swap(h->d.xC, h->d.xC_adj);
     std::swap(h->d.xCf, h->d.xCf_adj);
     std::swap(h->d.lam2, h->d.lam2_adj);

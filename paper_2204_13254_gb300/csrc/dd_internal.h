@@ -307,6 +307,10 @@ struct DevPtrs {
     double* mt_val = nullptr;
     double* lam_prev = nullptr;      // multipliers of the step before (warm_start 2 extrapolation)
     double* lam_prev_adj = nullptr;
+    double* xC_prev = nullptr;       // corner solution and DP2 second-side multipliers of the step
+    double* xC_prev_adj = nullptr;   // before (warm_start 2 with the coupled GMRES)
+    double* lam2_prev = nullptr;
+    double* lam2_prev_adj = nullptr;
     float* lamf_adj = nullptr;
     int32_t* tet_dof = nullptr;      // [n_tets*6] dof of each tet edge, -1 on the PEC wall
     double* That = nullptr;          // [n_tets*36] unit-eps oriented element mass matrices
@@ -528,7 +532,7 @@ int launch_jump(const dd_handle* h, const double* w, const float* wf, const doub
 int launch_pcg_init(const dd_handle* h, int have_q, double tol, const float* wf, float* zf, float* pf,
                     unsigned long long cond, int adaptive, void* stream);
 int launch_step_begin(const dd_handle* h, void* stream);
-int launch_extrapolate(const dd_handle* h, float* lamf, void* stream);
+int launch_extrapolate(const dd_handle* h, bool f32, void* stream);
 int launch_solve_end(const dd_handle* h, void* stream);
 int launch_refine_cond(const dd_handle* h, unsigned long long cond, void* stream);
 int launch_pcg_alpha(const dd_handle* h, const float* wf, float* pf, void* stream);

@@ -1197,10 +1197,19 @@ int launch_pcg_init(const dd_handle* h, int have_q, double tol, const float* wf,
     return (int)cudaGetLastError();
 }
 
-int launch_extrapolate(const dd_handle* h, float* lamf, void* stream) {
-    const int64_t nl = (int64_t)h->mult_dof.size();
+// warm_start 2: the multipliers (and, for the coupled GMRES, the corner solution
+// and DP2's second-side multipliers) of the next solve = 2 x^{n-1} - x^{n-2}.
+int launch_extrapolate(const dd_handle* h, bool f32, void* stream) {
+    const int64_t nl = (int64_t)h->mult_dof.size(), nc = (int64_t)h->corner_dof.size();
     if (nl == 0) return 0;
-    k_extrapolate<<<reduce_blocks(nl), kThreads, 0, S(stream)>>>(nl, h->d.lam, h->d.lam_prev, lamf, h->d.sc);
+    k_extrapolate<<<reduce_blocks(nl), kThreads, 0, S(stream)>>>(nl, h->d.lam, h->d.lam_prev, f32 ? h->d.lamf : nullptr,
+                                                                h->d.sc);
+    if (h->prm.solver == DD_SOLVER_COUPLED_GMRES && nc)
+        k_extrapolate<<<reduce_blocks(nc), kThreads, 0, S(stream)>>>(nc, h->d.xC, h->d.xC_prev,
+                                                                    f32 ? h->d.xCf : nullptr, h->d.sc);
+    if (h->factored_scheme == DD_SCHEME_DP2)
+        k_extrapolate<<<reduce_blocks(nl), kThreads, 0, S(stream)>>>(nl, h->d.lam2, h->d.lam2_prev,
+                                                                    f32 ? h->d.lam2f : nullptr, h->d.sc);
     k_levels_inc<<<1, 1, 0, S(stream)>>>(h->d.sc);
     return (int)cudaGetLastError();
 }

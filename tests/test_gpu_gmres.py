@@ -222,7 +222,7 @@ def test_parameter_errors_and_budget():
     fs = D.FieldSolver(w.xyz, w.tets, w.part, w.n_sub).bind()
     fs.factor(dt)
     for bad in (gmres_params(restart=0),
-                gmres_params(restart=D.DD_MAX_RESTART + 1), gmres_params(warm_start=2),
+                gmres_params(restart=D.DD_MAX_RESTART + 1), gmres_params(warm_start=3),
                 D.make_params(solver=7)):
         with pytest.raises(D.DDError) as ei:
             fs.set_params(bad)

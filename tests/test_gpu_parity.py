@@ -222,16 +222,26 @@ def test_error_status_without_fault():
     fs.close()
 
 
-@pytest.mark.parametrize("prec", [D.DD_FP64, D.DD_MIXED])
-def test_extrapolated_warm_start_matches_oracle(prec):
-    """warm_start 2 (lambda_0 = 2 lambda^{n-1} - lambda^{n-2}) changes only the CG start."""
+WARM2 = [(D.DD_FP64, D.DD_SOLVER_SCHUR_CG, D.DD_SCHEME_DP1, 0), (D.DD_MIXED, D.DD_SOLVER_SCHUR_CG, D.DD_SCHEME_DP1, 0),
+         (D.DD_FP64, D.DD_SOLVER_COUPLED_GMRES, D.DD_SCHEME_DP1, 0),
+         (D.DD_MIXED, D.DD_SOLVER_COUPLED_GMRES, D.DD_SCHEME_DP1, 1),
+         (D.DD_MIXED, D.DD_SOLVER_COUPLED_GMRES, D.DD_SCHEME_DP2, 0)]
+
+
+@pytest.mark.parametrize("prec,solver,scheme,graph", WARM2)
+def test_extrapolated_warm_start_matches_oracle(prec, solver, scheme, graph):
+    """warm_start 2 (the solve of a step starts from 2 x^{n-1} - x^{n-2}: lambda for
+    the CG, [lambda; x_c] -- DP2 [lambda1; lambda2; x_c] -- for the coupled GMRES)
+    changes only the start of the interface solve."""
     need_gpu()
     w = W.config(1)
     dt = DT["config1"]["dt"]
     n = 200
     _, _, _, _, ref = oracle_run(w, dt, n)
-    prm = D.make_params(precision=prec, tol=1e-13 if prec == D.DD_FP64 else 1e-6, refine_tol=1e-12, max_refine=6,
-                        warm_start=2)
+    fp64 = prec == D.DD_FP64
+    prm = D.make_params(precision=prec, tol=1e-13 if fp64 else (1e-6 if solver == D.DD_SOLVER_SCHUR_CG else 1e-5),
+                        refine_tol=1e-12, max_refine=8, warm_start=2, solver=solver, scheme=scheme,
+                        max_it=3000, use_graph=graph, chunk=2)
     fs, f, _, stats = gpu_run(w, dt, n, prm, probes=False)
     err = rel_err(f, ref["fields"])
     assert err[2:].max() <= (1e-10 if prec == D.DD_FP64 else 1e-8), err.max()
