@@ -437,9 +437,13 @@ int dd_profile(dd_handle* h, int enable, dd_profile_stats* out, void* stream);
  * coarse, interface rows) and each precision it times every candidate tile --
  * lanes per matrix row in {8, 16, 32} x rows per CTA in {8, 16, 32, 64, 128} --
  * on the factored operators with CUDA events (1 warm-up + 3 timed launches)
- * and keeps the fastest.  cache_path (host string, may be NULL): a text file of
- * "key precision kind lanes rows" lines keyed by device name and problem sizes;
- * a complete entry is reused without timing, new results are appended.
+ * and keeps the fastest.  For the kinds read from packed symmetric tiles
+ * (DD_MIXED, sym_fp32) it also times the kernel form, CTAs per subdomain and
+ * ring depth, then the number of subdomains kept in L2 (1 warm-up + 8 timed
+ * launches each; see dd_get_sym_config).  cache_path (host string, may be
+ * NULL): a text file of "key precision kind lanes rows" lines (and "key 2 kind
+ * cl st keep form" for the packed kinds) keyed by device name and problem
+ * sizes; a complete entry is reused without timing, new results are appended.
  * Requires dd_factor; results are bitwise unaffected only up to the order of
  * floating-point sums inside a row (lanes per row changes it).  seconds (host,
  * may be NULL) receives the wall time.  Synchronises `stream`. */

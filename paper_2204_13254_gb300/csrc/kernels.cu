@@ -1138,11 +1138,8 @@ int launch_gemv(const dd_handle* h, int mode, int prec, XSrc xs, GemvOut go, boo
         smem = 0;
     }
     const int32_t* done = check_done ? &h->d.sc->done : skip_flag;
-    {
-        int rm, cm;
-        if (prec == DD_MIXED && h->prm.sym_fp32 && h->sym_ok && sym_active(h, mode))
-            return launch_symgemv(h, mode, xs, go, done, stream);
-    }
+    if (prec == DD_MIXED && h->prm.sym_fp32 && h->sym_ok && sym_active(h, mode))
+        return launch_symgemv(h, mode, xs, go, done, stream);
     const unsigned nb = (unsigned)tl.size();
     const int lpr = h->tile[pi][mode].lpr;
     if (prec == DD_MIXED) {
