@@ -543,8 +543,7 @@ def main():
                     "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / cb["value"],
                     "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                     "data": "synthetic", "config": {"workload": W.config(args.config).name},
-                    "fp64_roofline": _fp64_roofline(st64),
-        "cpu_baseline": cb,
+                    "cpu_baseline": cb,
                     "e2e": {"value": cb["value"], "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
             print(json.dumps(line), flush=True)
         if world > 1:
@@ -594,10 +593,11 @@ def main():
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms_head / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if head == "mixed" else "f64", "data": "synthetic",
-        "config": {"workload": ("PIC cycle (1e5-particle beam push + Whitney deposition + DD field solve + Faraday), "
-                                if r["pic"] else "") + (f"{w.name}: PEC box {w.dims[0]}x{w.dims[1]}x{w.dims[2]} Kuhn cubes, {len(w.tets)} tets, "
-                                f"{sizes.n_dof} edge dofs, {w.n_sub} subdomains, {sizes.n_lambda} multipliers, "
-                                f"{sizes.n_corner} corners, Gaussian z-line pulse, dt=2xCFL={r['dt']:.6g}"),
+        "config": {"workload": w.name,
+                   "mesh": ("PIC cycle (1e5-particle beam push + Whitney deposition + DD field solve + Faraday), "
+                            if r["pic"] else "") + (f"PEC box {w.dims[0]}x{w.dims[1]}x{w.dims[2]} Kuhn cubes, {len(w.tets)} tets, "
+                            f"{sizes.n_dof} edge dofs, {w.n_sub} subdomains, {sizes.n_lambda} multipliers, "
+                            f"{sizes.n_corner} corners, Gaussian z-line pulse, dt=2xCFL={r['dt']:.6g}"),
                    "l2_policy": "inputs larger than L2 (dense subdomain operators "
                                 f"{sizes.dense_bytes_fp64 / 1e9:.1f} GB FP64 + half that FP32), no flush",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
@@ -615,6 +615,7 @@ def main():
         "rel_err_mixed_vs_fp64": r["rel"],
         "setup_s": r["t_setup"], "factor_s": r["t_factor"], "autotune_s": r["t_tune"],
         "gemv_tiles": r["tiles"],
+        "fp64_roofline": _fp64_roofline(st64),
         "roofline": {"bound": "hbm", "kernel": (f"{packed_kernel(r['tiles'], dom, args.solver)} (packed FP32 tiles, {dom})"
                                                 if head == "mixed" and not args.no_sym and dom in ("local_solve", "iface_apply")
                                                 else f"k_gemv<{'float' if head == 'mixed' else 'double'}> ({dom})"),
