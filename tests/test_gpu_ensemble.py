@@ -182,3 +182,27 @@ def test_ensemble_rejects_single_problem_features():
         fs.set_params(D.make_params(solver=G, members=3))
     assert e.value.code == D.DD_ERR_ARG
     fs.close()
+
+
+def test_five_members_two_groups():
+    """R = 5 with the multi-member form: groups of 4 and 1 copies per CTA; member r
+    carries the workload's source at amplitude a_r, so it equals a_r times the
+    oracle's unit-source march."""
+    need_gpu()
+    w = W.config(1)
+    dt = DT["config1"]["dt"]
+    n = 25
+    amps = [1.0, -0.5, 2.0, 0.25, -3.0]
+    sources = [(w.source_pairs, a) for a in amps]
+
+    def pin(fs):
+        for kind in ("local", "recover", "iface_rows", "coupled"):
+            D.dd_set_sym_config(fs.h, kind, 1, 2, 0, 2)
+
+    prm = D.make_params(precision=D.DD_MIXED, tol=1e-5, refine_tol=1e-12, max_refine=8, solver=G, members=5)
+    f, stats = run_ensemble(w, dt, n, prm, sources, after_factor=pin)
+    assert all(s["status"] == 0 for s in stats)
+    ref = oracle_member(w, dt, n, w.source_pairs, 1.0)
+    for r, a in enumerate(amps):
+        err = rel_err(f[:, r], a * ref)
+        assert err[2:].max() <= 1e-8, (r, err.max())
