@@ -169,3 +169,27 @@ def test_ensemble_setup_shares_the_operators(built):
         with pytest.raises(D.DDError) as e:
             D.dd_setup(w.xyz, w.tets, w.part, w.n_sub, params=bad)
         assert e.value.code == D.DD_ERR_ARG
+
+
+def test_ensemble_interface_mass_is_block_diagonal_by_member(built):
+    """members = R: the DP2 interface mass is the single problem's, repeated once per
+    member on the diagonal (member r's multipliers are rows r*n .. (r+1)*n - 1)."""
+    import scipy.sparse as sp
+    w = W.cavity(4, 2)
+    R = 3
+    g = D.make_params(solver=D.DD_SOLVER_COUPLED_GMRES)
+    one = D.dd_setup(w.xyz, w.tets, w.part, w.n_sub, params=g)
+    ens = D.dd_setup(w.xyz, w.tets, w.part, w.n_sub,
+                     params=D.make_params(solver=D.DD_SOLVER_COUPLED_GMRES, members=R))
+    try:
+        p1, c1, v1 = D.dd_get_interface_mass(one)
+        pR, cR, vR = D.dd_get_interface_mass(ens)
+        n = len(p1) - 1
+    finally:
+        D.dd_destroy(one)
+        D.dd_destroy(ens)
+    M1 = sp.csr_matrix((v1, c1, p1), shape=(n, n))
+    MR = sp.csr_matrix((vR, cR, pR), shape=(R * n, R * n))
+    ref = sp.block_diag([M1] * R, format="csr")
+    assert MR.nnz == ref.nnz
+    assert abs(MR - ref).max() == 0.0
