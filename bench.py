@@ -212,7 +212,7 @@ def packed_kernel(tiles, stage, solver):
     cfg = next((v for k, v in (tiles or {}).items() if k.startswith("packed")), {})
     kind = "local" if stage == "local_solve" else ("coupled" if solver == "gmres" else "iface_rows")
     ws = cfg.get(kind, (0, 0, 0, 0))[3]
-    return {0: "k_symgemv<1>", 1: "k_symgemv_ws", 2: "k_symgemv<NR>"}.get(ws, "k_symgemv")
+    return {0: "k_symgemv<1>", 1: "k_symgemv_ws", 2: "k_symgemv<NR>", 3: "k_symgemv<2>"}.get(ws, "k_symgemv")
 
 
 def run_ours(args, rank, world, local):

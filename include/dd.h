@@ -460,14 +460,15 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
  * CTA-synchronous kernel, 1 the warp-specialised one (a producer warp refills
  * the ring as the four consumer warps release slots, each consumer warp keeping
  * its own partial y), 2 (ensembles) one CTA applying every tile it loads to the
- * x of 2 or 4 ensemble copies of its subdomain (host int32[7] each, 0 for the
- * other kinds; any pointer may be NULL). */
+ * x of 2 or 4 ensemble copies of its subdomain, 3 (ensembles) the same for
+ * pairs of copies (host int32[7] each, 0 for the other kinds; any pointer may
+ * be NULL). */
 int dd_get_tiles(const dd_handle* h, int32_t* lpr, int32_t* rows);
 int dd_get_sym_config(const dd_handle* h, int32_t* cl, int32_t* st, int32_t* keep, int32_t* ws);
 
 /* Sets the packed-tile launch of GEMV kind `kind` (0, 5 or 6; 3 too for an
  * ensemble) to cl CTAs per subdomain (1, 2, 4 or 8), a ring of st tiles (2..4),
- * keep stored subdomains in L2 (0..n_sub) and kernel form ws (0, 1 or 2 as in
+ * keep stored subdomains in L2 (0..n_sub) and kernel form ws (0..3 as in
  * dd_get_sym_config), as dd_autotune would (its next run may change it again).
  * Results differ from another setting only in the order of FP32 sums.
  * DD_ERR_ARG for other kinds or values (or form 2 when its shared memory exceeds

@@ -1752,7 +1752,7 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
                 found[{p, m}] = TileCfg{lpr, rows};
             int keep = 0, ws = 0;
             if (p == 2 && sym_active(h, m) && (lpr == 1 || lpr == 2 || lpr == 4 || lpr == 8) && rows >= 2 &&
-                rows <= kSymStages && (is >> keep >> ws) && keep >= 0 && keep <= h->n_sub && ws >= 0 && ws <= 2)
+                rows <= kSymStages && (is >> keep >> ws) && keep >= 0 && keep <= h->n_sub && ws >= 0 && ws <= 3)
                 found_cl[m] = SymCfg{lpr, rows, keep, ws};
         }
     }
@@ -1793,7 +1793,8 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
                     // kernel forms: CTA-synchronous, warp-specialised and, for an ensemble whose
                     // shared memory allows it, the copies of a subdomain in one CTA
                     const bool form2 = h->members > 1 && sym_smem_bytes_nr(h, h->members <= 2 ? 2 : 4) <= 227 * 1024;
-                    const int nsweep = 12 * (form2 ? 3 : 2);
+                    const bool form3 = h->members > 2 && sym_smem_bytes_nr(h, 2) <= 227 * 1024;
+                    const int nsweep = 12 * (form3 ? 4 : (form2 ? 3 : 2));
                     for (int cand = 0; cand < nsweep + (repeated ? 3 : 0) && !rc; ++cand) {
                         int cl, st, keep = 0, ws;
                         if (cand < nsweep) {
@@ -1940,9 +1941,10 @@ int dd_set_sym_config(dd_handle* h, int32_t kind, int32_t cl, int32_t st, int32_
     if (kind < 0 || kind >= GEMV_NMODES || !sym_active(h, kind))
         return h->fail(DD_ERR_ARG, "dd_set_sym_config: not a packed GEMV kind");
     if (!(cl == 1 || cl == 2 || cl == 4 || cl == 8) || st < 2 || st > kSymStages || keep < 0 || keep > h->n_sub ||
-        ws < 0 || ws > 2)
-        return h->fail(DD_ERR_ARG, "dd_set_sym_config: cl in {1,2,4,8}, 2 <= st <= 4, 0 <= keep <= n_sub, ws in {0,1,2}");
-    if (ws == 2 && sym_smem_bytes_nr(h, h->members <= 2 ? 2 : 4) > 227 * 1024)
+        ws < 0 || ws > 3)
+        return h->fail(DD_ERR_ARG, "dd_set_sym_config: cl in {1,2,4,8}, 2 <= st <= 4, 0 <= keep <= n_sub, ws in {0..3}");
+    if ((ws == 2 && sym_smem_bytes_nr(h, h->members <= 2 ? 2 : 4) > 227 * 1024) ||
+        (ws == 3 && sym_smem_bytes_nr(h, 2) > 227 * 1024))
         return h->fail(DD_ERR_ARG, "dd_set_sym_config: the ensemble form needs more shared memory than a CTA has");
     if (!h->bound) return h->fail(DD_ERR_STATE, "dd_set_sym_config before dd_bind_workspace");
     if (h->capturing) return h->fail(DD_ERR_STATE, "dd_set_sym_config during capture");

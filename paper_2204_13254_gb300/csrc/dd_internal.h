@@ -425,7 +425,8 @@ struct dd_handle {
     int32_t sym_nl[GEMV_NMODES] = {};                      // longest tile list of one CTA (shared memory)
     int32_t sym_keep[GEMV_NMODES] = {};                    // subdomains whose tiles are kept in L2 (evict_last)
     int32_t sym_ws[GEMV_NMODES] = {};                      // packed kernel form: 0 CTA-synchronous, 1 warp-specialised,
-                                                           // 2 ensemble copies of a subdomain in one CTA
+                                                           // 2 ensemble copies of a subdomain in one CTA (up to 4),
+                                                           // 3 ensemble copies in pairs
     int32_t sym_max_tiles = 0;                     // largest tile count of one subdomain
     bool sym_ok = false;                           // the packed GEMV's shared memory fits one CTA
     size_t task_cap[GEMV_NMODES] = {};             // device capacity: tasks at the smallest row count

@@ -558,8 +558,11 @@ bool sym_active(const dd_handle* h, int mode) {
 }
 
 // Ensemble copies of a subdomain served by one CTA: 1 for the single-member
-// forms, 2 or 4 for the ensemble form.
+// forms; form 2: 4 (2 for a two-member ensemble); form 3: pairs (half the
+// shared memory of form 2, so more CTAs share an SM, at two tile reads per
+// four members).
 int sym_members_per_cta(const dd_handle* h, int mode) {
+    if (h->sym_ws[mode] == 3) return 2;
     if (h->sym_ws[mode] != 2) return 1;
     return h->members <= 2 ? 2 : 4;
 }

@@ -124,7 +124,8 @@ def test_ensemble_ragged_rcb_mixed():
         assert err[2:].max() <= 1e-8, (r, err.max())
 
 
-@pytest.mark.parametrize("form", [(2, 1, 2, 0), (2, 2, 3, 2), (2, 8, 4, 1), (0, 2, 3, 1), (1, 1, 4, 0)])
+@pytest.mark.parametrize("form", [(2, 1, 2, 0), (2, 2, 3, 2), (2, 8, 4, 1), (3, 1, 2, 0), (3, 4, 3, 1), (0, 2, 3, 1),
+                                  (1, 1, 4, 0)])
 def test_packed_kernel_forms_for_ensembles(form):
     """Each packed-tile kernel form (ws, cl, st, keep) pinned for every packed kind
     (for an ensemble the recovery reads the packed tiles too): form 2 serves the

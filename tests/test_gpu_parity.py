@@ -313,7 +313,7 @@ def test_sym_config_rejects_bad_values():
                        D.make_params(precision=D.DD_MIXED, tol=1e-5)).bind()
     fs.factor(DT["config1"]["dt"])
     for args in [("corner_rows", 1, 2, 0, 0), ("recover", 1, 2, 0, 0), ("local", 3, 2, 0, 0), ("local", 1, 5, 0, 0), ("local", 1, 1, 0, 0),
-                 ("local", 1, 2, w.n_sub + 1, 0), ("local", 1, 2, 0, 3), ("local", 1, 2, 0, -1)]:
+                 ("local", 1, 2, w.n_sub + 1, 0), ("local", 1, 2, 0, 4), ("local", 1, 2, 0, -1)]:
         with pytest.raises(RuntimeError):
             D.dd_set_sym_config(fs.h, *args)
     D.dd_set_sym_config(fs.h, "coupled", 2, 4, 1, 1)
