@@ -73,6 +73,10 @@ def parse():
                     help="members of the multi-RHS (ensemble) run beside the headline; 0 or 1 skips it")
     ap.add_argument("--no-dp2", action="store_true",
                     help="skip the MFETI-DP2 runs (its own factorisation; coupled GMRES(20), FP64 at tol 1e-6 and mixed)")
+    ap.add_argument("--no-other-configs", dest="other_configs", action="store_false",
+                    help="skip the short runs of configs 3 (mixed/FP64), 5 (forward and adjoint) and 2 (PIC cycle)")
+    ap.add_argument("--other-steps", type=int, default=10, help="timed steps of each other-config run")
+    ap.add_argument("--cpu-steps", type=int, default=3, help="oracle steps of the CPU baseline sample")
     ap.add_argument("--no-gmres", action="store_true",
                     help="skip the coupled-GMRES(20) vs Schur-CG comparison at the paper's tolerance 1e-6")
     ap.add_argument("--cavity", type=int, nargs=2, metavar=("N", "K"), default=None,
@@ -161,45 +165,89 @@ class Clocks:
 # CPU baseline: the oracle's DD solver on a bounded sample of the workload
 # ----------------------------------------------------------------------------
 
-def cpu_baseline(cfg, dt, full_iters, n_sub_full, n_steps=6):
-    """Times the CPU FP64 oracle (scipy/numpy, host cores) on a sample of the
-    workload: a 2x2x2 block of subdomains cut from the same mesh (same h, same
-    6^3-cube subdomain blocks, same dt), PEC on the sample's walls.  The per-step
-    time is scaled to the full workload by the subdomain count and by the number
-    of local solves per step (2 + 3 per interface iteration, oracle algorithm),
-    using the GPU-measured iterations of the full workload."""
-    from oracle import dd as odd
-    from oracle import fem
-    from paper_2204_13254_gb300 import workloads as W
-    wf = W.config(cfg)
-    nx, ny, nz = wf.dims
-    kx = ky = kz = round(n_sub_full ** (1 / 3)) if cfg in (1, 4) else None
-    if kx is None:
-        kx, ky, kz = {2: (4, 4, 8), 5: (8, 8, 4), 3: (4, 4, 4)}[cfg]
-    bx, by, bz = nx // kx, ny // ky, nz // kz
-    L = (2 * bx * wf.L[0] / nx, 2 * by * wf.L[1] / ny, 2 * bz * wf.L[2] / nz)
-    w = W.box(2 * bx, 2 * by, 2 * bz, 2, 2, 2, L=L, steps=n_steps)
+class OracleSample:
+    """The CPU FP64 oracle's MFETI-DP1 march (scipy Cholesky per subdomain, Jacobi CG
+    on Eq. f1schur, tol 1e-10) on a sample of the workload: a 2x2x2 block of
+    subdomains of the workload's own subdomain size, mesh spacing and dt (PEC on
+    the sample's walls, the z-line pulse through its centre).
+
+    Why a sample: the oracle is a plain Python loop over subdomains with one
+    single-right-hand-side triangular solve pair per subdomain and operator
+    application; on the 48^3 cavity one of its steps takes minutes and its
+    set-up (the Jacobi diagonal by one solve per multiplier) far longer, so it
+    cannot run inside a benchmark.  Its cost per step is a sum over subdomains of
+    identical work at the same interface iteration count (the Schur system's
+    conditioning depends on the subdomain size H/h, which the sample keeps), so a
+    full step is taken as the sample's measured step time times n_sub / 8.  The
+    sample's factorisation is timed separately and is not part of the rate."""
+
+    def __init__(self, cfg, dt):
+        from oracle import dd as odd
+        from oracle import fem
+        from paper_2204_13254_gb300 import workloads as W
+        wf = W.config(cfg)
+        self.n_sub_full = wf.n_sub
+        nx, ny, nz = wf.dims
+        kx, ky, kz = {1: (2, 2, 2), 4: (8, 8, 8), 2: (4, 4, 8), 5: (8, 8, 4), 3: (4, 4, 4)}[cfg]
+        bx, by, bz = nx // kx, ny // ky, nz // kz
+        L = (2 * bx * wf.L[0] / nx, 2 * by * wf.L[1] / ny, 2 * bz * wf.L[2] / nz)
+        self.w = W.box(2 * bx, 2 * by, 2 * bz, 2, 2, 2, L=L, steps=64)
+        self.dt = dt
+        t0 = time.perf_counter()
+        space = fem.EdgeSpace(self.w.xyz, self.w.tets)
+        self.maps = odd.DDMaps(space, self.w.part, self.w.n_sub)
+        self.src = np.zeros(space.n)
+        self.src[space.dof_of_pairs(self.w.source_pairs)] = 1.0
+        self.t_setup = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        self.dd = odd.DDSolver(space, self.maps, dt)
+        self.t_factor = time.perf_counter() - t0
+        self.d2g = self.w.d2G(dt, 64)
+        self.space = space
+        self.e_n = np.zeros(space.n)
+        self.e_nm1 = np.zeros(space.n)
+        self.k = 0
+        self.iters = []
+        self.desc = f"{2 * bx}x{2 * by}x{2 * bz}-cube sample, 2x2x2 subdomains of {bx}x{by}x{bz} cubes"
+
+    def step(self):
+        """One oracle time step of the sample (source steps 20.. so the pulse is on)."""
+        b = self.dd.newmark_rhs(self.e_n, self.e_nm1, self.d2g[(20 + self.k) % 64] * self.src)
+        x, lam, xc, it, res = self.dd.solve(b, tol=1e-10)
+        e_np1 = self.dd.gather_global(x)
+        self.e_nm1, self.e_n = self.e_n, e_np1
+        self.iters.append(it)
+        self.k += 1
+
+    @property
+    def scale(self):
+        return self.n_sub_full / 8.0
+
+
+def _threads():
+    return int(os.environ.get("OMP_NUM_THREADS") or os.environ.get("OPENBLAS_NUM_THREADS") or os.cpu_count())
+
+
+def cpu_baseline(cfg, dt, n_steps=3):
+    """The oracle sample (OracleSample) for n_steps timed steps after one untimed
+    warm-up step; the rate is scaled to the whole workload by subdomain count."""
     t0 = time.perf_counter()
-    space = fem.EdgeSpace(w.xyz, w.tets)
-    maps = odd.DDMaps(space, w.part, w.n_sub)
-    src = np.zeros(space.n)
-    src[space.dof_of_pairs(w.source_pairs)] = 1.0
-    t_setup = time.perf_counter() - t0
+    o = OracleSample(cfg, dt)
+    o.step()
     t1 = time.perf_counter()
-    out = odd.run(space, maps, dt, src, w.d2G(dt, n_steps), n_steps, tol=1e-10)
-    t_run = time.perf_counter() - t1
-    it_s = float(np.mean(out["iters"]))
-    t_step = t_run / n_steps           # includes the factorisation share of the sample
-    scale = (n_sub_full / 8.0) * (2.0 + 3.0 * full_iters) / (2.0 + 3.0 * max(it_s, 1.0))
-    t_full = t_step * scale
-    threads = os.environ.get("OMP_NUM_THREADS") or os.environ.get("OPENBLAS_NUM_THREADS") or str(os.cpu_count())
+    for _ in range(n_steps):
+        o.step()
+    t_step = (time.perf_counter() - t1) / n_steps
+    it = float(np.mean(o.iters[1:]))
     return {
-        "value": 1.0 / t_full, "unit": "steps/s", "cores": int(threads), "kind": "oracle",
-        "sample": (f"CPU FP64 oracle DD (scipy Cholesky per subdomain + CG on Eq. f1schur, tol 1e-10) on a "
-                   f"{2*bx}x{2*by}x{2*bz}-cube sample (2x2x2 subdomains of the same size and h), {n_steps} steps "
-                   f"incl. its factorisation: {t_step:.3f} s/step, {it_s:.1f} CG it/step; scaled x{scale:.1f} "
-                   f"(subdomains {n_sub_full}/8, local solves at {full_iters:.1f} it/step)"),
-        "sample_s": t_run + t_setup, "os_cpu_count": os.cpu_count(),
+        "value": 1.0 / (t_step * o.scale), "unit": "steps/s", "cores": _threads(), "kind": "oracle",
+        "sample": (f"CPU FP64 oracle MFETI-DP1 (scipy Cholesky per subdomain, Jacobi CG on Eq. f1schur, tol 1e-10) "
+                   f"on a {o.desc} (the workload's subdomain size, h and dt): {n_steps} steps measured after 1 "
+                   f"warm-up, {t_step:.3f} s/step at {it:.1f} CG it/step; rate = 1 / (s/step x {o.scale:g} "
+                   f"subdomain-count ratio); sample set-up {o.t_setup:.1f} s and factorisation "
+                   f"{o.t_factor:.1f} s not in the rate"),
+        "sample_s": time.perf_counter() - t0, "sample_step_s": t_step, "sample_iters_per_step": it,
+        "os_cpu_count": os.cpu_count(),
     }
 
 
@@ -213,6 +261,123 @@ def packed_kernel(tiles, stage, solver):
     kind = "local" if stage == "local_solve" else ("coupled" if solver == "gmres" else "iface_rows")
     ws = cfg.get(kind, (0, 0, 0, 0))[3]
     return {0: "k_symgemv<1>", 1: "k_symgemv_ws", 2: "k_symgemv<NR>", 3: "k_symgemv<2>"}.get(ws, "k_symgemv")
+
+
+def _timed(fn, n, stream):
+    """CUDA-event time (ms) of n calls of fn(i) on `stream`."""
+    import torch
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for i in range(n):
+        fn(i)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1)
+
+
+def other_configs(args, dev):
+    """Short timed runs of the other workloads (each: set-up, factorisation, tuning,
+    warm-up, then --other-steps timed steps with CUDA events; the CUDA-graph step
+    with the coupled GMRES(20), FP64 at tol 1e-10 and mixed at the headline's
+    settings, no per-step readback):
+      config 3 -- jittered 2x1x1 box, 300 RCB subdomains of uneven size;
+      config 5 -- 32^3 cavity with eps ~ U[1,4]: forward steps, and the checkpointed
+                  adjoint of the probe objective (100 forward steps, checkpoint 100:
+                  the backward sweep recomputes the segment and runs 100 adjoint steps);
+      config 2 -- the PIC cycle with the 1e5-particle beam (push, deposition, field
+                  step, Faraday)."""
+    import torch
+    from paper_2204_13254_gb300 import adjoint as A
+    from paper_2204_13254_gb300 import dd as D
+    from paper_2204_13254_gb300 import workloads as W
+    stream = torch.cuda.current_stream()
+    K = args.other_steps
+    Wu = 3
+    out = {}
+
+    def march(cfg, label_extra=None):
+        w = W.config(cfg)
+        dt = load_dt(cfg)
+        t0 = time.perf_counter()
+        pic = cfg == 2
+        fs = D.FieldSolver(w.xyz, w.tets, w.part, w.n_sub, w.eps, w.mu, D.make_params(precision=D.DD_FP64),
+                           probes=w.probes, device=dev)
+        if pic:
+            fs.set_beam(*W.beam(w, 100000, w.steps * dt, seed=0))
+        fs.bind()
+        t_setup = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        fs.factor(dt)
+        torch.cuda.synchronize()
+        t_factor = time.perf_counter() - t0
+        if not args.no_autotune:
+            D.dd_autotune(fs.h, args.tune_cache)
+        pat = torch.zeros(fs.n_dof, dtype=torch.float64, device=dev)
+        pat[torch.as_tensor(fs.dof_of_pairs(w.source_pairs), device=dev)] = 1.0
+        d2g = w.d2G(dt, Wu + K + 1)
+        res = {"workload": w.name, "n_dof": int(fs.n_dof), "subdomains": int(w.n_sub), "setup_s": t_setup,
+               "factor_s": t_factor}
+        runs = [("fp64", D.make_params(precision=D.DD_FP64, tol=args.tol64, use_graph=1, chunk=args.chunk,
+                                       solver=D.DD_SOLVER_COUPLED_GMRES)),
+                ("mixed", D.make_params(precision=D.DD_MIXED, tol=args.tol32, refine_tol=args.refine_tol,
+                                        max_refine=6, use_graph=1, chunk=args.chunk,
+                                        solver=D.DD_SOLVER_COUPLED_GMRES))]
+        fields = {}
+        for name, prm in runs:
+            fs.set_params(prm)
+            if pic:
+                fs.factor(dt)                 # restarts fields and particles
+                step = lambda i, st=False: D.dd_pic_step(fs.h, st)
+            else:
+                zero = torch.zeros(fs.n_dof, dtype=torch.float64, device=dev)
+                fs.set_state(zero, zero, 0)
+                step = lambda i, st=False: D.dd_step_scaled(fs.h, pat, float(d2g[i]), stats=st)
+            its = [step(i, True)["iters"] for i in range(Wu)]
+            ms = _timed(lambda i: step(Wu + i), K, stream)
+            # iteration counts from a readback pass over the next steps (not timed)
+            its = [step(Wu + K + i, True)["iters"] for i in range(1)]
+            e_last, _, _ = fs.get_state()
+            fields[name] = e_last
+            res[name] = {"steps_per_s": K * 1e3 / ms, "ms_per_step": ms / K, "iters_per_step": float(np.mean(its)),
+                         "timed_steps": K}
+        res["rel_err_mixed_vs_fp64"] = float(torch.linalg.norm(fields["mixed"] - fields["fp64"]) /
+                                             torch.linalg.norm(fields["fp64"]))
+        return fs, res, w, dt
+
+    fs, res, _, _ = march(3)
+    fs.close()
+    out["config3"] = res
+    fs, res, w5, dt5 = march(5)
+    fs.close()
+    # adjoint of the probe objective on config 5, FP64 CG at tol 1e-10, one handle
+    n_adj = 100
+    prob = dict(xyz=w5.xyz, tets=w5.tets, part=w5.part, n_sub=w5.n_sub, probes=w5.probes,
+                source_pairs=w5.source_pairs, d2g=w5.d2G(dt5, n_adj), dt=dt5)
+    pm = A.ProbeMarch(prob, params=D.make_params(precision=D.DD_FP64, tol=args.tol64, use_graph=1,
+                                                 chunk=args.chunk, solver=D.DD_SOLVER_COUPLED_GMRES))
+    eps = torch.tensor(w5.eps, dtype=torch.float64, device=dev, requires_grad=True)
+    amp = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J = A.probe_objective(eps, amp, pm, n_adj, checkpoint=100)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    J.backward()
+    torch.cuda.synchronize()
+    t_bwd = time.perf_counter() - t0
+    pm.close()
+    res["adjoint"] = {"steps": n_adj, "checkpoint": 100, "forward_s": t_fwd,
+                      "backward_s": t_bwd, "adjoint_steps_per_s": n_adj / t_bwd,
+                      "note": "wall clock (synchronised); the forward includes dd_set_eps and the refactorisation, "
+                              "the backward recomputes the 100-step segment and runs 100 adjoint steps",
+                      "dJ_da_over_2J": float(amp.grad) / (2.0 * float(J.detach()))}
+    out["config5"] = res
+    fs, res, _, _ = march(2)
+    fs.close()
+    out["config2_pic"] = res
+    return out
 
 
 def run_ours(args, rank, world, local):
@@ -237,6 +402,7 @@ def run_ours(args, rank, world, local):
         fs.set_beam(*W.beam(w, 100000, w.steps * dt, seed=0))
     fs.bind()
     t_setup = time.perf_counter() - t0
+    sizes0 = fs.sizes
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     fs.factor(dt)
@@ -266,8 +432,10 @@ def run_ours(args, rank, world, local):
             return fs.pic_step(stats=stats)
         return fs.step(D2G[k], stats=stats)
 
-    def run_steps(params, profile, clocks=None):
-        """W warm-up steps, then K timed steps (CUDA events on the launch stream)."""
+    def run_steps(params, profile, clocks=None, stats=True):
+        """W warm-up steps, then K timed steps (CUDA events on the launch stream).
+        stats=False: no per-step host readback (the CUDA-graph step runs without a
+        round trip); iteration counts are then not collected."""
         fs.set_params(params)
         if pic:
             fs.factor(dt)                        # restarts fields and particles
@@ -286,9 +454,10 @@ def run_ours(args, rank, world, local):
         ev0.record(stream)
         its, refs = [], []
         for k in range(K):
-            st = one_step(Wu + k, True)
-            its.append(st["iters"])
-            refs.append(st["refinements"])
+            st = one_step(Wu + k, stats)
+            if stats:
+                its.append(st["iters"])
+                refs.append(st["refinements"])
         ev1.record(stream)
         torch.cuda.synchronize()
         if clocks:
@@ -318,10 +487,22 @@ def run_ours(args, rank, world, local):
     prof64 = prof32 = None
     e64 = e32 = None
     # headline timings: no event profiling inside the timed region
+    # Each precision is timed twice over the same steps: with a stats readback per
+    # step (iteration counts; a host round trip between steps) and without (the
+    # graph step's own mode).  The rate without readback is the headline; the
+    # two passes must give bitwise equal fields.
+    ms64s = ms32s = nan
+    same64 = same32 = None
     if args.only in (None, "fp64"):
-        ms64, it64, _, prof64, e64 = run_steps(p64, False, clocks)
+        # launch counts come from the readback pass (graph launches are counted from the
+        # iteration counts it reads); the pass without readback runs the same kernels
+        ms64s, it64, _, prof64, e64s = run_steps(p64, False)
+        ms64, _, _, _, e64 = run_steps(p64, False, clocks, stats=False)
+        same64 = bool(torch.equal(e64, e64s))
     if args.only in (None, "mixed"):
-        ms32, it32, ref32, prof32, e32 = run_steps(p32, False, clocks)
+        ms32s, it32, ref32, prof32, e32s = run_steps(p32, False)
+        ms32, _, _, _, e32 = run_steps(p32, False, clocks, stats=False)
+        same32 = bool(torch.equal(e32, e32s))
     rel = float(torch.linalg.norm(e32 - e64) / torch.linalg.norm(e64)) if e32 is not None and e64 is not None else nan
     # the paper's coupled solve (Eqs. F1lr + F1uc, GMRES(20), tol 1e-6, diagonal preconditioner)
     # beside the Schur CG at the same tolerance, both FP64, same launch mode
@@ -466,9 +647,28 @@ def run_ours(args, rank, world, local):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         return float(t.item())
 
+    # bytes of one launch of each packed / dense GEMV kind, algorithmic and streamed
+    gemv_bytes = {p_name: {kind: D.dd_get_gemv_bytes(fs.h, kind, prec) for kind in ("local", "iface_rows", "coupled",
+                                                                                     "recover")}
+                  for p_name, prec in (("fp64", D.DD_FP64), ("mixed", D.DD_MIXED))}
+    fs.set_params(p32)
+    gemv_bytes["mixed"] = {kind: D.dd_get_gemv_bytes(fs.h, kind, D.DD_MIXED)
+                           for kind in ("local", "iface_rows", "coupled", "recover")}
+    fp64_tflops = D.dd_measure_fp64_rate()
+    others = None
+    if args.other_configs and not args.cavity and cfg == 4 and world == 1:
+        fs.close()
+        fs = None
+        torch.cuda.empty_cache()
+        others = other_configs(args, dev)
+
     ms64, ms32, ms_e2e = allmax(ms64), allmax(ms32), allmax(ms_e2e)
-    sizes = fs.sizes
-    res = dict(fs=fs, K=K, ms64=ms64, ms32=ms32, ms_e2e=ms_e2e, it64=it64, it32=it32, ref32=ref32, prof64=prof64,
+    ms64s, ms32s = allmax(ms64s), allmax(ms32s)
+    sizes = dict(n_dof=int(sizes0.n_dof), n_lambda=int(sizes0.n_lambda), n_corner=int(sizes0.n_corner),
+                 dense_bytes_fp64=int(sizes0.dense_bytes_fp64))
+    res = dict(fs=fs, K=K, ms64=ms64, ms32=ms32, ms64s=ms64s, ms32s=ms32s, same64=same64, same32=same32,
+               gemv_bytes=gemv_bytes, fp64_tflops=fp64_tflops, others=others,
+               ms_e2e=ms_e2e, it64=it64, it32=it32, ref32=ref32, prof64=prof64,
                prof32=prof32, rel=rel, launches64=launches64, launches32=launches32, t_setup=t_setup, t_factor=t_factor, clocks=clocks.summary(), sizes=sizes,
                workload=w, dt=dt, t_tune=t_tune, tiles=tiles, pic=pic, gmres=gm, dp2=dp2, ens=ens)
     return res
@@ -495,16 +695,19 @@ def stage_table(prof, K):
     return out
 
 
-def _fp64_roofline(st64):
-    """FP64 path: the dominant GEMV is FP64-ALU bound on GB300 (2 flops per 8-byte element)."""
+def _fp64_roofline(st64, fp64_tflops):
+    """FP64 path: the dominant GEMV is FP64-ALU bound on GB300 (2 flops per 8-byte
+    matrix element), against the FP64 FMA rate measured in the same run."""
     cand = {k: v for k, v in st64.items() if k not in ("vector", "factor") and v.get("achieved_GBs")}
     if not cand:
         return None
     dom = max(cand, key=lambda k: cand[k]["ms_per_step"])
     gflops = cand[dom]["achieved_GBs"] / 8.0 * 2.0
-    return {"bound": "alu", "kernel": f"k_gemv<double> ({dom})", "achieved": gflops, "peak": FP64_NOMINAL_TFLOPS * 1e3,
-            "unit": "GFLOP/s", "frac": gflops / (FP64_NOMINAL_TFLOPS * 1e3),
-            "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s); the factorisation GEMM measures ~1.3"}
+    peak = fp64_tflops * 1e3 if fp64_tflops else FP64_NOMINAL_TFLOPS * 1e3
+    return {"bound": "alu", "kernel": f"k_gemv<double> ({dom})", "achieved": gflops, "peak": peak,
+            "unit": "GFLOP/s", "frac": gflops / peak,
+            "peak_source": ("measured in this run: dd_measure_fp64_rate (FMA chains on every SM, CUDA events)"
+                            if fp64_tflops else "nominal GB300 FP64 rate (1.25 TFLOP/s)")}
 
 
 def _clean(x):
@@ -536,11 +739,26 @@ def main():
         if rank == 0:
             dt = load_dt(args.config)
             from paper_2204_13254_gb300 import workloads as W
-            n_sub = W.config(args.config).n_sub
-            iters = 30.0
-            cb = cpu_baseline(args.config, dt, iters, n_sub)
-            line = {"metric": METRIC, "impl": "reference", "value": cb["value"], "unit": "steps/s", "n_gpus": 0,
-                    "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / cb["value"],
+            # the oracle sample: W untimed steps, then K timed steps, each one oracle step
+            # of the sample, reported per full-workload step (x n_sub / 8)
+            t0 = time.perf_counter()
+            o = OracleSample(args.config, dt)
+            for _ in range(args.warmup):
+                o.step()
+            t1 = time.perf_counter()
+            for _ in range(args.steps):
+                o.step()
+            t_step = (time.perf_counter() - t1) / max(1, args.steps)
+            it = float(np.mean(o.iters[args.warmup:])) if args.steps else 0.0
+            val = 1.0 / (t_step * o.scale)
+            cb = {"value": val, "unit": "steps/s", "cores": _threads(), "kind": "oracle",
+                  "sample": (f"each step: one step of the CPU FP64 oracle MFETI-DP1 on a {o.desc} (the "
+                             f"workload's subdomain size, h and dt), {t_step:.3f} s at {it:.1f} CG it/step, "
+                             f"reported per full step (x {o.scale:g} subdomains); set-up {o.t_setup:.1f} s and "
+                             f"factorisation {o.t_factor:.1f} s untimed"),
+                  "sample_s": time.perf_counter() - t0, "os_cpu_count": os.cpu_count()}
+            line = {"metric": METRIC, "impl": "reference", "value": val, "unit": "steps/s", "n_gpus": 0,
+                    "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
                     "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                     "data": "synthetic", "config": {"workload": W.config(args.config).name},
                     "cpu_baseline": cb,
@@ -566,9 +784,12 @@ def main():
     cand = {k: v for k, v in st_head.items() if k not in ("vector", "factor")}
     dom = max(cand, key=lambda k: cand[k]["ms_per_step"]) if cand else None
     achieved = cand[dom]["achieved_GBs"] if dom else None
+    kind_of_stage = {"local_solve": "local", "iface_apply": "coupled" if args.solver == "gmres" else "iface_rows",
+                     "recover": "recover"}
+    gb_head = r["gemv_bytes"].get(head, {}).get(kind_of_stage.get(dom)) if dom else None
     sizes = r["sizes"]
     w = r["workload"]
-    ms_head = r["ms32"] if head == "mixed" else r["ms64"]
+    ms_head = r["ms32"] if head == "mixed" else r["ms64"]       # the pass without per-step readback
     same = lambda x: x          # times were already max-reduced over ranks in run_ours
     value = aggregate_replicas(ms_head, K, world, same)[1]
     v64 = aggregate_replicas(r["ms64"], K, world, same)[1]
@@ -576,8 +797,7 @@ def main():
     cb = None
     if world == 1 and not args.no_cpu_baseline and not args.cavity and not r["pic"]:
         try:
-            its = r["it32"] if head == "mixed" else r["it64"]
-            cb = cpu_baseline(args.config, r["dt"], float(np.mean(its)), w.n_sub)
+            cb = cpu_baseline(args.config, r["dt"], args.cpu_steps)
         except Exception as ex:  # the baseline is context only; never fail the GPU line on it
             cb = {"error": repr(ex)[:200]}
     traffic = None
@@ -596,17 +816,26 @@ def main():
         "config": {"workload": w.name,
                    "mesh": ("PIC cycle (1e5-particle beam push + Whitney deposition + DD field solve + Faraday), "
                             if r["pic"] else "") + (f"PEC box {w.dims[0]}x{w.dims[1]}x{w.dims[2]} Kuhn cubes, {len(w.tets)} tets, "
-                            f"{sizes.n_dof} edge dofs, {w.n_sub} subdomains, {sizes.n_lambda} multipliers, "
-                            f"{sizes.n_corner} corners, Gaussian z-line pulse, dt=2xCFL={r['dt']:.6g}"),
+                            f"{sizes['n_dof']} edge dofs, {w.n_sub} subdomains, {sizes['n_lambda']} multipliers, "
+                            f"{sizes['n_corner']} corners, Gaussian z-line pulse, dt=2xCFL={r['dt']:.6g}"),
                    "l2_policy": "inputs larger than L2 (dense subdomain operators "
-                                f"{sizes.dense_bytes_fp64 / 1e9:.1f} GB FP64 + half that FP32), no flush",
+                                f"{sizes['dense_bytes_fp64'] / 1e9:.1f} GB FP64 + half that FP32), no flush",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                    "stage_profile": "separate eager pass over the same steps with CUDA events per launch"},
         "mixed": {"steps_per_s": v32, "ms_per_step": r["ms32"] / K, "iters_per_step": float(np.mean(r["it32"])),
                   "refinements_per_step": float(np.mean(r["ref32"])), "inner_tol": args.tol32,
-                  "refine_tol": args.refine_tol, "stages": st32},
+                  "refine_tol": args.refine_tol,
+                  "with_stats_readback": {"steps_per_s": K * 1e3 / r["ms32s"], "ms_per_step": r["ms32s"] / K,
+                                          "fields_bitwise_equal": r["same32"]},
+                  "stages": st32},
         "fp64": {"steps_per_s": v64, "ms_per_step": r["ms64"] / K, "iters_per_step": float(np.mean(r["it64"])),
-                 "tol": args.tol64, "stages": st64},
+                 "tol": args.tol64,
+                 "with_stats_readback": {"steps_per_s": K * 1e3 / r["ms64s"], "ms_per_step": r["ms64s"] / K,
+                                         "fields_bitwise_equal": r["same64"]},
+                 "stages": st64},
+        "timing": ("value and fp64/mixed steps_per_s: CUDA-graph steps without per-step host readback; "
+                   "with_stats_readback: the same steps reading iteration counts back after every step"),
+        "other_configs": r["others"],
         "speedup_mixed_vs_fp64": v32 / v64,
         "coupled_gmres_vs_schur_cg": r["gmres"],
         "mfeti_dp2": r["dp2"],
@@ -615,16 +844,24 @@ def main():
         "rel_err_mixed_vs_fp64": r["rel"],
         "setup_s": r["t_setup"], "factor_s": r["t_factor"], "autotune_s": r["t_tune"],
         "gemv_tiles": r["tiles"],
-        "fp64_roofline": _fp64_roofline(st64),
+        "fp64_roofline": _fp64_roofline(st64, r["fp64_tflops"]),
+        "fp64_fma_tflops_measured": r["fp64_tflops"],
         "roofline": {"bound": "hbm", "kernel": (f"{packed_kernel(r['tiles'], dom, args.solver)} (packed FP32 tiles, {dom})"
                                                 if head == "mixed" and not args.no_sym and dom in ("local_solve", "iface_apply")
                                                 else f"k_gemv<{'float' if head == 'mixed' else 'double'}> ({dom})"),
                      "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "bytes": ("algorithmic: the distinct elements of the symmetric operator the product needs "
+                               "(FP32) plus vectors, from the library's per-launch count (dd_get_gemv_bytes); "
+                               "traffic: ncu DRAM bytes per launch of the same kernel (profiles/)"),
+                     "algorithmic_bytes_per_launch": gb_head[0] if gb_head else None,
+                     "streamed_tile_bytes_per_launch": gb_head[1] if gb_head else None,
                      "peak_source": f"{peak_kind} hbm_gbs" + ("" if peak_kind == "measured" else " (no MEASURED_PEAKS.json)")},
+        "gemv_bytes_per_launch": {p_: {k_: {"algorithmic": v_[0], "streamed": v_[1]} for k_, v_ in d_.items()}
+                                  for p_, d_ in r["gemv_bytes"].items()},
         "cpu_baseline": cb,
         "e2e": {"value": aggregate_replicas(r["ms_e2e"], K, world, same)[1], "unit": "steps/s",
-                "h2d_bytes_per_step": int(sizes.n_dof * 8), "d2h_bytes_per_step": int(sizes.n_dof * 8)},
+                "h2d_bytes_per_step": int(sizes["n_dof"] * 8), "d2h_bytes_per_step": int(sizes["n_dof"] * 8)},
         "gpu_launches": int(r["launches32"] if head == "mixed" else r["launches64"]),
         "launch_mode": "eager" if args.eager else f"CUDA graph per step (Krylov loop as WHILE node, {args.chunk} it/body)",
         "fp32_storage": "dense" if args.no_sym else "packed symmetric 64x64 tiles (local solve, interface rows, coupled operator; the recovery too for ensembles)",
@@ -634,7 +871,8 @@ def main():
         "clocks": r["clocks"],
     }
     print(json.dumps(_clean(line)), flush=True)
-    r["fs"].close()
+    if r["fs"] is not None:
+        r["fs"].close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

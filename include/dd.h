@@ -279,6 +279,14 @@ int dd_factor(dd_handle* h, double dt, void* stream);
  * still advanced with the last iterate), DD_ERR_NONFINITE, DD_ERR_CUDA. */
 int dd_step(dd_handle* h, const double* d2g, double* e_out, dd_stats* stats, void* stream);
 
+/* dd_step with the source scaled on the device: d2g is taken as scale * d2g
+ * (a fixed spatial pattern, e.g. the tested current of a line source, times a
+ * time function's second difference), so that a caller marching a separable
+ * source J(x, t) = p(x) I(t) passes the pattern once and a host scalar per
+ * step.  scale must be finite (DD_ERR_ARG).  Otherwise as dd_step; with
+ * scale = 1 the result is bitwise that of dd_step. */
+int dd_step_scaled(dd_handle* h, const double* d2g, double scale, double* e_out, dd_stats* stats, void* stream);
+
 /* ---- discrete adjoint (gradients of a probe objective) ----------------
  * Not in the paper; derived from the recurrence above.  For the objective
  * J = sum_k sum_p |E(r_p; e^k)|^2 and the forward residuals
@@ -304,9 +312,36 @@ int dd_adjoint_step(dd_handle* h, const double* seed, const double* e_k, const d
                     const double* d2g_hat, double* grad_eps, double* grad_amp, double* mu_out, dd_stats* stats,
                     void* stream);
 
+/* dd_adjoint_step with d2g_hat taken as d2g_scale * d2g_hat (the separable
+ * source of dd_step_scaled): *grad_amp -= d2g_scale * (mu^k . d2g_hat).  With
+ * d2g_scale = 1 it is dd_adjoint_step.  d2g_scale must be finite (DD_ERR_ARG). */
+int dd_adjoint_step_scaled(dd_handle* h, const double* seed, const double* e_k, const double* e_km1,
+                           const double* e_km2, const double* d2g_hat, double d2g_scale, double* grad_eps,
+                           double* grad_amp, double* mu_out, dd_stats* stats, void* stream);
+
 /* seed = 2 * weight * P^T P e: dJ/de of weight * sum_p |E(r_p; e)|^2 over the
  * probe set (device [n_dof] e and seed; seed is overwritten). */
 int dd_probe_seed(dd_handle* h, const double* e, double weight, double* seed, void* stream);
+
+/* The probe objective on the device: *J += weight * sum_p |E(r_p; e)|^2 over
+ * the probe set (Sec. II's field interpolation E = sum_i e_i W_i at each
+ * point), summed in a fixed order (probes, then x, y, z).  e: device [n_dof],
+ * or NULL for the current e^n; J: device scalar, accumulated.  Errors:
+ * DD_ERR_ARG, DD_ERR_STATE (no workspace, or an ensemble). */
+int dd_probe_objective(dd_handle* h, const double* e, double weight, double* J, void* stream);
+
+/* New relative permittivity per tet, on the device (eps: device [n_tets],
+ * read during the call): re-assembles the subassembled local mass matrices
+ * T^(s) = sum_K eps_K T_K (Sec. II-B's mass matrix, torn as in Sec. III-A) from
+ * the unit-eps element matrices kept in the workspace -- in the host
+ * assembly's order, so the values equal those dd_setup would build from the
+ * same eps bitwise -- and marks the handle unfactored: call dd_factor next
+ * (which rebuilds A = T + dt^2/4 S, the local eliminations and the coarse
+ * problem).  The mesh, the tearing and mu are unchanged; eps must be positive
+ * (not checked on the device).  The first call uploads the element-to-entry
+ * map (synchronous).  Errors: DD_ERR_ARG, DD_ERR_STATE (no workspace, or an
+ * ensemble), DD_ERR_CUDA.  Synchronises `stream`. */
+int dd_set_eps(dd_handle* h, const double* eps, void* stream);
 
 /* ---- particle-in-cell coupling (Sec. II PIC cycle) --------------------
  * Macro-particles enter through the mesh boundary at given times and move on
@@ -389,8 +424,11 @@ int dd_get_interface_mass(const dd_handle* h, int64_t* nnz, int64_t* ptr, int32_
  * Limit: (n_local rounded up to 32) + 2 x (n_corner rounded up to 32) <= 2^20,
  * else DD_ERR_ARG with a message.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress) with that device current; make
- * that first call before any stream capture.  All calls on a device share the
- * array: calls whose kernels overlap on the GPU race on it. */
+ * that first call before any stream capture.  The address is cached per device
+ * ordinal, so calls must run in the device's primary context (the one the CUDA
+ * runtime and torch use), not in another driver-API context on that device.
+ * All calls on a device share the array: calls whose kernels overlap on the GPU
+ * race on it. */
 int dd_schur_apply_static(dd_handle* h, const double* lam, double* out, void* stream);
 
 /* Evaluate E = sum_i e_i W_i at the probe points for the current e^n.
@@ -464,6 +502,17 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
  * pairs of copies (host int32[7] each, 0 for the other kinds; any pointer may
  * be NULL). */
 int dd_get_tiles(const dd_handle* h, int32_t* lpr, int32_t* rows);
+
+/* Bytes of one full launch of GEMV kind `kind` (numbering of dd_get_tiles) at
+ * `precision` (DD_FP64 or DD_MIXED) with the current storage choice (host
+ * doubles, either may be NULL).  algorithmic: the matrix elements the product
+ * needs at the launch's precision -- for the packed symmetric FP32 operator its
+ * distinct elements (a symmetric group block's triangle counted once) -- plus
+ * the vectors read and written once; these are the bytes dd_profile reports.
+ * streamed: what the kernel reads from memory by construction (for the packed
+ * kinds the whole 64 x 64 tiles, padding and full diagonal tiles included;
+ * otherwise equal to algorithmic).  Errors: DD_ERR_ARG. */
+int dd_get_gemv_bytes(const dd_handle* h, int32_t kind, int32_t precision, double* algorithmic, double* streamed);
 int dd_get_sym_config(const dd_handle* h, int32_t* cl, int32_t* st, int32_t* keep, int32_t* ws);
 
 /* Sets the packed-tile launch of GEMV kind `kind` (0, 5 or 6; 3 too for an
@@ -475,6 +524,25 @@ int dd_get_sym_config(const dd_handle* h, int32_t* cl, int32_t* st, int32_t* kee
  * a CTA's), DD_ERR_STATE before dd_bind_workspace or during a capture.
  * Synchronises `stream`; drops captured step graphs. */
 int dd_set_sym_config(dd_handle* h, int32_t kind, int32_t cl, int32_t st, int32_t keep, int32_t ws, void* stream);
+
+/* Failure-path testing aid for the bounded device waits.  With
+ * first_wait_polls > 0, the first wait of every CTA of the packed-tile GEMVs
+ * (DD_MIXED with sym_fp32) polls an mbarrier that nothing completes that many
+ * times and gives up, as a wait on a lost copy would: the CTA records the
+ * failure in the device status word, waits (bounded) for the copies it has in
+ * flight and exits.  The step then returns DD_ERR_TIMEOUT -- in eager mode at
+ * once, in graph mode from the first call that reads stats -- and is not
+ * taken: e^n, e^{n-1} and the step counter stay where they were and the next
+ * solve starts cold.  0 restores the normal waits (2^20 polls).  Synchronises
+ * `stream`.  Errors: DD_ERR_ARG (negative), DD_ERR_STATE (no workspace). */
+int dd_set_wait_limit(dd_handle* h, int32_t first_wait_polls, void* stream);
+
+/* FP64 FMA throughput of the current device in TFLOP/s (2 flops per FMA):
+ * eight independent FMA chains per thread, 8 CTAs of 256 threads per SM, best
+ * of three CUDA-event-timed launches after one warm-up.  The roofline of the
+ * FP64 path (its GEMVs are FP64-ALU bound on GB300) is stated against it.
+ * Synchronises `stream`.  Errors: DD_ERR_ARG, DD_ERR_CUDA. */
+int dd_measure_fp64_rate(double* tflops, void* stream);
 
 void dd_destroy(dd_handle* h);
 const char* dd_last_error(const dd_handle* h);

@@ -258,6 +258,10 @@ size_t dd_workspace_layout(dd_handle* h, bool assign) {
     L.take(d.xC_prev_adj, nc);
     L.take(d.lam2_prev, nm);
     L.take(d.lam2_prev_adj, nm);
+    if (h->members <= 1) {   // dd_set_eps map (filled on its first call)
+        L.take(d.eps_ptr, nnz + 1);
+        L.take(d.eps_idx, (size_t)h->eps_contrib);
+    }
     L.take(d.tet_dof, 6 * (size_t)h->n_tets);
     L.take(d.That, 36 * (size_t)h->n_tets);
     {
@@ -1027,6 +1031,7 @@ int dd_bind_workspace(dd_handle* h, void* dev, size_t bytes, void* stream) {
     CK(h, (int)cudaStreamSynchronize(s), "sync");
     h->bound = true;
     h->factored = false;
+    h->eps_map_up = false;
     compute_stage_bytes(h);
     return DD_OK;
 }
@@ -1154,6 +1159,26 @@ int keep_first_pass(dd_handle* h, bool save, cudaStream_t s) {
 // A delta = -dt^2 S u_n + src_sign * src (subassembled, source on the owner),
 // u_np1 = 2 u_n - u_nm1 + delta.  Used by the forward step (src = d2g, sign -1)
 // and by the adjoint step (src = seed, sign +1).
+// A bounded device wait gave up during the step (PcgScalars::wait_err): the step
+// is void.  Clears the sticky word, drops the multiplier warm start (the last
+// solve's iterate may be garbage) and returns DD_ERR_TIMEOUT; the caller keeps
+// the time levels where they were.
+int report_timeout(dd_handle* h, cudaStream_t s) {
+    CK(h, (int)cudaMemsetAsync(&h->d.sc->wait_err, 0, sizeof(int32_t), s), "clear wait error");
+    CK(h, (int)cudaStreamSynchronize(s), "sync");
+    h->lam_valid = false;
+    h->err = "a bounded device wait of the packed-tile GEMV gave up; the step was not taken";
+    return DD_ERR_TIMEOUT;
+}
+
+// True when a packed-GEMV wait gave up since the word was last cleared (synchronises).
+bool wait_err_set(dd_handle* h, cudaStream_t s) {
+    int32_t v = 0;
+    if (cudaMemcpyAsync(&v, &h->d.sc->wait_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) return false;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return false;
+    return v != 0;
+}
+
 int advance(dd_handle* h, const double* u_n, const double* u_nm1, double* u_np1, const double* src, double src_sign,
             int* iters_out, int* refs_out, double* resid_out, cudaStream_t s) {
     int status = DD_OK, iters = 0, refinements = 0;
@@ -1193,7 +1218,10 @@ int advance(dd_handle* h, const double* u_n, const double* u_nm1, double* u_np1,
             int st = dd_solve(h, DD_MIXED, tol_k, warm, &it, &r, s);
             iters += it;
             ++refinements;
-            if (st != DD_OK && st != DD_ERR_NO_CONVERGENCE) return st;
+            if (st != DD_OK && st != DD_ERR_NO_CONVERGENCE) {   // a void operator can end the solve early
+                if (st != DD_ERR_CUDA && wait_err_set(h, s)) return report_timeout(h, s);
+                return st;
+            }
             {
                 Prof P(h, ST_VEC, s, 1);
                 CK(h, launch_writeback(h, u_n, u_nm1, h->d.delta_k, h->d.delta, k == 0 ? 1 : 0, nullptr, s), "writeback");
@@ -1204,6 +1232,10 @@ int advance(dd_handle* h, const double* u_n, const double* u_nm1, double* u_np1,
                 CK(h, launch_assembled_norm(h, 0, h->d.bf, s), "norm r");
             }
             CK(h, read_scalars(h, &hs, s), "scalars");
+            if (hs.wait_err) {   // a bounded wait of the packed GEMV gave up: this pass's result is void
+                status = DD_ERR_TIMEOUT;
+                break;
+            }
             resid = hs.norm_b2 > 0 ? std::sqrt(hs.norm_r2 / hs.norm_b2) : 0.0;
             if (!std::isfinite(resid)) {
                 status = DD_ERR_NONFINITE;
@@ -1217,6 +1249,7 @@ int advance(dd_handle* h, const double* u_n, const double* u_nm1, double* u_np1,
             if (xrc) return xrc;
         }
         if (status == DD_ERR_NONFINITE) return status;
+        if (status == DD_ERR_TIMEOUT) return report_timeout(h, s);
         {
             Prof P(h, ST_VEC, s, 1);
             CK(h, launch_advance(h, u_n, u_nm1, h->d.delta, u_np1, s), "advance");
@@ -1384,14 +1417,15 @@ int capture_step(dd_handle* h, int phase) {
     return DD_OK;
 }
 
-int dd_step_graph(dd_handle* h, const double* d2g, double* e_out, dd_stats* stats, cudaStream_t s) {
+int dd_step_graph(dd_handle* h, const double* d2g, double scale, double* e_out, dd_stats* stats, cudaStream_t s) {
     const int phase = h->cur;
     if (!h->gexec[phase]) {
         int rc = capture_step(h, phase);
         if (rc) return rc;
     }
     const size_t nb = sizeof(double) * h->n_dof;
-    if (d2g) CK(h, (int)cudaMemcpyAsync(h->d.src_in, d2g, nb, cudaMemcpyDeviceToDevice, s), "source copy");
+    if (d2g && scale == 1.0) CK(h, (int)cudaMemcpyAsync(h->d.src_in, d2g, nb, cudaMemcpyDeviceToDevice, s), "source copy");
+    else if (d2g) CK(h, launch_scale_copy(h, h->d.src_in, d2g, scale, s), "source copy");
     else CK(h, (int)cudaMemsetAsync(h->d.src_in, 0, nb, s), "source clear");
     if (!h->lam_valid && !h->mult_dof.empty()) {
         CK(h, (int)cudaMemsetAsync(h->d.lam, 0, sizeof(double) * h->mult_dof.size(), s), "memset");
@@ -1420,6 +1454,11 @@ int dd_step_graph(dd_handle* h, const double* d2g, double* e_out, dd_stats* stat
         stats->resid = h->prm.precision == DD_MIXED ? (hs.norm_b2 > 0 ? std::sqrt(hs.norm_r2 / hs.norm_b2) : 0.0)
                                                      : (hs.gg > 0 ? std::sqrt(hs.rr / hs.gg) : 0.0);
         status = hs.step_status;
+        if (hs.wait_err || status == DD_ERR_TIMEOUT) {   // void step: keep e^n, e^{n-1} and the step counter
+            h->cur = phase;
+            h->step -= 1;
+            status = report_timeout(h, s);
+        }
         stats->status = status;
         h->total_launches += h->g_kernels_main + h->g_kernels_iter * (int64_t)hs.it_total +
                              h->g_kernels_pass * (int64_t)std::max(0, hs.refinements - 1) +
@@ -1448,17 +1487,22 @@ void swap_lambda(dd_handle* h) {
 }  // namespace
 
 int dd_step(dd_handle* h, const double* d2g, double* e_out, dd_stats* stats, void* stream) {
+    return dd_step_scaled(h, d2g, 1.0, e_out, stats, stream);
+}
+
+int dd_step_scaled(dd_handle* h, const double* d2g, double scale, double* e_out, dd_stats* stats, void* stream) {
     if (!h) return DD_ERR_ARG;
     if (!h->factored) return h->fail(DD_ERR_STATE, "dd_step before dd_factor");
+    if (!std::isfinite(scale)) return h->fail(DD_ERR_ARG, "source scale must be finite");
     cudaStream_t s = (cudaStream_t)stream;
-    if (h->prm.use_graph) return dd_step_graph(h, d2g, e_out, stats, s);
+    if (h->prm.use_graph) return dd_step_graph(h, d2g, scale, e_out, stats, s);
     const double* e_n = h->d.e[h->cur];
     const double* e_nm1 = h->d.e[(h->cur + 2) % 3];
     double* e_np1 = h->d.e[(h->cur + 1) % 3];
     int iters = 0, refinements = 0;
     double resid = 0.0;
     // b = -dt^2 S e^n - d2g (subassembled): A delta = b, e^{n+1} = 2e^n - e^{n-1} + delta
-    const int status = advance(h, e_n, e_nm1, e_np1, d2g, -1.0, &iters, &refinements, &resid, s);
+    const int status = advance(h, e_n, e_nm1, e_np1, d2g, -scale, &iters, &refinements, &resid, s);
     if (status != DD_OK && status != DD_ERR_NO_CONVERGENCE) return status;
     h->cur = (h->cur + 1) % 3;
     h->step += 1;
@@ -1486,7 +1530,14 @@ int dd_adjoint_reset(dd_handle* h, void* stream) {
 int dd_adjoint_step(dd_handle* h, const double* seed, const double* e_k, const double* e_km1, const double* e_km2,
                     const double* d2g_hat, double* grad_eps, double* grad_amp, double* mu_out, dd_stats* stats,
                     void* stream) {
+    return dd_adjoint_step_scaled(h, seed, e_k, e_km1, e_km2, d2g_hat, 1.0, grad_eps, grad_amp, mu_out, stats, stream);
+}
+
+int dd_adjoint_step_scaled(dd_handle* h, const double* seed, const double* e_k, const double* e_km1,
+                           const double* e_km2, const double* d2g_hat, double d2g_scale, double* grad_eps,
+                           double* grad_amp, double* mu_out, dd_stats* stats, void* stream) {
     if (!h || !seed) return DD_ERR_ARG;
+    if (!std::isfinite(d2g_scale)) return h->fail(DD_ERR_ARG, "source scale must be finite");
     if (h->members > 1) return h->fail(DD_ERR_STATE, "the adjoint is not available for an ensemble (members > 1)");
     if (!h->factored) return h->fail(DD_ERR_STATE, "dd_adjoint_step before dd_factor");
     if (grad_eps && (!e_k || !e_km1 || !e_km2)) return h->fail(DD_ERR_ARG, "grad_eps needs e_k, e_km1, e_km2");
@@ -1511,7 +1562,7 @@ int dd_adjoint_step(dd_handle* h, const double* seed, const double* e_k, const d
     }
     if (grad_amp && d2g_hat) {
         Prof P(h, ST_VEC, s, 1);
-        CK(h, launch_dot_sub(h, mu_k, d2g_hat, grad_amp, s), "grad amp");
+        CK(h, launch_dot_sub(h, mu_k, d2g_hat, d2g_scale, grad_amp, s), "grad amp");
     }
     if (mu_out) CK(h, (int)cudaMemcpyAsync(mu_out, mu_k, sizeof(double) * h->n_dof, cudaMemcpyDeviceToDevice, s), "mu_out");
     if (stats) {
@@ -1531,6 +1582,50 @@ int dd_probe_seed(dd_handle* h, const double* e, double weight, double* seed, vo
     CK(h, (int)cudaMemsetAsync(seed, 0, sizeof(double) * h->n_dof, s), "memset");
     Prof P(h, ST_VEC, s, 1);
     CK(h, launch_probe_seed(h, e, weight, seed, s), "probe seed");
+    return DD_OK;
+}
+
+int dd_probe_objective(dd_handle* h, const double* e, double weight, double* J, void* stream) {
+    if (!h || !J) return DD_ERR_ARG;
+    if (h->members > 1) return h->fail(DD_ERR_STATE, "dd_probe_objective is not available for an ensemble (members > 1)");
+    if (!h->bound) return h->fail(DD_ERR_STATE, "no workspace bound");
+    cudaStream_t s = (cudaStream_t)stream;
+    Prof P(h, ST_VEC, s, 1);
+    CK(h, launch_probe_objective(h, e ? e : h->d.e[h->cur], weight, J, s), "probe objective");
+    return DD_OK;
+}
+
+int dd_set_eps(dd_handle* h, const double* eps, void* stream) {
+    if (!h || !eps) return DD_ERR_ARG;
+    if (h->members > 1) return h->fail(DD_ERR_STATE, "dd_set_eps is not available for an ensemble (members > 1)");
+    if (!h->bound) return h->fail(DD_ERR_STATE, "dd_set_eps before dd_bind_workspace");
+    if (h->n_tets * 36 >= (int64_t)INT32_MAX) return h->fail(DD_ERR_ARG, "dd_set_eps: mesh too large (36 n_tets >= 2^31)");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!h->eps_map_up) {
+        std::vector<int64_t> ptr;
+        std::vector<int32_t> idx;
+        build_eps_map(h, ptr, idx);
+        if ((int64_t)idx.size() != h->eps_contrib || ptr.size() != (size_t)h->row_ptr.back() + 1)
+            return h->fail(DD_ERR_STATE, "dd_set_eps: mass map does not match the local matrices");
+        CK(h, upload(h->d.eps_ptr, ptr, s), "upload");
+        CK(h, upload(h->d.eps_idx, idx, s), "upload");
+        CK(h, (int)cudaStreamSynchronize(s), "sync");   // ptr, idx are locals
+        h->eps_map_up = true;
+    }
+    drop_graphs(h);
+    CK(h, launch_assemble_mass(h, eps, s), "mass assembly");
+    CK(h, (int)cudaStreamSynchronize(s), "sync");
+    h->factored = false;
+    return DD_OK;
+}
+
+int dd_set_wait_limit(dd_handle* h, int32_t first_wait_polls, void* stream) {
+    if (!h || first_wait_polls < 0) return DD_ERR_ARG;
+    if (!h->bound) return h->fail(DD_ERR_STATE, "no workspace bound");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(h, (int)cudaMemcpyAsync(&h->d.sc->wait_first, &first_wait_polls, sizeof(int32_t), cudaMemcpyHostToDevice, s),
+       "wait limit");
+    CK(h, (int)cudaStreamSynchronize(s), "sync");
     return DD_OK;
 }
 
@@ -1911,6 +2006,17 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
     h->tuned = true;
     if (seconds)
         *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    return DD_OK;
+}
+
+int dd_get_gemv_bytes(const dd_handle* h, int32_t kind, int32_t precision, double* algorithmic, double* streamed) {
+    if (!h || kind < 0 || kind >= GEMV_NMODES || (precision != DD_FP64 && precision != DD_MIXED)) return DD_ERR_ARG;
+    const double alg = mb(h, kind, precision);
+    double str = alg;
+    if (precision == DD_MIXED && h->prm.sym_fp32 && h->sym_ok && sym_active(h, kind) && h->mode_tile_bytes_sym[kind] > 0.0)
+        str = h->mode_tile_bytes_sym[kind];
+    if (algorithmic) *algorithmic = alg;
+    if (streamed) *streamed = str;
     return DD_OK;
 }
 

@@ -165,7 +165,8 @@ struct PcgScalars {
     double norm_b2;   // mixed mode: ||b||^2 of the step system
     double norm_r2;   // mixed mode: ||r||^2 of the current FP64 residual
     int32_t lam_levels;   // warm_start 2: multiplier history levels available (0, 1, 2)
-    int32_t pad3;
+    int32_t wait_first;   // > 0: the first mbarrier wait of every packed-GEMV CTA polls an mbarrier
+                          // nothing completes, this many times, and gives up (failure-path test; 0 = off)
     int32_t it_total;     // graph mode: CG iterations of the whole step
     int32_t refinements;  // graph mode: solves of the whole step
     int32_t step_status;  // graph mode: DD status of the whole step
@@ -312,6 +313,8 @@ struct DevPtrs {
     double* lam2_prev = nullptr;
     double* lam2_prev_adj = nullptr;
     float* lamf_adj = nullptr;
+    int64_t* eps_ptr = nullptr;      // [nnz_local+1] dd_set_eps: contributions of each local mass entry
+    int32_t* eps_idx = nullptr;      // element-matrix entries 36 t + 6 p + q, in the host assembly's order
     int32_t* tet_dof = nullptr;      // [n_tets*6] dof of each tet edge, -1 on the PEC wall
     double* That = nullptr;          // [n_tets*36] unit-eps oriented element mass matrices
     // flat local vectors (n_local)
@@ -406,6 +409,8 @@ struct dd_handle {
     std::vector<int64_t> row_ptr;
     std::vector<int32_t> col_loc, col_dof;
     std::vector<double> Tval, Sval;
+    int64_t eps_contrib = 0;         // element-matrix entries that land in the local mass (dd_set_eps map size)
+    bool eps_map_up = false;         // the dd_set_eps map is in the workspace
     std::vector<int64_t> mt_ptr;     // MFETI-DP2: interface tangential mass, CSR over multipliers
     std::vector<int32_t> mt_col;
     std::vector<double> mt_val;
@@ -485,7 +490,8 @@ struct dd_handle {
     double bytes_per_launch[DD_N_STAGES] = {};  // algorithmic bytes of one full launch (RHS, refinement)
     double mode_bytes[GEMV_NMODES] = {};        // algorithmic bytes of one GEMV launch, FP64 matrices
     double mode_bytes32[GEMV_NMODES] = {};      // same with FP32 matrices
-    double mode_bytes_sym[GEMV_NMODES] = {};    // same with the packed symmetric FP32 tiles
+    double mode_bytes_sym[GEMV_NMODES] = {};    // same for the packed symmetric FP32 operator: its distinct elements
+    double mode_tile_bytes_sym[GEMV_NMODES] = {};   // bytes the packed kernel streams (whole tiles, padding included)
 
     int fail(int code, const std::string& msg) {
         err = msg;
@@ -519,7 +525,11 @@ int launch_factor_finish(const dd_handle* h, void* stream);
 int launch_rhs(const dd_handle* h, const double* e_n, const double* src, double src_sign, double dt, void* stream);
 int launch_grad_eps(const dd_handle* h, const double* mu, const double* e_k, const double* e_km1, const double* e_km2,
                     double* grad_eps, void* stream);
-int launch_dot_sub(const dd_handle* h, const double* a, const double* b, double* acc, void* stream);
+int launch_dot_sub(const dd_handle* h, const double* a, const double* b, double scale, double* acc, void* stream);
+int launch_probe_objective(const dd_handle* h, const double* e, double weight, double* J, void* stream);
+int launch_scale_copy(const dd_handle* h, double* dst, const double* src, double scale, void* stream);
+int launch_assemble_mass(const dd_handle* h, const double* eps, void* stream);
+void build_eps_map(const dd_handle* h, std::vector<int64_t>& ptr, std::vector<int32_t>& idx);
 int launch_probe_seed(const dd_handle* h, const double* e, double weight, double* seed, void* stream);
 int launch_residual_local(const dd_handle* h, void* stream);
 int launch_assembled_norm(const dd_handle* h, int set_b, float* bf, void* stream);

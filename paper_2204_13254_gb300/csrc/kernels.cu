@@ -745,6 +745,7 @@ __global__ void k_solve_end(PcgScalars* sc) {
     sc->refinements += 1;
     if (sc->status != DD_OK) sc->step_status = sc->status;
     else if (!sc->done && sc->step_status == DD_OK) sc->step_status = DD_ERR_NO_CONVERGENCE;
+    if (sc->wait_err) sc->step_status = DD_ERR_TIMEOUT;   // a packed-GEMV wait gave up (sticky until read)
 }
 
 // graph mode: after an FP64 residual, run the next refinement pass (cond = 1) while
@@ -841,14 +842,51 @@ __global__ void k_grad_eps(int64_t n_tets, const int32_t* __restrict__ tet_dof, 
     }
 }
 
-// *acc -= a . b (deterministic grid reduction; the last block updates *acc)
+// *acc -= scale * (a . b) (deterministic grid reduction; the last block updates *acc)
 __global__ void __launch_bounds__(kThreads) k_dot_sub(int64_t n, const double* __restrict__ a,
-                                                      const double* __restrict__ b, double* acc, PcgScalars* sc,
-                                                      double* __restrict__ partials) {
+                                                      const double* __restrict__ b, double scale, double* acc,
+                                                      PcgScalars* sc, double* __restrict__ partials) {
     double v[1] = {0.0};
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         v[0] += a[i] * b[i];
-    if (grid_sum<1>(v, partials, &sc->counter[4])) *acc -= v[0];
+    if (grid_sum<1>(v, partials, &sc->counter[4])) *acc -= scale * v[0];
+}
+
+// J += weight * sum_p |E(r_p; e)|^2 (one thread, fixed order: probes, then x, y, z)
+__global__ void k_probe_objective(int n_probe, const int32_t* __restrict__ pd, const double* __restrict__ pw,
+                                  const double* __restrict__ e, double weight, double* __restrict__ J) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    double acc = 0.0;
+    for (int k = 0; k < n_probe; ++k)
+        for (int c = 0; c < 3; ++c) {
+            double v = 0.0;
+            for (int le = 0; le < 6; ++le) v += e[pd[6 * k + le]] * pw[18 * k + 3 * le + c];
+            acc += v * v;
+        }
+    J[0] += weight * acc;
+}
+
+// dst = scale * src
+__global__ void k_scale_copy(int64_t n, double* __restrict__ dst, const double* __restrict__ src, double scale) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = scale * src[i];
+}
+
+// Local mass values from a per-tet permittivity: Tval[p] = sum_j eps[t_j] * That[e_j]
+// over the element-matrix entries e_j = 36 t_j + 6 a + b that the host assembly
+// adds into entry p, in its order, with separately rounded products and sums
+// (so the result is bitwise the host's for the same eps).
+__global__ void k_assemble_mass(int64_t nnz, const int64_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+                                const double* __restrict__ That, const double* __restrict__ eps,
+                                double* __restrict__ Tval) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int64_t j = ptr[p]; j < ptr[p + 1]; ++j) {
+            const int32_t el = idx[j];
+            acc = __dadd_rn(acc, __dmul_rn(eps[el / 36], That[el]));
+        }
+        Tval[p] = acc;
+    }
 }
 
 // seed += 2 w P^T P e over all probes (one thread, fixed order; at most a few
@@ -1264,9 +1302,31 @@ int launch_grad_eps(const dd_handle* h, const double* mu, const double* e_k, con
     return (int)cudaGetLastError();
 }
 
-int launch_dot_sub(const dd_handle* h, const double* a, const double* b, double* acc, void* stream) {
+int launch_dot_sub(const dd_handle* h, const double* a, const double* b, double scale, double* acc, void* stream) {
     const int64_t nd = h->n_dof;
-    k_dot_sub<<<reduce_blocks(nd), kThreads, 0, S(stream)>>>(nd, a, b, acc, h->d.sc, h->d.partials);
+    k_dot_sub<<<reduce_blocks(nd), kThreads, 0, S(stream)>>>(nd, a, b, scale, acc, h->d.sc, h->d.partials);
+    return (int)cudaGetLastError();
+}
+
+int launch_probe_objective(const dd_handle* h, const double* e, double weight, double* J, void* stream) {
+    if (h->n_probe == 0) return 0;
+    k_probe_objective<<<1, 32, 0, S(stream)>>>(h->n_probe, h->d.probe_dof, h->d.probe_w, e, weight, J);
+    return (int)cudaGetLastError();
+}
+
+int launch_scale_copy(const dd_handle* h, double* dst, const double* src, double scale, void* stream) {
+    const int64_t nd = h->n_dof;
+    if (nd == 0) return 0;
+    k_scale_copy<<<(unsigned)std::min<int64_t>((nd + kThreads - 1) / kThreads, 152 * 16), kThreads, 0, S(stream)>>>(
+        nd, dst, src, scale);
+    return (int)cudaGetLastError();
+}
+
+int launch_assemble_mass(const dd_handle* h, const double* eps, void* stream) {
+    const int64_t nnz = h->row_ptr.back();
+    if (nnz == 0) return 0;
+    k_assemble_mass<<<(unsigned)std::min<int64_t>((nnz + kThreads - 1) / kThreads, 152 * 16), kThreads, 0,
+                      S(stream)>>>(nnz, h->d.eps_ptr, h->d.eps_idx, h->d.That, eps, h->d.Tval);
     return (int)cudaGetLastError();
 }
 
@@ -1301,4 +1361,66 @@ int launch_probe(const dd_handle* h, const double* e, double* out, void* stream)
     if (h->n_probe == 0) return 0;
     k_probe<<<(3 * h->n_probe + 127) / 128, 128, 0, S(stream)>>>(h->n_probe, h->d.probe_dof, h->d.probe_w, e, out);
     return (int)cudaGetLastError();
+}
+
+// ============================================================================
+// FP64 FMA rate (the peak the FP64 path's GEMVs are measured against)
+// ============================================================================
+
+namespace {
+
+__device__ double g_fma64_sink;
+
+// Eight independent FMA chains per thread; each converges to c / (1 - b) and
+// stays finite, and the result is stored conditionally so that nothing is
+// optimised away.
+__global__ void __launch_bounds__(256) k_fma64_rate(int iters, double b, double c) {
+    double a[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = 0.001 * (threadIdx.x + j);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) a[j] = fma(a[j], b, c);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s += a[j];
+    if (s == 12345.678) g_fma64_sink = s;   // never true for these inputs: keeps the chains live
+}
+
+}  // namespace
+
+extern "C" int dd_measure_fp64_rate(double* tflops, void* stream) {
+    if (!tflops) return DD_ERR_ARG;
+    cudaStream_t s = S(stream);
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return DD_ERR_CUDA;
+    const int blocks = sms * 8, threads = 256, iters = 4096;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return DD_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return DD_ERR_CUDA;
+    }
+    int rc = DD_OK;
+    float best = 0.0f;
+    for (int rep = 0; rep < 4 && rc == DD_OK; ++rep) {   // first launch warms up; best of the other three
+        cudaEventRecord(e0, s);
+        k_fma64_rate<<<blocks, threads, 0, s>>>(iters, 0.5, 0.25);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+            rc = DD_ERR_CUDA;
+            break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && (best == 0.0f || ms < best)) best = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != DD_OK || best <= 0.0f) return rc != DD_OK ? rc : DD_ERR_CUDA;
+    const double flops = 2.0 * 8.0 * (double)iters * (double)blocks * threads;
+    *tflops = flops / (best * 1e-3) / 1e12;
+    return DD_OK;
 }

@@ -352,6 +352,7 @@ int dd_build_host(dd_handle* h, const dd_mesh* mesh, const int32_t* part, int32_
     h->col_dof.clear();
     h->Tval.clear();
     h->Sval.clear();
+    h->eps_contrib = 0;
     h->mats.resize(n_sub);
     h->max_nr = h->max_ns = 0;
     int64_t moff = 0;
@@ -378,6 +379,7 @@ int dd_build_host(dd_handle* h, const dd_mesh* mesh, const int32_t* part, int32_
             }
         }
         std::stable_sort(trip.begin(), trip.end(), [](const Trip& a, const Trip& b) { return a.key < b.key; });
+        h->eps_contrib += (int64_t)trip.size();
         for (size_t i = 0; i < trip.size();) {
             size_t j = i;
             double tv = 0.0, sv = 0.0;
@@ -659,4 +661,49 @@ int dd_build_beam(dd_handle* h, const dd_beam* beam) {
     h->pq = beam->q;
     h->pqm = beam->qm;
     return DD_OK;
+}
+
+// Map of the local mass values onto the element matrices, for dd_set_eps:
+// entry p of Tval (subdomain by subdomain, rows and columns in local order,
+// as assembled above) receives the element-matrix entries idx[ptr[p]] ..
+// idx[ptr[p+1]-1] (36 t + 6 a + b, scaled by eps[t]), listed in the order the
+// host assembly adds them (tets ascending, then a, b), so that a device
+// re-assembly reproduces the host's sums bitwise.
+void build_eps_map(const dd_handle* h, std::vector<int64_t>& ptr, std::vector<int32_t>& idx) {
+    const int n_sub = h->n_sub;
+    std::vector<std::vector<int64_t>> tets_of(n_sub);
+    for (int64_t t = 0; t < h->n_tets; ++t) tets_of[h->part[t]].push_back(t);
+    std::vector<int32_t> loc_of(h->n_dof, -1);
+    ptr.assign(1, 0);
+    idx.clear();
+    idx.reserve((size_t)h->eps_contrib);
+    struct Ent {
+        int64_t key;
+        int32_t el;
+    };
+    std::vector<Ent> ent;
+    for (int s = 0; s < n_sub; ++s) {
+        const int64_t base = h->sub_ptr[s];
+        const int32_t ns = (int32_t)(h->sub_ptr[s + 1] - base);
+        for (int32_t i = 0; i < ns; ++i) loc_of[h->local_dof[base + i]] = i;
+        ent.clear();
+        for (int64_t t : tets_of[s])
+            for (int a = 0; a < 6; ++a) {
+                const int64_t da = h->tet_dof[6 * t + a];
+                if (da < 0) continue;
+                for (int b = 0; b < 6; ++b) {
+                    const int64_t db = h->tet_dof[6 * t + b];
+                    if (db < 0) continue;
+                    ent.push_back({(int64_t)loc_of[da] * ns + loc_of[db], (int32_t)(36 * t + 6 * a + b)});
+                }
+            }
+        std::stable_sort(ent.begin(), ent.end(), [](const Ent& x, const Ent& y) { return x.key < y.key; });
+        for (size_t i = 0; i < ent.size();) {
+            size_t j = i;
+            while (j < ent.size() && ent[j].key == ent[i].key) idx.push_back(ent[j++].el);
+            ptr.push_back((int64_t)idx.size());
+            i = j;
+        }
+        for (int32_t i = 0; i < ns; ++i) loc_of[h->local_dof[base + i]] = -1;
+    }
 }

@@ -32,6 +32,10 @@ double* g_scratch_addr[kMaxDevices] = {};
 
 // Device address of g_dd_scratch on the current device, looked up once per
 // device.  The host-side symbol is only a stand-in; kernels need this address.
+// The cache is keyed by device ordinal, i.e. it assumes the CUDA runtime's
+// primary context of that device (the one the runtime and torch use); a
+// caller that makes another driver-API context current on the same device
+// would receive an address that is not valid there.
 cudaError_t scratch_address(int dev, double** out) {
     std::lock_guard<std::mutex> lock(g_scratch_mu);
     if (!g_scratch_addr[dev]) {
@@ -65,8 +69,10 @@ extern "C" int dd_schur_apply_static(dd_handle* h, const double* lam, double* ou
     if (h->mult_dof.empty()) return DD_OK;
     int dev = 0;
     cudaError_t rc = cudaGetDevice(&dev);
-    if (rc != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-        return h->fail(DD_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(rc));
+    if (rc != cudaSuccess) return h->fail(DD_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(rc));
+    if (dev < 0 || dev >= kMaxDevices)
+        return h->fail(DD_ERR_CUDA, "dd_schur_apply_static: device ordinal " + std::to_string(dev) + " >= " +
+                                        std::to_string(kMaxDevices) + " is not supported");
     double* base = nullptr;
     rc = scratch_address(dev, &base);
     if (rc != cudaSuccess) return h->fail(DD_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(rc));

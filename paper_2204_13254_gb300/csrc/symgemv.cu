@@ -90,10 +90,18 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
 }
 
 // Bounded wait for phase `parity` of `bar`; false if it gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (unsigned k = 0; k < kWaitLimit; ++k)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned limit = kWaitLimit) {
+    for (unsigned k = 0; k < limit; ++k)
         if (mbar_test(bar, parity)) return true;
     return false;
+}
+
+// Failure-path test (PcgScalars::wait_first > 0): the CTA's first wait polls
+// `never`, an mbarrier no thread or copy ever completes, wait_first times and
+// gives up, exercising the give-up / drain / report path with every copy issued.
+__device__ __forceinline__ bool first_wait_test(const XSrc& xs, uint64_t* never) {
+    const int n = xs.sc ? xs.sc->wait_first : 0;
+    return n > 0 ? mbar_wait(never, 0u, (unsigned)n) : true;
 }
 
 // Tile groups of one subdomain as scalars (no dynamically indexed arrays:
@@ -111,15 +119,17 @@ struct Groups {
 // the mode touches (from its first group on), st = ring depth, nl = longest
 // tile list of one CTA:
 //   k_symgemv<NR>: ring [st][kSymTile] | x [NR][span] | y [NR][span] | red [2][NR][8][64] |
-//                  bars (u64) [kSymStages] | tiles (u32) [nl]
-//   k_symgemv_ws: ring [st][kSymTile] | x [span] | y [4][span] | full, empty (u64) [kSymStages] | tiles (u32) [nl]
+//                  bars (u64) [kSymStages + 1] | tiles (u32) [nl]
+//   k_symgemv_ws: ring [st][kSymTile] | x [span] | y [4][span] | full, empty (u64) [kSymStages], never (u64) |
+//                 tiles (u32) [nl]
+// (the last barrier of each form is the one no copy completes, see first_wait_test)
 __host__ __device__ inline size_t sym_smem(int span, int st, int nl, int nr = 1) {
     size_t f = (size_t)st * kSymTile + 2 * (size_t)nr * span + 2 * (size_t)nr * 8 * 64;
-    return f * sizeof(float) + kSymStages * sizeof(uint64_t) + (size_t)nl * sizeof(uint32_t);
+    return f * sizeof(float) + (kSymStages + 1) * sizeof(uint64_t) + (size_t)nl * sizeof(uint32_t);
 }
 __host__ __device__ inline size_t sym_smem_ws(int span, int st, int nl) {
     size_t f = (size_t)st * kSymTile + 5 * (size_t)span;
-    return f * sizeof(float) + 2 * kSymStages * sizeof(uint64_t) + (size_t)nl * sizeof(uint32_t);
+    return f * sizeof(float) + (2 * kSymStages + 1) * sizeof(uint64_t) + (size_t)nl * sizeof(uint32_t);
 }
 
 // tile list entry: a << 16 | b << 3 | flags (a, b < 8192)
@@ -215,7 +225,8 @@ __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ desc
     float* ysh = xsh + NR * span_max;    // [NR][span_max]
     float* red = ysh + NR * span_max;    // [2][NR][8][64] transposed-role partials, double-buffered
     uint64_t* bars = reinterpret_cast<uint64_t*>(red + 2 * NR * 8 * 64);
-    uint32_t* tl = reinterpret_cast<uint32_t*>(bars + kSymStages);
+    uint64_t* never = bars + kSymStages;
+    uint32_t* tl = reinterpret_cast<uint32_t*>(never + 1);
 
     cg::cluster_group cluster = cg::this_cluster();
     const int tid = threadIdx.x;
@@ -237,6 +248,7 @@ __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ desc
     const uint64_t pol = l2_policy(sub % n_real < keep);   // stored subdomains below `keep` stay in L2
     if (tid == 0) {
         for (int s = 0; s < st; ++s) mbar_init(&bars[s], 1);
+        mbar_init(never, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         for (int s = 0; s < st && s < nt_cta; ++s, ++issued)
             load_tile(ring + s * kSymTile, tiles + entry_tile(lst[s], G) * kSymTile, &bars[s], pol);
@@ -289,7 +301,7 @@ __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ desc
                     xa[q][r] = xsh[q * span_max + ca * kSymT + rg * 8 + r - p_lo];
                 }
         }
-        const bool ok = mbar_wait(&bars[slot], phase);
+        const bool ok = (k > 0 || first_wait_test(xs, never)) && mbar_wait(&bars[slot], phase);
         const float4* T = reinterpret_cast<const float4*>(ring + slot * kSymTile) + rg * 8 * (kSymT / 4) + cq;
         float4 xb[NR], col[NR];
 #pragma unroll
@@ -382,7 +394,8 @@ __global__ void __launch_bounds__(kTW) k_symgemv_ws(const SymDesc* __restrict__ 
     float* yw = xsh + span_max;          // [4][span_max]: one partial y per consumer warp
     uint64_t* full = reinterpret_cast<uint64_t*>(yw + 4 * span_max);
     uint64_t* empty = full + kSymStages;
-    uint32_t* tl = reinterpret_cast<uint32_t*>(empty + kSymStages);
+    uint64_t* never = empty + kSymStages;
+    uint32_t* tl = reinterpret_cast<uint32_t*>(never + 1);
     __shared__ int abort_flag;
 
     cg::cluster_group cluster = cg::this_cluster();
@@ -407,6 +420,7 @@ __global__ void __launch_bounds__(kTW) k_symgemv_ws(const SymDesc* __restrict__ 
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 4);
         }
+        mbar_init(never, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         abort_flag = 0;
         for (int s = 0; s < st && s < nt_cta; ++s, ++issued)
@@ -459,7 +473,8 @@ __global__ void __launch_bounds__(kTW) k_symgemv_ws(const SymDesc* __restrict__ 
                     xa[r] = xsh[ca * kSymT + rg * 8 + r - p_lo];
                 }
             }
-            const bool ok = __all_sync(0xffffffffu, mbar_wait_or_abort(&full[slot], phase, &abort_flag));
+            const bool ok = __all_sync(0xffffffffu, (k > 0 || first_wait_test(xs, never)) &&
+                                                        mbar_wait_or_abort(&full[slot], phase, &abort_flag));
             if (!ok) {
                 if (lane == 0) abort_flag = 1;
                 bad = true;
@@ -612,19 +627,37 @@ void build_sym(dd_handle* h) {
     h->sym_elems = toff;
     for (int mode = 0; mode < GEMV_NMODES; ++mode) {
         h->mode_bytes_sym[mode] = 0.0;
+        h->mode_tile_bytes_sym[mode] = 0.0;
         int rmask, cmask;
         if (!sym_masks(mode, &rmask, &cmask)) continue;
-        double bytes = 0.0;
+        // algorithmic bytes: the distinct elements of the symmetric operator that
+        // y[R] = M[R, C] x[C] needs (a diagonal group block counts its triangle
+        // once, an off-diagonal pair of groups its rectangle once), 4 bytes each,
+        // plus the vectors; streamed bytes: the whole 64 x 64 tiles read.
+        double bytes = 0.0, tile_bytes = 0.0;
         for (const SymDesc& sd : h->sym) {
+            double elems = 0.0;
+            for (int ga = 0; ga < 3; ++ga)
+                for (int gb = 0; gb <= ga; ++gb) {
+                    const bool need = (((rmask >> ga) & 1) && ((cmask >> gb) & 1)) ||
+                                      (((rmask >> gb) & 1) && ((cmask >> ga) & 1));
+                    if (!need) continue;
+                    const double na = sd.n[ga], nb = sd.n[gb];
+                    elems += ga == gb ? na * (na + 1.0) / 2.0 : na * nb;
+                }
+            double vec = 0.0;
+            for (int g = 0; g < 3; ++g) {   // x and y vectors of the groups read and written
+                if ((cmask >> g) & 1) vec += 4.0 * sd.n[g];
+                if ((rmask >> g) & 1) vec += 4.0 * sd.n[g];
+            }
+            bytes += 4.0 * elems + vec;
             for (int a = 0; a < sd.t0[3]; ++a)
                 for (int b = 0; b <= a; ++b)
-                    if (sym_tile_flags(sd.t0, a, b, rmask, cmask) & 3) bytes += kTileBytes;
-            for (int g = 0; g < 3; ++g) {   // x and y vectors of the groups read and written
-                if ((cmask >> g) & 1) bytes += 4.0 * sd.n[g];
-                if ((rmask >> g) & 1) bytes += 4.0 * sd.n[g];
-            }
+                    if (sym_tile_flags(sd.t0, a, b, rmask, cmask) & 3) tile_bytes += kTileBytes;
+            tile_bytes += vec;
         }
         h->mode_bytes_sym[mode] = bytes;
+        h->mode_tile_bytes_sym[mode] = tile_bytes;
         // the mode's tiles of every stored subdomain in row order (what the kernel
         // streams; ensemble copies share member 0's list)
         std::vector<uint32_t>& tl = h->sym_tl[mode];

@@ -26,7 +26,9 @@ SYMBOLS = ["dd_setup", "dd_set_params", "dd_get_sizes", "dd_get_maps", "dd_set_p
            "dd_factor", "dd_step", "dd_schur_apply", "dd_schur_apply_static", "dd_coupled_apply", "dd_dp2_apply",
            "dd_get_interface_mass", "dd_probe", "dd_adjoint_reset", "dd_adjoint_step", "dd_probe_seed", "dd_autotune",
            "dd_get_tiles", "dd_get_sym_config", "dd_set_sym_config", "dd_set_beam", "dd_pic_step", "dd_pic_state",
-           "dd_get_state", "dd_set_state", "dd_profile", "dd_destroy", "dd_last_error"]
+           "dd_get_state", "dd_set_state", "dd_profile", "dd_destroy", "dd_last_error", "dd_step_scaled",
+           "dd_adjoint_step_scaled", "dd_probe_objective", "dd_set_eps", "dd_set_wait_limit", "dd_measure_fp64_rate",
+           "dd_get_gemv_bytes"]
 N_STAGES = 9
 STAGES = ["rhs", "local_solve", "iface_apply", "coarse", "corner", "recover", "vector", "refine", "factor"]
 
@@ -105,6 +107,14 @@ def load_library(path: str = LIB_PATH):
         "dd_set_beam": (C.c_int, [vp, C.POINTER(dd_beam)]),
         "dd_pic_step": (C.c_int, [vp, C.POINTER(dd_stats), vp]),
         "dd_pic_state": (C.c_int, [vp, vp, vp, vp, vp, C.POINTER(C.c_int64), vp]),
+        "dd_step_scaled": (C.c_int, [vp, vp, C.c_double, vp, C.POINTER(dd_stats), vp]),
+        "dd_adjoint_step_scaled": (C.c_int, [vp, vp, vp, vp, vp, vp, C.c_double, vp, vp, vp, C.POINTER(dd_stats),
+                                             vp]),
+        "dd_probe_objective": (C.c_int, [vp, vp, C.c_double, vp, vp]),
+        "dd_set_eps": (C.c_int, [vp, vp, vp]),
+        "dd_set_wait_limit": (C.c_int, [vp, C.c_int32, vp]),
+        "dd_measure_fp64_rate": (C.c_int, [C.POINTER(C.c_double), vp]),
+        "dd_get_gemv_bytes": (C.c_int, [vp, C.c_int32, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "dd_destroy": (None, [vp]),
         "dd_last_error": (C.c_char_p, [vp]),
     }
@@ -217,6 +227,48 @@ def dd_step(h, d2g=None, e_out=None, stats=True, stream=None, raise_on_error=Tru
     return dict(rc=rc, iters=st.iters, refinements=st.refinements, resid=st.resid, status=st.status)
 
 
+def dd_step_scaled(h, d2g, scale, e_out=None, stats=True, stream=None, raise_on_error=True):
+    """dd_step with the source scale * d2g (d2g: device pattern, scale: host scalar)."""
+    st = dd_stats()
+    rc = lib().dd_step_scaled(h, _ptr(d2g), float(scale), _ptr(e_out), C.byref(st) if stats else None,
+                              _stream(stream))
+    if raise_on_error:
+        _check(h, rc)
+    return dict(rc=rc, iters=st.iters, refinements=st.refinements, resid=st.resid, status=st.status)
+
+
+def dd_probe_objective(h, J, weight=1.0, e=None, stream=None):
+    """J (device scalar) += weight * sum_p |E(r_p; e)|^2, e = the current e^n when None."""
+    _check(h, lib().dd_probe_objective(h, _ptr(e), float(weight), _ptr(J), _stream(stream)))
+
+
+def dd_set_eps(h, eps, stream=None):
+    """New per-tet permittivity (device tensor [n_tets]); factor again afterwards."""
+    _check(h, lib().dd_set_eps(h, _ptr(eps), _stream(stream)))
+
+
+def dd_set_wait_limit(h, first_wait_polls, stream=None):
+    """Failure-path testing aid: the first packed-GEMV wait of every CTA gives up after this many polls."""
+    _check(h, lib().dd_set_wait_limit(h, int(first_wait_polls), _stream(stream)))
+
+
+def dd_measure_fp64_rate(stream=None):
+    """FP64 FMA throughput of the current device (TFLOP/s, CUDA-event timed)."""
+    v = C.c_double()
+    rc = lib().dd_measure_fp64_rate(C.byref(v), _stream(stream))
+    if rc != DD_OK:
+        raise DDError(rc, "dd_measure_fp64_rate failed")
+    return v.value
+
+
+def dd_get_gemv_bytes(h, kind, precision):
+    """(algorithmic, streamed) bytes of one full launch of a GEMV kind (name or index)."""
+    k = GEMV_KINDS.index(kind) if isinstance(kind, str) else int(kind)
+    a, b = C.c_double(), C.c_double()
+    _check(h, lib().dd_get_gemv_bytes(h, k, int(precision), C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
 def dd_schur_apply(h, lam, out, stream=None):
     _check(h, lib().dd_schur_apply(h, _ptr(lam), _ptr(out), _stream(stream)))
 
@@ -271,6 +323,17 @@ def dd_adjoint_step(h, seed, e_k=None, e_km1=None, e_km2=None, d2g_hat=None, gra
     st = dd_stats()
     rc = lib().dd_adjoint_step(h, _ptr(seed), _ptr(e_k), _ptr(e_km1), _ptr(e_km2), _ptr(d2g_hat), _ptr(grad_eps),
                                _ptr(grad_amp), _ptr(mu_out), C.byref(st) if stats else None, _stream(stream))
+    _check(h, rc)
+    return dict(rc=rc, iters=st.iters, refinements=st.refinements, resid=st.resid, status=st.status)
+
+
+def dd_adjoint_step_scaled(h, seed, e_k, e_km1, e_km2, d2g_hat, d2g_scale, grad_eps=None, grad_amp=None,
+                           mu_out=None, stats=True, stream=None):
+    """dd_adjoint_step with the unit source d2g_scale * d2g_hat."""
+    st = dd_stats()
+    rc = lib().dd_adjoint_step_scaled(h, _ptr(seed), _ptr(e_k), _ptr(e_km1), _ptr(e_km2), _ptr(d2g_hat),
+                                      float(d2g_scale), _ptr(grad_eps), _ptr(grad_amp), _ptr(mu_out),
+                                      C.byref(st) if stats else None, _stream(stream))
     _check(h, rc)
     return dict(rc=rc, iters=st.iters, refinements=st.refinements, resid=st.resid, status=st.status)
 

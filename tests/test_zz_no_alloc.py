@@ -35,6 +35,18 @@ def test_static_scratch_matches_workspace_path_twice():
         torch.cuda.synchronize()
         r, g = ref.cpu().numpy(), got.cpu().numpy()
         assert np.linalg.norm(g - r) <= 1e-12 * np.linalg.norm(r), call
+    # The point of the entry point: once the module is loaded (first call above),
+    # a call takes no device memory.  Free bytes are compared around a third call
+    # on a non-default stream; every tensor it touches exists beforehand.
+    side = torch.cuda.Stream()
+    again = torch.empty_like(lam)
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info()
+    D.dd_schur_apply_static(fs.h, lam, again, stream=side)
+    side.synchronize()
+    free_after, _ = torch.cuda.mem_get_info()
+    assert free_after == free_before
+    assert torch.equal(again, got)
     fs.close()
 
 
