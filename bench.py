@@ -69,13 +69,18 @@ def parse():
                     help="interface solver of the headline runs: Schur CG (Eq. f1schur) or coupled GMRES(20)")
     ap.add_argument("--no-sym", action="store_true",
                     help="DD_MIXED GEMVs on the dense FP32 copy instead of the packed symmetric tiles")
-    ap.add_argument("--ensemble", type=int, default=4,
+    ap.add_argument("--ensemble", type=int, default=16,
                     help="members of the multi-RHS (ensemble) run beside the headline; 0 or 1 skips it")
+    ap.add_argument("--ens-form", type=int, default=None, choices=[0, 1, 2, 3, 4],
+                    help="pin the packed kernel form of the ensemble run's kinds instead of tuning them "
+                         "(4: the tcgen05 form for the local solve, recovery and coupled operator)")
     ap.add_argument("--no-dp2", action="store_true",
                     help="skip the MFETI-DP2 runs (its own factorisation; coupled GMRES(20), FP64 at tol 1e-6 and mixed)")
     ap.add_argument("--no-other-configs", dest="other_configs", action="store_false",
                     help="skip the short runs of configs 3 (mixed/FP64), 5 (forward and adjoint) and 2 (PIC cycle)")
     ap.add_argument("--other-steps", type=int, default=10, help="timed steps of each other-config run")
+    ap.add_argument("--no-sparse-study", dest="sparse_study", action="store_false",
+                    help="skip the measured comparison with sparse local factors (cuSPARSE triangular solves)")
     ap.add_argument("--cpu-steps", type=int, default=3, help="oracle steps of the CPU baseline sample")
     ap.add_argument("--no-gmres", action="store_true",
                     help="skip the coupled-GMRES(20) vs Schur-CG comparison at the paper's tolerance 1e-6")
@@ -380,6 +385,80 @@ def other_configs(args, dev):
     return out
 
 
+def sparse_factor_study(cfg, dt, dev, reps=5):
+    """Measured comparison for the choice of dense swept inverses over sparse local
+    factors.  The sparse alternative: A_rr = L D L^T with a fill-reducing ordering
+    (SuperLU, symmetric mode, minimum degree on A^T + A, no pivoting), applied by
+    a forward and a backward triangular solve per local solve and per Arnoldi
+    step (the coupled operator's F_rr and F_rc pieces need A_rr^-1 each time).
+    The largest subdomain of the workload is factored on the host and replicated
+    over all subdomains as one block-diagonal FP32 CSR matrix; the two
+    triangular solves are timed on the GPU (cuSPARSE through torch, CUDA events),
+    beside the bytes of the dense operators the library streams instead."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    import torch
+    from oracle import dd as odd
+    from oracle import fem
+    from paper_2204_13254_gb300 import workloads as W
+    wf = W.config(cfg)
+    nx, ny, nz = wf.dims
+    kx, ky, kz = {1: (2, 2, 2), 4: (8, 8, 8), 2: (4, 4, 8), 5: (8, 8, 4), 3: (4, 4, 4)}[cfg]
+    bx, by, bz = nx // kx, ny // ky, nz // kz
+    L3 = (3 * bx * wf.L[0] / nx, 3 * by * wf.L[1] / ny, 3 * bz * wf.L[2] / nz)
+    w = W.box(3 * bx, 3 * by, 3 * bz, 3, 3, 3, L=L3)     # the centre subdomain is an interior one
+    space = fem.EdgeSpace(w.xyz, w.tets)
+    maps = odd.DDMaps(space, w.part, w.n_sub)
+    s = 13
+    loc = maps.local[s]
+    dof_map = -np.ones(space.n, dtype=np.int64)
+    dof_map[loc] = np.arange(len(loc))
+    Ts, Ss = space.assemble(maps.tets_of[s], dof_map, len(loc))
+    nr, ns = int(maps.nr[s]), len(loc)
+    nG = int(np.sum(maps.mult_sub[:, 0] == s) + np.sum(maps.mult_sub[:, 1] == s))
+    A = (Ts + (dt * dt / 4.0) * Ss).tocsc()
+    lu = spla.splu(A[:nr, :nr].tocsc(), permc_spec="MMD_AT_PLUS_A", diag_pivot_thresh=0.0,
+                   options=dict(SymmetricMode=True))
+    Lf = sp.tril(lu.L).tocsr().astype(np.float32)
+    nnzL = int(Lf.nnz)
+    nsub = wf.n_sub
+    Lb = sp.block_diag([Lf] * nsub, format="csr")
+    Lt = torch.sparse_csr_tensor(torch.tensor(Lb.indptr, dtype=torch.int32), torch.tensor(Lb.indices, dtype=torch.int32),
+                                 torch.tensor(Lb.data), size=Lb.shape, device=dev)
+    Ut = torch.sparse_csr_tensor(*(torch.tensor(a) for a in (lambda U: (U.indptr.astype(np.int32),
+                                                                         U.indices.astype(np.int32), U.data))(
+        Lb.T.tocsr())), size=Lb.shape, device=dev)
+    b = torch.ones((Lb.shape[0], 1), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def solve():
+        y = torch.triangular_solve(b, Lt, upper=False).solution
+        return torch.triangular_solve(y, Ut, upper=True).solution
+
+    solve()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(reps):
+        solve()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / reps
+    nGc = ns - nr + nG   # [Gamma | c] of this subdomain
+    return {
+        "subdomain": f"interior subdomain of {bx}x{by}x{bz} cubes: {ns} local unknowns, {nr} in A_rr, "
+                     f"{nG} interface + {ns - nr} corner",
+        "nnz_L_minimum_degree": nnzL, "dense_triangle_A_rr^-1": nr * (nr + 1) // 2,
+        "sparse_solve_pair_ms_all_subdomains": ms, "subdomains": nsub,
+        "sparse_bytes_per_solve_pair_all_subdomains": 2.0 * nnzL * 8 * nsub,
+        "dense_bytes_per_local_solve_all_subdomains (packed FP32)": nsub * 4.0 * (nr * (nr + 1) / 2 + (ns - nr) * nr),
+        "dense_bytes_per_arnoldi_step_all_subdomains (packed FP32 [Gamma|c] block)": nsub * 4.0 * nGc * (nGc + 1) / 2,
+        "note": ("a sparse factor needs one solve pair per local solve and per Arnoldi step (A_rr^-1 inside "
+                 "F_rr and F_rc); the dense path reads the swept inverse for the local solve and only the "
+                 "[Gamma|c] block per Arnoldi step"),
+    }
+
+
 def run_ours(args, rank, world, local):
     import torch
     from paper_2204_13254_gb300 import dd as D
@@ -604,6 +683,10 @@ def run_ours(args, rank, world, local):
         t_fe = time.perf_counter() - t0
         if not args.no_autotune:
             D.dd_autotune(fe.h, args.tune_cache)
+        if args.ens_form is not None:
+            for kind in ("local", "recover", "coupled"):
+                D.dd_set_sym_config(fe.h, kind, 1, 2, 0, args.ens_form)
+        ens_forms = D.dd_get_sym_config(fe.h)
         amps = [[1.0, -0.5, 2.0, 0.25][r % 4] * (1 + r // 4) for r in range(R)]
         ne = fe.n_dof
         De = torch.zeros((Wu + K, ne), dtype=torch.float64, device=dev)
@@ -635,6 +718,8 @@ def run_ours(args, rank, world, local):
                "iters_per_step": float(np.mean(ite)), "refinements_per_step": float(np.mean(rfe)),
                "gpu_launches": int(pe_prof["total_launches"]), "setup_s": t_se, "factor_s": t_fe,
                "operator_bytes_fp64": int(fe.sizes.dense_bytes_fp64),
+               "packed_forms (CTAs per subdomain, ring depth, subdomains kept in L2, form: 4 = tcgen05 BF16x3 MMA "
+               "over 16 members)": ens_forms,
                "rel_err_member0_vs_single_mixed": (float(torch.linalg.norm(ee[0] - e32) / torch.linalg.norm(e32))
                                                    if e32 is not None and args.solver == "gmres" else None)}
         fe.close()
@@ -647,6 +732,12 @@ def run_ours(args, rank, world, local):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         return float(t.item())
 
+    sparse = None
+    if args.sparse_study and not args.cavity and not pic and world == 1:
+        try:
+            sparse = sparse_factor_study(cfg, dt, dev)
+        except Exception as ex:   # context only: never fail the GPU line on it
+            sparse = {"error": repr(ex)[:300]}
     # bytes of one launch of each packed / dense GEMV kind, algorithmic and streamed
     gemv_bytes = {p_name: {kind: D.dd_get_gemv_bytes(fs.h, kind, prec) for kind in ("local", "iface_rows", "coupled",
                                                                                      "recover")}
@@ -667,7 +758,7 @@ def run_ours(args, rank, world, local):
     sizes = dict(n_dof=int(sizes0.n_dof), n_lambda=int(sizes0.n_lambda), n_corner=int(sizes0.n_corner),
                  dense_bytes_fp64=int(sizes0.dense_bytes_fp64))
     res = dict(fs=fs, K=K, ms64=ms64, ms32=ms32, ms64s=ms64s, ms32s=ms32s, same64=same64, same32=same32,
-               gemv_bytes=gemv_bytes, fp64_tflops=fp64_tflops, others=others,
+               gemv_bytes=gemv_bytes, fp64_tflops=fp64_tflops, others=others, sparse=sparse,
                ms_e2e=ms_e2e, it64=it64, it32=it32, ref32=ref32, prof64=prof64,
                prof32=prof32, rel=rel, launches64=launches64, launches32=launches32, t_setup=t_setup, t_factor=t_factor, clocks=clocks.summary(), sizes=sizes,
                workload=w, dt=dt, t_tune=t_tune, tiles=tiles, pic=pic, gmres=gm, dp2=dp2, ens=ens)
@@ -836,6 +927,7 @@ def main():
         "timing": ("value and fp64/mixed steps_per_s: CUDA-graph steps without per-step host readback; "
                    "with_stats_readback: the same steps reading iteration counts back after every step"),
         "other_configs": r["others"],
+        "sparse_factor_study": r["sparse"],
         "speedup_mixed_vs_fp64": v32 / v64,
         "coupled_gmres_vs_schur_cg": r["gmres"],
         "mfeti_dp2": r["dp2"],

@@ -138,10 +138,12 @@ typedef struct {
  * robin_alpha DP2 Robin coefficient; <= 0 selects dt / 2 (the admittance of
  *            vacuum, eta = 1, times Newmark's dt/2).
  * sym_fp32   DD_MIXED: 1 = the FP32 GEMVs over symmetric blocks (local solve,
- *            interface rows, coupled operator) read packed lower-triangular
- *            FP32 tiles (the swept local matrix is J times a symmetric matrix,
- *            J = diag(I_r, -I_c)), about 60 % of the dense bytes; 0 = the
- *            dense FP32 copy.  Results differ by FP32 rounding only.
+ *            interface rows, coupled operator) read the packed lower triangle
+ *            of the symmetric matrix S = J M (the swept local matrix M is J
+ *            times a symmetric matrix, J = diag(I_r, -I_c)) in FP32 tiles cut
+ *            to the index groups' own sizes (no padding of the groups;
+ *            diagonal tiles as triangles), about half of the dense bytes;
+ *            0 = the dense FP32 copy.  Results differ by FP32 rounding only.
  * members    Ensemble size R, 1..64 (fixed by dd_setup; dd_set_params must keep
  *            it).  R > 1 marches R independent field problems on the same mesh,
  *            materials and dt at once (multi-RHS batching): member r is copy r
@@ -499,8 +501,13 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
  * the ring as the four consumer warps release slots, each consumer warp keeping
  * its own partial y), 2 (ensembles) one CTA applying every tile it loads to the
  * x of 2 or 4 ensemble copies of its subdomain, 3 (ensembles) the same for
- * pairs of copies (host int32[7] each, 0 for the other kinds; any pointer may
- * be NULL). */
+ * pairs of copies, 4 (ensembles; local solve, recovery and coupled operator)
+ * the tensor-core form: one CTA applies the kind's operator rectangle, stored
+ * as 128 x 64 panels of three BF16 pieces (their sum is the FP64 value to about
+ * 24 bits), to the x of 16 ensemble copies by tcgen05 MMAs accumulating in FP32
+ * in tensor memory, six piece products per panel (results agree with the FP32
+ * forms to FP32 rounding; cl, st and keep do not apply) (host int32[7] each, 0
+ * for the other kinds; any pointer may be NULL). */
 int dd_get_tiles(const dd_handle* h, int32_t* lpr, int32_t* rows);
 
 /* Bytes of one full launch of GEMV kind `kind` (numbering of dd_get_tiles) at
@@ -517,8 +524,9 @@ int dd_get_sym_config(const dd_handle* h, int32_t* cl, int32_t* st, int32_t* kee
 
 /* Sets the packed-tile launch of GEMV kind `kind` (0, 5 or 6; 3 too for an
  * ensemble) to cl CTAs per subdomain (1, 2, 4 or 8), a ring of st tiles (2..4),
- * keep stored subdomains in L2 (0..n_sub) and kernel form ws (0..3 as in
- * dd_get_sym_config), as dd_autotune would (its next run may change it again).
+ * keep stored subdomains in L2 (0..n_sub) and kernel form ws (0..4 as in
+ * dd_get_sym_config; 4 only for an ensemble's kinds 0, 3 and 6), as
+ * dd_autotune would (its next run may change it again).
  * Results differ from another setting only in the order of FP32 sums.
  * DD_ERR_ARG for other kinds or values (or form 2 when its shared memory exceeds
  * a CTA's), DD_ERR_STATE before dd_bind_workspace or during a capture.
@@ -543,6 +551,17 @@ int dd_set_wait_limit(dd_handle* h, int32_t first_wait_polls, void* stream);
  * FP64 path (its GEMVs are FP64-ALU bound on GB300) is stated against it.
  * Synchronises `stream`.  Errors: DD_ERR_ARG, DD_ERR_CUDA. */
 int dd_measure_fp64_rate(double* tflops, void* stream);
+
+/* Self-check of the fifth-generation tensor-core path the library builds on
+ * (tcgen05 MMA, BF16 operands in shared memory, FP32 accumulator in tensor
+ * memory): one 128 x 16 x 64 product per operand layout on integer-valued
+ * inputs, compared element by element with the same sums on the CUDA cores.
+ * *passed_mask (host) receives bit v set for each layout that matched exactly:
+ * v = 0 A K-major; v = 1, 2 A stored M-major (the transposed operand) with the
+ * two assignments of the descriptor's leading and stride offsets.  The paper
+ * has no counterpart (a hardware check).  Synchronises `stream`.  Errors:
+ * DD_ERR_ARG, DD_ERR_CUDA. */
+int dd_tc_selftest(int32_t* passed_mask, void* stream);
 
 void dd_destroy(dd_handle* h);
 const char* dd_last_error(const dd_handle* h);

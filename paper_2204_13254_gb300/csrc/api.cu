@@ -227,6 +227,10 @@ size_t dd_workspace_layout(dd_handle* h, bool assign) {
     L.take(d.M32, (size_t)h->dense_elems);
     L.take(d.Msym, (size_t)h->sym_elems);
     L.take(d.symd, (size_t)h->n_sub);
+    L.take(d.sym_dir, h->sym_dir.size());
+    L.take(d.Mtc, (size_t)h->tc_elems);
+    for (int k = 0; k < kTcKinds; ++k) L.take(d.tcd[k], h->tcd[k].size());
+    L.take(d.tc_dir, h->tc_dir.size());
     for (int m = 0; m < GEMV_NMODES; ++m) {
         int rm, cm;
         if (sym_masks(m, &rm, &cm)) {
@@ -995,6 +999,10 @@ int dd_bind_workspace(dd_handle* h, void* dev, size_t bytes, void* stream) {
     CK(h, upload(h->d.col_dof, h->col_dof, s), "upload");
     CK(h, upload(h->d.Tval, h->Tval, s), "upload");
     CK(h, upload(h->d.symd, h->sym, s), "upload");
+    if (!h->sym_dir.empty()) CK(h, upload(h->d.sym_dir, h->sym_dir, s), "upload");
+    for (int k = 0; k < kTcKinds; ++k)
+        if (!h->tcd[k].empty()) CK(h, upload(h->d.tcd[k], h->tcd[k], s), "upload");
+    if (!h->tc_dir.empty()) CK(h, upload(h->d.tc_dir, h->tc_dir, s), "upload");
     CK(h, upload(h->d.mt_ptr, h->mt_ptr, s), "upload");
     CK(h, upload(h->d.mt_col, h->mt_col, s), "upload");
     CK(h, upload(h->d.mt_val, h->mt_val, s), "upload");
@@ -1077,6 +1085,7 @@ int dd_factor(dd_handle* h, double dt, void* stream) {
     {
         Prof P(h, ST_FACTOR, s, 1);
         CK(h, launch_sym_pack(h, s), "packed symmetric tiles");
+        CK(h, launch_tc_pack(h, s), "tensor-core panels");
     }
     int32_t st = 0;
     CK(h, (int)cudaMemcpyAsync(&st, h->d.status, 4, cudaMemcpyDeviceToHost, s), "status");
@@ -1847,7 +1856,8 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
                 found[{p, m}] = TileCfg{lpr, rows};
             int keep = 0, ws = 0;
             if (p == 2 && sym_active(h, m) && (lpr == 1 || lpr == 2 || lpr == 4 || lpr == 8) && rows >= 2 &&
-                rows <= kSymStages && (is >> keep >> ws) && keep >= 0 && keep <= h->n_sub && ws >= 0 && ws <= 3)
+                rows <= kSymStages && (is >> keep >> ws) && keep >= 0 && keep <= h->n_sub && ws >= 0 &&
+                (ws <= 3 || (ws == 4 && tc_available(h, m))))
                 found_cl[m] = SymCfg{lpr, rows, keep, ws};
         }
     }
@@ -1890,17 +1900,24 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
                     const bool form2 = h->members > 1 && sym_smem_bytes_nr(h, h->members <= 2 ? 2 : 4) <= 227 * 1024;
                     const bool form3 = h->members > 2 && sym_smem_bytes_nr(h, 2) <= 227 * 1024;
                     const int nsweep = 12 * (form3 ? 4 : (form2 ? 3 : 2));
-                    for (int cand = 0; cand < nsweep + (repeated ? 3 : 0) && !rc; ++cand) {
+                    const int ntc = tc_available(h, m) ? 1 : 0;   // the tensor-core form (one configuration)
+                    for (int cand = 0; cand < nsweep + ntc + (repeated ? 3 : 0) && !rc; ++cand) {
                         int cl, st, keep = 0, ws;
                         if (cand < nsweep) {
                             ws = cand / 12;
                             cl = 1 << ((cand % 12) / 3);
                             st = 2 + cand % 3;
+                        } else if (cand < nsweep + ntc) {
+                            ws = 4;
+                            cl = 1;
+                            st = 2;
+                        } else if (bcl.ws == 4) {
+                            break;   // no L2-kept subset for the tensor-core form
                         } else {
                             cl = bcl.cl;
                             st = bcl.st;
                             ws = bcl.ws;
-                            keep = std::min(h->n_sub, (int)((cand - nsweep + 1) * 32.0e6 / std::max(1.0, per_sub)));
+                            keep = std::min(h->n_sub, (int)((cand - nsweep - ntc + 1) * 32.0e6 / std::max(1.0, per_sub)));
                         }
                         h->sym_st[m] = st;
                         h->sym_keep[m] = keep;
@@ -2047,8 +2064,11 @@ int dd_set_sym_config(dd_handle* h, int32_t kind, int32_t cl, int32_t st, int32_
     if (kind < 0 || kind >= GEMV_NMODES || !sym_active(h, kind))
         return h->fail(DD_ERR_ARG, "dd_set_sym_config: not a packed GEMV kind");
     if (!(cl == 1 || cl == 2 || cl == 4 || cl == 8) || st < 2 || st > kSymStages || keep < 0 || keep > h->n_sub ||
-        ws < 0 || ws > 3)
-        return h->fail(DD_ERR_ARG, "dd_set_sym_config: cl in {1,2,4,8}, 2 <= st <= 4, 0 <= keep <= n_sub, ws in {0..3}");
+        ws < 0 || ws > 4)
+        return h->fail(DD_ERR_ARG, "dd_set_sym_config: cl in {1,2,4,8}, 2 <= st <= 4, 0 <= keep <= n_sub, ws in {0..4}");
+    if (ws == 4 && !tc_available(h, kind))
+        return h->fail(DD_ERR_ARG, "dd_set_sym_config: the tensor-core form needs an ensemble and a local solve, "
+                                   "recovery or coupled kind");
     if ((ws == 2 && sym_smem_bytes_nr(h, h->members <= 2 ? 2 : 4) > 227 * 1024) ||
         (ws == 3 && sym_smem_bytes_nr(h, 2) > 227 * 1024))
         return h->fail(DD_ERR_ARG, "dd_set_sym_config: the ensemble form needs more shared memory than a CTA has");

@@ -28,41 +28,60 @@ struct MatDesc {
 
 // Packed symmetric FP32 storage of the swept local matrices (DD_MIXED GEMVs).
 // M_s = J S_s with S_s symmetric and J = diag(I_r, -I_c) (A_rr^-1 and the
-// corner Schur complement are symmetric, M_s[c][r] = -M_s[r][c]^T), so
-// M_s[i][j] = J_i J_j M_s[j][i] and the lower triangle determines M_s.  Each
-// group (interior I, interface Gamma, corner c) is padded to whole
-// kSymT x kSymT tiles; the tiles of the lower triangle (tile row a >= tile
-// column b) are stored one after the other in the order of sym_tile_index,
-// row-major inside a tile, zeros in the padding; diagonal tiles are stored
-// whole.
+// corner Schur complement are symmetric, M_s[c][r] = -M_s[r][c]^T); the
+// lower triangle of S_s is stored and y = M x is formed as J (S x).  The local
+// order [I | Gamma | c] is cut into two runs of tile rows of height kSymT, the
+// interior I (tile rows 0 .. tI-1) and G = [Gamma | c] (tile rows tI .. nt-1),
+// the last row of each run as short as the run leaves it.  Tile (a, b), b <= a,
+// is h(a) x h(b): stored row-major with its width rounded up to 4 floats
+// (zeros after the last column), or, on the diagonal (a == b), as its lower
+// triangle with row r padded to 4 * ceil((r+1)/4) floats and the diagonal
+// entries halved (the tile then serves as a lower and as an upper triangle
+// alike).  Per subdomain the tiles follow each other without gaps: the lower
+// triangle of the G x G block (row order; everything the interface rows and the
+// coupled operator read is one run), the G x I rectangle, the lower triangle of
+// the I block.  Every tile starts on a 16-byte boundary and its size is a
+// multiple of 16 bytes (one bulk copy each).
 constexpr int kSymT = 64;
-constexpr int kSymTile = kSymT * kSymT;
+constexpr int kSymTile = kSymT * kSymT;   // floats of the largest tile (a ring slot)
 constexpr int kSymCLMax = 8;       // most CTAs per subdomain (one thread-block cluster)
 constexpr int kSymStages = 4;      // deepest TMA ring (tiles in flight per CTA)
 
 struct SymDesc {
-    int64_t toff;     // float offset of tile (0, 0) in the packed buffer
+    int64_t toff;     // float offset of the subdomain's first tile in the packed buffer
     int64_t voff;     // first slot of the subdomain
     int32_t n[3];     // nI, nGamma, nc
-    int32_t t0[4];    // first tile of each group; t0[3] = tiles per side
+    int32_t tI;       // tile rows of I
+    int32_t nt;       // tile rows in all (I, then G)
 };
 
-DD_HD inline int sym_group(const int32_t* t0, int a) { return a < t0[1] ? 0 : (a < t0[2] ? 1 : 2); }
-
-// Storage position of lower tile (a, b) inside its subdomain, t1 = first tile of
-// Gamma, nt = tiles per side: first the lower triangle of the [Gamma|c] block
-// (row order; everything the interface rows and the coupled operator read is
-// one contiguous run), then the [Gamma|c] x I rectangle (row order), then the
-// lower triangle of the I block.
-DD_HD inline int64_t sym_tile_index(int a, int b, int t1, int nt) {
-    const int64_t m = nt - t1;
-    if (b >= t1) {
-        const int64_t x = a - t1;
-        return x * (x + 1) / 2 + (b - t1);
-    }
-    if (a >= t1) return m * (m + 1) / 2 + (int64_t)(a - t1) * t1 + b;
-    return m * (m + 1) / 2 + m * t1 + (int64_t)a * (a + 1) / 2 + b;
+// Height of tile row a.
+DD_HD inline int sym_h(const SymDesc& sd, int a) {
+    const int left = a < sd.tI ? sd.n[0] - kSymT * a : sd.n[1] + sd.n[2] - kSymT * (a - sd.tI);
+    return left < kSymT ? left : kSymT;
 }
+// Element groups (bit 0 I, bit 1 Gamma, bit 2 c) present in tile row a.
+DD_HD inline int sym_gmask(const SymDesc& sd, int a) {
+    if (a < sd.tI) return 1;
+    const int g0 = kSymT * (a - sd.tI), g1 = g0 + sym_h(sd, a);
+    return (g0 < sd.n[1] ? 2 : 0) | (g1 > sd.n[1] ? 4 : 0);
+}
+// Local index of padded position p = kSymT * a + q (-1 beyond the run's end).
+DD_HD inline int sym_local(const SymDesc& sd, int p) {
+    const int a = p / kSymT, q = p - kSymT * a;
+    if (a < sd.tI) return kSymT * a + q < sd.n[0] ? kSymT * a + q : -1;
+    const int g = kSymT * (a - sd.tI) + q;
+    return g < sd.n[1] + sd.n[2] ? sd.n[0] + g : -1;
+}
+DD_HD inline int sym_lgroup(const SymDesc& sd, int l) { return l < sd.n[0] ? 0 : (l < sd.n[0] + sd.n[1] ? 1 : 2); }
+// Diagonal tiles: padded length and start of row r (floats).
+DD_HD inline int sym_rowlen(int r) { return ((r + 4) >> 2) << 2; }
+DD_HD inline int sym_trioff(int r) {
+    const int k = r >> 2, m = r & 3;
+    return 8 * k * (k + 1) + 4 * m * (k + 1);
+}
+// Floats of a stored tile of h rows and w columns (diag: the padded triangle).
+DD_HD inline int sym_tile_floats(int h, int w, bool diag) { return diag ? sym_trioff(h) : h * ((w + 3) & ~3); }
 
 // Row and column groups (bit 0 I, bit 1 Gamma, bit 2 c) of the GEMV modes that
 // use the packed storage; false for the others.
@@ -78,15 +97,39 @@ DD_HD inline bool sym_masks(int mode, int* rmask, int* cmask) {
 
 // What stored tile (a, b), b <= a, contributes to y[R] = M[R, C] x[C]:
 // bit 0 direct (rows of a, columns of b), bit 1 mirrored (rows of b, columns
-// of a: the transposed tile), bit 2 the mirrored tile enters with sign -1.
-DD_HD inline int sym_tile_flags(const int32_t* t0, int a, int b, int rmask, int cmask) {
-    const int ga = sym_group(t0, a), gb = sym_group(t0, b);
+// of a: the transposed tile), bit 2 a diagonal tile (both roles of its stored
+// triangle).  Element-level masks (x staged as 0 outside C, rows outside R not
+// stored) make a tile that only partly overlaps R or C exact.
+DD_HD inline int sym_tile_flags(const SymDesc& sd, int a, int b, int rmask, int cmask) {
+    const int ga = sym_gmask(sd, a), gb = sym_gmask(sd, b);
+    if (a == b) return ((ga & rmask) && (ga & cmask)) ? 7 : 0;
     int f = 0;
-    if (((rmask >> ga) & 1) && ((cmask >> gb) & 1)) f |= 1;
-    if (a != b && ((rmask >> gb) & 1) && ((cmask >> ga) & 1)) f |= 2;
-    if ((ga == 2) != (gb == 2)) f |= 4;
+    if ((ga & rmask) && (gb & cmask)) f |= 1;
+    if ((gb & rmask) && (ga & cmask)) f |= 2;
     return f;
 }
+
+// Tensor-core operator storage of the ensemble GEMVs (members > 1; kernel form 4
+// of the packed kinds local solve, recovery and coupled operator): the mode's
+// rectangle M_s[r0:r1, c0:c1] of the swept matrix cut into panels of 128 rows x
+// 64 columns, each stored as three BF16 matrices whose sum is the FP64 value to
+// about 24 bits (A1 = bf16(m), A2 = bf16(m - A1), A3 = bf16(m - A1 - A2)), in the
+// K-major core-matrix layout of the tcgen05 operands (zeros past r1 / c1).
+// Panels follow each other column block by column block (block q, then panel p).
+constexpr int kTcP = 128;                 // panel rows (MMA M)
+constexpr int kTcK = 64;                  // panel columns
+constexpr int kTcN = 16;                  // ensemble members per CTA (MMA N)
+constexpr int kTcPieceElems = kTcP * kTcK;      // BF16 elements of one piece
+constexpr int kTcBlockElems = 3 * kTcPieceElems; // of one panel block (three pieces)
+struct TcDesc {
+    int64_t off;        // BF16 element offset of block (p = 0, q = 0)
+    int32_t r0, r1;     // local row range of the mode
+    int32_t c0, c1;     // local column range
+    int32_t P, Q;       // panels and column blocks
+};
+// The tensor-core kinds and their index in the per-kind tables.
+DD_HD inline int tc_kind_index(int mode) { return mode == 0 ? 0 : (mode == 3 ? 1 : (mode == 6 ? 2 : -1)); }
+constexpr int kTcKinds = 3;
 
 // One CTA of a batched GEMV: rows [row0, row1) of matrix `mat`.
 struct GemvTask {
@@ -266,6 +309,10 @@ struct DevPtrs {
     float* M32 = nullptr;            // FP32 copy
     float* Msym = nullptr;           // packed symmetric FP32 tiles (see SymDesc)
     SymDesc* symd = nullptr;         // [n_sub]
+    int32_t* sym_dir = nullptr;      // [tiles * 4] (stored subdomain, a, b, float offset) of every stored tile
+    uint16_t* Mtc = nullptr;         // tensor-core operator storage of the ensemble GEMVs (BF16 bits, see TcDesc)
+    TcDesc* tcd[kTcKinds] = {};      // [n_sub_real] per tensor-core kind
+    int32_t* tc_dir = nullptr;       // [blocks * 4] (kind, stored subdomain, p, q) of every stored panel block
     int32_t* sym_rng[GEMV_NMODES] = {};   // [n_sub * kSymCLMax * kSymRng] (list offset, tile count, end tile row,
                                           // subdomain, ensemble members served) per CTA
     uint32_t* sym_tl[GEMV_NMODES] = {};   // tiles of each packed mode, every subdomain in row order
@@ -420,10 +467,15 @@ struct dd_handle {
     int32_t max_nr = 0, max_ns = 0;
     std::vector<GemvTask> tasks[2][GEMV_NMODES];   // per precision (tile shapes may differ)
     std::vector<SymDesc> sym;                      // packed symmetric storage per subdomain
+    std::vector<int32_t> sym_dir;                  // (stored subdomain, a, b, float offset) of every stored tile
+    std::vector<TcDesc> tcd[kTcKinds];             // tensor-core storage per kind and stored subdomain (ensembles)
+    std::vector<int32_t> tc_dir;                   // (kind, stored subdomain, p, q) of every panel block
+    int64_t tc_elems = 0;                          // BF16 elements of the tensor-core storage
     int64_t sym_elems = 0;
     int32_t sym_np_max = 0;                        // largest padded side (floats)
     std::vector<int32_t> sym_rng[GEMV_NMODES];
-    std::vector<uint32_t> sym_tl[GEMV_NMODES];     // tile list of each packed mode (a << 16 | b << 3 | flags)
+    std::vector<uint32_t> sym_tl[GEMV_NMODES];     // tile list of each packed mode: pairs (a << 16 | b << 3 | flags,
+                                                   // float offset of the tile in its subdomain)
     std::vector<int64_t> sym_tl_off[GEMV_NMODES];  // start of each subdomain's run in sym_tl (n_sub + 1)
     int32_t sym_cl[GEMV_NMODES] = {4, 1, 1, 1, 1, 2, 2};   // CTAs per subdomain of each packed mode
     int32_t sym_st[GEMV_NMODES] = {4, 4, 4, 4, 4, 4, 4};   // TMA ring depth of each packed mode
@@ -433,6 +485,7 @@ struct dd_handle {
                                                            // 2 ensemble copies of a subdomain in one CTA (up to 4),
                                                            // 3 ensemble copies in pairs
     int32_t sym_max_tiles = 0;                     // largest tile count of one subdomain
+    int64_t sym_ntiles = 0;                        // stored tiles in all (entries of sym_dir / 4)
     bool sym_ok = false;                           // the packed GEMV's shared memory fits one CTA
     size_t task_cap[GEMV_NMODES] = {};             // device capacity: tasks at the smallest row count
     TileCfg tile[2][GEMV_NMODES];                  // lanes per row and rows per CTA, per precision and mode
@@ -566,6 +619,11 @@ size_t sym_smem_bytes(const dd_handle* h);
 // Packed kinds in use: the recovery reads the packed tiles only for an ensemble (its I x [Gamma|c]
 // rectangle has no symmetric twin, so one problem gains almost nothing; an ensemble shares the reads).
 bool sym_active(const dd_handle* h, int mode);
+// tensor.cu
+void build_tc(dd_handle* h);
+int launch_tc_pack(const dd_handle* h, void* stream);
+int launch_tc_gemv(const dd_handle* h, int mode, XSrc xs, GemvOut go, const int32_t* skip, void* stream);
+bool tc_available(const dd_handle* h, int mode);
 size_t sym_smem_bytes_nr(const dd_handle* h, int nr);
 int sym_members_per_cta(const dd_handle* h, int mode);
 

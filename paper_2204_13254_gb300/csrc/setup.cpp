@@ -477,6 +477,7 @@ int dd_build_host(dd_handle* h, const dd_mesh* mesh, const int32_t* part, int32_
     }
 
     build_sym(h);
+    build_tc(h);
     h->sym_ok = sym_smem_bytes(h) <= 227 * 1024;
 
     // ---- batched GEMV task lists (default tiles; dd_autotune may change them) ------

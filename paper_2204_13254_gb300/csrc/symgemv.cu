@@ -3,37 +3,38 @@
 //
 // The swept local matrix is M_s = J S_s with S_s symmetric, J = diag(I_r, -I_c)
 // (A_rr^-1 and the corner Schur complement are symmetric and
-// M_s[c][r] = -M_s[r][c]^T), so only the lower triangle of 64x64 tiles is
-// stored (SymDesc).  For y[R] = M[R, C] x[C] (R, C unions of the groups I,
-// Gamma, c) a stored tile (a, b) acts directly (rows of a, columns of b)
-// and/or transposed (rows of b, columns of a, sign J_a J_b): every needed
-// tile is read from HBM once for both roles, about 60 % of the dense bytes of
-// the local solve, the interface rows and the coupled operator.
+// M_s[c][r] = -M_s[r][c]^T), so only the lower triangle of S_s is stored
+// (SymDesc: two runs of tile rows, I and [Gamma|c], short last rows, diagonal
+// tiles as padded triangles with halved diagonals) and y[R] = J_R (S[R, C] x[C]).
+// A stored tile (a, b) acts directly (rows of a, columns of b) and/or
+// transposed (rows of b, columns of a): every needed tile is read from HBM once
+// for both roles, and no padding of the index groups is streamed.
 //
 // Work split: the cl CTAs of a cluster (1..kSymCLMax; per mode, like the ring
 // depth st <= kSymStages, chosen by dd_autotune) share one subdomain by ranges of
-// tile rows (balanced on the host by tile count).  The tiles a mode needs are
-// listed once on the host (row order, per subdomain); a CTA copies its run of
-// that list to shared memory and stages only the x entries its tile rows read,
-// issuing the index loads of eight entries before their value loads.  It streams its tiles
-// through an st-deep ring of shared-memory buffers filled by
-// cp.async.bulk (one 16 KB copy per tile, completion on an mbarrier) issued by
-// one thread, and accumulates its partial y over the subdomain's whole padded
-// index range in shared memory:
+// tile rows (balanced on the host by bytes).  The tiles a mode needs are
+// listed once on the host (row order, per subdomain, with their storage
+// offsets); a CTA copies its run of that list to shared memory and stages only
+// the x entries its tile rows read, issuing the index loads of eight entries
+// before their value loads.  It streams its tiles through an st-deep ring of
+// shared-memory slots filled by cp.async.bulk (one copy per tile, completion on
+// an mbarrier) issued by one thread, and accumulates its partial S x over the
+// subdomain's padded index range in shared memory:
 //  * 128 threads; thread (rg, cq) = (tid / 16, tid % 16) reads rows
 //    8 rg .. 8 rg + 7, columns 4 cq .. 4 cq + 3 of the tile with 16-byte
-//    loads (a half-warp reads 256 contiguous bytes of one row: no bank
-//    conflicts);
+//    loads (a half-warp reads one row's contiguous chunks: no bank conflicts);
+//    a full 64 x 64 tile takes an unpredicated path, a short, narrow or
+//    diagonal tile a predicated one;
 //  * direct role: per-thread row partials stay in registers across the tile
 //    row and are reduced over the half-warp (fixed shuffle tree) when the
 //    tile row ends;
 //  * transposed role: the 8-row column partials of the eight row groups are
 //    added in fixed order once per tile.
 // The cluster then sums the cl partial vectors through distributed shared
-// memory in rank order.  All sums have a fixed order: results are
-// deterministic.  Every mbarrier wait is bounded: a wait that gives up sets an
-// error word, the CTA drains its outstanding copies (bounded again) and still
-// takes part in both cluster barriers, so no wait can hang the GPU.
+// memory in rank order and applies J.  All sums have a fixed order: results
+// are deterministic.  Every mbarrier wait is bounded: a wait that gives up sets
+// an error word, the CTA drains its outstanding copies (bounded again) and
+// still takes part in both cluster barriers, so no wait can hang the GPU.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -68,14 +69,15 @@ __device__ __forceinline__ uint64_t l2_policy(bool keep) {
     return pol;
 }
 
-// One 16 KB tile global -> shared, completing on `bar` (which expects the bytes).
-__device__ __forceinline__ void load_tile(float* dst, const float* src, uint64_t* bar, uint64_t pol) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(kTileBytes)
+// One tile (bytes: a multiple of 16, at most kTileBytes) global -> shared,
+// completing on `bar` (which expects the bytes).
+__device__ __forceinline__ void load_tile(float* dst, const float* src, uint32_t bytes, uint64_t* bar, uint64_t pol) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
             smem_u32(dst)),
-        "l"(src), "r"(kTileBytes), "r"(smem_u32(bar)), "l"(pol)
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
         : "memory");
 }
 
@@ -104,46 +106,71 @@ __device__ __forceinline__ bool first_wait_test(const XSrc& xs, uint64_t* never)
     return n > 0 ? mbar_wait(never, 0u, (unsigned)n) : true;
 }
 
-// Tile groups of one subdomain as scalars (no dynamically indexed arrays:
-// those would live in local memory).
-struct Groups {
-    int t1, t2, nt;   // first tile of Gamma, first tile of c, tiles per side
-    int n0, n1, n2;   // group sizes
-    __device__ __forceinline__ int of(int a) const { return (a >= t1) + (a >= t2); }
-    __device__ __forceinline__ int first(int g) const { return g == 0 ? 0 : (g == 1 ? t1 : t2); }
-    __device__ __forceinline__ int size(int g) const { return g == 0 ? n0 : (g == 1 ? n1 : n2); }
-    __device__ __forceinline__ int start(int g) const { return g == 0 ? 0 : (g == 1 ? n0 : n0 + n1); }
+// Shape of a listed tile: rows, padded width (floats per row of a rectangle),
+// diagonal (padded triangle), bytes.
+struct TileShape {
+    int h, wp;
+    bool diag, full;
+    uint32_t bytes;
 };
+
+__device__ __forceinline__ TileShape tile_shape(const SymDesc& sd, uint32_t e) {
+    const int a = (int)(e >> 16), b = (int)((e >> 3) & 0x1fff);
+    const bool diag = (e & 4) != 0;
+    TileShape t;
+    t.h = sym_h(sd, a);
+    const int w = sym_h(sd, b);
+    t.wp = (w + 3) & ~3;
+    t.diag = diag;
+    t.full = !diag && t.h == kSymT && w == kSymT;
+    t.bytes = 4u * (uint32_t)sym_tile_floats(t.h, w, diag);
+    return t;
+}
+
+// Issue the bulk copy of list entry k (pair e0, e1 in the shared-memory list).
+__device__ __forceinline__ void issue_tile(const uint32_t* tl, int k, const SymDesc& sd, const float* tiles, float* dst,
+                                           uint64_t* bar, uint64_t pol) {
+    const uint32_t e0 = tl[2 * k], e1 = tl[2 * k + 1];
+    load_tile(dst, tiles + e1, tile_shape(sd, e0).bytes, bar, pol);
+}
+
+// Row `row` (0..63), column chunk cq (0..15) of a tile in a ring slot: the four
+// floats as a float4, zero outside the stored tile.
+__device__ __forceinline__ float4 tile_chunk(const float* slot, const TileShape& t, int row, int cq) {
+    const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (row >= t.h) return z;
+    if (t.diag) return 4 * cq < sym_rowlen(row) ? *reinterpret_cast<const float4*>(slot + sym_trioff(row) + 4 * cq) : z;
+    return 4 * cq < t.wp ? *reinterpret_cast<const float4*>(slot + row * t.wp + 4 * cq) : z;
+}
 
 // Shared-memory layouts (floats unless noted), span = the padded index range
 // the mode touches (from its first group on), st = ring depth, nl = longest
 // tile list of one CTA:
 //   k_symgemv<NR>: ring [st][kSymTile] | x [NR][span] | y [NR][span] | red [2][NR][8][64] |
-//                  bars (u64) [kSymStages + 1] | tiles (u32) [nl]
+//                  bars (u64) [kSymStages + 1] | tile list (u32 pairs) [nl]
 //   k_symgemv_ws: ring [st][kSymTile] | x [span] | y [4][span] | full, empty (u64) [kSymStages], never (u64) |
-//                 tiles (u32) [nl]
+//                 tile list (u32 pairs) [nl]
 // (the last barrier of each form is the one no copy completes, see first_wait_test)
 __host__ __device__ inline size_t sym_smem(int span, int st, int nl, int nr = 1) {
     size_t f = (size_t)st * kSymTile + 2 * (size_t)nr * span + 2 * (size_t)nr * 8 * 64;
-    return f * sizeof(float) + (kSymStages + 1) * sizeof(uint64_t) + (size_t)nl * sizeof(uint32_t);
+    return f * sizeof(float) + (kSymStages + 1) * sizeof(uint64_t) + 2 * (size_t)nl * sizeof(uint32_t);
 }
 __host__ __device__ inline size_t sym_smem_ws(int span, int st, int nl) {
     size_t f = (size_t)st * kSymTile + 5 * (size_t)span;
-    return f * sizeof(float) + (2 * kSymStages + 1) * sizeof(uint64_t) + (size_t)nl * sizeof(uint32_t);
+    return f * sizeof(float) + (2 * kSymStages + 1) * sizeof(uint64_t) + 2 * (size_t)nl * sizeof(uint32_t);
 }
 
-// tile list entry: a << 16 | b << 3 | flags (a, b < 8192)
+// tile list entry: a << 16 | b << 3 | flags (a, b < 8192), then the tile's float offset
 __host__ __device__ __forceinline__ uint32_t tile_entry(int a, int b, int f) { return ((uint32_t)a << 16) | ((uint32_t)b << 3) | f; }
-__device__ __forceinline__ int64_t entry_tile(uint32_t e, const Groups& G) {
-    return sym_tile_index((int)(e >> 16), (int)((e >> 3) & 0x1fff), G.t1, G.nt);
-}
 
-__host__ __device__ inline int lowest_group(int mask) { return (mask & 1) ? 0 : ((mask & 2) ? 1 : 2); }
+// First padded position a mode touches (the I run only when I is in the mask).
+__host__ __device__ inline int mask_lo(const SymDesc& sd, int mask) { return (mask & 1) ? 0 : kSymT * sd.tI; }
 
 // x over the column groups of tile rows < a_end (the only ones the CTA reads),
-// eight entries per thread per pass: their index loads, then their value loads.
-__device__ __forceinline__ void stage_x(const XSrc& xs, const SymDesc& sd, const Groups& G, int cmask, int p_lo,
-                                        int p_end, float* xsh, int tid, int nthr) {
+// eight entries per thread per pass: their index loads, then their value loads;
+// 0 outside the column groups and past a run's end.
+__device__ __forceinline__ void stage_x(const XSrc& xs, const SymDesc& sd, int cmask, int p_lo, int p_end, float* xsh,
+                                        int tid, int nthr) {
     const float beta = (xs.kind == X_PCG || xs.kind == X_PCG_CV) ? (float)xs.sc->beta : 0.0f;
     constexpr int kStage = 8;
     for (int p0 = p_lo + tid; p0 < p_end; p0 += nthr * kStage) {
@@ -151,12 +178,11 @@ __device__ __forceinline__ void stage_x(const XSrc& xs, const SymDesc& sd, const
 #pragma unroll
         for (int u = 0; u < kStage; ++u) {
             const int p = p0 + u * nthr;
-            const int g = G.of(p / kSymT);
-            const int q = p - G.first(g) * kSymT;
-            const bool need = p < p_end && ((cmask >> g) & 1) && q < G.size(g);
-            ll[u] = need ? G.start(g) + q : -1;
-            mm[u] = need ? xs.slot_mult[sd.voff + ll[u]] : 0;
-            cc[u] = need ? xs.slot_corner[sd.voff + ll[u]] : -1;
+            const int l = p < p_end ? sym_local(sd, p) : -1;
+            const bool need = l >= 0 && ((cmask >> sym_lgroup(sd, l)) & 1);
+            ll[u] = need ? l : -1;
+            mm[u] = need ? xs.slot_mult[sd.voff + l] : 0;
+            cc[u] = need ? xs.slot_corner[sd.voff + l] : -1;
         }
         float vv[kStage];
 #pragma unroll
@@ -173,17 +199,18 @@ __device__ __forceinline__ void stage_x(const XSrc& xs, const SymDesc& sd, const
     }
 }
 
-// y[R] = sum over the cluster's partial vectors ysh (rank order); this CTA
+// y[R] = J_R (sum over the cluster's partial vectors ysh, rank order); this CTA
 // stores every cl-th chunk of rows.  Both cluster barriers are taken by every CTA.
 __device__ __forceinline__ void cluster_store(cg::cluster_group& cluster, const float* ysh, const SymDesc& sd,
-                                              const Groups& G, int rmask, int r_lo, int p_lo, int np, int cl,
-                                              const GemvOut& go, int tid, int nthr) {
+                                              int rmask, int r_lo, int p_lo, int np, int cl, const GemvOut& go,
+                                              int tid, int nthr) {
     cluster.sync();
     const int rank = (int)cluster.block_rank();
     for (int p = r_lo + rank * nthr + tid; p < np; p += cl * nthr) {
-        const int g = G.of(p / kSymT);
-        const int q = p - G.first(g) * kSymT;
-        if (!((rmask >> g) & 1) || q >= G.size(g)) continue;
+        const int l = sym_local(sd, p);
+        if (l < 0) continue;
+        const int g = sym_lgroup(sd, l);
+        if (!((rmask >> g) & 1)) continue;
         float part[kSymCLMax];
 #pragma unroll
         for (int c = 0; c < kSymCLMax; ++c)
@@ -192,7 +219,8 @@ __device__ __forceinline__ void cluster_store(cg::cluster_group& cluster, const 
 #pragma unroll
         for (int c = 0; c < kSymCLMax; ++c)
             if (c < cl) v += part[c];
-        const int64_t o = sd.voff + G.start(g) + q;
+        if (g == 2) v = -v;   // J: the corner rows of M = J S
+        const int64_t o = sd.voff + l;
         const int64_t oo = go.pos ? (int64_t)go.pos[o] : o;
         if (go.out32) {
             float w = (float)go.alpha * v;
@@ -226,22 +254,21 @@ __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ desc
     float* red = ysh + NR * span_max;    // [2][NR][8][64] transposed-role partials, double-buffered
     uint64_t* bars = reinterpret_cast<uint64_t*>(red + 2 * NR * 8 * 64);
     uint64_t* never = bars + kSymStages;
-    uint32_t* tl = reinterpret_cast<uint32_t*>(never + 1);
+    uint32_t* tl = reinterpret_cast<uint32_t*>(never + 1);   // pairs (entry, offset)
 
     cg::cluster_group cluster = cg::this_cluster();
     const int tid = threadIdx.x;
     const int32_t* rg5 = ranges + kSymRng * blockIdx.x;
     const int sub = rg5[3], nmem = rg5[4];
     const SymDesc sd = descs[sub];
-    const Groups G{sd.t0[1], sd.t0[2], sd.t0[3], sd.n[0], sd.n[1], sd.n[2]};
-    const int np = G.nt * kSymT;
+    const int np = sd.nt * kSymT;
     // this CTA's run of the mode's tile list and the end of its tile rows
-    const uint32_t* lst = tlist + rg5[0];
+    const uint32_t* lst = tlist + 2 * (int64_t)rg5[0];
     const int nt_cta = rg5[1];
     const int a_end = rg5[2];
     const float* tiles = Msym + sd.toff;
-    const int p_lo = G.first(lowest_group(rmask | cmask)) * kSymT;
-    const int r_lo = G.first(lowest_group(rmask)) * kSymT;
+    const int p_lo = mask_lo(sd, rmask | cmask);
+    const int r_lo = mask_lo(sd, rmask);
 
     // thread 0: barriers and the first st tiles (in flight while the CTA stages x)
     int issued = 0;
@@ -250,16 +277,15 @@ __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ desc
         for (int s = 0; s < st; ++s) mbar_init(&bars[s], 1);
         mbar_init(never, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        for (int s = 0; s < st && s < nt_cta; ++s, ++issued)
-            load_tile(ring + s * kSymTile, tiles + entry_tile(lst[s], G) * kSymTile, &bars[s], pol);
+        for (int s = 0; s < st && s < nt_cta; ++s, ++issued) issue_tile(lst, s, sd, tiles, ring + s * kSymTile, &bars[s], pol);
     }
-    for (int k = tid; k < nt_cta; k += kT) tl[k] = lst[k];
+    for (int k = tid; k < 2 * nt_cta; k += kT) tl[k] = lst[k];
     const int p_end = min(np, a_end * kSymT);
 #pragma unroll
     for (int q = 0; q < NR; ++q) {
         for (int p = p_lo + tid; p < np; p += kT) ysh[q * span_max + p - p_lo] = 0.0f;
         if (q < nmem) {
-            stage_x(xs, descs[sub + q * n_real], G, cmask, p_lo, p_end, xsh + q * span_max, tid, kT);
+            stage_x(xs, descs[sub + q * n_real], cmask, p_lo, p_end, xsh + q * span_max, tid, kT);
         } else {   // an empty member slot of the group reads zeros
             for (int p = p_lo + tid; p < p_end; p += kT) xsh[q * span_max + p - p_lo] = 0.0f;
         }
@@ -288,8 +314,9 @@ __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ desc
             }
     };
     for (; k < nt_cta; ++k) {
-        const uint32_t e = tl[k];
+        const uint32_t e = tl[2 * k];
         const int ca = (int)(e >> 16), cb = (int)((e >> 3) & 0x1fff), cf = (int)(e & 7);
+        const TileShape ts = tile_shape(sd, e);
         if (ca != cur) {
             if (cur >= 0) flush(cur);
             cur = ca;
@@ -302,7 +329,7 @@ __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ desc
                 }
         }
         const bool ok = (k > 0 || first_wait_test(xs, never)) && mbar_wait(&bars[slot], phase);
-        const float4* T = reinterpret_cast<const float4*>(ring + slot * kSymTile) + rg * 8 * (kSymT / 4) + cq;
+        const float* Ts = ring + slot * kSymTile;
         float4 xb[NR], col[NR];
 #pragma unroll
         for (int q = 0; q < NR; ++q) {
@@ -313,7 +340,9 @@ __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ desc
         if (ok) {
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
-                const float4 m = T[r * (kSymT / 4)];
+                const int row = rg * 8 + r;
+                const float4 m = ts.full ? *reinterpret_cast<const float4*>(Ts + row * kSymT + 4 * cq)
+                                         : tile_chunk(Ts, ts, row, cq);
 #pragma unroll
                 for (int q = 0; q < NR; ++q) {
                     acc[q][r] = fmaf(m.x, xb[q].x, fmaf(m.y, xb[q].y, fmaf(m.z, xb[q].z, fmaf(m.w, xb[q].w, acc[q][r]))));
@@ -324,14 +353,19 @@ __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ desc
                 }
             }
         }
+        // A diagonal tile ends its tile row, and its transposed role adds to that row's
+        // y after the barrier below: the row's direct-role partials go first.
+        if (cf & 4) {   // (uniform over the CTA: every thread reads the same entry)
+            flush(cur);
+            cur = -1;
+        }
         float* rd = red + (k & 1) * NR * 8 * 64;
 #pragma unroll
         for (int q = 0; q < NR; ++q) *reinterpret_cast<float4*>(rd + q * 512 + rg * 64 + 4 * cq) = col[q];
         bad = __syncthreads_or(!ok) != 0;   // also: every thread is done with ring slot `slot`
         if (bad) break;
         if (tid == 0 && k + st < nt_cta) {
-            const uint32_t en = tl[k + st];
-            load_tile(ring + slot * kSymTile, tiles + entry_tile(en, G) * kSymTile, &bars[slot], pol);
+            issue_tile(tl, k + st, sd, tiles, ring + slot * kSymTile, &bars[slot], pol);
             ++issued;
         }
         if (cf & 2) {   // transposed role: column c of the tile for member q, 8 row groups in order
@@ -340,7 +374,7 @@ __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ desc
                 float sum = rd[q * 512 + c];
 #pragma unroll
                 for (int g = 1; g < 8; ++g) sum += rd[q * 512 + g * 64 + c];
-                ysh[q * span_max + cb * kSymT + c - p_lo] += (cf & 4) ? -sum : sum;
+                ysh[q * span_max + cb * kSymT + c - p_lo] += sum;
             }
         }
         if (++slot == st) {
@@ -355,7 +389,7 @@ __global__ void __launch_bounds__(kT) k_symgemv(const SymDesc* __restrict__ desc
     }
 
     for (int q = 0; q < nmem; ++q)
-        cluster_store(cluster, ysh + q * span_max, descs[sub + q * n_real], G, rmask, r_lo, p_lo, np, cl, go, tid, kT);
+        cluster_store(cluster, ysh + q * span_max, descs[sub + q * n_real], rmask, r_lo, p_lo, np, cl, go, tid, kT);
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -395,7 +429,7 @@ __global__ void __launch_bounds__(kTW) k_symgemv_ws(const SymDesc* __restrict__ 
     uint64_t* full = reinterpret_cast<uint64_t*>(yw + 4 * span_max);
     uint64_t* empty = full + kSymStages;
     uint64_t* never = empty + kSymStages;
-    uint32_t* tl = reinterpret_cast<uint32_t*>(never + 1);
+    uint32_t* tl = reinterpret_cast<uint32_t*>(never + 1);   // pairs (entry, offset)
     __shared__ int abort_flag;
 
     cg::cluster_group cluster = cg::this_cluster();
@@ -403,14 +437,13 @@ __global__ void __launch_bounds__(kTW) k_symgemv_ws(const SymDesc* __restrict__ 
     const int warp = tid >> 5, lane = tid & 31;
     const int sub = ranges[kSymRng * blockIdx.x + 3];
     const SymDesc sd = descs[sub];
-    const Groups G{sd.t0[1], sd.t0[2], sd.t0[3], sd.n[0], sd.n[1], sd.n[2]};
-    const int np = G.nt * kSymT;
-    const uint32_t* lst = tlist + ranges[kSymRng * blockIdx.x];
+    const int np = sd.nt * kSymT;
+    const uint32_t* lst = tlist + 2 * (int64_t)ranges[kSymRng * blockIdx.x];
     const int nt_cta = ranges[kSymRng * blockIdx.x + 1];
     const int a_end = ranges[kSymRng * blockIdx.x + 2];
     const float* tiles = Msym + sd.toff;
-    const int p_lo = G.first(lowest_group(rmask | cmask)) * kSymT;
-    const int r_lo = G.first(lowest_group(rmask)) * kSymT;
+    const int p_lo = mask_lo(sd, rmask | cmask);
+    const int r_lo = mask_lo(sd, rmask);
     const int span = np - p_lo;
 
     int issued = 0;   // producer lane only
@@ -423,12 +456,11 @@ __global__ void __launch_bounds__(kTW) k_symgemv_ws(const SymDesc* __restrict__ 
         mbar_init(never, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         abort_flag = 0;
-        for (int s = 0; s < st && s < nt_cta; ++s, ++issued)
-            load_tile(ring + s * kSymTile, tiles + entry_tile(lst[s], G) * kSymTile, &full[s], pol);
+        for (int s = 0; s < st && s < nt_cta; ++s, ++issued) issue_tile(lst, s, sd, tiles, ring + s * kSymTile, &full[s], pol);
     }
-    for (int k = tid; k < nt_cta; k += kTW) tl[k] = lst[k];
+    for (int k = tid; k < 2 * nt_cta; k += kTW) tl[k] = lst[k];
     for (int p = tid; p < 4 * span; p += kTW) yw[(p / span) * span_max + p % span] = 0.0f;
-    stage_x(xs, sd, G, cmask, p_lo, min(np, a_end * kSymT), xsh, tid, kTW);
+    stage_x(xs, sd, cmask, p_lo, min(np, a_end * kSymT), xsh, tid, kTW);
     __syncthreads();
 
     if (warp == 4) {
@@ -440,7 +472,7 @@ __global__ void __launch_bounds__(kTW) k_symgemv_ws(const SymDesc* __restrict__ 
                     abort_flag = 1;
                     break;
                 }
-                load_tile(ring + s * kSymTile, tiles + entry_tile(tl[k], G) * kSymTile, &full[s], pol);
+                issue_tile(tl, k, sd, tiles, ring + s * kSymTile, &full[s], pol);
                 ++issued;
             }
         }
@@ -462,8 +494,9 @@ __global__ void __launch_bounds__(kTW) k_symgemv_ws(const SymDesc* __restrict__ 
             __syncwarp();
         };
         for (int k = 0; k < nt_cta; ++k) {
-            const uint32_t e = tl[k];
+            const uint32_t e = tl[2 * k];
             const int ca = (int)(e >> 16), cb = (int)((e >> 3) & 0x1fff), cf = (int)(e & 7);
+            const TileShape ts = tile_shape(sd, e);
             if (ca != cur) {
                 if (cur >= 0) flush(cur);
                 cur = ca;
@@ -480,13 +513,15 @@ __global__ void __launch_bounds__(kTW) k_symgemv_ws(const SymDesc* __restrict__ 
                 bad = true;
                 break;
             }
-            const float4* T = reinterpret_cast<const float4*>(ring + slot * kSymTile) + rg * 8 * (kSymT / 4) + cq;
+            const float* Ts = ring + slot * kSymTile;
             const float4 xb = (cf & 1) ? *reinterpret_cast<const float4*>(xsh + cb * kSymT + 4 * cq - p_lo)
                                        : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             float4 col = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
-                const float4 m = T[r * (kSymT / 4)];
+                const int row = rg * 8 + r;
+                const float4 m = ts.full ? *reinterpret_cast<const float4*>(Ts + row * kSymT + 4 * cq)
+                                         : tile_chunk(Ts, ts, row, cq);
                 acc[r] = fmaf(m.x, xb.x, fmaf(m.y, xb.y, fmaf(m.z, xb.z, fmaf(m.w, xb.w, acc[r]))));
                 col.x = fmaf(m.x, xa[r], col.x);
                 col.y = fmaf(m.y, xa[r], col.y);
@@ -503,17 +538,10 @@ __global__ void __launch_bounds__(kTW) k_symgemv_ws(const SymDesc* __restrict__ 
                 if (lane < 16) {
                     float4* yp = reinterpret_cast<float4*>(yc + cb * kSymT + 4 * cq - p_lo);
                     float4 yv = *yp;
-                    if (cf & 4) {
-                        yv.x -= col.x;
-                        yv.y -= col.y;
-                        yv.z -= col.z;
-                        yv.w -= col.w;
-                    } else {
-                        yv.x += col.x;
-                        yv.y += col.y;
-                        yv.z += col.z;
-                        yv.w += col.w;
-                    }
+                    yv.x += col.x;
+                    yv.y += col.y;
+                    yv.z += col.z;
+                    yv.w += col.w;
                     *yp = yv;
                 }
                 __syncwarp();
@@ -537,31 +565,42 @@ __global__ void __launch_bounds__(kTW) k_symgemv_ws(const SymDesc* __restrict__ 
     // the four warp copies, added in warp order into copy 0
     for (int p = tid; p < span; p += kTW)
         yw[p] = ((yw[p] + yw[span_max + p]) + yw[2 * span_max + p]) + yw[3 * span_max + p];
-    cluster_store(cluster, yw, sd, G, rmask, r_lo, p_lo, np, cl, go, tid, kTW);
+    cluster_store(cluster, yw, sd, rmask, r_lo, p_lo, np, cl, go, tid, kTW);
 }
 
-// Pack: tile (a, b) of subdomain blockIdx.y from the swept FP64 matrix.
+// Pack: one CTA per stored tile (directory entry blockIdx.x) from the swept FP64
+// matrix: S = J M rounded to FP32 (corner rows negated), the diagonal halved on
+// diagonal tiles, zeros in the padding.
 __global__ void k_sym_pack(const SymDesc* __restrict__ descs, const MatDesc* __restrict__ mats,
-                           const double* __restrict__ M, float* __restrict__ Msym) {
-    const SymDesc sd = descs[blockIdx.y];
-    const int nt = sd.t0[3];
-    const int64_t kt = blockIdx.x;
-    if (kt >= (int64_t)nt * (nt + 1) / 2) return;
-    int a = (int)((sqrt(8.0 * (double)kt + 1.0) - 1.0) * 0.5);
-    while ((int64_t)a * (a + 1) / 2 > kt) --a;
-    while ((int64_t)(a + 1) * (a + 2) / 2 <= kt) ++a;
-    const int b = (int)(kt - (int64_t)a * (a + 1) / 2);
-    const MatDesc md = mats[blockIdx.y];
-    const int gstart[3] = {0, sd.n[0], sd.n[0] + sd.n[1]};
-    const int ga = sym_group(sd.t0, a), gb = sym_group(sd.t0, b);
-    float* out = Msym + sd.toff + sym_tile_index(a, b, sd.t0[1], nt) * kSymTile;
-    for (int e = threadIdx.x; e < kSymTile; e += blockDim.x) {
-        const int qi = (a - sd.t0[ga]) * kSymT + e / kSymT;
-        const int qj = (b - sd.t0[gb]) * kSymT + e % kSymT;
-        float v = 0.0f;
-        if (qi < sd.n[ga] && qj < sd.n[gb])
-            v = (float)M[md.moff + (int64_t)(gstart[ga] + qi) * md.ld + gstart[gb] + qj];
-        out[e] = v;
+                           const int32_t* __restrict__ dir, const double* __restrict__ M, float* __restrict__ Msym) {
+    const int32_t* dr = dir + 4 * (int64_t)blockIdx.x;
+    const int s = dr[0], a = dr[1], b = dr[2];
+    const SymDesc sd = descs[s];
+    const MatDesc md = mats[s];
+    const bool diag = a == b;
+    const int h = sym_h(sd, a), w = sym_h(sd, b), wp = (w + 3) & ~3;
+    const int nfl = sym_tile_floats(h, w, diag);
+    const int la0 = a < sd.tI ? kSymT * a : sd.n[0] + kSymT * (a - sd.tI);
+    const int lb0 = b < sd.tI ? kSymT * b : sd.n[0] + kSymT * (b - sd.tI);
+    float* out = Msym + sd.toff + dr[3];
+    for (int e = threadIdx.x; e < nfl; e += blockDim.x) {
+        int r, j;
+        if (diag) {
+            r = 0;
+            while (r + 1 < h && sym_trioff(r + 1) <= e) ++r;
+            j = e - sym_trioff(r);
+        } else {
+            r = e / wp;
+            j = e - r * wp;
+        }
+        double v = 0.0;
+        if (j < w && (!diag || j <= r)) {
+            const int li = la0 + r, lj = lb0 + j;
+            v = M[md.moff + (int64_t)li * md.ld + lj];
+            if (li >= sd.n[0] + sd.n[1]) v = -v;   // S = J M
+            if (diag && j == r) v *= 0.5;
+        }
+        out[e] = (float)v;
     }
 }
 
@@ -577,6 +616,7 @@ bool sym_active(const dd_handle* h, int mode) {
 // shared memory of form 2, so more CTAs share an SM, at two tile reads per
 // four members).
 int sym_members_per_cta(const dd_handle* h, int mode) {
+    if (h->sym_ws[mode] == 4) return 1;   // the tensor-core form has its own grid (sym_ranges unused)
     if (h->sym_ws[mode] == 3) return 2;
     if (h->sym_ws[mode] != 2) return 1;
     return h->members <= 2 ? 2 : 4;
@@ -594,37 +634,54 @@ size_t sym_smem_bytes(const dd_handle* h) {
 int sym_span(const dd_handle* h, int mode) {
     int rmask, cmask, span = 0;
     if (!sym_masks(mode, &rmask, &cmask)) return 0;
-    const int gl = lowest_group(rmask | cmask);
-    for (const SymDesc& sd : h->sym) span = std::max(span, (sd.t0[3] - sd.t0[gl]) * kSymT);
+    for (const SymDesc& sd : h->sym) span = std::max(span, sd.nt * kSymT - mask_lo(sd, rmask | cmask));
     return span;
 }
 
-// Host side: tile descriptors and the algorithmic bytes of every packed mode.
+// Host side: tile descriptors, the tile directory, the algorithmic and
+// streamed bytes and the tile list of every packed mode.
 void build_sym(dd_handle* h) {
     h->sym.assign(h->n_sub, SymDesc{});
+    h->sym_dir.clear();
     int64_t toff = 0;
     h->sym_np_max = 0;
     h->sym_max_tiles = 0;
+    std::vector<std::vector<int32_t>> offs(h->n_sub_real);   // float offset of tile (a, b) at a * nt + b
+    auto tile_fl = [](const SymDesc& sd, int a, int b) { return sym_tile_floats(sym_h(sd, a), sym_h(sd, b), a == b); };
     for (int s = 0; s < h->n_sub; ++s) {
         SymDesc& sd = h->sym[s];
-        sd.toff = toff;
         sd.voff = h->mats[s].voff;
         sd.n[0] = h->nI[s];
         sd.n[1] = h->nG[s];
         sd.n[2] = h->nC[s];
-        sd.t0[0] = 0;
-        for (int g = 0; g < 3; ++g) sd.t0[g + 1] = sd.t0[g] + (sd.n[g] + kSymT - 1) / kSymT;
-        const int nt = sd.t0[3];
-        const int64_t ntl = (int64_t)nt * (nt + 1) / 2;
+        sd.tI = (sd.n[0] + kSymT - 1) / kSymT;
+        sd.nt = sd.tI + (sd.n[1] + sd.n[2] + kSymT - 1) / kSymT;
         if (s >= h->n_sub_real) {   // ensemble copy: member 0's tiles
             sd.toff = h->sym[s % h->n_sub_real].toff;
             continue;
         }
-        toff += ntl * kSymTile;
+        const int nt = sd.nt, tI = sd.tI;
+        std::vector<int32_t>& off = offs[s];
+        off.assign((size_t)nt * nt, -1);
+        int64_t cur = 0;
+        auto put = [&](int a, int b) {
+            off[(size_t)a * nt + b] = (int32_t)cur;
+            h->sym_dir.insert(h->sym_dir.end(), {s, a, b, (int32_t)cur});
+            cur += tile_fl(sd, a, b);
+        };
+        for (int a = tI; a < nt; ++a)
+            for (int b = tI; b <= a; ++b) put(a, b);
+        for (int a = tI; a < nt; ++a)
+            for (int b = 0; b < tI; ++b) put(a, b);
+        for (int a = 0; a < tI; ++a)
+            for (int b = 0; b <= a; ++b) put(a, b);
+        sd.toff = toff;
+        toff += cur;
         h->sym_np_max = std::max(h->sym_np_max, nt * kSymT);
-        h->sym_max_tiles = std::max<int32_t>(h->sym_max_tiles, (int32_t)ntl);
+        h->sym_max_tiles = std::max<int32_t>(h->sym_max_tiles, (int32_t)((int64_t)nt * (nt + 1) / 2));
     }
     h->sym_elems = toff;
+    h->sym_ntiles = (int64_t)h->sym_dir.size() / 4;
     for (int mode = 0; mode < GEMV_NMODES; ++mode) {
         h->mode_bytes_sym[mode] = 0.0;
         h->mode_tile_bytes_sym[mode] = 0.0;
@@ -633,9 +690,10 @@ void build_sym(dd_handle* h) {
         // algorithmic bytes: the distinct elements of the symmetric operator that
         // y[R] = M[R, C] x[C] needs (a diagonal group block counts its triangle
         // once, an off-diagonal pair of groups its rectangle once), 4 bytes each,
-        // plus the vectors; streamed bytes: the whole 64 x 64 tiles read.
+        // plus the vectors; streamed bytes: the stored tiles read.
         double bytes = 0.0, tile_bytes = 0.0;
-        for (const SymDesc& sd : h->sym) {
+        for (int s = 0; s < h->n_sub; ++s) {
+            const SymDesc& sd = h->sym[s];
             double elems = 0.0;
             for (int ga = 0; ga < 3; ++ga)
                 for (int gb = 0; gb <= ga; ++gb) {
@@ -651,34 +709,36 @@ void build_sym(dd_handle* h) {
                 if ((rmask >> g) & 1) vec += 4.0 * sd.n[g];
             }
             bytes += 4.0 * elems + vec;
-            for (int a = 0; a < sd.t0[3]; ++a)
+            for (int a = 0; a < sd.nt; ++a)
                 for (int b = 0; b <= a; ++b)
-                    if (sym_tile_flags(sd.t0, a, b, rmask, cmask) & 3) tile_bytes += kTileBytes;
+                    if (sym_tile_flags(sd, a, b, rmask, cmask)) tile_bytes += 4.0 * tile_fl(sd, a, b);
             tile_bytes += vec;
         }
         h->mode_bytes_sym[mode] = bytes;
         h->mode_tile_bytes_sym[mode] = tile_bytes;
-        // the mode's tiles of every stored subdomain in row order (what the kernel
-        // streams; ensemble copies share member 0's list)
+        // the mode's tiles of every stored subdomain in row order, with their offsets
+        // (what the kernel streams; ensemble copies share member 0's list)
         std::vector<uint32_t>& tl = h->sym_tl[mode];
         std::vector<int64_t>& off = h->sym_tl_off[mode];
         tl.clear();
         off.assign(1, 0);
         for (int s = 0; s < h->n_sub_real; ++s) {
             const SymDesc& sd = h->sym[s];
-            for (int a = 0; a < sd.t0[3]; ++a)
+            for (int a = 0; a < sd.nt; ++a)
                 for (int b = 0; b <= a; ++b) {
-                    const int f = sym_tile_flags(sd.t0, a, b, rmask, cmask);
-                    if (f & 3) tl.push_back(tile_entry(a, b, f));
+                    const int f = sym_tile_flags(sd, a, b, rmask, cmask);
+                    if (!f) continue;
+                    tl.push_back(tile_entry(a, b, f));
+                    tl.push_back((uint32_t)offs[s][(size_t)a * sd.nt + b]);
                 }
-            off.push_back((int64_t)tl.size());
+            off.push_back((int64_t)tl.size() / 2);
         }
         sym_ranges(h, mode, h->sym_cl[mode]);
     }
 }
 
 // Work of each of the cl CTAs of every subdomain for `mode`: contiguous tile-row
-// ranges, CTA c ending where the running tile count comes closest to (c + 1) / cl
+// ranges, CTA c ending where the running byte count comes closest to (c + 1) / cl
 // of the subdomain's total; stored as (first entry in the mode's tile list, tile
 // count, end tile row, subdomain, members served).  Ensemble copies of a
 // subdomain follow each other (they stream the same tiles, which L2 then serves).
@@ -692,12 +752,15 @@ void sym_ranges(dd_handle* h, int mode, int cl) {
     const int per = sym_members_per_cta(h, mode);   // ensemble copies served by one CTA
     for (int s0 = 0; s0 < h->n_sub_real; ++s0) {
         const SymDesc& sd = h->sym[s0];
-        const int nt = sd.t0[3];
-        std::vector<int64_t> per_row(nt, 0);
+        const int nt = sd.nt;
+        std::vector<int64_t> per_row(nt, 0), cnt_row(nt, 0);   // needed floats / tiles of each tile row
         int64_t total = 0;
         for (int a = 0; a < nt; ++a) {
             for (int b = 0; b <= a; ++b)
-                if (sym_tile_flags(sd.t0, a, b, rmask, cmask) & 3) ++per_row[a];
+                if (sym_tile_flags(sd, a, b, rmask, cmask)) {
+                    per_row[a] += sym_tile_floats(sym_h(sd, a), sym_h(sd, b), a == b);
+                    ++cnt_row[a];
+                }
             total += per_row[a];
         }
         for (int m0 = 0; m0 < R; m0 += per) {
@@ -714,7 +777,7 @@ void sym_ranges(dd_handle* h, int mode, int cl) {
                     if (a < nt && target - run > run + per_row[a] - target) run += per_row[a++];
                 }
                 int64_t n = 0;
-                for (int q = begin; q < a; ++q) n += per_row[q];
+                for (int q = begin; q < a; ++q) n += cnt_row[q];
                 h->sym_rng[mode].push_back((int32_t)first);
                 h->sym_rng[mode].push_back((int32_t)n);
                 h->sym_rng[mode].push_back(n ? a : 0);
@@ -743,15 +806,15 @@ void sym_ranges(dd_handle* h, int mode, int cl) {
 }
 
 int launch_sym_pack(const dd_handle* h, void* stream) {
-    if (h->n_sub == 0 || h->sym_max_tiles == 0) return 0;
-    k_sym_pack<<<dim3((unsigned)h->sym_max_tiles, (unsigned)h->n_sub_real), kT, 0, S(stream)>>>(h->d.symd, h->d.mats,
-                                                                                           h->d.M64, h->d.Msym);
+    if (h->n_sub == 0 || h->sym_ntiles == 0) return 0;
+    k_sym_pack<<<(unsigned)h->sym_ntiles, kT, 0, S(stream)>>>(h->d.symd, h->d.mats, h->d.sym_dir, h->d.M64, h->d.Msym);
     return (int)cudaGetLastError();
 }
 
 int launch_symgemv(const dd_handle* h, int mode, XSrc xs, GemvOut go, const int32_t* skip, void* stream) {
     int rmask, cmask;
     if (!sym_masks(mode, &rmask, &cmask)) return (int)cudaErrorInvalidValue;
+    if (h->sym_ws[mode] == 4) return launch_tc_gemv(h, mode, xs, go, skip, stream);
     xs.slot_mult = h->d.slot_mult;
     xs.slot_corner = h->d.slot_corner;
     xs.sc = h->d.sc;

@@ -28,7 +28,7 @@ SYMBOLS = ["dd_setup", "dd_set_params", "dd_get_sizes", "dd_get_maps", "dd_set_p
            "dd_get_tiles", "dd_get_sym_config", "dd_set_sym_config", "dd_set_beam", "dd_pic_step", "dd_pic_state",
            "dd_get_state", "dd_set_state", "dd_profile", "dd_destroy", "dd_last_error", "dd_step_scaled",
            "dd_adjoint_step_scaled", "dd_probe_objective", "dd_set_eps", "dd_set_wait_limit", "dd_measure_fp64_rate",
-           "dd_get_gemv_bytes"]
+           "dd_get_gemv_bytes", "dd_tc_selftest"]
 N_STAGES = 9
 STAGES = ["rhs", "local_solve", "iface_apply", "coarse", "corner", "recover", "vector", "refine", "factor"]
 
@@ -115,6 +115,7 @@ def load_library(path: str = LIB_PATH):
         "dd_set_wait_limit": (C.c_int, [vp, C.c_int32, vp]),
         "dd_measure_fp64_rate": (C.c_int, [C.POINTER(C.c_double), vp]),
         "dd_get_gemv_bytes": (C.c_int, [vp, C.c_int32, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+        "dd_tc_selftest": (C.c_int, [C.POINTER(C.c_int32), vp]),
         "dd_destroy": (None, [vp]),
         "dd_last_error": (C.c_char_p, [vp]),
     }
@@ -267,6 +268,15 @@ def dd_get_gemv_bytes(h, kind, precision):
     a, b = C.c_double(), C.c_double()
     _check(h, lib().dd_get_gemv_bytes(h, k, int(precision), C.byref(a), C.byref(b)))
     return a.value, b.value
+
+
+def dd_tc_selftest(stream=None):
+    """Bitmask of the tcgen05 operand layouts whose 128x16x64 BF16 MMA matched the CUDA cores exactly."""
+    m = C.c_int32()
+    rc = lib().dd_tc_selftest(C.byref(m), _stream(stream))
+    if rc != DD_OK:
+        raise DDError(rc, "dd_tc_selftest failed")
+    return m.value
 
 
 def dd_schur_apply(h, lam, out, stream=None):

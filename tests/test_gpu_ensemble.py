@@ -207,3 +207,59 @@ def test_five_members_two_groups():
     for r, a in enumerate(amps):
         err = rel_err(f[:, r], a * ref)
         assert err[2:].max() <= 1e-8, (r, err.max())
+
+
+def _pin_tensor_core(fs):
+    """The tensor-core form (ws = 4) for the local solve, the recovery and the coupled
+    operator; the interface rows keep the CTA-synchronous packed form."""
+    for kind in ("local", "recover", "coupled"):
+        D.dd_set_sym_config(fs.h, kind, 1, 2, 0, 4)
+    D.dd_set_sym_config(fs.h, "iface_rows", 1, 2, 0, 0)
+    cfg = D.dd_get_sym_config(fs.h)
+    assert all(cfg[k][3] == 4 for k in ("local", "recover", "coupled"))
+
+
+@pytest.mark.parametrize("amps", [(1.0, -0.5, 2.0), tuple((-1.0) ** r * (1 + r % 5) for r in range(18))])
+def test_tensor_core_form_every_member_matches_oracle(amps):
+    """tcgen05 form: a CTA applies each BF16x3 operator panel to 16 members by MMA
+    (3 members: one group with 13 empty slots; 18 members: groups of 16 and 2);
+    member r carries the source at amplitude a_r and equals a_r times the oracle's
+    unit-source march to 1e-8 after FP64 refinement."""
+    need_gpu()
+    w = W.config(1)
+    dt = DT["config1"]["dt"]
+    n = 25
+    sources = [(w.source_pairs, a) for a in amps]
+    prm = D.make_params(precision=D.DD_MIXED, tol=1e-5, refine_tol=1e-12, max_refine=8, solver=G,
+                        members=len(amps))
+    f, stats = run_ensemble(w, dt, n, prm, sources, after_factor=_pin_tensor_core)
+    assert all(s["status"] == 0 for s in stats)
+    ref = oracle_member(w, dt, n, w.source_pairs, 1.0)
+    for r, a in enumerate(amps):
+        err = rel_err(f[:, r], a * ref)
+        assert err[2:].max() <= 1e-8, (r, err.max())
+
+
+def test_tensor_core_form_ragged_rcb():
+    """tcgen05 form on a jittered mesh with a ragged RCB split (rectangles not
+    multiples of the 128 x 64 panel), eps per tet: every member within 1e-8 of its
+    oracle march."""
+    need_gpu()
+    nx, ny, nz = 10, 8, 8
+    L = (1.2, 1.0, 1.0)
+    xyz, tets = W.kuhn_box(nx, ny, nz, *L)
+    xyz, rng = W.jitter_nodes(xyz, L[0] / nx, L, 0.2, seed=9)
+    part = W.rcb_partition(W.tet_centroids(xyz, tets), 6, rng.uniform(0.6, 1.4, size=6))
+    w = W.Workload("ragged", xyz, tets, part, 6, rng.uniform(1, 4, size=len(tets)), 1.0, 30,
+                   W.z_line_node_pairs(nx, ny, nz, 5, 4))
+    space = fem.EdgeSpace(xyz, tets, w.eps)
+    T, S = space.assemble()
+    dt = 2.0 * newmark.cfl_dt(T, S)
+    n = 30
+    sources = member_sources(w, (nx, ny, nz))[:2]
+    prm = D.make_params(precision=D.DD_MIXED, tol=1e-5, refine_tol=1e-12, max_refine=8, solver=G, members=2)
+    f, stats = run_ensemble(w, dt, n, prm, sources, after_factor=_pin_tensor_core)
+    assert all(s["status"] == 0 for s in stats)
+    for r, (pairs, amp) in enumerate(sources):
+        err = rel_err(f[:, r], oracle_member(w, dt, n, pairs, amp))
+        assert err[2:].max() <= 1e-8, (r, err.max())

@@ -59,3 +59,35 @@ def test_graph_ragged_and_no_stats():
     Fe, _ = march(w, dt, 30, D.make_params(tol=1e-12))
     Fg, _ = march(w, dt, 30, D.make_params(tol=1e-12, use_graph=1, chunk=1), stats=False)
     assert np.array_equal(Fe, Fg)
+
+
+@pytest.mark.parametrize("ws", [0, 1])
+def test_packed_forms_are_deterministic(ws):
+    """Two marches of the same mixed-precision problem with every packed kind on one
+    kernel form give bitwise equal fields (fixed summation order, no races), on a
+    cavity whose subdomains span many tiles (8^3-cube subdomains)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    w = W.cavity(16, 2, steps=12)
+    dt = 0.03
+    fs = D.FieldSolver(w.xyz, w.tets, w.part, w.n_sub,
+                       params=D.make_params(precision=D.DD_MIXED, tol=1e-5, refine_tol=1e-10, max_refine=6,
+                                            solver=D.DD_SOLVER_COUPLED_GMRES)).bind()
+    fs.factor(dt)
+    for kind in ("local", "iface_rows", "coupled"):
+        D.dd_set_sym_config(fs.h, kind, 2, 3, 0, ws)
+    pat = torch.zeros(fs.n_dof, dtype=torch.float64, device="cuda")
+    pat[torch.as_tensor(fs.dof_of_pairs(w.source_pairs), device="cuda")] = 1.0
+    d2g = w.d2G(dt, 12)
+    zero = torch.zeros(fs.n_dof, dtype=torch.float64, device="cuda")
+    runs = []
+    for _ in range(2):
+        fs.set_state(zero, zero, 0)
+        out = torch.empty_like(zero)
+        its = []
+        for k in range(12):
+            its.append(D.dd_step_scaled(fs.h, pat, d2g[k], out)["iters"])
+        runs.append((out.clone(), its))
+    fs.close()
+    assert torch.equal(runs[0][0], runs[1][0])
+    assert runs[0][1] == runs[1][1]
