@@ -714,6 +714,15 @@ def run_ours(args, rank, world, local):
         pe_prof = fe.profile(enable=0, read=True)
         ee, _, _ = fe.get_state()
         ee = ee.view(R, -1)
+        ens_stages = None
+        if not args.no_profile:   # per-stage split: an eager pass over a few steps with events per launch
+            fe.set_params(D.make_params(precision=D.DD_MIXED, tol=args.tol32, refine_tol=args.refine_tol,
+                                        max_refine=6, solver=D.DD_SOLVER_COUPLED_GMRES, sym_fp32=sym, members=R))
+            fe.profile(enable=1, read=False)
+            ks = min(K, 4)
+            for k in range(ks):
+                fe.step(De[Wu + k], stats=True)
+            ens_stages = stage_table(fe.profile(enable=0, read=True), ks)
         ens = {"members": R, "amplitudes": amps, "member_steps_per_s": R * K * 1e3 / mse, "ms_per_step": mse / K,
                "iters_per_step": float(np.mean(ite)), "refinements_per_step": float(np.mean(rfe)),
                "gpu_launches": int(pe_prof["total_launches"]), "setup_s": t_se, "factor_s": t_fe,
@@ -721,7 +730,8 @@ def run_ours(args, rank, world, local):
                "packed_forms (CTAs per subdomain, ring depth, subdomains kept in L2, form: 4 = tcgen05 BF16x3 MMA "
                "over 16 members)": ens_forms,
                "rel_err_member0_vs_single_mixed": (float(torch.linalg.norm(ee[0] - e32) / torch.linalg.norm(e32))
-                                                   if e32 is not None and args.solver == "gmres" else None)}
+                                                   if e32 is not None and args.solver == "gmres" else None),
+               "stages (eager pass, CUDA events per launch)": ens_stages}
         fe.close()
         del De
 

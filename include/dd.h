@@ -492,7 +492,7 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
 /* Current tiles: lpr[p*7 + k], rows[p*7 + k] for precision p (0 FP64, 1 FP32)
  * and GEMV kind k (0 local, 1 corner rows, 2 corner coupling, 3 recovery,
  * 4 coarse, 5 interface rows, 6 coupled operator) of the dense kernel; host
- * int32[14] each.  Kinds 0, 5 and 6 (and 3, the recovery, for an ensemble)
+ * int32[14] each.  Kinds 0, 3, 5 and 6
  * run in DD_MIXED on the packed symmetric tiles when sym_fp32 = 1: cl[k] CTAs (one cluster) per subdomain, a TMA ring
  * of st[k] tiles, and the tiles of subdomains 0 .. keep[k]-1 copied with an
  * L2 evict_last policy (the rest evict_first) so that they stay in L2 across
@@ -522,8 +522,7 @@ int dd_get_tiles(const dd_handle* h, int32_t* lpr, int32_t* rows);
 int dd_get_gemv_bytes(const dd_handle* h, int32_t kind, int32_t precision, double* algorithmic, double* streamed);
 int dd_get_sym_config(const dd_handle* h, int32_t* cl, int32_t* st, int32_t* keep, int32_t* ws);
 
-/* Sets the packed-tile launch of GEMV kind `kind` (0, 5 or 6; 3 too for an
- * ensemble) to cl CTAs per subdomain (1, 2, 4 or 8), a ring of st tiles (2..4),
+/* Sets the packed-tile launch of GEMV kind `kind` (0, 3, 5 or 6) to cl CTAs per subdomain (1, 2, 4 or 8), a ring of st tiles (2..4),
  * keep stored subdomains in L2 (0..n_sub) and kernel form ws (0..4 as in
  * dd_get_sym_config; 4 only for an ensemble's kinds 0, 3 and 6), as
  * dd_autotune would (its next run may change it again).

@@ -220,7 +220,10 @@ struct PcgScalars {
 constexpr int kMaxRestart = DD_MAX_RESTART;
 constexpr int kMaxMembers = 64;   // ensemble size limit
 constexpr int kSymRng = 5;        // ints per CTA in a packed GEMV work table
-constexpr int kGmElems = 4;                          // vector elements per thread in the GMRES kernels
+#ifndef DD_GM_ELEMS
+#define DD_GM_ELEMS 4
+#endif
+constexpr int kGmElems = DD_GM_ELEMS;                // vector elements per thread in the GMRES kernels
 constexpr int kGmChunk = kGmElems * 256;             // elements per block
 
 // Device state of the restarted GMRES of the coupled system (one struct in the

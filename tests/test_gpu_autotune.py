@@ -49,5 +49,6 @@ def test_autotune_results_and_cache(tmp_path):
         assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
         D.dd_autotune(fs.h, cache)               # complete cache entry: tiles read back, no timing
         assert D.dd_get_tiles(fs.h) == tiles
-        assert sum(1 for _ in open(cache)) == 2 * len(D.GEMV_KINDS) + 3      # + packed-mode cluster sizes and ring depths
+        # one line per dense kind and precision, one per packed kind (cluster size, ring depth, L2 kept, form)
+        assert sum(1 for _ in open(cache)) == 2 * len(D.GEMV_KINDS) + len(D.dd_get_sym_config(fs.h))
         fs.close()

@@ -74,7 +74,7 @@ def test_packed_forms_are_deterministic(ws):
                        params=D.make_params(precision=D.DD_MIXED, tol=1e-5, refine_tol=1e-10, max_refine=6,
                                             solver=D.DD_SOLVER_COUPLED_GMRES)).bind()
     fs.factor(dt)
-    for kind in ("local", "iface_rows", "coupled"):
+    for kind in ("local", "recover", "iface_rows", "coupled"):
         D.dd_set_sym_config(fs.h, kind, 2, 3, 0, ws)
     pat = torch.zeros(fs.n_dof, dtype=torch.float64, device="cuda")
     pat[torch.as_tensor(fs.dof_of_pairs(w.source_pairs), device="cuda")] = 1.0

@@ -248,7 +248,7 @@ def test_extrapolated_warm_start_matches_oracle(prec, solver, scheme, graph):
     fs.close()
 
 
-PACKED_KINDS = ("local", "iface_rows", "coupled")
+PACKED_KINDS = ("local", "recover", "iface_rows", "coupled")
 
 
 @pytest.mark.parametrize("solver", [D.DD_SOLVER_SCHUR_CG, D.DD_SOLVER_COUPLED_GMRES])
@@ -312,7 +312,7 @@ def test_sym_config_rejects_bad_values():
     fs = D.FieldSolver(w.xyz, w.tets, w.part, w.n_sub, w.eps, w.mu,
                        D.make_params(precision=D.DD_MIXED, tol=1e-5)).bind()
     fs.factor(DT["config1"]["dt"])
-    for args in [("corner_rows", 1, 2, 0, 0), ("recover", 1, 2, 0, 0), ("local", 3, 2, 0, 0), ("local", 1, 5, 0, 0), ("local", 1, 1, 0, 0),
+    for args in [("corner_rows", 1, 2, 0, 0), ("coarse", 1, 2, 0, 0), ("local", 3, 2, 0, 0), ("local", 1, 5, 0, 0), ("local", 1, 1, 0, 0),
                  ("local", 1, 2, w.n_sub + 1, 0), ("local", 1, 2, 0, 4), ("local", 1, 2, 0, -1)]:
         with pytest.raises(RuntimeError):
             D.dd_set_sym_config(fs.h, *args)
