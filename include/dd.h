@@ -64,6 +64,10 @@ extern "C" {
                                       Sec. IV, Fig. fetiIter)                                      */
 #define DD_MAX_RESTART 32          /* largest GMRES restart length                                */
 
+/* Factorisation paths (dd_params.factor_mode). */
+#define DD_FACTOR_FP64 0    /* trailing updates on the FP64 CUDA cores                      */
+#define DD_FACTOR_TENSOR 1  /* trailing updates from BF16 slices on the tensor cores, FP64-accurate */
+
 /* Domain-decomposition schemes (dd_params.scheme). */
 #define DD_SCHEME_DP1 0  /* MFETI-DP1 (Sec. III-A): one multiplier per interface edge         */
 #define DD_SCHEME_DP2 1  /* MFETI-DP2 (Sec. III-B), edge-only reading: Robin term alpha*M_T on
@@ -160,7 +164,16 @@ typedef struct {
  *            same absolute, not relative, accuracy).  R > 1 needs
  *            DD_SOLVER_COUPLED_GMRES (the Schur CG would need the dense inverse
  *            of the stacked coarse problem; DD_ERR_ARG otherwise); probes, the
- *            PIC cycle, the adjoint and dd_schur_apply return DD_ERR_STATE. */
+ *            PIC cycle, the adjoint and dd_schur_apply return DD_ERR_STATE.
+ * factor_mode DD_FACTOR_FP64 (0): the elimination's trailing updates (rank-32
+ *            GEMMs, Sec. III-C's one inverse per subdomain) on the FP64 CUDA
+ *            cores; DD_FACTOR_TENSOR (1): the same updates on the tensor cores,
+ *            FP64-accurate: every row of the column panel and every column of
+ *            the row panel is scaled by a power of two and cut into seven 8-bit
+ *            BF16 slices, the slice products of each weight class are summed
+ *            exactly in FP32 tensor memory (tcgen05 MMAs) and the classes are
+ *            combined in FP64 (an Ozaki splitting).  Results agree with the FP64
+ *            path to FP64 rounding.  Read by dd_factor. */
 typedef struct {
     int precision;
     double tol;
@@ -177,6 +190,7 @@ typedef struct {
     int scheme;
     double robin_alpha;
     int members;
+    int factor_mode;
 } dd_params;
 
 /* Sizes of a set-up problem. */

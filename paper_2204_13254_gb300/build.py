@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdd.so")
-SOURCES = ["setup.cpp", "kernels.cu", "api.cu", "gmres.cu", "symgemv.cu", "static_scratch.cu", "tensor.cu"]
+SOURCES = ["setup.cpp", "kernels.cu", "api.cu", "gmres.cu", "symgemv.cu", "static_scratch.cu", "tensor.cu", "ozaki.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3"]
 

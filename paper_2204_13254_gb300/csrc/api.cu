@@ -51,6 +51,7 @@ dd_params default_params() {
     p.scheme = DD_SCHEME_DP1;
     p.robin_alpha = 0.0;
     p.members = 1;
+    p.factor_mode = DD_FACTOR_FP64;
     return p;
 }
 
@@ -70,6 +71,8 @@ int check_params(dd_handle* h, const dd_params& p) {
     if (p.solver == DD_SOLVER_COUPLED_GMRES) {
         if (p.restart < 1 || p.restart > kMaxRestart) return h->fail(DD_ERR_ARG, "restart must be in 1..DD_MAX_RESTART");
     }
+    if (p.factor_mode != DD_FACTOR_FP64 && p.factor_mode != DD_FACTOR_TENSOR)
+        return h->fail(DD_ERR_ARG, "factor_mode must be DD_FACTOR_FP64 or DD_FACTOR_TENSOR");
     if (p.members < 1 || p.members > kMaxMembers) return h->fail(DD_ERR_ARG, "members must be in 1..64");
     if (p.members > 1 && p.solver != DD_SOLVER_COUPLED_GMRES)
         return h->fail(DD_ERR_ARG, "an ensemble (members > 1) is solved by the coupled GMRES");
@@ -241,6 +244,11 @@ size_t dd_workspace_layout(dd_handle* h, bool assign) {
     L.take(d.K64, nc * (size_t)h->ldc);
     L.take(d.K32, nc * (size_t)h->ldc);
     L.take(d.Pinv, (size_t)(h->n_sub + 1) * kNB * kNB);
+    {   // slices and exponents of one pivot block for the tensor-core trailing update (local or coarse)
+        const int nloc = std::max(1, h->n_sub_real), ncor = (int)nc;
+        L.take(d.oz_slices, std::max(oz_slice_elems(nloc, h->max_ns), oz_slice_elems(1, ncor)));
+        L.take(d.oz_exps, 2 * std::max((size_t)nloc * h->max_ns, (size_t)ncor));
+    }
     L.take(d.dinv, nm);
     for (int k = 0; k < 3; ++k) L.take(d.e[k], nd);
     for (int k = 0; k < 3; ++k) L.take(d.mu[k], nd);
@@ -342,6 +350,14 @@ size_t dd_workspace_layout(dd_handle* h, bool assign) {
 }
 
 namespace {
+
+// True when a bounded device wait gave up since the word was last cleared (synchronises).
+bool wait_err_set(dd_handle* h, cudaStream_t s) {
+    int32_t v = 0;
+    if (cudaMemcpyAsync(&v, &h->d.sc->wait_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) return false;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return false;
+    return v != 0;
+}
 
 // Read the CG scalars back (synchronises the stream).
 int read_scalars(dd_handle* h, PcgScalars* out, cudaStream_t s) {
@@ -1091,6 +1107,11 @@ int dd_factor(dd_handle* h, double dt, void* stream) {
     CK(h, (int)cudaMemcpyAsync(&st, h->d.status, 4, cudaMemcpyDeviceToHost, s), "status");
     CK(h, (int)cudaStreamSynchronize(s), "sync");
     if (st != 0) return h->fail(DD_ERR_NOT_SPD, "non-positive pivot in the local or coarse elimination");
+    if (wait_err_set(h, s)) {   // a bounded wait of the tensor-core update gave up: the factors are void
+        CK(h, (int)cudaMemsetAsync(&h->d.sc->wait_err, 0, sizeof(int32_t), s), "clear wait error");
+        CK(h, (int)cudaStreamSynchronize(s), "sync");
+        return h->fail(DD_ERR_TIMEOUT, "a bounded device wait of the tensor-core elimination gave up");
+    }
     const size_t nd = (size_t)h->n_dof;
     for (int k = 0; k < 3; ++k) CK(h, (int)cudaMemsetAsync(h->d.e[k], 0, sizeof(double) * nd, s), "memset");
     CK(h, (int)cudaStreamSynchronize(s), "sync");
@@ -1180,13 +1201,6 @@ int report_timeout(dd_handle* h, cudaStream_t s) {
     return DD_ERR_TIMEOUT;
 }
 
-// True when a packed-GEMV wait gave up since the word was last cleared (synchronises).
-bool wait_err_set(dd_handle* h, cudaStream_t s) {
-    int32_t v = 0;
-    if (cudaMemcpyAsync(&v, &h->d.sc->wait_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) return false;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return false;
-    return v != 0;
-}
 
 int advance(dd_handle* h, const double* u_n, const double* u_nm1, double* u_np1, const double* src, double src_sign,
             int* iters_out, int* refs_out, double* resid_out, cudaStream_t s) {

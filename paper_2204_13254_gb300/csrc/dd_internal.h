@@ -322,6 +322,8 @@ struct DevPtrs {
     double* K64 = nullptr;           // K~cc^-1, n_corner x ldc
     float* K32 = nullptr;
     double* Pinv = nullptr;          // [n_sub+1][NB*NB] pivot-block inverses while factoring
+    uint16_t* oz_slices = nullptr;   // DD_FACTOR_TENSOR: BF16 slices of one pivot block's panels
+    int32_t* oz_exps = nullptr;      // and their row / column exponents
     double* dinv = nullptr;          // [n_lambda] inverse Jacobi diagonal
     // particles (dd_set_beam): state, per-tet geometry and faces
     double* px = nullptr;            // [n_p*3] positions
@@ -622,6 +624,10 @@ size_t sym_smem_bytes(const dd_handle* h);
 // Packed kinds in use: the recovery reads the packed tiles only for an ensemble (its I x [Gamma|c]
 // rectangle has no symmetric twin, so one problem gains almost nothing; an ensemble shares the reads).
 bool sym_active(const dd_handle* h, int mode);
+// ozaki.cu
+size_t oz_slice_elems(int nm, int nmax);
+int launch_oz_update(const MatDesc* mats, double* M, int nm, int nmax, int k0, uint16_t* slices, int32_t* exps,
+                     int32_t* err, void* stream);
 // tensor.cu
 void build_tc(dd_handle* h);
 int launch_tc_pack(const dd_handle* h, void* stream);

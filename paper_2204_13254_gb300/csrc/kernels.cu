@@ -1099,9 +1099,14 @@ int launch_sweep(const dd_handle* h, bool coarse, int k0, void* stream) {
     const int nmax = coarse ? (int)h->corner_dof.size() : h->max_ns;
     double* Pinv = coarse ? h->d.Pinv + (size_t)h->n_sub * kNB * kNB : h->d.Pinv;
     k_sweep_pivot<<<nm, kThreads, 0, S(stream)>>>(mats, M, k0, Pinv, h->d.status);
-    const int tiles = (nmax + 63) / 64;
-    dim3 grid(tiles, tiles, nm);
-    k_sweep_update<<<grid, kThreads, 0, S(stream)>>>(mats, M, k0);
+    if (h->prm.factor_mode == DD_FACTOR_TENSOR) {
+        const int rc = launch_oz_update(mats, M, nm, nmax, k0, h->d.oz_slices, h->d.oz_exps, &h->d.sc->wait_err, stream);
+        if (rc) return rc;
+    } else {
+        const int tiles = (nmax + 63) / 64;
+        dim3 grid(tiles, tiles, nm);
+        k_sweep_update<<<grid, kThreads, 0, S(stream)>>>(mats, M, k0);
+    }
     k_sweep_colpanel<<<nm, kThreads, 0, S(stream)>>>(mats, M, k0, Pinv);
     return (int)cudaGetLastError();
 }

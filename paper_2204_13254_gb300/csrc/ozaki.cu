@@ -1,0 +1,266 @@
+// FP64-accurate trailing update of the elimination on the tensor cores (sm_103a).
+//
+// The exchange sweep's trailing update C[i][j] += A[i][:] B[:][j] (A the pivot
+// block's column panel, B its row panel already multiplied by -P^-1, K = 32) is
+// formed from BF16 slices on tcgen05 instead of FP64 FMAs (the Ozaki splitting
+// of a product into exact low-precision products):
+//  * each row i of A is scaled by a power of two 2^-e_i so that |A_ik| 2^-e_i < 1,
+//    each column j of B by 2^-f_j likewise;
+//  * the scaled values are cut into seven slices of 8 bits: r_0 = A 2^-e, then
+//    a_p = rint(r_p 2^8), r_{p+1} = r_p 2^8 - a_p, so that
+//    A 2^-e = sum_p 2^-8(p+1) a_p with integer slices |a_0| <= 256, |a_p| <= 128
+//    (exact in BF16), and the same for B;
+//  * for every weight class d = p + q <= 6 the products a_p b_q are summed over
+//    K = 32 and over the (d + 1) slice pairs of the class in one FP32
+//    accumulator in tensor memory: every partial sum is an integer below 2^24,
+//    so the accumulation is exact;
+//  * the classes are combined in FP64 (Horner in 2^-8) and scaled back:
+//    C_ij += 2^(e_i + f_j - 16) sum_d 2^-8d D_d[i][j].
+// Dropping the classes d >= 7 leaves an error below 2^-55 of |A_i||B_j| per
+// term, i.e. FP64 accuracy.  The FP64 work per matrix element and pivot block
+// falls from 32 FMAs to 7 Horner steps; the tensor cores do 28 x 2 MMAs
+// (M = 128 rows, N = 32 columns, K = 16) per 128 x 32 tile.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include "dd_internal.h"
+#include "tcgen05.cuh"
+
+namespace {
+
+constexpr int kOzS = 7;                      // slices per operand (8 bits each)
+constexpr int kOzRows = 128;                 // rows of a tile (MMA M)
+constexpr int kOzCols = 32;                  // columns of a tile (MMA N)
+constexpr int kOzK = kNB;                    // pivot block width (MMA K = 2 x 16)
+constexpr uint32_t kOzAPiece = kOzRows * kOzK * 2;   // 8 KB: one slice of a 128-row block
+constexpr uint32_t kOzBPiece = kOzCols * kOzK * 2;   // 2 KB: one slice of a 32-column block
+constexpr uint32_t kOzABytes = kOzS * kOzAPiece;     // 56 KB
+constexpr uint32_t kOzBBytes = kOzS * kOzBPiece;     // 14 KB
+// dynamic shared memory per CTA: what the tile needs, padded so that at most two
+// CTAs share an SM (two 256-column tensor-memory allocations fill its 512 columns)
+constexpr size_t kOzSmemUsed = kOzABytes + kOzBBytes + 4 * sizeof(uint64_t) + 16;
+constexpr size_t kOzSmem = kOzSmemUsed > 100 * 1024 ? kOzSmemUsed : 100 * 1024;
+constexpr unsigned kOzPolls = 1u << 22;
+static_assert(kOzK == 32, "the slice layout assumes a 32-wide pivot block");
+
+inline cudaStream_t S(void* s) { return (cudaStream_t)s; }
+
+// Exponent e with |x| < 2^e for the largest |x| (0 for an all-zero vector).
+__device__ __forceinline__ int scale_exp(double maxabs) {
+    if (!(maxabs > 0.0)) return 0;
+    int e;
+    frexp(maxabs, &e);   // maxabs = f 2^e, f in [0.5, 1)
+    return e;
+}
+
+// The seven 8-bit slices of r = x 2^-e (|r| < 1) as BF16 bits.
+__device__ __forceinline__ void cut(double x, int e, uint16_t* out) {
+    double r = ldexp(x, -e);
+#pragma unroll
+    for (int p = 0; p < kOzS; ++p) {
+        const double t = r * 256.0;
+        const double a = rint(t);
+        r = t - a;
+        out[p] = __bfloat16_as_ushort(__double2bfloat16(a));
+    }
+}
+
+// Column panel A = M[i][k0 .. k0+nb) of every matrix: one CTA per (128-row block,
+// matrix), one thread per row.  Slices in the K-major core-matrix layout of the
+// MMA's A operand (K = 32), row exponents e_i.
+__global__ void __launch_bounds__(kOzRows) k_oz_split_a(const MatDesc* __restrict__ mats, const double* __restrict__ M,
+                                                        int k0, int nblk, uint16_t* __restrict__ As,
+                                                        int32_t* __restrict__ ea, int nmax) {
+    const int m = blockIdx.y, rb = blockIdx.x;
+    const MatDesc md = mats[m];
+    if (k0 >= md.nr || rb * kOzRows >= md.ns) return;
+    const int nb = min(kOzK, md.nr - k0);
+    const int r = threadIdx.x, i = rb * kOzRows + r;
+    double v[kOzK];
+    double mx = 0.0;
+#pragma unroll
+    for (int k = 0; k < kOzK; ++k) {
+        v[k] = (i < md.ns && k < nb) ? M[md.moff + (int64_t)i * md.ld + k0 + k] : 0.0;
+        mx = fmax(mx, fabs(v[k]));
+    }
+    const int e = scale_exp(mx);
+    if (i < md.ns) ea[(int64_t)m * nmax + i] = e;
+    uint16_t* out = As + ((int64_t)m * nblk + rb) * (kOzABytes / 2);
+#pragma unroll
+    for (int k = 0; k < kOzK; ++k) {
+        uint16_t s[kOzS];
+        cut(v[k], e, s);
+        const uint32_t o = tc::kmajor_off(r, k, kOzK) / 2;
+#pragma unroll
+        for (int p = 0; p < kOzS; ++p) out[p * (kOzAPiece / 2) + o] = s[p];
+    }
+}
+
+// Row panel B = M[k0 .. k0+nb)[j] (already -P^-1 times the pivot rows): one CTA
+// per (32-column block, matrix), one thread per column; slices in the K-major
+// layout of the MMA's B operand (N = 32 columns, K = 32), column exponents f_j.
+__global__ void __launch_bounds__(kOzCols) k_oz_split_b(const MatDesc* __restrict__ mats, const double* __restrict__ M,
+                                                        int k0, int nblk, uint16_t* __restrict__ Bs,
+                                                        int32_t* __restrict__ fb, int nmax) {
+    const int m = blockIdx.y, cb = blockIdx.x;
+    const MatDesc md = mats[m];
+    if (k0 >= md.nr || cb * kOzCols >= md.ns) return;
+    const int nb = min(kOzK, md.nr - k0);
+    const int c = threadIdx.x, j = cb * kOzCols + c;
+    double v[kOzK];
+    double mx = 0.0;
+#pragma unroll
+    for (int k = 0; k < kOzK; ++k) {
+        v[k] = (j < md.ns && k < nb) ? M[md.moff + (int64_t)(k0 + k) * md.ld + j] : 0.0;
+        mx = fmax(mx, fabs(v[k]));
+    }
+    const int f = scale_exp(mx);
+    if (j < md.ns) fb[(int64_t)m * nmax + j] = f;
+    uint16_t* out = Bs + ((int64_t)m * nblk + cb) * (kOzBBytes / 2);
+#pragma unroll
+    for (int k = 0; k < kOzK; ++k) {
+        uint16_t s[kOzS];
+        cut(v[k], f, s);
+        const uint32_t o = tc::kmajor_off(c, k, kOzK) / 2;
+#pragma unroll
+        for (int p = 0; p < kOzS; ++p) out[p * (kOzBPiece / 2) + o] = s[p];
+    }
+}
+
+__device__ __forceinline__ bool oz_wait(uint64_t* bar, uint32_t parity) {
+    for (unsigned k = 0; k < kOzPolls; ++k) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(tc::smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// One 128 x 32 tile of the trailing update of one matrix: bulk copies of its
+// A and B slices, 28 slice products x 2 K-steps into seven class accumulators
+// (224 tensor-memory columns), FP64 combination and C += in the epilogue (one
+// thread per row; the pivot rows and columns are left alone).
+__global__ void __launch_bounds__(128) k_oz_update(const MatDesc* __restrict__ mats, double* __restrict__ M, int k0,
+                                                   int nrb, int ncb, const uint16_t* __restrict__ As,
+                                                   const uint16_t* __restrict__ Bs, const int32_t* __restrict__ ea,
+                                                   const int32_t* __restrict__ fb, int nmax, int32_t* __restrict__ err) {
+    const int m = blockIdx.z, rb = blockIdx.y, cb = blockIdx.x;
+    const MatDesc md = mats[m];
+    if (k0 >= md.nr || rb * kOzRows >= md.ns || cb * kOzCols >= md.ns) return;
+    const int nb = min(kOzK, md.nr - k0);
+    extern __shared__ __align__(128) unsigned char sm[];
+    unsigned char* sA = sm;
+    unsigned char* sB = sm + kOzABytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kOzBBytes);   // [0] loads, [1] MMAs
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 4);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_addr(&bars[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_addr(&bars[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_addr(&bars[0])),
+                     "r"(kOzABytes + kOzBBytes)
+                     : "memory");
+        const uint16_t* ga = As + ((int64_t)m * nrb + rb) * (kOzABytes / 2);
+        const uint16_t* gb = Bs + ((int64_t)m * ncb + cb) * (kOzBBytes / 2);
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                tc::smem_addr(sA)),
+            "l"(ga), "r"(kOzABytes), "r"(tc::smem_addr(&bars[0]))
+            : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                tc::smem_addr(sB)),
+            "l"(gb), "r"(kOzBBytes), "r"(tc::smem_addr(&bars[0]))
+            : "memory");
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, 256);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    int ok = 1;
+    if (tid == 0) {
+        ok = oz_wait(&bars[0], 0u) ? 1 : 0;
+        if (ok) {
+            tc::fence_after_sync();
+            const uint32_t idesc = tc::idesc_bf16_f32(kOzRows, kOzCols);
+            const uint32_t a0 = tc::smem_addr(sA), b0 = tc::smem_addr(sB);
+            for (int d = 0; d < kOzS; ++d) {
+                bool first = true;
+                for (int p = 0; p <= d; ++p) {
+                    const int q = d - p;
+                    for (int ks = 0; ks < kOzK / 16; ++ks) {
+                        const uint64_t ad = tc::smem_desc(a0 + p * kOzAPiece + ks * 256, 128, (kOzK / 8) * 128);
+                        const uint64_t bd = tc::smem_desc(b0 + q * kOzBPiece + ks * 256, 128, (kOzK / 8) * 128);
+                        tc::mma_bf16(tmem + d * kOzCols, ad, bd, idesc, first ? 0u : 1u);
+                        first = false;
+                    }
+                }
+            }
+        }
+        tc::mma_commit(&bars[1]);   // arrives once the MMAs issued above (if any) have completed
+        if (!ok) oz_wait(&bars[0], 0u);   // copies still in flight land before the CTA ends (bounded)
+    }
+    const bool done = oz_wait(&bars[1], 0u);
+    tc::fence_after_sync();
+    const int good = __syncthreads_and(done && ok);
+    if (good) {
+        const int r = 32 * warp + lane;
+        const int i = rb * kOzRows + r;
+        const bool row_ok = i < md.ns && (i < k0 || i >= k0 + nb);
+        const int e = row_ok ? ea[(int64_t)m * nmax + i] : 0;
+        double* crow = M + md.moff + (int64_t)i * md.ld;
+#pragma unroll
+        for (int h = 0; h < kOzCols / 16; ++h) {
+            float D[kOzS][16];
+#pragma unroll
+            for (int d = 0; d < kOzS; ++d)
+                tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + d * kOzCols + h * 16, D[d]);
+            if (!row_ok) continue;
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                const int j = cb * kOzCols + h * 16 + c;
+                if (j >= md.ns || (j >= k0 && j < k0 + nb)) continue;
+                double v = (double)D[kOzS - 1][c];
+#pragma unroll
+                for (int d = kOzS - 2; d >= 0; --d) v = fma(v, 0.00390625, (double)D[d][c]);
+                crow[j] += ldexp(v, e + fb[(int64_t)m * nmax + j] - 16);
+            }
+        }
+    } else if (tid == 0) {
+        atomicExch(err, 1);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_free(tmem, 256);
+}
+
+}  // namespace
+
+// Workspace of the tensor-core update: slices and exponents of one pivot block.
+size_t oz_slice_elems(int nm, int nmax) {
+    const size_t nrb = (size_t)(nmax + kOzRows - 1) / kOzRows, ncb = (size_t)(nmax + kOzCols - 1) / kOzCols;
+    return (size_t)nm * (nrb * (kOzABytes / 2) + ncb * (kOzBBytes / 2));
+}
+
+int launch_oz_update(const MatDesc* mats, double* M, int nm, int nmax, int k0, uint16_t* slices, int32_t* exps,
+                     int32_t* err, void* stream) {
+    const int nrb = (nmax + kOzRows - 1) / kOzRows, ncb = (nmax + kOzCols - 1) / kOzCols;
+    uint16_t* As = slices;
+    uint16_t* Bs = slices + (size_t)nm * nrb * (kOzABytes / 2);
+    int32_t* ea = exps;
+    int32_t* fb = exps + (size_t)nm * nmax;
+    k_oz_split_a<<<dim3((unsigned)nrb, (unsigned)nm), kOzRows, 0, S(stream)>>>(mats, M, k0, nrb, As, ea, nmax);
+    k_oz_split_b<<<dim3((unsigned)ncb, (unsigned)nm), kOzCols, 0, S(stream)>>>(mats, M, k0, ncb, Bs, fb, nmax);
+    cudaError_t e = cudaFuncSetAttribute(k_oz_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem);
+    if (e != cudaSuccess) return (int)e;
+    k_oz_update<<<dim3((unsigned)ncb, (unsigned)nrb, (unsigned)nm), 128, kOzSmem, S(stream)>>>(
+        mats, M, k0, nrb, ncb, As, Bs, ea, fb, nmax, err);
+    return (int)cudaGetLastError();
+}

@@ -21,6 +21,7 @@ DD_FP64, DD_MIXED = 0, 1
 DD_SOLVER_SCHUR_CG, DD_SOLVER_COUPLED_GMRES = 0, 1
 DD_MAX_RESTART = 32
 DD_SCHEME_DP1, DD_SCHEME_DP2 = 0, 1
+DD_FACTOR_FP64, DD_FACTOR_TENSOR = 0, 1
 
 SYMBOLS = ["dd_setup", "dd_set_params", "dd_get_sizes", "dd_get_maps", "dd_set_probes", "dd_bind_workspace",
            "dd_factor", "dd_step", "dd_schur_apply", "dd_schur_apply_static", "dd_coupled_apply", "dd_dp2_apply",
@@ -42,7 +43,7 @@ class dd_params(C.Structure):
     _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("max_it", C.c_int), ("precond", C.c_int),
                 ("warm_start", C.c_int), ("refine_tol", C.c_double), ("max_refine", C.c_int), ("chunk", C.c_int),
                 ("use_graph", C.c_int), ("solver", C.c_int), ("restart", C.c_int), ("sym_fp32", C.c_int),
-                ("scheme", C.c_int), ("robin_alpha", C.c_double), ("members", C.c_int)]
+                ("scheme", C.c_int), ("robin_alpha", C.c_double), ("members", C.c_int), ("factor_mode", C.c_int)]
 
 
 class dd_sizes(C.Structure):
@@ -154,9 +155,9 @@ def _stream(stream=None):
 
 def make_params(precision=DD_FP64, tol=1e-12, max_it=500, precond=1, warm_start=1, refine_tol=1e-12, max_refine=4,
                 chunk=8, use_graph=0, solver=DD_SOLVER_SCHUR_CG, restart=20, sym_fp32=1, scheme=DD_SCHEME_DP1,
-                robin_alpha=0.0, members=1):
+                robin_alpha=0.0, members=1, factor_mode=DD_FACTOR_FP64):
     return dd_params(precision, tol, max_it, precond, warm_start, refine_tol, max_refine, chunk, use_graph, solver,
-                     restart, sym_fp32, scheme, robin_alpha, members)
+                     restart, sym_fp32, scheme, robin_alpha, members, factor_mode)
 
 
 # ---- C-ABI-named wrappers ------------------------------------------------------
