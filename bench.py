@@ -647,8 +647,14 @@ def run_ours(args, rank, world, local):
     if not pic and world == 1:
         nu = int(fs.sizes.n_lambda + fs.sizes.n_corner)
         u = torch.randn(nu, dtype=torch.float64, device=dev, generator=torch.Generator(device=dev).manual_seed(5))
-        pf = D.make_params(precision=D.DD_FP64, tol=args.tol64, solver=D.DD_SOLVER_COUPLED_GMRES)
+        pf = D.make_params(precision=D.DD_FP64, tol=args.tol64, solver=D.DD_SOLVER_COUPLED_GMRES,
+                           factor_mode=D.DD_FACTOR_FP64)
         fs.set_params(pf)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fs.factor(dt)
+        torch.cuda.synchronize()
+        t_f64 = time.perf_counter() - t0
         ref_apply = fs.coupled_apply(u)
         fs.set_params(D.make_params(precision=D.DD_FP64, tol=args.tol64, solver=D.DD_SOLVER_COUPLED_GMRES,
                                     factor_mode=D.DD_FACTOR_TENSOR))
@@ -658,12 +664,12 @@ def run_ours(args, rank, world, local):
         torch.cuda.synchronize()
         t_tc = time.perf_counter() - t0
         got_apply = fs.coupled_apply(u)
-        tcf = {"factor_s_fp64_cuda_cores": t_factor, "factor_s_tensor_cores": t_tc,
-               "speedup": t_factor / t_tc,
+        tcf = {"factor_s_fp64_cuda_cores": t_f64, "factor_s_tensor_cores": t_tc,
+               "speedup": t_f64 / t_tc,
                "coupled_operator_rel_diff": float(torch.linalg.norm(got_apply - ref_apply) / torch.linalg.norm(ref_apply)),
                "method": "trailing updates from 7 x 7 BF16 slices (8 bits each, power-of-two row/column scaling), "
                          "weight classes summed exactly in FP32 tensor memory by tcgen05 MMAs, combined in FP64"}
-        fs.set_params(pf)   # (the runs below refactor with their own settings)
+        # (the runs below refactor with their own settings)
 
     # MFETI-DP2 (Sec. III-B): refactor with the Robin term, FP64 at the paper's tolerance and
     # the headline's mixed settings; last, so that the runs above keep the DP1 factorisation

@@ -167,7 +167,7 @@ typedef struct {
  *            PIC cycle, the adjoint and dd_schur_apply return DD_ERR_STATE.
  * factor_mode DD_FACTOR_FP64 (0): the elimination's trailing updates (rank-32
  *            GEMMs, Sec. III-C's one inverse per subdomain) on the FP64 CUDA
- *            cores; DD_FACTOR_TENSOR (1): the same updates on the tensor cores,
+ *            cores; DD_FACTOR_TENSOR (1, the default): the same updates on the tensor cores,
  *            FP64-accurate: every row of the column panel and every column of
  *            the row panel is scaled by a power of two and cut into seven 8-bit
  *            BF16 slices, the slice products of each weight class are summed
@@ -253,7 +253,8 @@ typedef struct {
  * matrices, multiplicities, local numbering, B_r / B_c, local CSR matrices.
  * part [n_tets] (host) gives the subdomain 0..n_sub-1 of every tet.
  * params may be NULL (defaults: FP64, tol 1e-12, max_it 500, Jacobi, warm
- * start, refine_tol 1e-12, max_refine 4, chunk 8, eager launches).  On success *out owns a new
+ * start, refine_tol 1e-12, max_refine 4, chunk 8, eager launches, tensor-core
+ * trailing updates).  On success *out owns a new
  * handle (free with dd_destroy).  Errors: DD_ERR_ARG, DD_ERR_MESH,
  * DD_ERR_PARTITION.  No GPU work is done. */
 int dd_setup(const dd_mesh* mesh, const int32_t* part, int32_t n_sub, const dd_params* params,

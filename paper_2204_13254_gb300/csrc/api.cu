@@ -51,7 +51,7 @@ dd_params default_params() {
     p.scheme = DD_SCHEME_DP1;
     p.robin_alpha = 0.0;
     p.members = 1;
-    p.factor_mode = DD_FACTOR_FP64;
+    p.factor_mode = DD_FACTOR_TENSOR;
     return p;
 }
 

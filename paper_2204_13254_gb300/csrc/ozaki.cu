@@ -14,11 +14,12 @@
 //    K = 32 and over the (d + 1) slice pairs of the class in one FP32
 //    accumulator in tensor memory: every partial sum is an integer below 2^24,
 //    so the accumulation is exact;
-//  * the classes are combined in FP64 (Horner in 2^-8) and scaled back:
+//  * the classes are combined exactly in 64-bit integers (two partial sums, each
+//    exact as a double) and scaled back with one FP64 FMA:
 //    C_ij += 2^(e_i + f_j - 16) sum_d 2^-8d D_d[i][j].
 // Dropping the classes d >= 7 leaves an error below 2^-55 of |A_i||B_j| per
 // term, i.e. FP64 accuracy.  The FP64 work per matrix element and pivot block
-// falls from 32 FMAs to 7 Horner steps; the tensor cores do 28 x 2 MMAs
+// falls from 32 FMAs to two conversions and two FMAs; the tensor cores do 28 x 2 MMAs
 // (M = 128 rows, N = 32 columns, K = 16) per 128 x 32 tile.
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -226,10 +227,20 @@ __global__ void __launch_bounds__(128) k_oz_update(const MatDesc* __restrict__ m
             for (int c = 0; c < 16; ++c) {
                 const int j = cb * kOzCols + h * 16 + c;
                 if (j >= md.ns || (j >= k0 && j < k0 + nb)) continue;
-                double v = (double)D[kOzS - 1][c];
-#pragma unroll
-                for (int d = kOzS - 2; d >= 0; --d) v = fma(v, 0.00390625, (double)D[d][c]);
-                crow[j] += ldexp(v, e + fb[(int64_t)m * nmax + j] - 16);
+                // The class sums are exact integers below 2^22: combine them in 64-bit
+                // integer arithmetic (no FP64 work), H = D0 2^16 + D1 2^8 + D2 and
+                // L = D3 2^24 + D4 2^16 + D5 2^8 + D6, both exact as doubles, so that
+                // sum_d D_d 2^-8d = H 2^-16 + L 2^-48 with one rounding.
+                const long long H = ((long long)__float2int_rn(D[0][c]) << 16) +
+                                    ((long long)__float2int_rn(D[1][c]) << 8) + (long long)__float2int_rn(D[2][c]);
+                const long long L = ((long long)__float2int_rn(D[3][c]) << 24) +
+                                    ((long long)__float2int_rn(D[4][c]) << 16) +
+                                    ((long long)__float2int_rn(D[5][c]) << 8) + (long long)__float2int_rn(D[6][c]);
+                const double v = fma((double)L, 0x1p-48, (double)H * 0x1p-16);
+                // 2^(e + f - 16) from its exponent bits when that is a normal double
+                const int x = e + fb[(int64_t)m * nmax + j] - 16;
+                if (x > -1023 && x < 1024) crow[j] = fma(v, __longlong_as_double((long long)(x + 1023) << 52), crow[j]);
+                else crow[j] += ldexp(v, x);
             }
         }
     } else if (tid == 0) {

@@ -155,7 +155,7 @@ def _stream(stream=None):
 
 def make_params(precision=DD_FP64, tol=1e-12, max_it=500, precond=1, warm_start=1, refine_tol=1e-12, max_refine=4,
                 chunk=8, use_graph=0, solver=DD_SOLVER_SCHUR_CG, restart=20, sym_fp32=1, scheme=DD_SCHEME_DP1,
-                robin_alpha=0.0, members=1, factor_mode=DD_FACTOR_FP64):
+                robin_alpha=0.0, members=1, factor_mode=DD_FACTOR_TENSOR):
     return dd_params(precision, tol, max_it, precond, warm_start, refine_tol, max_refine, chunk, use_graph, solver,
                      restart, sym_fp32, scheme, robin_alpha, members, factor_mode)
 
