@@ -521,8 +521,14 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
  * as 128 x 64 panels of three BF16 pieces (their sum is the FP64 value to about
  * 24 bits), to the x of 16 ensemble copies by tcgen05 MMAs accumulating in FP32
  * in tensor memory, six piece products per panel (results agree with the FP32
- * forms to FP32 rounding; cl, st and keep do not apply) (host int32[7] each, 0
- * for the other kinds; any pointer may be NULL). */
+ * forms to FP32 rounding; cl, st and keep do not apply), 5 (single problems)
+ * the persistent form: as many CTAs as the SMs hold, each streaming the
+ * tiles of a queue of whole subdomains through one ring of st[k] (2..10)
+ * tiles, the queues filled largest subdomain first to the least-loaded CTA,
+ * cl[k] (1, 2 or 4) groups of four consumer warps taking alternate tiles,
+ * helper warps staging x of the next subdomain and storing y of the last
+ * (with one group bitwise the results of form 1 with cl = 1) (host int32[7]
+ * each, 0 for the other kinds; any pointer may be NULL). */
 int dd_get_tiles(const dd_handle* h, int32_t* lpr, int32_t* rows);
 
 /* Bytes of one full launch of GEMV kind `kind` (numbering of dd_get_tiles) at
@@ -538,12 +544,15 @@ int dd_get_gemv_bytes(const dd_handle* h, int32_t kind, int32_t precision, doubl
 int dd_get_sym_config(const dd_handle* h, int32_t* cl, int32_t* st, int32_t* keep, int32_t* ws);
 
 /* Sets the packed-tile launch of GEMV kind `kind` (0, 3, 5 or 6) to cl CTAs per subdomain (1, 2, 4 or 8), a ring of st tiles (2..4),
- * keep stored subdomains in L2 (0..n_sub) and kernel form ws (0..4 as in
- * dd_get_sym_config; 4 only for an ensemble's kinds 0, 3 and 6), as
+ * keep stored subdomains in L2 (0..n_sub) and kernel form ws (0..5 as in
+ * dd_get_sym_config; 4 only for an ensemble's kinds 0, 3 and 6; 5 only for a
+ * single problem, with cl = consumer groups (1, 2 or 4) and st up to 10 a
+ * multiple of cl), as
  * dd_autotune would (its next run may change it again).
  * Results differ from another setting only in the order of FP32 sums.
  * DD_ERR_ARG for other kinds or values (or form 2 when its shared memory exceeds
- * a CTA's), DD_ERR_STATE before dd_bind_workspace or during a capture.
+ * a CTA's, or form 5 when cl of its CTAs do not fit one SM's shared memory; the
+ * setting is then unchanged), DD_ERR_STATE before dd_bind_workspace or during a capture.
  * Synchronises `stream`; drops captured step graphs. */
 int dd_set_sym_config(dd_handle* h, int32_t kind, int32_t cl, int32_t st, int32_t keep, int32_t ws, void* stream);
 

@@ -990,6 +990,11 @@ int dd_bind_workspace(dd_handle* h, void* dev, size_t bytes, void* stream) {
     const size_t need = dd_workspace_layout(h, false);
     if (bytes < need) return h->fail(DD_ERR_ARG, "workspace too small: need " + std::to_string(need) + " bytes");
     drop_graphs(h);
+    {
+        int dev_id = 0;
+        CK(h, (int)cudaGetDevice(&dev_id), "device");
+        CK(h, (int)cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, dev_id), "device attribute");
+    }
     h->ws = static_cast<char*>(dev);
     h->ws_bytes = bytes;
     dd_workspace_layout(h, true);
@@ -1869,9 +1874,11 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
             if (p >= 0 && p < 2 && (lpr == 8 || lpr == 16 || lpr == 32) && rows >= kMinRowsPerTask)
                 found[{p, m}] = TileCfg{lpr, rows};
             int keep = 0, ws = 0;
-            if (p == 2 && sym_active(h, m) && (lpr == 1 || lpr == 2 || lpr == 4 || lpr == 8) && rows >= 2 &&
-                rows <= kSymStages && (is >> keep >> ws) && keep >= 0 && keep <= h->n_sub && ws >= 0 &&
-                (ws <= 3 || (ws == 4 && tc_available(h, m))))
+            if (p == 2 && sym_active(h, m) && rows >= 2 && (is >> keep >> ws) && keep >= 0 && keep <= h->n_sub &&
+                ((ws <= 3 && (lpr == 1 || lpr == 2 || lpr == 4 || lpr == 8) && rows <= kSymStages) ||
+                 (ws == 4 && tc_available(h, m) && lpr == 1 && rows <= kSymStages) ||
+                 (ws == 5 && h->members <= 1 && (lpr == 1 || lpr == 2 || lpr == 4) && rows % lpr == 0 &&
+                  rows <= kSymStagesPs)))
                 found_cl[m] = SymCfg{lpr, rows, keep, ws};
         }
     }
@@ -1915,7 +1922,9 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
                     const bool form3 = h->members > 2 && sym_smem_bytes_nr(h, 2) <= 227 * 1024;
                     const int nsweep = 12 * (form3 ? 4 : (form2 ? 3 : 2));
                     const int ntc = tc_available(h, m) ? 1 : 0;   // the tensor-core form (one configuration)
-                    for (int cand = 0; cand < nsweep + ntc + (repeated ? 3 : 0) && !rc; ++cand) {
+                    // the persistent form (single problems): 1, 2 or 4 consumer groups, rings of 2 to 10 tiles
+                    const int nps = h->members <= 1 ? 15 : 0;
+                    for (int cand = 0; cand < nsweep + ntc + nps + (repeated ? 3 : 0) && !rc; ++cand) {
                         int cl, st, keep = 0, ws;
                         if (cand < nsweep) {
                             ws = cand / 12;
@@ -1925,18 +1934,24 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
                             ws = 4;
                             cl = 1;
                             st = 2;
+                        } else if (cand < nsweep + ntc + nps) {
+                            const int q = cand - nsweep - ntc;
+                            ws = 5;
+                            cl = 1 << (q / 5);
+                            st = 2 + 2 * (q % 5);
                         } else if (bcl.ws == 4) {
                             break;   // no L2-kept subset for the tensor-core form
                         } else {
                             cl = bcl.cl;
                             st = bcl.st;
                             ws = bcl.ws;
-                            keep = std::min(h->n_sub, (int)((cand - nsweep - ntc + 1) * 32.0e6 / std::max(1.0, per_sub)));
+                            keep = std::min(h->n_sub, (int)((cand - nsweep - ntc - nps + 1) * 32.0e6 / std::max(1.0, per_sub)));
                         }
                         h->sym_st[m] = st;
                         h->sym_keep[m] = keep;
                         h->sym_ws[m] = ws;
                         sym_ranges(h, m, cl);
+                        if (ws == 5 && h->sym_grid[m] < 1) continue;   // no room, or fewer slots than groups
                         rc = upload(h->d.sym_rng[m], h->sym_rng[m], s);
                         // one warm-up and eight timed launches: the forms are often within a few per cent
                         for (int it = 0; it < 9 && !rc; ++it) {
@@ -1950,6 +1965,11 @@ int dd_autotune(dd_handle* h, const char* cache_path, double* seconds, void* str
                         h->launches[ST_FACTOR] += 9;
                         h->total_launches += 9;
                         if (rc) break;
+                        if (wait_err_set(h, s)) {   // a bounded wait gave up: not a candidate
+                            rc = (int)cudaMemsetAsync(&h->d.sc->wait_err, 0, sizeof(int32_t), s);
+                            if (rc) break;
+                            continue;
+                        }
                         if (ms < best) {
                             best = ms;
                             bcl = SymCfg{cl, st, keep, ws};
@@ -2077,9 +2097,16 @@ int dd_set_sym_config(dd_handle* h, int32_t kind, int32_t cl, int32_t st, int32_
     if (!h) return DD_ERR_ARG;
     if (kind < 0 || kind >= GEMV_NMODES || !sym_active(h, kind))
         return h->fail(DD_ERR_ARG, "dd_set_sym_config: not a packed GEMV kind");
-    if (!(cl == 1 || cl == 2 || cl == 4 || cl == 8) || st < 2 || st > kSymStages || keep < 0 || keep > h->n_sub ||
-        ws < 0 || ws > 4)
-        return h->fail(DD_ERR_ARG, "dd_set_sym_config: cl in {1,2,4,8}, 2 <= st <= 4, 0 <= keep <= n_sub, ws in {0..4}");
+    if (ws == 5) {
+        if (!(cl == 1 || cl == 2 || cl == 4) || st < 2 || st % cl != 0 || st > kSymStagesPs || keep < 0 ||
+            keep > h->n_sub)
+            return h->fail(DD_ERR_ARG, "dd_set_sym_config: the persistent form takes cl (consumer groups) in {1,2,4}, "
+                                       "2 <= st <= 10 a multiple of cl, 0 <= keep <= n_sub");
+        if (h->members > 1) return h->fail(DD_ERR_ARG, "dd_set_sym_config: the persistent form serves single problems");
+    } else if (!(cl == 1 || cl == 2 || cl == 4 || cl == 8) || st < 2 || st > kSymStages || keep < 0 ||
+               keep > h->n_sub || ws < 0 || ws > 4) {
+        return h->fail(DD_ERR_ARG, "dd_set_sym_config: cl in {1,2,4,8}, 2 <= st <= 4, 0 <= keep <= n_sub, ws in {0..5}");
+    }
     if (ws == 4 && !tc_available(h, kind))
         return h->fail(DD_ERR_ARG, "dd_set_sym_config: the tensor-core form needs an ensemble and a local solve, "
                                    "recovery or coupled kind");
@@ -2089,10 +2116,19 @@ int dd_set_sym_config(dd_handle* h, int32_t kind, int32_t cl, int32_t st, int32_
     if (!h->bound) return h->fail(DD_ERR_STATE, "dd_set_sym_config before dd_bind_workspace");
     if (h->capturing) return h->fail(DD_ERR_STATE, "dd_set_sym_config during capture");
     cudaStream_t s = (cudaStream_t)stream;
+    const int32_t old_st = h->sym_st[kind], old_keep = h->sym_keep[kind], old_ws = h->sym_ws[kind], old_cl = h->sym_cl[kind];
     h->sym_st[kind] = st;
     h->sym_keep[kind] = keep;
     h->sym_ws[kind] = ws;
     sym_ranges(h, kind, cl);
+    if (ws == 5 && h->sym_grid[kind] < 1) {
+        h->sym_st[kind] = old_st;
+        h->sym_keep[kind] = old_keep;
+        h->sym_ws[kind] = old_ws;
+        sym_ranges(h, kind, old_cl);
+        return h->fail(DD_ERR_ARG, "dd_set_sym_config: the persistent form's ring and buffers need more shared "
+                                   "memory than one CTA can have");
+    }
     CK(h, upload(h->d.sym_rng[kind], h->sym_rng[kind], s), "upload ranges");
     CK(h, (int)cudaStreamSynchronize(s), "sync");
     drop_graphs(h);

@@ -46,6 +46,7 @@ constexpr int kSymT = 64;
 constexpr int kSymTile = kSymT * kSymT;   // floats of the largest tile (a ring slot)
 constexpr int kSymCLMax = 8;       // most CTAs per subdomain (one thread-block cluster)
 constexpr int kSymStages = 4;      // deepest TMA ring (tiles in flight per CTA)
+constexpr int kSymStagesPs = 10;   // deepest ring of the persistent packed form (one or two CTAs per SM)
 
 struct SymDesc {
     int64_t toff;     // float offset of the subdomain's first tile in the packed buffer
@@ -220,6 +221,7 @@ struct PcgScalars {
 constexpr int kMaxRestart = DD_MAX_RESTART;
 constexpr int kMaxMembers = 64;   // ensemble size limit
 constexpr int kSymRng = 5;        // ints per CTA in a packed GEMV work table
+constexpr int kTlW = 2;           // u32 words per tile-list entry (a << 16 | b << 3 | flags, float offset)
 #ifndef DD_GM_ELEMS
 #define DD_GM_ELEMS 4
 #endif
@@ -488,7 +490,10 @@ struct dd_handle {
     int32_t sym_keep[GEMV_NMODES] = {};                    // subdomains whose tiles are kept in L2 (evict_last)
     int32_t sym_ws[GEMV_NMODES] = {};                      // packed kernel form: 0 CTA-synchronous, 1 warp-specialised,
                                                            // 2 ensemble copies of a subdomain in one CTA (up to 4),
-                                                           // 3 ensemble copies in pairs
+                                                           // 3 ensemble copies in pairs, 4 tensor cores (ensembles),
+                                                           // 5 persistent queues of subdomains (sym_cl = CTAs per SM)
+    int32_t sym_grid[GEMV_NMODES] = {};                    // CTAs of the launch (sym_ranges)
+    int32_t n_sm = 0;                                      // multiprocessors of the bound device
     int32_t sym_max_tiles = 0;                     // largest tile count of one subdomain
     int64_t sym_ntiles = 0;                        // stored tiles in all (entries of sym_dir / 4)
     bool sym_ok = false;                           // the packed GEMV's shared memory fits one CTA

@@ -26,9 +26,12 @@ def need_gpu():
         pytest.skip("no CUDA device")
 
 
+@pytest.mark.parametrize("form", [None, 5])
 @pytest.mark.parametrize("use_graph", [0, 1])
 @pytest.mark.parametrize("solver", [D.DD_SOLVER_SCHUR_CG, D.DD_SOLVER_COUPLED_GMRES])
-def test_wait_timeout_reported_and_recovered(use_graph, solver):
+def test_wait_timeout_reported_and_recovered(use_graph, solver, form):
+    """form None: the default packed forms; 5: the persistent queues (a consumer
+    that gives up stops the producer and the stager warps too)."""
     need_gpu()
     n = 10
     w = W.cavity(4, 2, steps=n)
@@ -45,6 +48,9 @@ def test_wait_timeout_reported_and_recovered(use_graph, solver):
                                             use_graph=use_graph, sym_fp32=1)).bind()
     try:
         fs.factor(dt)
+        if form is not None:
+            for kind in ("local", "recover", "iface_rows", "coupled"):
+                D.dd_set_sym_config(fs.h, kind, 1, 4, 0, form)
         pat = torch.zeros(fs.n_dof, dtype=torch.float64, device="cuda")
         pat[torch.as_tensor(fs.dof_of_pairs(w.source_pairs), device="cuda")] = 1.0
         out = torch.empty_like(pat)

@@ -61,7 +61,7 @@ def test_graph_ragged_and_no_stats():
     assert np.array_equal(Fe, Fg)
 
 
-@pytest.mark.parametrize("ws", [0, 1])
+@pytest.mark.parametrize("ws", [0, 1, 5])
 def test_packed_forms_are_deterministic(ws):
     """Two marches of the same mixed-precision problem with every packed kind on one
     kernel form give bitwise equal fields (fixed summation order, no races), on a
@@ -75,7 +75,10 @@ def test_packed_forms_are_deterministic(ws):
                                             solver=D.DD_SOLVER_COUPLED_GMRES)).bind()
     fs.factor(dt)
     for kind in ("local", "recover", "iface_rows", "coupled"):
-        D.dd_set_sym_config(fs.h, kind, 2, 3, 0, ws)
+        # the persistent form: one consumer group where x and y of a whole subdomain are staged
+        # (local solve, recovery), two groups (a ring depth that is a multiple of 2) for the others
+        cl, st = ((1, 3) if kind in ("local", "recover") else (2, 4)) if ws == 5 else (2, 3)
+        D.dd_set_sym_config(fs.h, kind, cl, st, 0, ws)
     pat = torch.zeros(fs.n_dof, dtype=torch.float64, device="cuda")
     pat[torch.as_tensor(fs.dof_of_pairs(w.source_pairs), device="cuda")] = 1.0
     d2g = w.d2G(dt, 12)

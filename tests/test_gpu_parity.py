@@ -259,7 +259,7 @@ def test_packed_symmetric_fp32_tiles(solver):
     the same iteration counts, and the packed path deterministic -- for both
     kernel forms (CTA-synchronous, warp-specialised) over cluster sizes 1..8,
     ring depths 2..4 and L2-kept subdomain counts (clusters of 8 leave some CTAs
-    of these small subdomains without tiles)."""
+    of these small subdomains without tiles), and for the persistent queues."""
     need_gpu()
     nx, ny, nz = 10, 8, 8
     L = (1.2, 1.0, 1.0)
@@ -285,7 +285,8 @@ def test_packed_symmetric_fp32_tiles(solver):
     cases = [("dense", 0, None), ("packed", 1, None), ("packed", 1, None),
              ("ws 2x3 keep 2", 1, pin(2, 3, 2, 1)), ("ws 1x2", 1, pin(1, 2, 0, 1)),
              ("ws 8x4 keep 6", 1, pin(8, 4, 6, 1)), ("ws 8x4 keep 6", 1, pin(8, 4, 6, 1)),
-             ("sync 8x4 keep 3", 1, pin(8, 4, 3, 0))]
+             ("sync 8x4 keep 3", 1, pin(8, 4, 3, 0)), ("queues 1x6 keep 2", 1, pin(1, 6, 2, 5)),
+             ("queues 1x6 keep 2", 1, pin(1, 6, 2, 5)), ("queues 2x4", 1, pin(2, 4, 0, 5))]
     runs = {}
     for name, sym, hook in cases:
         prm = D.make_params(precision=D.DD_MIXED, tol=1e-5, refine_tol=1e-12, max_refine=6, solver=solver,
