@@ -37,10 +37,6 @@ constexpr uint32_t kOzAPiece = kOzRows * kOzK * 2;   // 8 KB: one slice of a 128
 constexpr uint32_t kOzBPiece = kOzCols * kOzK * 2;   // 2 KB: one slice of a 32-column block
 constexpr uint32_t kOzABytes = kOzS * kOzAPiece;     // 56 KB
 constexpr uint32_t kOzBBytes = kOzS * kOzBPiece;     // 14 KB
-// dynamic shared memory per CTA: what the tile needs, padded so that at most two
-// CTAs share an SM (two 256-column tensor-memory allocations fill its 512 columns)
-constexpr size_t kOzSmemUsed = kOzABytes + kOzBBytes + 4 * sizeof(uint64_t) + 16;
-constexpr size_t kOzSmem = kOzSmemUsed > 100 * 1024 ? kOzSmemUsed : 100 * 1024;
 constexpr unsigned kOzPolls = 1u << 22;
 static_assert(kOzK == 32, "the slice layout assumes a 32-wide pivot block");
 
@@ -141,110 +137,142 @@ __device__ __forceinline__ bool oz_wait(uint64_t* bar, uint32_t parity) {
     return false;
 }
 
-// One 128 x 32 tile of the trailing update of one matrix: bulk copies of its
-// A and B slices, 28 slice products x 2 K-steps into seven class accumulators
-// (224 tensor-memory columns), FP64 combination and C += in the epilogue (one
-// thread per row; the pivot rows and columns are left alone).
-__global__ void __launch_bounds__(128) k_oz_update(const MatDesc* __restrict__ mats, double* __restrict__ M, int k0,
-                                                   int nrb, int ncb, const uint16_t* __restrict__ As,
-                                                   const uint16_t* __restrict__ Bs, const int32_t* __restrict__ ea,
-                                                   const int32_t* __restrict__ fb, int nmax, int32_t* __restrict__ err) {
-    const int m = blockIdx.z, rb = blockIdx.y, cb = blockIdx.x;
+// One CTA per (128-row block, run of kOzCb 32-column blocks, matrix) of the
+// trailing update: the row block's A slices are copied once and serve every
+// column block of the run; the B slices come through two buffers, the next
+// column block's copy in flight while the current one is combined.  Per column
+// block one thread issues the 28 slice products x 2 K-steps into the seven
+// class accumulators (224 tensor-memory columns), then the 256 threads combine
+// them: warp w reads rows 32 (w mod 4) .. + 31 (its tensor-memory lane
+// quarter) and columns 16 (w / 4) .. + 15, and adds the exact FP64 update to C
+// (the pivot rows and columns are left alone).  Every wait is bounded; a CTA
+// whose wait gives up sets the error word, lets its copies land and frees its
+// tensor memory.
+constexpr int kOzCb = 8;   // column blocks per CTA
+constexpr int kOzThreads = 256;
+constexpr size_t kOzSmem = kOzABytes + 2 * kOzBBytes + 8 * sizeof(uint64_t) + 16;
+
+__device__ __forceinline__ void oz_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            tc::smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(tc::smem_addr(bar))
+        : "memory");
+}
+
+__global__ void __launch_bounds__(kOzThreads, 2) k_oz_update(const MatDesc* __restrict__ mats, double* __restrict__ M,
+                                                          int k0, int nrb, int ncb, const uint16_t* __restrict__ As,
+                                                          const uint16_t* __restrict__ Bs,
+                                                          const int32_t* __restrict__ ea,
+                                                          const int32_t* __restrict__ fb, int nmax,
+                                                          int32_t* __restrict__ err) {
+    const int m = blockIdx.z, rb = blockIdx.y, cb0 = blockIdx.x * kOzCb;
     const MatDesc md = mats[m];
-    if (k0 >= md.nr || rb * kOzRows >= md.ns || cb * kOzCols >= md.ns) return;
+    const int ncb_m = (md.ns + kOzCols - 1) / kOzCols;
+    if (k0 >= md.nr || rb * kOzRows >= md.ns || cb0 >= ncb_m) return;
+    const int nc = min(kOzCb, ncb_m - cb0);   // column blocks of this CTA
     const int nb = min(kOzK, md.nr - k0);
     extern __shared__ __align__(128) unsigned char sm[];
     unsigned char* sA = sm;
-    unsigned char* sB = sm + kOzABytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kOzBBytes);   // [0] loads, [1] MMAs
+    unsigned char* sB = sm + kOzABytes;   // [2][kOzBBytes]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + 2 * kOzBBytes);   // [0] A, [1..2] B buffers, [3] MMAs
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 4);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint16_t* gb = Bs + ((int64_t)m * ncb + cb0) * (kOzBBytes / 2);
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_addr(&bars[0])) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_addr(&bars[1])) : "memory");
+        for (int q = 0; q < 4; ++q)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_addr(&bars[q])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_addr(&bars[0])),
-                     "r"(kOzABytes + kOzBBytes)
-                     : "memory");
-        const uint16_t* ga = As + ((int64_t)m * nrb + rb) * (kOzABytes / 2);
-        const uint16_t* gb = Bs + ((int64_t)m * ncb + cb) * (kOzBBytes / 2);
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                tc::smem_addr(sA)),
-            "l"(ga), "r"(kOzABytes), "r"(tc::smem_addr(&bars[0]))
-            : "memory");
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                tc::smem_addr(sB)),
-            "l"(gb), "r"(kOzBBytes), "r"(tc::smem_addr(&bars[0]))
-            : "memory");
+        oz_copy(sA, As + ((int64_t)m * nrb + rb) * (kOzABytes / 2), kOzABytes, &bars[0]);
+        oz_copy(sB, gb, kOzBBytes, &bars[1]);
     }
     if (warp == 0) tc::tmem_alloc(tslot, 256);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
-    int ok = 1;
-    if (tid == 0) {
-        ok = oz_wait(&bars[0], 0u) ? 1 : 0;
-        if (ok) {
-            tc::fence_after_sync();
-            const uint32_t idesc = tc::idesc_bf16_f32(kOzRows, kOzCols);
-            const uint32_t a0 = tc::smem_addr(sA), b0 = tc::smem_addr(sB);
-            for (int d = 0; d < kOzS; ++d) {
-                bool first = true;
-                for (int p = 0; p <= d; ++p) {
-                    const int q = d - p;
-                    for (int ks = 0; ks < kOzK / 16; ++ks) {
-                        const uint64_t ad = tc::smem_desc(a0 + p * kOzAPiece + ks * 256, 128, (kOzK / 8) * 128);
-                        const uint64_t bd = tc::smem_desc(b0 + q * kOzBPiece + ks * 256, 128, (kOzK / 8) * 128);
-                        tc::mma_bf16(tmem + d * kOzCols, ad, bd, idesc, first ? 0u : 1u);
-                        first = false;
+    const uint32_t idesc = tc::idesc_bf16_f32(kOzRows, kOzCols);
+    const int r = 32 * (warp & 3) + lane, hcol = 16 * (warp >> 2);
+    const int i = rb * kOzRows + r;
+    const bool row_ok = i < md.ns && (i < k0 || i >= k0 + nb);
+    const int e = row_ok ? ea[(int64_t)m * nmax + i] : 0;
+    double* crow = M + md.moff + (int64_t)i * md.ld;
+    int issued_b = 1;   // B copies issued (thread 0)
+    bool good = true;
+    for (int c = 0; c < nc && good; ++c) {
+        const int buf = c & 1;
+        bool ok = true;   // thread 0: the copies of this column block arrived
+        if (tid == 0) {
+            ok = (c > 0 || oz_wait(&bars[0], 0u)) && oz_wait(&bars[1 + buf], (uint32_t)(c >> 1) & 1u);
+            if (ok) {
+                tc::fence_after_sync();
+                const uint32_t a0 = tc::smem_addr(sA), b0 = tc::smem_addr(sB + buf * kOzBBytes);
+                for (int d = 0; d < kOzS; ++d) {
+                    bool first = true;
+                    for (int p = 0; p <= d; ++p) {
+                        const int q = d - p;
+                        for (int ks = 0; ks < kOzK / 16; ++ks) {
+                            const uint64_t ad = tc::smem_desc(a0 + p * kOzAPiece + ks * 256, 128, (kOzK / 8) * 128);
+                            const uint64_t bd = tc::smem_desc(b0 + q * kOzBPiece + ks * 256, 128, (kOzK / 8) * 128);
+                            tc::mma_bf16(tmem + d * kOzCols, ad, bd, idesc, first ? 0u : 1u);
+                            first = false;
+                        }
                     }
                 }
             }
-        }
-        tc::mma_commit(&bars[1]);   // arrives once the MMAs issued above (if any) have completed
-        if (!ok) oz_wait(&bars[0], 0u);   // copies still in flight land before the CTA ends (bounded)
-    }
-    const bool done = oz_wait(&bars[1], 0u);
-    tc::fence_after_sync();
-    const int good = __syncthreads_and(done && ok);
-    if (good) {
-        const int r = 32 * warp + lane;
-        const int i = rb * kOzRows + r;
-        const bool row_ok = i < md.ns && (i < k0 || i >= k0 + nb);
-        const int e = row_ok ? ea[(int64_t)m * nmax + i] : 0;
-        double* crow = M + md.moff + (int64_t)i * md.ld;
-#pragma unroll
-        for (int h = 0; h < kOzCols / 16; ++h) {
-            float D[kOzS][16];
-#pragma unroll
-            for (int d = 0; d < kOzS; ++d)
-                tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + d * kOzCols + h * 16, D[d]);
-            if (!row_ok) continue;
-#pragma unroll
-            for (int c = 0; c < 16; ++c) {
-                const int j = cb * kOzCols + h * 16 + c;
-                if (j >= md.ns || (j >= k0 && j < k0 + nb)) continue;
-                // The class sums are exact integers below 2^22: combine them in 64-bit
-                // integer arithmetic (no FP64 work), H = D0 2^16 + D1 2^8 + D2 and
-                // L = D3 2^24 + D4 2^16 + D5 2^8 + D6, both exact as doubles, so that
-                // sum_d D_d 2^-8d = H 2^-16 + L 2^-48 with one rounding.
-                const long long H = ((long long)__float2int_rn(D[0][c]) << 16) +
-                                    ((long long)__float2int_rn(D[1][c]) << 8) + (long long)__float2int_rn(D[2][c]);
-                const long long L = ((long long)__float2int_rn(D[3][c]) << 24) +
-                                    ((long long)__float2int_rn(D[4][c]) << 16) +
-                                    ((long long)__float2int_rn(D[5][c]) << 8) + (long long)__float2int_rn(D[6][c]);
-                const double v = fma((double)L, 0x1p-48, (double)H * 0x1p-16);
-                // 2^(e + f - 16) from its exponent bits when that is a normal double
-                const int x = e + fb[(int64_t)m * nmax + j] - 16;
-                if (x > -1023 && x < 1024) crow[j] = fma(v, __longlong_as_double((long long)(x + 1023) << 52), crow[j]);
-                else crow[j] += ldexp(v, x);
+            tc::mma_commit(&bars[3]);   // arrives once the MMAs issued above (if any) have completed
+            // the other buffer's products (column block c - 1) completed before its combination
+            if (ok && c + 1 < nc) {
+                oz_copy(sB + (buf ^ 1) * kOzBBytes, gb + (int64_t)(c + 1) * (kOzBBytes / 2), kOzBBytes,
+                        &bars[1 + (buf ^ 1)]);
+                ++issued_b;
             }
         }
-    } else if (tid == 0) {
+        const bool done = oz_wait(&bars[3], (uint32_t)c & 1u);
+        tc::fence_after_sync();
+        good = __syncthreads_and(done && ok) != 0;
+        if (!good) break;
+        const int cb = cb0 + c;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {   // eight columns at a time (registers)
+            float D[kOzS][8];
+#pragma unroll
+            for (int d = 0; d < kOzS; ++d)
+                tc::tmem_ld8(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + d * kOzCols + hcol + 8 * half, D[d]);
+            if (row_ok) {
+#pragma unroll
+                for (int cc = 0; cc < 8; ++cc) {
+                    const int j = cb * kOzCols + hcol + 8 * half + cc;
+                    if (j >= md.ns || (j >= k0 && j < k0 + nb)) continue;
+                    // The class sums are exact integers below 2^22: combine them in 64-bit
+                    // integer arithmetic (no FP64 work), H = D0 2^16 + D1 2^8 + D2 and
+                    // L = D3 2^24 + D4 2^16 + D5 2^8 + D6, both exact as doubles, so that
+                    // sum_d D_d 2^-8d = H 2^-16 + L 2^-48 with one rounding.
+                    const long long H = ((long long)__float2int_rn(D[0][cc]) << 16) +
+                                        ((long long)__float2int_rn(D[1][cc]) << 8) + (long long)__float2int_rn(D[2][cc]);
+                    const long long L = ((long long)__float2int_rn(D[3][cc]) << 24) +
+                                        ((long long)__float2int_rn(D[4][cc]) << 16) +
+                                        ((long long)__float2int_rn(D[5][cc]) << 8) + (long long)__float2int_rn(D[6][cc]);
+                    const double v = fma((double)L, 0x1p-48, (double)H * 0x1p-16);
+                    // 2^(e + f - 16) from its exponent bits when that is a normal double
+                    const int x = e + fb[(int64_t)m * nmax + j] - 16;
+                    if (x > -1023 && x < 1024) crow[j] = fma(v, __longlong_as_double((long long)(x + 1023) << 52), crow[j]);
+                    else crow[j] += ldexp(v, x);
+                }
+            }
+        }
+        // every thread's tensor-memory reads complete before the next products overwrite the accumulators
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    }
+    if (!good && tid == 0) {
         atomicExch(err, 1);
+        // the copies issued land before the CTA ends (bounded): A, and the last one of each B buffer
+        oz_wait(&bars[0], 0u);
+        for (int q = issued_b > 2 ? issued_b - 2 : 0; q < issued_b; ++q) oz_wait(&bars[1 + (q & 1)], (uint32_t)(q >> 1) & 1u);
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -269,9 +297,13 @@ int launch_oz_update(const MatDesc* mats, double* M, int nm, int nmax, int k0, u
     int32_t* fb = exps + (size_t)nm * nmax;
     k_oz_split_a<<<dim3((unsigned)nrb, (unsigned)nm), kOzRows, 0, S(stream)>>>(mats, M, k0, nrb, As, ea, nmax);
     k_oz_split_b<<<dim3((unsigned)ncb, (unsigned)nm), kOzCols, 0, S(stream)>>>(mats, M, k0, ncb, Bs, fb, nmax);
+    // (84 KB of shared memory: at most two CTAs per SM, whose two 256-column tensor-memory allocations
+    // fill its 512 columns)
+    static_assert(3 * (kOzSmem + 1024) > 228 * 1024 && 2 * (kOzSmem + 1024) <= 228 * 1024, "two CTAs per SM");
     cudaError_t e = cudaFuncSetAttribute(k_oz_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem);
     if (e != cudaSuccess) return (int)e;
-    k_oz_update<<<dim3((unsigned)ncb, (unsigned)nrb, (unsigned)nm), 128, kOzSmem, S(stream)>>>(
+    const int nchunk = (ncb + kOzCb - 1) / kOzCb;
+    k_oz_update<<<dim3((unsigned)nchunk, (unsigned)nrb, (unsigned)nm), kOzThreads, kOzSmem, S(stream)>>>(
         mats, M, k0, nrb, ncb, As, Bs, ea, fb, nmax, err);
     return (int)cudaGetLastError();
 }
