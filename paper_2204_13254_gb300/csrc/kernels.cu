@@ -129,14 +129,17 @@ __global__ void k_dense_assemble(int64_t n_local, const int64_t* __restrict__ ro
     }
 }
 
-// Exchange-sweep step on pivot block p = [k0, k0+nb), part 1 (one CTA per matrix):
-//   P^-1 by an in-shared-memory Gauss-Jordan sweep (SPD: no pivoting), stored to
-//   Pinv; row panel M[p, j] <- -P^-1 M[p, j] for every j outside p.
+// Exchange-sweep step on pivot block p = [k0, k0+nb), part 1 (CTA (matrix, y):
+// columns kThreads y .. kThreads (y + 1) - 1 of the matrix, one per thread):
+//   P^-1 by an in-shared-memory Gauss-Jordan sweep (SPD: no pivoting; every CTA
+//   of the matrix forms it, CTA y = 0 stores it to Pinv); row panel
+//   M[p, j] <- -P^-1 M[p, j] for every j of the CTA outside p.  No CTA writes
+//   the pivot block itself (part 3 does), so every CTA reads the same P.
 __global__ void __launch_bounds__(kThreads) k_sweep_pivot(const MatDesc* __restrict__ mats, double* __restrict__ M,
                                                           int k0, double* __restrict__ Pinv,
                                                           int32_t* __restrict__ status) {
     const MatDesc md = mats[blockIdx.x];
-    if (k0 >= md.nr) return;
+    if (k0 >= md.nr || (int)blockIdx.y * kThreads >= md.ns) return;
     const int nb = min(kNB, md.nr - k0);
     __shared__ double P[kNB][kNB + 1];
     double* A = M + md.moff;
@@ -168,11 +171,14 @@ __global__ void __launch_bounds__(kThreads) k_sweep_pivot(const MatDesc* __restr
         for (int t = threadIdx.x; t < nb * nb; t += blockDim.x, ++cnt) P[t / nb][t % nb] = nv[cnt];
         __syncthreads();
     }
-    double* Pout = Pinv + (size_t)blockIdx.x * kNB * kNB;
-    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) Pout[t] = P[t / nb][t % nb];
+    if (blockIdx.y == 0) {
+        double* Pout = Pinv + (size_t)blockIdx.x * kNB * kNB;
+        for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) Pout[t] = P[t / nb][t % nb];
+    }
     // row panel, one column per thread
-    for (int j = threadIdx.x; j < md.ns; j += blockDim.x) {
-        if (j >= k0 && j < k0 + nb) continue;
+    {
+        const int j = (int)blockIdx.y * kThreads + threadIdx.x;
+        if (j >= md.ns || (j >= k0 && j < k0 + nb)) return;
         double col[kNB];
 #pragma unroll
         for (int l = 0; l < kNB; ++l) col[l] = l < nb ? A[(int64_t)(k0 + l) * md.ld + j] : 0.0;
@@ -234,11 +240,14 @@ __global__ void __launch_bounds__(kThreads) k_sweep_update(const MatDesc* __rest
     }
 }
 
-// Part 3: column panel M[i][p] <- M[i][p] P^-1 for i outside p, and M[p][p] <- P^-1.
+// Part 3: column panel M[i][p] <- M[i][p] P^-1 for i outside p, and M[p][p] <- P^-1
+// (CTA (matrix, y): kColRows rows).
+constexpr int kColRows = 64;
 __global__ void __launch_bounds__(kThreads) k_sweep_colpanel(const MatDesc* __restrict__ mats, double* __restrict__ M,
                                                              int k0, const double* __restrict__ Pinv) {
     const MatDesc md = mats[blockIdx.x];
-    if (k0 >= md.nr) return;
+    const int r0 = (int)blockIdx.y * kColRows;   // this CTA's rows r0 .. r0 + kColRows - 1, a warp per row
+    if (k0 >= md.nr || r0 >= md.ns) return;
     const int nb = min(kNB, md.nr - k0);
     __shared__ double P[kNB][kNB + 1];
     const double* Pin = Pinv + (size_t)blockIdx.x * kNB * kNB;
@@ -246,7 +255,8 @@ __global__ void __launch_bounds__(kThreads) k_sweep_colpanel(const MatDesc* __re
     __syncthreads();
     double* A = M + md.moff;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int i = warp; i < md.ns; i += nw) {
+    const int r1 = min(md.ns, r0 + kColRows);
+    for (int i = r0 + warp; i < r1; i += nw) {
         double* row = A + (int64_t)i * md.ld + k0;
         if (i >= k0 && i < k0 + nb) {
             if (lane < nb) row[lane] = P[i - k0][lane];
@@ -1098,7 +1108,10 @@ int launch_sweep(const dd_handle* h, bool coarse, int k0, void* stream) {
     const int nm = coarse ? 1 : h->n_sub_real;
     const int nmax = coarse ? (int)h->corner_dof.size() : h->max_ns;
     double* Pinv = coarse ? h->d.Pinv + (size_t)h->n_sub * kNB * kNB : h->d.Pinv;
-    k_sweep_pivot<<<nm, kThreads, 0, S(stream)>>>(mats, M, k0, Pinv, h->d.status);
+    // chunks of columns (row panel) and of rows (column panel): the coarse matrix alone has thousands
+    // of rows, which one CTA per matrix would serialise
+    const unsigned gp = (unsigned)((nmax + kThreads - 1) / kThreads), gc = (unsigned)((nmax + kColRows - 1) / kColRows);
+    k_sweep_pivot<<<dim3((unsigned)nm, gp), kThreads, 0, S(stream)>>>(mats, M, k0, Pinv, h->d.status);
     if (h->prm.factor_mode == DD_FACTOR_TENSOR) {
         const int rc = launch_oz_update(mats, M, nm, nmax, k0, h->d.oz_slices, h->d.oz_exps, &h->d.sc->wait_err, stream);
         if (rc) return rc;
@@ -1107,7 +1120,7 @@ int launch_sweep(const dd_handle* h, bool coarse, int k0, void* stream) {
         dim3 grid(tiles, tiles, nm);
         k_sweep_update<<<grid, kThreads, 0, S(stream)>>>(mats, M, k0);
     }
-    k_sweep_colpanel<<<nm, kThreads, 0, S(stream)>>>(mats, M, k0, Pinv);
+    k_sweep_colpanel<<<dim3((unsigned)nm, gc), kThreads, 0, S(stream)>>>(mats, M, k0, Pinv);
     return (int)cudaGetLastError();
 }
 
