@@ -358,24 +358,41 @@ __device__ __forceinline__ void local_rows(const MatDesc& md, const int64_t* __r
     const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     // this CTA's share of the rows: part blockIdx.y of gridDim.y
     const int ra = (int)((int64_t)md.ns * blockIdx.y / gridDim.y), rb = (int)((int64_t)md.ns * (blockIdx.y + 1) / gridDim.y);
-    for (int r0 = ra + warp * 8; r0 < rb; r0 += nwarp * 8) {
-        const int r = r0 + ((threadIdx.x & 31) >> 2);
-        const int64_t i = md.voff + r;
-        double s = 0.0;
-        if (r < rb) {
-            const int64_t k1 = row_ptr[i + 1];
-            int64_t k = row_ptr[i] + lane4;
-            for (; k + 12 < k1; k += 16) {
-                const double a0 = __ldcs(A + k), a1 = __ldcs(A + k + 4), a2 = __ldcs(A + k + 8), a3 = __ldcs(A + k + 12);
-                const int32_t c0 = __ldcs(col_loc + k), c1 = __ldcs(col_loc + k + 4), c2 = __ldcs(col_loc + k + 8),
-                              c3 = __ldcs(col_loc + k + 12);
-                s += a0 * vl[c0] + a1 * vl[c1] + a2 * vl[c2] + a3 * vl[c3];
-            }
-            for (; k < k1; k += 4) s += __ldcs(A + k) * vl[__ldcs(col_loc + k)];
+    // two groups of 8 rows per warp and pass (r0 and r0 + 8 nwarp): both groups' row bounds, then
+    // their first 16 entries' loads, are issued before any is used
+    for (int r0 = ra + warp * 8; r0 < rb; r0 += 2 * nwarp * 8) {
+        int64_t i[2], k[2], k1[2];
+        double s[2];
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            const int r = r0 + g * nwarp * 8 + ((threadIdx.x & 31) >> 2);
+            i[g] = md.voff + r;
+            const bool on = r < rb;
+            k[g] = on ? row_ptr[i[g]] + lane4 : 0;
+            k1[g] = on ? row_ptr[i[g] + 1] : 0;
+            s[g] = 0.0;
         }
-        s += __shfl_xor_sync(0xffffffffu, s, 2, 4);
-        s += __shfl_xor_sync(0xffffffffu, s, 1, 4);
-        if (lane4 == 0 && r < rb) fn(i, s);
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            for (; k[g] + 12 < k1[g]; k[g] += 16) {
+                const int64_t q = k[g];
+                const double a0 = __ldcs(A + q), a1 = __ldcs(A + q + 4), a2 = __ldcs(A + q + 8), a3 = __ldcs(A + q + 12);
+                const int32_t c0 = __ldcs(col_loc + q), c1 = __ldcs(col_loc + q + 4), c2 = __ldcs(col_loc + q + 8),
+                              c3 = __ldcs(col_loc + q + 12);
+                s[g] += a0 * vl[c0] + a1 * vl[c1] + a2 * vl[c2] + a3 * vl[c3];
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < 2; ++g)
+            for (; k[g] < k1[g]; k[g] += 4) s[g] += __ldcs(A + k[g]) * vl[__ldcs(col_loc + k[g])];
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            double v = s[g];
+            v += __shfl_xor_sync(0xffffffffu, v, 2, 4);
+            v += __shfl_xor_sync(0xffffffffu, v, 1, 4);
+            const int r = r0 + g * nwarp * 8 + ((threadIdx.x & 31) >> 2);
+            if (lane4 == 0 && r < rb) fn(i[g], v);
+        }
     }
 }
 
@@ -808,17 +825,36 @@ __global__ void __launch_bounds__(kThreads) k_assemble_rhs(int64_t n_dof, const 
                                                            float* __restrict__ bf, PcgScalars* sc,
                                                            double* __restrict__ partials, int set_b) {
     double v[1] = {0.0};
-    for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < n_dof; d += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t c0 = copy_ptr[d], c1 = copy_ptr[d + 1];
-        double s = 0.0;
-        for (int64_t c = c0; c < c1; ++c) s += b[copy_slot[c]];
-        b[copy_slot[c0]] = s;                       // the first copy is the owner
-        if (bf) bf[copy_slot[c0]] = (float)s;
-        for (int64_t c = c0 + 1; c < c1; ++c) {
-            b[copy_slot[c]] = 0.0;
-            if (bf) bf[copy_slot[c]] = 0.0f;
+    // four dofs per thread and pass (d, d + stride, ...: the same order as one at a time), the index
+    // loads of all four, then their first copies, issued before the sums
+    constexpr int kU = 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t d0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d0 < n_dof; d0 += kU * stride) {
+        int64_t c0[kU], c1[kU], s0[kU];
+        double x0[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int64_t d = d0 + u * stride;
+            c0[u] = d < n_dof ? copy_ptr[d] : 0;
+            c1[u] = d < n_dof ? copy_ptr[d + 1] : 0;
         }
-        v[0] += s * s;
+#pragma unroll
+        for (int u = 0; u < kU; ++u) s0[u] = c1[u] > c0[u] ? copy_slot[c0[u]] : 0;
+#pragma unroll
+        for (int u = 0; u < kU; ++u) x0[u] = c1[u] > c0[u] ? b[s0[u]] : 0.0;
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            if (d0 + u * stride >= n_dof || c1[u] <= c0[u]) continue;
+            double s = 0.0 + x0[u];
+            for (int64_t c = c0[u] + 1; c < c1[u]; ++c) s += b[copy_slot[c]];
+            b[s0[u]] = s;                       // the first copy is the owner
+            if (bf) bf[s0[u]] = (float)s;
+            for (int64_t c = c0[u] + 1; c < c1[u]; ++c) {
+                b[copy_slot[c]] = 0.0;
+                if (bf) bf[copy_slot[c]] = 0.0f;
+            }
+            v[0] += s * s;
+        }
     }
     if (grid_sum<1>(v, partials, &sc->counter[3])) {
         if (set_b) sc->norm_b2 = v[0];
