@@ -14,7 +14,8 @@
 // depth st <= kSymStages, chosen by dd_autotune) share one subdomain by ranges of
 // tile rows (balanced on the host by bytes).  The tiles a mode needs are
 // listed once on the host (row order, per subdomain, with their storage
-// offsets); a CTA copies its run of that list to shared memory and stages only
+// offsets); a CTA copies its run of that list to shared memory (or reads it
+// from global memory where the copy would cost a CTA per SM) and stages only
 // the x entries its tile rows read, issuing the index loads of eight entries
 // before their value loads.  It streams its tiles through an st-deep ring of
 // shared-memory slots filled by cp.async.bulk (one copy per tile, completion on
@@ -35,6 +36,12 @@
 // are deterministic.  Every mbarrier wait is bounded: a wait that gives up sets
 // an error word, the CTA drains its outstanding copies (bounded again) and
 // still takes part in both cluster barriers, so no wait can hang the GPU.
+//
+// Forms (dd_autotune picks one per mode): the CTA-synchronous kernel above, a
+// warp-specialised one (producer warp, four consumer warps with their own
+// partial y), the ensemble forms (one CTA applying each tile to the x of 2 or 4
+// members), and persistent queues (whole subdomains balanced over the SMs'
+// CTAs, one ring per queue, helper warps staging x and storing y).
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
