@@ -130,7 +130,7 @@ __global__ void k_dense_assemble(int64_t n_local, const int64_t* __restrict__ ro
 }
 
 // Exchange-sweep step on pivot block p = [k0, k0+nb), part 1 (CTA (matrix, y):
-// columns kThreads y .. kThreads (y + 1) - 1 of the matrix, one per thread):
+// columns j = kThreads y + t + kThreads gridDim.y k, one per thread t and pass):
 //   P^-1 by an in-shared-memory Gauss-Jordan sweep (SPD: no pivoting; every CTA
 //   of the matrix forms it, CTA y = 0 stores it to Pinv); row panel
 //   M[p, j] <- -P^-1 M[p, j] for every j of the CTA outside p.  No CTA writes
@@ -175,10 +175,9 @@ __global__ void __launch_bounds__(kThreads) k_sweep_pivot(const MatDesc* __restr
         double* Pout = Pinv + (size_t)blockIdx.x * kNB * kNB;
         for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) Pout[t] = P[t / nb][t % nb];
     }
-    // row panel, one column per thread
-    {
-        const int j = (int)blockIdx.y * kThreads + threadIdx.x;
-        if (j >= md.ns || (j >= k0 && j < k0 + nb)) return;
+    // row panel, one column per thread and pass
+    for (int j = (int)blockIdx.y * kThreads + threadIdx.x; j < md.ns; j += (int)gridDim.y * kThreads) {
+        if (j >= k0 && j < k0 + nb) continue;
         double col[kNB];
 #pragma unroll
         for (int l = 0; l < kNB; ++l) col[l] = l < nb ? A[(int64_t)(k0 + l) * md.ld + j] : 0.0;
@@ -1144,9 +1143,11 @@ int launch_sweep(const dd_handle* h, bool coarse, int k0, void* stream) {
     const int nm = coarse ? 1 : h->n_sub_real;
     const int nmax = coarse ? (int)h->corner_dof.size() : h->max_ns;
     double* Pinv = coarse ? h->d.Pinv + (size_t)h->n_sub * kNB * kNB : h->d.Pinv;
-    // chunks of columns (row panel) and of rows (column panel): the coarse matrix alone has thousands
-    // of rows, which one CTA per matrix would serialise
-    const unsigned gp = (unsigned)((nmax + kThreads - 1) / kThreads), gc = (unsigned)((nmax + kColRows - 1) / kColRows);
+    // chunks of rows (column panel), and of columns (row panel) for the coarse matrix, whose
+    // thousands of rows one CTA per pivot block would serialise; the many local matrices keep one CTA
+    // each for the row panel (every chunk forms P^-1 again: measured slower there)
+    const unsigned gp = coarse ? (unsigned)((nmax + kThreads - 1) / kThreads) : 1u;
+    const unsigned gc = (unsigned)((nmax + kColRows - 1) / kColRows);
     k_sweep_pivot<<<dim3((unsigned)nm, gp), kThreads, 0, S(stream)>>>(mats, M, k0, Pinv, h->d.status);
     if (h->prm.factor_mode == DD_FACTOR_TENSOR) {
         const int rc = launch_oz_update(mats, M, nm, nmax, k0, h->d.oz_slices, h->d.oz_exps, &h->d.sc->wait_err, stream);

@@ -15,7 +15,7 @@
 //    accumulator in tensor memory: every partial sum is an integer below 2^24,
 //    so the accumulation is exact;
 //  * the classes are combined exactly in 64-bit integers (two partial sums, each
-//    exact as a double) and scaled back with one FP64 FMA:
+//    exact as a double, joined by one FMA) and scaled back with one FP64 FMA:
 //    C_ij += 2^(e_i + f_j - 16) sum_d 2^-8d D_d[i][j].
 // Dropping the classes d >= 7 leaves an error below 2^-55 of |A_i||B_j| per
 // term, i.e. FP64 accuracy.  The FP64 work per matrix element and pivot block
@@ -241,26 +241,36 @@ __global__ void __launch_bounds__(kOzThreads, 2) k_oz_update(const MatDesc* __re
 #pragma unroll
             for (int d = 0; d < kOzS; ++d)
                 tc::tmem_ld8(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + d * kOzCols + hcol + 8 * half, D[d]);
-            if (row_ok) {
+            if (!row_ok) continue;
+            const int jb = cb * kOzCols + hcol + 8 * half;
+            bool on[8];
+            double cv[8];
+            int fe[8];
 #pragma unroll
-                for (int cc = 0; cc < 8; ++cc) {
-                    const int j = cb * kOzCols + hcol + 8 * half + cc;
-                    if (j >= md.ns || (j >= k0 && j < k0 + nb)) continue;
-                    // The class sums are exact integers below 2^22: combine them in 64-bit
-                    // integer arithmetic (no FP64 work), H = D0 2^16 + D1 2^8 + D2 and
-                    // L = D3 2^24 + D4 2^16 + D5 2^8 + D6, both exact as doubles, so that
-                    // sum_d D_d 2^-8d = H 2^-16 + L 2^-48 with one rounding.
-                    const long long H = ((long long)__float2int_rn(D[0][cc]) << 16) +
-                                        ((long long)__float2int_rn(D[1][cc]) << 8) + (long long)__float2int_rn(D[2][cc]);
-                    const long long L = ((long long)__float2int_rn(D[3][cc]) << 24) +
-                                        ((long long)__float2int_rn(D[4][cc]) << 16) +
-                                        ((long long)__float2int_rn(D[5][cc]) << 8) + (long long)__float2int_rn(D[6][cc]);
-                    const double v = fma((double)L, 0x1p-48, (double)H * 0x1p-16);
-                    // 2^(e + f - 16) from its exponent bits when that is a normal double
-                    const int x = e + fb[(int64_t)m * nmax + j] - 16;
-                    if (x > -1023 && x < 1024) crow[j] = fma(v, __longlong_as_double((long long)(x + 1023) << 52), crow[j]);
-                    else crow[j] += ldexp(v, x);
-                }
+            for (int cc = 0; cc < 8; ++cc) {   // C and the column exponents first, all loads in flight
+                const int j = jb + cc;
+                on[cc] = j < md.ns && (j < k0 || j >= k0 + nb);
+                cv[cc] = on[cc] ? crow[j] : 0.0;
+                fe[cc] = on[cc] ? fb[(int64_t)m * nmax + j] : 0;
+            }
+#pragma unroll
+            for (int cc = 0; cc < 8; ++cc) {
+                if (!on[cc]) continue;
+                // The class sums are exact integers below 2^22: combine them in 64-bit
+                // integer arithmetic, H = D0 2^16 + D1 2^8 + D2 and L = D3 2^24 + D4 2^16 +
+                // D5 2^8 + D6, both exact as doubles, so that
+                // 2^16 sum_d D_d 2^-8d = H + L 2^-32 with one rounding.
+                const long long H = ((long long)__float2int_rn(D[0][cc]) << 16) +
+                                    ((long long)__float2int_rn(D[1][cc]) << 8) + (long long)__float2int_rn(D[2][cc]);
+                const long long L = ((long long)__float2int_rn(D[3][cc]) << 24) +
+                                    ((long long)__float2int_rn(D[4][cc]) << 16) +
+                                    ((long long)__float2int_rn(D[5][cc]) << 8) + (long long)__float2int_rn(D[6][cc]);
+                const double v = fma((double)L, 0x1p-32, (double)H);
+                // times 2^(e + f - 32) from its exponent bits when that is a normal double
+                const int x = e + fe[cc] - 32;
+                const int j = jb + cc;
+                if (x > -1023 && x < 1024) crow[j] = fma(v, __longlong_as_double((long long)(x + 1023) << 52), cv[cc]);
+                else crow[j] = cv[cc] + ldexp(v, x);
             }
         }
         // every thread's tensor-memory reads complete before the next products overwrite the accumulators
